@@ -1,0 +1,214 @@
+"""Pins of the oracle's source model and detector readout (Sec. III.B).
+
+* discrete Gauss law: eps div E^N at every interior node equals the charge the
+  moving shower has carried there, sum_n qbar^{n+1/2} w_ij [S(z_k - z^{n+1}) -
+  S(z_k - z^n)] / dx^3 (S = linear charge-assignment hat), for an asymmetric
+  lateral table so that a transposed or mirrored index fails;
+* linearity in the charge and zero field without a source;
+* the detector readout of a uniform field;
+* the shower-profile and lateral tables against their closed forms, and the
+  Gaussian fit of the Greisen profile at 10 TeV against the paper's l ~ 2 m.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from physics import EPS0, cic_hat, nkg_norm
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _asym_lateral(L, seed=3):
+    rng = np.random.default_rng(seed)
+    w = rng.uniform(0.1, 1.0, size=(2 * L + 1) ** 2)
+    return w / w.sum()
+
+
+def _table_profile(z0, bin_dz, q, z):
+    u = (z - z0) / bin_dz
+    if u < 0 or u > q.size - 1:
+        return 0.0
+    b = min(int(math.floor(u)), q.size - 2)
+    t = u - b
+    return q[b] * (1 - t) + q[b + 1] * t
+
+
+@pytest.mark.parametrize("boundary,npml,v_frac", [(oracle.PEC, 0, 1.0), (oracle.MUR1, 0, 0.7),
+                                                  (oracle.CPML, 6, 1.0), (oracle.PEC, 0, 2.3)])
+def test_gauss_law_matches_carried_charge(boundary, npml, v_frac):
+    nx, ny, nz = 24, 22, 40
+    dx = 0.02
+    dt = W.courant_dt(dx, W.EPS_R_ICE)
+    o = oracle.Oracle(nx, ny, nz, dx, dt, W.EPS_R_ICE, boundary, npml)
+    L = 2
+    w = _asym_lateral(L)
+    z0 = (npml + 3) * dx + 0.37 * dx
+    bin_dz = dx / 3
+    nb = 90
+    rng = np.random.default_rng(11)
+    q = -1e-9 * rng.uniform(0.2, 1.0, size=nb)   # a rough profile: charge created every step
+    v = v_frac * W.C0
+    o.set_shower(q, z0, bin_dz, v, w, L)
+    nsteps = 70
+    o.step(nsteps)
+    Ex, Ey, Ez = o.field(0), o.field(1), o.field(2)
+    eps = W.EPS_R_ICE * EPS0
+    div = np.zeros((nz + 1, ny + 1, nx + 1))
+    div[1:nz, 1:ny, 1:nx] = (
+        (Ex[1:nz, 1:ny, 1:nx] - Ex[1:nz, 1:ny, 0:nx - 1]) +
+        (Ey[1:nz, 1:ny, 1:nx] - Ey[1:nz, 0:ny - 1, 1:nx]) +
+        (Ez[1:nz, 1:ny, 1:nx] - Ez[0:nz - 1, 1:ny, 1:nx])) / dx
+    rho = np.zeros_like(div)
+    ic, jc = nx // 2, ny // 2
+    zk = np.arange(nz + 1) * dx
+    for n in range(nsteps):
+        za, zb = z0 + v * n * dt, z0 + v * (n + 1) * dt
+        qb = _table_profile(z0, bin_dz, q, z0 + v * (n + 0.5) * dt)
+        col = qb * (cic_hat((zk - zb) / dx) - cic_hat((zk - za) / dx)) / dx ** 3
+        for dj in range(-L, L + 1):
+            for di in range(-L, L + 1):
+                rho[:, jc + dj, ic + di] += w[(dj + L) * (2 * L + 1) + (di + L)] * col
+    # interior nodes: away from the outer faces and, with a CPML, outside its
+    # slabs (the stretched curl there does not conserve the plain divergence)
+    lo = max(1, npml + 1)
+    sl = (slice(lo, nz - lo + 1), slice(lo, ny - lo + 1), slice(lo, nx - lo + 1))
+    scale = np.abs(rho).max()
+    assert scale > 0
+    err = np.abs(eps * div[sl] - rho[sl]).max()
+    assert err < 1e-10 * scale, err / scale
+
+
+def test_no_source_no_field_and_linearity():
+    w = W.parity96(n=28, steps=60, n_probes=4)
+    o0 = oracle.Oracle(w.nx, w.ny, w.nz, w.dx, w.dt, w.eps_r, w.boundary)
+    o0.set_probes(w.probes_xyz, w.steps)
+    o0.step(w.steps)
+    assert np.all(o0.probes() == 0.0)
+    assert all(np.all(o0.field(c) == 0.0) for c in range(6))
+    a = oracle.from_workload(w)
+    a.step(w.steps)
+    q, lw = oracle.tables(w)
+    b = oracle.Oracle(w.nx, w.ny, w.nz, w.dx, w.dt, w.eps_r, w.boundary)
+    b.set_shower(2.5 * q, w.z0, w.bin_dz, w.v, lw, w.lateral["L"])
+    b.set_probes(w.probes_xyz, w.steps)
+    b.step(w.steps)
+    ta, tb = a.probes(), b.probes()
+    assert np.abs(ta).max() > 0
+    assert np.allclose(tb, 2.5 * ta, rtol=1e-12, atol=1e-12 * np.abs(tb).max())
+
+
+def test_mirror_symmetry_of_axisymmetric_source():
+    """A lateral table symmetric under x <-> y gives Ez(x, y) = Ez(y, x) and
+    Ex(i+1/2, j) = Ey(j, i+1/2) (same stencil, mirrored)."""
+    w = W.parity96(n=30, steps=80, n_probes=2)
+    o = oracle.from_workload(w)
+    o.step(w.steps)
+    Ez, Ex, Ey = o.field(2), o.field(0), o.field(1)
+    # the axis is node (15, 15): the transposed grid is the mirrored one
+    assert np.abs(Ez).max() > 0
+    assert np.allclose(Ez, np.swapaxes(Ez, 1, 2), rtol=0, atol=1e-9 * np.abs(Ez).max())
+    assert np.allclose(Ex, np.swapaxes(Ey, 1, 2), rtol=0, atol=1e-9 * np.abs(Ex).max())
+
+
+def test_probe_readout_of_uniform_field():
+    nx, ny, nz = 20, 18, 16
+    dx = 0.02
+    dt = W.courant_dt(dx, W.EPS_R_ICE)
+    o = oracle.Oracle(nx, ny, nz, dx, dt, W.EPS_R_ICE, oracle.PEC)
+    a, b, c = 1.5, -0.75, 2.25
+    from physics import live_masks
+    m = live_masks(nx, ny, nz)
+    for comp, val in ((0, a), (1, b), (2, c)):
+        o.set_field(comp, np.where(m[comp], val, 0.0))
+    nodes = [(5, 6, 7), (14, 4, 8), (10, 9, 5), (3, 12, 9)]
+    o.set_probes(np.array(nodes, float) * dx, 1)
+    o.step(1)
+    tr = o.probes()[:, 0, :]
+    for p, (i, j, k) in enumerate(nodes):
+        X, Y = (i - nx // 2) * dx, (j - ny // 2) * dx
+        r = math.hypot(X, Y)
+        assert tr[p, 0] == pytest.approx(c, rel=1e-13)
+        # E_r about the axis; a detector on the axis reads E_r = 0
+        er = (X * a + Y * b) / r if r > 0 else 0.0
+        assert tr[p, 1] == pytest.approx(er, rel=1e-12, abs=1e-300)
+
+
+def test_probe_outside_interior_rejected():
+    o = oracle.Oracle(20, 20, 20, 0.02, 1e-11, W.EPS_R_ICE, oracle.CPML, 5)
+    with pytest.raises(ValueError):
+        o.set_probes([[5 * 0.02, 10 * 0.02, 10 * 0.02]], 4)
+    o.set_probes([[6 * 0.02, 10 * 0.02, 10 * 0.02]], 4)
+
+
+# ---- tables --------------------------------------------------------------
+
+def test_greisen_maximum_closed_form():
+    """The Greisen profile peaks at t = beta0 = ln(E0/Ec), where s = 1 and
+    N = 0.31 exp(beta0) / sqrt(beta0)."""
+    for E0 in (1e13, 1e16, 1e18):
+        b0 = math.log(E0 / W.E_CRIT_ICE_EV)
+        t = np.linspace(b0 - 0.05, b0 + 0.05, 2001)
+        N = np.array([oracle.greisen(x, E0, W.E_CRIT_ICE_EV) for x in t])
+        assert abs(t[N.argmax()] - b0) < 1e-4
+        assert oracle.greisen(b0, E0, W.E_CRIT_ICE_EV) == pytest.approx(0.31 / math.sqrt(b0) * math.exp(b0), rel=1e-12)
+
+
+def test_greisen_gaussian_width_matches_paper():
+    """Sec. III.B: the Gaussian fit of the profile at E0 = 10 TeV in ice has
+    l ~ 2 m.  The rms length of the Greisen profile with the ice radiation length
+    lands within 25 % of it."""
+    g = json.load(open(os.path.join(GOLDEN, "paper_values.json")))
+    item = g["gaussian_fit_length_10TeV_ice"]
+    t = np.linspace(1e-6, 80, 160001)
+    N = np.array([oracle.greisen(x, item["E0_eV"], W.E_CRIT_ICE_EV) for x in t])
+    m = (N * t).sum() / N.sum()
+    l = math.sqrt((N * (t - m) ** 2).sum() / N.sum()) * W.X0_ICE_M
+    assert abs(l - item["l_m"]) < 0.25 * item["l_m"]
+
+
+def test_profile_tables_and_charge_excess():
+    g = json.load(open(os.path.join(GOLDEN, "paper_values.json")))
+    frac = g["charge_excess_fraction"]["value"]
+    assert frac == W.CHARGE_EXCESS
+    q = oracle.profile_greisen(0.3, 0.01, 3000, 1e17, W.E_CRIT_ICE_EV, W.X0_ICE_M, frac)
+    t = np.arange(3000) * 0.01 / W.X0_ICE_M
+    N = np.array([oracle.greisen(x, 1e17, W.E_CRIT_ICE_EV) for x in t])
+    assert np.allclose(q, -1.602176634e-19 * frac * N, rtol=1e-14, atol=0)
+    # Gaussian table (eq. showerModel)
+    qg = oracle.profile_gaussian(0.0, 0.005, 400, 0.96, 0.25, -1e-9)
+    assert qg[192] == pytest.approx(-1e-9)
+    assert qg[192 + 50] == pytest.approx(-1e-9 * math.exp(-0.5), rel=1e-12)
+    # Gaisser-Hillas: peak N_max at z_max, zero before z_1
+    qh = oracle.profile_gh(0.0, 0.01, 2001, [2.0], [6.0], [0.6], [3e8], frac)
+    assert qh[600] == pytest.approx(-1.602176634e-19 * frac * 3e8, rel=1e-12)
+    assert np.all(qh[:201] == 0.0)
+    assert np.argmin(qh) == 600
+
+
+def test_lateral_tables():
+    w = oracle.lateral_gaussian(4, 1.0).reshape(9, 9)
+    assert w.sum() == pytest.approx(1.0)
+    assert w[4, 5] / w[4, 4] == pytest.approx(math.exp(-0.5))
+    assert np.allclose(w, w.T) and np.allclose(w, w[::-1, ::-1])
+    # NKG: the fraction of the analytic density inside r_cut, cell-averaged
+    dx, rM, s = 0.02, 0.10, 1.0
+    L = 15
+    wn = oracle.lateral_nkg(L, dx, rM, s, 4, 3 * rM).reshape(2 * L + 1, 2 * L + 1)
+    assert wn.sum() == pytest.approx(1.0)
+    assert np.allclose(wn, wn.T) and np.allclose(wn, wn[::-1, :])
+    # ring weights follow 2 pi r rho(r) dr of the normalised density
+    from scipy.integrate import quad
+    C = nkg_norm(s)
+    dens = lambda x: 2 * math.pi * x * C * x ** (s - 2) * (1 + x) ** (s - 4.5)
+    inside = quad(dens, 0, 3.0)[0]
+    inner = quad(dens, 0, 1.0)[0] / inside
+    ii, jj = np.meshgrid(np.arange(-L, L + 1), np.arange(-L, L + 1))
+    rr = np.hypot(ii, jj) * dx
+    # nodes whose cell lies well inside r_M carry about that fraction
+    frac_model = wn[rr < rM].sum()
+    assert abs(frac_model - inner) < 0.06
