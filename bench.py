@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Throughput of the 3D Yee FDTD near-field path on GB300.
+
+One bench "step" is one leapfrog step of the whole hot path over the grid:
+H-curl update, E-curl update with the moving shower's current, CPML, detector
+readout.  The workload is the 384 x 384 x 1536-cell ice grid (dx = 2 cm,
+10-cell CPML, Greisen shower of seeded energy, NKG lateral spread, 64
+detectors at r = 1-5 m).  Metric: Gcell-updates/s = cells x steps / time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) each rank runs an independent replica (its own seeded
+shower) on its own GPU; there is no data-path communication.  Rank 0 prints
+one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def bytes_per_cell(w) -> float:
+    """Compulsory HBM bytes per cell-update: six float32 components read and
+    written once (48 B), plus the CPML memory (4 psi per slab cell per axis,
+    each read and written, 8 B) averaged over the grid."""
+    b = 48.0
+    if w.boundary == W.CPML:
+        P = w.npml
+        W_ = 2 * P + 1
+        slab = (W_ * w.ny * w.nz + w.nx * W_ * w.nz + w.nx * w.ny * W_)
+        b += 4 * 8.0 * slab / w.cells
+    return b
+
+
+def hbm_peak():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1001_5341_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_name, workload_name):
+    """DRAM bytes per cell-update from a committed ncu capture of this kernel,
+    or None when none exists or the kernel sources changed since."""
+    try:
+        with open(TRAFFIC) as f:
+            rec = json.load(f).get(kernel_name)
+    except Exception:
+        return None
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_cell")
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1001_5341_gb300 as fd
+
+    # each replica draws its own shower; rank 0 runs the named seed
+    w = W.greisen384(seed=2002 + rank, steps=args.warmup + args.steps)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = fd.Simulation.from_workload(w, max_steps=args.warmup + args.steps, stream=stream)
+        sim.step(args.warmup)
+        sim.sync()
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.3)
+        l0 = sim.launches
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sim.timing_begin(4 * args.steps)
+        ev0.record(stream)
+        sim.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        kern_ms, kern_launches = sim.timing_end()
+        launches = sim.launches - l0
+        ms = ev0.elapsed_time(ev1)
+        clk = clocks.stop()
+        try:
+            sim.energy()   # stability check after the timed region
+            stable = True
+        except fd.FdtdError:
+            stable = False
+
+        # end to end through the public API with host buffers: upload the
+        # shower and detector tables, step, read the traces back to the host
+        q, lw = fd.tables(w)
+        xyz = np.ascontiguousarray(w.probes_xyz)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.reset()
+        sim.set_shower(q, w.z0, w.bin_dz, w.v, lw, w.lateral["L"])
+        sim.set_probes(xyz, args.steps)
+        sim.step(args.steps)
+        tr = sim.probes()
+        t1 = time.perf_counter()
+        e2e_s = t1 - t0
+        h2d = q.nbytes + lw.nbytes + xyz.nbytes
+        d2h = tr.nbytes
+        kernel_name = sim.kernel_name
+        sim.close()
+
+    t = torch.tensor([ms, e2e_s * 1e3], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max, e2e_ms_max = float(t[0]), float(t[1])
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return None
+
+    cells = w.cells
+    value = ws * cells * args.steps / (ms_max * 1e-3) / 1e9
+    b = bytes_per_cell(w)
+    peak, peak_kind = hbm_peak()
+    achieved = b * cells * args.steps / (kern_ms * 1e-3) / 1e9 if kern_ms > 0 else None
+    traffic = ncu_traffic(kernel_name, w.name)
+    line = {
+        "metric": "Gcell-updates/s", "value": round(value, 3), "unit": "Gcell/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {**w.describe(), "seed": 2002, "inputs_vs_l2": "fields 11.8 GB >> 129 MB L2",
+                   "parallelism": f"replicas{ws}" if ws > 1 else "single-gpu",
+                   "replica_seeds": "2002 + rank"},
+        "roofline": {"bound": "hbm", "kernel": kernel_name,
+                     "achieved": round(achieved, 1) if achieved else None,
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4) if achieved else None,
+                     "bytes_per_cell_alg": round(b, 3),
+                     "traffic": (traffic * cells if traffic else None),
+                     "kernel_ms_per_step": round(kern_ms / args.steps, 5),
+                     "kernel_launches_timed": kern_launches},
+        "e2e": {"value": round(ws * cells * args.steps / (e2e_ms_max * 1e-3) / 1e9, 3),
+                "unit": "Gcell/s", "h2d_bytes_per_step": round(h2d / args.steps, 1),
+                "d2h_bytes_per_step": round(d2h / args.steps, 1),
+                "what": "reset + set_shower + set_probes (host tables) + step(K) + probes() to host"},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "stable": stable,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget)
+    if ws > 1:
+        dist.destroy_process_group()
+    return line
+
+
+def _oracle_sample(w, target_cells):
+    """The workload's physics (dx, dt, CPML, shower, lateral spread) on a
+    sub-grid of about target_cells cells with the same aspect ratio."""
+    f = (target_cells / w.cells) ** (1.0 / 3.0)
+    min_n = 2 * w.npml + 8
+    nx = max(min_n, int(w.nx * f) // 2 * 2)
+    ny = max(min_n, int(w.ny * f) // 2 * 2)
+    nz = max(min_n, int(w.nz * f) // 2 * 2)
+    return W.greisen384(nx=nx, ny=ny, nz=nz, npml=w.npml, steps=1, n_probes=8,
+                        r_lo=0.1, r_hi=min(0.3, (min(nx, ny) // 2 - w.npml - 2) * w.dx * 0.9),
+                        E0=w.profile["E0_eV"])
+
+
+def _omp_threads():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
+def cpu_baseline(w, budget_s=15.0):
+    """The FP64 oracle as it stands, on the host cores, over a bounded sample."""
+    import oracle
+    t0 = time.perf_counter()
+    sw = _oracle_sample(w, 4.0e6)
+    o = oracle.from_workload(sw, max_steps=100000)
+    o.step(1)
+    done = 0
+    t1 = time.perf_counter()
+    while True:
+        o.step(1)
+        done += 1
+        if time.perf_counter() - t1 > budget_s:
+            break
+    el = time.perf_counter() - t1
+    return {"value": round(sw.cells * done / el / 1e9, 5), "unit": "Gcell/s", "cores": _omp_threads(),
+            "kind": "oracle",
+            "sample": f"{sw.nx}x{sw.ny}x{sw.nz} cells of the same physics (CPML {sw.npml}, Greisen "
+                      f"E0={w.profile['E0_eV']:.3g} eV, NKG lateral), {done} steps, "
+                      f"{el:.1f} s (setup {t1 - t0:.1f} s excluded)"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    w = W.greisen384()
+    # size the per-step sample so that W + K oracle steps take about two minutes
+    cal = _oracle_sample(w, 2.0e5)
+    o = oracle.from_workload(cal, max_steps=100)
+    o.step(1)
+    t = time.perf_counter()
+    o.step(3)
+    rate = 3 * cal.cells / (time.perf_counter() - t)
+    del o
+    per_step_s = min(2.0, 120.0 / max(1, args.steps + args.warmup))
+    sw = _oracle_sample(w, max(5e4, rate * per_step_s))
+    o = oracle.from_workload(sw, max_steps=args.warmup + args.steps)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    v = sw.cells * args.steps / el / 1e9
+    sample = (f"each step: one oracle step on {sw.nx}x{sw.ny}x{sw.nz} cells of the same physics "
+              f"(CPML {sw.npml}, Greisen shower, NKG lateral)")
+    return {"impl": "reference", "metric": "Gcell-updates/s", "value": round(v, 6), "unit": "Gcell/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(el * 1e3 / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {**w.describe(), "seed": 2002},
+            "cpu_baseline": {"value": round(v, 6), "unit": "Gcell/s", "cores": _omp_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 6), "unit": "Gcell/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

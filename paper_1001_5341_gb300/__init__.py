@@ -1,0 +1,283 @@
+"""Python binding of libfdtd_gb300.so (GB300 near-field FDTD of Askaryan pulses).
+
+Argument marshalling only: every step of the field update, the source deposit,
+the boundary and the detector readout runs in the library's CUDA kernels.  The
+functions keep the C names of ``include/fdtd.h``; ``Simulation`` wraps a handle.
+PyTorch is used for device buffers and streams only.  There is no CPU fallback:
+importing this package fails if the compiled library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libfdtd_gb300.so")
+
+FDTD_PEC, FDTD_MUR1, FDTD_CPML = 0, 1, 2
+FDTD_OK = 0
+STATUS = {0: "FDTD_OK", -1: "FDTD_ERR_ARG", -2: "FDTD_ERR_CFL", -3: "FDTD_ERR_OOM",
+          -4: "FDTD_ERR_UNSTABLE", -5: "FDTD_ERR_CUDA", -6: "FDTD_ERR_TIMEOUT",
+          -7: "FDTD_ERR_CAPACITY"}
+COMPONENTS = ("Ex", "Ey", "Ez", "Hx", "Hy", "Hz")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                      "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+
+_d, _i, _vp, _sz = C.c_double, C.c_int, C.c_void_p, C.c_size_t
+_pd, _pf, _pi = C.POINTER(C.c_double), C.POINTER(C.c_float), C.POINTER(C.c_int)
+_pi64 = C.POINTER(C.c_int64)
+
+lib = C.CDLL(LIB_PATH)
+_SIGS = {
+    "fdtd_create": (_i, [C.POINTER(_vp), _i, _i, _i, _d, _d, _d, _i, _i, _vp]),
+    "fdtd_destroy": (None, [_vp]),
+    "fdtd_set_shower": (_i, [_vp, _pd, _i, _d, _d, _i, _d, _pd, _i]),
+    "fdtd_clear_shower": (_i, [_vp]),
+    "fdtd_set_probes": (_i, [_vp, _pd, _i, _i]),
+    "fdtd_probe_nodes": (_i, [_vp, _pi]),
+    "fdtd_step": (_i, [_vp, _i]),
+    "fdtd_sync": (_i, [_vp]),
+    "fdtd_steps_done": (_i, [_vp, _pi64]),
+    "fdtd_probes": (_i, [_vp, _vp, _i]),
+    "fdtd_fields": (_i, [_vp, _i, _vp, _i]),
+    "fdtd_set_field": (_i, [_vp, _i, _vp, _i]),
+    "fdtd_reset": (_i, [_vp]),
+    "fdtd_energy": (_i, [_vp, _pd]),
+    "fdtd_save_state": (_i, [_vp, _vp, C.POINTER(_sz)]),
+    "fdtd_load_state": (_i, [_vp, _vp, _sz]),
+    "fdtd_timing_begin": (_i, [_vp, _i]),
+    "fdtd_timing_end": (_i, [_vp, _pd, _pi]),
+    "fdtd_launch_count": (_i, [_vp, _pi64]),
+    "fdtd_kernel_name": (C.c_char_p, [_vp]),
+    "fdtd_strerror": (C.c_char_p, [_i]),
+    "fdtd_profile_gaussian": (_i, [_d, _d, _i, _d, _d, _d, _pd]),
+    "fdtd_profile_greisen": (_i, [_d, _i, _d, _d, _d, _d, _pd]),
+    "fdtd_profile_gaisser_hillas": (_i, [_d, _d, _i, _i, _pd, _pd, _pd, _pd, _d, _pd]),
+    "fdtd_lateral_gaussian": (_i, [_i, _d, _pd]),
+    "fdtd_lateral_nkg": (_i, [_i, _d, _d, _d, _i, _d, _pd]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+    globals()[_name] = _f
+
+
+class FdtdError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({fdtd_strerror(code).decode()})")
+
+
+def check(code: int, where: str = "fdtd") -> int:
+    if code != FDTD_OK:
+        raise FdtdError(code, where)
+    return code
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_pd)
+
+
+# ---- shower tables ---------------------------------------------------------
+
+def profile_gaussian(z0, bin_dz, n_bins, z_peak, l, q_max):
+    out = np.zeros(n_bins)
+    check(fdtd_profile_gaussian(z0, bin_dz, n_bins, z_peak, l, q_max, _dp(out)), "profile_gaussian")
+    return out
+
+
+def profile_greisen(bin_dz, n_bins, E0, Ec, X0, frac):
+    out = np.zeros(n_bins)
+    check(fdtd_profile_greisen(bin_dz, n_bins, E0, Ec, X0, frac, _dp(out)), "profile_greisen")
+    return out
+
+
+def profile_gaisser_hillas(z0, bin_dz, n_bins, z1, zmax, lam, nmax, frac):
+    a = [np.ascontiguousarray(x, dtype=np.float64) for x in (z1, zmax, lam, nmax)]
+    out = np.zeros(n_bins)
+    check(fdtd_profile_gaisser_hillas(z0, bin_dz, n_bins, a[0].size, *[_dp(x) for x in a], frac,
+                                      _dp(out)), "profile_gaisser_hillas")
+    return out
+
+
+def lateral_gaussian(L, sigma_cells):
+    out = np.zeros((2 * L + 1) ** 2)
+    check(fdtd_lateral_gaussian(L, sigma_cells, _dp(out)), "lateral_gaussian")
+    return out
+
+
+def lateral_nkg(L, dx, r_moliere, age, nsub, r_cut):
+    out = np.zeros((2 * L + 1) ** 2)
+    check(fdtd_lateral_nkg(L, dx, r_moliere, age, nsub, r_cut, _dp(out)), "lateral_nkg")
+    return out
+
+
+def tables(w):
+    """Profile and lateral tables of a ``workloads.Workload`` from the library's
+    own host generators."""
+    p, lt = w.profile, w.lateral
+    if p["kind"] == "gaussian":
+        q = profile_gaussian(w.z0, w.bin_dz, w.n_bins, p["z_peak"], p["l"], p["q_max"])
+    elif p["kind"] == "greisen":
+        q = profile_greisen(w.bin_dz, w.n_bins, p["E0_eV"], p["Ec_eV"], p["X0_m"], p["frac"])
+    elif p["kind"] == "gh":
+        q = profile_gaisser_hillas(w.z0, w.bin_dz, w.n_bins, p["z1"], p["zmax"], p["lam"],
+                                   p["nmax"], p["frac"])
+    elif p["kind"] == "table":
+        q = np.asarray(p["q"], dtype=np.float64)
+    else:
+        raise ValueError(p["kind"])
+    if lt["kind"] == "gaussian":
+        lw = lateral_gaussian(lt["L"], lt["sigma_cells"])
+    elif lt["kind"] == "nkg":
+        lw = lateral_nkg(lt["L"], w.dx, lt["r_moliere"], lt["age"], lt["nsub"], lt["r_cut"])
+    elif lt["kind"] == "table":
+        lw = np.asarray(lt["w"], dtype=np.float64)
+    else:
+        raise ValueError(lt["kind"])
+    return q, lw
+
+
+# ---- simulation handle -------------------------------------------------------
+
+class Simulation:
+    """One simulation on the current CUDA device.  ``stream`` is a
+    ``torch.cuda.Stream`` (or a raw cudaStream_t int); default: torch's current
+    stream."""
+
+    def __init__(self, nx, ny, nz, dx, dt, eps_r, boundary=FDTD_MUR1, npml=0, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        raw = stream if isinstance(stream, int) else stream.cuda_stream
+        h = _vp()
+        check(fdtd_create(C.byref(h), nx, ny, nz, dx, dt, eps_r, boundary, npml, _vp(raw)),
+              "fdtd_create")
+        self.h = h
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.dx, self.dt, self.eps_r = dx, dt, eps_r
+        self.boundary, self.npml = boundary, npml
+        self.np, self.max_steps = 0, 0
+
+    @classmethod
+    def from_workload(cls, w, max_steps: Optional[int] = None, stream=None):
+        s = cls(w.nx, w.ny, w.nz, w.dx, w.dt, w.eps_r, w.boundary, w.npml, stream=stream)
+        q, lw = tables(w)
+        s.set_shower(q, w.z0, w.bin_dz, w.v, lw, w.lateral["L"])
+        s.set_probes(w.probes_xyz, w.steps if max_steps is None else max_steps)
+        return s
+
+    def close(self):
+        if getattr(self, "h", None):
+            fdtd_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def shape(self):
+        return (self.nz + 1, self.ny + 1, self.nx + 1)
+
+    def set_shower(self, q, z0, bin_dz, v, w, L, axis=2):
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        check(fdtd_set_shower(self.h, _dp(q), q.size, z0, bin_dz, axis, v, _dp(w), L), "fdtd_set_shower")
+
+    def clear_shower(self):
+        check(fdtd_clear_shower(self.h), "fdtd_clear_shower")
+
+    def set_probes(self, xyz, max_steps):
+        xyz = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
+        check(fdtd_set_probes(self.h, _dp(xyz), xyz.shape[0], max_steps), "fdtd_set_probes")
+        self.np, self.max_steps = xyz.shape[0], max_steps
+
+    def probe_nodes(self):
+        out = np.zeros((self.np, 3), dtype=np.int32)
+        check(fdtd_probe_nodes(self.h, out.ctypes.data_as(_pi)), "fdtd_probe_nodes")
+        return out
+
+    def step(self, n=1):
+        check(fdtd_step(self.h, n), "fdtd_step")
+
+    def sync(self):
+        check(fdtd_sync(self.h), "fdtd_sync")
+
+    @property
+    def steps_done(self):
+        v = C.c_int64()
+        check(fdtd_steps_done(self.h, C.byref(v)), "fdtd_steps_done")
+        return v.value
+
+    def probes(self, out=None):
+        """Traces [n_probes][max_steps][2] (Ez, E_r): numpy, or into a CUDA tensor."""
+        if out is not None:
+            check(fdtd_probes(self.h, _vp(out.data_ptr()), 1), "fdtd_probes")
+            return out
+        a = np.zeros((self.np, self.max_steps, 2), dtype=np.float32)
+        check(fdtd_probes(self.h, _vp(a.ctypes.data), 0), "fdtd_probes")
+        return a
+
+    def field(self, comp, out=None):
+        c = COMPONENTS.index(comp) if isinstance(comp, str) else comp
+        if out is not None:
+            check(fdtd_fields(self.h, c, _vp(out.data_ptr()), 1), "fdtd_fields")
+            return out
+        a = np.zeros(self.shape, dtype=np.float32)
+        check(fdtd_fields(self.h, c, _vp(a.ctypes.data), 0), "fdtd_fields")
+        return a
+
+    def set_field(self, comp, arr):
+        c = COMPONENTS.index(comp) if isinstance(comp, str) else comp
+        a = np.ascontiguousarray(arr, dtype=np.float32)
+        assert a.shape == self.shape
+        check(fdtd_set_field(self.h, c, _vp(a.ctypes.data), 0), "fdtd_set_field")
+
+    def reset(self):
+        check(fdtd_reset(self.h), "fdtd_reset")
+
+    def energy(self):
+        e = C.c_double()
+        check(fdtd_energy(self.h, C.byref(e)), "fdtd_energy")
+        return e.value
+
+    def save_state(self) -> bytes:
+        n = _sz(0)
+        check(fdtd_save_state(self.h, None, C.byref(n)), "fdtd_save_state")
+        buf = C.create_string_buffer(n.value)
+        check(fdtd_save_state(self.h, C.cast(buf, _vp), C.byref(n)), "fdtd_save_state")
+        return buf.raw
+
+    def load_state(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        check(fdtd_load_state(self.h, C.cast(buf, _vp), len(blob)), "fdtd_load_state")
+
+    def timing_begin(self, max_launches):
+        check(fdtd_timing_begin(self.h, max_launches), "fdtd_timing_begin")
+
+    def timing_end(self):
+        ms, n = C.c_double(), C.c_int()
+        check(fdtd_timing_end(self.h, C.byref(ms), C.byref(n)), "fdtd_timing_end")
+        return ms.value, n.value
+
+    @property
+    def launches(self):
+        v = C.c_int64()
+        check(fdtd_launch_count(self.h, C.byref(v)), "fdtd_launch_count")
+        return v.value
+
+    @property
+    def kernel_name(self):
+        return fdtd_kernel_name(self.h).decode()

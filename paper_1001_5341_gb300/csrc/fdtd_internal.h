@@ -1,0 +1,131 @@
+// fdtd_internal.h -- device views and the handle of the GB300 FDTD library.
+//
+// Layout in HBM.  Each of the six components is a float32 array over the node
+// grid (nz+1) x (ny+1) x pitch, x fastest, pitch = nx+1 rounded up to 32
+// floats so that every x row starts on a 128-byte boundary.  Two complete
+// sets of the six arrays exist (ping-pong): a step reads set `cur` and writes
+// set `cur ^ 1`, so no kernel ever reads a value that the same step has
+// already overwritten.
+//
+// CPML memory is kept only in the slabs.  Per axis there are four psi arrays
+// (two for the E update, two for the H update) over the slab cells of that
+// axis: cells 0..P and N-P..N-1 (W = 2P+1 cells), stored
+//   x: [nz][ny][W]   y: [nz][W][nx]   z: [W][ny][nx]
+// so that consecutive threads along x touch consecutive floats.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <vector>
+
+#include "../../include/fdtd.h"
+
+namespace fdtd {
+
+struct Grid {
+    int nx, ny, nz;
+    int pitch;       // floats per x row
+    long long plane; // floats per z plane = (ny+1) * pitch
+    long long comp;  // floats per component = (nz+1) * plane
+};
+
+__host__ __device__ inline long long gidx(const Grid &g, int i, int j, int k) {
+    return (long long)k * g.plane + (long long)j * g.pitch + i;
+}
+
+// slab cell index of cell i on an axis with N cells and P PML cells, or -1
+__host__ __device__ inline int slab_cell(int i, int N, int P) {
+    if (P <= 0) return -1;
+    if (i <= P) return i;
+    if (i >= N - P) return i - (N - P) + (P + 1);
+    return -1;
+}
+
+struct Cpml {
+    int P, W;                 // depth, slab cells per axis (2P+1); P = 0: no CPML
+    float *psi[3][4];         // [axis][0,1 = E terms, 2,3 = H terms]
+    const float *aE[3], *bE[3], *aH[3], *bH[3]; // per position index, length n_axis
+};
+
+struct Source {
+    int active;
+    int L, ic, jc;
+    int kmin, kmax;           // Ez edges k+1/2 that may carry current
+    int nbins;
+    double z0, v, dt, dx, bin_dz;
+    double coef;              // 1 / (eps dx^2): E-increment per coulomb of charge crossing
+    const double *q;          // profile samples
+    const double *w;          // lateral weights (2L+1)^2
+};
+
+struct Probes {
+    int n, max_steps;
+    const int *ijk;           // [n][3]
+    const float *cxy;         // [n][2]: X/r, Y/r about the axis (0,0 on the axis)
+    float *trace;             // [n][max_steps][2]
+};
+
+struct TimingRec {
+    std::vector<cudaEvent_t> ev; // start/stop pairs
+    int used = 0;
+    int cap = 0;
+    bool on = false;
+};
+
+}  // namespace fdtd
+
+struct fdtd_ctx {
+    fdtd::Grid g;
+    int boundary, P;
+    double dx, dt, eps_r, eps, kE, kH, mur_m;
+    cudaStream_t stream;
+    int dev;
+
+    float *fields[2];         // two sets, each 6 * g.comp floats
+    int cur;                  // index of the set holding E^n, H^{n-1/2}
+
+    // CPML
+    float *psi_block;         // all psi arrays, one allocation
+    size_t psi_floats;
+    float *coef_block;        // aE,bE,aH,bH per axis
+    fdtd::Cpml cpml;
+
+    // source
+    double *d_q;
+    double *d_w;
+    fdtd::Source src;
+
+    // detectors
+    int np, max_steps;
+    int *d_ijk;
+    float *d_cxy;
+    float *d_trace;
+    std::vector<int> h_ijk;
+
+    // energy / stability scratch
+    double *d_partial;        // per-block partial sums
+    int partial_cap;
+    double *d_result;         // [3]: energy E, energy H, non-finite count
+
+    int64_t steps;
+    int64_t launches;
+    int status;               // sticky error
+    fdtd::TimingRec timing;
+};
+
+namespace fdtd {
+
+// kernels (kernels_basic.cu)
+void launch_update_h(const fdtd_ctx *h, cudaStream_t s);
+void launch_update_e(const fdtd_ctx *h, cudaStream_t s);
+void launch_mur(const fdtd_ctx *h, cudaStream_t s);
+void launch_probes(const fdtd_ctx *h, cudaStream_t s);
+void launch_energy(const fdtd_ctx *h, cudaStream_t s, int *launches);
+void launch_set_field(const fdtd_ctx *h, int comp, const float *compact, cudaStream_t s);
+void launch_get_field(const fdtd_ctx *h, int comp, float *compact, cudaStream_t s);
+
+// host tables (tables.cpp)
+void cpml_coefficients(int n, int P, double dx, double dt, double eps_r, float *aE, float *bE,
+                       float *aH, float *bH);
+
+}  // namespace fdtd

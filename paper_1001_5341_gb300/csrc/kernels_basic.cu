@@ -1,0 +1,342 @@
+// kernels_basic.cu -- the unfused field update (one H sweep, one E sweep) and
+// the small kernels every path shares: Mur faces, detector readout, field
+// copies, energy/stability reduction.
+//
+// The H sweep reads E^n, H^{n-1/2} from set `cur` and writes H^{n+1/2} to set
+// `cur^1`; the E sweep reads E^n from `cur` and H^{n+1/2} from `cur^1` and writes
+// E^{n+1} to `cur^1` (Yee leapfrog, Sec. III.A; curl differences as in the
+// paper's central-difference scheme).  One thread updates the up-to-six
+// components owned by one cell (i,j,k), 0 <= i < nx etc.:
+//   Hx(i,j+1/2,k+1/2) i>=1   Hy(i+1/2,j,k+1/2) j>=1   Hz(i+1/2,j+1/2,k) k>=1
+//   Ex(i+1/2,j,k) j,k>=1     Ey(i,j+1/2,k) i,k>=1     Ez(i,j,k+1/2) i,j>=1
+// Cells at i = 0 skip the components that lie on the x = 0 face (tangential
+// E, boundary owned) and the H normal to it (it drives no updated E); the
+// far faces i = nx etc. are never touched by the sweeps.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "fdtd_internal.h"
+
+namespace fdtd {
+
+__device__ __forceinline__ void cpml_term(float *psi, const float *a, const float *b, int pos,
+                                          float &d) {
+    float p = b[pos] * (*psi) + a[pos] * d;
+    *psi = p;
+    d = d + p;
+}
+
+// Ein: Ex (Ey, Ez follow at +comp); Hin, Hout: Hx (Hy, Hz follow at +comp).
+__global__ void __launch_bounds__(256) k_update_h(Grid g, const float *__restrict__ Ein,
+                                                  const float *__restrict__ Hin,
+                                                  float *__restrict__ Hout, Cpml pml, float kH) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const float *Ex = Ein, *Ey = Ein + g.comp, *Ez = Ein + 2 * g.comp;
+    long long c = gidx(g, i, j, k);
+    const int P = pml.P;
+    int lx = slab_cell(i, g.nx, P), ly = slab_cell(j, g.ny, P), lz = slab_cell(k, g.nz, P);
+    if (i >= 1) {  // Hx
+        float dy = Ez[c + g.pitch] - Ez[c];
+        float dz = Ey[c + g.plane] - Ey[c];
+        if (ly >= 0) cpml_term(pml.psi[1][2] + ((long long)k * pml.W + ly) * g.nx + i, pml.aH[1], pml.bH[1], j, dy);
+        if (lz >= 0) cpml_term(pml.psi[2][2] + ((long long)lz * g.ny + j) * g.nx + i, pml.aH[2], pml.bH[2], k, dz);
+        Hout[c] = Hin[c] - kH * (dy - dz);
+    }
+    if (j >= 1) {  // Hy
+        float dz = Ex[c + g.plane] - Ex[c];
+        float dx = Ez[c + 1] - Ez[c];
+        if (lz >= 0) cpml_term(pml.psi[2][3] + ((long long)lz * g.ny + j) * g.nx + i, pml.aH[2], pml.bH[2], k, dz);
+        if (lx >= 0) cpml_term(pml.psi[0][2] + ((long long)k * g.ny + j) * pml.W + lx, pml.aH[0], pml.bH[0], i, dx);
+        Hout[g.comp + c] = Hin[g.comp + c] - kH * (dz - dx);
+    }
+    if (k >= 1) {  // Hz
+        float dx = Ey[c + 1] - Ey[c];
+        float dy = Ex[c + g.pitch] - Ex[c];
+        if (lx >= 0) cpml_term(pml.psi[0][3] + ((long long)k * g.ny + j) * pml.W + lx, pml.aH[0], pml.bH[0], i, dx);
+        if (ly >= 0) cpml_term(pml.psi[1][3] + ((long long)k * pml.W + ly) * g.nx + i, pml.aH[1], pml.bH[1], j, dy);
+        Hout[2 * g.comp + c] = Hin[2 * g.comp + c] - kH * (dx - dy);
+    }
+}
+
+// E increment on edge (i, j, k+1/2) from the charge carried across it during
+// step n (FP64, as the integer node index k0 = floor(z/dx) must be decided in
+// the same precision as the reference arithmetic).
+__device__ __forceinline__ float source_term(const Source &s, int i, int j, int k, long long n) {
+    int di = i - s.ic, dj = j - s.jc;
+    if (di < -s.L || di > s.L || dj < -s.L || dj > s.L || k < s.kmin || k > s.kmax) return 0.0f;
+    double za = s.z0 + s.v * (double)n * s.dt;
+    double zb = s.z0 + s.v * (double)(n + 1) * s.dt;
+    // C_k(z): fraction of the charge on nodes <= k of the untruncated CIC line
+    double ua = za / s.dx, ub = zb / s.dx;
+    double ka = floor(ua), kb = floor(ub);
+    double ca = (double)k < ka ? 0.0 : ((double)k == ka ? 1.0 - (ua - ka) : 1.0);
+    double cb = (double)k < kb ? 0.0 : ((double)k == kb ? 1.0 - (ub - kb) : 1.0);
+    double dC = cb - ca;
+    if (dC == 0.0) return 0.0f;
+    double zm = s.z0 + s.v * ((double)n + 0.5) * s.dt;
+    double u = (zm - s.z0) / s.bin_dz;
+    if (!(u >= 0.0) || u > (double)(s.nbins - 1)) return 0.0f;
+    int b = (int)floor(u);
+    double qbar = b >= s.nbins - 1 ? s.q[s.nbins - 1]
+                                   : s.q[b] * (1.0 - (u - b)) + s.q[b + 1] * (u - b);
+    double wij = s.w[(dj + s.L) * (2 * s.L + 1) + (di + s.L)];
+    // -(dt/eps) J with J = -(dx/dt) qbar w dC / dx^3
+    return (float)(qbar * wij * s.coef * dC);
+}
+
+// Ein, Eout: Ex of sets cur / cur^1; Hnew: Hx of set cur^1.
+__global__ void __launch_bounds__(256) k_update_e(Grid g, const float *__restrict__ Ein,
+                                                  const float *__restrict__ Hnew,
+                                                  float *__restrict__ Eout, Cpml pml, float kE,
+                                                  Source src, long long n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const float *Hx = Hnew, *Hy = Hnew + g.comp, *Hz = Hnew + 2 * g.comp;
+    long long c = gidx(g, i, j, k);
+    const int P = pml.P;
+    int lx = slab_cell(i, g.nx, P), ly = slab_cell(j, g.ny, P), lz = slab_cell(k, g.nz, P);
+    if (j >= 1 && k >= 1) {  // Ex
+        float dy = Hz[c] - Hz[c - g.pitch];
+        float dz = Hy[c] - Hy[c - g.plane];
+        if (ly >= 0) cpml_term(pml.psi[1][0] + ((long long)k * pml.W + ly) * g.nx + i, pml.aE[1], pml.bE[1], j, dy);
+        if (lz >= 0) cpml_term(pml.psi[2][0] + ((long long)lz * g.ny + j) * g.nx + i, pml.aE[2], pml.bE[2], k, dz);
+        Eout[c] = Ein[c] + kE * (dy - dz);
+    }
+    if (i >= 1 && k >= 1) {  // Ey
+        float dz = Hx[c] - Hx[c - g.plane];
+        float dx = Hz[c] - Hz[c - 1];
+        if (lz >= 0) cpml_term(pml.psi[2][1] + ((long long)lz * g.ny + j) * g.nx + i, pml.aE[2], pml.bE[2], k, dz);
+        if (lx >= 0) cpml_term(pml.psi[0][0] + ((long long)k * g.ny + j) * pml.W + lx, pml.aE[0], pml.bE[0], i, dx);
+        Eout[g.comp + c] = Ein[g.comp + c] + kE * (dz - dx);
+    }
+    if (i >= 1 && j >= 1) {  // Ez
+        float dx = Hy[c] - Hy[c - 1];
+        float dy = Hx[c] - Hx[c - g.pitch];
+        if (lx >= 0) cpml_term(pml.psi[0][1] + ((long long)k * g.ny + j) * pml.W + lx, pml.aE[0], pml.bE[0], i, dx);
+        if (ly >= 0) cpml_term(pml.psi[1][1] + ((long long)k * pml.W + ly) * g.nx + i, pml.aE[1], pml.bE[1], j, dy);
+        float e = Ein[2 * g.comp + c] + kE * (dx - dy);
+        if (src.active) e += source_term(src, i, j, k, n);
+        Eout[2 * g.comp + c] = e;
+    }
+}
+
+void launch_update_h(const fdtd_ctx *h, cudaStream_t s) {
+    const Grid &g = h->g;
+    dim3 blk(32, 8, 1), grd((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+    const float *in = h->fields[h->cur];
+    float *out = h->fields[h->cur ^ 1];
+    k_update_h<<<grd, blk, 0, s>>>(g, in, in + 3 * g.comp, out + 3 * g.comp, h->cpml, (float)h->kH);
+}
+
+void launch_update_e(const fdtd_ctx *h, cudaStream_t s) {
+    const Grid &g = h->g;
+    dim3 blk(32, 8, 1), grd((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+    const float *in = h->fields[h->cur];
+    float *out = h->fields[h->cur ^ 1];
+    k_update_e<<<grd, blk, 0, s>>>(g, in, out + 3 * g.comp, out, h->cpml, (float)h->kE, h->src, h->steps);
+}
+
+// First-order Mur on the tangential E of face f (0..5 = x-, x+, y-, y+, z-, z+):
+// E0^{n+1} = E1^n + m (E1^{n+1} - E0^n); edge entries are not touched (PEC).
+__global__ void k_mur(Grid g, const float *__restrict__ Eold, float *__restrict__ Enew, float m) {
+    int f = blockIdx.z;
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    int b = blockIdx.y * blockDim.y + threadIdx.y;
+    int ax = f >> 1, hi = f & 1;
+    if (ax == 0) {  // (a, b) = (j, k)
+        int i0 = hi ? g.nx : 0, i1 = hi ? g.nx - 1 : 1;
+        if (a <= g.ny && b <= g.nz) {
+            const long long o0 = gidx(g, i0, a, b), o1 = gidx(g, i1, a, b);
+            if (a <= g.ny - 1 && b >= 1 && b <= g.nz - 1) {
+                const float *eo = Eold + g.comp; float *en = Enew + g.comp;
+                en[o0] = eo[o1] + m * (en[o1] - eo[o0]);
+            }
+            if (a >= 1 && a <= g.ny - 1 && b <= g.nz - 1) {
+                const float *eo = Eold + 2 * g.comp; float *en = Enew + 2 * g.comp;
+                en[o0] = eo[o1] + m * (en[o1] - eo[o0]);
+            }
+        }
+    } else if (ax == 1) {  // (a, b) = (i, k)
+        int j0 = hi ? g.ny : 0, j1 = hi ? g.ny - 1 : 1;
+        if (a <= g.nx && b <= g.nz) {
+            const long long o0 = gidx(g, a, j0, b), o1 = gidx(g, a, j1, b);
+            if (a <= g.nx - 1 && b >= 1 && b <= g.nz - 1) {
+                const float *eo = Eold; float *en = Enew;
+                en[o0] = eo[o1] + m * (en[o1] - eo[o0]);
+            }
+            if (a >= 1 && a <= g.nx - 1 && b <= g.nz - 1) {
+                const float *eo = Eold + 2 * g.comp; float *en = Enew + 2 * g.comp;
+                en[o0] = eo[o1] + m * (en[o1] - eo[o0]);
+            }
+        }
+    } else {  // (a, b) = (i, j)
+        int k0 = hi ? g.nz : 0, k1 = hi ? g.nz - 1 : 1;
+        if (a <= g.nx && b <= g.ny) {
+            const long long o0 = gidx(g, a, b, k0), o1 = gidx(g, a, b, k1);
+            if (a <= g.nx - 1 && b >= 1 && b <= g.ny - 1) {
+                const float *eo = Eold; float *en = Enew;
+                en[o0] = eo[o1] + m * (en[o1] - eo[o0]);
+            }
+            if (a >= 1 && a <= g.nx - 1 && b <= g.ny - 1) {
+                const float *eo = Eold + g.comp; float *en = Enew + g.comp;
+                en[o0] = eo[o1] + m * (en[o1] - eo[o0]);
+            }
+        }
+    }
+}
+
+void launch_mur(const fdtd_ctx *h, cudaStream_t s) {
+    const Grid &g = h->g;
+    int amax = (g.nx > g.ny ? g.nx : g.ny) + 1;
+    int bmax = (g.ny > g.nz ? g.ny : g.nz) + 1;
+    if (g.nz + 1 > bmax) bmax = g.nz + 1;
+    dim3 blk(32, 8, 1), grd((amax + 31) / 32, (bmax + 7) / 8, 6);
+    k_mur<<<grd, blk, 0, s>>>(g, h->fields[h->cur], h->fields[h->cur ^ 1], (float)h->mur_m);
+}
+
+// Detector readout of E^{n+1} (set cur^1) into trace slot n.
+__global__ void k_probes(Grid g, const float *__restrict__ E, Probes p, long long slot) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= p.n) return;
+    int i = p.ijk[3 * t], j = p.ijk[3 * t + 1], k = p.ijk[3 * t + 2];
+    long long c = gidx(g, i, j, k);
+    const float *Ex = E, *Ey = E + g.comp, *Ez = E + 2 * g.comp;
+    float ex = 0.5f * (Ex[c - 1] + Ex[c]);
+    float ey = 0.5f * (Ey[c - g.pitch] + Ey[c]);
+    float ez = 0.5f * (Ez[c - g.plane] + Ez[c]);
+    float er = p.cxy[2 * t] * ex + p.cxy[2 * t + 1] * ey;
+    float *o = p.trace + ((long long)t * p.max_steps + slot) * 2;
+    o[0] = ez;
+    o[1] = er;
+}
+
+void launch_probes(const fdtd_ctx *h, cudaStream_t s) {
+    Probes p{h->np, h->max_steps, h->d_ijk, h->d_cxy, h->d_trace};
+    k_probes<<<(h->np + 127) / 128, 128, 0, s>>>(h->g, h->fields[h->cur ^ 1], p, h->steps);
+}
+
+// ---- field copies -----------------------------------------------------------
+
+// Whether node-grid entry (i,j,k) of component c is state the update keeps.
+__device__ __forceinline__ bool kept(const Grid &g, int c, int i, int j, int k, bool mur) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    switch (c) {
+    case 0: {
+        if (i > nx - 1) return false;
+        bool jin = j >= 1 && j <= ny - 1, kin = k >= 1 && k <= nz - 1;
+        return (jin && kin) || (mur && (jin || kin));
+    }
+    case 1: {
+        if (j > ny - 1) return false;
+        bool iin = i >= 1 && i <= nx - 1, kin = k >= 1 && k <= nz - 1;
+        return (iin && kin) || (mur && (iin || kin));
+    }
+    case 2: {
+        if (k > nz - 1) return false;
+        bool iin = i >= 1 && i <= nx - 1, jin = j >= 1 && j <= ny - 1;
+        return (iin && jin) || (mur && (iin || jin));
+    }
+    case 3: return i >= 1 && i <= nx - 1 && j <= ny - 1 && k <= nz - 1;
+    case 4: return i <= nx - 1 && j >= 1 && j <= ny - 1 && k <= nz - 1;
+    default: return i <= nx - 1 && j <= ny - 1 && k >= 1 && k <= nz - 1;
+    }
+}
+
+__global__ void k_set_field(Grid g, int c, const float *__restrict__ in, float *__restrict__ f,
+                            bool mur) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y, k = blockIdx.z;
+    if (i > g.nx) return;
+    long long s = ((long long)k * (g.ny + 1) + j) * (g.nx + 1) + i;
+    f[c * g.comp + gidx(g, i, j, k)] = kept(g, c, i, j, k, mur) ? in[s] : 0.0f;
+}
+
+__global__ void k_get_field(Grid g, int c, const float *__restrict__ f, float *__restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y, k = blockIdx.z;
+    if (i > g.nx) return;
+    long long s = ((long long)k * (g.ny + 1) + j) * (g.nx + 1) + i;
+    out[s] = f[c * g.comp + gidx(g, i, j, k)];
+}
+
+void launch_set_field(const fdtd_ctx *h, int comp, const float *compact, cudaStream_t s) {
+    const Grid &g = h->g;
+    dim3 blk(128), grd((g.nx + 1 + 127) / 128, g.ny + 1, g.nz + 1);
+    k_set_field<<<grd, blk, 0, s>>>(g, comp, compact, h->fields[h->cur], h->boundary == FDTD_MUR1);
+}
+
+void launch_get_field(const fdtd_ctx *h, int comp, float *compact, cudaStream_t s) {
+    const Grid &g = h->g;
+    dim3 blk(128), grd((g.nx + 1 + 127) / 128, g.ny + 1, g.nz + 1);
+    k_get_field<<<grd, blk, 0, s>>>(g, comp, h->fields[h->cur], compact);
+}
+
+// ---- energy / stability -----------------------------------------------------
+// Pass 1: each block sums E^2 and H^2 (FP64) and counts non-finite values over a
+// grid-stride range of the six arrays (entries the update does not keep are
+// zero) into partial[3*block].  Pass 2: one block folds the partials.
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(256) k_energy_partial(const float4 *__restrict__ f,
+                                                        long long comp4, double *partial) {
+    double se = 0.0, sh = 0.0, bad = 0.0;
+    long long total = 6 * comp4;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        float4 v = f[t];
+        double s = (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+        if (!isfinite(v.x) || !isfinite(v.y) || !isfinite(v.z) || !isfinite(v.w)) bad += 1.0;
+        if (t < 3 * comp4) se += s; else sh += s;
+    }
+    __shared__ double red[3][8];
+    se = warp_sum(se); sh = warp_sum(sh); bad = warp_sum(bad);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { red[0][w] = se; red[1][w] = sh; red[2][w] = bad; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int nw = blockDim.x >> 5;
+        double a = l < nw ? red[0][l] : 0.0, b = l < nw ? red[1][l] : 0.0, c = l < nw ? red[2][l] : 0.0;
+        a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
+        if (l == 0) {
+            partial[3 * blockIdx.x] = a;
+            partial[3 * blockIdx.x + 1] = b;
+            partial[3 * blockIdx.x + 2] = c;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_energy_final(const double *partial, int nblk, double *out) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int t = threadIdx.x; t < nblk; t += blockDim.x) {
+        a += partial[3 * t]; b += partial[3 * t + 1]; c += partial[3 * t + 2];
+    }
+    __shared__ double red[3][8];
+    a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { red[0][w] = a; red[1][w] = b; red[2][w] = c; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int nw = blockDim.x >> 5;
+        a = l < nw ? red[0][l] : 0.0; b = l < nw ? red[1][l] : 0.0; c = l < nw ? red[2][l] : 0.0;
+        a = warp_sum(a); b = warp_sum(b); c = warp_sum(c);
+        if (l == 0) { out[0] = a; out[1] = b; out[2] = c; }
+    }
+}
+
+void launch_energy(const fdtd_ctx *h, cudaStream_t s, int *launches) {
+    const float4 *f = reinterpret_cast<const float4 *>(h->fields[h->cur]);
+    k_energy_partial<<<h->partial_cap, 256, 0, s>>>(f, h->g.comp / 4, h->d_partial);
+    k_energy_final<<<1, 256, 0, s>>>(h->d_partial, h->partial_cap, h->d_result);
+    *launches = 2;
+}
+
+}  // namespace fdtd

@@ -1,0 +1,117 @@
+"""The full-size CPML workload (384 x 384 x 1536 cells, dx = 2 cm, Greisen
+shower, NKG lateral spread), in the launch configuration the benchmark times,
+checked where the oracle can follow it and by properties that hold at any size:
+
+* exact sub-domain parity: after N steps the fields depend only on sources and
+  boundaries within N cells (each Yee step couples nearest neighbours only),
+  so an oracle run on a sub-box that keeps the real z- CPML and contains that
+  dependency region reproduces the full grid there;
+* causality: outside that region every GPU field value is exactly zero;
+* discrete Gauss law over the whole grid: eps div E equals the charge the
+  shower has carried, computed on the host from the profile and lateral tables.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from physics import EPS0, cic_hat
+
+pytestmark = pytest.mark.gpu
+N_STEPS = 120
+
+
+@pytest.fixture(scope="module")
+def full():
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1001_5341_gb300 as fd
+    w = W.greisen384(steps=N_STEPS)
+    ax = (w.nx // 2) * w.dx
+    near = np.array([[ax + 0.24, ax, 0.46], [ax, ax - 0.32, 0.62], [ax + 0.2, ax + 0.2, 0.90],
+                     [ax - 0.5, ax + 0.1, 0.70]])
+    w.probes_xyz = np.vstack([w.probes_xyz, near])
+    sim = fd.Simulation.from_workload(w)
+    sim.step(N_STEPS)
+    sim.sync()
+    return fd, w, sim, torch
+
+
+def _sub_box(w):
+    L = w.lateral["L"]
+    half = N_STEPS + L + 2
+    nz_sub = int(math.ceil(w.z0 / w.dx + w.v * w.dt / w.dx * N_STEPS)) + N_STEPS + 4
+    off = w.nx // 2 - half
+    return 2 * half, nz_sub, off
+
+
+def test_subdomain_parity_and_causality(full):
+    fd, w, sim, torch = full
+    ns, nzs, off = _sub_box(w)
+    sub = W.Workload(name="sub", nx=ns, ny=ns, nz=nzs, dx=w.dx, dt=w.dt, eps_r=w.eps_r,
+                     boundary=w.boundary, npml=w.npml, steps=N_STEPS, profile=w.profile,
+                     lateral=w.lateral, z0=w.z0, bin_dz=w.bin_dz, n_bins=w.n_bins, v=w.v,
+                     probes_xyz=w.probes_xyz[-4:] - np.array([off * w.dx, off * w.dx, 0.0]))
+    ref = oracle.from_workload(sub)
+    ref.step(N_STEPS)
+    dev = torch.empty((w.nz + 1, w.ny + 1, w.nx + 1), dtype=torch.float32, device="cuda")
+    for c in range(6):
+        sim.field(c, out=dev)
+        region = dev[: nzs + 1, off: off + ns + 1, off: off + ns + 1].cpu().numpy().astype(np.float64)
+        o = ref.field(c)
+        if c >= 3:  # normal H on the sub-box faces is not kept by the library
+            keep = np.ones_like(o, bool)
+            if c == 3: keep[:, :, [0, ns]] = False
+            if c == 4: keep[:, [0, ns], :] = False
+            if c == 5: keep[[0, nzs], :, :] = False
+            region, o = region[keep], o[keep]
+        err = np.linalg.norm(region - o) / np.linalg.norm(o)
+        assert err <= 1e-4, (oracle.COMPONENTS[c], err)
+        # outside the dependency region the full grid is exactly zero
+        dev[: nzs + 1, off: off + ns + 1, off: off + ns + 1] = 0
+        assert float(dev.abs().max()) == 0.0, oracle.COMPONENTS[c]
+    tg = sim.probes()[-4:].astype(np.float64)
+    to = ref.probes()
+    assert np.abs(to).max() > 0
+    assert np.linalg.norm(tg - to) / np.linalg.norm(to) <= 1e-4
+    # the 64 detectors at r >= 1 m have not been reached yet
+    assert np.all(sim.probes()[:-4] == 0.0)
+
+
+def test_gauss_law_full_grid(full):
+    fd, w, sim, torch = full
+    E = []
+    for c in range(3):
+        t = torch.empty((w.nz + 1, w.ny + 1, w.nx + 1), dtype=torch.float64, device="cuda")
+        f = torch.empty((w.nz + 1, w.ny + 1, w.nx + 1), dtype=torch.float32, device="cuda")
+        sim.field(c, out=f)
+        t.copy_(f)
+        E.append(t)
+        del f
+    P = w.npml
+    sl = (slice(P + 1, w.nz - P), slice(P + 1, w.ny - P), slice(P + 1, w.nx - P))
+    Ex, Ey, Ez = E
+    div = ((Ex[sl] - Ex[sl[0], sl[1], P:w.nx - P - 1]) + (Ey[sl] - Ey[sl[0], P:w.ny - P - 1, sl[2]]) +
+           (Ez[sl] - Ez[P:w.nz - P - 1, sl[1], sl[2]])) / w.dx
+    eps = w.eps_r * EPS0
+    q, lw = fd.tables(w)
+    L = w.lateral["L"]
+    zk = np.arange(w.nz + 1) * w.dx
+    col = np.zeros(w.nz + 1)
+    zt = w.z0 + w.bin_dz * np.arange(q.size)
+    for n in range(N_STEPS):
+        za, zb = w.z0 + w.v * n * w.dt, w.z0 + w.v * (n + 1) * w.dt
+        qb = np.interp(w.z0 + w.v * (n + 0.5) * w.dt, zt, q)
+        col += qb * (cic_hat((zk - zb) / w.dx) - cic_hat((zk - za) / w.dx)) / w.dx ** 3
+    rho = torch.zeros_like(div)
+    ic, jc = w.nx // 2, w.ny // 2
+    wt = torch.tensor(lw.reshape(2 * L + 1, 2 * L + 1), dtype=torch.float64, device="cuda")
+    colt = torch.tensor(col[P + 1: w.nz - P], dtype=torch.float64, device="cuda")
+    rho[:, jc - L - (P + 1): jc + L + 1 - (P + 1), ic - L - (P + 1): ic + L + 1 - (P + 1)] = \
+        colt[:, None, None] * wt[None, :, :]
+    scale = float(rho.abs().max())
+    assert scale > 0
+    err = float((eps * div - rho).abs().max())
+    assert err <= 1e-4 * scale, err / scale
