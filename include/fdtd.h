@@ -175,6 +175,13 @@ int fdtd_launch_count(fdtd_t h, int64_t *launches);
 /* Name of the field-update path in use (static string). */
 const char *fdtd_kernel_name(fdtd_t h);
 
+/*
+ * Select the field-update path: 1 = fused z-march (one pass per step, the
+ * default when the device supports it), 0 = one H sweep then one E sweep.
+ * Both compute the same update (Sec. III.A); the unfused pair is a cross-check.
+ */
+int fdtd_set_kernel(fdtd_t h, int which);
+
 /* Human-readable text of a status code (static string). */
 const char *fdtd_strerror(int status);
 

@@ -54,6 +54,7 @@ _SIGS = {
     "fdtd_timing_end": (_i, [_vp, _pd, _pi]),
     "fdtd_launch_count": (_i, [_vp, _pi64]),
     "fdtd_kernel_name": (C.c_char_p, [_vp]),
+    "fdtd_set_kernel": (_i, [_vp, _i]),
     "fdtd_strerror": (C.c_char_p, [_i]),
     "fdtd_profile_gaussian": (_i, [_d, _d, _i, _d, _d, _d, _pd]),
     "fdtd_profile_greisen": (_i, [_d, _i, _d, _d, _d, _d, _pd]),
@@ -167,8 +168,10 @@ class Simulation:
         self.np, self.max_steps = 0, 0
 
     @classmethod
-    def from_workload(cls, w, max_steps: Optional[int] = None, stream=None):
+    def from_workload(cls, w, max_steps: Optional[int] = None, stream=None, kernel=None):
         s = cls(w.nx, w.ny, w.nz, w.dx, w.dt, w.eps_r, w.boundary, w.npml, stream=stream)
+        if kernel is not None:
+            s.set_kernel(kernel)
         q, lw = tables(w)
         s.set_shower(q, w.z0, w.bin_dz, w.v, lw, w.lateral["L"])
         s.set_probes(w.probes_xyz, w.steps if max_steps is None else max_steps)
@@ -281,3 +284,7 @@ class Simulation:
     @property
     def kernel_name(self):
         return fdtd_kernel_name(self.h).decode()
+
+    def set_kernel(self, which: int):
+        """1: fused z-march (default), 0: unfused H sweep then E sweep."""
+        check(fdtd_set_kernel(self.h, which), "fdtd_set_kernel")

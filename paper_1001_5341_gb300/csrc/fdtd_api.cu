@@ -47,6 +47,8 @@ void release(fdtd_ctx *h) {
     free_dev(h->d_trace);
     free_dev(h->d_partial);
     free_dev(h->d_result);
+    free_dev(h->d_flags);
+    fused_release(h);
     for (cudaEvent_t e : h->timing.ev) cudaEventDestroy(e);
     delete h;
 }
@@ -56,6 +58,30 @@ int interior_lo(const fdtd_ctx *h) { return h->boundary == FDTD_CPML ? h->P + 1 
 size_t field_bytes(const fdtd_ctx *h) { return sizeof(float) * 6 * (size_t)h->g.comp; }
 
 }  // namespace
+
+namespace fdtd {
+Cpml cpml_view(const fdtd_ctx *h) {
+    Cpml v{};
+    v.P = h->P;
+    v.W = h->P > 0 ? 2 * h->P + 1 : 0;
+    if (h->P <= 0) return v;
+    float *p = h->psi_block;
+    const size_t set = 2 * (h->psi_axis[0] + h->psi_axis[1] + h->psi_axis[2]);
+    float *hin = h->psi_block + set * (1 + h->cur), *hout = h->psi_block + set * (1 + (h->cur ^ 1));
+    size_t off = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int t = 0; t < 2; ++t) {
+            v.e[a][t] = p + off;
+            v.hin[a][t] = hin + off;
+            v.hout[a][t] = hout + off;
+            off += h->psi_axis[a];
+        }
+    for (int a = 0; a < 3; ++a) {
+        v.aE[a] = h->aE[a]; v.bE[a] = h->bE[a]; v.aH[a] = h->aH[a]; v.bH[a] = h->bH[a];
+    }
+    return v;
+}
+}  // namespace fdtd
 
 extern "C" {
 
@@ -123,8 +149,6 @@ int fdtd_create(fdtd_t *out, int nx, int ny, int nz, double dx, double dt, doubl
     h->cur = 0;
 
     // CPML: coefficient tables and psi arrays over the slabs
-    h->cpml.P = P;
-    h->cpml.W = P > 0 ? 2 * P + 1 : 0;
     if (P > 0) {
         const int N[3] = {nx, ny, nz};
         size_t ncoef = 0;
@@ -134,30 +158,34 @@ int fdtd_create(fdtd_t *out, int nx, int ny, int nz, double dx, double dt, doubl
         if (!hc) return fail(FDTD_ERR_OOM);
         size_t off = 0;
         for (int a = 0; a < 3; ++a) {
-            float *aE = hc + off, *bE = aE + (N[a] + 1), *aH = bE + (N[a] + 1), *bH = aH + (N[a] + 1);
+            const size_t n1 = (size_t)N[a] + 1;
+            float *aE = hc + off, *bE = aE + n1, *aH = bE + n1, *bH = aH + n1;
             cpml_coefficients(N[a], P, dx, dt, eps_r, aE, bE, aH, bH);
-            h->cpml.aE[a] = h->coef_block + off;
-            h->cpml.bE[a] = h->coef_block + off + (N[a] + 1);
-            h->cpml.aH[a] = h->coef_block + off + 2 * (N[a] + 1);
-            h->cpml.bH[a] = h->coef_block + off + 3 * (N[a] + 1);
-            off += 4 * (size_t)(N[a] + 1);
+            h->aE[a] = h->coef_block + off;
+            h->bE[a] = h->coef_block + off + n1;
+            h->aH[a] = h->coef_block + off + 2 * n1;
+            h->bH[a] = h->coef_block + off + 3 * n1;
+            off += 4 * n1;
         }
         rc = note(h, cudaMemcpy(h->coef_block, hc, ncoef * sizeof(float), cudaMemcpyHostToDevice));
         std::free(hc);
         if (rc != FDTD_OK) return fail(rc);
-        const int W = h->cpml.W;
-        size_t per[3] = {(size_t)nz * ny * W, (size_t)nz * W * nx, (size_t)W * ny * nx};
-        h->psi_floats = 4 * (per[0] + per[1] + per[2]);
+        const int W = 2 * P + 1;
+        h->psi_axis[0] = (size_t)nz * ny * W;
+        h->psi_axis[1] = (size_t)nz * W * nx;
+        h->psi_axis[2] = (size_t)W * ny * nx;
+        // E psi (2 per axis), then H psi set 0 and set 1 (2 per axis each)
+        h->psi_floats = 3 * 2 * (h->psi_axis[0] + h->psi_axis[1] + h->psi_axis[2]);
         if (cudaMalloc(&h->psi_block, h->psi_floats * sizeof(float)) != cudaSuccess) { cudaGetLastError(); return fail(FDTD_ERR_OOM); }
         if ((rc = note(h, cudaMemsetAsync(h->psi_block, 0, h->psi_floats * sizeof(float), h->stream))) != FDTD_OK) return fail(rc);
-        float *p = h->psi_block;
-        for (int a = 0; a < 3; ++a)
-            for (int t = 0; t < 4; ++t) { h->cpml.psi[a][t] = p; p += per[a]; }
     }
+    if (cudaMalloc(&h->d_flags, sizeof(int)) != cudaSuccess) { cudaGetLastError(); return fail(FDTD_ERR_OOM); }
+    if ((rc = note(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int), h->stream))) != FDTD_OK) return fail(rc);
 
     // scratch of the energy / stability reduction
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev);
+    h->num_sms = sms > 0 ? sms : 1;
     h->partial_cap = sms > 0 ? 4 * sms : 512;
     if (cudaMalloc(&h->d_partial, 3 * (size_t)h->partial_cap * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&h->d_result, 3 * sizeof(double)) != cudaSuccess) {
@@ -165,6 +193,11 @@ int fdtd_create(fdtd_t *out, int nx, int ny, int nz, double dx, double dt, doubl
         return fail(FDTD_ERR_OOM);
     }
     if ((rc = note(h, cudaStreamSynchronize(h->stream))) != FDTD_OK) return fail(rc);
+    // the fused z-march is the default field-update path; the unfused pair of
+    // sweeps stays available (fdtd_set_kernel) as a cross-check
+    h->kernel = 0;
+    if (fused_prepare(h) == FDTD_OK) h->kernel = 1;
+    cudaGetLastError();
     *out = h;
     return FDTD_OK;
 }
@@ -277,8 +310,12 @@ int fdtd_step(fdtd_t h, int n) {
     if (h->status != FDTD_OK) return h->status;
     if (h->np > 0 && h->steps + n > h->max_steps) return FDTD_ERR_CAPACITY;
     for (int s = 0; s < n; ++s) {
-        timed_launch(h, launch_update_h);
-        timed_launch(h, launch_update_e);
+        if (h->kernel == 1) {
+            timed_launch(h, [](const fdtd_ctx *c, cudaStream_t st) { launch_fused(const_cast<fdtd_ctx *>(c), st); });
+        } else {
+            timed_launch(h, launch_update_h);
+            timed_launch(h, launch_update_e);
+        }
         if (h->boundary == FDTD_MUR1) { launch_mur(h, h->stream); h->launches++; }
         if (h->np > 0) { launch_probes(h, h->stream); h->launches++; }
         h->cur ^= 1;
@@ -287,10 +324,18 @@ int fdtd_step(fdtd_t h, int n) {
     return note(h, cudaGetLastError());
 }
 
+// Read the device error flags (after a synchronisation) into the sticky status.
+static int check_flags(fdtd_ctx *h) {
+    int f = 0;
+    if (note(h, cudaMemcpy(&f, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost)) != FDTD_OK) return h->status;
+    if (f != 0 && h->status == FDTD_OK) h->status = FDTD_ERR_TIMEOUT;
+    return h->status;
+}
+
 int fdtd_sync(fdtd_t h) {
     if (!h) return FDTD_ERR_ARG;
     note(h, cudaStreamSynchronize(h->stream));
-    return h->status;
+    return check_flags(h);
 }
 
 int fdtd_steps_done(fdtd_t h, int64_t *steps) {
@@ -302,7 +347,7 @@ int fdtd_steps_done(fdtd_t h, int64_t *steps) {
 int fdtd_probes(fdtd_t h, float *out, int on_device) {
     if (!h || (h->np > 0 && !out)) return FDTD_ERR_ARG;
     TRY(h, cudaStreamSynchronize(h->stream));
-    if (h->status != FDTD_OK) return h->status;
+    if (check_flags(h) != FDTD_OK) return h->status;
     if (h->np == 0 || h->max_steps == 0) return FDTD_OK;
     size_t tb = sizeof(float) * 2 * (size_t)h->np * h->max_steps;
     TRY(h, cudaMemcpyAsync(out, h->d_trace, tb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -399,7 +444,7 @@ int fdtd_save_state(fdtd_t h, void *buf, size_t *bytes) {
     hd.boundary = h->boundary; hd.P = h->P; hd.pitch = h->g.pitch;
     hd.np = h->np; hd.max_steps = h->max_steps; hd.steps = h->steps;
     hd.field_bytes = field_bytes(h);
-    hd.psi_bytes = h->psi_floats * sizeof(float);
+    hd.psi_bytes = (h->psi_floats / 3) * 2 * sizeof(float);  // E psi + H psi of set cur
     hd.trace_bytes = h->np > 0 ? sizeof(float) * 2 * (size_t)h->np * h->max_steps : 0;
     size_t need = sizeof(hd) + hd.field_bytes + hd.psi_bytes + hd.trace_bytes;
     if (!buf) { *bytes = need; return FDTD_OK; }
@@ -409,7 +454,12 @@ int fdtd_save_state(fdtd_t h, void *buf, size_t *bytes) {
     char *p = (char *)buf;
     std::memcpy(p, &hd, sizeof(hd)); p += sizeof(hd);
     TRY(h, cudaMemcpy(p, h->fields[h->cur], hd.field_bytes, cudaMemcpyDeviceToHost)); p += hd.field_bytes;
-    if (hd.psi_bytes) { TRY(h, cudaMemcpy(p, h->psi_block, hd.psi_bytes, cudaMemcpyDeviceToHost)); p += hd.psi_bytes; }
+    if (hd.psi_bytes) {
+        const size_t third = h->psi_floats / 3 * sizeof(float);
+        TRY(h, cudaMemcpy(p, h->psi_block, third, cudaMemcpyDeviceToHost));
+        TRY(h, cudaMemcpy(p + third, (char *)h->psi_block + third * (1 + h->cur), third, cudaMemcpyDeviceToHost));
+        p += hd.psi_bytes;
+    }
     if (hd.trace_bytes) { TRY(h, cudaMemcpy(p, h->d_trace, hd.trace_bytes, cudaMemcpyDeviceToHost)); }
     *bytes = need;
     return FDTD_OK;
@@ -423,13 +473,18 @@ int fdtd_load_state(fdtd_t h, const void *buf, size_t bytes) {
     if (hd.nx != h->g.nx || hd.ny != h->g.ny || hd.nz != h->g.nz || hd.boundary != h->boundary ||
         hd.P != h->P || hd.pitch != h->g.pitch || hd.np != h->np || hd.max_steps != h->max_steps)
         return FDTD_ERR_ARG;
-    if (hd.field_bytes != field_bytes(h) || hd.psi_bytes != h->psi_floats * sizeof(float) ||
+    if (hd.field_bytes != field_bytes(h) || hd.psi_bytes != (h->psi_floats / 3) * 2 * sizeof(float) ||
         bytes < sizeof(hd) + hd.field_bytes + hd.psi_bytes + hd.trace_bytes)
         return FDTD_ERR_ARG;
     TRY(h, cudaStreamSynchronize(h->stream));
     const char *p = (const char *)buf + sizeof(hd);
     TRY(h, cudaMemcpy(h->fields[h->cur], p, hd.field_bytes, cudaMemcpyHostToDevice)); p += hd.field_bytes;
-    if (hd.psi_bytes) { TRY(h, cudaMemcpy(h->psi_block, p, hd.psi_bytes, cudaMemcpyHostToDevice)); p += hd.psi_bytes; }
+    if (hd.psi_bytes) {
+        const size_t third = h->psi_floats / 3 * sizeof(float);
+        TRY(h, cudaMemcpy(h->psi_block, p, third, cudaMemcpyHostToDevice));
+        TRY(h, cudaMemcpy((char *)h->psi_block + third * (1 + h->cur), p + third, third, cudaMemcpyHostToDevice));
+        p += hd.psi_bytes;
+    }
     if (hd.trace_bytes) { TRY(h, cudaMemcpy(h->d_trace, p, hd.trace_bytes, cudaMemcpyHostToDevice)); }
     h->steps = hd.steps;
     return FDTD_OK;
@@ -474,8 +529,15 @@ int fdtd_launch_count(fdtd_t h, int64_t *launches) {
 }
 
 const char *fdtd_kernel_name(fdtd_t h) {
-    (void)h;
+    if (h && h->kernel == 1) return fused_name();
     return "unfused-h-then-e";
+}
+
+int fdtd_set_kernel(fdtd_t h, int which) {
+    if (!h || which < 0 || which > 1) return FDTD_ERR_ARG;
+    if (which == 1 && !h->fused) return FDTD_ERR_ARG;
+    h->kernel = which;
+    return FDTD_OK;
 }
 
 }  // extern "C"

@@ -11,7 +11,10 @@
 // (two for the E update, two for the H update) over the slab cells of that
 // axis: cells 0..P and N-P..N-1 (W = 2P+1 cells), stored
 //   x: [nz][ny][W]   y: [nz][W][nx]   z: [W][ny][nx]
-// so that consecutive threads along x touch consecutive floats.
+// so that consecutive threads along x touch consecutive floats.  The E-update
+// psi are updated in place by the one thread that owns the cell; the H-update
+// psi are ping-ponged like the fields, because a tile of the fused kernel
+// recomputes its neighbours' halo H and must read their psi before the update.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -41,11 +44,27 @@ __host__ __device__ inline int slab_cell(int i, int N, int P) {
     return -1;
 }
 
+// psi roles per axis a: e[a][0..1] and h*[a][0..1] are
+//   x: (Ey, Ez) and (Hy, Hz) x-derivative terms
+//   y: (Ex, Ez) and (Hx, Hz) y-derivative terms
+//   z: (Ex, Ey) and (Hx, Hy) z-derivative terms
 struct Cpml {
     int P, W;                 // depth, slab cells per axis (2P+1); P = 0: no CPML
-    float *psi[3][4];         // [axis][0,1 = E terms, 2,3 = H terms]
-    const float *aE[3], *bE[3], *aH[3], *bH[3]; // per position index, length n_axis
+    float *e[3][2];           // E-update psi, in place
+    const float *hin[3][2];   // H-update psi at step n-1/2 (read)
+    float *hout[3][2];        // H-update psi at step n+1/2 (written)
+    const float *aE[3], *bE[3], *aH[3], *bH[3]; // per position index, length n_axis (+1)
 };
+
+__host__ __device__ inline long long psi_x(const Grid &g, int W, int l, int j, int k) {
+    return ((long long)k * g.ny + j) * W + l;
+}
+__host__ __device__ inline long long psi_y(const Grid &g, int W, int i, int l, int k) {
+    return ((long long)k * W + l) * g.nx + i;
+}
+__host__ __device__ inline long long psi_z(const Grid &g, int W, int i, int j, int l) {
+    return ((long long)l * g.ny + j) * g.nx + i;
+}
 
 struct Source {
     int active;
@@ -85,10 +104,15 @@ struct fdtd_ctx {
     int cur;                  // index of the set holding E^n, H^{n-1/2}
 
     // CPML
-    float *psi_block;         // all psi arrays, one allocation
-    size_t psi_floats;
+    float *psi_block;         // E psi, then two sets of H psi (one allocation)
+    size_t psi_floats;        // total floats of psi_block
+    size_t psi_axis[3];       // floats of one psi array of each axis
     float *coef_block;        // aE,bE,aH,bH per axis
-    fdtd::Cpml cpml;
+    const float *aE[3], *bE[3], *aH[3], *bH[3];
+    int kernel;               // field-update path: 0 unfused, 1 fused z-march
+    void *fused;              // host state of the fused path (tensor maps, launch shape)
+    int *d_flags;             // device error flags (bit 0: a bounded wait gave up)
+    int num_sms;
 
     // source
     double *d_q;
@@ -115,6 +139,9 @@ struct fdtd_ctx {
 
 namespace fdtd {
 
+// psi views of the current step (H psi read from set cur, written to cur^1)
+Cpml cpml_view(const fdtd_ctx *h);
+
 // kernels (kernels_basic.cu)
 void launch_update_h(const fdtd_ctx *h, cudaStream_t s);
 void launch_update_e(const fdtd_ctx *h, cudaStream_t s);
@@ -123,6 +150,12 @@ void launch_probes(const fdtd_ctx *h, cudaStream_t s);
 void launch_energy(const fdtd_ctx *h, cudaStream_t s, int *launches);
 void launch_set_field(const fdtd_ctx *h, int comp, const float *compact, cudaStream_t s);
 void launch_get_field(const fdtd_ctx *h, int comp, float *compact, cudaStream_t s);
+
+// fused z-march (kernels_fused.cu)
+int fused_prepare(fdtd_ctx *h);   // tensor maps + launch shape; FDTD_OK or error
+void launch_fused(fdtd_ctx *h, cudaStream_t s);
+const char *fused_name();
+void fused_release(fdtd_ctx *h);
 
 // host tables (tables.cpp)
 void cpml_coefficients(int n, int P, double dx, double dt, double eps_r, float *aE, float *bE,

@@ -16,13 +16,21 @@
 #include <math.h>
 
 #include "fdtd_internal.h"
+#include "source_term.cuh"
 
 namespace fdtd {
 
-__device__ __forceinline__ void cpml_term(float *psi, const float *a, const float *b, int pos,
-                                          float &d) {
+// psi^{new} = b psi + a d; the derivative d gains psi^{new}.
+__device__ __forceinline__ void cpml_inplace(float *psi, const float *a, const float *b, int pos,
+                                             float &d) {
     float p = b[pos] * (*psi) + a[pos] * d;
     *psi = p;
+    d = d + p;
+}
+__device__ __forceinline__ void cpml_pingpong(const float *pin, float *pout, const float *a,
+                                              const float *b, int pos, float &d) {
+    float p = b[pos] * (*pin) + a[pos] * d;
+    *pout = p;
     d = d + p;
 }
 
@@ -36,55 +44,29 @@ __global__ void __launch_bounds__(256) k_update_h(Grid g, const float *__restric
     if (i >= g.nx || j >= g.ny) return;
     const float *Ex = Ein, *Ey = Ein + g.comp, *Ez = Ein + 2 * g.comp;
     long long c = gidx(g, i, j, k);
-    const int P = pml.P;
+    const int P = pml.P, W = pml.W;
     int lx = slab_cell(i, g.nx, P), ly = slab_cell(j, g.ny, P), lz = slab_cell(k, g.nz, P);
     if (i >= 1) {  // Hx
         float dy = Ez[c + g.pitch] - Ez[c];
         float dz = Ey[c + g.plane] - Ey[c];
-        if (ly >= 0) cpml_term(pml.psi[1][2] + ((long long)k * pml.W + ly) * g.nx + i, pml.aH[1], pml.bH[1], j, dy);
-        if (lz >= 0) cpml_term(pml.psi[2][2] + ((long long)lz * g.ny + j) * g.nx + i, pml.aH[2], pml.bH[2], k, dz);
+        if (ly >= 0) { long long q = psi_y(g, W, i, ly, k); cpml_pingpong(pml.hin[1][0] + q, pml.hout[1][0] + q, pml.aH[1], pml.bH[1], j, dy); }
+        if (lz >= 0) { long long q = psi_z(g, W, i, j, lz); cpml_pingpong(pml.hin[2][0] + q, pml.hout[2][0] + q, pml.aH[2], pml.bH[2], k, dz); }
         Hout[c] = Hin[c] - kH * (dy - dz);
     }
     if (j >= 1) {  // Hy
         float dz = Ex[c + g.plane] - Ex[c];
         float dx = Ez[c + 1] - Ez[c];
-        if (lz >= 0) cpml_term(pml.psi[2][3] + ((long long)lz * g.ny + j) * g.nx + i, pml.aH[2], pml.bH[2], k, dz);
-        if (lx >= 0) cpml_term(pml.psi[0][2] + ((long long)k * g.ny + j) * pml.W + lx, pml.aH[0], pml.bH[0], i, dx);
+        if (lz >= 0) { long long q = psi_z(g, W, i, j, lz); cpml_pingpong(pml.hin[2][1] + q, pml.hout[2][1] + q, pml.aH[2], pml.bH[2], k, dz); }
+        if (lx >= 0) { long long q = psi_x(g, W, lx, j, k); cpml_pingpong(pml.hin[0][0] + q, pml.hout[0][0] + q, pml.aH[0], pml.bH[0], i, dx); }
         Hout[g.comp + c] = Hin[g.comp + c] - kH * (dz - dx);
     }
     if (k >= 1) {  // Hz
         float dx = Ey[c + 1] - Ey[c];
         float dy = Ex[c + g.pitch] - Ex[c];
-        if (lx >= 0) cpml_term(pml.psi[0][3] + ((long long)k * g.ny + j) * pml.W + lx, pml.aH[0], pml.bH[0], i, dx);
-        if (ly >= 0) cpml_term(pml.psi[1][3] + ((long long)k * pml.W + ly) * g.nx + i, pml.aH[1], pml.bH[1], j, dy);
+        if (lx >= 0) { long long q = psi_x(g, W, lx, j, k); cpml_pingpong(pml.hin[0][1] + q, pml.hout[0][1] + q, pml.aH[0], pml.bH[0], i, dx); }
+        if (ly >= 0) { long long q = psi_y(g, W, i, ly, k); cpml_pingpong(pml.hin[1][1] + q, pml.hout[1][1] + q, pml.aH[1], pml.bH[1], j, dy); }
         Hout[2 * g.comp + c] = Hin[2 * g.comp + c] - kH * (dx - dy);
     }
-}
-
-// E increment on edge (i, j, k+1/2) from the charge carried across it during
-// step n (FP64, as the integer node index k0 = floor(z/dx) must be decided in
-// the same precision as the reference arithmetic).
-__device__ __forceinline__ float source_term(const Source &s, int i, int j, int k, long long n) {
-    int di = i - s.ic, dj = j - s.jc;
-    if (di < -s.L || di > s.L || dj < -s.L || dj > s.L || k < s.kmin || k > s.kmax) return 0.0f;
-    double za = s.z0 + s.v * (double)n * s.dt;
-    double zb = s.z0 + s.v * (double)(n + 1) * s.dt;
-    // C_k(z): fraction of the charge on nodes <= k of the untruncated CIC line
-    double ua = za / s.dx, ub = zb / s.dx;
-    double ka = floor(ua), kb = floor(ub);
-    double ca = (double)k < ka ? 0.0 : ((double)k == ka ? 1.0 - (ua - ka) : 1.0);
-    double cb = (double)k < kb ? 0.0 : ((double)k == kb ? 1.0 - (ub - kb) : 1.0);
-    double dC = cb - ca;
-    if (dC == 0.0) return 0.0f;
-    double zm = s.z0 + s.v * ((double)n + 0.5) * s.dt;
-    double u = (zm - s.z0) / s.bin_dz;
-    if (!(u >= 0.0) || u > (double)(s.nbins - 1)) return 0.0f;
-    int b = (int)floor(u);
-    double qbar = b >= s.nbins - 1 ? s.q[s.nbins - 1]
-                                   : s.q[b] * (1.0 - (u - b)) + s.q[b + 1] * (u - b);
-    double wij = s.w[(dj + s.L) * (2 * s.L + 1) + (di + s.L)];
-    // -(dt/eps) J with J = -(dx/dt) qbar w dC / dx^3
-    return (float)(qbar * wij * s.coef * dC);
 }
 
 // Ein, Eout: Ex of sets cur / cur^1; Hnew: Hx of set cur^1.
@@ -98,27 +80,27 @@ __global__ void __launch_bounds__(256) k_update_e(Grid g, const float *__restric
     if (i >= g.nx || j >= g.ny) return;
     const float *Hx = Hnew, *Hy = Hnew + g.comp, *Hz = Hnew + 2 * g.comp;
     long long c = gidx(g, i, j, k);
-    const int P = pml.P;
+    const int P = pml.P, W = pml.W;
     int lx = slab_cell(i, g.nx, P), ly = slab_cell(j, g.ny, P), lz = slab_cell(k, g.nz, P);
     if (j >= 1 && k >= 1) {  // Ex
         float dy = Hz[c] - Hz[c - g.pitch];
         float dz = Hy[c] - Hy[c - g.plane];
-        if (ly >= 0) cpml_term(pml.psi[1][0] + ((long long)k * pml.W + ly) * g.nx + i, pml.aE[1], pml.bE[1], j, dy);
-        if (lz >= 0) cpml_term(pml.psi[2][0] + ((long long)lz * g.ny + j) * g.nx + i, pml.aE[2], pml.bE[2], k, dz);
+        if (ly >= 0) cpml_inplace(pml.e[1][0] + psi_y(g, W, i, ly, k), pml.aE[1], pml.bE[1], j, dy);
+        if (lz >= 0) cpml_inplace(pml.e[2][0] + psi_z(g, W, i, j, lz), pml.aE[2], pml.bE[2], k, dz);
         Eout[c] = Ein[c] + kE * (dy - dz);
     }
     if (i >= 1 && k >= 1) {  // Ey
         float dz = Hx[c] - Hx[c - g.plane];
         float dx = Hz[c] - Hz[c - 1];
-        if (lz >= 0) cpml_term(pml.psi[2][1] + ((long long)lz * g.ny + j) * g.nx + i, pml.aE[2], pml.bE[2], k, dz);
-        if (lx >= 0) cpml_term(pml.psi[0][0] + ((long long)k * g.ny + j) * pml.W + lx, pml.aE[0], pml.bE[0], i, dx);
+        if (lz >= 0) cpml_inplace(pml.e[2][1] + psi_z(g, W, i, j, lz), pml.aE[2], pml.bE[2], k, dz);
+        if (lx >= 0) cpml_inplace(pml.e[0][0] + psi_x(g, W, lx, j, k), pml.aE[0], pml.bE[0], i, dx);
         Eout[g.comp + c] = Ein[g.comp + c] + kE * (dz - dx);
     }
     if (i >= 1 && j >= 1) {  // Ez
         float dx = Hy[c] - Hy[c - 1];
         float dy = Hx[c] - Hx[c - g.pitch];
-        if (lx >= 0) cpml_term(pml.psi[0][1] + ((long long)k * g.ny + j) * pml.W + lx, pml.aE[0], pml.bE[0], i, dx);
-        if (ly >= 0) cpml_term(pml.psi[1][1] + ((long long)k * pml.W + ly) * g.nx + i, pml.aE[1], pml.bE[1], j, dy);
+        if (lx >= 0) cpml_inplace(pml.e[0][1] + psi_x(g, W, lx, j, k), pml.aE[0], pml.bE[0], i, dx);
+        if (ly >= 0) cpml_inplace(pml.e[1][1] + psi_y(g, W, i, ly, k), pml.aE[1], pml.bE[1], j, dy);
         float e = Ein[2 * g.comp + c] + kE * (dx - dy);
         if (src.active) e += source_term(src, i, j, k, n);
         Eout[2 * g.comp + c] = e;
@@ -130,7 +112,7 @@ void launch_update_h(const fdtd_ctx *h, cudaStream_t s) {
     dim3 blk(32, 8, 1), grd((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
     const float *in = h->fields[h->cur];
     float *out = h->fields[h->cur ^ 1];
-    k_update_h<<<grd, blk, 0, s>>>(g, in, in + 3 * g.comp, out + 3 * g.comp, h->cpml, (float)h->kH);
+    k_update_h<<<grd, blk, 0, s>>>(g, in, in + 3 * g.comp, out + 3 * g.comp, cpml_view(h), (float)h->kH);
 }
 
 void launch_update_e(const fdtd_ctx *h, cudaStream_t s) {
@@ -138,7 +120,7 @@ void launch_update_e(const fdtd_ctx *h, cudaStream_t s) {
     dim3 blk(32, 8, 1), grd((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
     const float *in = h->fields[h->cur];
     float *out = h->fields[h->cur ^ 1];
-    k_update_e<<<grd, blk, 0, s>>>(g, in, out + 3 * g.comp, out, h->cpml, (float)h->kE, h->src, h->steps);
+    k_update_e<<<grd, blk, 0, s>>>(g, in, out + 3 * g.comp, out, cpml_view(h), (float)h->kE, h->src, h->steps);
 }
 
 // First-order Mur on the tangential E of face f (0..5 = x-, x+, y-, y+, z-, z+):

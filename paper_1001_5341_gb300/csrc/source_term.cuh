@@ -1,0 +1,34 @@
+// source_term.cuh -- the moving shower's current on one Ez edge (device).
+#pragma once
+
+#include "fdtd_internal.h"
+
+namespace fdtd {
+
+// E increment on edge (i, j, k+1/2) from the charge carried across it during
+// step n (FP64, as the integer node index k0 = floor(z/dx) must be decided in
+// the same precision as the reference arithmetic).
+__device__ __forceinline__ float source_term(const Source &s, int i, int j, int k, long long n) {
+    int di = i - s.ic, dj = j - s.jc;
+    if (di < -s.L || di > s.L || dj < -s.L || dj > s.L || k < s.kmin || k > s.kmax) return 0.0f;
+    double za = s.z0 + s.v * (double)n * s.dt;
+    double zb = s.z0 + s.v * (double)(n + 1) * s.dt;
+    // C_k(z): fraction of the charge on nodes <= k of the untruncated CIC line
+    double ua = za / s.dx, ub = zb / s.dx;
+    double ka = floor(ua), kb = floor(ub);
+    double ca = (double)k < ka ? 0.0 : ((double)k == ka ? 1.0 - (ua - ka) : 1.0);
+    double cb = (double)k < kb ? 0.0 : ((double)k == kb ? 1.0 - (ub - kb) : 1.0);
+    double dC = cb - ca;
+    if (dC == 0.0) return 0.0f;
+    double zm = s.z0 + s.v * ((double)n + 0.5) * s.dt;
+    double u = (zm - s.z0) / s.bin_dz;
+    if (!(u >= 0.0) || u > (double)(s.nbins - 1)) return 0.0f;
+    int b = (int)floor(u);
+    double qbar = b >= s.nbins - 1 ? s.q[s.nbins - 1]
+                                   : s.q[b] * (1.0 - (u - b)) + s.q[b + 1] * (u - b);
+    double wij = s.w[(dj + s.L) * (2 * s.L + 1) + (di + s.L)];
+    // -(dt/eps) J with J = -(dx/dt) qbar w dC / dx^3
+    return (float)(qbar * wij * s.coef * dC);
+}
+
+}  // namespace fdtd

@@ -23,6 +23,12 @@ def fd():
     return m
 
 
+# both field-update paths: 1 = fused z-march (default), 0 = unfused sweeps
+@pytest.fixture(params=[1, 0], ids=["fused", "unfused"])
+def kernel(request):
+    return request.param
+
+
 def rel_l2(a, b):
     nb = np.linalg.norm(b)
     return np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a)
@@ -59,8 +65,9 @@ def compare_fields(sim, ref, tol=TOL):
     return errs
 
 
-def run_pair(fd, w, snaps):
-    sim = fd.Simulation.from_workload(w)
+def run_pair(fd, w, snaps, kernel=1):
+    sim = fd.Simulation.from_workload(w, kernel=kernel)
+    assert sim.kernel_name.startswith("fused" if kernel == 1 else "unfused")
     ref = oracle.from_workload(w)
     done = 0
     out = []
@@ -77,21 +84,36 @@ def run_pair(fd, w, snaps):
     return sim, ref, e_all, per, out
 
 
-def test_parity96_mur_full(fd):
+def test_parity96_mur_full(fd, kernel):
     w = W.parity96()
-    sim, ref, e, per, snaps = run_pair(fd, w, [w.steps // 2, w.steps])
+    sim, ref, e, per, snaps = run_pair(fd, w, [w.steps // 2, w.steps], kernel)
     assert max(per) <= 3 * TOL
     assert np.array_equal(sim.probe_nodes(), ref.probe_nodes())
 
 
-def test_greisen_small_cpml(fd):
+def test_greisen_small_cpml(fd, kernel):
     w = W.greisen_small()
-    run_pair(fd, w, [150, w.steps])
+    run_pair(fd, w, [150, w.steps], kernel)
 
 
-def test_gh_small_cpml(fd):
+def test_gh_small_cpml(fd, kernel):
     w = W.gh_small()
-    run_pair(fd, w, [w.steps])
+    run_pair(fd, w, [w.steps], kernel)
+
+
+def test_fused_and_unfused_agree(fd):
+    """The two paths compute the same update; they may differ only by FP32
+    rounding (FMA contraction)."""
+    w = W.greisen_small(nx=72, ny=70, nz=140, steps=160, n_probes=6)
+    a = fd.Simulation.from_workload(w, kernel=1)
+    b = fd.Simulation.from_workload(w, kernel=0)
+    a.step(w.steps)
+    b.step(w.steps)
+    for c in range(6):
+        fa, fb = a.field(c), b.field(c)
+        nrm = max(np.linalg.norm(fb), 1e-30)
+        assert np.linalg.norm(fa - fb) / nrm < 1e-5 or np.linalg.norm(fa - fb) == 0.0
+    assert rel_l2(a.probes(), b.probes()) < 1e-5
 
 
 def _custom(nx, ny, nz, boundary, npml, v_frac=1.0, L=2, steps=80, seed=0):
@@ -120,9 +142,9 @@ def _custom(nx, ny, nz, boundary, npml, v_frac=1.0, L=2, steps=80, seed=0):
     ((29, 31, 37), oracle.CPML, 5, 1.0),
     ((70, 66, 45), oracle.CPML, 8, 2.2),
 ])
-def test_ragged_grids(fd, dims, boundary, npml, v_frac):
+def test_ragged_grids(fd, kernel, dims, boundary, npml, v_frac):
     w = _custom(*dims, boundary, npml, v_frac, L=2 if min(dims[:2]) > 2 * npml + 7 else 1)
-    run_pair(fd, w, [w.steps // 3, w.steps])
+    run_pair(fd, w, [w.steps // 3, w.steps], kernel)
 
 
 def test_zero_source_and_no_probes(fd):
@@ -157,17 +179,17 @@ def test_errors_are_reported(fd):
     sim.sync()
 
 
-def test_steps_are_deterministic_and_resumable(fd):
+def test_steps_are_deterministic_and_resumable(fd, kernel):
     w = W.greisen_small(nx=40, ny=36, nz=90, steps=120, n_probes=4)
-    a = fd.Simulation.from_workload(w)
+    a = fd.Simulation.from_workload(w, kernel=kernel)
     a.step(w.steps)
     ta = a.probes()
     fa = [a.field(c) for c in range(6)]
-    b = fd.Simulation.from_workload(w)
+    b = fd.Simulation.from_workload(w, kernel=kernel)
     b.step(50)
     blob = b.save_state()
     b.step(20)                # diverge, then restore
-    c = fd.Simulation.from_workload(w)
+    c = fd.Simulation.from_workload(w, kernel=kernel)
     c.load_state(blob)
     assert c.steps_done == 50
     c.step(w.steps - 50)

@@ -205,8 +205,9 @@ def greisen_small(seed: int = 2002, nx: int = 64, ny: int = 56, nz: int = 200, n
     """The greisen384 physics on a grid the oracle finishes in seconds: same dx,
     dt, CPML depth, Greisen profile (the first nz cells of it) and NKG spread;
     detectors at r in [0.2, 0.45] m."""
+    r_hi = min(0.45, (min(nx, ny) // 2 - npml - 2) * 0.02)
     w = greisen384(seed=seed, nx=nx, ny=ny, nz=nz, npml=npml, steps=steps, n_probes=n_probes,
-                   r_lo=0.2, r_hi=min(0.45, (min(nx, ny) // 2 - npml - 2) * 0.02))
+                   r_lo=min(0.2, 0.5 * r_hi), r_hi=r_hi)
     w.name = f"greisen_small{nx}x{ny}x{nz}"
     return w
 
@@ -215,9 +216,9 @@ def gh_small(seed: int = 3003, nx: int = 60, ny: int = 52, nz: int = 160, npml: 
              steps: int = 250, n_probes: int = 16) -> Workload:
     """The gh640 physics (dx = 3 cm, 12-cell CPML, Gaisser-Hillas sum) on a
     small grid; subshowers spread over the short axis; r in [0.3, 0.45] m."""
+    r_hi = min(0.45, (min(nx, ny) // 2 - npml - 2) * 0.03)
     w = gh640(seed=seed, nx=nx, ny=ny, nz=nz, npml=npml, steps=steps, n_probes=n_probes,
-              r_lo=0.3, r_hi=min(0.45, (min(nx, ny) // 2 - npml - 2) * 0.03),
-              spread_m=0.5 * nz * 0.03)
+              r_lo=min(0.3, 0.5 * r_hi), r_hi=r_hi, spread_m=0.5 * nz * 0.03)
     # keep the subshowers short enough to develop inside the small grid
     p = w.profile
     rng = np.random.default_rng(seed + 1)
