@@ -180,7 +180,7 @@ def test_errors_are_reported(fd):
 
 
 def test_steps_are_deterministic_and_resumable(fd, kernel):
-    w = W.greisen_small(nx=40, ny=36, nz=90, steps=120, n_probes=4)
+    w = W.greisen_small(nx=64, ny=60, nz=80, steps=120, n_probes=4)
     a = fd.Simulation.from_workload(w, kernel=kernel)
     a.step(w.steps)
     ta = a.probes()

@@ -32,10 +32,32 @@ def test_benchmark_workload_matches_the_stated_configuration():
     assert w.dt == pytest.approx(34.2885e-12, rel=1e-5)
 
 
-def test_gpu_test_shapes_build():
-    # shapes used by tests/test_gpu_*.py
-    W.greisen_small(nx=40, ny=36, nz=90, steps=120, n_probes=4)
-    W.parity96(n=24, steps=10, n_probes=2)
-    W.parity96(n=32, steps=60, n_probes=2)
-    W.parity96(n=40, steps=120, n_probes=4)
-    W.greisen384(steps=120)
+GPU_TEST_SHAPES = [
+    # workloads built by tests/test_gpu_*.py and smoke(); each must be a valid
+    # simulation (the oracle rejects footprints or detectors outside the interior)
+    lambda: W.greisen_small(nx=64, ny=60, nz=80, steps=120, n_probes=4),
+    lambda: W.greisen_small(nx=72, ny=70, nz=140, steps=160, n_probes=6),
+    lambda: W.parity96(n=24, steps=10, n_probes=2),
+    lambda: W.parity96(n=24, steps=30, n_probes=3),
+    lambda: W.parity96(n=32, steps=60, n_probes=2),
+    lambda: W.parity96(n=32, steps=20, n_probes=2),
+    lambda: W.parity96(n=40, steps=120, n_probes=4),
+    W.greisen_small, W.gh_small, W.parity96,
+]
+
+
+@pytest.mark.parametrize("make", GPU_TEST_SHAPES)
+def test_gpu_test_shapes_are_valid(make):
+    import oracle
+    w = make()
+    oracle.from_workload(w)   # raises on an invalid footprint or detector
+
+
+def test_fullsize_test_workload_is_valid():
+    w = W.greisen384(steps=120)
+    ax = (w.nx // 2) * w.dx
+    lo = w.npml + 1
+    near = np.array([[ax + 0.24, ax, 0.46], [ax, ax - 0.32, 0.62], [ax + 0.2, ax + 0.2, 0.90],
+                     [ax - 0.5, ax + 0.1, 0.70]])
+    ijk = np.floor(near / w.dx + 0.5).astype(int)
+    assert ijk.min() >= lo and ijk[:, 0].max() <= w.nx - lo
