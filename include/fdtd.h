@@ -176,9 +176,11 @@ int fdtd_launch_count(fdtd_t h, int64_t *launches);
 const char *fdtd_kernel_name(fdtd_t h);
 
 /*
- * Select the field-update path: 1 = fused z-march (one pass per step, the
- * default when the device supports it), 0 = one H sweep then one E sweep.
- * Both compute the same update (Sec. III.A); the unfused pair is a cross-check.
+ * Select the field-update path (all compute the same update, Sec. III.A):
+ *   1 = register-strip z-march, one pass per step (the default);
+ *   2 = TMA-staged z-march, one pass per step;
+ *   0 = one H sweep then one E sweep.
+ * Returns FDTD_ERR_ARG for a path the handle cannot run.
  */
 int fdtd_set_kernel(fdtd_t h, int which);
 

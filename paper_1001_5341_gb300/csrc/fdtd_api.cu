@@ -49,6 +49,7 @@ void release(fdtd_ctx *h) {
     free_dev(h->d_result);
     free_dev(h->d_flags);
     fused_release(h);
+    strip_release(h);
     for (cudaEvent_t e : h->timing.ev) cudaEventDestroy(e);
     delete h;
 }
@@ -193,10 +194,12 @@ int fdtd_create(fdtd_t *out, int nx, int ny, int nz, double dx, double dt, doubl
         return fail(FDTD_ERR_OOM);
     }
     if ((rc = note(h, cudaStreamSynchronize(h->stream))) != FDTD_OK) return fail(rc);
-    // the fused z-march is the default field-update path; the unfused pair of
-    // sweeps stays available (fdtd_set_kernel) as a cross-check
+    // the register-strip z-march is the default field-update path; the
+    // TMA-staged z-march and the unfused pair of sweeps stay available
+    // (fdtd_set_kernel) as cross-checks
     h->kernel = 0;
-    if (fused_prepare(h) == FDTD_OK) h->kernel = 1;
+    if (fused_prepare(h) == FDTD_OK) h->kernel = 2;
+    if (strip_prepare(h) == FDTD_OK) h->kernel = 1;
     cudaGetLastError();
     *out = h;
     return FDTD_OK;
@@ -311,6 +314,8 @@ int fdtd_step(fdtd_t h, int n) {
     if (h->np > 0 && h->steps + n > h->max_steps) return FDTD_ERR_CAPACITY;
     for (int s = 0; s < n; ++s) {
         if (h->kernel == 1) {
+            timed_launch(h, [](const fdtd_ctx *c, cudaStream_t st) { launch_strip(const_cast<fdtd_ctx *>(c), st); });
+        } else if (h->kernel == 2) {
             timed_launch(h, [](const fdtd_ctx *c, cudaStream_t st) { launch_fused(const_cast<fdtd_ctx *>(c), st); });
         } else {
             timed_launch(h, launch_update_h);
@@ -529,13 +534,14 @@ int fdtd_launch_count(fdtd_t h, int64_t *launches) {
 }
 
 const char *fdtd_kernel_name(fdtd_t h) {
-    if (h && h->kernel == 1) return fused_name();
+    if (h && h->kernel == 1) return strip_name();
+    if (h && h->kernel == 2) return fused_name();
     return "unfused-h-then-e";
 }
 
 int fdtd_set_kernel(fdtd_t h, int which) {
-    if (!h || which < 0 || which > 1) return FDTD_ERR_ARG;
-    if (which == 1 && !h->fused) return FDTD_ERR_ARG;
+    if (!h || which < 0 || which > 2) return FDTD_ERR_ARG;
+    if ((which == 1 && !h->strip) || (which == 2 && !h->fused)) return FDTD_ERR_ARG;
     h->kernel = which;
     return FDTD_OK;
 }

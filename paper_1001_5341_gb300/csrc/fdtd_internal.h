@@ -77,6 +77,12 @@ struct Source {
     const double *w;          // lateral weights (2L+1)^2
 };
 
+// window of planes whose Ez edges may carry the shower's current in step n
+struct SourceStep {
+    long long n;
+    int klo, khi;
+};
+
 struct Probes {
     int n, max_steps;
     const int *ijk;           // [n][3]
@@ -109,8 +115,10 @@ struct fdtd_ctx {
     size_t psi_axis[3];       // floats of one psi array of each axis
     float *coef_block;        // aE,bE,aH,bH per axis
     const float *aE[3], *bE[3], *aH[3], *bH[3];
-    int kernel;               // field-update path: 0 unfused, 1 fused z-march
-    void *fused;              // host state of the fused path (tensor maps, launch shape)
+    int kernel;               // field-update path: 0 unfused sweeps, 1 register-strip
+                              // z-march, 2 TMA-staged z-march
+    void *fused;              // host state of the TMA path (tensor maps, launch shape)
+    void *strip;              // host state of the register-strip path
     int *d_flags;             // device error flags (bit 0: a bounded wait gave up)
     int num_sms;
 
@@ -156,6 +164,12 @@ int fused_prepare(fdtd_ctx *h);   // tensor maps + launch shape; FDTD_OK or erro
 void launch_fused(fdtd_ctx *h, cudaStream_t s);
 const char *fused_name();
 void fused_release(fdtd_ctx *h);
+
+// register-strip z-march (kernels_strip.cu)
+int strip_prepare(fdtd_ctx *h);
+void launch_strip(fdtd_ctx *h, cudaStream_t s);
+const char *strip_name();
+void strip_release(fdtd_ctx *h);
 
 // host tables (tables.cpp)
 void cpml_coefficients(int n, int P, double dx, double dt, double eps_r, float *aE, float *bE,

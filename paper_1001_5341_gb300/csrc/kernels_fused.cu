@@ -346,7 +346,7 @@ typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, 
 
 }  // namespace
 
-const char *fused_name() { return "fused-zmarch-tma-64x8"; }
+const char *fused_name() { return "fused-tma-64x8"; }
 
 int fused_prepare(fdtd_ctx *h) {
     int major = 0, minor = 0;

@@ -31,4 +31,27 @@ __device__ __forceinline__ float source_term(const Source &s, int i, int j, int 
     return (float)(qbar * wij * s.coef * dC);
 }
 
+// The planes k whose Ez edges may carry current during step n: a host-side,
+// conservative window [klo, khi] around the charge's path (the device decides
+// each edge exactly in source_term).
+inline SourceStep source_window(const Source &s, long long n) {
+    SourceStep w;
+    w.n = n;
+    w.klo = 1;
+    w.khi = 0;  // empty
+    if (!s.active) return w;
+    double za = s.z0 + s.v * (double)n * s.dt, zb = s.z0 + s.v * (double)(n + 1) * s.dt;
+    double lo = za < zb ? za : zb, hi = za < zb ? zb : za;
+    double klo = floor(lo / s.dx) - 2.0, khi = floor(hi / s.dx) + 2.0;
+    if (khi < (double)s.kmin || klo > (double)s.kmax) return w;
+    w.klo = klo < (double)s.kmin ? s.kmin : (int)klo;
+    w.khi = khi > (double)s.kmax ? s.kmax : (int)khi;
+    return w;
+}
+
+__device__ __forceinline__ float source_at(const Source &s, const SourceStep &w, int i, int j, int k) {
+    if (!s.active || k < w.klo || k > w.khi) return 0.0f;
+    return source_term(s, i, j, k, w.n);
+}
+
 }  // namespace fdtd

@@ -23,8 +23,9 @@ def fd():
     return m
 
 
-# both field-update paths: 1 = fused z-march (default), 0 = unfused sweeps
-@pytest.fixture(params=[1, 0], ids=["fused", "unfused"])
+# the field-update paths: 1 = register-strip z-march (default), 2 = TMA-staged
+# z-march, 0 = unfused sweeps
+@pytest.fixture(params=[1, 2, 0], ids=["strip", "tma", "unfused"])
 def kernel(request):
     return request.param
 
@@ -67,7 +68,7 @@ def compare_fields(sim, ref, tol=TOL):
 
 def run_pair(fd, w, snaps, kernel=1):
     sim = fd.Simulation.from_workload(w, kernel=kernel)
-    assert sim.kernel_name.startswith("fused" if kernel == 1 else "unfused")
+    assert sim.kernel_name.startswith("unfused" if kernel == 0 else "fused")
     ref = oracle.from_workload(w)
     done = 0
     out = []
@@ -101,11 +102,12 @@ def test_gh_small_cpml(fd, kernel):
     run_pair(fd, w, [w.steps], kernel)
 
 
-def test_fused_and_unfused_agree(fd):
-    """The two paths compute the same update; they may differ only by FP32
+@pytest.mark.parametrize("fused", [1, 2])
+def test_fused_and_unfused_agree(fd, fused):
+    """The paths compute the same update; they may differ only by FP32
     rounding (FMA contraction)."""
     w = W.greisen_small(nx=72, ny=70, nz=140, steps=160, n_probes=6)
-    a = fd.Simulation.from_workload(w, kernel=1)
+    a = fd.Simulation.from_workload(w, kernel=fused)
     b = fd.Simulation.from_workload(w, kernel=0)
     a.step(w.steps)
     b.step(w.steps)
