@@ -10,8 +10,10 @@
 // i = 30 t - 1 + L: lanes 1..30 own their column, lane 0 carries the column to
 // the left (its H is needed by lane 1's E update) and lane 31 the column to
 // the right (its E is needed by lane 30's H update).  Per plane k a lane
-//   - loads E^n(k) Ez, E^n(k+1) Ex/Ey and H^{n-1/2}(k) for rows j0-1 .. j0+TY
-//     of its column (E^n(k) Ex/Ey are carried from the previous plane);
+//   - has in registers E^n(k) Ez, E^n(k+1) Ex/Ey and H^{n-1/2}(k) for rows
+//     j0-1 .. j0+TY of its column (E^n(k) Ex/Ey carried from plane k-1), and
+//     issues the loads of plane k+1 into a second register buffer before it
+//     computes, so every warp always has a plane of loads in flight;
 //   - computes H^{n+1/2}(k) on rows j0-1 .. j0+TY-1; the x neighbour i+1 comes
 //     from lane L+1 by a warp shuffle, the y neighbour from the next register;
 //   - computes E^{n+1}(k) on its own rows; the x neighbour i-1 of H comes from
@@ -33,191 +35,215 @@
 namespace fdtd {
 namespace {
 
-constexpr int TY = 8;        // rows per lane
-constexpr int OWN = 30;      // owned columns per warp
-constexpr int WARPS = 8;     // warps per block, stacked in y
+#ifndef STRIP_TY
+#define STRIP_TY 4
+#endif
+#ifndef STRIP_MINB
+#define STRIP_MINB 2
+#endif
+#ifndef STRIP_WARPS
+#define STRIP_WARPS 8
+#endif
+constexpr int TY = STRIP_TY;        // rows per lane
+constexpr int OWN = 30;             // owned columns per warp
+constexpr int WARPS = STRIP_WARPS;  // warps per block, stacked in y
 constexpr int NT = 32 * WARPS;
 
 struct Args {
     Grid g;
-    const float *ein;   // Ex of the input set (Ey, Ez, Hx, Hy, Hz follow at +comp)
-    float *eout;        // Ex of the output set
+    const float *ex, *ey, *ez, *hx, *hy, *hz;   // input set
+    float *oex, *oey, *oez, *ohx, *ohy, *ohz;   // output set
     Cpml pml;
     Source src;
-    SourceStep ss;      // this step's charge position and window
+    SourceStep ss;      // this step's window of planes that may carry current
     float kE, kH;
     int chunk;          // planes per block
+};
+
+// One plane's loads: rows r = -1..TY of the lane's column at index a = r + 1.
+struct Plane {
+    float ez0[TY + 2];  // Ez^n(k)
+    float ex1[TY + 2];  // Ex^n(k+1)
+    float ey1[TY + 1];  // Ey^n(k+1)
+    float hx[TY + 1];   // Hx^{n-1/2}(k), becomes H^{n+1/2}(k)
+    float hz[TY + 1];   // Hz
+    float hy[TY];       // Hy (own rows only)
 };
 
 __device__ __forceinline__ float ld(const float *p, unsigned off, bool ok) {
     return ok ? __ldg(p + off) : 0.0f;
 }
 
-// psi^{new} = b psi + a d (H terms: read step n-1/2, write n+1/2 if owned)
-__device__ __forceinline__ float psih(const float *pin, float *pout, long long q, float a, float b,
+// Loads of plane k (E^n(k) Ez, E^n(k+1) Ex/Ey, H^{n-1/2}(k)); rowok[a] says row
+// j0 - 1 + a exists, colok the lane's column.
+__device__ __forceinline__ void load_plane(const Args &A, Plane &p, int k, unsigned cofs,
+                                           bool colok, int j0) {
+    const Grid &g = A.g;
+    const unsigned base = cofs + (unsigned)k * (unsigned)g.plane;
+    const unsigned up = (unsigned)g.plane;
+#pragma unroll
+    for (int a = 0; a < TY + 2; ++a) {
+        const int j = j0 + a - 1;
+        const bool ok = colok && j >= 0 && j <= g.ny;
+        const unsigned o = base + (unsigned)(a - 1) * (unsigned)g.pitch;
+        p.ez0[a] = ld(A.ez, o, ok);
+        p.ex1[a] = ld(A.ex, o + up, ok);
+        if (a < TY + 1) {
+            p.ey1[a] = ld(A.ey, o + up, ok);
+            p.hx[a] = ld(A.hx, o, ok);
+            p.hz[a] = ld(A.hz, o, ok);
+        }
+        if (a >= 1 && a < TY + 1) p.hy[a - 1] = ld(A.hy, o, ok);
+    }
+}
+
+// psi^{new} = b psi + a d; the derivative gains psi^{new}.  H terms read the
+// step n-1/2 copy and write the n+1/2 copy only for the cell's owner.
+__device__ __forceinline__ float psih(const float *pin, float *pout, unsigned q, float a, float b,
                                       float d, bool write) {
     float p = b * pin[q] + a * d;
     if (write) pout[q] = p;
     return d + p;
 }
-__device__ __forceinline__ float psie(float *pe, long long q, float a, float b, float d) {
+__device__ __forceinline__ float psie(float *pe, unsigned q, float a, float b, float d) {
     float p = b * pe[q] + a * d;
     pe[q] = p;
     return d + p;
 }
 
 template <bool SLOW>
-__device__ __forceinline__ void plane(const Args &A, int k, bool own, int lane, int i, int j0,
-                                      bool colok, bool lane_owns, unsigned cofs, float (&ex0)[TY + 2],
-                                      float (&ey0)[TY + 1], float (&hxp)[TY], float (&hyp)[TY]) {
+__device__ __forceinline__ void compute_plane(const Args &A, Plane &p, int k, bool own, int i,
+                                              int j0, bool colok, bool lane_owns, unsigned cofs,
+                                              float (&ex0)[TY + 2], float (&ey0)[TY + 1],
+                                              float (&hxp)[TY], float (&hyp)[TY]) {
     const Grid &g = A.g;
-    const size_t comp = (size_t)g.comp;  // component stride (pointer arithmetic in 64 bits)
-    const unsigned plane_off = (unsigned)k * (unsigned)g.plane;  // offsets inside one component
-    const unsigned pitch = (unsigned)g.pitch;
-    const float *Exi = A.ein, *Eyi = Exi + comp, *Ezi = Eyi + comp;
-    const float *Hxi = Ezi + comp, *Hyi = Hxi + comp, *Hzi = Hyi + comp;
-    // rows r = -1..TY map to array index a = r + 1; row j = j0 + r
-    float ez0[TY + 2], ex1[TY + 2], ey1[TY + 1], hx[TY + 1], hy[TY], hz[TY + 1];
-#pragma unroll
-    for (int a = 0; a < TY + 2; ++a) {
-        const int j = j0 + a - 1;
-        const bool ok = colok && j >= 0 && j <= g.ny;
-        const unsigned o = cofs + plane_off + (unsigned)(a - 1) * pitch;
-        ez0[a] = ld(Ezi, o, ok);
-        ex1[a] = ld(Exi, o + (unsigned)g.plane, ok);
-        if (a < TY + 1) {
-            ey1[a] = ld(Eyi, o + (unsigned)g.plane, ok);
-            hx[a] = ld(Hxi, o, ok);
-            hz[a] = ld(Hzi, o, ok);
-        }
-        if (a >= 1 && a < TY + 1) hy[a - 1] = ld(Hyi, o, ok);
-    }
-
+    const Cpml &pm = A.pml;
     // ---- H^{n+1/2}(k) on rows j0-1 .. j0+TY-1 ----
     const float kH = A.kH;
+    int lx = -1, lz = -1;
+    if (SLOW) {
+        lx = (colok && i < g.nx) ? slab_cell(i, g.nx, pm.P) : -1;
+        lz = slab_cell(k, g.nz, pm.P);
+    }
 #pragma unroll
     for (int a = 0; a < TY + 1; ++a) {
         const int j = j0 + a - 1;
-        const float ezR = __shfl_down_sync(0xffffffffu, ez0[a], 1);
+        const float ezR = __shfl_down_sync(0xffffffffu, p.ez0[a], 1);
         const float eyR = __shfl_down_sync(0xffffffffu, ey0[a], 1);
-        float dyx = ez0[a + 1] - ez0[a];      // Hx: dEz/dy
-        float dzx = ey1[a] - ey0[a];          //     dEy/dz
-        float dxz = eyR - ey0[a];             // Hz: dEy/dx
-        float dyz = ex0[a + 1] - ex0[a];      //     dEx/dy
-        float dzy = 0.0f, dxy = 0.0f;         // Hy (own rows only)
+        float dyx = p.ez0[a + 1] - p.ez0[a];   // Hx: dEz/dy
+        float dzx = p.ey1[a] - ey0[a];         //     dEy/dz
+        float dxz = eyR - ey0[a];              // Hz: dEy/dx
+        float dyz = ex0[a + 1] - ex0[a];       //     dEx/dy
+        float dzy = 0.0f, dxy = 0.0f;          // Hy (own rows only)
         if (a >= 1) {
-            dzy = ex1[a] - ex0[a];
-            dxy = ezR - ez0[a];
+            dzy = p.ex1[a] - ex0[a];
+            dxy = ezR - p.ez0[a];
         }
         if (SLOW) {
-            // psi of the H update: read at n-1/2 always, written at n+1/2 only by
-            // the owner of the cell and only for components the step updates
-            const Cpml &p = A.pml;
-            const bool w = own && a >= 1 && lane_owns && j >= 0 && j < g.ny && i < g.nx;
-            const bool wx = w && i >= 1, wy = w && j >= 1, wz = w && k >= 1;
             const bool in = colok && i < g.nx && j >= 0 && j < g.ny;
-            const int lx = in ? slab_cell(i, g.nx, p.P) : -1;
-            const int ly = in ? slab_cell(j, g.ny, p.P) : -1;
-            const int lz = in ? slab_cell(k, g.nz, p.P) : -1;
+            const bool w = in && own && a >= 1 && lane_owns;
+            const bool wx = w && i >= 1, wy = w && j >= 1, wz = w && k >= 1;
+            const int ly = in ? slab_cell(j, g.ny, pm.P) : -1;
             if (ly >= 0) {
-                const long long q = psi_y(g, p.W, i, ly, k);
-                const float aa = p.aH[1][j], bb = p.bH[1][j];
-                dyx = psih(p.hin[1][0], p.hout[1][0], q, aa, bb, dyx, wx);
-                dyz = psih(p.hin[1][1], p.hout[1][1], q, aa, bb, dyz, wz);
+                const unsigned q = (unsigned)psi_y(g, pm.W, i, ly, k);
+                const float aa = pm.aH[1][j], bb = pm.bH[1][j];
+                dyx = psih(pm.hin[1][0], pm.hout[1][0], q, aa, bb, dyx, wx);
+                dyz = psih(pm.hin[1][1], pm.hout[1][1], q, aa, bb, dyz, wz);
             }
-            if (lz >= 0) {
-                const long long q = psi_z(g, p.W, i, j, lz);
-                const float aa = p.aH[2][k], bb = p.bH[2][k];
-                dzx = psih(p.hin[2][0], p.hout[2][0], q, aa, bb, dzx, wx);
-                if (a >= 1) dzy = psih(p.hin[2][1], p.hout[2][1], q, aa, bb, dzy, wy);
+            if (lz >= 0 && in) {
+                const unsigned q = (unsigned)psi_z(g, pm.W, i, j, lz);
+                const float aa = pm.aH[2][k], bb = pm.bH[2][k];
+                dzx = psih(pm.hin[2][0], pm.hout[2][0], q, aa, bb, dzx, wx);
+                if (a >= 1) dzy = psih(pm.hin[2][1], pm.hout[2][1], q, aa, bb, dzy, wy);
             }
-            if (lx >= 0) {
-                const long long q = psi_x(g, p.W, lx, j, k);
-                const float aa = p.aH[0][i], bb = p.bH[0][i];
-                if (a >= 1) dxy = psih(p.hin[0][0], p.hout[0][0], q, aa, bb, dxy, wy);
-                dxz = psih(p.hin[0][1], p.hout[0][1], q, aa, bb, dxz, wz);
+            if (lx >= 0 && in) {
+                const unsigned q = (unsigned)psi_x(g, pm.W, lx, j, k);
+                const float aa = pm.aH[0][i], bb = pm.bH[0][i];
+                if (a >= 1) dxy = psih(pm.hin[0][0], pm.hout[0][0], q, aa, bb, dxy, wy);
+                dxz = psih(pm.hin[0][1], pm.hout[0][1], q, aa, bb, dxz, wz);
             }
         }
-        hx[a] = hx[a] - kH * (dyx - dzx);
-        hz[a] = hz[a] - kH * (dxz - dyz);
-        if (a >= 1) hy[a - 1] = hy[a - 1] - kH * (dzy - dxy);
+        p.hx[a] = p.hx[a] - kH * (dyx - dzx);
+        p.hz[a] = p.hz[a] - kH * (dxz - dyz);
+        if (a >= 1) p.hy[a - 1] = p.hy[a - 1] - kH * (dzy - dxy);
     }
 
     if (own) {
-        // ---- store H^{n+1/2}(k), own rows ----
-        float *Hxo = A.eout + 3 * comp, *Hyo = Hxo + comp, *Hzo = Hyo + comp;
-        float *Exo = A.eout, *Eyo = Exo + comp, *Ezo = Eyo + comp;
-#pragma unroll
-        for (int r = 0; r < TY; ++r) {
-            const int j = j0 + r;
-            if (lane_owns && j < g.ny) {
-                const unsigned o = cofs + plane_off + (unsigned)r * pitch;
-                if (i >= 1) Hxo[o] = hx[r + 1];
-                if (j >= 1) Hyo[o] = hy[r];
-                if (k >= 1) Hzo[o] = hz[r + 1];
-            }
-        }
-        // ---- E^{n+1}(k), own rows ----
+        const unsigned base = cofs + (unsigned)k * (unsigned)g.plane;
         const float kE = A.kE;
 #pragma unroll
         for (int r = 0; r < TY; ++r) {
             const int j = j0 + r;
             const int a = r + 1;
-            const float hzL = __shfl_up_sync(0xffffffffu, hz[a], 1);
-            const float hyL = __shfl_up_sync(0xffffffffu, hy[r], 1);
-            float dyEx = hz[a] - hz[a - 1];
-            float dzEx = hy[r] - hyp[r];
-            float dzEy = hx[a] - hxp[r];
-            float dxEy = hz[a] - hzL;
-            float dxEz = hy[r] - hyL;
-            float dyEz = hx[a] - hx[a - 1];
+            const float hzL = __shfl_up_sync(0xffffffffu, p.hz[a], 1);
+            const float hyL = __shfl_up_sync(0xffffffffu, p.hy[r], 1);
+            float dyEx = p.hz[a] - p.hz[a - 1];
+            float dzEx = p.hy[r] - hyp[r];
+            float dzEy = p.hx[a] - hxp[r];
+            float dxEy = p.hz[a] - hzL;
+            float dxEz = p.hy[r] - hyL;
+            float dyEz = p.hx[a] - p.hx[a - 1];
             const bool store = lane_owns && j < g.ny;
             float src = 0.0f;
             if (SLOW && store) {
-                const Cpml &p = A.pml;
-                const int lx = slab_cell(i, g.nx, p.P), ly = slab_cell(j, g.ny, p.P),
-                          lz = slab_cell(k, g.nz, p.P);
+                const int ly = slab_cell(j, g.ny, pm.P);
                 if (ly >= 0) {
-                    const long long q = psi_y(g, p.W, i, ly, k);
-                    const float aa = p.aE[1][j], bb = p.bE[1][j];
-                    if (j >= 1 && k >= 1) dyEx = psie(p.e[1][0], q, aa, bb, dyEx);
-                    if (i >= 1 && j >= 1) dyEz = psie(p.e[1][1], q, aa, bb, dyEz);
+                    const unsigned q = (unsigned)psi_y(g, pm.W, i, ly, k);
+                    const float aa = pm.aE[1][j], bb = pm.bE[1][j];
+                    if (j >= 1 && k >= 1) dyEx = psie(pm.e[1][0], q, aa, bb, dyEx);
+                    if (i >= 1 && j >= 1) dyEz = psie(pm.e[1][1], q, aa, bb, dyEz);
                 }
                 if (lz >= 0) {
-                    const long long q = psi_z(g, p.W, i, j, lz);
-                    const float aa = p.aE[2][k], bb = p.bE[2][k];
-                    if (j >= 1 && k >= 1) dzEx = psie(p.e[2][0], q, aa, bb, dzEx);
-                    if (i >= 1 && k >= 1) dzEy = psie(p.e[2][1], q, aa, bb, dzEy);
+                    const unsigned q = (unsigned)psi_z(g, pm.W, i, j, lz);
+                    const float aa = pm.aE[2][k], bb = pm.bE[2][k];
+                    if (j >= 1 && k >= 1) dzEx = psie(pm.e[2][0], q, aa, bb, dzEx);
+                    if (i >= 1 && k >= 1) dzEy = psie(pm.e[2][1], q, aa, bb, dzEy);
                 }
                 if (lx >= 0) {
-                    const long long q = psi_x(g, p.W, lx, j, k);
-                    const float aa = p.aE[0][i], bb = p.bE[0][i];
-                    if (i >= 1 && k >= 1) dxEy = psie(p.e[0][0], q, aa, bb, dxEy);
-                    if (i >= 1 && j >= 1) dxEz = psie(p.e[0][1], q, aa, bb, dxEz);
+                    const unsigned q = (unsigned)psi_x(g, pm.W, lx, j, k);
+                    const float aa = pm.aE[0][i], bb = pm.bE[0][i];
+                    if (i >= 1 && k >= 1) dxEy = psie(pm.e[0][0], q, aa, bb, dxEy);
+                    if (i >= 1 && j >= 1) dxEz = psie(pm.e[0][1], q, aa, bb, dxEz);
                 }
                 src = source_at(A.src, A.ss, i, j, k);
             }
             if (store) {
-                const unsigned o = cofs + plane_off + (unsigned)r * pitch;
-                if (j >= 1 && k >= 1) Exo[o] = ex0[a] + kE * (dyEx - dzEx);
-                if (i >= 1 && k >= 1) Eyo[o] = ey0[a] + kE * (dzEy - dxEy);
-                if (i >= 1 && j >= 1) Ezo[o] = ez0[a] + kE * (dxEz - dyEz) + src;
+                const unsigned o = base + (unsigned)r * (unsigned)g.pitch;
+                if (i >= 1) A.ohx[o] = p.hx[a];
+                if (j >= 1) A.ohy[o] = p.hy[r];
+                if (k >= 1) A.ohz[o] = p.hz[a];
+                if (j >= 1 && k >= 1) A.oex[o] = ex0[a] + kE * (dyEx - dzEx);
+                if (i >= 1 && k >= 1) A.oey[o] = ey0[a] + kE * (dzEy - dxEy);
+                if (i >= 1 && j >= 1) A.oez[o] = p.ez0[a] + kE * (dxEz - dyEz) + src;
             }
         }
     }
     // carry to the next plane
 #pragma unroll
     for (int r = 0; r < TY; ++r) {
-        hxp[r] = hx[r + 1];
-        hyp[r] = hy[r];
+        hxp[r] = p.hx[r + 1];
+        hyp[r] = p.hy[r];
     }
 #pragma unroll
-    for (int a = 0; a < TY + 2; ++a) ex0[a] = ex1[a];
+    for (int a = 0; a < TY + 2; ++a) ex0[a] = p.ex1[a];
 #pragma unroll
-    for (int a = 0; a < TY + 1; ++a) ey0[a] = ey1[a];
+    for (int a = 0; a < TY + 1; ++a) ey0[a] = p.ey1[a];
 }
 
-__global__ void __launch_bounds__(NT, 2) k_strip(const Args A) {
+__device__ __forceinline__ void do_plane(const Args &A, Plane &p, int k, bool own, int i, int j0,
+                                         bool colok, bool lane_owns, unsigned cofs, bool xy_slow,
+                                         bool src_xy, float (&ex0)[TY + 2], float (&ey0)[TY + 1],
+                                         float (&hxp)[TY], float (&hyp)[TY]) {
+    const int P = A.pml.P;
+    const bool slow = xy_slow || (P > 0 && (k <= P || k >= A.g.nz - P)) ||
+                      (src_xy && k >= A.ss.klo && k <= A.ss.khi);
+    if (slow)
+        compute_plane<true>(A, p, k, own, i, j0, colok, lane_owns, cofs, ex0, ey0, hxp, hyp);
+    else
+        compute_plane<false>(A, p, k, own, i, j0, colok, lane_owns, cofs, ex0, ey0, hxp, hyp);
+}
+
+__global__ void __launch_bounds__(NT, STRIP_MINB) k_strip(const Args A) {
     const Grid &g = A.g;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -230,17 +256,17 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const Args A) {
     const int kstart = k0 > 0 ? k0 - 1 : 0;
     const bool colok = i >= 0 && i <= g.nx;
     const bool lane_owns = lane >= 1 && lane <= OWN && i < g.nx;
-    // offset of (i, j0) inside a component plane; row j0 + r is cofs + r * pitch
-    // (unsigned wrap-around for r = -1 at j0 = 0 is never dereferenced: the load
+    // offset of (i, j0) inside one component plane; row j0 + r is cofs + r * pitch
+    // (the unsigned wrap-around at r = -1, j0 = 0 is never dereferenced: the load
     // predicate tests j >= 0)
     const unsigned cofs = colok ? (unsigned)i + (unsigned)j0 * (unsigned)g.pitch : 0u;
 
     // warp-uniform: does the strip meet an x/y PML slab or the current's footprint?
     const int P = A.pml.P;
     const int ilo = (int)blockIdx.x * OWN - 1, ihi = ilo + 31;
-    bool xy_pml = P > 0 && (ilo <= P || ihi >= g.nx - P || j0 - 1 <= P || j0 + TY - 1 >= g.ny - P);
-    bool src_xy = A.src.active && ilo <= A.src.ic + A.src.L && ihi >= A.src.ic - A.src.L &&
-                  j0 <= A.src.jc + A.src.L && j0 + TY - 1 >= A.src.jc - A.src.L;
+    const bool xy_slow = P > 0 && (ilo <= P || ihi >= g.nx - P || j0 - 1 <= P || j0 + TY - 1 >= g.ny - P);
+    const bool src_xy = A.src.active && ilo <= A.src.ic + A.src.L && ihi >= A.src.ic - A.src.L &&
+                        j0 <= A.src.jc + A.src.L && j0 + TY - 1 >= A.src.jc - A.src.L;
 
     float ex0[TY + 2], ey0[TY + 1], hxp[TY], hyp[TY];
     {
@@ -249,20 +275,25 @@ __global__ void __launch_bounds__(NT, 2) k_strip(const Args A) {
         for (int a = 0; a < TY + 2; ++a) {
             const int j = j0 + a - 1;
             const bool ok = colok && j >= 0 && j <= g.ny;
-            ex0[a] = ld(A.ein, o0 + (unsigned)(a - 1) * (unsigned)g.pitch, ok);
-            if (a < TY + 1) ey0[a] = ld(A.ein + (size_t)g.comp, o0 + (unsigned)(a - 1) * (unsigned)g.pitch, ok);
+            ex0[a] = ld(A.ex, o0 + (unsigned)(a - 1) * (unsigned)g.pitch, ok);
+            if (a < TY + 1) ey0[a] = ld(A.ey, o0 + (unsigned)(a - 1) * (unsigned)g.pitch, ok);
         }
 #pragma unroll
         for (int r = 0; r < TY; ++r) { hxp[r] = 0.0f; hyp[r] = 0.0f; }
     }
-    for (int k = kstart; k < k1; ++k) {
-        const bool own = k >= k0;
-        const bool slow = xy_pml || (P > 0 && (k <= P || k >= g.nz - P)) ||
-                          (src_xy && k >= A.ss.klo && k <= A.ss.khi);
-        if (slow)
-            plane<true>(A, k, own, lane, i, j0, colok, lane_owns, cofs, ex0, ey0, hxp, hyp);
-        else
-            plane<false>(A, k, own, lane, i, j0, colok, lane_owns, cofs, ex0, ey0, hxp, hyp);
+    // two register buffers: while plane k is computed from one, the loads of
+    // plane k+1 are in flight into the other
+    Plane pa, pb;
+    load_plane(A, pa, kstart, cofs, colok, j0);
+    int k = kstart;
+    while (k < k1) {
+        if (k + 1 < k1) load_plane(A, pb, k + 1, cofs, colok, j0);
+        do_plane(A, pa, k, k >= k0, i, j0, colok, lane_owns, cofs, xy_slow, src_xy, ex0, ey0, hxp, hyp);
+        ++k;
+        if (k >= k1) break;
+        if (k + 1 < k1) load_plane(A, pa, k + 1, cofs, colok, j0);
+        do_plane(A, pb, k, k >= k0, i, j0, colok, lane_owns, cofs, xy_slow, src_xy, ex0, ey0, hxp, hyp);
+        ++k;
     }
 }
 
@@ -272,12 +303,14 @@ struct HostState {
 
 }  // namespace
 
-const char *strip_name() { return "fused-strip-30x8"; }
+const char *strip_name() { return "fused-strip-30x4"; }
 
 int strip_prepare(fdtd_ctx *h) {
     const Grid &g = h->g;
-    // 32-bit offsets inside one component array
+    // 32-bit offsets inside one component array and inside one psi array
     if ((unsigned long long)g.comp >= (1ull << 32)) return FDTD_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if ((unsigned long long)h->psi_axis[a] >= (1ull << 32)) return FDTD_ERR_ARG;
     HostState *st = new HostState();
     st->bx = (g.nx + OWN - 1) / OWN;
     st->by = (g.ny + WARPS * TY - 1) / (WARPS * TY);
@@ -300,10 +333,14 @@ void strip_release(fdtd_ctx *h) {
 
 void launch_strip(fdtd_ctx *h, cudaStream_t s) {
     HostState *st = static_cast<HostState *>(h->strip);
+    const Grid &g = h->g;
     Args a;
-    a.g = h->g;
-    a.ein = h->fields[h->cur];
-    a.eout = h->fields[h->cur ^ 1];
+    a.g = g;
+    const float *in = h->fields[h->cur];
+    float *out = h->fields[h->cur ^ 1];
+    const size_t c = (size_t)g.comp;
+    a.ex = in; a.ey = in + c; a.ez = in + 2 * c; a.hx = in + 3 * c; a.hy = in + 4 * c; a.hz = in + 5 * c;
+    a.oex = out; a.oey = out + c; a.oez = out + 2 * c; a.ohx = out + 3 * c; a.ohy = out + 4 * c; a.ohz = out + 5 * c;
     a.pml = cpml_view(h);
     a.src = h->src;
     a.ss = source_window(h->src, h->steps);
