@@ -163,7 +163,7 @@ int fdtd_load_state(fdtd_t h, const void *buf, size_t bytes);
 
 /*
  * Instrumentation.  fdtd_timing_begin(h, max_launches) records a CUDA event pair
- * around each launch of the field-update kernel(s) on the handle's stream;
+ * around each launch of the main field-update kernel(s) on the handle's stream;
  * fdtd_timing_end(h, &ms, &launches) synchronises and returns their summed
  * device time and count.  fdtd_launch_count returns the number of kernels the
  * handle has launched since creation.
@@ -172,12 +172,18 @@ int fdtd_timing_begin(fdtd_t h, int max_launches);
 int fdtd_timing_end(fdtd_t h, double *total_ms, int *launches);
 int fdtd_launch_count(fdtd_t h, int64_t *launches);
 
+/* Cells updated by one launch of the timed kernel(s) (the whole grid for the
+   sweeps; the CPML-free interior box for the fused z-march, whose shell of
+   CPML cells is updated by two small untimed launches). */
+int fdtd_timed_cells(fdtd_t h, int64_t *cells);
+
 /* Name of the field-update path in use (static string). */
 const char *fdtd_kernel_name(fdtd_t h);
 
 /*
  * Select the field-update path (all compute the same update, Sec. III.A):
- *   1 = register-strip z-march, one pass per step (the default);
+ *   1 = register-strip z-march over the CPML-free interior, one pass per step,
+ *       plus an H and an E sweep over the CPML shell (the default);
  *   2 = TMA-staged z-march, one pass per step;
  *   0 = one H sweep then one E sweep.
  * Returns FDTD_ERR_ARG for a path the handle cannot run.

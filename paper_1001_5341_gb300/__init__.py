@@ -53,6 +53,7 @@ _SIGS = {
     "fdtd_timing_begin": (_i, [_vp, _i]),
     "fdtd_timing_end": (_i, [_vp, _pd, _pi]),
     "fdtd_launch_count": (_i, [_vp, _pi64]),
+    "fdtd_timed_cells": (_i, [_vp, _pi64]),
     "fdtd_kernel_name": (C.c_char_p, [_vp]),
     "fdtd_set_kernel": (_i, [_vp, _i]),
     "fdtd_strerror": (C.c_char_p, [_i]),
@@ -279,6 +280,13 @@ class Simulation:
     def launches(self):
         v = C.c_int64()
         check(fdtd_launch_count(self.h, C.byref(v)), "fdtd_launch_count")
+        return v.value
+
+    @property
+    def timed_cells(self):
+        """Cells one launch of the timed kernel updates."""
+        v = C.c_int64()
+        check(fdtd_timed_cells(self.h, C.byref(v)), "fdtd_timed_cells")
         return v.value
 
     @property

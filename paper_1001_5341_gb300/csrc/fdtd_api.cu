@@ -315,6 +315,7 @@ int fdtd_step(fdtd_t h, int n) {
     for (int s = 0; s < n; ++s) {
         if (h->kernel == 1) {
             timed_launch(h, [](const fdtd_ctx *c, cudaStream_t st) { launch_strip(const_cast<fdtd_ctx *>(c), st); });
+            h->launches += launch_strip_shell(h, h->stream);
         } else if (h->kernel == 2) {
             timed_launch(h, [](const fdtd_ctx *c, cudaStream_t st) { launch_fused(const_cast<fdtd_ctx *>(c), st); });
         } else {
@@ -524,6 +525,13 @@ int fdtd_timing_end(fdtd_t h, double *total_ms, int *launches) {
     }
     *total_ms = tot;
     *launches = t.used;
+    return FDTD_OK;
+}
+
+int fdtd_timed_cells(fdtd_t h, int64_t *cells) {
+    if (!h || !cells) return FDTD_ERR_ARG;
+    const Grid &g = h->g;
+    *cells = h->kernel == 1 ? strip_interior_cells(h) : (int64_t)g.nx * g.ny * g.nz;
     return FDTD_OK;
 }
 

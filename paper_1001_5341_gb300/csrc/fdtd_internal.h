@@ -90,6 +90,14 @@ struct Probes {
     float *trace;             // [n][max_steps][2]
 };
 
+// Cells outside the fused kernel's interior box: up to six disjoint boxes
+// [lo, hi] (inclusive, cell indices) and the prefix sums of their cell counts.
+struct Shell {
+    int n;
+    int lo[6][3], hi[6][3];
+    long long start[7];
+};
+
 struct TimingRec {
     std::vector<cudaEvent_t> ev; // start/stop pairs
     int used = 0;
@@ -156,6 +164,7 @@ void launch_update_e(const fdtd_ctx *h, cudaStream_t s);
 void launch_mur(const fdtd_ctx *h, cudaStream_t s);
 void launch_probes(const fdtd_ctx *h, cudaStream_t s);
 void launch_energy(const fdtd_ctx *h, cudaStream_t s, int *launches);
+void launch_shell(const fdtd_ctx *h, const Shell &sh, cudaStream_t s, int *launches);
 void launch_set_field(const fdtd_ctx *h, int comp, const float *compact, cudaStream_t s);
 void launch_get_field(const fdtd_ctx *h, int comp, float *compact, cudaStream_t s);
 
@@ -168,6 +177,8 @@ void fused_release(fdtd_ctx *h);
 // register-strip z-march (kernels_strip.cu)
 int strip_prepare(fdtd_ctx *h);
 void launch_strip(fdtd_ctx *h, cudaStream_t s);
+int launch_strip_shell(fdtd_ctx *h, cudaStream_t s);   // returns kernels launched
+long long strip_interior_cells(const fdtd_ctx *h);
 const char *strip_name();
 void strip_release(fdtd_ctx *h);
 

@@ -34,14 +34,11 @@ __device__ __forceinline__ void cpml_pingpong(const float *pin, float *pout, con
     d = d + p;
 }
 
+// H^{n+1/2} of the components owned by cell (i,j,k).
 // Ein: Ex (Ey, Ez follow at +comp); Hin, Hout: Hx (Hy, Hz follow at +comp).
-__global__ void __launch_bounds__(256) k_update_h(Grid g, const float *__restrict__ Ein,
-                                                  const float *__restrict__ Hin,
-                                                  float *__restrict__ Hout, Cpml pml, float kH) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y * blockDim.y + threadIdx.y;
-    int k = blockIdx.z;
-    if (i >= g.nx || j >= g.ny) return;
+__device__ __forceinline__ void cell_h(const Grid &g, const float *__restrict__ Ein,
+                                       const float *__restrict__ Hin, float *__restrict__ Hout,
+                                       const Cpml &pml, float kH, int i, int j, int k) {
     const float *Ex = Ein, *Ey = Ein + g.comp, *Ez = Ein + 2 * g.comp;
     long long c = gidx(g, i, j, k);
     const int P = pml.P, W = pml.W;
@@ -69,15 +66,12 @@ __global__ void __launch_bounds__(256) k_update_h(Grid g, const float *__restric
     }
 }
 
+// E^{n+1} of the components owned by cell (i,j,k).
 // Ein, Eout: Ex of sets cur / cur^1; Hnew: Hx of set cur^1.
-__global__ void __launch_bounds__(256) k_update_e(Grid g, const float *__restrict__ Ein,
-                                                  const float *__restrict__ Hnew,
-                                                  float *__restrict__ Eout, Cpml pml, float kE,
-                                                  Source src, long long n) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y * blockDim.y + threadIdx.y;
-    int k = blockIdx.z;
-    if (i >= g.nx || j >= g.ny) return;
+__device__ __forceinline__ void cell_e(const Grid &g, const float *__restrict__ Ein,
+                                       const float *__restrict__ Hnew, float *__restrict__ Eout,
+                                       const Cpml &pml, float kE, const Source &src, long long n,
+                                       int i, int j, int k) {
     const float *Hx = Hnew, *Hy = Hnew + g.comp, *Hz = Hnew + 2 * g.comp;
     long long c = gidx(g, i, j, k);
     const int P = pml.P, W = pml.W;
@@ -107,6 +101,27 @@ __global__ void __launch_bounds__(256) k_update_e(Grid g, const float *__restric
     }
 }
 
+__global__ void __launch_bounds__(256) k_update_h(Grid g, const float *__restrict__ Ein,
+                                                  const float *__restrict__ Hin,
+                                                  float *__restrict__ Hout, Cpml pml, float kH) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    cell_h(g, Ein, Hin, Hout, pml, kH, i, j, k);
+}
+
+__global__ void __launch_bounds__(256) k_update_e(Grid g, const float *__restrict__ Ein,
+                                                  const float *__restrict__ Hnew,
+                                                  float *__restrict__ Eout, Cpml pml, float kE,
+                                                  Source src, long long n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    cell_e(g, Ein, Hnew, Eout, pml, kE, src, n, i, j, k);
+}
+
 void launch_update_h(const fdtd_ctx *h, cudaStream_t s) {
     const Grid &g = h->g;
     dim3 blk(32, 8, 1), grd((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
@@ -121,6 +136,58 @@ void launch_update_e(const fdtd_ctx *h, cudaStream_t s) {
     const float *in = h->fields[h->cur];
     float *out = h->fields[h->cur ^ 1];
     k_update_e<<<grd, blk, 0, s>>>(g, in, out + 3 * g.comp, out, cpml_view(h), (float)h->kE, h->src, h->steps);
+}
+
+// ---- the shell of cells outside the interior box --------------------------------
+// The shell is up to six disjoint boxes (z slabs, then y slabs, then x slabs of
+// what is left); cell number t of the shell is found by a scan of the boxes'
+// prefix sums.  H must be complete on the whole grid before E, so the shell is
+// updated by two launches after the interior kernel has written its cells.
+
+__device__ __forceinline__ bool shell_cell(const Shell &sh, long long t, int &i, int &j, int &k) {
+    int b = 0;
+    while (b < sh.n && t >= sh.start[b + 1]) ++b;
+    if (b >= sh.n) return false;
+    long long r = t - sh.start[b];
+    const int ex = sh.hi[b][0] - sh.lo[b][0] + 1, ey = sh.hi[b][1] - sh.lo[b][1] + 1;
+    i = sh.lo[b][0] + (int)(r % ex);
+    r /= ex;
+    j = sh.lo[b][1] + (int)(r % ey);
+    k = sh.lo[b][2] + (int)(r / ey);
+    return true;
+}
+
+__global__ void __launch_bounds__(256) k_shell_h(Grid g, Shell sh, const float *__restrict__ Ein,
+                                                 const float *__restrict__ Hin,
+                                                 float *__restrict__ Hout, Cpml pml, float kH) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    int i, j, k;
+    if (t >= sh.start[sh.n] || !shell_cell(sh, t, i, j, k)) return;
+    cell_h(g, Ein, Hin, Hout, pml, kH, i, j, k);
+}
+
+__global__ void __launch_bounds__(256) k_shell_e(Grid g, Shell sh, const float *__restrict__ Ein,
+                                                 const float *__restrict__ Hnew,
+                                                 float *__restrict__ Eout, Cpml pml, float kE,
+                                                 Source src, long long n) {
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    int i, j, k;
+    if (t >= sh.start[sh.n] || !shell_cell(sh, t, i, j, k)) return;
+    cell_e(g, Ein, Hnew, Eout, pml, kE, src, n, i, j, k);
+}
+
+void launch_shell(const fdtd_ctx *h, const Shell &sh, cudaStream_t s, int *launches) {
+    *launches = 0;
+    if (sh.n == 0 || sh.start[sh.n] == 0) return;
+    const Grid &g = h->g;
+    const float *in = h->fields[h->cur];
+    float *out = h->fields[h->cur ^ 1];
+    const long long cells = sh.start[sh.n];
+    const unsigned blocks = (unsigned)((cells + 255) / 256);
+    const Cpml pml = cpml_view(h);
+    k_shell_h<<<blocks, 256, 0, s>>>(g, sh, in, in + 3 * g.comp, out + 3 * g.comp, pml, (float)h->kH);
+    k_shell_e<<<blocks, 256, 0, s>>>(g, sh, in, out + 3 * g.comp, out, pml, (float)h->kE, h->src, h->steps);
+    *launches = 2;
 }
 
 // First-order Mur on the tangential E of face f (0..5 = x-, x+, y-, y+, z-, z+):

@@ -1,36 +1,37 @@
-// kernels_strip.cu -- one-pass leapfrog step as a vectorised register-strip
-// z-march.
+// kernels_strip.cu -- one-pass leapfrog step over the interior box as a
+// register-strip z-march.
 //
 // H^{n+1/2} and E^{n+1} of a plane are computed together (Yee scheme,
 // Sec. III.A; shower current of Sec. III.B), so a step reads E^n and
 // H^{n-1/2} once and writes H^{n+1/2} and E^{n+1} once: 24 B read and 24 B
-// written per cell (plus CPML memory in the slabs).
+// written per cell.
 //
-// Work decomposition.  A lane holds four consecutive x columns (one 16-byte
-// vector per row and component); a warp spans 128 columns starting at
-// x0 = 120 t - 4, and lanes 1..30 own their 120 columns while lane 0 (the four
-// columns to the left) and lane 31 (the four to the right) are halo.  Each
-// warp takes a strip of TY rows in y and marches up a chunk of z planes.  Per
-// plane k a lane
-//   - loads E^n(k) Ez, E^n(k+1) Ex/Ey and H^{n-1/2}(k) for rows j0-1 .. j0+TY
-//     (E^n(k) Ex/Ey are carried from the previous plane), 16 B per load;
-//   - computes H^{n+1/2}(k) on rows j0-1 .. j0+TY-1; the x neighbour of its
-//     last column is the next lane's first (warp shuffle), y neighbours are
-//     the next row's registers;
-//   - computes E^{n+1}(k) on its own rows; the x neighbour of its first column
-//     is the previous lane's last (shuffle), the z neighbours k-1 of Hx, Hy are
-//     kept in registers from the previous plane;
-//   - stores its own H and E as 16-byte vectors.  Entries the step does not
-//     update (faces, edges, the grid's padding) are written as zero: the
-//     boundary kernel that runs after overwrites the Mur faces, and PEC faces
-//     stay zero.
+// The kernel covers the interior box of cells [P+1, N-P-1] on each axis (the
+// whole grid without a CPML).  No CPML memory is touched there: the E-type
+// positions of the box lie outside the layers, and so do the H-type positions
+// P+1/2 .. N-P-3/2 and the halo H at cell P that the box's first cells need.
+// The shell of cells around the box is updated afterwards by kernels_basic.cu.
+//
+// Work decomposition.  A warp owns 30 consecutive x columns and a strip of TY
+// rows in y, and marches up a chunk of z planes.  Lane L sits on column
+// i = ilo + 30 t - 1 + L: lanes 1..30 own their column, lane 0 carries the
+// column to the left (its H is needed by lane 1's E update) and lane 31 the
+// column to the right (its E is needed by lane 30's H update).  Per plane k a
+// lane
+//   - has in registers E^n(k) Ez, E^n(k+1) Ex/Ey and H^{n-1/2}(k) for rows
+//     j0-1 .. j0+TY of its column (E^n(k) Ex/Ey carried from plane k-1), and
+//     issues the loads of plane k+1 into a second register buffer before it
+//     computes, so every warp keeps a plane of loads in flight;
+//   - computes H^{n+1/2}(k) on rows j0-1 .. j0+TY-1; the x neighbour i+1 comes
+//     from lane L+1 by a warp shuffle, the y neighbour from the next register;
+//   - computes E^{n+1}(k) on its own rows; the x neighbour i-1 of H comes from
+//     lane L-1 by a shuffle, the z neighbour k-1 of Hx, Hy from registers kept
+//     from the previous plane;
+//   - stores its own H and E.
 // Row j0-1 and lanes 0/31 are recomputed halo and never stored.  There is no
-// shared memory and no block-level barrier: warps are independent.
-//
-// The CPML terms and the shower current are evaluated only in a warp-uniform
-// slow path taken by warps whose strip meets a PML slab or the current's
-// footprint in this plane.  A chunk that starts at k0 > 0 first recomputes
-// H^{n+1/2}(k0-1) of its own rows (no stores).
+// shared memory and no block-level barrier: warps are independent.  A chunk
+// that starts above the box's first plane first recomputes H^{n+1/2}(k0-1) of
+// its own rows (no stores).
 #include <cuda_runtime.h>
 
 #include "fdtd_internal.h"
@@ -40,16 +41,16 @@ namespace fdtd {
 namespace {
 
 #ifndef STRIP_TY
-#define STRIP_TY 2
-#endif
-#ifndef STRIP_WARPS
-#define STRIP_WARPS 4
+#define STRIP_TY 4
 #endif
 #ifndef STRIP_MINB
-#define STRIP_MINB 3
+#define STRIP_MINB 2
+#endif
+#ifndef STRIP_WARPS
+#define STRIP_WARPS 8
 #endif
 constexpr int TY = STRIP_TY;        // rows per lane
-constexpr int OWN = 120;            // owned columns per warp (lanes 1..30)
+constexpr int OWN = 30;             // owned columns per warp
 constexpr int WARPS = STRIP_WARPS;  // warps per block, stacked in y
 constexpr int NT = 32 * WARPS;
 
@@ -57,285 +58,210 @@ struct Args {
     Grid g;
     const float *ex, *ey, *ez, *hx, *hy, *hz;   // input set
     float *oex, *oey, *oez, *ohx, *ohy, *ohz;   // output set
-    Cpml pml;
+    int ilo, ihi, jlo, jhi, klo, khi;           // interior box (cells, inclusive)
     Source src;
     SourceStep ss;      // this step's window of planes that may carry current
     float kE, kH;
     int chunk;          // planes per block
 };
 
-__device__ __forceinline__ float4 ld4(const float *p, unsigned off, bool ok) {
-    if (!ok) return make_float4(0.f, 0.f, 0.f, 0.f);
-    return __ldg(reinterpret_cast<const float4 *>(p + off));
-}
-
-__device__ __forceinline__ float &el(float4 &v, int e) {
-    return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
-}
-__device__ __forceinline__ float elc(const float4 &v, int e) {
-    return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
-}
-
-// psi^{new} = b psi + a d; the derivative gains psi^{new}.  H terms read the
-// step n-1/2 copy and write the n+1/2 copy only for the cell's owner.
-__device__ __forceinline__ float psih(const float *pin, float *pout, unsigned q, float a, float b,
-                                      float d, bool write) {
-    float p = b * pin[q] + a * d;
-    if (write) pout[q] = p;
-    return d + p;
-}
-__device__ __forceinline__ float psie(float *pe, unsigned q, float a, float b, float d) {
-    float p = b * pe[q] + a * d;
-    pe[q] = p;
-    return d + p;
-}
-
-struct Lane {
-    int c0;          // first of the lane's four columns
-    unsigned cofs;   // offset of (c0, j0) inside a component plane
-    bool colok;      // the lane's vector lies inside the padded row
-    bool owner;      // lanes 1..30
-    int j0;
+// One plane's loads: rows r = -1..TY of the lane's column at index a = r + 1.
+struct Plane {
+    float ez0[TY + 2];  // Ez^n(k)
+    float ex1[TY + 2];  // Ex^n(k+1)
+    float ey1[TY + 1];  // Ey^n(k+1)
+    float hx[TY + 1];   // Hx^{n-1/2}(k), becomes H^{n+1/2}(k)
+    float hz[TY + 1];   // Hz
+    float hy[TY];       // Hy (own rows only)
 };
 
-template <bool SLOW>
-__device__ __forceinline__ void plane_step(const Args &A, const Lane &L, int k, bool own,
-                                           float4 (&ex0)[TY + 2], float4 (&ey0)[TY + 1],
-                                           float4 (&hxp)[TY], float4 (&hyp)[TY]) {
+__device__ __forceinline__ float ld(const float *p, unsigned off, bool ok) {
+    return ok ? __ldg(p + off) : 0.0f;
+}
+
+// Loads of plane k (E^n(k) Ez, E^n(k+1) Ex/Ey, H^{n-1/2}(k)) for the lane's
+// column; a row is loaded if it lies on the node grid.
+__device__ __forceinline__ void load_plane(const Args &A, Plane &p, int k, unsigned cofs,
+                                           bool colok, int j0) {
     const Grid &g = A.g;
-    const unsigned pitch = (unsigned)g.pitch;
-    const unsigned base = L.cofs + (unsigned)k * (unsigned)g.plane;
+    const unsigned base = cofs + (unsigned)k * (unsigned)g.plane;
     const unsigned up = (unsigned)g.plane;
-    // rows r = -1..TY at index a = r + 1
-    float4 ez0[TY + 2], ex1[TY + 2], ey1[TY + 1], hx[TY + 1], hz[TY + 1], hy[TY];
 #pragma unroll
     for (int a = 0; a < TY + 2; ++a) {
-        const int j = L.j0 + a - 1;
-        const bool ok = L.colok && j >= 0 && j <= g.ny;
-        const unsigned o = base + (unsigned)(a - 1) * pitch;
-        ez0[a] = ld4(A.ez, o, ok);
-        ex1[a] = ld4(A.ex, o + up, ok);
+        const int j = j0 + a - 1;
+        const bool ok = colok && j >= 0 && j <= g.ny;
+        const unsigned o = base + (unsigned)(a - 1) * (unsigned)g.pitch;
+        p.ez0[a] = ld(A.ez, o, ok);
+        p.ex1[a] = ld(A.ex, o + up, ok);
         if (a < TY + 1) {
-            ey1[a] = ld4(A.ey, o + up, ok);
-            hx[a] = ld4(A.hx, o, ok);
-            hz[a] = ld4(A.hz, o, ok);
+            p.ey1[a] = ld(A.ey, o + up, ok);
+            p.hx[a] = ld(A.hx, o, ok);
+            p.hz[a] = ld(A.hz, o, ok);
         }
-        if (a >= 1 && a < TY + 1) hy[a - 1] = ld4(A.hy, o, ok);
+        if (a >= 1 && a < TY + 1) p.hy[a - 1] = ld(A.hy, o, ok);
     }
+}
 
-    const Cpml &pm = A.pml;
-    const float kH = A.kH, kE = A.kE;
-    const int lz = SLOW ? slab_cell(k, g.nz, pm.P) : -1;
-
+__device__ __forceinline__ void compute_plane(const Args &A, Plane &p, int k, bool own, int i,
+                                              int j0, bool lane_owns, unsigned cofs, bool src_here,
+                                              float (&ex0)[TY + 2], float (&ey0)[TY + 1],
+                                              float (&hxp)[TY], float (&hyp)[TY]) {
+    const Grid &g = A.g;
+    const float kH = A.kH;
     // ---- H^{n+1/2}(k) on rows j0-1 .. j0+TY-1 ----
 #pragma unroll
     for (int a = 0; a < TY + 1; ++a) {
-        const int j = L.j0 + a - 1;
-        // the column right of the lane's last one: the next lane's first
-        const float ezR = __shfl_down_sync(0xffffffffu, ez0[a].x, 1);
-        const float eyR = __shfl_down_sync(0xffffffffu, ey0[a].x, 1);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int i = L.c0 + e;
-            const float ezr = e < 3 ? elc(ez0[a], e + 1) : ezR;
-            const float eyr = e < 3 ? elc(ey0[a], e + 1) : eyR;
-            float dyx = elc(ez0[a + 1], e) - elc(ez0[a], e);   // Hx: dEz/dy
-            float dzx = elc(ey1[a], e) - elc(ey0[a], e);       //     dEy/dz
-            float dxz = eyr - elc(ey0[a], e);                  // Hz: dEy/dx
-            float dyz = elc(ex0[a + 1], e) - elc(ex0[a], e);   //     dEx/dy
-            float dzy = 0.f, dxy = 0.f;                        // Hy (own rows)
-            if (a >= 1) {
-                dzy = elc(ex1[a], e) - elc(ex0[a], e);
-                dxy = ezr - elc(ez0[a], e);
-            }
-            if (SLOW) {
-                const bool in = L.colok && i >= 0 && i < g.nx && j >= 0 && j < g.ny;
-                const bool w = in && own && a >= 1 && L.owner;
-                const bool wx = w && i >= 1, wy = w && j >= 1, wz = w && k >= 1;
-                const int lx = in ? slab_cell(i, g.nx, pm.P) : -1;
-                const int ly = in ? slab_cell(j, g.ny, pm.P) : -1;
-                if (ly >= 0) {
-                    const unsigned q = (unsigned)psi_y(g, pm.W, i, ly, k);
-                    const float aa = pm.aH[1][j], bb = pm.bH[1][j];
-                    dyx = psih(pm.hin[1][0], pm.hout[1][0], q, aa, bb, dyx, wx);
-                    dyz = psih(pm.hin[1][1], pm.hout[1][1], q, aa, bb, dyz, wz);
-                }
-                if (lz >= 0 && in) {
-                    const unsigned q = (unsigned)psi_z(g, pm.W, i, j, lz);
-                    const float aa = pm.aH[2][k], bb = pm.bH[2][k];
-                    dzx = psih(pm.hin[2][0], pm.hout[2][0], q, aa, bb, dzx, wx);
-                    if (a >= 1) dzy = psih(pm.hin[2][1], pm.hout[2][1], q, aa, bb, dzy, wy);
-                }
-                if (lx >= 0) {
-                    const unsigned q = (unsigned)psi_x(g, pm.W, lx, j, k);
-                    const float aa = pm.aH[0][i], bb = pm.bH[0][i];
-                    if (a >= 1) dxy = psih(pm.hin[0][0], pm.hout[0][0], q, aa, bb, dxy, wy);
-                    dxz = psih(pm.hin[0][1], pm.hout[0][1], q, aa, bb, dxz, wz);
-                }
-            }
-            el(hx[a], e) = elc(hx[a], e) - kH * (dyx - dzx);
-            el(hz[a], e) = elc(hz[a], e) - kH * (dxz - dyz);
-            if (a >= 1) el(hy[a - 1], e) = elc(hy[a - 1], e) - kH * (dzy - dxy);
-        }
+        const float ezR = __shfl_down_sync(0xffffffffu, p.ez0[a], 1);
+        const float eyR = __shfl_down_sync(0xffffffffu, ey0[a], 1);
+        p.hx[a] = p.hx[a] - kH * ((p.ez0[a + 1] - p.ez0[a]) - (p.ey1[a] - ey0[a]));
+        p.hz[a] = p.hz[a] - kH * ((eyR - ey0[a]) - (ex0[a + 1] - ex0[a]));
+        if (a >= 1) p.hy[a - 1] = p.hy[a - 1] - kH * ((p.ex1[a] - ex0[a]) - (ezR - p.ez0[a]));
     }
 
     if (own) {
+        const unsigned base = cofs + (unsigned)k * (unsigned)g.plane;
+        const float kE = A.kE;
 #pragma unroll
         for (int r = 0; r < TY; ++r) {
-            const int j = L.j0 + r;
+            const int j = j0 + r;
             const int a = r + 1;
-            // the column left of the lane's first one: the previous lane's last
-            const float hzL = __shfl_up_sync(0xffffffffu, hz[a].w, 1);
-            const float hyL = __shfl_up_sync(0xffffffffu, hy[r].w, 1);
-            float4 nex, ney, nez, ohx = hx[a], ohy = hy[r], ohz = hz[a];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int i = L.c0 + e;
-                const float hzl = e > 0 ? elc(hz[a], e - 1) : hzL;
-                const float hyl = e > 0 ? elc(hy[r], e - 1) : hyL;
-                float dyEx = elc(hz[a], e) - elc(hz[a - 1], e);
-                float dzEx = elc(hy[r], e) - elc(hyp[r], e);
-                float dzEy = elc(hx[a], e) - elc(hxp[r], e);
-                float dxEy = elc(hz[a], e) - hzl;
-                float dxEz = elc(hy[r], e) - hyl;
-                float dyEz = elc(hx[a], e) - elc(hx[a - 1], e);
-                float src = 0.f;
-                const bool inx = i >= 1 && i < g.nx;   // Ey, Ez, Hx live here
-                if (SLOW && L.owner && i >= 0 && i < g.nx && j < g.ny) {
-                    const int lx = slab_cell(i, g.nx, pm.P), ly = slab_cell(j, g.ny, pm.P);
-                    if (ly >= 0) {
-                        const unsigned q = (unsigned)psi_y(g, pm.W, i, ly, k);
-                        const float aa = pm.aE[1][j], bb = pm.bE[1][j];
-                        if (j >= 1 && k >= 1) dyEx = psie(pm.e[1][0], q, aa, bb, dyEx);
-                        if (inx && j >= 1) dyEz = psie(pm.e[1][1], q, aa, bb, dyEz);
-                    }
-                    if (lz >= 0) {
-                        const unsigned q = (unsigned)psi_z(g, pm.W, i, j, lz);
-                        const float aa = pm.aE[2][k], bb = pm.bE[2][k];
-                        if (j >= 1 && k >= 1) dzEx = psie(pm.e[2][0], q, aa, bb, dzEx);
-                        if (inx && k >= 1) dzEy = psie(pm.e[2][1], q, aa, bb, dzEy);
-                    }
-                    if (lx >= 0) {
-                        const unsigned q = (unsigned)psi_x(g, pm.W, lx, j, k);
-                        const float aa = pm.aE[0][i], bb = pm.bE[0][i];
-                        if (inx && k >= 1) dxEy = psie(pm.e[0][0], q, aa, bb, dxEy);
-                        if (inx && j >= 1) dxEz = psie(pm.e[0][1], q, aa, bb, dxEz);
-                    }
-                    if (inx && j >= 1) src = source_at(A.src, A.ss, i, j, k);
-                }
-                // entries the step does not update are written as zero
-                const bool ix = i >= 0 && i < g.nx;
-                el(nex, e) = (ix && j >= 1 && k >= 1) ? elc(ex0[a], e) + kE * (dyEx - dzEx) : 0.f;
-                el(ney, e) = (inx && k >= 1) ? elc(ey0[a], e) + kE * (dzEy - dxEy) : 0.f;
-                el(nez, e) = (inx && j >= 1) ? elc(ez0[a], e) + kE * (dxEz - dyEz) + src : 0.f;
-                if (!inx) el(ohx, e) = 0.f;
-                if (!(ix && j >= 1)) el(ohy, e) = 0.f;
-                if (!(ix && k >= 1)) el(ohz, e) = 0.f;
-            }
-            if (L.owner && L.colok && j < g.ny) {
-                const unsigned o = base + (unsigned)r * pitch;
-                *reinterpret_cast<float4 *>(A.ohx + o) = ohx;
-                *reinterpret_cast<float4 *>(A.ohy + o) = ohy;
-                *reinterpret_cast<float4 *>(A.ohz + o) = ohz;
-                *reinterpret_cast<float4 *>(A.oex + o) = nex;
-                *reinterpret_cast<float4 *>(A.oey + o) = ney;
-                *reinterpret_cast<float4 *>(A.oez + o) = nez;
+            const float hzL = __shfl_up_sync(0xffffffffu, p.hz[a], 1);
+            const float hyL = __shfl_up_sync(0xffffffffu, p.hy[r], 1);
+            if (lane_owns && j <= A.jhi) {
+                const unsigned o = base + (unsigned)r * (unsigned)g.pitch;
+                float src = 0.0f;
+                if (src_here) src = source_at(A.src, A.ss, i, j, k);
+                // components a cell owns on the grid's low faces are not updated
+                if (i >= 1) A.ohx[o] = p.hx[a];
+                if (j >= 1) A.ohy[o] = p.hy[r];
+                if (k >= 1) A.ohz[o] = p.hz[a];
+                if (j >= 1 && k >= 1)
+                    A.oex[o] = ex0[a] + kE * ((p.hz[a] - p.hz[a - 1]) - (p.hy[r] - hyp[r]));
+                if (i >= 1 && k >= 1)
+                    A.oey[o] = ey0[a] + kE * ((p.hx[a] - hxp[r]) - (p.hz[a] - hzL));
+                if (i >= 1 && j >= 1)
+                    A.oez[o] = p.ez0[a] + kE * ((p.hy[r] - hyL) - (p.hx[a] - p.hx[a - 1])) + src;
             }
         }
     }
     // carry to the next plane
 #pragma unroll
     for (int r = 0; r < TY; ++r) {
-        hxp[r] = hx[r + 1];
-        hyp[r] = hy[r];
+        hxp[r] = p.hx[r + 1];
+        hyp[r] = p.hy[r];
     }
 #pragma unroll
-    for (int a = 0; a < TY + 2; ++a) ex0[a] = ex1[a];
+    for (int a = 0; a < TY + 2; ++a) ex0[a] = p.ex1[a];
 #pragma unroll
-    for (int a = 0; a < TY + 1; ++a) ey0[a] = ey1[a];
+    for (int a = 0; a < TY + 1; ++a) ey0[a] = p.ey1[a];
 }
 
 __global__ void __launch_bounds__(NT, STRIP_MINB) k_strip(const Args A) {
     const Grid &g = A.g;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    Lane L;
-    const int x0 = (int)blockIdx.x * OWN - 4;
-    L.c0 = x0 + 4 * lane;
-    L.j0 = ((int)blockIdx.y * WARPS + warp) * TY;
-    if (L.j0 >= g.ny) return;  // the whole warp is above the grid
-    const int k0 = (int)blockIdx.z * A.chunk;
-    if (k0 >= g.nz) return;
-    const int k1 = min(g.nz, k0 + A.chunk);
+    const int i = A.ilo + (int)blockIdx.x * OWN - 1 + lane;
+    const int j0 = A.jlo + ((int)blockIdx.y * WARPS + warp) * TY;
+    if (j0 > A.jhi) return;  // the whole warp is outside the box
+    const int k0 = A.klo + (int)blockIdx.z * A.chunk;
+    if (k0 > A.khi) return;
+    const int k1 = min(A.khi + 1, k0 + A.chunk);
     const int kstart = k0 > 0 ? k0 - 1 : 0;
-    // a vector is loaded/stored only if it lies inside the padded row; pitch is
-    // a multiple of 32 and c0 of 4, so it lies wholly inside or wholly outside
-    L.colok = L.c0 >= 0 && L.c0 < g.pitch;
-    L.owner = lane >= 1 && lane <= 30 && L.c0 < g.nx;
-    // offset of (c0, j0) inside a component plane; row j0 + r is cofs + r*pitch
-    // (the unsigned wrap-around at r = -1, j0 = 0 is never dereferenced)
-    L.cofs = L.colok ? (unsigned)L.c0 + (unsigned)L.j0 * (unsigned)g.pitch : 0u;
+    const bool colok = i >= 0 && i <= g.nx;
+    const bool lane_owns = lane >= 1 && lane <= OWN && i <= A.ihi;
+    // offset of (i, j0) inside one component plane; row j0 + r is cofs + r * pitch
+    // (the unsigned wrap-around at r = -1, j0 = 0 is never dereferenced: the load
+    // predicate tests j >= 0)
+    const unsigned cofs = colok ? (unsigned)i + (unsigned)j0 * (unsigned)g.pitch : 0u;
+    // warp-uniform: does the strip meet the current's footprint?
+    const int xlo = A.ilo + (int)blockIdx.x * OWN;
+    const bool src_xy = A.src.active && xlo <= A.src.ic + A.src.L && xlo + OWN - 1 >= A.src.ic - A.src.L &&
+                        j0 <= A.src.jc + A.src.L && j0 + TY - 1 >= A.src.jc - A.src.L;
 
-    // warp-uniform: does the strip meet an x/y PML slab or the current's footprint?
-    const int P = A.pml.P;
-    const int ilo = x0, ihi = x0 + 127;
-    const bool xy_slow = P > 0 && (ilo <= P || ihi >= g.nx - P || L.j0 - 1 <= P || L.j0 + TY - 1 >= g.ny - P);
-    const bool src_xy = A.src.active && ilo <= A.src.ic + A.src.L && ihi >= A.src.ic - A.src.L &&
-                        L.j0 <= A.src.jc + A.src.L && L.j0 + TY - 1 >= A.src.jc - A.src.L;
-
-    float4 ex0[TY + 2], ey0[TY + 1], hxp[TY], hyp[TY];
+    float ex0[TY + 2], ey0[TY + 1], hxp[TY], hyp[TY];
     {
-        const unsigned o0 = L.cofs + (unsigned)kstart * (unsigned)g.plane;
+        const unsigned o0 = cofs + (unsigned)kstart * (unsigned)g.plane;
 #pragma unroll
         for (int a = 0; a < TY + 2; ++a) {
-            const int j = L.j0 + a - 1;
-            const bool ok = L.colok && j >= 0 && j <= g.ny;
-            ex0[a] = ld4(A.ex, o0 + (unsigned)(a - 1) * (unsigned)g.pitch, ok);
-            if (a < TY + 1) ey0[a] = ld4(A.ey, o0 + (unsigned)(a - 1) * (unsigned)g.pitch, ok);
+            const int j = j0 + a - 1;
+            const bool ok = colok && j >= 0 && j <= g.ny;
+            ex0[a] = ld(A.ex, o0 + (unsigned)(a - 1) * (unsigned)g.pitch, ok);
+            if (a < TY + 1) ey0[a] = ld(A.ey, o0 + (unsigned)(a - 1) * (unsigned)g.pitch, ok);
         }
 #pragma unroll
-        for (int r = 0; r < TY; ++r) {
-            hxp[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-            hyp[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+        for (int r = 0; r < TY; ++r) { hxp[r] = 0.0f; hyp[r] = 0.0f; }
     }
-    for (int k = kstart; k < k1; ++k) {
-        const bool own = k >= k0;
-        const bool slow = xy_slow || (P > 0 && (k <= P || k >= g.nz - P)) ||
-                          (src_xy && k >= A.ss.klo && k <= A.ss.khi);
-        if (slow)
-            plane_step<true>(A, L, k, own, ex0, ey0, hxp, hyp);
-        else
-            plane_step<false>(A, L, k, own, ex0, ey0, hxp, hyp);
+    // two register buffers: while plane k is computed from one, the loads of
+    // plane k+1 are in flight into the other
+    Plane pa, pb;
+    load_plane(A, pa, kstart, cofs, colok, j0);
+    int k = kstart;
+    while (k < k1) {
+        if (k + 1 < k1) load_plane(A, pb, k + 1, cofs, colok, j0);
+        compute_plane(A, pa, k, k >= k0, i, j0, lane_owns, cofs,
+                      src_xy && k >= A.ss.klo && k <= A.ss.khi, ex0, ey0, hxp, hyp);
+        ++k;
+        if (k >= k1) break;
+        if (k + 1 < k1) load_plane(A, pa, k + 1, cofs, colok, j0);
+        compute_plane(A, pb, k, k >= k0, i, j0, lane_owns, cofs,
+                      src_xy && k >= A.ss.klo && k <= A.ss.khi, ex0, ey0, hxp, hyp);
+        ++k;
     }
 }
 
 struct HostState {
+    int ilo, ihi, jlo, jhi, klo, khi;
     int bx, by, chunks, chunk;
+    Shell shell;
 };
 
 }  // namespace
 
-const char *strip_name() { return "fused-strip-v4x120"; }
+const char *strip_name() { return "fused-strip-30x4"; }
 
 int strip_prepare(fdtd_ctx *h) {
     const Grid &g = h->g;
-    // 32-bit offsets inside one component array and inside one psi array
+    // 32-bit offsets inside one component array
     if ((unsigned long long)g.comp >= (1ull << 32)) return FDTD_ERR_ARG;
-    for (int a = 0; a < 3; ++a)
-        if ((unsigned long long)h->psi_axis[a] >= (1ull << 32)) return FDTD_ERR_ARG;
-    if (g.pitch % 4 != 0) return FDTD_ERR_ARG;
     HostState *st = new HostState();
-    st->bx = (g.nx + OWN - 1) / OWN;
-    st->by = (g.ny + WARPS * TY - 1) / (WARPS * TY);
+    const int P = h->P;
+    const int lo = P > 0 ? P + 1 : 0;
+    st->ilo = lo; st->ihi = g.nx - 1 - (P > 0 ? P : 0);
+    st->jlo = lo; st->jhi = g.ny - 1 - (P > 0 ? P : 0);
+    st->klo = lo; st->khi = g.nz - 1 - (P > 0 ? P : 0);
+    const int ex = st->ihi - st->ilo + 1, ey = st->jhi - st->jlo + 1, ez = st->khi - st->klo + 1;
+    st->bx = (ex + OWN - 1) / OWN;
+    st->by = (ey + WARPS * TY - 1) / (WARPS * TY);
     int sms = h->num_sms > 0 ? h->num_sms : 1;
     // about eight waves of resident blocks, chunks of >= 16 planes
     const long long want = 8LL * STRIP_MINB * sms;
     long long chunks = (want + (long long)st->bx * st->by - 1) / ((long long)st->bx * st->by);
-    if (chunks > g.nz / 16) chunks = g.nz / 16;
+    if (chunks > ez / 16) chunks = ez / 16;
     if (chunks < 1) chunks = 1;
-    st->chunk = (int)((g.nz + chunks - 1) / chunks);
-    st->chunks = (g.nz + st->chunk - 1) / st->chunk;
+    st->chunk = (int)((ez + chunks - 1) / chunks);
+    st->chunks = (ez + st->chunk - 1) / st->chunk;
+    // the shell: z slabs, y slabs of the remaining planes, x slabs of the rest
+    Shell &sh = st->shell;
+    sh.n = 0;
+    auto add = [&](int i0, int i1, int j0, int j1, int k0, int k1) {
+        if (i1 < i0 || j1 < j0 || k1 < k0) return;
+        sh.lo[sh.n][0] = i0; sh.hi[sh.n][0] = i1;
+        sh.lo[sh.n][1] = j0; sh.hi[sh.n][1] = j1;
+        sh.lo[sh.n][2] = k0; sh.hi[sh.n][2] = k1;
+        sh.n++;
+    };
+    if (P > 0) {
+        add(0, g.nx - 1, 0, g.ny - 1, 0, st->klo - 1);
+        add(0, g.nx - 1, 0, g.ny - 1, st->khi + 1, g.nz - 1);
+        add(0, g.nx - 1, 0, st->jlo - 1, st->klo, st->khi);
+        add(0, g.nx - 1, st->jhi + 1, g.ny - 1, st->klo, st->khi);
+        add(0, st->ilo - 1, st->jlo, st->jhi, st->klo, st->khi);
+        add(st->ihi + 1, g.nx - 1, st->jlo, st->jhi, st->klo, st->khi);
+    }
+    sh.start[0] = 0;
+    for (int b = 0; b < sh.n; ++b)
+        sh.start[b + 1] = sh.start[b] + (long long)(sh.hi[b][0] - sh.lo[b][0] + 1) *
+                                            (sh.hi[b][1] - sh.lo[b][1] + 1) * (sh.hi[b][2] - sh.lo[b][2] + 1);
     h->strip = st;
     return FDTD_OK;
 }
@@ -343,6 +269,11 @@ int strip_prepare(fdtd_ctx *h) {
 void strip_release(fdtd_ctx *h) {
     delete static_cast<HostState *>(h->strip);
     h->strip = nullptr;
+}
+
+long long strip_interior_cells(const fdtd_ctx *h) {
+    const HostState *st = static_cast<const HostState *>(h->strip);
+    return (long long)(st->ihi - st->ilo + 1) * (st->jhi - st->jlo + 1) * (st->khi - st->klo + 1);
 }
 
 void launch_strip(fdtd_ctx *h, cudaStream_t s) {
@@ -355,7 +286,7 @@ void launch_strip(fdtd_ctx *h, cudaStream_t s) {
     const size_t c = (size_t)g.comp;
     a.ex = in; a.ey = in + c; a.ez = in + 2 * c; a.hx = in + 3 * c; a.hy = in + 4 * c; a.hz = in + 5 * c;
     a.oex = out; a.oey = out + c; a.oez = out + 2 * c; a.ohx = out + 3 * c; a.ohy = out + 4 * c; a.ohz = out + 5 * c;
-    a.pml = cpml_view(h);
+    a.ilo = st->ilo; a.ihi = st->ihi; a.jlo = st->jlo; a.jhi = st->jhi; a.klo = st->klo; a.khi = st->khi;
     a.src = h->src;
     a.ss = source_window(h->src, h->steps);
     a.kE = (float)h->kE;
@@ -363,6 +294,13 @@ void launch_strip(fdtd_ctx *h, cudaStream_t s) {
     a.chunk = st->chunk;
     dim3 grid(st->bx, st->by, st->chunks);
     k_strip<<<grid, NT, 0, s>>>(a);
+}
+
+int launch_strip_shell(fdtd_ctx *h, cudaStream_t s) {
+    HostState *st = static_cast<HostState *>(h->strip);
+    int n = 0;
+    launch_shell(h, st->shell, s, &n);
+    return n;
 }
 
 }  // namespace fdtd
