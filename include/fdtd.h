@@ -172,9 +172,9 @@ int fdtd_timing_begin(fdtd_t h, int max_launches);
 int fdtd_timing_end(fdtd_t h, double *total_ms, int *launches);
 int fdtd_launch_count(fdtd_t h, int64_t *launches);
 
-/* Cells updated by one launch of the timed kernel(s) (the whole grid for the
-   sweeps; the CPML-free interior box for the fused z-march, whose shell of
-   CPML cells is updated by two small untimed launches). */
+/* Cells updated by one launch of the timed kernel(s): the CPML-free interior
+   box for path 1 (whose CPML shell is updated by a second, untimed launch),
+   the whole grid otherwise. */
 int fdtd_timed_cells(fdtd_t h, int64_t *cells);
 
 /* Name of the field-update path in use (static string). */
@@ -182,9 +182,10 @@ const char *fdtd_kernel_name(fdtd_t h);
 
 /*
  * Select the field-update path (all compute the same update, Sec. III.A):
- *   1 = register-strip z-march over the CPML-free interior, one pass per step,
- *       plus an H and an E sweep over the CPML shell (the default);
- *   2 = TMA-staged z-march, one pass per step;
+ *   1 = one pass per step: aligned-tile z-march over the CPML-free interior
+ *       box plus a register-strip z-march over the CPML shell (the default);
+ *   3 = one pass per step: register-strip z-march over interior and shell;
+ *   2 = one pass per step: TMA-staged z-march;
  *   0 = one H sweep then one E sweep.
  * Returns FDTD_ERR_ARG for a path the handle cannot run.
  */

@@ -50,6 +50,7 @@ void release(fdtd_ctx *h) {
     free_dev(h->d_flags);
     fused_release(h);
     strip_release(h);
+    tile_release(h);
     for (cudaEvent_t e : h->timing.ev) cudaEventDestroy(e);
     delete h;
 }
@@ -199,7 +200,8 @@ int fdtd_create(fdtd_t *out, int nx, int ny, int nz, double dx, double dt, doubl
     // (fdtd_set_kernel) as cross-checks
     h->kernel = 0;
     if (fused_prepare(h) == FDTD_OK) h->kernel = 2;
-    if (strip_prepare(h) == FDTD_OK) h->kernel = 1;
+    if (strip_prepare(h) == FDTD_OK) h->kernel = 3;
+    if (h->strip && tile_prepare(h) == FDTD_OK) h->kernel = 1;
     cudaGetLastError();
     *out = h;
     return FDTD_OK;
@@ -314,8 +316,13 @@ int fdtd_step(fdtd_t h, int n) {
     if (h->np > 0 && h->steps + n > h->max_steps) return FDTD_ERR_CAPACITY;
     for (int s = 0; s < n; ++s) {
         if (h->kernel == 1) {
-            timed_launch(h, [](const fdtd_ctx *c, cudaStream_t st) { launch_strip(const_cast<fdtd_ctx *>(c), st); });
-            h->launches += launch_strip_shell(h, h->stream);
+            timed_launch(h, [](const fdtd_ctx *c, cudaStream_t st) { launch_tile(const_cast<fdtd_ctx *>(c), st); });
+            if (strip_has_shell(h)) {
+                launch_strip(h, h->stream, true);
+                h->launches++;
+            }
+        } else if (h->kernel == 3) {
+            timed_launch(h, [](const fdtd_ctx *c, cudaStream_t st) { launch_strip(const_cast<fdtd_ctx *>(c), st, false); });
         } else if (h->kernel == 2) {
             timed_launch(h, [](const fdtd_ctx *c, cudaStream_t st) { launch_fused(const_cast<fdtd_ctx *>(c), st); });
         } else {
@@ -531,7 +538,7 @@ int fdtd_timing_end(fdtd_t h, double *total_ms, int *launches) {
 int fdtd_timed_cells(fdtd_t h, int64_t *cells) {
     if (!h || !cells) return FDTD_ERR_ARG;
     const Grid &g = h->g;
-    *cells = h->kernel == 1 ? strip_interior_cells(h) : (int64_t)g.nx * g.ny * g.nz;
+    *cells = h->kernel == 1 ? tile_cells(h) : (int64_t)g.nx * g.ny * g.nz;
     return FDTD_OK;
 }
 
@@ -542,14 +549,16 @@ int fdtd_launch_count(fdtd_t h, int64_t *launches) {
 }
 
 const char *fdtd_kernel_name(fdtd_t h) {
-    if (h && h->kernel == 1) return strip_name();
+    if (h && h->kernel == 1) return tile_name();
     if (h && h->kernel == 2) return fused_name();
+    if (h && h->kernel == 3) return strip_name();
     return "unfused-h-then-e";
 }
 
 int fdtd_set_kernel(fdtd_t h, int which) {
-    if (!h || which < 0 || which > 2) return FDTD_ERR_ARG;
-    if ((which == 1 && !h->strip) || (which == 2 && !h->fused)) return FDTD_ERR_ARG;
+    if (!h || which < 0 || which > 3) return FDTD_ERR_ARG;
+    if ((which == 1 && (!h->tile || !h->strip)) || (which == 2 && !h->fused) || (which == 3 && !h->strip))
+        return FDTD_ERR_ARG;
     h->kernel = which;
     return FDTD_OK;
 }

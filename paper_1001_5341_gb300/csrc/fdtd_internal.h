@@ -123,10 +123,11 @@ struct fdtd_ctx {
     size_t psi_axis[3];       // floats of one psi array of each axis
     float *coef_block;        // aE,bE,aH,bH per axis
     const float *aE[3], *bE[3], *aH[3], *bH[3];
-    int kernel;               // field-update path: 0 unfused sweeps, 1 register-strip
-                              // z-march, 2 TMA-staged z-march
+    int kernel;               // field-update path: 0 unfused sweeps, 1 tile interior +
+                              // strip CPML shell, 2 TMA-staged z-march, 3 strip only
     void *fused;              // host state of the TMA path (tensor maps, launch shape)
     void *strip;              // host state of the register-strip path
+    void *tile;               // host state of the aligned-tile path
     int *d_flags;             // device error flags (bit 0: a bounded wait gave up)
     int num_sms;
 
@@ -176,9 +177,16 @@ void fused_release(fdtd_ctx *h);
 
 // register-strip z-march (kernels_strip.cu)
 int strip_prepare(fdtd_ctx *h);
-void launch_strip(fdtd_ctx *h, cudaStream_t s);
-int launch_strip_shell(fdtd_ctx *h, cudaStream_t s);   // returns kernels launched
+void launch_strip(fdtd_ctx *h, cudaStream_t s, bool shell_only);
 long long strip_interior_cells(const fdtd_ctx *h);
+bool strip_has_shell(const fdtd_ctx *h);
+
+// aligned-tile z-march of the interior box (kernels_tile.cu)
+int tile_prepare(fdtd_ctx *h);
+void launch_tile(fdtd_ctx *h, cudaStream_t s);
+const char *tile_name();
+void tile_release(fdtd_ctx *h);
+long long tile_cells(const fdtd_ctx *h);
 const char *strip_name();
 void strip_release(fdtd_ctx *h);
 

@@ -77,6 +77,7 @@ struct Args {
     SourceStep ss;      // this step's window of planes that may carry current
     float kE, kH;
     int nbox;
+    int block0;         // block index offset (launches of a tail of the box list)
     Box box[MAXBOX];
 };
 
@@ -368,10 +369,11 @@ __device__ __forceinline__ void march(const Args &A, const Box &B, int tile, int
 __global__ void __launch_bounds__(NT, STRIP_MINB) k_strip(const Args A) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
+    const int blk = (int)blockIdx.x + A.block0;
     int b = 0;
-    while (b + 1 < A.nbox && (int)blockIdx.x >= A.box[b + 1].first) ++b;
+    while (b + 1 < A.nbox && blk >= A.box[b + 1].first) ++b;
     const Box &B = A.box[b];
-    const int tile = (int)blockIdx.x - B.first;
+    const int tile = blk - B.first;
     if (B.pml)
         march<TYP, true>(A, B, tile, lane, warp);
     else
@@ -388,6 +390,7 @@ struct HostState {
 }  // namespace
 
 const char *strip_name() { return "fused-strip-30"; }
+bool strip_has_shell(const fdtd_ctx *h) { return static_cast<const HostState *>(h->strip)->nbox > 1; }
 
 int strip_prepare(fdtd_ctx *h) {
     const Grid &g = h->g;
@@ -453,7 +456,7 @@ long long strip_interior_cells(const fdtd_ctx *h) {
     return (long long)g.nx * g.ny * g.nz;
 }
 
-void launch_strip(fdtd_ctx *h, cudaStream_t s) {
+void launch_strip(fdtd_ctx *h, cudaStream_t s, bool shell_only) {
     HostState *st = static_cast<HostState *>(h->strip);
     const Grid &g = h->g;
     Args a;
@@ -470,13 +473,10 @@ void launch_strip(fdtd_ctx *h, cudaStream_t s) {
     a.kH = (float)h->kH;
     a.nbox = st->nbox;
     for (int b = 0; b < st->nbox; ++b) a.box[b] = st->box[b];
-    k_strip<<<st->blocks, NT, 0, s>>>(a);
-}
-
-int launch_strip_shell(fdtd_ctx *h, cudaStream_t s) {
-    (void)h;
-    (void)s;
-    return 0;  // the shell boxes are part of the same launch
+    // box 0 is the interior box; the shell boxes follow it
+    a.block0 = shell_only ? (st->nbox > 1 ? st->box[1].first : st->blocks) : 0;
+    const int blocks = st->blocks - a.block0;
+    if (blocks > 0) k_strip<<<blocks, NT, 0, s>>>(a);
 }
 
 }  // namespace fdtd
