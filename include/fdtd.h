@@ -182,8 +182,9 @@ const char *fdtd_kernel_name(fdtd_t h);
 
 /*
  * Select the field-update path (all compute the same update, Sec. III.A):
- *   1 = one pass per step: aligned-tile z-march over the CPML-free interior
- *       box plus a register-strip z-march over the CPML shell (the default);
+ *   1 = one pass per step: TMA-staged vector-tile z-march over the CPML-free
+ *       interior box plus a register-strip z-march over the CPML shell (the
+ *       default);
  *   3 = one pass per step: register-strip z-march over interior and shell;
  *   2 = one pass per step: TMA-staged z-march;
  *   0 = one H sweep then one E sweep.

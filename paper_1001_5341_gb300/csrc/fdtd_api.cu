@@ -50,7 +50,7 @@ void release(fdtd_ctx *h) {
     free_dev(h->d_flags);
     fused_release(h);
     strip_release(h);
-    tile_release(h);
+    vtile_release(h);
     for (cudaEvent_t e : h->timing.ev) cudaEventDestroy(e);
     delete h;
 }
@@ -62,6 +62,18 @@ size_t field_bytes(const fdtd_ctx *h) { return sizeof(float) * 6 * (size_t)h->g.
 }  // namespace
 
 namespace fdtd {
+void interior_box(const fdtd_ctx *h, int lo[3], int hi[3]) {
+    const Grid &g = h->g;
+    const int P = h->P;
+    const int l = P > 0 ? P + 1 : 0;
+    lo[0] = (l + 3) / 4 * 4;
+    hi[0] = (g.nx - P) / 4 * 4 - 1;
+    lo[1] = l;
+    hi[1] = g.ny - 1 - P;
+    lo[2] = l;
+    hi[2] = g.nz - 1 - P;
+}
+
 Cpml cpml_view(const fdtd_ctx *h) {
     Cpml v{};
     v.P = h->P;
@@ -201,7 +213,7 @@ int fdtd_create(fdtd_t *out, int nx, int ny, int nz, double dx, double dt, doubl
     h->kernel = 0;
     if (fused_prepare(h) == FDTD_OK) h->kernel = 2;
     if (strip_prepare(h) == FDTD_OK) h->kernel = 3;
-    if (h->strip && tile_prepare(h) == FDTD_OK) h->kernel = 1;
+    if (h->strip && vtile_prepare(h) == FDTD_OK) h->kernel = 1;
     cudaGetLastError();
     *out = h;
     return FDTD_OK;
@@ -316,7 +328,7 @@ int fdtd_step(fdtd_t h, int n) {
     if (h->np > 0 && h->steps + n > h->max_steps) return FDTD_ERR_CAPACITY;
     for (int s = 0; s < n; ++s) {
         if (h->kernel == 1) {
-            timed_launch(h, [](const fdtd_ctx *c, cudaStream_t st) { launch_tile(const_cast<fdtd_ctx *>(c), st); });
+            timed_launch(h, [](const fdtd_ctx *c, cudaStream_t st) { launch_vtile(const_cast<fdtd_ctx *>(c), st); });
             if (strip_has_shell(h)) {
                 launch_strip(h, h->stream, true);
                 h->launches++;
@@ -538,7 +550,7 @@ int fdtd_timing_end(fdtd_t h, double *total_ms, int *launches) {
 int fdtd_timed_cells(fdtd_t h, int64_t *cells) {
     if (!h || !cells) return FDTD_ERR_ARG;
     const Grid &g = h->g;
-    *cells = h->kernel == 1 ? tile_cells(h) : (int64_t)g.nx * g.ny * g.nz;
+    *cells = h->kernel == 1 ? vtile_cells(h) : (int64_t)g.nx * g.ny * g.nz;
     return FDTD_OK;
 }
 
@@ -549,7 +561,7 @@ int fdtd_launch_count(fdtd_t h, int64_t *launches) {
 }
 
 const char *fdtd_kernel_name(fdtd_t h) {
-    if (h && h->kernel == 1) return tile_name();
+    if (h && h->kernel == 1) return vtile_name();
     if (h && h->kernel == 2) return fused_name();
     if (h && h->kernel == 3) return strip_name();
     return "unfused-h-then-e";
@@ -557,7 +569,7 @@ const char *fdtd_kernel_name(fdtd_t h) {
 
 int fdtd_set_kernel(fdtd_t h, int which) {
     if (!h || which < 0 || which > 3) return FDTD_ERR_ARG;
-    if ((which == 1 && (!h->tile || !h->strip)) || (which == 2 && !h->fused) || (which == 3 && !h->strip))
+    if ((which == 1 && (!h->vtile || !h->strip)) || (which == 2 && !h->fused) || (which == 3 && !h->strip))
         return FDTD_ERR_ARG;
     h->kernel = which;
     return FDTD_OK;

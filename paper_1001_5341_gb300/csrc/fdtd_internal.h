@@ -123,11 +123,11 @@ struct fdtd_ctx {
     size_t psi_axis[3];       // floats of one psi array of each axis
     float *coef_block;        // aE,bE,aH,bH per axis
     const float *aE[3], *bE[3], *aH[3], *bH[3];
-    int kernel;               // field-update path: 0 unfused sweeps, 1 tile interior +
+    int kernel;               // field-update path: 0 unfused sweeps, 1 vector-tile interior +
                               // strip CPML shell, 2 TMA-staged z-march, 3 strip only
     void *fused;              // host state of the TMA path (tensor maps, launch shape)
     void *strip;              // host state of the register-strip path
-    void *tile;               // host state of the aligned-tile path
+    void *vtile;              // host state of the vector-tile path
     int *d_flags;             // device error flags (bit 0: a bounded wait gave up)
     int num_sms;
 
@@ -181,12 +181,18 @@ void launch_strip(fdtd_ctx *h, cudaStream_t s, bool shell_only);
 long long strip_interior_cells(const fdtd_ctx *h);
 bool strip_has_shell(const fdtd_ctx *h);
 
-// aligned-tile z-march of the interior box (kernels_tile.cu)
-int tile_prepare(fdtd_ctx *h);
-void launch_tile(fdtd_ctx *h, cudaStream_t s);
-const char *tile_name();
-void tile_release(fdtd_ctx *h);
-long long tile_cells(const fdtd_ctx *h);
+// The CPML-free interior box, cells [lo, hi] inclusive per axis: [P+1, N-P-1]
+// (all of [0, N-1] without CPML), its x range shrunk to whole groups of four
+// columns (lo[0] and hi[0]+1 multiples of 4).  The cells around it form the
+// shell updated by the register-strip kernel's shell boxes.
+void interior_box(const fdtd_ctx *h, int lo[3], int hi[3]);
+
+// TMA-staged vector-tile z-march of the interior box (kernels_vtile.cu)
+int vtile_prepare(fdtd_ctx *h);
+void launch_vtile(fdtd_ctx *h, cudaStream_t s);
+const char *vtile_name();
+void vtile_release(fdtd_ctx *h);
+long long vtile_cells(const fdtd_ctx *h);
 const char *strip_name();
 void strip_release(fdtd_ctx *h);
 

@@ -6,9 +6,10 @@
 // written per cell, plus the CPML memory of the cells in the layers.
 //
 // The grid is covered by up to seven boxes of cells, all updated by one
-// launch: the interior box [P+1, N-P-1]^3, where no CPML term exists, and six
-// shell boxes (two z slabs over the whole x-y plane, two y slabs over the
-// interior z range, two x slabs over the interior y and z ranges).  Every box
+// launch: the interior box [P+1, N-P-1]^3 (x range shrunk to whole groups of
+// four columns), where no CPML term exists, and up to six shell boxes (two z
+// slabs over the whole x-y plane, two y slabs over the interior z range, two x
+// slabs over the interior y and z ranges).  Every box
 // reads only the input set and writes only its own cells of the output set, so
 // the boxes are independent.  Interior blocks run the plain update with a
 // register double buffer; shell blocks run the update with the CPML memory
@@ -399,9 +400,9 @@ int strip_prepare(fdtd_ctx *h) {
     for (int a = 0; a < 3; ++a)
         if ((unsigned long long)h->psi_axis[a] >= (1ull << 32)) return FDTD_ERR_ARG;
     HostState *st = new HostState();
-    const int P = h->P;
-    const int lo = P > 0 ? P + 1 : 0;
-    const int ihi = g.nx - 1 - P, jhi = g.ny - 1 - P, khi = g.nz - 1 - P;
+    int blo[3], bhi[3];
+    interior_box(h, blo, bhi);
+    const int ilo = blo[0], ihi = bhi[0], lo = blo[1], jhi = bhi[1], khi = bhi[2];
     st->nbox = 0;
     const int sms = h->num_sms > 0 ? h->num_sms : 1;
     int first = 0;
@@ -430,16 +431,16 @@ int strip_prepare(fdtd_ctx *h) {
         B.first = first;
         first += B.tx * B.ty * (int)chunks;
     };
-    add(lo, ihi, lo, jhi, lo, khi, 0);
-    st->interior_cells = (long long)(ihi - lo + 1) * (jhi - lo + 1) * (khi - lo + 1);
-    if (P > 0) {
-        add(0, g.nx - 1, 0, g.ny - 1, 0, lo - 1, 1);           // z- slab
-        add(0, g.nx - 1, 0, g.ny - 1, khi + 1, g.nz - 1, 1);   // z+ slab
-        add(0, g.nx - 1, 0, lo - 1, lo, khi, 1);               // y- slab
-        add(0, g.nx - 1, jhi + 1, g.ny - 1, lo, khi, 1);       // y+ slab
-        add(0, lo - 1, lo, jhi, lo, khi, 1);                   // x- slab
-        add(ihi + 1, g.nx - 1, lo, jhi, lo, khi, 1);           // x+ slab
-    }
+    add(ilo, ihi, lo, jhi, lo, khi, 0);
+    st->interior_cells = (long long)(ihi - ilo + 1) * (jhi - lo + 1) * (khi - lo + 1);
+    // the shell: empty boxes are skipped (no CPML: at most the x+ columns
+    // beyond the last whole group of four)
+    add(0, g.nx - 1, 0, g.ny - 1, 0, lo - 1, 1);           // z- slab
+    add(0, g.nx - 1, 0, g.ny - 1, khi + 1, g.nz - 1, 1);   // z+ slab
+    add(0, g.nx - 1, 0, lo - 1, lo, khi, 1);               // y- slab
+    add(0, g.nx - 1, jhi + 1, g.ny - 1, lo, khi, 1);       // y+ slab
+    add(0, ilo - 1, lo, jhi, lo, khi, 1);                  // x- slab
+    add(ihi + 1, g.nx - 1, lo, jhi, lo, khi, 1);           // x+ slab
     st->blocks = first;
     h->strip = st;
     return FDTD_OK;

@@ -23,9 +23,9 @@ def fd():
     return m
 
 
-# the field-update paths: 1 = aligned-tile interior + register-strip CPML shell
+# the field-update paths: 1 = vector-tile interior + register-strip CPML shell
 # (default), 3 = register strip everywhere, 2 = TMA-staged z-march, 0 = unfused
-@pytest.fixture(params=[1, 3, 2, 0], ids=["tile", "strip", "tma", "unfused"])
+@pytest.fixture(params=[1, 3, 2, 0], ids=["vtile", "strip", "tma", "unfused"])
 def kernel(request):
     return request.param
 
