@@ -172,9 +172,8 @@ int fdtd_timing_begin(fdtd_t h, int max_launches);
 int fdtd_timing_end(fdtd_t h, double *total_ms, int *launches);
 int fdtd_launch_count(fdtd_t h, int64_t *launches);
 
-/* Cells updated by one launch of the timed kernel(s): the CPML-free interior
-   box for path 1 (whose CPML shell is updated by a second, untimed launch),
-   the whole grid otherwise. */
+/* Cells updated by one launch of the timed kernel(s): the whole grid (the
+   unfused path 0 times its H sweep and its E sweep as separate launches). */
 int fdtd_timed_cells(fdtd_t h, int64_t *cells);
 
 /* Name of the field-update path in use (static string). */
@@ -182,9 +181,8 @@ const char *fdtd_kernel_name(fdtd_t h);
 
 /*
  * Select the field-update path (all compute the same update, Sec. III.A):
- *   1 = one pass per step: TMA-staged vector-tile z-march over the CPML-free
- *       interior box plus a register-strip z-march over the CPML shell (the
- *       default);
+ *   1 = one pass per step: TMA-staged vector-tile z-march over the whole
+ *       grid, CPML included (the default);
  *   3 = one pass per step: register-strip z-march over interior and shell;
  *   2 = one pass per step: TMA-staged z-march;
  *   0 = one H sweep then one E sweep.

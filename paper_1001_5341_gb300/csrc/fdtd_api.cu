@@ -185,9 +185,11 @@ int fdtd_create(fdtd_t *out, int nx, int ny, int nz, double dx, double dt, doubl
         std::free(hc);
         if (rc != FDTD_OK) return fail(rc);
         const int W = 2 * P + 1;
-        h->psi_axis[0] = (size_t)nz * ny * W;
-        h->psi_axis[1] = (size_t)nz * W * nx;
-        h->psi_axis[2] = (size_t)W * ny * nx;
+        const size_t pitch = (size_t)h->g.pitch;
+        auto r32 = [](size_t n) { return (n + 31) / 32 * 32; };
+        h->psi_axis[0] = r32((size_t)nz * ny * psi_x_row(nx, P));
+        h->psi_axis[1] = r32((size_t)nz * W * pitch);
+        h->psi_axis[2] = r32((size_t)W * ny * pitch);
         // E psi (2 per axis), then H psi set 0 and set 1 (2 per axis each)
         h->psi_floats = 3 * 2 * (h->psi_axis[0] + h->psi_axis[1] + h->psi_axis[2]);
         if (cudaMalloc(&h->psi_block, h->psi_floats * sizeof(float)) != cudaSuccess) { cudaGetLastError(); return fail(FDTD_ERR_OOM); }
@@ -213,7 +215,7 @@ int fdtd_create(fdtd_t *out, int nx, int ny, int nz, double dx, double dt, doubl
     h->kernel = 0;
     if (fused_prepare(h) == FDTD_OK) h->kernel = 2;
     if (strip_prepare(h) == FDTD_OK) h->kernel = 3;
-    if (h->strip && vtile_prepare(h) == FDTD_OK) h->kernel = 1;
+    if (vtile_prepare(h) == FDTD_OK) h->kernel = 1;
     cudaGetLastError();
     *out = h;
     return FDTD_OK;
@@ -329,12 +331,8 @@ int fdtd_step(fdtd_t h, int n) {
     for (int s = 0; s < n; ++s) {
         if (h->kernel == 1) {
             timed_launch(h, [](const fdtd_ctx *c, cudaStream_t st) { launch_vtile(const_cast<fdtd_ctx *>(c), st); });
-            if (strip_has_shell(h)) {
-                launch_strip(h, h->stream, true);
-                h->launches++;
-            }
         } else if (h->kernel == 3) {
-            timed_launch(h, [](const fdtd_ctx *c, cudaStream_t st) { launch_strip(const_cast<fdtd_ctx *>(c), st, false); });
+            timed_launch(h, [](const fdtd_ctx *c, cudaStream_t st) { launch_strip(const_cast<fdtd_ctx *>(c), st); });
         } else if (h->kernel == 2) {
             timed_launch(h, [](const fdtd_ctx *c, cudaStream_t st) { launch_fused(const_cast<fdtd_ctx *>(c), st); });
         } else {
@@ -550,7 +548,7 @@ int fdtd_timing_end(fdtd_t h, double *total_ms, int *launches) {
 int fdtd_timed_cells(fdtd_t h, int64_t *cells) {
     if (!h || !cells) return FDTD_ERR_ARG;
     const Grid &g = h->g;
-    *cells = h->kernel == 1 ? vtile_cells(h) : (int64_t)g.nx * g.ny * g.nz;
+    *cells = (int64_t)g.nx * g.ny * g.nz;
     return FDTD_OK;
 }
 
@@ -569,7 +567,7 @@ const char *fdtd_kernel_name(fdtd_t h) {
 
 int fdtd_set_kernel(fdtd_t h, int which) {
     if (!h || which < 0 || which > 3) return FDTD_ERR_ARG;
-    if ((which == 1 && (!h->vtile || !h->strip)) || (which == 2 && !h->fused) || (which == 3 && !h->strip))
+    if ((which == 1 && !h->vtile) || (which == 2 && !h->fused) || (which == 3 && !h->strip))
         return FDTD_ERR_ARG;
     h->kernel = which;
     return FDTD_OK;

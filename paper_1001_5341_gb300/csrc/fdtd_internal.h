@@ -10,8 +10,12 @@
 // CPML memory is kept only in the slabs.  Per axis there are four psi arrays
 // (two for the E update, two for the H update) over the slab cells of that
 // axis: cells 0..P and N-P..N-1 (W = 2P+1 cells), stored
-//   x: [nz][ny][W]   y: [nz][W][nx]   z: [W][ny][nx]
-// so that consecutive threads along x touch consecutive floats.  The E-update
+//   x: [nz][ny][WX]   y: [nz][W][pitch]   z: [W][ny][pitch]   (WX: psi_x_row)
+// so that consecutive threads along x touch consecutive floats; the y and z
+// rows use the field pitch, so four consecutive columns from a multiple of
+// four form one aligned 16-byte vector, and every row of every psi array is a
+// multiple of 16 bytes (TMA-addressable).  Every psi array starts on a
+// 128-byte boundary.  The E-update
 // psi are updated in place by the one thread that owns the cell; the H-update
 // psi are ping-ponged like the fields, because a tile of the fused kernel
 // recomputes its neighbours' halo H and must read their psi before the update.
@@ -56,14 +60,31 @@ struct Cpml {
     const float *aE[3], *bE[3], *aH[3], *bH[3]; // per position index, length n_axis (+1)
 };
 
-__host__ __device__ inline long long psi_x(const Grid &g, int W, int l, int j, int k) {
-    return ((long long)k * g.ny + j) * W + l;
+// An x row holds the low layer's columns 0..P at positions 0..P and the high
+// layer's columns N-P..N-1 at positions lo4 + (i - hb), lo4 = P+1 rounded up
+// to 4 and hb = N-P rounded down to 4: four consecutive columns from a
+// multiple of four sit at four consecutive positions from a multiple of four
+// (one aligned 16-byte vector).  Rows are padded to a multiple of four.
+__host__ __device__ inline int psi_x_lo4(int P) { return (P + 4) / 4 * 4; }
+__host__ __device__ inline int psi_x_hb(int nx, int P) { return (nx - P) / 4 * 4; }
+__host__ __device__ inline int psi_x_row(int nx, int P) {
+    return (psi_x_lo4(P) + nx - psi_x_hb(nx, P) + 3) / 4 * 4;
+}
+// position of column i in an x row, or -1 outside the layers
+__host__ __device__ inline int psi_x_pos(int i, int nx, int P) {
+    if (P <= 0) return -1;
+    if (i <= P) return i;
+    if (i >= nx - P) return psi_x_lo4(P) + i - psi_x_hb(nx, P);
+    return -1;
+}
+__host__ __device__ inline long long psi_x(const Grid &g, int P, int l, int j, int k) {
+    return ((long long)k * g.ny + j) * psi_x_row(g.nx, P) + l;
 }
 __host__ __device__ inline long long psi_y(const Grid &g, int W, int i, int l, int k) {
-    return ((long long)k * W + l) * g.nx + i;
+    return ((long long)k * W + l) * g.pitch + i;
 }
 __host__ __device__ inline long long psi_z(const Grid &g, int W, int i, int j, int l) {
-    return ((long long)l * g.ny + j) * g.nx + i;
+    return ((long long)l * g.ny + j) * g.pitch + i;
 }
 
 struct Source {
@@ -123,8 +144,8 @@ struct fdtd_ctx {
     size_t psi_axis[3];       // floats of one psi array of each axis
     float *coef_block;        // aE,bE,aH,bH per axis
     const float *aE[3], *bE[3], *aH[3], *bH[3];
-    int kernel;               // field-update path: 0 unfused sweeps, 1 vector-tile interior +
-                              // strip CPML shell, 2 TMA-staged z-march, 3 strip only
+    int kernel;               // field-update path: 0 unfused sweeps, 1 vector tile,
+                              // 2 TMA-staged z-march, 3 register strip
     void *fused;              // host state of the TMA path (tensor maps, launch shape)
     void *strip;              // host state of the register-strip path
     void *vtile;              // host state of the vector-tile path
@@ -177,9 +198,7 @@ void fused_release(fdtd_ctx *h);
 
 // register-strip z-march (kernels_strip.cu)
 int strip_prepare(fdtd_ctx *h);
-void launch_strip(fdtd_ctx *h, cudaStream_t s, bool shell_only);
-long long strip_interior_cells(const fdtd_ctx *h);
-bool strip_has_shell(const fdtd_ctx *h);
+void launch_strip(fdtd_ctx *h, cudaStream_t s);
 
 // The CPML-free interior box, cells [lo, hi] inclusive per axis: [P+1, N-P-1]
 // (all of [0, N-1] without CPML), its x range shrunk to whole groups of four
@@ -187,12 +206,11 @@ bool strip_has_shell(const fdtd_ctx *h);
 // shell updated by the register-strip kernel's shell boxes.
 void interior_box(const fdtd_ctx *h, int lo[3], int hi[3]);
 
-// TMA-staged vector-tile z-march of the interior box (kernels_vtile.cu)
+// TMA-staged vector-tile z-march over the whole grid, CPML included (kernels_vtile.cu)
 int vtile_prepare(fdtd_ctx *h);
 void launch_vtile(fdtd_ctx *h, cudaStream_t s);
 const char *vtile_name();
 void vtile_release(fdtd_ctx *h);
-long long vtile_cells(const fdtd_ctx *h);
 const char *strip_name();
 void strip_release(fdtd_ctx *h);
 

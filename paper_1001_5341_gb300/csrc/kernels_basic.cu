@@ -42,7 +42,7 @@ __device__ __forceinline__ void cell_h(const Grid &g, const float *__restrict__ 
     const float *Ex = Ein, *Ey = Ein + g.comp, *Ez = Ein + 2 * g.comp;
     long long c = gidx(g, i, j, k);
     const int P = pml.P, W = pml.W;
-    int lx = slab_cell(i, g.nx, P), ly = slab_cell(j, g.ny, P), lz = slab_cell(k, g.nz, P);
+    int lx = psi_x_pos(i, g.nx, P), ly = slab_cell(j, g.ny, P), lz = slab_cell(k, g.nz, P);
     if (i >= 1) {  // Hx
         float dy = Ez[c + g.pitch] - Ez[c];
         float dz = Ey[c + g.plane] - Ey[c];
@@ -54,13 +54,13 @@ __device__ __forceinline__ void cell_h(const Grid &g, const float *__restrict__ 
         float dz = Ex[c + g.plane] - Ex[c];
         float dx = Ez[c + 1] - Ez[c];
         if (lz >= 0) { long long q = psi_z(g, W, i, j, lz); cpml_pingpong(pml.hin[2][1] + q, pml.hout[2][1] + q, pml.aH[2], pml.bH[2], k, dz); }
-        if (lx >= 0) { long long q = psi_x(g, W, lx, j, k); cpml_pingpong(pml.hin[0][0] + q, pml.hout[0][0] + q, pml.aH[0], pml.bH[0], i, dx); }
+        if (lx >= 0) { long long q = psi_x(g, P, lx, j, k); cpml_pingpong(pml.hin[0][0] + q, pml.hout[0][0] + q, pml.aH[0], pml.bH[0], i, dx); }
         Hout[g.comp + c] = Hin[g.comp + c] - kH * (dz - dx);
     }
     if (k >= 1) {  // Hz
         float dx = Ey[c + 1] - Ey[c];
         float dy = Ex[c + g.pitch] - Ex[c];
-        if (lx >= 0) { long long q = psi_x(g, W, lx, j, k); cpml_pingpong(pml.hin[0][1] + q, pml.hout[0][1] + q, pml.aH[0], pml.bH[0], i, dx); }
+        if (lx >= 0) { long long q = psi_x(g, P, lx, j, k); cpml_pingpong(pml.hin[0][1] + q, pml.hout[0][1] + q, pml.aH[0], pml.bH[0], i, dx); }
         if (ly >= 0) { long long q = psi_y(g, W, i, ly, k); cpml_pingpong(pml.hin[1][1] + q, pml.hout[1][1] + q, pml.aH[1], pml.bH[1], j, dy); }
         Hout[2 * g.comp + c] = Hin[2 * g.comp + c] - kH * (dx - dy);
     }
@@ -75,7 +75,7 @@ __device__ __forceinline__ void cell_e(const Grid &g, const float *__restrict__ 
     const float *Hx = Hnew, *Hy = Hnew + g.comp, *Hz = Hnew + 2 * g.comp;
     long long c = gidx(g, i, j, k);
     const int P = pml.P, W = pml.W;
-    int lx = slab_cell(i, g.nx, P), ly = slab_cell(j, g.ny, P), lz = slab_cell(k, g.nz, P);
+    int lx = psi_x_pos(i, g.nx, P), ly = slab_cell(j, g.ny, P), lz = slab_cell(k, g.nz, P);
     if (j >= 1 && k >= 1) {  // Ex
         float dy = Hz[c] - Hz[c - g.pitch];
         float dz = Hy[c] - Hy[c - g.plane];
@@ -87,13 +87,13 @@ __device__ __forceinline__ void cell_e(const Grid &g, const float *__restrict__ 
         float dz = Hx[c] - Hx[c - g.plane];
         float dx = Hz[c] - Hz[c - 1];
         if (lz >= 0) cpml_inplace(pml.e[2][1] + psi_z(g, W, i, j, lz), pml.aE[2], pml.bE[2], k, dz);
-        if (lx >= 0) cpml_inplace(pml.e[0][0] + psi_x(g, W, lx, j, k), pml.aE[0], pml.bE[0], i, dx);
+        if (lx >= 0) cpml_inplace(pml.e[0][0] + psi_x(g, P, lx, j, k), pml.aE[0], pml.bE[0], i, dx);
         Eout[g.comp + c] = Ein[g.comp + c] + kE * (dz - dx);
     }
     if (i >= 1 && j >= 1) {  // Ez
         float dx = Hy[c] - Hy[c - 1];
         float dy = Hx[c] - Hx[c - g.pitch];
-        if (lx >= 0) cpml_inplace(pml.e[0][1] + psi_x(g, W, lx, j, k), pml.aE[0], pml.bE[0], i, dx);
+        if (lx >= 0) cpml_inplace(pml.e[0][1] + psi_x(g, P, lx, j, k), pml.aE[0], pml.bE[0], i, dx);
         if (ly >= 0) cpml_inplace(pml.e[1][1] + psi_y(g, W, i, ly, k), pml.aE[1], pml.bE[1], j, dy);
         float e = Ein[2 * g.comp + c] + kE * (dx - dy);
         if (src.active) e += source_term(src, i, j, k, n);

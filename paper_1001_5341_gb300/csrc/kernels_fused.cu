@@ -161,9 +161,9 @@ __device__ __forceinline__ float calc_hy(const Args &A, const float *s0, const f
     float dx = s0[2 * BOXP + bx(ii + 1, jj)] - s0[2 * BOXP + bx(ii, jj)];
     const Cpml &p = A.pml;
     if (p.P > 0) {
-        int lz = slab_cell(k, A.g.nz, p.P), lx = slab_cell(i, A.g.nx, p.P);
+        int lz = slab_cell(k, A.g.nz, p.P), lx = psi_x_pos(i, A.g.nx, p.P);
         if (lz >= 0) psi_h(p.hin[2][1], p.hout[2][1], psi_z(A.g, p.W, i, j, lz), p.aH[2], p.bH[2], k, dz, w);
-        if (lx >= 0) psi_h(p.hin[0][0], p.hout[0][0], psi_x(A.g, p.W, lx, j, k), p.aH[0], p.bH[0], i, dx, w);
+        if (lx >= 0) psi_h(p.hin[0][0], p.hout[0][0], psi_x(A.g, p.P, lx, j, k), p.aH[0], p.bH[0], i, dx, w);
     }
     return s0[4 * BOXP + bx(ii, jj)] - A.kH * (dz - dx);
 }
@@ -174,8 +174,8 @@ __device__ __forceinline__ float calc_hz(const Args &A, const float *s0, int ii,
     float dy = s0[0 * BOXP + bx(ii, jj + 1)] - s0[0 * BOXP + bx(ii, jj)];
     const Cpml &p = A.pml;
     if (p.P > 0) {
-        int lx = slab_cell(i, A.g.nx, p.P), ly = slab_cell(j, A.g.ny, p.P);
-        if (lx >= 0) psi_h(p.hin[0][1], p.hout[0][1], psi_x(A.g, p.W, lx, j, k), p.aH[0], p.bH[0], i, dx, w);
+        int lx = psi_x_pos(i, A.g.nx, p.P), ly = slab_cell(j, A.g.ny, p.P);
+        if (lx >= 0) psi_h(p.hin[0][1], p.hout[0][1], psi_x(A.g, p.P, lx, j, k), p.aH[0], p.bH[0], i, dx, w);
         if (ly >= 0) psi_h(p.hin[1][1], p.hout[1][1], psi_y(A.g, p.W, i, ly, k), p.aH[1], p.bH[1], j, dy, w);
     }
     return s0[5 * BOXP + bx(ii, jj)] - A.kH * (dx - dy);
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused(const Args A, const __grid_cons
                 const int j = j0 + jj;
                 if (i < g.nx && j < g.ny) {
                     const long long c = gidx(g, i, j, k);
-                    const int lx = slab_cell(i, g.nx, p.P), ly = slab_cell(j, g.ny, p.P),
+                    const int lx = psi_x_pos(i, g.nx, p.P), ly = slab_cell(j, g.ny, p.P),
                               lz = slab_cell(k, g.nz, p.P);
                     if (j >= 1 && k >= 1) {  // Ex
                         float dy = Hs[2 * HSZ + hx(tx, jj)] - Hs[2 * HSZ + hx(tx, jj - 1)];
@@ -311,13 +311,13 @@ __global__ void __launch_bounds__(NT, 2) k_fused(const Args A, const __grid_cons
                         float dz = hxv[r] - hxp[r];
                         float dx = Hs[2 * HSZ + hx(tx, jj)] - Hs[2 * HSZ + hx(tx - 1, jj)];
                         if (lz >= 0) psi_e(p.e[2][1], psi_z(g, p.W, i, j, lz), p.aE[2], p.bE[2], k, dz);
-                        if (lx >= 0) psi_e(p.e[0][0], psi_x(g, p.W, lx, j, k), p.aE[0], p.bE[0], i, dx);
+                        if (lx >= 0) psi_e(p.e[0][0], psi_x(g, p.P, lx, j, k), p.aE[0], p.bE[0], i, dx);
                         A.eout[g.comp + c] = s0[1 * BOXP + bx(tx, jj)] + A.kE * (dz - dx);
                     }
                     if (i >= 1 && j >= 1) {  // Ez
                         float dx = Hs[1 * HSZ + hx(tx, jj)] - Hs[1 * HSZ + hx(tx - 1, jj)];
                         float dy = Hs[0 * HSZ + hx(tx, jj)] - Hs[0 * HSZ + hx(tx, jj - 1)];
-                        if (lx >= 0) psi_e(p.e[0][1], psi_x(g, p.W, lx, j, k), p.aE[0], p.bE[0], i, dx);
+                        if (lx >= 0) psi_e(p.e[0][1], psi_x(g, p.P, lx, j, k), p.aE[0], p.bE[0], i, dx);
                         if (ly >= 0) psi_e(p.e[1][1], psi_y(g, p.W, i, ly, k), p.aE[1], p.bE[1], j, dy);
                         float e = s0[2 * BOXP + bx(tx, jj)] + A.kE * (dx - dy);
                         if (A.src.active) e += source_term(A.src, i, j, k, A.n);

@@ -78,7 +78,6 @@ struct Args {
     SourceStep ss;      // this step's window of planes that may carry current
     float kE, kH;
     int nbox;
-    int block0;         // block index offset (launches of a tail of the box list)
     Box box[MAXBOX];
 };
 
@@ -141,7 +140,7 @@ __device__ __forceinline__ void load_psi(const Args &A, PlanePsi<TY> &q, int k, 
     const Grid &g = A.g;
     const Cpml &p = A.pml;
     const bool xin = c.colok && c.i < g.nx;
-    const int lx = xin ? slab_cell(c.i, g.nx, p.P) : -1;
+    const int lx = xin ? psi_x_pos(c.i, g.nx, p.P) : -1;
     const int lz = slab_cell(k, g.nz, p.P);
 #pragma unroll
     for (int a = 0; a < TY + 1; ++a) {
@@ -149,7 +148,7 @@ __device__ __forceinline__ void load_psi(const Args &A, PlanePsi<TY> &q, int k, 
         const bool in = xin && j >= 0 && j < g.ny;
         const int ly = in ? slab_cell(j, g.ny, p.P) : -1;
         const bool bx = in && lx >= 0, bz = in && lz >= 0;
-        const unsigned ix = bx ? (unsigned)psi_x(g, p.W, lx, j, k) : 0u;
+        const unsigned ix = bx ? (unsigned)psi_x(g, p.P, lx, j, k) : 0u;
         const unsigned iy = ly >= 0 ? (unsigned)psi_y(g, p.W, c.i, ly, k) : 0u;
         const unsigned iz = bz ? (unsigned)psi_z(g, p.W, c.i, j, lz) : 0u;
         q.xHz[a] = bx ? p.hin[0][1][ix] : 0.f;
@@ -187,7 +186,7 @@ __device__ __forceinline__ void compute_plane(const Args &A, Plane<TY> &p, Plane
     const float kH = A.kH;
     int lx = -1, lz = -1;
     if (PML) {
-        lx = (c.colok && i < g.nx) ? slab_cell(i, g.nx, pm.P) : -1;
+        lx = (c.colok && i < g.nx) ? psi_x_pos(i, g.nx, pm.P) : -1;
         lz = slab_cell(k, g.nz, pm.P);
     }
     // ---- H^{n+1/2}(k) on rows j0-1 .. j0+TY-1 ----
@@ -269,7 +268,7 @@ __device__ __forceinline__ void compute_plane(const Args &A, Plane<TY> &p, Plane
                         const float aa = pm.aE[0][i], bb = pm.bE[0][i];
                         dxEy = cpml(q.xEy[r], aa, bb, dxEy);
                         dxEz = cpml(q.xEz[r], aa, bb, dxEz);
-                        const unsigned ix = (unsigned)psi_x(g, pm.W, lx, j, k);
+                        const unsigned ix = (unsigned)psi_x(g, pm.P, lx, j, k);
                         if (i >= 1 && k >= 1) pm.e[0][0][ix] = q.xEy[r];
                         if (i >= 1 && j >= 1) pm.e[0][1][ix] = q.xEz[r];
                         if (j >= 1) pm.hout[0][0][ix] = q.xHy[r];
@@ -370,7 +369,7 @@ __device__ __forceinline__ void march(const Args &A, const Box &B, int tile, int
 __global__ void __launch_bounds__(NT, STRIP_MINB) k_strip(const Args A) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int blk = (int)blockIdx.x + A.block0;
+    const int blk = (int)blockIdx.x;
     int b = 0;
     while (b + 1 < A.nbox && blk >= A.box[b + 1].first) ++b;
     const Box &B = A.box[b];
@@ -391,7 +390,6 @@ struct HostState {
 }  // namespace
 
 const char *strip_name() { return "fused-strip-30"; }
-bool strip_has_shell(const fdtd_ctx *h) { return static_cast<const HostState *>(h->strip)->nbox > 1; }
 
 int strip_prepare(fdtd_ctx *h) {
     const Grid &g = h->g;
@@ -451,13 +449,7 @@ void strip_release(fdtd_ctx *h) {
     h->strip = nullptr;
 }
 
-long long strip_interior_cells(const fdtd_ctx *h) {
-    const Grid &g = h->g;
-    (void)static_cast<const HostState *>(h->strip);
-    return (long long)g.nx * g.ny * g.nz;
-}
-
-void launch_strip(fdtd_ctx *h, cudaStream_t s, bool shell_only) {
+void launch_strip(fdtd_ctx *h, cudaStream_t s) {
     HostState *st = static_cast<HostState *>(h->strip);
     const Grid &g = h->g;
     Args a;
@@ -474,10 +466,7 @@ void launch_strip(fdtd_ctx *h, cudaStream_t s, bool shell_only) {
     a.kH = (float)h->kH;
     a.nbox = st->nbox;
     for (int b = 0; b < st->nbox; ++b) a.box[b] = st->box[b];
-    // box 0 is the interior box; the shell boxes follow it
-    a.block0 = shell_only ? (st->nbox > 1 ? st->box[1].first : st->blocks) : 0;
-    const int blocks = st->blocks - a.block0;
-    if (blocks > 0) k_strip<<<blocks, NT, 0, s>>>(a);
+    if (st->blocks > 0) k_strip<<<st->blocks, NT, 0, s>>>(a);
 }
 
 }  // namespace fdtd

@@ -1,17 +1,22 @@
-// kernels_vtile.cu -- one-pass leapfrog step over the CPML-free interior box:
-// TMA-staged planes, four columns per lane.
+// kernels_vtile.cu -- one-pass leapfrog step over the whole grid: TMA-staged
+// planes, four columns per lane, CPML folded in.
 //
 // H^{n+1/2} and E^{n+1} of a plane are computed together (Yee scheme,
-// Sec. III.A; shower current of Sec. III.B): a step reads E^n and H^{n-1/2}
-// once and writes H^{n+1/2} and E^{n+1} once, 24 B + 24 B per cell.
+// Sec. III.A; shower current of Sec. III.B; CPML of Sec. III.C): a step reads
+// E^n and H^{n-1/2} once and writes H^{n+1/2} and E^{n+1} once, 24 B + 24 B
+// per cell, plus the CPML memory of the cells in the layers (16 B read and
+// 16 B written per cell and layer axis).
 //
 // A block owns a tile of 128 columns [i0, i0+128) (i0 a multiple of 128) by
-// BY rows and marches up a chunk of z planes.  For every plane p of the input
-// set, one thread issues six TMA loads (cp.async.bulk.tensor.3d), one box per
-// component of 136 columns x (BY+2) rows starting at (i0-4, jb-1): the tile
-// plus a one-cell halo on every side, the x origin on a 16-byte boundary.
-// Planes stream into a ring of NS stages tracked by mbarriers, several planes
-// ahead of the compute.
+// BY rows and marches up a chunk of z planes.  For every plane of the input
+// set, one thread issues the TMA loads (cp.async.bulk.tensor.3d) of one
+// pipeline stage: one box per field component of 136 columns x (BY+2) rows
+// starting at (i0-4, jb-1) -- the tile plus a one-cell halo on every side,
+// the x origin on a 16-byte boundary; outside the node grid a box reads zeros
+// -- and, where the block touches a CPML layer, boxes of the four psi arrays
+// of that axis (below).  Stages form a ring tracked by mbarriers; a block
+// without CPML work holds up to NSMAX planes in flight, a block with it as
+// many as its larger stages leave room for (at least two).
 //
 // Warps 0..BY-1 each own one row of the tile; lane L holds the four columns
 // i0+4L .. i0+4L+3 as float4.  Per plane k:
@@ -23,10 +28,28 @@
 //   barrier
 //   E phase: E^{n+1}(k) from the H plane (neighbours j-1 and i-1) and the
 //     own H^{n+1/2}(k-1) Hx, Hy kept in registers; stored.
-//   barrier; the stage of plane k is refilled with plane k+NS.
-// A chunk that starts above the box's first plane first runs the H phase of
-// plane k0-1 without stores.  Every mbarrier wait is bounded; on expiry the
-// block records the failure in a device flag and stops.
+//   barrier; the stage of plane k is refilled with plane k+ns.
+// A chunk that starts above plane 0 first runs the H phase of plane k0-1
+// without stores.  Every mbarrier wait is bounded; on expiry the block records
+// the failure in a device flag and stops.
+//
+// CPML.  psi boxes of a stage (rows jb-1 .. jb+BY-1, so that the halo H has
+// its terms too):
+//   x: the half of the x rows (low layer or high layer, psi_x_pos) that the
+//      tile or its halo column meets;
+//   y: 132 columns from i0-4, BY+1 slab rows from l0, when a row of the tile
+//      (or the halo row) lies in a y layer; the slab rows of BY+1 consecutive
+//      grid rows are consecutive in the slab index, so one box holds them;
+//   z: 132 columns x BY+1 rows at slab plane lz, when plane k lies in a z layer.
+// A warp is one row, so "row j lies in a y layer" is uniform over the warp;
+// "plane k lies in a z layer" is uniform over the block.  In a tile that meets
+// an x layer every lane runs the x recursion on its float4: the coefficients
+// are zero outside the layer, where it leaves the derivative unchanged, and
+// only the lanes with layer columns store psi.  The z chunks are split at the
+// z layers, so only the short layer chunks carry z boxes (a middle chunk whose
+// warm-up plane lies in a layer reads that plane's H psi directly).  The halo H that a
+// block recomputes uses its neighbours' H psi at n-1/2 (read only); the E psi
+// are updated in place and the H psi written to the n+1/2 copy by the owner.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -41,36 +64,57 @@ namespace {
 #ifndef VT_BY
 #define VT_BY 8
 #endif
-#ifndef VT_NS
-#define VT_NS 4
+#ifndef VT_NSMAX
+#define VT_NSMAX 6
 #endif
 constexpr int BY = VT_BY;              // rows per tile (one warp each)
-constexpr int NS = VT_NS;              // pipeline stages
+constexpr int NSMAX = VT_NSMAX;        // most pipeline stages
 constexpr int NW = BY + 1;             // warps: BY row warps + one halo warp
 constexpr int NT = 32 * NW;
 constexpr int TXC = 128;               // tile columns
-constexpr int BXC = TXC + 8;           // box columns: i0-4 .. i0+131
-constexpr int BYR = BY + 2;            // box rows: jb-1 .. jb+BY
-constexpr int BOX = BXC * BYR;         // floats per component box
-constexpr int BOXP = (BOX + 31) / 32 * 32;  // box stride (128-byte aligned)
-constexpr int STAGE = 6 * BOXP;        // floats per stage
-constexpr unsigned STAGE_BYTES = 6u * BOX * 4u;
+constexpr int BXC = TXC + 8;           // field box columns: i0-4 .. i0+131
+constexpr int BYR = BY + 2;            // field box rows: jb-1 .. jb+BY
+constexpr int BOX = BXC * BYR;         // floats per field box
+constexpr int BOXP = (BOX + 31) / 32 * 32;  // field box stride (128-byte aligned)
+constexpr int FIELDS = 6 * BOXP;       // floats of the field boxes of a stage
+constexpr unsigned FIELD_BYTES = 6u * BOX * 4u;
+constexpr int PW = TXC + 4;            // y/z psi box columns: i0-4 .. i0+127
+constexpr int PR = BY + 1;             // psi box rows: jb-1 .. jb+BY-1
+constexpr int PBOX = PW * PR;
+constexpr int PBOXP = (PBOX + 31) / 32 * 32;
 constexpr int HR = BY + 1;             // H plane rows: jb-1 .. jb+BY-1
 constexpr int HPL = HR * BXC;          // floats per H-plane component
-constexpr size_t BAR_BYTES = 128;
-constexpr size_t SMEM_BYTES = BAR_BYTES + (size_t)NS * STAGE * 4 + 3 * (size_t)HPL * 4;
-static_assert((BXC * 4) % 16 == 0, "box rows must be a multiple of 16 bytes");
-static_assert(NS * 8 <= (int)BAR_BYTES, "barrier area");
+constexpr int BAR_BYTES = 128;
+// CPML coefficient table: aH, bH, aE, bE of the tile's columns i0-4 .. i0+127
+// (CXN each; column c at c - i0 + 4, 16-byte aligned per lane), of its rows
+// jb-1 .. jb+BY-1 (HR each), of the chunk's planes kstart .. k1-1 (zc each)
+constexpr int CXN = PW;
+constexpr int CY = 4 * CXN;
+constexpr int CZ = CY + 4 * HR;
+static_assert((BXC * 4) % 16 == 0 && (PW * 4) % 16 == 0, "box rows must be a multiple of 16 bytes");
+static_assert(NSMAX * 8 <= BAR_BYTES, "barrier area");
+static_assert(BY <= 32, "one halo lane per row");
+
+// shared memory: barriers, H plane, coefficient table, then the stage ring
+__host__ __device__ constexpr int head_floats(int zc) { return (3 * HPL + CZ + 4 * zc + 31) / 32 * 32; }
 
 struct Maps {
-    CUtensorMap m[2][6];  // [set][component]
+    CUtensorMap f[2][6];    // fields [set][component]
+    CUtensorMap x[4][2];    // psi x: xHy, xHz (H, [set]) then xEy, xEz (E, one map)
+    CUtensorMap y[4][2];    // psi y: yHx, yHz, yEx, yEz
+    CUtensorMap z[4][2];    // psi z: zHx, zHy, zEx, zEy
 };
 
 struct Args {
     Grid g;
     float *oex, *oey, *oez, *ohx, *ohy, *ohz;   // output set
-    int ilo, ihi, jlo, jhi, klo, khi;           // interior box (ilo, ihi+1 multiples of 4)
-    int tx0, tiles_x, tiles_y, chunk;
+    Cpml pml;
+    int tiles_x, tiles_y;
+    int za, zb, cm, m;                          // z chunks: [0, za), m of cm planes over [za, zb), [zb, nz)
+    int zc;                                     // planes of the coefficient table (longest chunk + 1)
+    int ring;                                   // floats available to the stage ring
+    int xlo4, xhb, xbw;                         // x psi: high half start, first column of the high
+                                                // half, box width
     int cur;
     Source src;
     SourceStep ss;
@@ -116,188 +160,514 @@ __device__ __forceinline__ void tma_load(float *dst, const CUtensorMap *map, uin
 __device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ void sts4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 
-// box offset of (box column bc, box row br) for component c
-__device__ __forceinline__ int bo(int c, int br, int bc) { return c * BOXP + br * BXC + bc; }
-
-__device__ __forceinline__ void issue_plane(const CUtensorMap *mp, float *stage, uint64_t *bar, int i0, int jb, int z) {
-    mbar_expect_tx(bar, STAGE_BYTES);
-    for (int c = 0; c < 6; ++c) tma_load(stage + c * BOXP, &mp[c], bar, i0 - 4, jb - 1, z);
+__device__ __forceinline__ float4 operator-(float4 a, float4 b) {
+    return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+// a + s * d, elementwise
+__device__ __forceinline__ float4 axpy(float4 a, float s, float4 d) {
+    return make_float4(a.x + s * d.x, a.y + s * d.y, a.z + s * d.z, a.w + s * d.w);
 }
 
-__global__ void __launch_bounds__(NT, 1) k_vtile(const Args A, const __grid_constant__ Maps maps) {
+// CPML recursion psi <- b psi + a d; the derivative becomes d + psi
+__device__ __forceinline__ float cpml1(float &psi, float a, float b, float d) {
+    psi = b * psi + a * d;
+    return d + psi;
+}
+__device__ __forceinline__ float4 cpml4(float4 &psi, float a, float b, float4 d) {
+    return make_float4(cpml1(psi.x, a, b, d.x), cpml1(psi.y, a, b, d.y), cpml1(psi.z, a, b, d.z),
+                       cpml1(psi.w, a, b, d.w));
+}
+
+// elementwise coefficients
+__device__ __forceinline__ float4 cpmlv(float4 &psi, float4 a, float4 b, float4 d) {
+    return make_float4(cpml1(psi.x, a.x, b.x, d.x), cpml1(psi.y, a.y, b.y, d.y), cpml1(psi.z, a.z, b.z, d.z),
+                       cpml1(psi.w, a.w, b.w, d.w));
+}
+
+// zero the whole vector (all) or its first element (first): the components a
+// cell owns on the grid's low faces are not updated
+__device__ __forceinline__ float4 mask(float4 v, bool all, bool first) {
+    if (all) return make_float4(0.f, 0.f, 0.f, 0.f);
+    if (first) v.x = 0.f;
+    return v;
+}
+// store the first n (1..4) elements; a 16-byte store when n == 4
+__device__ __forceinline__ void st4n(float *p, float4 v, int n) {
+    if (n == 4) {
+        *reinterpret_cast<float4 *>(p) = v;
+    } else {
+        p[0] = v.x;
+        if (n > 1) p[1] = v.y;
+        if (n > 2) p[2] = v.z;
+    }
+}
+
+// field box offset of (box column bc, box row br) for component c
+__device__ __forceinline__ int bo(int c, int br, int bc) { return c * BOXP + br * BXC + bc; }
+
+// Block geometry and stage layout, fixed for the whole march.
+struct Blk {
+    int i0, jb, k0, k1, kstart, nplanes;
+    bool src_blk;
+    bool hx, hy, hz;     // the stages carry x / y / z psi boxes
+    int l0;              // first y slab row of the y box
+    int xo, yo, zo;      // psi region offsets inside a stage
+    int stage, ns;       // floats per stage, stages in the ring
+    int xlo, xhi;        // x box index of the low / high half, or -1
+    int nxb, xb;         // x boxes per array, floats per x box (128-byte aligned)
+};
+
+__device__ __forceinline__ void issue_plane(const Args &A, const Maps &M, const Blk &B, float *st, uint64_t *bar,
+                                            int r) {
+    const int z = B.kstart + r;
+    const int set = A.cur;
+    const int lz = (B.hz && z < B.k1) ? slab_cell(z, A.g.nz, A.pml.P) : -1;
+    unsigned bytes = FIELD_BYTES;
+    if (B.hx) bytes += 4u * (unsigned)B.nxb * (unsigned)A.xbw * PR * 4u;
+    if (B.hy) bytes += 4u * PBOX * 4u;
+    if (lz >= 0) bytes += 4u * PBOX * 4u;
+    mbar_expect_tx(bar, bytes);
+    for (int c = 0; c < 6; ++c) tma_load(st + c * BOXP, &M.f[set][c], bar, B.i0 - 4, B.jb - 1, z);
+    if (B.hx)
+        for (int a = 0; a < 4; ++a) {
+            float *d = st + B.xo + a * B.nxb * B.xb;
+            if (B.xlo >= 0) tma_load(d + B.xlo * B.xb, &M.x[a][a < 2 ? set : 0], bar, 0, B.jb - 1, z);
+            if (B.xhi >= 0) tma_load(d + B.xhi * B.xb, &M.x[a][a < 2 ? set : 0], bar, A.xlo4, B.jb - 1, z);
+        }
+    if (B.hy)
+        for (int a = 0; a < 4; ++a) tma_load(st + B.yo + a * PBOXP, &M.y[a][a < 2 ? set : 0], bar, B.i0 - 4, B.l0, z);
+    if (lz >= 0)
+        for (int a = 0; a < 4; ++a) tma_load(st + B.zo + a * PBOXP, &M.z[a][a < 2 ? set : 0], bar, B.i0 - 4, B.jb - 1, lz);
+}
+
+// Per-lane geometry, fixed for the whole march.
+struct Lane {
+    int lane, w, c0, nval;
+    bool roww, colin;
+    int j;          // row of the lane's cells (row warps) or jb-1 (halo warp)
+    bool rowin;     // 0 <= j < ny
+    int ly;         // y slab index of row j, or -1 (also -1 off the grid)
+    bool xl;        // some column lies in an x layer (and the row on the grid)
+    int xpos;       // x psi position of column c0 (xl lanes)
+    int xs;         // offset of the lane's x psi in a stage's x region (row jb-1 based)
+    // halo column i0-1 (halo warp, lanes < BY): row jc
+    int jc, lyc;
+    int xsc;        // offset of column i0-1's x psi (row 0 based), or -1
+    bool cin;
+};
+
+// One plane: H phase, barrier, E phase, barrier, refill.  Returns false when
+// a wait expired (the block then stops).
+// Ring position of plane rel: its stage s0, the stage s1 of plane rel+1 and
+// the phase parity of that stage's barrier
+struct RingPos {
+    int s0, s1;
+    uint32_t ph1;
+};
+
+// One plane: H phase, barrier, E phase, barrier, refill.  HX: the block
+// meets an x layer; HYZ: it meets a y layer or a z layer (or its warm-up plane
+// lies in one).  A block runs the instance of its case, so the plain update of
+// the CPML-free interior carries no layer code at all.  Returns false when a
+// wait expired (the block then stops).
+template <bool HX, bool HYZ>
+__device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &L, const Blk &B, uint64_t *bar,
+                                      float *ring, float *HS, const float *CT, int rel, RingPos &rp,
+                                      float4 &hxp, float4 &hyp) {
+    const Grid &g = A.g;
+    const Cpml &pm = A.pml;
+    const int tid = threadIdx.x;
+    const int k = B.kstart + rel;
+    const bool own = k >= B.k0;
+    const int s0i = rp.s0, s1i = rp.s1;
+
+    bool ok = true;
+    if (rel == 0) ok = mbar_wait(&bar[0], 0);
+    ok = ok && mbar_wait(&bar[s1i], rp.ph1);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+            atomicOr(A.flags, 1);
+            for (int r = rel; r < B.nplanes && r < rel + B.ns; ++r) mbar_wait(&bar[r % B.ns], (r / B.ns) & 1);
+        }
+        __syncthreads();
+        return false;
+    }
+    const float *s0 = ring + s0i * B.stage;   // plane k
+    const float *s1 = ring + s1i * B.stage;   // plane k+1
+    const int lzk = slab_cell(k, g.nz, pm.P);
+    const int lz = B.hz ? lzk : -1;   // z layer plane with z boxes in the stage
+    const float kH = A.kH, kE = A.kE;
+    const int bc0 = 4 + 4 * L.lane;
+    const unsigned goffk = (unsigned)L.c0 + (unsigned)L.j * (unsigned)g.pitch + (unsigned)k * (unsigned)g.plane;
+    const bool storable = L.roww && L.rowin && L.colin;
+    const bool zl = HYZ && lz >= 0 && L.rowin && L.colin;
+    // psi of this lane's cells in the stage of plane k
+    const float *PX = s0 + B.xo + L.xs + (L.j - B.jb + 1) * A.xbw;
+    const int XA = B.nxb * B.xb;   // floats per x psi array in a stage
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float *PY = s0 + B.yo + (L.ly - B.l0) * PW + bc0;
+    const float *PZ = s0 + B.zo + (L.j - B.jb + 1) * PW + bc0;
+
+    float4 ex0, ey0, ez0, hxn, hyn, hzn;
+    if (L.roww) {
+        const int br = L.w + 1;  // box row of j
+        ex0 = lds4(s0 + bo(0, br, bc0));
+        ey0 = lds4(s0 + bo(1, br, bc0));
+        ez0 = lds4(s0 + bo(2, br, bc0));
+        const float4 hx = lds4(s0 + bo(3, br, bc0));
+        const float4 hy = lds4(s0 + bo(4, br, bc0));
+        const float4 hz = lds4(s0 + bo(5, br, bc0));
+        const float4 exU = lds4(s0 + bo(0, br + 1, bc0));  // row j+1
+        const float4 ezU = lds4(s0 + bo(2, br + 1, bc0));
+        const float eyR = s0[bo(1, br, bc0 + 4)];         // column c0+4
+        const float ezR = s0[bo(2, br, bc0 + 4)];
+        const float4 ex1 = lds4(s1 + bo(0, br, bc0));
+        const float4 ey1 = lds4(s1 + bo(1, br, bc0));
+        float4 dyEz = ezU - ez0, dzEy = ey1 - ey0;                                    // Hx
+        float4 dzEx = ex1 - ex0, dxEz = make_float4(ez0.y, ez0.z, ez0.w, ezR) - ez0;  // Hy
+        float4 dxEy = make_float4(ey0.y, ey0.z, ey0.w, eyR) - ey0, dyEx = exU - ex0;  // Hz
+        float4 qy0, qy1, qz0, qz1, qx0, qx1;
+        if (HYZ && L.ly >= 0) {
+            const float a = CT[CY + br], b = CT[CY + HR + br];
+            qy0 = lds4(PY);
+            qy1 = lds4(PY + PBOXP);
+            dyEz = cpml4(qy0, a, b, dyEz);
+            dyEx = cpml4(qy1, a, b, dyEx);
+        }
+        if (zl) {
+            const float a = CT[CZ + rel], b = CT[CZ + A.zc + rel];
+            qz0 = lds4(PZ);
+            qz1 = lds4(PZ + PBOXP);
+            dzEy = cpml4(qz0, a, b, dzEy);
+            dzEx = cpml4(qz1, a, b, dzEx);
+        } else if (HYZ && !own && lzk >= 0 && L.rowin && L.colin) {
+            // warm-up plane in a z layer, the stage has no z boxes
+            const unsigned o = (unsigned)psi_z(g, pm.W, L.c0, L.j, lzk);
+            const float a = CT[CZ + rel], b = CT[CZ + A.zc + rel];
+            qz0 = *reinterpret_cast<const float4 *>(pm.hin[2][0] + o);
+            qz1 = *reinterpret_cast<const float4 *>(pm.hin[2][1] + o);
+            dzEy = cpml4(qz0, a, b, dzEy);
+            dzEx = cpml4(qz1, a, b, dzEx);
+        }
+        if (HX) {
+            const float4 a = lds4(CT + bc0), b = lds4(CT + CXN + bc0);
+            qx0 = L.xl ? lds4(PX) : z4;
+            qx1 = L.xl ? lds4(PX + XA) : z4;
+            dxEz = cpmlv(qx0, a, b, dxEz);
+            dxEy = cpmlv(qx1, a, b, dxEy);
+        }
+        hxn = axpy(hx, -kH, dyEz - dzEy);
+        hyn = axpy(hy, -kH, dzEx - dxEz);
+        hzn = axpy(hz, -kH, dxEy - dyEx);
+        if (own) {
+            sts4(HS + 0 * HPL + br * BXC + bc0, hxn);
+            sts4(HS + 1 * HPL + br * BXC + bc0, hyn);
+            sts4(HS + 2 * HPL + br * BXC + bc0, hzn);
+            if (storable) {
+                const bool f0 = L.c0 == 0, j0 = L.j == 0, k0 = k == 0;
+                st4n(A.ohx + goffk, mask(hxn, false, f0), L.nval);
+                st4n(A.ohy + goffk, mask(hyn, j0, false), L.nval);
+                st4n(A.ohz + goffk, mask(hzn, k0, false), L.nval);
+                if (HYZ && L.ly >= 0) {
+                    const unsigned o = (unsigned)psi_y(g, pm.W, L.c0, L.ly, k);
+                    st4n(pm.hout[1][0] + o, mask(qy0, false, f0), L.nval);
+                    st4n(pm.hout[1][1] + o, mask(qy1, k0, false), L.nval);
+                }
+                if (zl) {
+                    const unsigned o = (unsigned)psi_z(g, pm.W, L.c0, L.j, lz);
+                    st4n(pm.hout[2][0] + o, mask(qz0, false, f0), L.nval);
+                    st4n(pm.hout[2][1] + o, mask(qz1, j0, false), L.nval);
+                }
+                if (L.xl) {
+                    const unsigned o = (unsigned)psi_x(g, pm.P, L.xpos, L.j, k);
+                    st4n(pm.hout[0][0] + o, mask(qx0, j0, false), L.nval);
+                    st4n(pm.hout[0][1] + o, mask(qx1, k0, false), L.nval);
+                }
+            }
+        }
+    } else if (own) {
+        // halo warp: H at row jb-1 (Hx, Hz) over the tile's columns
+        {
+            const float4 ex = lds4(s0 + bo(0, 0, bc0)), ey = lds4(s0 + bo(1, 0, bc0)), ez = lds4(s0 + bo(2, 0, bc0));
+            const float4 hx = lds4(s0 + bo(3, 0, bc0)), hz = lds4(s0 + bo(5, 0, bc0));
+            const float4 exU = lds4(s0 + bo(0, 1, bc0)), ezU = lds4(s0 + bo(2, 1, bc0));
+            const float4 ey1 = lds4(s1 + bo(1, 0, bc0));
+            const float eyR = s0[bo(1, 0, bc0 + 4)];
+            float4 dyEz = ezU - ez, dzEy = ey1 - ey;
+            float4 dxEy = make_float4(ey.y, ey.z, ey.w, eyR) - ey, dyEx = exU - ex;
+            if (HYZ && L.ly >= 0) {
+                const float a = CT[CY], b = CT[CY + HR];
+                float4 q0 = lds4(PY), q1 = lds4(PY + PBOXP);
+                dyEz = cpml4(q0, a, b, dyEz);
+                dyEx = cpml4(q1, a, b, dyEx);
+            }
+            if (zl) {
+                float4 q0 = lds4(PZ);
+                dzEy = cpml4(q0, CT[CZ + rel], CT[CZ + A.zc + rel], dzEy);
+            }
+            if (HX) {
+                float4 q1 = L.xl ? lds4(PX + XA) : z4;
+                dxEy = cpmlv(q1, lds4(CT + bc0), lds4(CT + CXN + bc0), dxEy);
+            }
+            sts4(HS + 0 * HPL + bc0, axpy(hx, -kH, dyEz - dzEy));
+            sts4(HS + 2 * HPL + bc0, axpy(hz, -kH, dxEy - dyEx));
+        }
+        // column i0-1 (box column 3), rows jb .. jb+BY-1 (Hy, Hz)
+        if (L.lane < BY) {
+            const int b = L.lane + 1;
+            const float ey = s0[bo(1, b, 3)], eyR = s0[bo(1, b, 4)];
+            const float ex = s0[bo(0, b, 3)], exU = s0[bo(0, b + 1, 3)], ex1 = s1[bo(0, b, 3)];
+            const float ez = s0[bo(2, b, 3)], ezR = s0[bo(2, b, 4)];
+            const float hy = s0[bo(4, b, 3)], hz = s0[bo(5, b, 3)];
+            float dzEx = ex1 - ex, dxEz = ezR - ez, dxEy = eyR - ey, dyEx = exU - ex;
+            if (L.cin) {
+                if (HYZ && lz >= 0) {
+                    float q = s0[B.zo + PBOXP + b * PW + 3];
+                    dzEx = cpml1(q, CT[CZ + rel], CT[CZ + A.zc + rel], dzEx);
+                }
+                if (HX && L.xsc >= 0) {
+                    const float *px = s0 + B.xo + L.xsc + b * A.xbw;
+                    float q0 = px[0], q1 = px[XA];
+                    dxEz = cpml1(q0, CT[3], CT[CXN + 3], dxEz);
+                    dxEy = cpml1(q1, CT[3], CT[CXN + 3], dxEy);
+                }
+                if (HYZ && L.lyc >= 0) {
+                    float q = s0[B.yo + PBOXP + (L.lyc - B.l0) * PW + 3];
+                    dyEx = cpml1(q, CT[CY + b], CT[CY + HR + b], dyEx);
+                }
+            }
+            HS[1 * HPL + b * BXC + 3] = hy - kH * (dzEx - dxEz);
+            HS[2 * HPL + b * BXC + 3] = hz - kH * (dxEy - dyEx);
+        }
+    }
+    __syncthreads();
+
+    // ---- E phase ----
+    if (L.roww && own) {
+        const int br = L.w + 1;
+        const float4 hzD = lds4(HS + 2 * HPL + (br - 1) * BXC + bc0);   // row j-1
+        const float4 hxD = lds4(HS + 0 * HPL + (br - 1) * BXC + bc0);
+        const float hzL = HS[2 * HPL + br * BXC + bc0 - 1];             // column c0-1
+        const float hyL = HS[1 * HPL + br * BXC + bc0 - 1];
+        float4 dyHz = hzn - hzD, dzHy = hyn - hyp;                                       // Ex
+        float4 dzHx = hxn - hxp, dxHz = hzn - make_float4(hzL, hzn.x, hzn.y, hzn.z);     // Ey
+        float4 dxHy = hyn - make_float4(hyL, hyn.x, hyn.y, hyn.z), dyHx = hxn - hxD;     // Ez
+        float4 qy0, qy1, qz0, qz1, qx0, qx1;
+        if (HYZ && L.ly >= 0) {
+            const float a = CT[CY + 2 * HR + br], b = CT[CY + 3 * HR + br];
+            qy0 = lds4(PY + 2 * PBOXP);
+            qy1 = lds4(PY + 3 * PBOXP);
+            dyHz = cpml4(qy0, a, b, dyHz);
+            dyHx = cpml4(qy1, a, b, dyHx);
+        }
+        if (zl) {
+            const float a = CT[CZ + 2 * A.zc + rel], b = CT[CZ + 3 * A.zc + rel];
+            qz0 = lds4(PZ + 2 * PBOXP);
+            qz1 = lds4(PZ + 3 * PBOXP);
+            dzHy = cpml4(qz0, a, b, dzHy);
+            dzHx = cpml4(qz1, a, b, dzHx);
+        }
+        if (HX) {
+            const float4 a = lds4(CT + 2 * CXN + bc0), b = lds4(CT + 3 * CXN + bc0);
+            qx0 = L.xl ? lds4(PX + 2 * XA) : z4;
+            qx1 = L.xl ? lds4(PX + 3 * XA) : z4;
+            dxHz = cpmlv(qx0, a, b, dxHz);
+            dxHy = cpmlv(qx1, a, b, dxHy);
+        }
+        float4 nex = axpy(ex0, kE, dyHz - dzHy);
+        float4 ney = axpy(ey0, kE, dzHx - dxHz);
+        float4 nez = axpy(ez0, kE, dxHy - dyHx);
+        if (storable) {
+            if (B.src_blk) {
+                nez.x += source_at(A.src, A.ss, L.c0, L.j, k);
+                nez.y += source_at(A.src, A.ss, L.c0 + 1, L.j, k);
+                nez.z += source_at(A.src, A.ss, L.c0 + 2, L.j, k);
+                nez.w += source_at(A.src, A.ss, L.c0 + 3, L.j, k);
+            }
+            const bool f0 = L.c0 == 0, j0 = L.j == 0, k0 = k == 0;
+            st4n(A.oex + goffk, mask(nex, j0 || k0, false), L.nval);
+            st4n(A.oey + goffk, mask(ney, k0, f0), L.nval);
+            st4n(A.oez + goffk, mask(nez, j0, f0), L.nval);
+            if (HYZ && L.ly >= 0) {
+                const unsigned o = (unsigned)psi_y(g, pm.W, L.c0, L.ly, k);
+                st4n(pm.e[1][0] + o, mask(qy0, j0 || k0, false), L.nval);
+                st4n(pm.e[1][1] + o, mask(qy1, j0, f0), L.nval);
+            }
+            if (zl) {
+                const unsigned o = (unsigned)psi_z(g, pm.W, L.c0, L.j, lz);
+                st4n(pm.e[2][0] + o, mask(qz0, j0 || k0, false), L.nval);
+                st4n(pm.e[2][1] + o, mask(qz1, k0, f0), L.nval);
+            }
+            if (L.xl) {
+                const unsigned o = (unsigned)psi_x(g, pm.P, L.xpos, L.j, k);
+                st4n(pm.e[0][0] + o, mask(qx0, k0, f0), L.nval);
+                st4n(pm.e[0][1] + o, mask(qx1, j0, f0), L.nval);
+            }
+        }
+    }
+    if (L.roww) { hxp = hxn; hyp = hyn; }
+    __syncthreads();  // stage of plane k and the H plane are free
+    if (tid == 0 && rel + B.ns < B.nplanes) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue_plane(A, M, B, ring + s0i * B.stage, &bar[s0i], rel + B.ns);
+    }
+    rp.s0 = s1i;
+    rp.s1 = s1i + 1;
+    if (rp.s1 == B.ns) {
+        rp.s1 = 0;
+        rp.ph1 ^= 1u;
+    }
+    return true;
+}
+
+template <bool HX, bool HYZ>
+__device__ __forceinline__ void march(const Args &A, const Maps &M, const Lane &L, const Blk &B, uint64_t *bar,
+                                      float *ring, float *HS, const float *CT) {
+    float4 hxp = make_float4(0.f, 0.f, 0.f, 0.f), hyp = hxp;   // own H^{n+1/2}(k-1) Hx, Hy
+    RingPos rp{0, 1, 0u};   // two stages at least
+    int rel = 0;
+    // a warm-up plane in a z layer (stages without z boxes) needs the layer
+    // code once
+    if (!HYZ && B.kstart < B.k0 && slab_cell(B.kstart, A.g.nz, A.pml.P) >= 0) {
+        if (!plane<HX, true>(A, M, L, B, bar, ring, HS, CT, rel, rp, hxp, hyp)) return;
+        ++rel;
+    }
+    for (; B.kstart + rel < B.k1; ++rel)
+        if (!plane<HX, HYZ>(A, M, L, B, bar, ring, HS, CT, rel, rp, hxp, hyp)) return;
+}
+
+__global__ void __launch_bounds__(NT, 1) k_vtile(const Args A, const __grid_constant__ Maps M) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
-    float *stages = reinterpret_cast<float *>(smem_raw + BAR_BYTES);
-    float *HS = stages + NS * STAGE;   // [3][HR][BXC]: Hx, Hy, Hz of plane k, column index col - i0 + 4
+    float *HS = reinterpret_cast<float *>(smem_raw + BAR_BYTES);  // [3][HR][BXC]: Hx, Hy, Hz of plane k
+    float *CT = HS + 3 * HPL;                                     // CPML coefficient table
+    float *ring = HS + head_floats(A.zc);                         // stage ring
 
     const Grid &g = A.g;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const Cpml &pm = A.pml;
+    const int P = pm.P;
+    const int tid = threadIdx.x;
+    Blk B;
     const int tx = (int)blockIdx.x % A.tiles_x, ty = (int)blockIdx.x / A.tiles_x;
-    const int i0 = (A.tx0 + tx) * TXC;
-    const int jb = A.jlo + ty * BY;
-    const int k0 = A.klo + (int)blockIdx.y * A.chunk;
-    const int k1 = min(A.khi + 1, k0 + A.chunk);
-    const int kstart = k0 > 0 ? k0 - 1 : 0;
-    const int nplanes = k1 - kstart + 1;   // input planes kstart .. k1
-    const CUtensorMap *mp = maps.m[A.cur];
+    B.i0 = tx * TXC;
+    B.jb = ty * BY;
+    {
+        const int c = (int)blockIdx.y, nfirst = A.za > 0 ? 1 : 0;
+        if (nfirst && c == 0) {
+            B.k0 = 0;
+            B.k1 = A.za;
+        } else if (c - nfirst < A.m) {
+            B.k0 = A.za + (c - nfirst) * A.cm;
+            B.k1 = min(A.zb, B.k0 + A.cm);
+        } else {
+            B.k0 = A.zb;
+            B.k1 = g.nz;
+        }
+    }
+    B.kstart = B.k0 > 0 ? B.k0 - 1 : 0;
+    B.nplanes = B.k1 - B.kstart + 1;   // input planes kstart .. k1
+    B.src_blk = A.src.active && B.i0 <= A.src.ic + A.src.L && B.i0 + TXC - 1 >= A.src.ic - A.src.L &&
+                B.jb <= A.src.jc + A.src.L && B.jb + BY - 1 >= A.src.jc - A.src.L;
+    // which psi boxes the stages carry
+    B.hx = B.hy = B.hz = false;
+    B.l0 = 0;
+    B.xlo = B.xhi = -1;
+    B.nxb = 0;
+    B.xb = (A.xbw * PR + 31) / 32 * 32;
+    if (P > 0) {
+        const int ilo = max(B.i0 - 1, 0), ihi = min(B.i0 + TXC - 1, g.nx - 1);
+        if (ilo <= P) B.xlo = B.nxb++;
+        if (ihi >= g.nx - P) B.xhi = B.nxb++;
+        B.hx = B.nxb > 0;
+        int lmin = 1 << 30;
+        for (int j = max(B.jb - 1, 0); j < min(B.jb + BY, g.ny); ++j) {
+            const int l = slab_cell(j, g.ny, P);
+            if (l >= 0 && l < lmin) lmin = l;
+        }
+        B.hy = lmin < (1 << 30);
+        B.l0 = B.hy ? lmin : 0;
+        B.hz = B.k0 < A.za || B.k0 >= A.zb;   // a layer chunk
+    }
+    B.xo = FIELDS;
+    B.yo = B.xo + 4 * B.nxb * B.xb;
+    B.zo = B.yo + (B.hy ? 4 * PBOXP : 0);
+    B.stage = B.zo + (B.hz ? 4 * PBOXP : 0);
+    B.ns = min(NSMAX, A.ring / B.stage);
 
     if (tid == 0) {
-        for (int s = 0; s < NS; ++s) mbar_init(&bar[s], 1);
+        for (int s = 0; s < B.ns; ++s) mbar_init(&bar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    if (P > 0) {
+        for (int t = tid; t < CXN; t += NT) {
+            const int i = B.i0 - 4 + t;
+            const bool in = i >= 0 && i < g.nx;
+            CT[t] = in ? pm.aH[0][i] : 0.f;
+            CT[CXN + t] = in ? pm.bH[0][i] : 0.f;
+            CT[2 * CXN + t] = in ? pm.aE[0][i] : 0.f;
+            CT[3 * CXN + t] = in ? pm.bE[0][i] : 0.f;
+        }
+        for (int t = tid; t < HR; t += NT) {
+            const int j = B.jb - 1 + t;
+            const bool in = j >= 0 && j < g.ny;
+            CT[CY + t] = in ? pm.aH[1][j] : 0.f;
+            CT[CY + HR + t] = in ? pm.bH[1][j] : 0.f;
+            CT[CY + 2 * HR + t] = in ? pm.aE[1][j] : 0.f;
+            CT[CY + 3 * HR + t] = in ? pm.bE[1][j] : 0.f;
+        }
+        for (int t = tid; t < A.zc; t += NT) {
+            const int k = B.kstart + t;
+            const bool in = k < B.k1;
+            CT[CZ + t] = in ? pm.aH[2][k] : 0.f;
+            CT[CZ + A.zc + t] = in ? pm.bH[2][k] : 0.f;
+            CT[CZ + 2 * A.zc + t] = in ? pm.aE[2][k] : 0.f;
+            CT[CZ + 3 * A.zc + t] = in ? pm.bE[2][k] : 0.f;
+        }
+    }
     __syncthreads();
     if (tid == 0)
-        for (int r = 0; r < NS && r < nplanes; ++r) issue_plane(mp, stages + r * STAGE, &bar[r], i0, jb, kstart + r);
+        for (int r = 0; r < B.ns && r < B.nplanes; ++r) issue_plane(A, M, B, ring + r * B.stage, &bar[r], r);
 
-    // row warps: row j, columns c0..c0+3 (box column bc0 = 4 + 4 lane)
-    const bool roww = w < BY;
-    const int j = jb + w;
-    const int c0 = i0 + 4 * lane;
-    const int bc0 = 4 + 4 * lane;
-    const int br = w + 1;                 // box row of j
-    const bool storable = roww && j <= A.jhi && c0 >= A.ilo && c0 + 3 <= A.ihi;
-    const unsigned goff = (unsigned)c0 + (unsigned)j * (unsigned)g.pitch;
-    const bool src_blk = A.src.active && i0 <= A.src.ic + A.src.L && i0 + TXC - 1 >= A.src.ic - A.src.L &&
-                         jb <= A.src.jc + A.src.L && jb + BY - 1 >= A.src.jc - A.src.L;
-    float4 hxp = make_float4(0.f, 0.f, 0.f, 0.f), hyp = hxp;   // own H^{n+1/2}(k-1) Hx, Hy
-    const float kH = A.kH, kE = A.kE;
+    Lane L;
+    L.lane = tid & 31;
+    L.w = tid >> 5;
+    L.roww = L.w < BY;
+    L.c0 = B.i0 + 4 * L.lane;
+    L.colin = L.c0 < g.nx;
+    L.nval = L.colin ? min(4, g.nx - L.c0) : 0;
+    L.j = L.roww ? B.jb + L.w : B.jb - 1;
+    L.rowin = L.j >= 0 && L.j < g.ny;
+    L.ly = (L.rowin && L.colin) ? slab_cell(L.j, g.ny, P) : -1;
+    L.xl = false;
+    L.xpos = L.xs = 0;
+    if (B.hx && L.rowin && L.colin) {
+        if (L.c0 <= P) {
+            L.xl = true;
+            L.xpos = L.c0;
+            L.xs = B.xlo * B.xb + L.c0;
+        } else if (L.c0 + 3 >= g.nx - P) {
+            L.xl = true;
+            L.xpos = A.xlo4 + L.c0 - A.xhb;
+            L.xs = B.xhi * B.xb + (L.c0 - A.xhb);
+        }
+    }
+    L.jc = B.jb + L.lane;
+    L.cin = !L.roww && L.lane < BY && L.jc < g.ny && B.i0 >= 1;
+    L.lyc = L.cin ? slab_cell(L.jc, g.ny, P) : -1;
+    L.xsc = -1;
+    if (L.cin && B.hx) {
+        const int ic = B.i0 - 1;
+        if (ic <= P) L.xsc = B.xlo * B.xb + ic;
+        else if (ic >= g.nx - P) L.xsc = B.xhi * B.xb + (ic - A.xhb);
+    }
 
-    for (int rel = 0; kstart + rel < k1; ++rel) {
-        const int k = kstart + rel;
-        bool ok = true;
-        if (rel == 0) ok = mbar_wait(&bar[0], 0);
-        ok = ok && mbar_wait(&bar[(rel + 1) % NS], ((rel + 1) / NS) & 1);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicOr(A.flags, 1);
-                for (int r = rel; r < nplanes && r < rel + NS; ++r) mbar_wait(&bar[r % NS], (r / NS) & 1);
-            }
-            __syncthreads();
-            return;
-        }
-        const float *s0 = stages + (rel % NS) * STAGE;        // plane k
-        const float *s1 = stages + ((rel + 1) % NS) * STAGE;  // plane k+1
-        const bool own = k >= k0;
-        const unsigned goffk = goff + (unsigned)k * (unsigned)g.plane;
-
-        float4 ex0, ey0, ez0, hxn, hyn, hzn;
-        if (roww) {
-            // ---- H phase, own cells ----
-            ex0 = lds4(s0 + bo(0, br, bc0));
-            ey0 = lds4(s0 + bo(1, br, bc0));
-            ez0 = lds4(s0 + bo(2, br, bc0));
-            const float4 hx = lds4(s0 + bo(3, br, bc0));
-            const float4 hy = lds4(s0 + bo(4, br, bc0));
-            const float4 hz = lds4(s0 + bo(5, br, bc0));
-            const float4 exU = lds4(s0 + bo(0, br + 1, bc0));      // row j+1
-            const float4 ezU = lds4(s0 + bo(2, br + 1, bc0));
-            const float4 eyR = lds4(s0 + bo(1, br, bc0 + 4));      // columns +4: .x is i+1 of .w
-            const float4 ezR = lds4(s0 + bo(2, br, bc0 + 4));
-            const float4 ex1 = lds4(s1 + bo(0, br, bc0));
-            const float4 ey1 = lds4(s1 + bo(1, br, bc0));
-            hxn.x = hx.x - kH * ((ezU.x - ez0.x) - (ey1.x - ey0.x));
-            hxn.y = hx.y - kH * ((ezU.y - ez0.y) - (ey1.y - ey0.y));
-            hxn.z = hx.z - kH * ((ezU.z - ez0.z) - (ey1.z - ey0.z));
-            hxn.w = hx.w - kH * ((ezU.w - ez0.w) - (ey1.w - ey0.w));
-            hyn.x = hy.x - kH * ((ex1.x - ex0.x) - (ez0.y - ez0.x));
-            hyn.y = hy.y - kH * ((ex1.y - ex0.y) - (ez0.z - ez0.y));
-            hyn.z = hy.z - kH * ((ex1.z - ex0.z) - (ez0.w - ez0.z));
-            hyn.w = hy.w - kH * ((ex1.w - ex0.w) - (ezR.x - ez0.w));
-            hzn.x = hz.x - kH * ((ey0.y - ey0.x) - (exU.x - ex0.x));
-            hzn.y = hz.y - kH * ((ey0.z - ey0.y) - (exU.y - ex0.y));
-            hzn.z = hz.z - kH * ((ey0.w - ey0.z) - (exU.z - ex0.z));
-            hzn.w = hz.w - kH * ((eyR.x - ey0.w) - (exU.w - ex0.w));
-            if (own) {
-                sts4(HS + 0 * HPL + br * BXC + bc0, hxn);
-                sts4(HS + 1 * HPL + br * BXC + bc0, hyn);
-                sts4(HS + 2 * HPL + br * BXC + bc0, hzn);
-                if (storable) {
-                    // components on the grid's low faces are not updated
-                    float4 sx = hxn, sy = hyn, sz = hzn;
-                    if (c0 == 0) sx.x = 0.f;
-                    if (j == 0) sy = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (k == 0) sz = make_float4(0.f, 0.f, 0.f, 0.f);
-                    *reinterpret_cast<float4 *>(A.ohx + goffk) = sx;
-                    *reinterpret_cast<float4 *>(A.ohy + goffk) = sy;
-                    *reinterpret_cast<float4 *>(A.ohz + goffk) = sz;
-                }
-            }
-        } else if (own) {
-            // ---- halo warp: H at row jb-1 (Hx, Hz), columns i0-4 .. i0+127 ----
-            for (int q = lane; q < TXC / 4 + 1; q += 32) {
-                const int bc = 4 * q;   // box columns bc .. bc+3
-                const float4 ex = lds4(s0 + bo(0, 0, bc)), ey = lds4(s0 + bo(1, 0, bc)), ez = lds4(s0 + bo(2, 0, bc));
-                const float4 hx = lds4(s0 + bo(3, 0, bc)), hz = lds4(s0 + bo(5, 0, bc));
-                const float4 exU = lds4(s0 + bo(0, 1, bc)), ezU = lds4(s0 + bo(2, 1, bc));
-                const float4 ey1 = lds4(s1 + bo(1, 0, bc));
-                const float eyRx = s0[bo(1, 0, bc + 4)];
-                float4 ox, oz;
-                ox.x = hx.x - kH * ((ezU.x - ez.x) - (ey1.x - ey.x));
-                ox.y = hx.y - kH * ((ezU.y - ez.y) - (ey1.y - ey.y));
-                ox.z = hx.z - kH * ((ezU.z - ez.z) - (ey1.z - ey.z));
-                ox.w = hx.w - kH * ((ezU.w - ez.w) - (ey1.w - ey.w));
-                oz.x = hz.x - kH * ((ey.y - ey.x) - (exU.x - ex.x));
-                oz.y = hz.y - kH * ((ey.z - ey.y) - (exU.y - ex.y));
-                oz.z = hz.z - kH * ((ey.w - ey.z) - (exU.z - ex.z));
-                oz.w = hz.w - kH * ((eyRx - ey.w) - (exU.w - ex.w));
-                sts4(HS + 0 * HPL + 0 * BXC + bc, ox);
-                sts4(HS + 2 * HPL + 0 * BXC + bc, oz);
-            }
-            // column i0-1 (box column 3), rows jb .. jb+BY-1 (Hy, Hz)
-            if (lane < BY) {
-                const int b = lane + 1;
-                const float ey = s0[bo(1, b, 3)], eyR = s0[bo(1, b, 4)];
-                const float ex = s0[bo(0, b, 3)], exU = s0[bo(0, b + 1, 3)], ex1 = s1[bo(0, b, 3)];
-                const float ez = s0[bo(2, b, 3)], ezR = s0[bo(2, b, 4)];
-                const float hy = s0[bo(4, b, 3)], hz = s0[bo(5, b, 3)];
-                HS[1 * HPL + b * BXC + 3] = hy - kH * ((ex1 - ex) - (ezR - ez));
-                HS[2 * HPL + b * BXC + 3] = hz - kH * ((eyR - ey) - (exU - ex));
-            }
-        }
-        __syncthreads();
-
-        // ---- E phase ----
-        if (roww && own) {
-            const float4 hzD = lds4(HS + 2 * HPL + (br - 1) * BXC + bc0);   // row j-1
-            const float4 hxD = lds4(HS + 0 * HPL + (br - 1) * BXC + bc0);
-            const float hzL = HS[2 * HPL + br * BXC + bc0 - 1];             // column i-1 of .x
-            const float hyL = HS[1 * HPL + br * BXC + bc0 - 1];
-            float4 nex, ney, nez;
-            nex.x = ex0.x + kE * ((hzn.x - hzD.x) - (hyn.x - hyp.x));
-            nex.y = ex0.y + kE * ((hzn.y - hzD.y) - (hyn.y - hyp.y));
-            nex.z = ex0.z + kE * ((hzn.z - hzD.z) - (hyn.z - hyp.z));
-            nex.w = ex0.w + kE * ((hzn.w - hzD.w) - (hyn.w - hyp.w));
-            ney.x = ey0.x + kE * ((hxn.x - hxp.x) - (hzn.x - hzL));
-            ney.y = ey0.y + kE * ((hxn.y - hxp.y) - (hzn.y - hzn.x));
-            ney.z = ey0.z + kE * ((hxn.z - hxp.z) - (hzn.z - hzn.y));
-            ney.w = ey0.w + kE * ((hxn.w - hxp.w) - (hzn.w - hzn.z));
-            nez.x = ez0.x + kE * ((hyn.x - hyL) - (hxn.x - hxD.x));
-            nez.y = ez0.y + kE * ((hyn.y - hyn.x) - (hxn.y - hxD.y));
-            nez.z = ez0.z + kE * ((hyn.z - hyn.y) - (hxn.z - hxD.z));
-            nez.w = ez0.w + kE * ((hyn.w - hyn.z) - (hxn.w - hxD.w));
-            if (storable) {
-                if (src_blk) {
-                    nez.x += source_at(A.src, A.ss, c0, j, k);
-                    nez.y += source_at(A.src, A.ss, c0 + 1, j, k);
-                    nez.z += source_at(A.src, A.ss, c0 + 2, j, k);
-                    nez.w += source_at(A.src, A.ss, c0 + 3, j, k);
-                }
-                if (j == 0 || k == 0) nex = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (k == 0) ney = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (c0 == 0) { ney.x = 0.f; nez.x = 0.f; }
-                if (j == 0) nez = make_float4(0.f, 0.f, 0.f, 0.f);
-                *reinterpret_cast<float4 *>(A.oex + goffk) = nex;
-                *reinterpret_cast<float4 *>(A.oey + goffk) = ney;
-                *reinterpret_cast<float4 *>(A.oez + goffk) = nez;
-            }
-        }
-        if (roww) { hxp = hxn; hyp = hyn; }
-        __syncthreads();  // stage of plane k and the H plane are free
-        if (tid == 0 && rel + NS < nplanes) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue_plane(mp, stages + ((rel + NS) % NS) * STAGE, &bar[(rel + NS) % NS], i0, jb, kstart + rel + NS);
-        }
+    if (B.hy || B.hz) {
+        if (B.hx) march<true, true>(A, M, L, B, bar, ring, HS, CT);
+        else march<false, true>(A, M, L, B, bar, ring, HS, CT);
+    } else {
+        if (B.hx) march<true, false>(A, M, L, B, bar, ring, HS, CT);
+        else march<false, false>(A, M, L, B, bar, ring, HS, CT);
     }
 }
 
@@ -307,17 +677,40 @@ typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, 
 
 struct HostState {
     Maps maps;
-    Args proto;
-    int blocks_x, chunks;
+    int tiles_x, tiles_y, za, zb, cm, m, zc, chunks, ring;
+    int xlo4, xhb, xbw;
+    size_t smem;
 };
+
+// 3-D float32 tensor map: extents d0 (innermost) .. d2, strides s1, s2 in
+// floats, box b0 x b1 x 1
+bool encode3(EncodeTiled encode, CUtensorMap *m, const float *base, cuuint64_t d0, cuuint64_t d1, cuuint64_t d2,
+             cuuint64_t s1, cuuint64_t s2, cuuint32_t b0, cuuint32_t b1) {
+    cuuint64_t dims[3] = {d0, d1, d2};
+    cuuint64_t strides[2] = {s1 * 4, s2 * 4};
+    cuuint32_t box[3] = {b0, b1, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 }  // namespace
 
-const char *vtile_name() { return "fused-vtile-128x" "8"; }
+const char *vtile_name() { return "fused-vtile-128x8"; }
 
 int vtile_prepare(fdtd_ctx *h) {
     const Grid &g = h->g;
+    const int P = h->P;
     if ((unsigned long long)g.comp >= (1ull << 32) || g.pitch % 4 != 0) return FDTD_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if ((unsigned long long)h->psi_axis[a] >= (1ull << 32)) return FDTD_ERR_ARG;
+    // the x layers must not share a group of four columns; x boxes within the
+    // TMA box extent
+    const int xlo4 = P > 0 ? psi_x_lo4(P) : 0, xhb = P > 0 ? psi_x_hb(g.nx, P) : 0;
+    const int WX = P > 0 ? psi_x_row(g.nx, P) : 0;
+    const int xbw = P > 0 ? (xlo4 > WX - xlo4 ? xlo4 : WX - xlo4) : 4;
+    if (P > 0 && (g.nx < 2 * P + 8 || xbw > 256 || g.nz < 2 * P + 2)) return FDTD_ERR_ARG;
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
@@ -328,40 +721,87 @@ int vtile_prepare(fdtd_ctx *h) {
     EncodeTiled encode = reinterpret_cast<EncodeTiled>(fn);
     HostState *st = new (std::nothrow) HostState();
     if (!st) return FDTD_ERR_OOM;
-    cuuint64_t dims[3] = {(cuuint64_t)g.nx + 1, (cuuint64_t)g.ny + 1, (cuuint64_t)g.nz + 1};
-    cuuint64_t strides[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4};
-    cuuint32_t box[3] = {BXC, BYR, 1};
-    cuuint32_t estr[3] = {1, 1, 1};
+    st->xlo4 = xlo4;
+    st->xhb = xhb;
+    st->xbw = xbw;
+    bool ok = true;
     for (int s = 0; s < 2; ++s)
         for (int c = 0; c < 6; ++c)
-            if (encode(&st->maps.m[s][c], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->fields[s] + (size_t)c * g.comp, dims,
-                       strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
-                delete st;
-                return FDTD_ERR_CUDA;
-            }
-    if (cudaFuncSetAttribute(k_vtile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES) != cudaSuccess) {
+            ok = ok && encode3(encode, &st->maps.f[s][c], h->fields[s] + (size_t)c * g.comp, g.nx + 1, g.ny + 1,
+                               g.nz + 1, g.pitch, g.plane, BXC, BYR);
+    if (P > 0) {
+        // psi block: E psi, then H psi set 0, then H psi set 1 (each set the
+        // x, y, z arrays in turn, two per axis); the H set read when cur == s
+        // is set s
+        const size_t set = 2 * (h->psi_axis[0] + h->psi_axis[1] + h->psi_axis[2]);
+        const int W = 2 * P + 1;
+        for (int s = 0; s < 2; ++s) {
+            size_t off = 0;
+            for (int axis = 0; axis < 3; ++axis)
+                for (int t = 0; t < 2; ++t) {
+                    const float *hp = h->psi_block + set * (1 + s) + off;   // H array t of axis
+                    const float *ep = h->psi_block + off;                   // E array t of axis
+                    off += h->psi_axis[axis];
+                    for (int half = 0; half < 2; ++half) {
+                        const float *base = half == 0 ? hp : ep;
+                        const int a = 2 * half + t;
+                        if (half == 1 && s == 1) continue;   // E maps: one copy
+                        CUtensorMap *m = axis == 0 ? &st->maps.x[a][s] : axis == 1 ? &st->maps.y[a][s] : &st->maps.z[a][s];
+                        if (axis == 0)
+                            ok = ok && encode3(encode, m, base, WX, g.ny, g.nz, WX, (cuuint64_t)g.ny * WX, xbw, PR);
+                        else if (axis == 1)
+                            ok = ok && encode3(encode, m, base, g.nx, W, g.nz, g.pitch, (cuuint64_t)W * g.pitch, PW, PR);
+                        else
+                            ok = ok && encode3(encode, m, base, g.nx, g.ny, W, g.pitch, (cuuint64_t)g.ny * g.pitch, PW, PR);
+                    }
+                }
+        }
+    }
+    if (!ok) {
+        delete st;
+        return FDTD_ERR_CUDA;
+    }
+    st->tiles_x = (g.nx + TXC - 1) / TXC;
+    st->tiles_y = (g.ny + BY - 1) / BY;
+    // z chunks: the layers [0, P] and [nz-P, nz) as chunks of their own, the
+    // planes between them in m chunks of cm.  With one block per SM, the
+    // middle blocks run in ceil(tiles m / SMs) waves of about cm + 4 plane
+    // times each (warm-up plane and pipeline fill); m minimises that, chunks
+    // of at least 16 planes.  More chunks where the coefficient table of a
+    // long chunk leaves the ring too small for two of the largest stages.
+    st->za = P > 0 ? P + 1 : 0;
+    st->zb = P > 0 ? g.nz - P : g.nz;
+    const int mid = st->zb - st->za;
+    const long long sms = h->num_sms > 0 ? h->num_sms : 1;
+    const long long tiles = (long long)st->tiles_x * st->tiles_y;
+    long long m = 1, best = -1;
+    for (long long mm = 1; mm <= (mid / 16 > 1 ? mid / 16 : 1); ++mm) {
+        const long long cm = (mid + mm - 1) / mm;
+        const long long cost = (tiles * mm + sms - 1) / sms * (cm + 4);
+        if (best < 0 || cost < best) { best = cost; m = mm; }
+    }
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
+    const long long xb = (xbw * PR + 31) / 32 * 32;
+    const long long big = FIELDS + 8 * xb + 8LL * PBOXP;   // largest stage: two x boxes, y and z
+    long long ring = 0;
+    for (;;) {
+        st->cm = (int)((mid + m - 1) / m);
+        st->zc = (st->cm > st->za ? st->cm : st->za) + 1;
+        ring = (long long)max_smem / 4 - BAR_BYTES / 4 - head_floats(st->zc);
+        if (ring >= 2 * big || st->cm <= 1) break;
+        ++m;
+    }
+    st->m = (mid + st->cm - 1) / st->cm;
+    st->chunks = (st->za > 0 ? 1 : 0) + st->m + (st->zb < g.nz ? 1 : 0);
+    st->ring = (int)ring;
+    st->smem = BAR_BYTES + 4 * (size_t)(head_floats(st->zc) + st->ring);
+    if (ring < 2 * big ||
+        cudaFuncSetAttribute(k_vtile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->smem) != cudaSuccess) {
         cudaGetLastError();
         delete st;
         return FDTD_ERR_CUDA;
     }
-    int lo[3], hi[3];
-    interior_box(h, lo, hi);
-    Args &a = st->proto;
-    a.ilo = lo[0]; a.ihi = hi[0]; a.jlo = lo[1]; a.jhi = hi[1]; a.klo = lo[2]; a.khi = hi[2];
-    if (a.ihi < a.ilo || a.jhi < a.jlo || a.khi < a.klo) { delete st; return FDTD_ERR_ARG; }
-    a.tx0 = a.ilo / TXC;
-    a.tiles_x = a.ihi / TXC - a.tx0 + 1;
-    a.tiles_y = (a.jhi - a.jlo + BY) / BY;
-    const int ez = a.khi - a.klo + 1;
-    const int sms = h->num_sms > 0 ? h->num_sms : 1;
-    const long long want = 8LL * sms;
-    long long chunks = (want + (long long)a.tiles_x * a.tiles_y - 1) / ((long long)a.tiles_x * a.tiles_y);
-    if (chunks > ez / 16) chunks = ez / 16;
-    if (chunks < 1) chunks = 1;
-    a.chunk = (int)((ez + chunks - 1) / chunks);
-    st->chunks = (ez + a.chunk - 1) / a.chunk;
-    st->blocks_x = a.tiles_x * a.tiles_y;
     h->vtile = st;
     return FDTD_OK;
 }
@@ -371,27 +811,34 @@ void vtile_release(fdtd_ctx *h) {
     h->vtile = nullptr;
 }
 
-long long vtile_cells(const fdtd_ctx *h) {
-    const Args &a = static_cast<const HostState *>(h->vtile)->proto;
-    return (long long)(a.ihi - a.ilo + 1) * (a.jhi - a.jlo + 1) * (a.khi - a.klo + 1);
-}
-
 void launch_vtile(fdtd_ctx *h, cudaStream_t s) {
     HostState *st = static_cast<HostState *>(h->vtile);
     const Grid &g = h->g;
-    Args a = st->proto;
+    Args a;
     a.g = g;
     float *out = h->fields[h->cur ^ 1];
     const size_t c = (size_t)g.comp;
     a.oex = out; a.oey = out + c; a.oez = out + 2 * c; a.ohx = out + 3 * c; a.ohy = out + 4 * c; a.ohz = out + 5 * c;
+    a.pml = cpml_view(h);
+    a.tiles_x = st->tiles_x;
+    a.tiles_y = st->tiles_y;
+    a.za = st->za;
+    a.zb = st->zb;
+    a.cm = st->cm;
+    a.m = st->m;
+    a.zc = st->zc;
+    a.ring = st->ring;
+    a.xlo4 = st->xlo4;
+    a.xhb = st->xhb;
+    a.xbw = st->xbw;
     a.cur = h->cur;
     a.src = h->src;
     a.ss = source_window(h->src, h->steps);
     a.kE = (float)h->kE;
     a.kH = (float)h->kH;
     a.flags = h->d_flags;
-    dim3 grid(st->blocks_x, st->chunks);
-    k_vtile<<<grid, NT, SMEM_BYTES, s>>>(a, st->maps);
+    dim3 grid(st->tiles_x * st->tiles_y, st->chunks);
+    k_vtile<<<grid, NT, st->smem, s>>>(a, st->maps);
 }
 
 }  // namespace fdtd

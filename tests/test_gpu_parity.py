@@ -145,6 +145,10 @@ def _custom(nx, ny, nz, boundary, npml, v_frac=1.0, L=2, steps=80, seed=0):
     ((33, 9, 41), oracle.MUR1, 0, 1.0),
     ((29, 31, 37), oracle.CPML, 5, 1.0),
     ((70, 66, 45), oracle.CPML, 8, 2.2),
+    # several 128-column tiles: a tile edge inside the x+ layer, a partial
+    # group of four columns at x+
+    ((136, 30, 30), oracle.CPML, 10, 1.0),
+    ((262, 26, 28), oracle.CPML, 6, 1.0),
 ])
 def test_ragged_grids(fd, kernel, dims, boundary, npml, v_frac):
     w = _custom(*dims, boundary, npml, v_frac, L=2 if min(dims[:2]) > 2 * npml + 7 else 1)
