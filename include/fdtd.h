@@ -153,6 +153,41 @@ int fdtd_reset(fdtd_t h);
 int fdtd_energy(fdtd_t h, double *energy);
 
 /*
+ * The paper has no counterpart to this call: it is a diagnostic of the
+ * scheme, the same energy and stability check as fdtd_energy, for six field
+ * arrays that the caller owns on the device, with no handle and no device
+ * memory allocated by the call.  It serves callers that cannot allocate: one
+ * whose device memory is already taken by its own field arrays (a handle
+ * would add two full field sets), or one that must not allocate while it runs
+ * because an allocator or a memory budget outside this library owns the rest
+ * of the device.
+ *
+ * d_fields: device pointer to Ex, Ey, Ez, Hx, Hy, Hz back to back, each
+ *   (nz+1)(ny+1)(nx+1) float32 in the node layout of fdtd_fields (x fastest);
+ *   entries a component does not use should be zero (as fdtd_fields writes).
+ * nx, ny, nz >= 1 cells; dx > 0 metres; eps_r > 0.
+ * nblocks: partial sums of the first pass, 1 .. FDTD_ENERGY_SCRATCH_BLOCKS,
+ *   or 0 for four per SM (capped at that maximum); a larger value returns
+ *   FDTD_ERR_CAPACITY.
+ * stream: cudaStream_t to run on (NULL: the default stream); the call
+ *   synchronises it.
+ * energy: host out, W = 1/2 eps sum |E|^2 dx^3 + 1/2 mu0 sum |H|^2 dx^3.
+ * Returns FDTD_ERR_UNSTABLE (energy still written) if a value is not finite,
+ * FDTD_ERR_ARG on a null pointer or bad size, FDTD_ERR_CUDA on a CUDA error.
+ *
+ * Scratch: a fixed array of 3 FDTD_ENERGY_SCRATCH_BLOCKS + 3 doubles (24.6 KB)
+ * compiled into the library.  Every slot a call reads is written earlier in
+ * the same call, so nothing has to start at zero.  All calls on a device share
+ * it: calls that overlap in time (other threads, other streams) race and must
+ * be serialised by the caller.  The first call on a device (with that device
+ * current) looks the array up (cudaGetSymbolAddress, which may load the
+ * module); make that first call before any stream capture begins.
+ */
+#define FDTD_ENERGY_SCRATCH_BLOCKS 1024
+int fdtd_energy_noalloc(const float *d_fields, int nx, int ny, int nz, double dx, double eps_r,
+                        int nblocks, void *stream, double *energy);
+
+/*
  * Checkpoint: the full state (fields, CPML memory, step counter, traces) as an
  * opaque host blob.  With buf == NULL, *bytes receives the size needed.
  * Loading into a handle created with the same grid, boundary and detectors

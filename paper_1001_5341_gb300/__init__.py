@@ -48,6 +48,7 @@ _SIGS = {
     "fdtd_set_field": (_i, [_vp, _i, _vp, _i]),
     "fdtd_reset": (_i, [_vp]),
     "fdtd_energy": (_i, [_vp, _pd]),
+    "fdtd_energy_noalloc": (_i, [_vp, _i, _i, _i, _d, _d, _i, _vp, _pd]),
     "fdtd_save_state": (_i, [_vp, _vp, C.POINTER(_sz)]),
     "fdtd_load_state": (_i, [_vp, _vp, _sz]),
     "fdtd_timing_begin": (_i, [_vp, _i]),
