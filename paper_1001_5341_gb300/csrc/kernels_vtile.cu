@@ -10,11 +10,13 @@
 // A block owns a tile of 128 columns [i0, i0+128) (i0 a multiple of 128) by
 // BY rows and marches up a chunk of z planes.  For every plane of the input
 // set, one thread issues the TMA loads (cp.async.bulk.tensor.3d) of one
-// pipeline stage: one box per field component of 136 columns x (BY+2) rows
-// starting at (i0-4, jb-1) -- the tile plus a one-cell halo on every side,
-// the x origin on a 16-byte boundary; outside the node grid a box reads zeros
-// -- and, where the block touches a CPML layer, boxes of the four psi arrays
-// of that axis (below).  Stages form a ring tracked by mbarriers; a block
+// pipeline stage: one box per field component holding the tile and the halo
+// that component is read at (the x origin on a 16-byte boundary; outside the
+// node grid a box reads zeros) -- Ex: columns i0-4..i0+127, rows jb-1..jb+BY;
+// Ey: i0-4..i0+131, jb-1..jb+BY-1; Ez: i0-4..i0+131, jb-1..jb+BY; Hx:
+// i0..i0+127, jb-1..jb+BY-1; Hy: i0-4..i0+127, jb..jb+BY-1; Hz: i0-4..i0+127,
+// jb-1..jb+BY-1 -- and, where the block touches a CPML layer, boxes of the
+// four psi arrays of that axis (below).  Stages form a ring tracked by mbarriers; a block
 // without CPML work holds up to NSMAX planes in flight, a block with it as
 // many as its larger stages leave room for (at least two).
 //
@@ -65,19 +67,29 @@ namespace {
 #define VT_BY 8
 #endif
 #ifndef VT_NSMAX
-#define VT_NSMAX 6
+#define VT_NSMAX 8
 #endif
 constexpr int BY = VT_BY;              // rows per tile (one warp each)
 constexpr int NSMAX = VT_NSMAX;        // most pipeline stages
 constexpr int NW = BY + 1;             // warps: BY row warps + one halo warp
 constexpr int NT = 32 * NW;
 constexpr int TXC = 128;               // tile columns
-constexpr int BXC = TXC + 8;           // field box columns: i0-4 .. i0+131
-constexpr int BYR = BY + 2;            // field box rows: jb-1 .. jb+BY
-constexpr int BOX = BXC * BYR;         // floats per field box
-constexpr int BOXP = (BOX + 31) / 32 * 32;  // field box stride (128-byte aligned)
-constexpr int FIELDS = 6 * BOXP;       // floats of the field boxes of a stage
-constexpr unsigned FIELD_BYTES = 6u * BOX * 4u;
+constexpr int BXC = TXC + 8;           // H-plane row: columns i0-4 .. i0+131
+// field boxes, component c (Ex Ey Ez Hx Hy Hz): columns from i0-4+fb_cb(c),
+// rows from jb-1+fb_rb(c), fb_w(c) x fb_r(c) (box column bc = column - i0 + 4,
+// box row br = row - jb + 1 in the accessors)
+__host__ __device__ constexpr int fb_cb(int c) { return c == 3 ? 4 : 0; }
+__host__ __device__ constexpr int fb_rb(int c) { return c == 4 ? 1 : 0; }
+__host__ __device__ constexpr int fb_w(int c) { return c == 1 || c == 2 ? TXC + 8 : c == 3 ? TXC : TXC + 4; }
+__host__ __device__ constexpr int fb_r(int c) { return c == 0 || c == 2 ? BY + 2 : c == 4 ? BY : BY + 1; }
+__host__ __device__ constexpr int fb_size(int c) { return (fb_w(c) * fb_r(c) + 31) / 32 * 32; }
+__host__ __device__ constexpr int fb_off(int c) {
+    return (c > 0 ? fb_size(0) : 0) + (c > 1 ? fb_size(1) : 0) + (c > 2 ? fb_size(2) : 0) +
+           (c > 3 ? fb_size(3) : 0) + (c > 4 ? fb_size(4) : 0);
+}
+constexpr int FIELDS = fb_off(5) + fb_size(5);   // floats of the field boxes of a stage
+constexpr unsigned FIELD_BYTES = 4u * (fb_w(0) * fb_r(0) + fb_w(1) * fb_r(1) + fb_w(2) * fb_r(2) +
+                                       fb_w(3) * fb_r(3) + fb_w(4) * fb_r(4) + fb_w(5) * fb_r(5));
 constexpr int PW = TXC + 4;            // y/z psi box columns: i0-4 .. i0+127
 constexpr int PR = BY + 1;             // psi box rows: jb-1 .. jb+BY-1
 constexpr int PBOX = PW * PR;
@@ -91,7 +103,9 @@ constexpr int BAR_BYTES = 128;
 constexpr int CXN = PW;
 constexpr int CY = 4 * CXN;
 constexpr int CZ = CY + 4 * HR;
-static_assert((BXC * 4) % 16 == 0 && (PW * 4) % 16 == 0, "box rows must be a multiple of 16 bytes");
+static_assert((PW * 4) % 16 == 0 && (fb_w(0) * 4) % 16 == 0 && (fb_w(1) * 4) % 16 == 0 &&
+                  (fb_w(3) * 4) % 16 == 0 && (fb_cb(3) * 4) % 16 == 0,
+              "box rows and origins must be multiples of 16 bytes");
 static_assert(NSMAX * 8 <= BAR_BYTES, "barrier area");
 static_assert(BY <= 32, "one halo lane per row");
 
@@ -110,7 +124,7 @@ struct Args {
     float *oex, *oey, *oez, *ohx, *ohy, *ohz;   // output set
     Cpml pml;
     int tiles_x, tiles_y;
-    int za, zb, cm, m;                          // z chunks: [0, za), m of cm planes over [za, zb), [zb, nz)
+    int za, zb, cm, m;                          // z chunks: m of cm planes over [za, zb), then [0, za), [zb, nz)
     int zc;                                     // planes of the coefficient table (longest chunk + 1)
     int ring;                                   // floats available to the stage ring
     int xlo4, xhb, xbw;                         // x psi: high half start, first column of the high
@@ -202,8 +216,13 @@ __device__ __forceinline__ void st4n(float *p, float4 v, int n) {
     }
 }
 
-// field box offset of (box column bc, box row br) for component c
-__device__ __forceinline__ int bo(int c, int br, int bc) { return c * BOXP + br * BXC + bc; }
+// stage offset of component c at box row br (row jb-1+br), box column bc
+// (column i0-4+bc)
+template <int C>
+__device__ __forceinline__ int bo(int br, int bc) {
+    constexpr int off = fb_off(C) - fb_rb(C) * fb_w(C) - fb_cb(C), w = fb_w(C);
+    return off + br * w + bc;
+}
 
 // Block geometry and stage layout, fixed for the whole march.
 struct Blk {
@@ -227,7 +246,9 @@ __device__ __forceinline__ void issue_plane(const Args &A, const Maps &M, const 
     if (B.hy) bytes += 4u * PBOX * 4u;
     if (lz >= 0) bytes += 4u * PBOX * 4u;
     mbar_expect_tx(bar, bytes);
-    for (int c = 0; c < 6; ++c) tma_load(st + c * BOXP, &M.f[set][c], bar, B.i0 - 4, B.jb - 1, z);
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+        tma_load(st + fb_off(c), &M.f[set][c], bar, B.i0 - 4 + fb_cb(c), B.jb - 1 + fb_rb(c), z);
     if (B.hx)
         for (int a = 0; a < 4; ++a) {
             float *d = st + B.xo + a * B.nxb * B.xb;
@@ -311,18 +332,18 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
     float4 ex0, ey0, ez0, hxn, hyn, hzn;
     if (L.roww) {
         const int br = L.w + 1;  // box row of j
-        ex0 = lds4(s0 + bo(0, br, bc0));
-        ey0 = lds4(s0 + bo(1, br, bc0));
-        ez0 = lds4(s0 + bo(2, br, bc0));
-        const float4 hx = lds4(s0 + bo(3, br, bc0));
-        const float4 hy = lds4(s0 + bo(4, br, bc0));
-        const float4 hz = lds4(s0 + bo(5, br, bc0));
-        const float4 exU = lds4(s0 + bo(0, br + 1, bc0));  // row j+1
-        const float4 ezU = lds4(s0 + bo(2, br + 1, bc0));
-        const float eyR = s0[bo(1, br, bc0 + 4)];         // column c0+4
-        const float ezR = s0[bo(2, br, bc0 + 4)];
-        const float4 ex1 = lds4(s1 + bo(0, br, bc0));
-        const float4 ey1 = lds4(s1 + bo(1, br, bc0));
+        ex0 = lds4(s0 + bo<0>(br, bc0));
+        ey0 = lds4(s0 + bo<1>(br, bc0));
+        ez0 = lds4(s0 + bo<2>(br, bc0));
+        const float4 hx = lds4(s0 + bo<3>(br, bc0));
+        const float4 hy = lds4(s0 + bo<4>(br, bc0));
+        const float4 hz = lds4(s0 + bo<5>(br, bc0));
+        const float4 exU = lds4(s0 + bo<0>(br + 1, bc0));  // row j+1
+        const float4 ezU = lds4(s0 + bo<2>(br + 1, bc0));
+        const float eyR = s0[bo<1>(br, bc0 + 4)];         // column c0+4
+        const float ezR = s0[bo<2>(br, bc0 + 4)];
+        const float4 ex1 = lds4(s1 + bo<0>(br, bc0));
+        const float4 ey1 = lds4(s1 + bo<1>(br, bc0));
         float4 dyEz = ezU - ez0, dzEy = ey1 - ey0;                                    // Hx
         float4 dzEx = ex1 - ex0, dxEz = make_float4(ez0.y, ez0.z, ez0.w, ezR) - ez0;  // Hy
         float4 dxEy = make_float4(ey0.y, ey0.z, ey0.w, eyR) - ey0, dyEx = exU - ex0;  // Hz
@@ -388,11 +409,11 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
     } else if (own) {
         // halo warp: H at row jb-1 (Hx, Hz) over the tile's columns
         {
-            const float4 ex = lds4(s0 + bo(0, 0, bc0)), ey = lds4(s0 + bo(1, 0, bc0)), ez = lds4(s0 + bo(2, 0, bc0));
-            const float4 hx = lds4(s0 + bo(3, 0, bc0)), hz = lds4(s0 + bo(5, 0, bc0));
-            const float4 exU = lds4(s0 + bo(0, 1, bc0)), ezU = lds4(s0 + bo(2, 1, bc0));
-            const float4 ey1 = lds4(s1 + bo(1, 0, bc0));
-            const float eyR = s0[bo(1, 0, bc0 + 4)];
+            const float4 ex = lds4(s0 + bo<0>(0, bc0)), ey = lds4(s0 + bo<1>(0, bc0)), ez = lds4(s0 + bo<2>(0, bc0));
+            const float4 hx = lds4(s0 + bo<3>(0, bc0)), hz = lds4(s0 + bo<5>(0, bc0));
+            const float4 exU = lds4(s0 + bo<0>(1, bc0)), ezU = lds4(s0 + bo<2>(1, bc0));
+            const float4 ey1 = lds4(s1 + bo<1>(0, bc0));
+            const float eyR = s0[bo<1>(0, bc0 + 4)];
             float4 dyEz = ezU - ez, dzEy = ey1 - ey;
             float4 dxEy = make_float4(ey.y, ey.z, ey.w, eyR) - ey, dyEx = exU - ex;
             if (HYZ && L.ly >= 0) {
@@ -415,10 +436,10 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
         // column i0-1 (box column 3), rows jb .. jb+BY-1 (Hy, Hz)
         if (L.lane < BY) {
             const int b = L.lane + 1;
-            const float ey = s0[bo(1, b, 3)], eyR = s0[bo(1, b, 4)];
-            const float ex = s0[bo(0, b, 3)], exU = s0[bo(0, b + 1, 3)], ex1 = s1[bo(0, b, 3)];
-            const float ez = s0[bo(2, b, 3)], ezR = s0[bo(2, b, 4)];
-            const float hy = s0[bo(4, b, 3)], hz = s0[bo(5, b, 3)];
+            const float ey = s0[bo<1>(b, 3)], eyR = s0[bo<1>(b, 4)];
+            const float ex = s0[bo<0>(b, 3)], exU = s0[bo<0>(b + 1, 3)], ex1 = s1[bo<0>(b, 3)];
+            const float ez = s0[bo<2>(b, 3)], ezR = s0[bo<2>(b, 4)];
+            const float hy = s0[bo<4>(b, 3)], hz = s0[bo<5>(b, 3)];
             float dzEx = ex1 - ex, dxEz = ezR - ez, dxEy = eyR - ey, dyEx = exU - ex;
             if (L.cin) {
                 if (HYZ && lz >= 0) {
@@ -552,13 +573,16 @@ __global__ void __launch_bounds__(NT, 1) k_vtile(const Args A, const __grid_cons
     B.i0 = tx * TXC;
     B.jb = ty * BY;
     {
-        const int c = (int)blockIdx.y, nfirst = A.za > 0 ? 1 : 0;
-        if (nfirst && c == 0) {
+        // chunk-major launch order: the m middle chunks first, so the tiles
+        // of a chunk start together; the short layer chunks last, where they
+        // fill the SMs of the final wave
+        const int c = (int)blockIdx.y;
+        if (c < A.m) {
+            B.k0 = A.za + c * A.cm;
+            B.k1 = min(A.zb, B.k0 + A.cm);
+        } else if (c == A.m && A.za > 0) {
             B.k0 = 0;
             B.k1 = A.za;
-        } else if (c - nfirst < A.m) {
-            B.k0 = A.za + (c - nfirst) * A.cm;
-            B.k1 = min(A.zb, B.k0 + A.cm);
         } else {
             B.k0 = A.zb;
             B.k1 = g.nz;
@@ -728,7 +752,7 @@ int vtile_prepare(fdtd_ctx *h) {
     for (int s = 0; s < 2; ++s)
         for (int c = 0; c < 6; ++c)
             ok = ok && encode3(encode, &st->maps.f[s][c], h->fields[s] + (size_t)c * g.comp, g.nx + 1, g.ny + 1,
-                               g.nz + 1, g.pitch, g.plane, BXC, BYR);
+                               g.nz + 1, g.pitch, g.plane, fb_w(c), fb_r(c));
     if (P > 0) {
         // psi block: E psi, then H psi set 0, then H psi set 1 (each set the
         // x, y, z arrays in turn, two per axis); the H set read when cur == s
