@@ -25,12 +25,18 @@
 //   H phase: H^{n+1/2}(k) of the own cells from the stages of planes k and k+1
 //     (y neighbour j+1 and x neighbour i+1 are vector reads of the stage);
 //     warp BY computes the halo H the E update needs: row jb-1 (Hx, Hz) and
-//     column i0-1 (Hy, Hz).  All of it goes to a shared H plane; own H is
-//     stored to global memory.
+//     column i0-1 (Hy, Hz).  Hx, Hz of the rows a warp below needs and the
+//     halo go to a shared H plane (two of them, used by alternate planes);
+//     own H is stored to global memory.
 //   barrier
-//   E phase: E^{n+1}(k) from the H plane (neighbours j-1 and i-1) and the
-//     own H^{n+1/2}(k-1) Hx, Hy kept in registers; stored.
-//   barrier; the stage of plane k is refilled with plane k+ns.
+//   E phase: E^{n+1}(k) from the H plane (neighbour j-1), the lane to the
+//     left (neighbour i-1, a warp shuffle) and the own H^{n+1/2}(k-1) Hx, Hy
+//     kept in registers; stored.
+// Each thread waits on the mbarrier of the stages it reads itself, so the
+// barrier in the middle of the plane is the only one a block without CPML
+// boxes needs: after it no thread reads the stage of plane k, which is
+// refilled with plane k+ns at once.  Blocks with CPML boxes read E psi from
+// the stage in the E phase and refill it after a second barrier.
 // A chunk that starts above plane 0 first runs the H phase of plane k0-1
 // without stores.  Every mbarrier wait is bounded; on expiry the block records
 // the failure in a device flag and stops.
@@ -74,7 +80,6 @@ constexpr int NSMAX = VT_NSMAX;        // most pipeline stages
 constexpr int NW = BY + 1;             // warps: BY row warps + one halo warp
 constexpr int NT = 32 * NW;
 constexpr int TXC = 128;               // tile columns
-constexpr int BXC = TXC + 8;           // H-plane row: columns i0-4 .. i0+131
 // field boxes, component c (Ex Ey Ez Hx Hy Hz): columns from i0-4+fb_cb(c),
 // rows from jb-1+fb_rb(c), fb_w(c) x fb_r(c) (box column bc = column - i0 + 4,
 // box row br = row - jb + 1 in the accessors)
@@ -94,8 +99,12 @@ constexpr int PW = TXC + 4;            // y/z psi box columns: i0-4 .. i0+127
 constexpr int PR = BY + 1;             // psi box rows: jb-1 .. jb+BY-1
 constexpr int PBOX = PW * PR;
 constexpr int PBOXP = (PBOX + 31) / 32 * 32;
-constexpr int HR = BY + 1;             // H plane rows: jb-1 .. jb+BY-1
-constexpr int HPL = HR * BXC;          // floats per H-plane component
+constexpr int HR = BY + 1;             // rows jb-1 .. jb+BY-1 (coefficient table)
+// shared H plane (one of two): Hx and Hz of rows jb-1 .. jb+BY-2 (the rows
+// below each row warp), columns i0 .. i0+127; Hz and Hy of column i0-1, rows
+// jb .. jb+BY-1
+constexpr int HS_X = 0, HS_Z = BY * TXC, HS_ZC = 2 * BY * TXC, HS_YC = HS_ZC + BY;
+constexpr int HSB = (HS_YC + BY + 31) / 32 * 32;
 constexpr int BAR_BYTES = 128;
 // CPML coefficient table: aH, bH, aE, bE of the tile's columns i0-4 .. i0+127
 // (CXN each; column c at c - i0 + 4, 16-byte aligned per lane), of its rows
@@ -110,7 +119,7 @@ static_assert(NSMAX * 8 <= BAR_BYTES, "barrier area");
 static_assert(BY <= 32, "one halo lane per row");
 
 // shared memory: barriers, H plane, coefficient table, then the stage ring
-__host__ __device__ constexpr int head_floats(int zc) { return (3 * HPL + CZ + 4 * zc + 31) / 32 * 32; }
+__host__ __device__ constexpr int head_floats(int zc) { return (2 * HSB + CZ + 4 * zc + 31) / 32 * 32; }
 
 struct Maps {
     CUtensorMap f[2][6];    // fields [set][component]
@@ -302,17 +311,12 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
     const bool own = k >= B.k0;
     const int s0i = rp.s0, s1i = rp.s1;
 
+    // psi in the stage: the E phase reads the stage too
+    constexpr bool STAGE_IN_E = HX || HYZ;
     bool ok = true;
     if (rel == 0) ok = mbar_wait(&bar[0], 0);
     ok = ok && mbar_wait(&bar[s1i], rp.ph1);
-    if (__syncthreads_or(!ok)) {
-        if (tid == 0) {
-            atomicOr(A.flags, 1);
-            for (int r = rel; r < B.nplanes && r < rel + B.ns; ++r) mbar_wait(&bar[r % B.ns], (r / B.ns) & 1);
-        }
-        __syncthreads();
-        return false;
-    }
+    float *H = HS + (rel & 1) * HSB;          // this plane's shared H plane
     const float *s0 = ring + s0i * B.stage;   // plane k
     const float *s1 = ring + s1i * B.stage;   // plane k+1
     const int lzk = slab_cell(k, g.nz, pm.P);
@@ -381,9 +385,10 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
         hyn = axpy(hy, -kH, dzEx - dxEz);
         hzn = axpy(hz, -kH, dxEy - dyEx);
         if (own) {
-            sts4(HS + 0 * HPL + br * BXC + bc0, hxn);
-            sts4(HS + 1 * HPL + br * BXC + bc0, hyn);
-            sts4(HS + 2 * HPL + br * BXC + bc0, hzn);
+            if (L.w < BY - 1) {   // the warp above reads this row
+                sts4(H + HS_X + br * TXC + 4 * L.lane, hxn);
+                sts4(H + HS_Z + br * TXC + 4 * L.lane, hzn);
+            }
             if (storable) {
                 const bool f0 = L.c0 == 0, j0 = L.j == 0, k0 = k == 0;
                 st4n(A.ohx + goffk, mask(hxn, false, f0), L.nval);
@@ -430,8 +435,8 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
                 float4 q1 = L.xl ? lds4(PX + XA) : z4;
                 dxEy = cpmlv(q1, lds4(CT + bc0), lds4(CT + CXN + bc0), dxEy);
             }
-            sts4(HS + 0 * HPL + bc0, axpy(hx, -kH, dyEz - dzEy));
-            sts4(HS + 2 * HPL + bc0, axpy(hz, -kH, dxEy - dyEx));
+            sts4(H + HS_X + 4 * L.lane, axpy(hx, -kH, dyEz - dzEy));
+            sts4(H + HS_Z + 4 * L.lane, axpy(hz, -kH, dxEy - dyEx));
         }
         // column i0-1 (box column 3), rows jb .. jb+BY-1 (Hy, Hz)
         if (L.lane < BY) {
@@ -457,19 +462,35 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
                     dyEx = cpml1(q, CT[CY + b], CT[CY + HR + b], dyEx);
                 }
             }
-            HS[1 * HPL + b * BXC + 3] = hy - kH * (dzEx - dxEz);
-            HS[2 * HPL + b * BXC + 3] = hz - kH * (dxEy - dyEx);
+            H[HS_YC + b - 1] = hy - kH * (dzEx - dxEz);
+            H[HS_ZC + b - 1] = hz - kH * (dxEy - dyEx);
         }
     }
-    __syncthreads();
+    if (__syncthreads_or(!ok)) {
+        // a wait expired: record it, let the copies in flight land, stop
+        if (tid == 0) {
+            atomicOr(A.flags, 1);
+            for (int r = rel; r < B.nplanes && r < rel + B.ns; ++r) mbar_wait(&bar[r % B.ns], (r / B.ns) & 1);
+        }
+        __syncthreads();
+        return false;
+    }
+    if (!STAGE_IN_E && tid == 0 && rel + B.ns < B.nplanes) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue_plane(A, M, B, ring + s0i * B.stage, &bar[s0i], rel + B.ns);
+    }
 
     // ---- E phase ----
     if (L.roww && own) {
         const int br = L.w + 1;
-        const float4 hzD = lds4(HS + 2 * HPL + (br - 1) * BXC + bc0);   // row j-1
-        const float4 hxD = lds4(HS + 0 * HPL + (br - 1) * BXC + bc0);
-        const float hzL = HS[2 * HPL + br * BXC + bc0 - 1];             // column c0-1
-        const float hyL = HS[1 * HPL + br * BXC + bc0 - 1];
+        const float4 hzD = lds4(H + HS_Z + L.w * TXC + 4 * L.lane);   // row j-1
+        const float4 hxD = lds4(H + HS_X + L.w * TXC + 4 * L.lane);
+        float hzL = __shfl_up_sync(0xffffffffu, hzn.w, 1);           // column c0-1
+        float hyL = __shfl_up_sync(0xffffffffu, hyn.w, 1);
+        if (L.lane == 0) {
+            hzL = H[HS_ZC + L.w];
+            hyL = H[HS_YC + L.w];
+        }
         float4 dyHz = hzn - hzD, dzHy = hyn - hyp;                                       // Ex
         float4 dzHx = hxn - hxp, dxHz = hzn - make_float4(hzL, hzn.x, hzn.y, hzn.z);     // Ey
         float4 dxHy = hyn - make_float4(hyL, hyn.x, hyn.y, hyn.z), dyHx = hxn - hxD;     // Ez
@@ -527,10 +548,12 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
         }
     }
     if (L.roww) { hxp = hxn; hyp = hyn; }
-    __syncthreads();  // stage of plane k and the H plane are free
-    if (tid == 0 && rel + B.ns < B.nplanes) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue_plane(A, M, B, ring + s0i * B.stage, &bar[s0i], rel + B.ns);
+    if (STAGE_IN_E) {
+        __syncthreads();  // the E psi of plane k are read: its stage is free
+        if (tid == 0 && rel + B.ns < B.nplanes) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue_plane(A, M, B, ring + s0i * B.stage, &bar[s0i], rel + B.ns);
+        }
     }
     rp.s0 = s1i;
     rp.s1 = s1i + 1;
@@ -560,8 +583,8 @@ __device__ __forceinline__ void march(const Args &A, const Maps &M, const Lane &
 __global__ void __launch_bounds__(NT, 1) k_vtile(const Args A, const __grid_constant__ Maps M) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
-    float *HS = reinterpret_cast<float *>(smem_raw + BAR_BYTES);  // [3][HR][BXC]: Hx, Hy, Hz of plane k
-    float *CT = HS + 3 * HPL;                                     // CPML coefficient table
+    float *HS = reinterpret_cast<float *>(smem_raw + BAR_BYTES);  // two shared H planes
+    float *CT = HS + 2 * HSB;                                     // CPML coefficient table
     float *ring = HS + head_floats(A.zc);                         // stage ring
 
     const Grid &g = A.g;
