@@ -63,6 +63,23 @@ _SIGS = {
     "fdtd_profile_gaisser_hillas": (_i, [_d, _d, _i, _i, _pd, _pd, _pd, _pd, _d, _pd]),
     "fdtd_lateral_gaussian": (_i, [_i, _d, _pd]),
     "fdtd_lateral_nkg": (_i, [_i, _d, _d, _d, _i, _d, _pd]),
+    # learned surrogate kernels (surrogate.h); pointers are device addresses
+    "sur_gemm_bf16": (_i, [_vp, _i, _i, _vp, _i, _i, _vp, _i, _vp, _i, _i, _i, _vp, _i, _i, _vp]),
+    "sur_conv1d_fwd": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _vp]),
+    "sur_conv1d_bwd": (_i, [_vp, _i, _vp, _vp, _vp, _i, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _vp]),
+    "sur_relu_bwd": (_i, [_vp, _vp, _vp, _vp, C.c_longlong, _vp]),
+    "sur_bias_grad": (_i, [_vp, _i, _i, _i, _vp, _vp]),
+    "sur_cast_bf16": (_i, [_vp, _vp, C.c_longlong, _vp]),
+    "sur_concat_bf16": (_i, [_vp, _i, _vp, _i, _vp, _i, _vp]),
+    "sur_mse": (_i, [_vp, _vp, C.c_longlong, _vp, _vp, _vp]),
+    "sur_adam": (_i, [_vp, _vp, _vp, _vp, _vp, C.c_longlong, C.c_float, C.c_float, C.c_float, C.c_float, _i, _vp]),
+    "sur_normalize_rows": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
+    "sur_antenna_features": (_i, [_vp, _i, C.c_float, C.c_float, C.c_float, C.c_float, _vp, _vp]),
+    "sur_scale_rows": (_i, [_vp, _i, _i, _vp, C.c_float, _i, _vp]),
+    "sur_pairs": (_i, [_vp, _i, _i, C.c_float, C.c_float, _vp, _vp]),
+    "sur_assemble": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, C.c_float, C.c_float, C.c_float, _i, _vp, _vp]),
+    "sur_assemble_bwd": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, C.c_float, C.c_float, C.c_float, _i, _vp, _vp,
+                              _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)

@@ -1,5 +1,5 @@
 """C ABI checks that need no GPU: the library loads, exports every function
-include/fdtd.h declares, rejects bad arguments on the host before touching the
+include/*.h declares, rejects bad arguments on the host before touching the
 device, and its host-side shower tables agree with the oracle's independent
 ones."""
 import ctypes as C
@@ -30,13 +30,13 @@ def _declared():
         if fn.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", fn)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            names |= set(re.findall(r"\b(fdtd_\w+)\s*\(", txt))
+            names |= set(re.findall(r"\b((?:fdtd|sur)_\w+)\s*\(", txt))
     return names
 
 
 def test_every_declared_symbol_is_exported(fd):
     names = _declared()
-    assert len(names) >= 25
+    assert len(names) >= 40
     lib = C.CDLL(fd.LIB_PATH)
     missing = [n for n in sorted(names) if not hasattr(lib, n)]
     assert not missing, missing

@@ -1,0 +1,234 @@
+"""GPU parity of the surrogate kernels (surrogate.h) with the FP64 CPU
+reference (oracle/surrogate_ref.py): the tensor-core GEMM in all operand
+layouts, the convolutions, the input kernels, Adam, and one full forward +
+backward pass of the network; then a short training run on FDTD traces."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import surrogate_ref as R
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1001_5341_gb300 as fd
+    from paper_1001_5341_gb300 import surrogate as S
+    return torch, fd, S
+
+
+def _p(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _dev(torch, a, dt=None):
+    return torch.tensor(np.asarray(a), dtype=dt or torch.float32, device="cuda")
+
+
+def _host(t):
+    import torch
+    return t.detach().to(torch.float64).cpu().numpy()
+
+
+@pytest.mark.parametrize("ak,bk", [(1, 1), (1, 0), (0, 1), (0, 0)])
+@pytest.mark.parametrize("M,N,K", [(70, 50, 40), (129, 200, 2112), (4, 1024, 1024)])
+def test_gemm_all_layouts(env, ak, bk, M, N, K):
+    torch, fd, S = env
+    rng = np.random.default_rng(M + N + K + 2 * ak + bk)
+    a = R.bf16(rng.normal(size=(M, K)))
+    b = R.bf16(rng.normal(size=(N, K)))
+    bias = rng.normal(size=N)
+    ref = np.maximum(a @ b.T + bias, 0.0)
+    A = _dev(torch, a if ak else a.T.copy(), torch.bfloat16)
+    Bm = _dev(torch, b if bk else b.T.copy(), torch.bfloat16)
+    ldy = N + 3
+    Y = torch.zeros(M, ldy, dtype=torch.float32, device="cuda")
+    Yb = torch.zeros(M, ldy, dtype=torch.bfloat16, device="cuda")
+    rc = fd.sur_gemm_bf16(_p(A), K if ak else M, ak, _p(Bm), K if bk else N, bk, _p(Y), ldy, _p(Yb), M, N, K,
+                          _p(_dev(torch, bias)), 1, 0, None)
+    assert rc == 0
+    torch.cuda.synchronize()
+    y = _host(Y)[:, :N]
+    assert np.abs(y - ref).max() <= 2e-5 * np.abs(ref).max()
+    assert np.all(_host(Y)[:, N:] == 0)
+    assert np.array_equal(_host(Yb)[:, :N], R.bf16(y))
+    # accumulate: Y += A B^T (no bias, no relu)
+    rc = fd.sur_gemm_bf16(_p(A), K if ak else M, ak, _p(Bm), K if bk else N, bk, _p(Y), ldy, None, M, N, K,
+                          None, 0, 1, None)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert np.abs(_host(Y)[:, :N] - (y + a @ b.T)).max() <= 4e-5 * np.abs(ref).max()
+
+
+def test_gemm_rejects_bad_sizes(env):
+    torch, fd, S = env
+    x = torch.zeros(16, dtype=torch.bfloat16, device="cuda")
+    y = torch.zeros(16, dtype=torch.float32, device="cuda")
+    assert fd.sur_gemm_bf16(_p(x), 4, 1, _p(x), 4, 1, _p(y), 4, None, 4, 4, 0, None, 0, 0, None) == -1
+    assert fd.sur_gemm_bf16(_p(x), 2, 1, _p(x), 4, 1, _p(y), 4, None, 4, 4, 4, None, 0, 0, None) == -1
+    assert fd.sur_gemm_bf16(None, 4, 1, _p(x), 4, 1, _p(y), 4, None, 4, 4, 4, None, 0, 0, None) == -1
+
+
+@pytest.mark.parametrize("cin,cout,lin,k,s,pad", [(1, 32, 128, 5, 1, 2), (32, 64, 128, 5, 2, 2), (3, 5, 19, 5, 2, 2)])
+def test_conv_forward_and_backward(env, cin, cout, lin, k, s, pad):
+    torch, fd, S = env
+    rng = np.random.default_rng(cin * 7 + cout)
+    B = 5
+    x = rng.normal(size=(B, cin, lin)).astype(np.float32).astype(np.float64)
+    w = R.bf16(rng.normal(size=(cout, cin, k)) * 0.3)
+    b = rng.normal(size=cout).astype(np.float32).astype(np.float64)
+    lout = R.conv_out_len(lin, k, s, pad)
+    y_ref = np.maximum(R.conv1d(x, w, b, s, pad), 0.0)
+    X, Wt, Bt = _dev(torch, x), _dev(torch, w, torch.bfloat16), _dev(torch, b)
+    Y = torch.empty(B, cout, lout, dtype=torch.float32, device="cuda")
+    assert fd.sur_conv1d_fwd(_p(X), cin * lin, _p(Wt), _p(Bt), _p(Y), B, cin, lin, cout, k, s, pad, 1, None) == 0
+    torch.cuda.synchronize()
+    assert np.abs(_host(Y) - y_ref).max() <= 1e-5 * np.abs(y_ref).max()
+    dy = rng.normal(size=(B, cout, lout)).astype(np.float32).astype(np.float64)
+    dz = dy * (_host(Y) > 0)
+    dx_ref, dw_ref, db_ref = R.conv1d_grads(x, w, dz, s, pad)
+    DX = torch.empty(B, cin, lin, dtype=torch.float32, device="cuda")
+    DW = torch.empty(cout, cin, k, dtype=torch.float32, device="cuda")
+    DB = torch.empty(cout, dtype=torch.float32, device="cuda")
+    assert fd.sur_conv1d_bwd(_p(X), cin * lin, _p(Wt), _p(Y), _p(_dev(torch, dy)), cout * lout, _p(DX), _p(DW),
+                             _p(DB), B, cin, lin, cout, k, s, pad, None) == 0
+    torch.cuda.synchronize()
+    for got, ref in ((DX, dx_ref), (DW, dw_ref), (DB, db_ref)):
+        assert np.abs(_host(got) - ref).max() <= 1e-4 * max(np.abs(ref).max(), 1e-6)
+
+
+def test_input_kernels_and_adam(env):
+    torch, fd, S = env
+    rng = np.random.default_rng(5)
+    B = 37
+    q = -rng.uniform(0, 3, size=(B, 128))
+    q[3] = 0.0
+    qn_ref, s_ref = R.normalize_rows(q)
+    Q = _dev(torch, q)
+    QN = torch.empty(B, 128, dtype=torch.float32, device="cuda")
+    Sv = torch.empty(B, dtype=torch.float32, device="cuda")
+    assert fd.sur_normalize_rows(_p(Q), B, 128, _p(QN), _p(Sv), None) == 0
+    rz = rng.uniform([0.3, 0.5], [0.9, 9.5], size=(B, 2))
+    F = torch.empty(B, 64, dtype=torch.float32, device="cuda")
+    assert fd.sur_antenna_features(_p(_dev(torch, rz)), B, *S.Geometry().feat, _p(F), None) == 0
+    Y = _dev(torch, rng.normal(size=(B, 10)))
+    y0 = _host(Y)
+    assert fd.sur_scale_rows(_p(Y), B, 10, _p(Sv), 2.0, 0, None) == 0
+    torch.cuda.synchronize()
+    assert np.allclose(_host(QN), qn_ref, rtol=1e-6, atol=1e-7)
+    assert np.allclose(_host(Sv), s_ref, rtol=1e-6)
+    assert np.abs(_host(F) - R.antenna_features(rz, *S.Geometry().feat)).max() < 2e-5
+    assert np.allclose(_host(Y), y0 * 2.0 * s_ref[:, None], rtol=1e-6, atol=1e-7)
+    assert fd.sur_scale_rows(_p(Y), B, 10, _p(Sv), 0.5, 1, None) == 0
+    torch.cuda.synchronize()
+    assert np.allclose(_host(Y), np.where(s_ref[:, None] > 0, y0, 0.0), rtol=1e-5, atol=1e-6)
+    # Adam, three steps
+    n = 1000
+    w, g = rng.normal(size=n), rng.normal(size=(3, n))
+    Wt, Wb = _dev(torch, w), torch.empty(n, dtype=torch.bfloat16, device="cuda")
+    Mt, Vt = torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
+    m, v, wr = np.zeros(n), np.zeros(n), w.astype(np.float32).astype(np.float64)
+    for t in range(3):
+        assert fd.sur_adam(_p(Wt), _p(Wb), _p(_dev(torch, g[t])), _p(Mt), _p(Vt), n, 1e-2, 0.9, 0.999, 1e-8, t + 1,
+                           None) == 0
+        wr, m, v = R.adam(wr, g[t].astype(np.float32).astype(np.float64), m, v, t + 1, 1e-2)
+    torch.cuda.synchronize()
+    assert np.abs(_host(Wt) - wr).max() < 1e-5
+    assert np.array_equal(_host(Wb), R.bf16(_host(Wt)))
+
+
+def test_pairs_and_assembly(env):
+    torch, fd, S = env
+    rng = np.random.default_rng(8)
+    B, K, Tg, T = 5, 37, 60, 90
+    g = {"z0": 0.28, "dz": 0.08, "shift": 3, "T": T, "cps": 0.0119, "J0": 5}
+    rz = rng.uniform([0.1, 0.5], [0.5, 3.0], size=(B, 2))
+    RZ = _dev(torch, rz)
+    P = torch.empty(B * K, 2, dtype=torch.float32, device="cuda")
+    assert fd.sur_pairs(_p(RZ), B, K, g["z0"], g["dz"], _p(P), None) == 0
+    G = rng.normal(size=(B * K, Tg))
+    qn = rng.normal(size=(B, K))
+    Y = torch.empty(B, T, dtype=torch.float32, device="cuda")
+    assert fd.sur_assemble(_p(_dev(torch, G)), _p(_dev(torch, qn)), _p(RZ), B, K, Tg, g["shift"], T, g["z0"],
+                           g["dz"], g["cps"], g["J0"], _p(Y), None) == 0
+    d = rng.normal(size=(B, T))
+    DG = torch.empty(B * K, Tg, dtype=torch.float32, device="cuda")
+    DGb = torch.empty(B * K, Tg, dtype=torch.bfloat16, device="cuda")
+    assert fd.sur_assemble_bwd(_p(_dev(torch, d)), _p(_dev(torch, qn)), _p(RZ), B, K, Tg, g["shift"], T, g["z0"],
+                               g["dz"], g["cps"], g["J0"], _p(DG), _p(DGb), None) == 0
+    torch.cuda.synchronize()
+    rz32 = rz.astype(np.float32).astype(np.float64)
+    assert np.abs(_host(P) - R.pairs(rz32, K, g["z0"], g["dz"])).max() < 2e-6
+    y_ref = R.assemble(G, qn, rz32, g)
+    assert np.linalg.norm(_host(Y) - y_ref) <= 1e-4 * np.linalg.norm(y_ref)
+    dg_ref = R.assemble_grad(d, qn, rz32, g, Tg)
+    assert np.linalg.norm(_host(DG) - dg_ref) <= 1e-4 * np.linalg.norm(dg_ref)
+    assert np.array_equal(_host(DGb), R.bf16(_host(DG)))
+
+
+def test_network_step_matches_reference(env):
+    """One forward + backward pass of the whole network, GPU kernels against
+    the CPU reference with the same bf16 weights and rounding points."""
+    torch, fd, S = env
+    rng = np.random.default_rng(6)
+    geo = S.Geometry(K=40, z0=0.28, dz=0.0822, shift=4, T=160, Tg=160, cps=0.0119, J0=8)
+    net = S.Net(geo, hidden=256, seed=11)
+    for k in net.p:   # non-zero biases so every term is exercised
+        if k.endswith("b"):
+            net.p[k].copy_(_dev(torch, rng.normal(scale=0.05, size=tuple(net.p[k].shape))))
+    B = 6
+    q = -rng.uniform(0, 1, size=(B, geo.K)) * 1e-9
+    rz = rng.uniform([0.3, 0.5], [0.9, 3.5], size=(B, 2))
+    tgt = rng.normal(size=(B, geo.T))
+    y = net.forward(_dev(torch, q), _dev(torch, rz), scale_out=False)
+    net._workspace(B)["tn"].copy_(_dev(torch, tgt))
+    net.backward(B)
+    torch.cuda.synchronize()
+    p = {k: (_host(net.pb[k]) if k in net.pb else _host(net.p[k])) for k in net.p}
+    qn, _ = R.normalize_rows(q.astype(np.float32).astype(np.float64))
+    gd = {"z0": geo.z0, "dz": geo.dz, "shift": geo.shift, "T": geo.T, "cps": geo.cps, "J0": geo.J0,
+          "feat": geo.feat}
+    y_ref, cache = R.forward(p, qn, rz.astype(np.float32).astype(np.float64), gd)
+    g_ref = R.backward(p, cache, R.mse(y_ref, tgt.astype(np.float32).astype(np.float64))[1])
+
+    def rel(a, b):
+        return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+    assert rel(_host(y), y_ref) < 1e-3
+    for k in g_ref:
+        assert rel(_host(net.g[k]), g_ref[k]) < 5e-3, k
+
+
+def test_training_on_fdtd_traces_beats_the_mean_trace(env):
+    """A short run of the whole pipeline: FDTD traces of a small grid (48
+    showers, 32 antennas each), 3000 optimiser steps, and traces of 8
+    held-out showers predicted far better than by the training set's mean
+    normalised trace (the best a fixed template does without the network)."""
+    torch, fd, S = env
+    grid = W.surrogate_grid(nx=64, ny=64, nz=256, steps=640, n_bins=56)
+    runs = W.surrogate_runs(seed=21, n_runs=48, n_probes=32, grid=grid, r_range=(0.15, 0.4),
+                            z_range=(0.4, 4.6), z1_range=(0.2, 1.0), len_range=(0.5, 1.8))
+    data = S.generate(grid, runs, decim=1)
+    geo = S.Geometry.of(grid, decim=1, m=8, feat=(0.275, 0.125, 0.0, 5.0))
+    N = data.trace.shape[0]
+    assert N == 48 * 32 and data.trace.shape[1] == geo.T == 640
+    ntr = 40 * 32
+    tr = _host(data.trace)
+    s = np.abs(_host(data.q)).max(axis=1)
+    c_out = float(np.sqrt(np.mean((tr[:ntr] / s[:ntr, None]) ** 2)))
+    net = S.Net(geo, hidden=512, seed=3, c_out=c_out)
+    rng = np.random.default_rng(0)
+    for it in range(3000):
+        idx = torch.tensor(rng.choice(ntr, size=32, replace=False), device="cuda")
+        net.train_batch(data.q[idx].contiguous(), data.rz[idx].contiguous(), data.trace[idx].contiguous(),
+                        lr=1e-3 if it < 2000 else 2e-4)
+    pred = _host(net.predict(data.q[ntr:], data.rz[ntr:]))
+    err = S.rel_l2(pred, tr[ntr:])
+    mean_tmpl = np.mean(tr[:ntr] / s[:ntr, None], axis=0)
+    err_mean = S.rel_l2(mean_tmpl[None, :] * s[ntr:, None], tr[ntr:])
+    assert np.median(err) < 0.6 * np.median(err_mean), (np.median(err), np.median(err_mean))

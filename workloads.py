@@ -229,5 +229,46 @@ def gh_small(seed: int = 3003, nx: int = 60, ny: int = 52, nz: int = 160, npml: 
     return w
 
 
+def surrogate_grid(nx: int = 128, ny: int = 128, nz: int = 512, npml: int = 10, steps: int = 2048,
+                   n_bins: int = 128, m_steps: int = 8) -> Workload:
+    """The grid of the surrogate's training runs: 128x128x512 cells, dx = 2 cm,
+    10-cell CPML, 2048 steps; the profile is a 128-bin table from z0 =
+    (npml + 4) dx whose bins are the distance the shower (v = c) covers in
+    m_steps steps (8: 8.22 cm, 10.5 m in all); NKG lateral spread.  Shower and
+    detectors are set per run (surrogate_runs)."""
+    dx = 0.02
+    dt = courant_dt(dx, EPS_R_ICE)
+    bin_dz = m_steps * C0 * dt
+    L = int(math.ceil(3.0 * R_MOLIERE_M / dx))
+    return Workload(
+        name=f"surrogate{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, dx=dx, dt=dt, eps_r=EPS_R_ICE,
+        boundary=CPML, npml=npml, steps=steps,
+        profile={"kind": "gh", "frac": CHARGE_EXCESS},
+        lateral={"kind": "nkg", "L": L, "r_moliere": R_MOLIERE_M, "age": 1.0, "nsub": 4,
+                 "r_cut": 3.0 * R_MOLIERE_M},
+        z0=(npml + 4) * dx, bin_dz=bin_dz, n_bins=n_bins, v=C0, probes_xyz=np.zeros((0, 3)))
+
+
+def surrogate_runs(seed: int, n_runs: int, n_probes: int = 64, grid: Optional[Workload] = None,
+                   r_range=(0.3, 0.9), z_range=(0.5, 9.5), z1_range=(0.4, 2.0), len_range=(1.0, 3.5)) -> list:
+    """Seeded draws of the surrogate's training runs: per run one Gaisser-Hillas
+    shower (start z1 ~ z0 + U[z1_range] m, z_max - z1 ~ U[len_range] m,
+    lambda ~ U[0.25, 0.6] m, N_max ~ 10^U[8, 9]) and n_probes detectors at
+    r ~ U[r_range], z ~ U[z_range] (metres), phi ~ U[0, 2 pi) about the axis."""
+    g = grid if grid is not None else surrogate_grid()
+    rng = np.random.default_rng(seed)
+    box = _interior(g.nx, g.ny, g.nz, g.npml)
+    axis = ((g.nx // 2) * g.dx, (g.ny // 2) * g.dx)
+    runs = []
+    for _ in range(n_runs):
+        z1 = g.z0 + rng.uniform(*z1_range)
+        zmax = z1 + rng.uniform(*len_range)
+        lam = rng.uniform(0.25, 0.6)
+        nmax = 10.0 ** rng.uniform(8.0, 9.0)
+        probes = _probes_cylindrical(rng, n_probes, axis, r_range[0], r_range[1], z_range[0], z_range[1], g.dx, box)
+        runs.append({"z1": [z1], "zmax": [zmax], "lam": [lam], "nmax": [nmax], "probes_xyz": probes})
+    return runs
+
+
 WORKLOADS = {"parity96": parity96, "greisen384": greisen384, "gh640": gh640,
-             "greisen_small": greisen_small, "gh_small": gh_small}
+             "greisen_small": greisen_small, "gh_small": gh_small, "surrogate_grid": surrogate_grid}
