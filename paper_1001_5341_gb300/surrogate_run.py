@@ -40,6 +40,7 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--hidden", type=int, default=512)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--zs", type=float, default=10.5, help="axial-offset feature scale (metres)")
     ap.add_argument("--out", default="")
     args = ap.parse_args(argv)
 
@@ -53,7 +54,7 @@ def main(argv=None):
     decim = 1
     train = S.generate(grid, W.surrogate_runs(seed=5000, n_runs=args.train_runs, n_probes=args.probes), decim, log)
     test = S.generate(grid, W.surrogate_runs(seed=9000, n_runs=args.test_runs, n_probes=args.probes), decim, log)
-    geo = S.Geometry.of(grid, decim=decim, m=8)
+    geo = S.Geometry.of(grid, decim=decim, m=8, feat=(0.6, 0.3, 0.0, args.zs))
     fdtd_run_s = (train.fdtd_s + test.fdtd_s) / (args.train_runs + args.test_runs)
     fdtd_pps = args.probes / fdtd_run_s
 
@@ -126,7 +127,7 @@ def main(argv=None):
         "what": "learned surrogate (learned bin response in retarded time, summed over the profile) vs FDTD",
         "grid": grid.describe(), "train_showers": args.train_runs, "test_showers": args.test_runs,
         "antennas_per_run": args.probes, "trace_samples": ref.shape[1], "params_per_net": nets[0].n_params,
-        "hidden": args.hidden, "optimizer_steps": args.steps, "batch": args.batch,
+        "hidden": args.hidden, "optimizer_steps": args.steps, "batch": args.batch, "feature_zs": args.zs,
         "train_seconds_two_nets": round(t_train, 1),
         "fdtd_seconds_per_run": round(fdtd_run_s, 4), "fdtd_pulses_per_s": round(fdtd_pps, 1),
         "surrogate_pulses_per_s_batch4096": round(sur_pps, 1), "surrogate_vs_fdtd": round(sur_pps / fdtd_pps, 1),
