@@ -259,6 +259,111 @@ def run_ours(args):
     return line
 
 
+def run_cyl(args):
+    """The paper's 2D axisymmetric solver on an n x n grid (Table I sizes),
+    n steps by default, 64 detectors, the paper's Gaussian shower."""
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    import paper_1001_5341_gb300 as fd
+
+    n = args.n
+    w = W.cyl_table1(n, seed=4004 + rank)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g = fd.Cylinder(w.nr, w.nz, w.d, w.dt, w.eps_r, w.boundary, stream=stream)
+        if args.cyl_kernel >= 0:
+            g.set_kernel(args.cyl_kernel, args.seg_rows)
+        info = g.kernel_info
+        K = info["steps_per_launch"]
+        steps = args.steps if args.steps else n
+        steps = max(K, steps // K * K)
+        g.set_shower(w.q, w.z0, w.bin_dz, w.v, w.w)
+        g.set_probes(w.probes_rz, args.warmup * K + steps)
+        g.step(args.warmup * K)
+        g.sync()
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.3)
+        l0 = g.launches
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        g.step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        launches = g.launches - l0
+        clk = clocks.stop()
+        g.sync()
+        # end to end with host buffers
+        q, wr, rz = (np.ascontiguousarray(a) for a in (w.q, w.w, w.probes_rz))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.reset()
+        g.set_shower(q, w.z0, w.bin_dz, w.v, wr)
+        g.set_probes(rz, steps)
+        g.step(steps)
+        tr = g.probes()
+        e2e_s = time.perf_counter() - t0
+        g.close()
+    if rank != 0:
+        return None
+    cells = w.cells
+    value = ws * cells * steps / (ms * 1e-3) / 1e9
+    peak, peak_kind = hbm_peak()
+    comp_cells = 3 * cells + w.nr + w.nz                  # E_r, E_z, H_phi
+    bytes_launch = 8.0 * comp_cells if K > 1 else 36.0 * cells / 1.0
+    n_launch = steps // K if K > 1 else steps
+    achieved = bytes_launch * n_launch / (ms * 1e-3) / 1e9
+    kname = {0: "k_cyl_h+k_cyl_e", 1: "k_cyl_wave<4,2>", 2: "k_cyl_wave<8,2>", 3: "k_cyl_wave<4,4>"}[info["kernel"]]
+    fset = 2 * 3 * (w.nr + 1) * ((w.nz + 1 + 16 + 63) // 32 * 32) * 4 / 1e9
+    line = {
+        "metric": "Gcell-updates/s", "value": round(value, 3), "unit": "Gcell/s", "solver": "cyl2d",
+        "n_gpus": ws, "steps": steps, "warmup": args.warmup * K,
+        "ms_per_step": round(ms / steps, 6), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {**w.describe(), "seed": 4004, **info,
+                   "inputs_vs_l2": f"fields {fset:.3f} GB vs 129 MB L2 (no flush: one timed call)"},
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "bytes_per_launch_alg": bytes_launch, "steps_per_launch": K, "traffic": None,
+                     "single_step_equiv_GBps": round(24.0 * value, 1)},
+        "e2e": {"value": round(ws * cells * steps / e2e_s / 1e9, 3), "unit": "Gcell/s",
+                "h2d_bytes_per_step": round((q.nbytes + wr.nbytes + rz.nbytes) / steps, 2),
+                "d2h_bytes_per_step": round(tr.nbytes / steps, 2),
+                "what": "reset + set_shower + set_probes (host tables) + step(n) + probes() to host"},
+        "gpu_launches": launches, "clocks": clk,
+        "paper_table1_t_gpu_s": PAPER_T_GPU.get(n),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cyl_cpu_baseline(w, budget_s=args.cpu_budget)
+    return line
+
+
+# Table I: GTX285 seconds per N^2 run (step count not printed; read as N steps)
+PAPER_T_GPU = {256: 0.040, 512: 0.186, 1024: 1.167, 2048: 8.372, 4096: 67.617, 8192: 681.082}
+
+
+def cyl_cpu_baseline(w, budget_s=15.0):
+    """The 2D FP64 oracle as it stands, on a 1024 x 1024 sample of the same physics."""
+    from oracle import cyl_oracle as CO
+    m = min(1024, w.nr)
+    s = W.cyl_table1(m, extent_m=w.d * m)
+    o = CO.CylOracle(s.nr, s.nz, s.d, s.dt, s.eps_r, boundary=s.boundary)
+    o.set_shower(s.q, s.z0, s.bin_dz, s.v, s.w)
+    o.set_probes(s.probes_rz)
+    o.step(1)
+    done = 0
+    t1 = time.perf_counter()
+    while time.perf_counter() - t1 < budget_s:
+        o.step(1)
+        done += 1
+    el = time.perf_counter() - t1
+    return {"value": round(s.cells * done / el / 1e9, 6), "unit": "Gcell/s", "cores": _omp_threads(),
+            "kind": "oracle", "sample": f"{m}x{m} cells, same d and shower model, {done} steps, {el:.1f} s"}
+
+
 def _oracle_sample(w, target_cells):
     """The workload's physics (dx, dt, CPML, shower, lateral spread) on a
     sub-grid of about target_cells cells with the same aspect ratio."""
@@ -334,10 +439,38 @@ def run_reference(args):
                     "d2h_bytes_per_step": 0}}
 
 
+def run_cyl_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return None
+    from oracle import cyl_oracle as CO
+    n = args.n
+    w = W.cyl_table1(n)
+    m = min(512, n)
+    s = W.cyl_table1(m, extent_m=w.d * m)
+    steps = args.steps or 64
+    o = CO.CylOracle(s.nr, s.nz, s.d, s.dt, s.eps_r, boundary=s.boundary)
+    o.set_shower(s.q, s.z0, s.bin_dz, s.v, s.w)
+    o.set_probes(s.probes_rz)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(steps)
+    el = time.perf_counter() - t0
+    v = s.cells * steps / el / 1e9
+    sample = f"each step: one oracle step on {m}x{m} cells of the same d and shower model"
+    return {"impl": "reference", "solver": "cyl2d", "metric": "Gcell-updates/s", "value": round(v, 6),
+            "unit": "Gcell/s", "n_gpus": ws, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": round(el * 1e3 / steps, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": w.describe(),
+            "cpu_baseline": {"value": round(v, 6), "unit": "Gcell/s", "cores": _omp_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 6), "unit": "Gcell/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=0, help="timed steps (0: 1000 for yee3d, n for cyl)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -345,10 +478,23 @@ def main():
     ap.add_argument("--nz", type=int, default=0,
                     help="z planes of a reduced grid with the benchmark physics (profiler captures "
                          "of a few GB); 0 = the benchmark grid")
+    ap.add_argument("--solver", choices=["yee3d", "cyl"], default="yee3d",
+                    help="cyl: the paper's 2D axisymmetric solver on an n x n grid (Table I)")
+    ap.add_argument("--n", type=int, default=8192, help="cyl grid side")
+    ap.add_argument("--cyl-kernel", type=int, default=-1, help="cyl kernel (-1: library default)")
+    ap.add_argument("--seg-rows", type=int, default=0, help="cyl rows per segment (0: automatic)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.solver == "cyl":
+        if args.impl == "reference":
+            line = run_cyl_reference(args)
+        else:
+            line = run_cyl(args)
+    else:
+        if not args.steps:
+            args.steps = 1000
+        line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)
 

@@ -45,15 +45,22 @@ EPS0 = 1.0 / (MU0 * C0 * C0)
 PEC, MUR1 = 0, 1
 
 
-def ring_area(nr, d):
-    A = 2.0 * math.pi * np.arange(nr + 1) * d * d
-    A[0] = math.pi * d * d / 4.0
+def ring_area(nr, d, i0=0):
+    """Cross-section of the rings of rows i0 .. i0+nr (axis disc pi d^2 / 4)."""
+    A = 2.0 * math.pi * (i0 + np.arange(nr + 1)) * d * d
+    if i0 == 0:
+        A[0] = math.pi * d * d / 4.0
     return A
 
 
 class CylOracle:
-    def __init__(self, nr, nz, d, dt, eps_r, boundary=MUR1):
+    def __init__(self, nr, nz, d, dt, eps_r, boundary=MUR1, i0=0):
+        """i0 > 0: the grid is the patch of rows i0 .. i0+nr of a larger grid
+        (radii (i0 + i) d); its row 0 is then not the axis and its E_z is held
+        fixed, so only cells whose dependency cone stays inside the patch are
+        those of the larger grid."""
         self.nr, self.nz, self.d, self.dt = nr, nz, d, dt
+        self.i0 = int(i0)
         self.eps = eps_r * EPS0
         self.boundary = boundary
         self.Er = np.zeros((nr, nz + 1))        # (i+1/2, j)
@@ -106,10 +113,10 @@ class CylOracle:
         if qbar == 0.0:
             return J
         dC = (self._cum(zb) - self._cum(za))[:self.nz]          # crossing of face j+1/2
-        A = ring_area(self.nr, self.d)
-        nw = min(len(w), self.nr + 1)
-        for i in range(nw):
-            J[i] = -(self.d / self.dt) * qbar * w[i] * dC / (A[i] * self.d)
+        A = ring_area(self.nr, self.d, self.i0)
+        for i in range(self.nr + 1):
+            if self.i0 + i < len(w):
+                J[i] = -(self.d / self.dt) * qbar * w[self.i0 + i] * dC / (A[i] * self.d)
         return J
 
     # ---- detectors ------------------------------------------------------------
@@ -136,8 +143,8 @@ class CylOracle:
     def step(self, n=1):
         d, dt, eps = self.d, self.dt, self.eps
         nr, nz = self.nr, self.nz
-        r_half = (np.arange(nr) + 0.5) * d          # r_{i+1/2}
-        r_node = np.arange(nr + 1) * d
+        r_half = (self.i0 + np.arange(nr) + 0.5) * d          # r_{i+1/2}
+        r_node = (self.i0 + np.arange(nr + 1)) * d
         for _ in range(n):
             J = self.current()
             Er0, Ez0 = self.Er.copy(), self.Ez.copy()
@@ -147,8 +154,11 @@ class CylOracle:
             self.Er[:, 1:nz] -= dt / (eps * d) * (self.Hp[:, 1:] - self.Hp[:, :-1])
             rH = r_half[:, None] * self.Hp
             self.Ez[1:nr, :] += dt / (eps * d * r_node[1:nr, None]) * (rH[1:, :] - rH[:-1, :])
-            self.Ez[0, :] += 4.0 * dt / (eps * d) * self.Hp[0, :]
-            self.Ez -= dt / eps * J
+            if self.i0 == 0:
+                self.Ez[0, :] += 4.0 * dt / (eps * d) * self.Hp[0, :]
+                self.Ez -= dt / eps * J
+            else:
+                self.Ez[1:] -= dt / eps * J[1:]
             if self.boundary == MUR1:
                 m = self.mur
                 # wall r = nr d: E_z(nr, j+1/2) from E_z(nr-1, .)

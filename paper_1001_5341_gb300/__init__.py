@@ -80,6 +80,21 @@ _SIGS = {
     "sur_assemble": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, C.c_float, C.c_float, C.c_float, _i, _vp, _vp]),
     "sur_assemble_bwd": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, C.c_float, C.c_float, C.c_float, _i, _vp, _vp,
                               _vp]),
+    # 2D axisymmetric solver (cyl.h)
+    "cyl_create": (_i, [C.POINTER(_vp), _i, _i, _d, _d, _d, _i, _vp]),
+    "cyl_destroy": (None, [_vp]),
+    "cyl_set_shower": (_i, [_vp, _pd, _i, _d, _d, _d, _pd, _i]),
+    "cyl_set_probes": (_i, [_vp, _pd, _i, _i]),
+    "cyl_step": (_i, [_vp, _i]),
+    "cyl_set_kernel": (_i, [_vp, _i, _i]),
+    "cyl_kernel_info": (_i, [_vp, _pi, _pi, _pi]),
+    "cyl_steps_done": (_i, [_vp, _pi64]),
+    "cyl_sync": (_i, [_vp]),
+    "cyl_probes": (_i, [_vp, _vp, _i]),
+    "cyl_fields": (_i, [_vp, _i, _vp, _i]),
+    "cyl_set_field": (_i, [_vp, _i, _vp, _i]),
+    "cyl_reset": (_i, [_vp]),
+    "cyl_launch_count": (_i, [_vp, _pi64]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -314,3 +329,116 @@ class Simulation:
     def set_kernel(self, which: int):
         """1: fused z-march (default), 0: unfused H sweep then E sweep."""
         check(fdtd_set_kernel(self.h, which), "fdtd_set_kernel")
+
+
+# ---- 2D axisymmetric solver ---------------------------------------------------
+
+CYL_COMPONENTS = ("Er", "Ez", "Hphi")
+
+
+class Cylinder:
+    """The paper's (E_r, E_z, H_phi) solver on an (r, z) grid of nr x nz cells
+    (cyl.h).  ``stream``: a ``torch.cuda.Stream`` or raw cudaStream_t int;
+    default: torch's current stream."""
+
+    def __init__(self, nr, nz, d, dt, eps_r, boundary=FDTD_MUR1, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        raw = stream if isinstance(stream, int) else stream.cuda_stream
+        h = _vp()
+        check(cyl_create(C.byref(h), nr, nz, d, dt, eps_r, boundary, _vp(raw)), "cyl_create")
+        self.h = h
+        self.nr, self.nz, self.d, self.dt, self.eps_r, self.boundary = nr, nz, d, dt, eps_r, boundary
+        self.np, self.max_steps = 0, 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            cyl_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def shape(self, comp):
+        c = CYL_COMPONENTS.index(comp) if isinstance(comp, str) else comp
+        return ((self.nr, self.nz + 1), (self.nr + 1, self.nz), (self.nr, self.nz))[c]
+
+    def set_shower(self, q, z0, bin_dz, v, w):
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        check(cyl_set_shower(self.h, _dp(q), q.size, z0, bin_dz, v, _dp(w), w.size), "cyl_set_shower")
+
+    def set_probes(self, rz, max_steps):
+        rz = np.ascontiguousarray(np.asarray(rz, dtype=np.float64).reshape(-1, 2))
+        check(cyl_set_probes(self.h, _dp(rz), rz.shape[0], max_steps), "cyl_set_probes")
+        self.np, self.max_steps = rz.shape[0], max_steps
+
+    def set_kernel(self, which: int, seg_rows: int = 0):
+        """0: two kernels per step; 1, 2, 3: wavefront, K = 4, 8, 4 steps per launch (default 2)."""
+        check(cyl_set_kernel(self.h, which, seg_rows), "cyl_set_kernel")
+
+    @property
+    def kernel_info(self):
+        w, k, l = C.c_int(), C.c_int(), C.c_int()
+        check(cyl_kernel_info(self.h, C.byref(w), C.byref(k), C.byref(l)), "cyl_kernel_info")
+        return {"kernel": w.value, "steps_per_launch": k.value, "seg_rows": l.value}
+
+    def step(self, n=1):
+        check(cyl_step(self.h, n), "cyl_step")
+
+    def sync(self):
+        check(cyl_sync(self.h), "cyl_sync")
+
+    @property
+    def steps_done(self):
+        v = C.c_int64()
+        check(cyl_steps_done(self.h, C.byref(v)), "cyl_steps_done")
+        return v.value
+
+    @property
+    def launches(self):
+        v = C.c_int64()
+        check(cyl_launch_count(self.h, C.byref(v)), "cyl_launch_count")
+        return v.value
+
+    def probes(self, out=None):
+        """Traces [n_probes][max_steps][2] (E_z, E_r): numpy, or into a CUDA tensor."""
+        if out is not None:
+            check(cyl_probes(self.h, _vp(out.data_ptr()), 1), "cyl_probes")
+            return out
+        a = np.zeros((self.np, self.max_steps, 2), dtype=np.float32)
+        check(cyl_probes(self.h, _vp(a.ctypes.data), 0), "cyl_probes")
+        return a
+
+    def field(self, comp, out=None):
+        c = CYL_COMPONENTS.index(comp) if isinstance(comp, str) else comp
+        if out is not None:
+            check(cyl_fields(self.h, c, _vp(out.data_ptr()), 1), "cyl_fields")
+            return out
+        a = np.zeros(self.shape(c), dtype=np.float32)
+        check(cyl_fields(self.h, c, _vp(a.ctypes.data), 0), "cyl_fields")
+        return a
+
+    def set_field(self, comp, arr):
+        """From a host array, or from a contiguous float32 CUDA tensor."""
+        c = CYL_COMPONENTS.index(comp) if isinstance(comp, str) else comp
+        if hasattr(arr, "data_ptr") and getattr(arr, "is_cuda", False):
+            import torch
+            if arr.dtype != torch.float32 or not arr.is_contiguous() or tuple(arr.shape) != self.shape(c):
+                raise ValueError(f"{CYL_COMPONENTS[c]}: need a contiguous float32 tensor of shape {self.shape(c)}")
+            check(cyl_set_field(self.h, c, _vp(arr.data_ptr()), 1), "cyl_set_field")
+            return
+        a = np.ascontiguousarray(arr, dtype=np.float32)
+        if a.shape != self.shape(c):
+            raise ValueError(f"{CYL_COMPONENTS[c]}: shape {a.shape}, expected {self.shape(c)}")
+        check(cyl_set_field(self.h, c, _vp(a.ctypes.data), 0), "cyl_set_field")
+
+    def reset(self):
+        check(cyl_reset(self.h), "cyl_reset")

@@ -1,0 +1,956 @@
+// cyl.cu -- the paper's 2D axisymmetric FDTD (E_r, E_z, H_phi); the ABI and
+// its conventions are in cyl.h.
+//
+// Storage: two sets (ping-pong) of three float32 arrays with nr+1 rows
+// (radius) of `pitch` floats (z fastest).  Element (i, j) of a component sits
+// at row i, position PADL + j; the PADL floats before column 0 and the floats
+// after column nz are never written and stay zero, so that a warp may read a
+// band of columns that starts left of column 0 or ends right of column nz.
+// Cells outside a component's shape (E_r and H_phi on row nr, E_z and H_phi
+// on column nz) are never written either.
+//
+// Two paths advance the fields:
+//  * the two-kernel path (one H launch and one E launch per step, in place on
+//    the current set; 36 bytes of DRAM per cell-update), which also runs the
+//    steps that are left when a step count is not a multiple of K;
+//  * the wavefront path (default): one launch advances K steps, reading the
+//    current set once and writing the other set once (24 bytes per cell per
+//    launch).  Each warp owns a band of z columns and marches up the rows of
+//    one radial segment; time level s is computed one row behind level s-1,
+//    all levels in registers, so that every input of a cell of level s (rows
+//    r and r+1 of level s-1, row r-1 of level s, columns j-1..j+1 through warp
+//    shuffles) is at hand.  A warp's columns overlap its neighbours' by K on
+//    each side and its rows start K below its segment, so that the cells it
+//    stores depend only on cells it computed.  Rows arrive in shared memory
+//    through a ring of bulk asynchronous copies (TMA engine), STAGES rows
+//    ahead, one mbarrier per stage.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "../../include/cyl.h"
+#include "../../include/fdtd.h"
+
+namespace {
+
+constexpr double kC = 299792458.0;
+constexpr double kMu0 = 1.25663706212e-6;
+constexpr double kPi = 3.14159265358979323846;
+constexpr int PADL = 16;     // zero floats before column 0 (>= the widest left halo, 16-byte multiple)
+constexpr int MSRC = 8;      // faces one step's deposit may touch (|v| dt / d <= 4)
+constexpr int NW = 4;        // warps per block of the wavefront kernel
+constexpr int STAGES = 8;    // rows in flight per warp
+
+// ---------------------------------------------------------------------------
+// Source: q(z_s) linear in a bin table, cloud-in-cell along z.
+// ---------------------------------------------------------------------------
+struct Src {
+    int active, nbins, nw;
+    double z0, bin_dz, v, dt, d;
+    const double *q;      // bin table (device)
+    const float *coef;    // per ring: w_i / (eps A_i) (device)
+};
+
+__device__ __forceinline__ double src_q(const Src &s, double z) {
+    const double x = (z - s.z0) / s.bin_dz;
+    if (!(x >= 0.0) || x > (double)(s.nbins - 1)) return 0.0;
+    int b = (int)floor(x);
+    if (b > s.nbins - 2) b = s.nbins - 2;
+    const double f = x - (double)b;
+    return (1.0 - f) * s.q[b] + f * s.q[b + 1];
+}
+
+// cumulative cloud-in-cell weight of the nodes <= j of a unit charge at z
+__device__ __forceinline__ double cum(double z, double d, int j) {
+    const double x = z / d;
+    const double jj = floor(x);
+    const double f = x - jj;
+    double c = 0.0;
+    if ((double)j >= jj) c += 1.0 - f;
+    if ((double)j >= jj + 1.0) c += f;
+    return c;
+}
+
+// First face of the window of step n (n -> n+1); the deposit is zero outside
+// jlo .. jlo + MSRC - 1.
+__device__ __forceinline__ int src_jlo(const Src &s, long long n) {
+    const double za = s.z0 + s.v * (double)n * s.dt, zb = s.z0 + s.v * (double)(n + 1) * s.dt;
+    return (int)floor(fmin(za, zb) / s.d) - 1;
+}
+
+// qbar dC_j of step n at face j+1/2, to be scaled by coef[i] for ring i.
+__device__ __forceinline__ float src_face(const Src &s, long long n, int j) {
+    const double za = s.z0 + s.v * (double)n * s.dt, zb = s.z0 + s.v * (double)(n + 1) * s.dt;
+    const double qb = src_q(s, s.z0 + s.v * ((double)n + 0.5) * s.dt);
+    return (float)(qb * (cum(zb, s.d, j) - cum(za, s.d, j)));
+}
+
+struct Set {
+    float *Er, *Ez, *Hp;   // element (0, 0) of each component
+};
+
+struct Dev {
+    int nr, nz, pitch;
+    Set f;
+    const float2 *rowc;    // per row i: (cA_i, cB_i), E_z += cA_i H(i) - cB_i H(i-1)
+};
+
+// ---------------------------------------------------------------------------
+// Two-kernel path
+// ---------------------------------------------------------------------------
+__global__ void k_cyl_h(Dev D, float kH) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+    if (i >= D.nr || j >= D.nz) return;
+    const long long o = (long long)i * D.pitch + j;
+    const float der = D.f.Er[o + 1] - D.f.Er[o];
+    const float dez = D.f.Ez[o + D.pitch] - D.f.Ez[o];
+    D.f.Hp[o] -= kH * (der - dez);
+}
+
+// E update of one step with the boundary: the thread of E_r(i, 1) also sets
+// the cap E_r(i, 0), that of E_r(i, nz-1) the cap E_r(i, nz), that of
+// E_z(nr-1, j) the wall E_z(nr, j) (first-order Mur from the old and new
+// values next to them, or zero for PEC); no other thread of the launch reads
+// or writes those cells.
+__global__ void k_cyl_e(Dev D, float kE, float mur, int mur_on, Src S, long long n) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+    const int nr = D.nr, nz = D.nz;
+    if (i >= nr || j > nz) return;
+    const long long o = (long long)i * D.pitch + j;
+    float *Er = D.f.Er, *Ez = D.f.Ez;
+    const float *Hp = D.f.Hp;
+    if (j >= 1 && j <= nz - 1) {
+        const float er0 = Er[o];
+        const float er1 = er0 - kE * (Hp[o] - Hp[o - 1]);
+        Er[o] = er1;
+        if (j == 1) Er[o - 1] = mur_on ? er0 + mur * (er1 - Er[o - 1]) : 0.f;
+        if (j == nz - 1) Er[o + 1] = mur_on ? er0 + mur * (er1 - Er[o + 1]) : 0.f;
+    }
+    if (j < nz) {
+        const float ez0 = Ez[o];
+        const float2 c = D.rowc[i];
+        float ez1 = ez0 + c.x * Hp[o] - (i > 0 ? c.y * Hp[o - D.pitch] : 0.f);
+        if (S.active && i < S.nw && (unsigned)(j - src_jlo(S, n)) < (unsigned)MSRC)
+            ez1 += S.coef[i] * src_face(S, n, j);
+        Ez[o] = ez1;
+        if (i == nr - 1) Ez[o + D.pitch] = mur_on ? ez0 + mur * (ez1 - Ez[o + D.pitch]) : 0.f;
+    }
+}
+
+__global__ void k_cyl_probes(Dev D, const int *ij, int np, float *trace, int max_steps, long long slot) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const int i = ij[2 * p], j = ij[2 * p + 1];
+    const long long o = (long long)i * D.pitch + j;
+    const float ez = 0.5f * (D.f.Ez[o - 1] + D.f.Ez[o]);
+    const float er = i == 0 ? 0.f : 0.5f * (D.f.Er[o - D.pitch] + D.f.Er[o]);
+    float *t = trace + ((long long)p * max_steps + slot) * 2;
+    t[0] = ez;
+    t[1] = er;
+}
+
+__global__ void k_cyl_copy(const float *src, int sp, float *dst, int dp, int rows, int cols) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+    if (i < rows && j < cols) dst[(long long)i * dp + j] = src[(long long)i * sp + j];
+}
+
+// ---------------------------------------------------------------------------
+// Wavefront path
+// ---------------------------------------------------------------------------
+struct Wave {
+    int nr, nz, pitch;
+    Set in, out;
+    const float2 *rowc;
+    float kE, kH, mur;
+    int mur_on;
+    int U, L, nbands;        // owned columns per band, rows per segment, bands
+    Src src;
+    long long n0;            // steps done before the launch
+    const int *poff;         // per warp (segment-major): first detector record
+    const int4 *prec;        // detector records (row, column, id, 0), sorted by warp then row
+    float *trace;
+    int max_steps;
+    int *flags;
+};
+
+__device__ __forceinline__ uint32_t sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(sa(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded: gives up after about two seconds of clock cycles
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > (4LL << 30)) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_load(float *dst, const float *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     sa(dst)),
+                 "l"(src), "r"(bytes), "r"(sa(bar))
+                 : "memory");
+}
+
+template <int CPL>
+struct Row {
+    float er[CPL], ez[CPL], h[CPL];
+};
+
+template <int CPL>
+__device__ __forceinline__ void lds_row(Row<CPL> &r, const float *st, int lane) {
+    constexpr int W = 32 * CPL;
+    if constexpr (CPL == 2) {
+        const float2 a = reinterpret_cast<const float2 *>(st)[lane];
+        const float2 b = reinterpret_cast<const float2 *>(st + W)[lane];
+        const float2 c = reinterpret_cast<const float2 *>(st + 2 * W)[lane];
+        r.er[0] = a.x; r.er[1] = a.y;
+        r.ez[0] = b.x; r.ez[1] = b.y;
+        r.h[0] = c.x; r.h[1] = c.y;
+    } else {
+        static_assert(CPL == 4, "2 or 4 columns per lane");
+        const float4 a = reinterpret_cast<const float4 *>(st)[lane];
+        const float4 b = reinterpret_cast<const float4 *>(st + W)[lane];
+        const float4 c = reinterpret_cast<const float4 *>(st + 2 * W)[lane];
+        r.er[0] = a.x; r.er[1] = a.y; r.er[2] = a.z; r.er[3] = a.w;
+        r.ez[0] = b.x; r.ez[1] = b.y; r.ez[2] = b.z; r.ez[3] = b.w;
+        r.h[0] = c.x; r.h[1] = c.y; r.h[2] = c.z; r.h[3] = c.w;
+    }
+}
+
+// n of the lane's CPL columns (a prefix) to global memory
+template <int CPL>
+__device__ __forceinline__ void st_cols(float *p, const float (&v)[CPL], int n) {
+    if (n >= CPL) {
+        if constexpr (CPL == 2) *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+        else *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < CPL; ++q)
+            if (q < n) p[q] = v[q];
+    }
+}
+
+template <int K, int CPL>
+__global__ void __launch_bounds__(NW * 32) k_cyl_wave(Wave A) {
+    constexpr int W = 32 * CPL;          // columns per warp
+    constexpr int HL = K;                // left halo
+    constexpr int STAGE = 3 * W;         // floats per ring stage
+    static_assert(K % 4 == 0 && K % CPL == 0, "the halo keeps the bulk copies 16-byte aligned");
+    extern __shared__ __align__(128) float smem[];
+    __shared__ __align__(8) uint64_t bars[NW][STAGES];
+    __shared__ int sjlo[K];
+    __shared__ float ssrc[K][MSRC];
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (A.src.active && tid < K * MSRC) {
+        const int s = tid / MSRC, m = tid % MSRC;
+        const int jlo = src_jlo(A.src, A.n0 + s);
+        if (m == 0) sjlo[s] = jlo;
+        ssrc[s][m] = src_face(A.src, A.n0 + s, jlo + m);
+    }
+    if (lane == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[w][s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    const int b = blockIdx.x * NW + w;
+    if (b >= A.nbands) return;
+    const int g = blockIdx.y;
+    const int nr = A.nr, nz = A.nz, pitch = A.pitch;
+    const int own0 = g * A.L, own1 = min(own0 + A.L, nr + 1);   // owned rows [own0, own1)
+    const int p0 = max(0, own0 - K);
+    const int p_end = own1 - 1 + K;
+    const int load_end = min(p_end, nr);
+    const int col0 = b * A.U - HL;
+    const int oc0 = b * A.U, oc1 = min(oc0 + A.U, nz + 1);     // owned columns [oc0, oc1)
+    float *ring = smem + w * STAGES * STAGE;
+    uint64_t *bar = bars[w];
+
+    if (lane == 0)
+        for (int s = 0; s < STAGES && p0 + s <= load_end; ++s) {
+            const long long o = (long long)(p0 + s) * pitch + col0;
+            mbar_expect_tx(&bar[s], STAGE * 4);
+            bulk_load(ring + s * STAGE, A.in.Er + o, W * 4, &bar[s]);
+            bulk_load(ring + s * STAGE + W, A.in.Ez + o, W * 4, &bar[s]);
+            bulk_load(ring + s * STAGE + 2 * W, A.in.Hp + o, W * 4, &bar[s]);
+        }
+
+    int col[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) col[q] = col0 + lane * CPL + q;
+    const bool owned = col[0] >= oc0 && col[0] < oc1;    // a lane owns all or none of its columns
+    const int nE = nz + 1 - col[0], nZ = nz - col[0];    // E_r columns <= nz, E_z and H_phi columns < nz
+    const bool cap_lo = b == 0 && lane == HL / CPL;      // holds columns 0 and 1
+    const bool cap_hi = nz - col0 >= 1 && nz - col0 < W; // this warp holds columns nz - 1 and nz
+
+    // detectors of this warp, one cursor per level
+    const int wid = g * A.nbands + b;
+    const int pfin = A.poff[wid + 1];
+    int pc[K + 1], prow[K + 1];
+    {
+        const int pbeg = A.poff[wid];
+        const int r0 = pbeg < pfin ? A.prec[pbeg].x : INT_MAX;
+#pragma unroll
+        for (int s = 1; s <= K; ++s) {
+            pc[s] = pbeg;
+            prow[s] = r0;
+        }
+    }
+
+    Row<CPL> prv[K + 1], cur[K + 1];
+    float wall[K + 1][CPL];
+#pragma unroll
+    for (int s = 0; s <= K; ++s)
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            prv[s].er[q] = prv[s].ez[q] = prv[s].h[q] = 0.f;
+            cur[s].er[q] = cur[s].ez[q] = cur[s].h[q] = 0.f;
+            wall[s][q] = 0.f;
+        }
+
+    int st = 0;
+    uint32_t phase = 0;
+    int failed_at = -1;
+    for (int p = p0; p <= p_end; ++p) {
+        // level 0: row p from the ring
+        prv[0] = cur[0];
+        if (p <= load_end) {
+            if (!__all_sync(0xffffffffu, mbar_wait(&bar[st], phase))) {
+                failed_at = p;
+                break;
+            }
+            lds_row(cur[0], ring + st * STAGE, lane);
+            __syncwarp();
+            if (lane == 0 && p + STAGES <= load_end) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                const long long o = (long long)(p + STAGES) * pitch + col0;
+                mbar_expect_tx(&bar[st], STAGE * 4);
+                bulk_load(ring + st * STAGE, A.in.Er + o, W * 4, &bar[st]);
+                bulk_load(ring + st * STAGE + W, A.in.Ez + o, W * 4, &bar[st]);
+                bulk_load(ring + st * STAGE + 2 * W, A.in.Hp + o, W * 4, &bar[st]);
+            }
+            if (++st == STAGES) {
+                st = 0;
+                phase ^= 1u;
+            }
+        }
+        // level s computes row p - s from rows p - s, p - s + 1 of level s - 1
+#pragma unroll
+        for (int s = 1; s <= K; ++s) {
+            const int r = p - s;
+            prv[s] = cur[s];
+            if (r < p0 || r > nr) continue;
+            const Row<CPL> &a = prv[s - 1];   // level s-1, row r
+            const Row<CPL> &bn = cur[s - 1];  // level s-1, row r+1
+            Row<CPL> &o = cur[s];
+            if (r < nr) {
+                // H_phi(r, j) from E_r(r, j), E_r(r, j+1), E_z(r, j), E_z(r+1, j)
+                const float er_right = __shfl_down_sync(0xffffffffu, a.er[0], 1);
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) {
+                    const float eR = q + 1 < CPL ? a.er[q + 1] : er_right;
+                    o.h[q] = a.h[q] - A.kH * ((eR - a.er[q]) - (bn.ez[q] - a.ez[q]));
+                }
+                // E_r(r, j) from H_phi(r, j-1), H_phi(r, j)
+                const float h_left = __shfl_up_sync(0xffffffffu, o.h[CPL - 1], 1);
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) {
+                    const float hL = q > 0 ? o.h[q - 1] : h_left;
+                    o.er[q] = a.er[q] - A.kE * (o.h[q] - hL);
+                }
+                // E_z(r, j) from H_phi(r, j), H_phi(r-1, j); on the axis cB = 0
+                const float2 c = __ldg(&A.rowc[r]);
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) o.ez[q] = a.ez[q] + c.x * o.h[q] - c.y * prv[s].h[q];
+                if (A.src.active && r < A.src.nw) {
+                    const float cf = __ldg(&A.src.coef[r]);
+                    const int jlo = sjlo[s - 1];
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q) {
+                        const unsigned m = (unsigned)(col[q] - jlo);
+                        if (m < (unsigned)MSRC) o.ez[q] += cf * ssrc[s - 1][m];
+                    }
+                }
+                // end caps: E_r(r, 0) from column 1 (same lane), E_r(r, nz) from column nz - 1
+                if (cap_lo) o.er[0] = A.mur_on ? a.er[1] + A.mur * (o.er[1] - a.er[0]) : 0.f;
+                if (cap_hi) {
+                    const float old_l = __shfl_up_sync(0xffffffffu, a.er[CPL - 1], 1);
+                    const float new_l = __shfl_up_sync(0xffffffffu, o.er[CPL - 1], 1);
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q)
+                        if (col[q] == nz) {
+                            const float ol = q > 0 ? a.er[q - 1] : old_l;
+                            const float nl = q > 0 ? o.er[q - 1] : new_l;
+                            o.er[q] = A.mur_on ? ol + A.mur * (nl - a.er[q]) : 0.f;
+                        }
+                }
+                // the wall E_z(nr, j) of this level, from E_z(nr-1, j) old (a) and
+                // new (o) and E_z(nr, j) old (bn)
+                if (r == nr - 1)
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q)
+                        wall[s][q] = A.mur_on ? a.ez[q] + A.mur * (o.ez[q] - bn.ez[q]) : 0.f;
+                // detectors on row r at step n0 + s
+                if (r == prow[s]) {
+                    const float ez_up = __shfl_up_sync(0xffffffffu, o.ez[CPL - 1], 1);
+                    do {
+                        const int4 pr = __ldg(&A.prec[pc[s]]);
+                        const int lj = pr.y - col0;
+                        if (lane == lj / CPL) {
+                            const int qj = lj % CPL;
+                            float ezj = 0.f, ezl = 0.f, erj = 0.f, erb = 0.f;
+#pragma unroll
+                            for (int q = 0; q < CPL; ++q)
+                                if (q == qj) {
+                                    ezj = o.ez[q];
+                                    erj = o.er[q];
+                                    erb = prv[s].er[q];
+                                    ezl = q > 0 ? o.ez[q > 0 ? q - 1 : 0] : ez_up;
+                                }
+                            float *t = A.trace + ((long long)pr.z * A.max_steps + A.n0 + s - 1) * 2;
+                            t[0] = 0.5f * (ezl + ezj);
+                            t[1] = r == 0 ? 0.f : 0.5f * (erb + erj);
+                        }
+                        ++pc[s];
+                        prow[s] = pc[s] < pfin ? __ldg(&A.prec[pc[s]].x) : INT_MAX;
+                    } while (prow[s] == r);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) {
+                    o.er[q] = 0.f;
+                    o.h[q] = 0.f;
+                    o.ez[q] = wall[s][q];
+                }
+            }
+        }
+        // level K, row p - K: store the owned cells
+        const int r = p - K;
+        if (owned && r >= own0 && r < own1) {
+            const long long o = (long long)r * pitch + col[0];
+            if (r < nr) {
+                st_cols<CPL>(A.out.Er + o, cur[K].er, nE);
+                st_cols<CPL>(A.out.Hp + o, cur[K].h, nZ);
+            }
+            st_cols<CPL>(A.out.Ez + o, cur[K].ez, nZ);
+        }
+    }
+    if (failed_at >= 0) {
+        // give up: flag it, and let the copies still in flight land before the block ends
+        if (lane == 0) {
+            atomicOr(A.flags, 1);
+            int s2 = st;
+            uint32_t ph = phase;
+            for (int m = 0; m < STAGES && failed_at + m <= load_end; ++m) {
+                mbar_wait(&bar[s2], ph);
+                if (++s2 == STAGES) {
+                    s2 = 0;
+                    ph ^= 1u;
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+struct Variant {
+    int K, CPL;
+    void (*fn)(Wave);
+};
+const Variant kVariants[] = {{0, 0, nullptr}, {4, 2, k_cyl_wave<4, 2>}, {8, 2, k_cyl_wave<8, 2>},
+                             {4, 4, k_cyl_wave<4, 4>}};
+constexpr int kNumKernels = 4;
+
+size_t ring_bytes(int CPL) { return (size_t)NW * STAGES * 3 * 32 * CPL * sizeof(float); }
+
+}  // namespace
+
+struct cyl_ctx {
+    int nr, nz, pitch;
+    int boundary;
+    double d, dt, eps, kE, kH, mur;
+    cudaStream_t stream;
+    float *block;
+    size_t comp;             // floats per component array
+    Set set[2];
+    int cur;
+    float2 *d_rowc;
+    int *d_flags;
+    // shower
+    double *d_q;
+    float *d_coef;
+    Src src;
+    // detectors
+    std::vector<int> pij;    // (i, j) per detector
+    int np, max_steps;
+    int *d_ij;
+    float *d_trace;
+    int *d_poff;
+    int4 *d_prec;
+    // kernel
+    int kernel, K, CPL, U, L, nbands, nseg, seg_req;
+    long long steps, launches;
+    int status;
+};
+
+namespace {
+
+int note(cyl_ctx *h, cudaError_t e) {
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (h && h->status == FDTD_OK) h->status = FDTD_ERR_CUDA;
+        return FDTD_ERR_CUDA;
+    }
+    return FDTD_OK;
+}
+
+void free_src(cyl_ctx *h) {
+    if (h->d_q) cudaFree(h->d_q);
+    if (h->d_coef) cudaFree(h->d_coef);
+    h->d_q = nullptr;
+    h->d_coef = nullptr;
+    h->src = Src{};
+}
+
+void free_probes(cyl_ctx *h) {
+    if (h->d_ij) cudaFree(h->d_ij);
+    if (h->d_trace) cudaFree(h->d_trace);
+    if (h->d_poff) cudaFree(h->d_poff);
+    if (h->d_prec) cudaFree(h->d_prec);
+    h->d_ij = nullptr;
+    h->d_trace = nullptr;
+    h->d_poff = nullptr;
+    h->d_prec = nullptr;
+    h->pij.clear();
+    h->np = 0;
+    h->max_steps = 0;
+}
+
+// widest column a warp of any wavefront variant reads, + 1
+int read_extent(int nz) {
+    int e = nz + 1;
+    for (int v = 1; v < kNumKernels; ++v) {
+        const int K = kVariants[v].K, W = 32 * kVariants[v].CPL, U = W - 2 * K;
+        const int nb = (nz + 1 + U - 1) / U;
+        e = std::max(e, (nb - 1) * U - K + W);
+    }
+    return e;
+}
+
+// Rows per segment: the fewest waves of blocks times the march length of one
+// segment (L + 2K rows), larger L on ties.
+int choose_L(cyl_ctx *h) {
+    if (h->seg_req > 0) return std::min(h->seg_req, h->nr + 1);
+    int dev = 0, sms = 152, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const Variant &v = kVariants[h->kernel];
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.fn, NW * 32, ring_bytes(v.CPL)) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const long long slots = (long long)sms * per_sm;
+    const long long bx = (h->nbands + NW - 1) / NW;
+    int best = h->nr + 1;
+    double best_cost = 1e300;
+    for (int L = 16; L <= h->nr + 1 + 15; L += 16) {
+        const int Lc = std::min(L, h->nr + 1);
+        const long long nseg = (h->nr + 1 + Lc - 1) / Lc;
+        const long long waves = (bx * nseg + slots - 1) / slots;
+        const double cost = (double)waves * (Lc + 2 * h->K);
+        if (cost <= best_cost * (1 + 1e-12)) {
+            best_cost = cost;
+            best = Lc;
+        }
+    }
+    return best;
+}
+
+// Detector records of the wavefront kernel: per warp (segment, band), sorted by row.
+int build_wave_probes(cyl_ctx *h) {
+    if (h->d_poff) cudaFree(h->d_poff);
+    if (h->d_prec) cudaFree(h->d_prec);
+    h->d_poff = nullptr;
+    h->d_prec = nullptr;
+    if (h->kernel == 0) return FDTD_OK;
+    const long long nwarps = (long long)h->nseg * h->nbands;
+    std::vector<int> off(nwarps + 1, 0);
+    std::vector<long long> key(h->np);
+    for (int p = 0; p < h->np; ++p) {
+        const int i = h->pij[2 * p], j = h->pij[2 * p + 1];
+        key[p] = ((long long)(i / h->L) * h->nbands + j / h->U);
+        off[key[p] + 1]++;
+    }
+    for (long long w = 0; w < nwarps; ++w) off[w + 1] += off[w];
+    std::vector<int> order(h->np);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return key[a] != key[b] ? key[a] < key[b] : h->pij[2 * a] < h->pij[2 * b];
+    });
+    std::vector<int4> rec(std::max(h->np, 1));
+    for (int k = 0; k < h->np; ++k) {
+        const int p = order[k];
+        rec[k] = make_int4(h->pij[2 * p], h->pij[2 * p + 1], p, 0);
+    }
+    if (cudaMalloc(&h->d_poff, off.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&h->d_prec, rec.size() * sizeof(int4)) != cudaSuccess) {
+        cudaGetLastError();
+        return FDTD_ERR_OOM;
+    }
+    if (note(h, cudaMemcpy(h->d_poff, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice)) != FDTD_OK ||
+        note(h, cudaMemcpy(h->d_prec, rec.data(), rec.size() * sizeof(int4), cudaMemcpyHostToDevice)) != FDTD_OK)
+        return FDTD_ERR_CUDA;
+    return FDTD_OK;
+}
+
+int configure(cyl_ctx *h, int which, int seg_rows) {
+    h->kernel = which;
+    h->seg_req = seg_rows;
+    if (which == 0) {
+        h->K = 1;
+        h->CPL = 1;
+        h->U = h->L = h->nbands = h->nseg = 0;
+    } else {
+        const Variant &v = kVariants[which];
+        h->K = v.K;
+        h->CPL = v.CPL;
+        h->U = 32 * v.CPL - 2 * v.K;
+        h->nbands = (h->nz + 1 + h->U - 1) / h->U;
+        h->L = choose_L(h);
+        h->nseg = (h->nr + 1 + h->L - 1) / h->L;
+    }
+    return build_wave_probes(h);
+}
+
+Dev dev_of(const cyl_ctx *h) {
+    Dev D;
+    D.nr = h->nr;
+    D.nz = h->nz;
+    D.pitch = h->pitch;
+    D.f = h->set[h->cur];
+    D.rowc = h->d_rowc;
+    return D;
+}
+
+void launch_two_kernel(cyl_ctx *h) {
+    const Dev D = dev_of(h);
+    const dim3 blk(256), gh((h->nz + 255) / 256, h->nr), ge((h->nz + 1 + 255) / 256, h->nr);
+    k_cyl_h<<<gh, blk, 0, h->stream>>>(D, (float)h->kH);
+    k_cyl_e<<<ge, blk, 0, h->stream>>>(D, (float)h->kE, (float)h->mur, h->boundary == FDTD_MUR1, h->src, h->steps);
+    h->launches += 2;
+    if (h->np > 0) {
+        k_cyl_probes<<<(h->np + 127) / 128, 128, 0, h->stream>>>(D, h->d_ij, h->np, h->d_trace, h->max_steps,
+                                                                 h->steps);
+        h->launches++;
+    }
+    h->steps++;
+}
+
+void launch_wave(cyl_ctx *h) {
+    const Variant &v = kVariants[h->kernel];
+    Wave A;
+    A.nr = h->nr;
+    A.nz = h->nz;
+    A.pitch = h->pitch;
+    A.in = h->set[h->cur];
+    A.out = h->set[h->cur ^ 1];
+    A.rowc = h->d_rowc;
+    A.kE = (float)h->kE;
+    A.kH = (float)h->kH;
+    A.mur = (float)h->mur;
+    A.mur_on = h->boundary == FDTD_MUR1;
+    A.U = h->U;
+    A.L = h->L;
+    A.nbands = h->nbands;
+    A.src = h->src;
+    A.n0 = h->steps;
+    A.poff = h->d_poff;
+    A.prec = h->d_prec;
+    A.trace = h->d_trace;
+    A.max_steps = h->max_steps;
+    A.flags = h->d_flags;
+    const dim3 grid((h->nbands + NW - 1) / NW, h->nseg);
+    v.fn<<<grid, NW * 32, ring_bytes(v.CPL), h->stream>>>(A);
+    h->launches++;
+    h->cur ^= 1;
+    h->steps += v.K;
+}
+
+size_t comp_rows(const cyl_ctx *h, int comp) { return comp == 1 ? (size_t)h->nr + 1 : (size_t)h->nr; }
+size_t comp_cols(const cyl_ctx *h, int comp) { return comp == 0 ? (size_t)h->nz + 1 : (size_t)h->nz; }
+float *comp_ptr(cyl_ctx *h, int comp) {
+    const Set &s = h->set[h->cur];
+    return comp == 0 ? s.Er : comp == 1 ? s.Ez : s.Hp;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cyl_create(cyl_t *out, int nr, int nz, double d, double dt, double eps_r, int boundary, void *stream) {
+    if (!out) return FDTD_ERR_ARG;
+    *out = nullptr;
+    if (nr < 4 || nz < 4 || !(d > 0.0) || !(dt > 0.0) || !(eps_r >= 1.0) ||
+        (boundary != FDTD_PEC && boundary != FDTD_MUR1))
+        return FDTD_ERR_ARG;
+    if (nr > 65534 || (long long)(nr + 1) * (nz + 1) > (1LL << 34)) return FDTD_ERR_ARG;   // rows index grid.y
+    if (dt > d * std::sqrt(eps_r) / (kC * std::sqrt(2.0))) return FDTD_ERR_CFL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return FDTD_ERR_CUDA;
+    }
+    cyl_ctx *h = new (std::nothrow) cyl_ctx();
+    if (!h) return FDTD_ERR_OOM;
+    h->nr = nr;
+    h->nz = nz;
+    h->pitch = (PADL + read_extent(nz) + 31) / 32 * 32;
+    h->boundary = boundary;
+    h->d = d;
+    h->dt = dt;
+    h->eps = eps_r / (kMu0 * kC * kC);
+    h->kE = dt / (h->eps * d);
+    h->kH = dt / (kMu0 * d);
+    const double S = kC / std::sqrt(eps_r) * dt / d;
+    h->mur = (S - 1.0) / (S + 1.0);
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->comp = (size_t)(nr + 1) * h->pitch;
+    const size_t bytes = 6 * h->comp * sizeof(float);
+    std::vector<float2> rowc(nr + 1);
+    rowc[0] = make_float2((float)(4.0 * h->kE), 0.f);
+    for (int i = 1; i <= nr; ++i)
+        rowc[i] = make_float2((float)(h->kE * (i + 0.5) / i), (float)(h->kE * (i - 0.5) / i));
+    if (cudaMalloc(&h->block, bytes) != cudaSuccess || cudaMalloc(&h->d_rowc, (nr + 1) * sizeof(float2)) != cudaSuccess ||
+        cudaMalloc(&h->d_flags, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        cyl_destroy(h);
+        return FDTD_ERR_OOM;
+    }
+    for (int s = 0; s < 2; ++s) {
+        float *base = h->block + 3 * s * h->comp + PADL;
+        h->set[s] = Set{base, base + h->comp, base + 2 * h->comp};
+    }
+    for (int v = 1; v < kNumKernels; ++v)
+        if (ring_bytes(kVariants[v].CPL) > 48 * 1024)
+            note(h, cudaFuncSetAttribute(kVariants[v].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ring_bytes(kVariants[v].CPL)));
+    note(h, cudaMemsetAsync(h->block, 0, bytes, h->stream));
+    note(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int), h->stream));
+    note(h, cudaMemcpyAsync(h->d_rowc, rowc.data(), rowc.size() * sizeof(float2), cudaMemcpyHostToDevice, h->stream));
+    note(h, cudaStreamSynchronize(h->stream));
+    if (h->status == FDTD_OK) h->status = configure(h, 2, 0);
+    if (h->status != FDTD_OK) {
+        const int st = h->status;
+        cyl_destroy(h);
+        return st;
+    }
+    *out = h;
+    return FDTD_OK;
+}
+
+void cyl_destroy(cyl_t h) {
+    if (!h) return;
+    free_src(h);
+    free_probes(h);
+    if (h->block) cudaFree(h->block);
+    if (h->d_rowc) cudaFree(h->d_rowc);
+    if (h->d_flags) cudaFree(h->d_flags);
+    delete h;
+}
+
+int cyl_set_kernel(cyl_t h, int which, int seg_rows) {
+    if (!h || which < 0 || which >= kNumKernels || seg_rows < 0) return FDTD_ERR_ARG;
+    if (h->status != FDTD_OK) return h->status;
+    const int st = configure(h, which, seg_rows);
+    if (st != FDTD_OK && h->status == FDTD_OK) h->status = st;
+    return st;
+}
+
+int cyl_kernel_info(cyl_t h, int *which, int *steps_per_launch, int *seg_rows) {
+    if (!h) return FDTD_ERR_ARG;
+    if (which) *which = h->kernel;
+    if (steps_per_launch) *steps_per_launch = h->K;
+    if (seg_rows) *seg_rows = h->L;
+    return FDTD_OK;
+}
+
+int cyl_set_shower(cyl_t h, const double *q, int n_bins, double z0, double bin_dz, double v, const double *w,
+                   int nw) {
+    if (!h || !q || !w || n_bins < 2 || !(bin_dz > 0.0) || nw < 1 || nw > h->nr + 1 || !std::isfinite(z0) ||
+        !std::isfinite(v) || std::fabs(v) * h->dt > 4.0 * h->d)
+        return FDTD_ERR_ARG;
+    if (h->status != FDTD_OK) return h->status;
+    free_src(h);
+    std::vector<float> coef(nw);
+    for (int i = 0; i < nw; ++i) {
+        const double A = i == 0 ? kPi * h->d * h->d / 4.0 : 2.0 * kPi * (double)i * h->d * h->d;
+        coef[i] = (float)(w[i] / (h->eps * A));
+    }
+    if (cudaMalloc(&h->d_q, n_bins * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h->d_coef, nw * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        free_src(h);
+        return FDTD_ERR_OOM;
+    }
+    if (note(h, cudaMemcpy(h->d_q, q, n_bins * sizeof(double), cudaMemcpyHostToDevice)) != FDTD_OK ||
+        note(h, cudaMemcpy(h->d_coef, coef.data(), nw * sizeof(float), cudaMemcpyHostToDevice)) != FDTD_OK)
+        return h->status;
+    h->src.active = 1;
+    h->src.nbins = n_bins;
+    h->src.nw = std::min(nw, h->nr);   // ring nr lies on the wall, whose E_z the boundary sets
+    h->src.z0 = z0;
+    h->src.bin_dz = bin_dz;
+    h->src.v = v;
+    h->src.dt = h->dt;
+    h->src.d = h->d;
+    h->src.q = h->d_q;
+    h->src.coef = h->d_coef;
+    return FDTD_OK;
+}
+
+int cyl_set_probes(cyl_t h, const double *rz, int n, int max_steps) {
+    if (!h || n < 0 || (n > 0 && !rz) || max_steps < 0) return FDTD_ERR_ARG;
+    if (h->status != FDTD_OK) return h->status;
+    std::vector<int> ij(2 * (size_t)n);
+    for (int p = 0; p < n; ++p) {
+        if (!std::isfinite(rz[2 * p]) || !std::isfinite(rz[2 * p + 1])) return FDTD_ERR_ARG;
+        const double fi = std::floor(rz[2 * p] / h->d + 0.5), fj = std::floor(rz[2 * p + 1] / h->d + 0.5);
+        if (fi < 0 || fi >= h->nr || fj < 1 || fj >= h->nz) return FDTD_ERR_ARG;
+        ij[2 * p] = (int)fi;
+        ij[2 * p + 1] = (int)fj;
+    }
+    free_probes(h);
+    if (n == 0) {
+        // the wavefront kernel reads its (empty) per-warp lists
+        const int st = build_wave_probes(h);
+        if (st != FDTD_OK && h->status == FDTD_OK) h->status = st;
+        return st;
+    }
+    const size_t tbytes = std::max<size_t>((size_t)n * max_steps * 2 * sizeof(float), 16);
+    if (cudaMalloc(&h->d_ij, ij.size() * sizeof(int)) != cudaSuccess || cudaMalloc(&h->d_trace, tbytes) != cudaSuccess) {
+        cudaGetLastError();
+        free_probes(h);
+        return FDTD_ERR_OOM;
+    }
+    if (note(h, cudaMemcpy(h->d_ij, ij.data(), ij.size() * sizeof(int), cudaMemcpyHostToDevice)) != FDTD_OK ||
+        note(h, cudaMemsetAsync(h->d_trace, 0, tbytes, h->stream)) != FDTD_OK)
+        return h->status;
+    h->pij = ij;
+    h->np = n;
+    h->max_steps = max_steps;
+    const int st = build_wave_probes(h);
+    if (st != FDTD_OK && h->status == FDTD_OK) h->status = st;
+    return st;
+}
+
+int cyl_step(cyl_t h, int n) {
+    if (!h || n < 0) return FDTD_ERR_ARG;
+    if (h->status != FDTD_OK) return h->status;
+    if (h->np > 0 && h->steps + n > h->max_steps) return FDTD_ERR_CAPACITY;
+    if (h->kernel > 0)
+        for (; n >= h->K; n -= h->K) launch_wave(h);
+    for (; n > 0; --n) launch_two_kernel(h);
+    return note(h, cudaGetLastError());
+}
+
+int cyl_sync(cyl_t h) {
+    if (!h) return FDTD_ERR_ARG;
+    if (note(h, cudaStreamSynchronize(h->stream)) != FDTD_OK) return h->status;
+    int flag = 0;
+    if (note(h, cudaMemcpy(&flag, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost)) != FDTD_OK) return h->status;
+    if (flag && h->status == FDTD_OK) h->status = FDTD_ERR_TIMEOUT;
+    return h->status;
+}
+
+int cyl_probes(cyl_t h, float *out, int on_device) {
+    if (!h || !out) return FDTD_ERR_ARG;
+    if (h->status != FDTD_OK) return h->status;
+    if (h->np == 0) return FDTD_OK;
+    const size_t bytes = (size_t)h->np * h->max_steps * 2 * sizeof(float);
+    if (bytes &&
+        note(h, cudaMemcpyAsync(out, h->d_trace, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                h->stream)) != FDTD_OK)
+        return h->status;
+    return cyl_sync(h);
+}
+
+int cyl_fields(cyl_t h, int comp, float *out, int on_device) {
+    if (!h || !out || comp < 0 || comp > 2) return FDTD_ERR_ARG;
+    if (h->status != FDTD_OK) return h->status;
+    const int rows = (int)comp_rows(h, comp), cols = (int)comp_cols(h, comp);
+    if (on_device) {
+        const dim3 g((cols + 255) / 256, rows);
+        k_cyl_copy<<<g, 256, 0, h->stream>>>(comp_ptr(h, comp), h->pitch, out, cols, rows, cols);
+        h->launches++;
+        if (note(h, cudaGetLastError()) != FDTD_OK) return h->status;
+        return cyl_sync(h);
+    }
+    if (note(h, cudaMemcpy2DAsync(out, cols * sizeof(float), comp_ptr(h, comp), h->pitch * sizeof(float),
+                                  cols * sizeof(float), rows, cudaMemcpyDeviceToHost, h->stream)) != FDTD_OK)
+        return h->status;
+    return cyl_sync(h);
+}
+
+int cyl_set_field(cyl_t h, int comp, const float *in, int on_device) {
+    if (!h || !in || comp < 0 || comp > 2) return FDTD_ERR_ARG;
+    if (h->status != FDTD_OK) return h->status;
+    const int rows = (int)comp_rows(h, comp), cols = (int)comp_cols(h, comp);
+    if (note(h, cudaMemcpy2DAsync(comp_ptr(h, comp), h->pitch * sizeof(float), in, cols * sizeof(float),
+                                  cols * sizeof(float), rows,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream)) !=
+        FDTD_OK)
+        return h->status;
+    return cyl_sync(h);
+}
+
+int cyl_reset(cyl_t h) {
+    if (!h) return FDTD_ERR_ARG;
+    if (h->status != FDTD_OK) return h->status;
+    if (note(h, cudaMemsetAsync(h->block, 0, 6 * h->comp * sizeof(float), h->stream)) != FDTD_OK) return h->status;
+    if (h->d_trace &&
+        note(h, cudaMemsetAsync(h->d_trace, 0, (size_t)h->np * h->max_steps * 2 * sizeof(float), h->stream)) !=
+            FDTD_OK)
+        return h->status;
+    h->steps = 0;
+    h->cur = 0;
+    return cyl_sync(h);
+}
+
+int cyl_steps_done(cyl_t h, int64_t *steps) {
+    if (!h || !steps) return FDTD_ERR_ARG;
+    *steps = h->steps;
+    return FDTD_OK;
+}
+
+int cyl_launch_count(cyl_t h, int64_t *launches) {
+    if (!h || !launches) return FDTD_ERR_ARG;
+    *launches = h->launches;
+    return FDTD_OK;
+}
+
+}  // extern "C"

@@ -30,7 +30,7 @@ def _declared():
         if fn.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", fn)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            names |= set(re.findall(r"\b((?:fdtd|sur)_\w+)\s*\(", txt))
+            names |= set(re.findall(r"\b((?:fdtd|sur|cyl)_\w+)\s*\(", txt))
     return names
 
 
@@ -94,6 +94,29 @@ def test_null_handle_calls_are_argument_errors(fd):
     assert fd.fdtd_sync(None) == -1
     assert fd.fdtd_reset(None) == -1
     fd.fdtd_destroy(None)
+
+
+def test_cyl_create_rejects_bad_arguments_on_host(fd):
+    d = 0.01
+    dt = W.courant_dt_2d(d, W.EPS_R_ICE)
+    assert fd.cyl_create(None, 8, 8, d, dt, 3.17, 1, None) == -1
+    cases = [
+        (3, 8, d, dt, 3.17, 1),        # too few rows
+        (8, 3, d, dt, 3.17, 1),        # too few columns
+        (8, 8, -d, dt, 3.17, 1),       # negative cell
+        (8, 8, d, 0.0, 3.17, 1),       # zero dt
+        (8, 8, d, dt, 0.5, 1),         # eps_r < 1
+        (8, 8, d, dt, 3.17, 2),        # no CPML on the 2D grid
+    ]
+    for a in cases:
+        h = C.c_void_p()
+        assert fd.cyl_create(C.byref(h), *a, None) == -1, a
+        assert not h.value
+    h = C.c_void_p()
+    dt_max = d * math.sqrt(W.EPS_R_ICE) / (W.C0 * math.sqrt(2.0))
+    assert fd.cyl_create(C.byref(h), 8, 8, d, dt_max * 1.001, W.EPS_R_ICE, 1, None) == -2
+    assert fd.cyl_step(None, 1) == -1 and fd.cyl_sync(None) == -1 and fd.cyl_set_kernel(None, 1, 0) == -1
+    fd.cyl_destroy(None)
 
 
 # ---- the library's host tables against the oracle's -------------------------

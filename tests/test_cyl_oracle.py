@@ -123,3 +123,39 @@ def test_zero_source_and_linearity():
     z.set_probes([[0.05, 0.2]])
     z.step(30)
     assert np.all(z.traces() == 0)
+
+
+def test_patch_matches_full_grid_inside_its_dependency_cone():
+    """A patch (rows i0.., columns j0..) advanced n steps reproduces the full
+    grid wherever the cells are more than n + 1 cells from an edge of the patch
+    that is not an edge of the full grid (each step reaches one cell)."""
+    rng = np.random.default_rng(11)
+    nr, nz, d, n = 40, 60, 0.01, 9
+    dt = O.courant_dt(d, 3.17)
+    q = -1e-12 * np.exp(-0.5 * ((np.arange(40) - 12) / 5.0) ** 2)
+    w = np.array([0.3, 0.25, 0.2, 0.15, 0.1])
+    for boundary in (O.PEC, O.MUR1):
+        full = O.CylOracle(nr, nz, d, dt, 3.17, boundary=boundary)
+        full.Er[:] = rng.normal(size=full.Er.shape)
+        full.Ez[:] = rng.normal(size=full.Ez.shape)
+        full.Hp[:] = rng.normal(size=full.Hp.shape) / 212.0
+        E0 = (full.Er.copy(), full.Ez.copy(), full.Hp.copy())
+        full.set_shower(q, 0.123, 0.01, O.C0, w)
+        full.step(n)
+        for i0, j0 in ((0, 0), (3, 17), (18, 25), (14, 0)):
+            pr, pz = nr - i0, nz - j0
+            p = O.CylOracle(pr, pz, d, dt, 3.17, boundary=boundary, i0=i0)
+            p.Er[:] = E0[0][i0:, j0:]
+            p.Ez[:] = E0[1][i0:, j0:]
+            p.Hp[:] = E0[2][i0:, j0:]
+            p.set_shower(q, 0.123 - j0 * d, 0.01, O.C0, w)
+            p.step(n)
+            lo_i = 0 if i0 == 0 else n + 2
+            lo_j = 0 if j0 == 0 else n + 2
+            for a, b in ((p.Er, full.Er[i0:, j0:]), (p.Ez, full.Ez[i0:, j0:]), (p.Hp, full.Hp[i0:, j0:])):
+                sl = (slice(lo_i, None), slice(lo_j, None))
+                scale = np.abs(b).max()
+                assert np.abs(a[sl] - b[sl]).max() <= 1e-12 * scale, (boundary, i0, j0)
+            # the cone is tight: one cell closer to the cut, the patch differs
+            if i0 > 0:
+                assert np.abs(p.Ez[n - 1] - full.Ez[i0 + n - 1, j0:]).max() > 1e-9 * np.abs(full.Ez).max()

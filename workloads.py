@@ -22,6 +22,22 @@ The paper uses a parameterised shower instead of Monte Carlo output
                  of 3-6 Gaisser-Hillas subshowers spread over 40 m (seed 3003);
                  256 detectors at r in [2, 10] m.
 
+2D axisymmetric grids (the paper's own formulation, Table I):
+
+* ``cyl_table1(n)`` n x n cells (nr = nz = n) over 40.96 m x 40.96 m, half the
+                 2D Courant step, Mur-1, n steps (Table I's rates grow as
+                 N_side, read as one step per cell of the side); the paper's
+                 Gaussian shower model (Sec. III.B: longitudinal l = 2 m,
+                 radial sigma_r = 5 cm) given as a 256-bin charge table and
+                 ring weights, moving at c from 8 l before its maximum; 64
+                 detectors at R in [2, 0.4 n d] m, theta in [40, 70] deg
+                 around the maximum (seed 4004).  The 2D solver takes tables,
+                 so both sides receive the same tables.
+* ``cyl_field(seed, comp, i, j, xp)`` counter-based initial field values
+                 (uniform in [-1/2, 1/2), E in V/m, H_phi divided by the
+                 impedance of ice), computable on any patch with NumPy or
+                 torch with identical float32 results.
+
 ``scaled(...)`` shrinks a workload to a grid the oracle finishes in seconds
 while keeping its physics (dx, dt, boundary, profile family, lateral family).
 """
@@ -268,6 +284,89 @@ def surrogate_runs(seed: int, n_runs: int, n_probes: int = 64, grid: Optional[Wo
         probes = _probes_cylindrical(rng, n_probes, axis, r_range[0], r_range[1], z_range[0], z_range[1], g.dx, box)
         runs.append({"z1": [z1], "zmax": [zmax], "lam": [lam], "nmax": [nmax], "probes_xyz": probes})
     return runs
+
+
+@dataclasses.dataclass
+class CylWorkload:
+    name: str
+    nr: int
+    nz: int
+    d: float
+    dt: float
+    eps_r: float
+    boundary: int
+    steps: int
+    q: np.ndarray          # charge per bin (C)
+    z0: float              # position of bin 0 (m)
+    bin_dz: float
+    v: float
+    w: np.ndarray          # ring weights, sum 1
+    probes_rz: np.ndarray  # [n, 2] (r, z) in metres
+
+    @property
+    def cells(self) -> int:
+        return self.nr * self.nz
+
+    def describe(self) -> dict:
+        return {"workload": self.name, "grid_rz": [self.nr, self.nz], "d_m": self.d, "dt_s": self.dt,
+                "eps_r": self.eps_r, "boundary": {PEC: "pec", MUR1: "mur1"}[self.boundary],
+                "steps": self.steps, "rings": int(len(self.w)), "probes": int(len(self.probes_rz))}
+
+
+def courant_dt_2d(d: float, eps_r: float) -> float:
+    """dt = 0.5 d sqrt(eps_r) / (c sqrt 2): half the 2D Courant limit."""
+    return 0.5 * d * math.sqrt(eps_r) / (C0 * math.sqrt(2.0))
+
+
+def cyl_table1(n: int = 8192, seed: int = 4004, extent_m: float = 40.96, steps: Optional[int] = None,
+               n_probes: int = 64, l_m: float = 2.0, sigma_r_m: float = 0.05, q_max: float = -1e-9,
+               boundary: int = MUR1) -> CylWorkload:
+    d = extent_m / n
+    dt = courant_dt_2d(d, EPS_R_ICE)
+    rng = np.random.default_rng(seed)
+    z_max = extent_m * (0.45 + 0.1 * rng.random())
+    n_bins = 256
+    z0 = z_max - 4.0 * l_m
+    bin_dz = 8.0 * l_m / (n_bins - 1)
+    zb = z0 + bin_dz * np.arange(n_bins)
+    q = q_max * np.exp(-0.5 * ((zb - z_max) / l_m) ** 2)
+    # ring weights of the radial Gaussian: ring i covers [(i - 1/2) d, (i + 1/2) d]
+    n_rings = max(1, min(n, int(math.ceil(3.0 * sigma_r_m / d)) + 1))
+    edges = np.concatenate([[0.0], (np.arange(n_rings) + 0.5) * d])
+    cdf = 1.0 - np.exp(-0.5 * (edges / sigma_r_m) ** 2)
+    w = np.diff(cdf)
+    w = w / w.sum()
+    R = rng.uniform(min(2.0, 0.1 * extent_m), 0.4 * extent_m, n_probes)
+    th = np.radians(rng.uniform(40.0, 70.0, n_probes))
+    rz = np.stack([R * np.sin(th), z_max + R * np.cos(th)], axis=1)
+    rz[:, 0] = np.clip(rz[:, 0], 0.0, (n - 1) * d)
+    rz[:, 1] = np.clip(rz[:, 1], d, (n - 1) * d)
+    return CylWorkload(f"cyl{n}x{n}", n, n, d, dt, EPS_R_ICE, boundary, n if steps is None else steps,
+                       q, z0, bin_dz, C0, w, rz)
+
+
+Z_ICE = 376.730313668 / math.sqrt(EPS_R_ICE)
+
+
+def cyl_field(seed: int, comp: int, i, j, xp=np):
+    """Initial value of component comp (0 E_r, 1 E_z, 2 H_phi) at integer
+    indices i, j (broadcast arrays of NumPy or torch int64): a 32-bit
+    multiply-xorshift hash of (seed, comp, i, j) mapped to [-1/2, 1/2), H_phi
+    divided by Z_ICE.  Identical float32 values from NumPy and torch."""
+    M = 0xFFFFFFFF
+    x = (i * 0x9E3779B1 + (j + 0x632BE5AB) * 0x85EBCA77 + (seed * 4 + comp) * 0xC2B2AE3D) & M
+    for _ in range(3):
+        x = x ^ (x >> 15)
+        x = (x * 0x2C1B3C6D) & M
+        x = x ^ (x >> 12)
+        x = (x * 0x297A2D39) & M
+    x = x ^ (x >> 15)
+    f = (x >> 8)
+    if xp is np:
+        v = f.astype(np.float32) * np.float32(2.0 ** -24) - np.float32(0.5)
+        return v / np.float32(Z_ICE) if comp == 2 else v
+    v = f.to(xp.float32) * (2.0 ** -24) - 0.5
+    return v / Z_ICE if comp == 2 else v
 
 
 WORKLOADS = {"parity96": parity96, "greisen384": greisen384, "gh640": gh640,
