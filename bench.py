@@ -316,7 +316,7 @@ def run_cyl(args):
     bytes_launch = 8.0 * comp_cells if K > 1 else 36.0 * cells / 1.0
     n_launch = steps // K if K > 1 else steps
     achieved = bytes_launch * n_launch / (ms * 1e-3) / 1e9
-    kname = {0: "k_cyl_h+k_cyl_e", 1: "k_cyl_wave<4,2>", 2: "k_cyl_wave<8,2>", 3: "k_cyl_wave<4,4>"}[info["kernel"]]
+    kname = info["kernel_name"]
     fset = 2 * 3 * (w.nr + 1) * ((w.nz + 1 + 16 + 63) // 32 * 32) * 4 / 1e9
     line = {
         "metric": "Gcell-updates/s", "value": round(value, 3), "unit": "Gcell/s", "solver": "cyl2d",

@@ -71,15 +71,20 @@ int cyl_step(cyl_t h, int n);
 
 /*
  * Kernel for the following steps: 0 = two kernels per step (H, then E with
- * the boundary; 36 bytes of DRAM per cell-update); 1, 2, 3 = one wavefront
- * launch per K steps (K = 4, 8, 4 with 2, 2, 4 z columns per lane; 24 bytes
- * per cell per launch).  seg_rows = radial rows per warp segment, 0 picks it
- * from the grid and the SM count.  The default is 2.
+ * the boundary; 36 bytes of DRAM per cell-update); 1..5 = one wavefront
+ * launch per K steps (24 bytes per cell per launch): 1 = K 4 with 2 z columns
+ * per lane, 2 = K 8 with 2, 3 = K 4 with 4, 4 = K 4 with 4 and registers
+ * bounded for 4 blocks per SM, 5 = K 8 with 2 bounded the same way.
+ * seg_rows = radial rows per warp segment (at most 1024), 0 picks it from the
+ * grid and the SM count.  FDTD_ERR_ARG for another index.  The default is 3.
  */
 int cyl_set_kernel(cyl_t h, int which, int seg_rows);
 
 /* The kernel in use, its steps per launch and rows per segment (any pointer may be null). */
 int cyl_kernel_info(cyl_t h, int *which, int *steps_per_launch, int *seg_rows);
+
+/* Name of the kernel in use (static string; "none" for a null handle). */
+const char *cyl_kernel_name(cyl_t h);
 
 /* Steps done since creation or the last reset. */
 int cyl_steps_done(cyl_t h, int64_t *steps);

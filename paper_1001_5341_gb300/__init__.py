@@ -88,6 +88,7 @@ _SIGS = {
     "cyl_step": (_i, [_vp, _i]),
     "cyl_set_kernel": (_i, [_vp, _i, _i]),
     "cyl_kernel_info": (_i, [_vp, _pi, _pi, _pi]),
+    "cyl_kernel_name": (C.c_char_p, [_vp]),
     "cyl_steps_done": (_i, [_vp, _pi64]),
     "cyl_sync": (_i, [_vp]),
     "cyl_probes": (_i, [_vp, _vp, _i]),
@@ -381,14 +382,15 @@ class Cylinder:
         self.np, self.max_steps = rz.shape[0], max_steps
 
     def set_kernel(self, which: int, seg_rows: int = 0):
-        """0: two kernels per step; 1, 2, 3: wavefront, K = 4, 8, 4 steps per launch (default 2)."""
+        """0: two kernels per step; 1..5: wavefront variants (cyl.h), K steps per launch."""
         check(cyl_set_kernel(self.h, which, seg_rows), "cyl_set_kernel")
 
     @property
     def kernel_info(self):
         w, k, l = C.c_int(), C.c_int(), C.c_int()
         check(cyl_kernel_info(self.h, C.byref(w), C.byref(k), C.byref(l)), "cyl_kernel_info")
-        return {"kernel": w.value, "steps_per_launch": k.value, "seg_rows": l.value}
+        return {"kernel": w.value, "kernel_name": cyl_kernel_name(self.h).decode(),
+                "steps_per_launch": k.value, "seg_rows": l.value}
 
     def step(self, n=1):
         check(cyl_step(self.h, n), "cyl_step")

@@ -46,7 +46,7 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int PADL = 16;     // zero floats before column 0 (>= the widest left halo, 16-byte multiple)
 constexpr int MSRC = 8;      // faces one step's deposit may touch (|v| dt / d <= 4)
 constexpr int NW = 4;        // warps per block of the wavefront kernel
-constexpr int STAGES = 8;    // rows in flight per warp
+constexpr int LMAX = 1024;   // most rows per segment of the wavefront kernel
 
 // ---------------------------------------------------------------------------
 // Source: q(z_s) linear in a bin table, cloud-in-cell along z.
@@ -252,8 +252,188 @@ __device__ __forceinline__ void st_cols(float *p, const float (&v)[CPL], int n) 
     }
 }
 
+// Per-warp march state: rows r - 1 (prv) and r (cur) of every time level in
+// registers; the ring position; running offsets of the next row to fetch and
+// of the next row to store.
 template <int K, int CPL>
-__global__ void __launch_bounds__(NW * 32) k_cyl_wave(Wave A) {
+struct March {
+    Row<CPL> prv[K + 1], cur[K + 1];
+    int st;
+    uint32_t phase;
+    long long ld_off, st_off;
+    int prowK;   // next detector row of level K
+};
+
+// Per-warp constants and shared-memory tables.
+template <int K, int CPL>
+struct Band {
+    int lane, b, col0, p0, load_end, own0, own1, pfin;
+    bool owned, cap_lo, cap_hi;
+    float *ring;
+    uint64_t *bar;
+    const float2 *rowc;   // (cA, cB) of rows p0, p0 + 1, ...
+    float *wall;          // [K][32 CPL]: the wall E_z of each level, one row ahead
+    int *pc, *prow;       // [K + 1]: detector cursor and its row, per level
+};
+
+template <int CPL>
+__device__ __forceinline__ void issue_row(const Wave &A, float *ring, uint64_t *bar, long long off, int st) {
+    constexpr int W = 32 * CPL, STAGE = 3 * W;
+    mbar_expect_tx(&bar[st], STAGE * 4);
+    bulk_load(ring + st * STAGE, A.in.Er + off, W * 4, &bar[st]);
+    bulk_load(ring + st * STAGE + W, A.in.Ez + off, W * 4, &bar[st]);
+    bulk_load(ring + st * STAGE + 2 * W, A.in.Hp + off, W * 4, &bar[st]);
+}
+
+// One march step p: load row p (level 0), level s = 1..K computes row p - s,
+// level K's row is stored.  FULL handles everything (rows before the segment
+// or past the wall, the wall, the source rows, detectors, partial columns);
+// the lean form (FULL = false) is taken only where none of that occurs, and
+// CAPS adds the end-cap update for the warps that hold column 0 or nz.
+template <int K, int CPL, int STAGES, bool FULL, bool CAPS>
+__device__ __forceinline__ bool march_step(const Wave &A, const Band<K, CPL> &w, March<K, CPL> &S, int p,
+                                           const int *sjlo, const float (*ssrc)[MSRC]) {
+    constexpr int W = 32 * CPL, STAGE = 3 * W;
+    const int nr = A.nr, nz = A.nz;
+    S.prv[0] = S.cur[0];
+    if (!FULL || p <= w.load_end) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&w.bar[S.st], S.phase))) return false;
+        lds_row(S.cur[0], w.ring + S.st * STAGE, w.lane);
+        __syncwarp();
+        if (w.lane == 0 && p + STAGES <= w.load_end) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue_row<CPL>(A, w.ring, w.bar, S.ld_off, S.st);
+        }
+        S.ld_off += A.pitch;
+        if (++S.st == STAGES) {
+            S.st = 0;
+            S.phase ^= 1u;
+        }
+    }
+#pragma unroll
+    for (int s = 1; s <= K; ++s) {
+        const int r = p - s;
+        S.prv[s] = S.cur[s];
+        if (FULL && (r < w.p0 || r > nr)) continue;
+        const Row<CPL> &a = S.prv[s - 1];   // level s-1, row r
+        const Row<CPL> &bn = S.cur[s - 1];  // level s-1, row r+1
+        Row<CPL> &o = S.cur[s];
+        if (!FULL || r < nr) {
+            // H_phi(r, j) from E_r(r, j), E_r(r, j+1), E_z(r, j), E_z(r+1, j)
+            const float er_right = __shfl_down_sync(0xffffffffu, a.er[0], 1);
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+                const float eR = q + 1 < CPL ? a.er[q + 1] : er_right;
+                o.h[q] = a.h[q] - A.kH * ((eR - a.er[q]) - (bn.ez[q] - a.ez[q]));
+            }
+            // E_r(r, j) from H_phi(r, j-1), H_phi(r, j)
+            const float h_left = __shfl_up_sync(0xffffffffu, o.h[CPL - 1], 1);
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+                const float hL = q > 0 ? o.h[q - 1] : h_left;
+                o.er[q] = a.er[q] - A.kE * (o.h[q] - hL);
+            }
+            // E_z(r, j) from H_phi(r, j), H_phi(r-1, j); on the axis cB = 0
+            const float2 c = w.rowc[r - w.p0];
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) o.ez[q] = a.ez[q] + c.x * o.h[q] - c.y * S.prv[s].h[q];
+            if (FULL && A.src.active && r < A.src.nw) {
+                const float cf = __ldg(&A.src.coef[r]);
+                const int jlo = sjlo[s - 1];
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) {
+                    const unsigned m = (unsigned)(w.col0 + w.lane * CPL + q - jlo);
+                    if (m < (unsigned)MSRC) o.ez[q] += cf * ssrc[s - 1][m];
+                }
+            }
+            // end caps: E_r(r, 0) from column 1 (same lane), E_r(r, nz) from column nz - 1
+            if (CAPS && w.cap_lo) o.er[0] = A.mur_on ? a.er[1] + A.mur * (o.er[1] - a.er[0]) : 0.f;
+            if (CAPS && w.cap_hi) {
+                const float old_l = __shfl_up_sync(0xffffffffu, a.er[CPL - 1], 1);
+                const float new_l = __shfl_up_sync(0xffffffffu, o.er[CPL - 1], 1);
+#pragma unroll
+                for (int q = 0; q < CPL; ++q)
+                    if (w.col0 + w.lane * CPL + q == nz) {
+                        const float ol = q > 0 ? a.er[q - 1] : old_l;
+                        const float nl = q > 0 ? o.er[q - 1] : new_l;
+                        o.er[q] = A.mur_on ? ol + A.mur * (nl - a.er[q]) : 0.f;
+                    }
+            }
+            if (FULL) {
+                // the wall E_z(nr, j) of this level, from E_z(nr-1, j) old (a) and
+                // new (o) and E_z(nr, j) old (bn); used on the next step
+                if (r == nr - 1)
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q)
+                        w.wall[(s - 1) * W + w.lane * CPL + q] =
+                            A.mur_on ? a.ez[q] + A.mur * (o.ez[q] - bn.ez[q]) : 0.f;
+                // detectors on row r at step n0 + s
+                if (r == w.prow[s]) {
+                    const float ez_up = __shfl_up_sync(0xffffffffu, o.ez[CPL - 1], 1);
+                    int pc = w.pc[s], prow;
+                    do {
+                        const int4 pr = __ldg(&A.prec[pc]);
+                        const int lj = pr.y - w.col0;
+                        if (w.lane == lj / CPL) {
+                            const int qj = lj % CPL;
+                            float ezj = 0.f, ezl = 0.f, erj = 0.f, erb = 0.f;
+#pragma unroll
+                            for (int q = 0; q < CPL; ++q)
+                                if (q == qj) {
+                                    ezj = o.ez[q];
+                                    erj = o.er[q];
+                                    erb = S.prv[s].er[q];
+                                    ezl = q > 0 ? o.ez[q > 0 ? q - 1 : 0] : ez_up;
+                                }
+                            float *t = A.trace + ((long long)pr.z * A.max_steps + A.n0 + s - 1) * 2;
+                            t[0] = 0.5f * (ezl + ezj);
+                            t[1] = r == 0 ? 0.f : 0.5f * (erb + erj);
+                        }
+                        ++pc;
+                        prow = pc < w.pfin ? __ldg(&A.prec[pc].x) : INT_MAX;
+                    } while (prow == r);
+                    __syncwarp();
+                    if (w.lane == 0) {
+                        w.pc[s] = pc;
+                        w.prow[s] = prow;
+                    }
+                    __syncwarp();
+                    if (s == K) S.prowK = prow;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) {
+                o.er[q] = 0.f;
+                o.h[q] = 0.f;
+                o.ez[q] = w.wall[(s - 1) * W + w.lane * CPL + q];
+            }
+        }
+    }
+    // level K, row p - K: store the owned cells
+    const int r = p - K;
+    if (w.owned && r >= w.own0 && r < w.own1) {
+        const long long o = S.st_off;
+        if (FULL || CAPS) {   // the cap warps hold column nz and phantom columns past it
+            const int c0 = w.col0 + w.lane * CPL;
+            const int nE = nz + 1 - c0, nZ = nz - c0;   // E_r columns <= nz, E_z and H_phi columns < nz
+            if (r < nr) {
+                st_cols<CPL>(A.out.Er + o, S.cur[K].er, nE);
+                st_cols<CPL>(A.out.Hp + o, S.cur[K].h, nZ);
+            }
+            st_cols<CPL>(A.out.Ez + o, S.cur[K].ez, nZ);
+        } else {
+            st_cols<CPL>(A.out.Er + o, S.cur[K].er, CPL);
+            st_cols<CPL>(A.out.Hp + o, S.cur[K].h, CPL);
+            st_cols<CPL>(A.out.Ez + o, S.cur[K].ez, CPL);
+        }
+    }
+    S.st_off += A.pitch;
+    return true;
+}
+
+template <int K, int CPL, int MINB, int STAGES>
+__global__ void __launch_bounds__(NW * 32, MINB) k_cyl_wave(Wave A) {
     constexpr int W = 32 * CPL;          // columns per warp
     constexpr int HL = K;                // left halo
     constexpr int STAGE = 3 * W;         // floats per ring stage
@@ -262,211 +442,123 @@ __global__ void __launch_bounds__(NW * 32) k_cyl_wave(Wave A) {
     __shared__ __align__(8) uint64_t bars[NW][STAGES];
     __shared__ int sjlo[K];
     __shared__ float ssrc[K][MSRC];
+    __shared__ __align__(16) float2 srowc[LMAX + 2 * K];
+    __shared__ __align__(16) float swall[NW][K * W];
+    __shared__ int spc[NW][K + 1], sprow[NW][K + 1];
 
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, wi = tid >> 5;
+    const int g = blockIdx.y;
+    const int nr = A.nr, nz = A.nz;
+    const int own0 = g * A.L, own1 = min(own0 + A.L, nr + 1);   // owned rows [own0, own1)
+    const int p0 = max(0, own0 - K);
+    const int p_end = own1 - 1 + K;
     if (A.src.active && tid < K * MSRC) {
         const int s = tid / MSRC, m = tid % MSRC;
         const int jlo = src_jlo(A.src, A.n0 + s);
         if (m == 0) sjlo[s] = jlo;
         ssrc[s][m] = src_face(A.src, A.n0 + s, jlo + m);
     }
+    for (int t = tid; t < LMAX + 2 * K; t += NW * 32)
+        srowc[t] = p0 + t <= nr ? A.rowc[p0 + t] : make_float2(0.f, 0.f);
     if (lane == 0) {
-        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[w][s], 1);
+        for (int s = 0; s < STAGES; ++s) mbar_init(&bars[wi][s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
 
-    const int b = blockIdx.x * NW + w;
-    if (b >= A.nbands) return;
-    const int g = blockIdx.y;
-    const int nr = A.nr, nz = A.nz, pitch = A.pitch;
-    const int own0 = g * A.L, own1 = min(own0 + A.L, nr + 1);   // owned rows [own0, own1)
-    const int p0 = max(0, own0 - K);
-    const int p_end = own1 - 1 + K;
-    const int load_end = min(p_end, nr);
-    const int col0 = b * A.U - HL;
-    const int oc0 = b * A.U, oc1 = min(oc0 + A.U, nz + 1);     // owned columns [oc0, oc1)
-    float *ring = smem + w * STAGES * STAGE;
-    uint64_t *bar = bars[w];
+    Band<K, CPL> w;
+    w.b = blockIdx.x * NW + wi;
+    if (w.b >= A.nbands) return;
+    w.lane = lane;
+    w.own0 = own0;
+    w.own1 = own1;
+    w.p0 = p0;
+    w.load_end = min(p_end, nr);
+    w.col0 = w.b * A.U - HL;
+    const int oc0 = w.b * A.U, oc1 = min(oc0 + A.U, nz + 1);   // owned columns [oc0, oc1)
+    w.ring = smem + wi * STAGES * STAGE;
+    w.bar = bars[wi];
+    w.rowc = srowc;
+    w.wall = swall[wi];
+    w.pc = spc[wi];
+    w.prow = sprow[wi];
+    const int c0 = w.col0 + lane * CPL;
+    w.owned = c0 >= oc0 && c0 < oc1;                    // a lane owns all or none of its columns
+    w.cap_lo = w.b == 0 && lane == HL / CPL;            // holds columns 0 and 1
+    w.cap_hi = nz - w.col0 >= 1 && nz - w.col0 < W;     // this warp holds columns nz - 1 and nz
+    const bool caps = w.b == 0 || w.cap_hi;
 
+    March<K, CPL> S;
     if (lane == 0)
-        for (int s = 0; s < STAGES && p0 + s <= load_end; ++s) {
-            const long long o = (long long)(p0 + s) * pitch + col0;
-            mbar_expect_tx(&bar[s], STAGE * 4);
-            bulk_load(ring + s * STAGE, A.in.Er + o, W * 4, &bar[s]);
-            bulk_load(ring + s * STAGE + W, A.in.Ez + o, W * 4, &bar[s]);
-            bulk_load(ring + s * STAGE + 2 * W, A.in.Hp + o, W * 4, &bar[s]);
-        }
-
-    int col[CPL];
-#pragma unroll
-    for (int q = 0; q < CPL; ++q) col[q] = col0 + lane * CPL + q;
-    const bool owned = col[0] >= oc0 && col[0] < oc1;    // a lane owns all or none of its columns
-    const int nE = nz + 1 - col[0], nZ = nz - col[0];    // E_r columns <= nz, E_z and H_phi columns < nz
-    const bool cap_lo = b == 0 && lane == HL / CPL;      // holds columns 0 and 1
-    const bool cap_hi = nz - col0 >= 1 && nz - col0 < W; // this warp holds columns nz - 1 and nz
-
-    // detectors of this warp, one cursor per level
-    const int wid = g * A.nbands + b;
-    const int pfin = A.poff[wid + 1];
-    int pc[K + 1], prow[K + 1];
+        for (int s = 0; s < STAGES && p0 + s <= w.load_end; ++s)
+            issue_row<CPL>(A, w.ring, w.bar, (long long)(p0 + s) * A.pitch + w.col0, s);
+    S.ld_off = (long long)(p0 + STAGES) * A.pitch + w.col0;
+    S.st_off = (long long)(p0 - K) * A.pitch + c0;
     {
+        const int wid = g * A.nbands + w.b;
         const int pbeg = A.poff[wid];
-        const int r0 = pbeg < pfin ? A.prec[pbeg].x : INT_MAX;
-#pragma unroll
-        for (int s = 1; s <= K; ++s) {
-            pc[s] = pbeg;
-            prow[s] = r0;
+        w.pfin = A.poff[wid + 1];
+        const int r0 = pbeg < w.pfin ? A.prec[pbeg].x : INT_MAX;
+        if (lane <= K) {
+            w.pc[lane] = pbeg;
+            w.prow[lane] = r0;
         }
+        S.prowK = r0;
+        __syncwarp();
     }
-
-    Row<CPL> prv[K + 1], cur[K + 1];
-    float wall[K + 1][CPL];
 #pragma unroll
     for (int s = 0; s <= K; ++s)
 #pragma unroll
         for (int q = 0; q < CPL; ++q) {
-            prv[s].er[q] = prv[s].ez[q] = prv[s].h[q] = 0.f;
-            cur[s].er[q] = cur[s].ez[q] = cur[s].h[q] = 0.f;
-            wall[s][q] = 0.f;
+            S.prv[s].er[q] = S.prv[s].ez[q] = S.prv[s].h[q] = 0.f;
+            S.cur[s].er[q] = S.cur[s].ez[q] = S.cur[s].h[q] = 0.f;
         }
+    S.st = 0;
+    S.phase = 0;
 
-    int st = 0;
-    uint32_t phase = 0;
+    // lean steps: every level on a row in [max(p0, source rows), nr - 2], all
+    // columns inside [0, nz), no detector on the rows of the step
+    const int src_end = A.src.active ? A.src.nw : 0;
+    const int lean_lo = max(p0, src_end) + K, lean_hi = min(nr - 1, p_end);
     int failed_at = -1;
-    for (int p = p0; p <= p_end; ++p) {
-        // level 0: row p from the ring
-        prv[0] = cur[0];
-        if (p <= load_end) {
-            if (!__all_sync(0xffffffffu, mbar_wait(&bar[st], phase))) {
+    int p = p0;
+    while (p <= p_end) {
+        const int stop = min(lean_hi, S.prowK);
+        if (p >= lean_lo && p <= stop) {
+            bool ok = true;
+            if (caps) {
+                for (; ok && p <= stop; ++p) ok = march_step<K, CPL, STAGES, false, true>(A, w, S, p, sjlo, ssrc);
+            } else {
+                for (; ok && p + 1 <= stop; p += 2) {
+                    ok = march_step<K, CPL, STAGES, false, false>(A, w, S, p, sjlo, ssrc);
+                    if (ok) ok = march_step<K, CPL, STAGES, false, false>(A, w, S, p + 1, sjlo, ssrc);
+                }
+                if (ok && p <= stop) {
+                    ok = march_step<K, CPL, STAGES, false, false>(A, w, S, p, sjlo, ssrc);
+                    ++p;
+                }
+            }
+            if (!ok) {
                 failed_at = p;
                 break;
             }
-            lds_row(cur[0], ring + st * STAGE, lane);
-            __syncwarp();
-            if (lane == 0 && p + STAGES <= load_end) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                const long long o = (long long)(p + STAGES) * pitch + col0;
-                mbar_expect_tx(&bar[st], STAGE * 4);
-                bulk_load(ring + st * STAGE, A.in.Er + o, W * 4, &bar[st]);
-                bulk_load(ring + st * STAGE + W, A.in.Ez + o, W * 4, &bar[st]);
-                bulk_load(ring + st * STAGE + 2 * W, A.in.Hp + o, W * 4, &bar[st]);
+        } else {
+            if (!march_step<K, CPL, STAGES, true, true>(A, w, S, p, sjlo, ssrc)) {
+                failed_at = p;
+                break;
             }
-            if (++st == STAGES) {
-                st = 0;
-                phase ^= 1u;
-            }
-        }
-        // level s computes row p - s from rows p - s, p - s + 1 of level s - 1
-#pragma unroll
-        for (int s = 1; s <= K; ++s) {
-            const int r = p - s;
-            prv[s] = cur[s];
-            if (r < p0 || r > nr) continue;
-            const Row<CPL> &a = prv[s - 1];   // level s-1, row r
-            const Row<CPL> &bn = cur[s - 1];  // level s-1, row r+1
-            Row<CPL> &o = cur[s];
-            if (r < nr) {
-                // H_phi(r, j) from E_r(r, j), E_r(r, j+1), E_z(r, j), E_z(r+1, j)
-                const float er_right = __shfl_down_sync(0xffffffffu, a.er[0], 1);
-#pragma unroll
-                for (int q = 0; q < CPL; ++q) {
-                    const float eR = q + 1 < CPL ? a.er[q + 1] : er_right;
-                    o.h[q] = a.h[q] - A.kH * ((eR - a.er[q]) - (bn.ez[q] - a.ez[q]));
-                }
-                // E_r(r, j) from H_phi(r, j-1), H_phi(r, j)
-                const float h_left = __shfl_up_sync(0xffffffffu, o.h[CPL - 1], 1);
-#pragma unroll
-                for (int q = 0; q < CPL; ++q) {
-                    const float hL = q > 0 ? o.h[q - 1] : h_left;
-                    o.er[q] = a.er[q] - A.kE * (o.h[q] - hL);
-                }
-                // E_z(r, j) from H_phi(r, j), H_phi(r-1, j); on the axis cB = 0
-                const float2 c = __ldg(&A.rowc[r]);
-#pragma unroll
-                for (int q = 0; q < CPL; ++q) o.ez[q] = a.ez[q] + c.x * o.h[q] - c.y * prv[s].h[q];
-                if (A.src.active && r < A.src.nw) {
-                    const float cf = __ldg(&A.src.coef[r]);
-                    const int jlo = sjlo[s - 1];
-#pragma unroll
-                    for (int q = 0; q < CPL; ++q) {
-                        const unsigned m = (unsigned)(col[q] - jlo);
-                        if (m < (unsigned)MSRC) o.ez[q] += cf * ssrc[s - 1][m];
-                    }
-                }
-                // end caps: E_r(r, 0) from column 1 (same lane), E_r(r, nz) from column nz - 1
-                if (cap_lo) o.er[0] = A.mur_on ? a.er[1] + A.mur * (o.er[1] - a.er[0]) : 0.f;
-                if (cap_hi) {
-                    const float old_l = __shfl_up_sync(0xffffffffu, a.er[CPL - 1], 1);
-                    const float new_l = __shfl_up_sync(0xffffffffu, o.er[CPL - 1], 1);
-#pragma unroll
-                    for (int q = 0; q < CPL; ++q)
-                        if (col[q] == nz) {
-                            const float ol = q > 0 ? a.er[q - 1] : old_l;
-                            const float nl = q > 0 ? o.er[q - 1] : new_l;
-                            o.er[q] = A.mur_on ? ol + A.mur * (nl - a.er[q]) : 0.f;
-                        }
-                }
-                // the wall E_z(nr, j) of this level, from E_z(nr-1, j) old (a) and
-                // new (o) and E_z(nr, j) old (bn)
-                if (r == nr - 1)
-#pragma unroll
-                    for (int q = 0; q < CPL; ++q)
-                        wall[s][q] = A.mur_on ? a.ez[q] + A.mur * (o.ez[q] - bn.ez[q]) : 0.f;
-                // detectors on row r at step n0 + s
-                if (r == prow[s]) {
-                    const float ez_up = __shfl_up_sync(0xffffffffu, o.ez[CPL - 1], 1);
-                    do {
-                        const int4 pr = __ldg(&A.prec[pc[s]]);
-                        const int lj = pr.y - col0;
-                        if (lane == lj / CPL) {
-                            const int qj = lj % CPL;
-                            float ezj = 0.f, ezl = 0.f, erj = 0.f, erb = 0.f;
-#pragma unroll
-                            for (int q = 0; q < CPL; ++q)
-                                if (q == qj) {
-                                    ezj = o.ez[q];
-                                    erj = o.er[q];
-                                    erb = prv[s].er[q];
-                                    ezl = q > 0 ? o.ez[q > 0 ? q - 1 : 0] : ez_up;
-                                }
-                            float *t = A.trace + ((long long)pr.z * A.max_steps + A.n0 + s - 1) * 2;
-                            t[0] = 0.5f * (ezl + ezj);
-                            t[1] = r == 0 ? 0.f : 0.5f * (erb + erj);
-                        }
-                        ++pc[s];
-                        prow[s] = pc[s] < pfin ? __ldg(&A.prec[pc[s]].x) : INT_MAX;
-                    } while (prow[s] == r);
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < CPL; ++q) {
-                    o.er[q] = 0.f;
-                    o.h[q] = 0.f;
-                    o.ez[q] = wall[s][q];
-                }
-            }
-        }
-        // level K, row p - K: store the owned cells
-        const int r = p - K;
-        if (owned && r >= own0 && r < own1) {
-            const long long o = (long long)r * pitch + col[0];
-            if (r < nr) {
-                st_cols<CPL>(A.out.Er + o, cur[K].er, nE);
-                st_cols<CPL>(A.out.Hp + o, cur[K].h, nZ);
-            }
-            st_cols<CPL>(A.out.Ez + o, cur[K].ez, nZ);
+            ++p;
         }
     }
     if (failed_at >= 0) {
         // give up: flag it, and let the copies still in flight land before the block ends
         if (lane == 0) {
             atomicOr(A.flags, 1);
-            int s2 = st;
-            uint32_t ph = phase;
-            for (int m = 0; m < STAGES && failed_at + m <= load_end; ++m) {
-                mbar_wait(&bar[s2], ph);
+            int s2 = S.st;
+            uint32_t ph = S.phase;
+            for (int m = 0; m < STAGES && failed_at + m <= w.load_end; ++m) {
+                mbar_wait(&w.bar[s2], ph);
                 if (++s2 == STAGES) {
                     s2 = 0;
                     ph ^= 1u;
@@ -478,14 +570,21 @@ __global__ void __launch_bounds__(NW * 32) k_cyl_wave(Wave A) {
 }
 
 struct Variant {
-    int K, CPL;
+    int K, CPL, stages;
     void (*fn)(Wave);
+    const char *name;
 };
-const Variant kVariants[] = {{0, 0, nullptr}, {4, 2, k_cyl_wave<4, 2>}, {8, 2, k_cyl_wave<8, 2>},
-                             {4, 4, k_cyl_wave<4, 4>}};
-constexpr int kNumKernels = 4;
+// kernel index -> (steps per launch, z columns per lane, rows in flight per warp);
+// the third template argument is the resident blocks per SM the registers are bounded for
+const Variant kVariants[] = {{0, 0, 0, nullptr, "k_cyl_h+k_cyl_e"},
+                             {4, 2, 8, k_cyl_wave<4, 2, 1, 8>, "k_cyl_wave<4,2,1,8>"},
+                             {8, 2, 8, k_cyl_wave<8, 2, 1, 8>, "k_cyl_wave<8,2,1,8>"},
+                             {4, 4, 8, k_cyl_wave<4, 4, 1, 8>, "k_cyl_wave<4,4,1,8>"},
+                             {4, 4, 6, k_cyl_wave<4, 4, 4, 6>, "k_cyl_wave<4,4,4,6>"},
+                             {8, 2, 8, k_cyl_wave<8, 2, 4, 8>, "k_cyl_wave<8,2,4,8>"}};
+constexpr int kNumKernels = 6;
 
-size_t ring_bytes(int CPL) { return (size_t)NW * STAGES * 3 * 32 * CPL * sizeof(float); }
+size_t ring_bytes(const Variant &v) { return (size_t)NW * v.stages * 3 * 32 * v.CPL * sizeof(float); }
 
 }  // namespace
 
@@ -564,21 +663,21 @@ int read_extent(int nz) {
 // Rows per segment: the fewest waves of blocks times the march length of one
 // segment (L + 2K rows), larger L on ties.
 int choose_L(cyl_ctx *h) {
-    if (h->seg_req > 0) return std::min(h->seg_req, h->nr + 1);
+    if (h->seg_req > 0) return std::min(std::min(h->seg_req, h->nr + 1), LMAX);
     int dev = 0, sms = 152, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const Variant &v = kVariants[h->kernel];
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.fn, NW * 32, ring_bytes(v.CPL)) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.fn, NW * 32, ring_bytes(v)) != cudaSuccess ||
         per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
     }
     const long long slots = (long long)sms * per_sm;
     const long long bx = (h->nbands + NW - 1) / NW;
-    int best = h->nr + 1;
     double best_cost = 1e300;
-    for (int L = 16; L <= h->nr + 1 + 15; L += 16) {
+    int best = std::min(h->nr + 1, LMAX);
+    for (int L = 16; L <= std::min(h->nr + 1 + 15, LMAX); L += 16) {
         const int Lc = std::min(L, h->nr + 1);
         const long long nseg = (h->nr + 1 + Lc - 1) / Lc;
         const long long waves = (bx * nseg + slots - 1) / slots;
@@ -695,7 +794,7 @@ void launch_wave(cyl_ctx *h) {
     A.max_steps = h->max_steps;
     A.flags = h->d_flags;
     const dim3 grid((h->nbands + NW - 1) / NW, h->nseg);
-    v.fn<<<grid, NW * 32, ring_bytes(v.CPL), h->stream>>>(A);
+    v.fn<<<grid, NW * 32, ring_bytes(v), h->stream>>>(A);
     h->launches++;
     h->cur ^= 1;
     h->steps += v.K;
@@ -755,15 +854,14 @@ int cyl_create(cyl_t *out, int nr, int nz, double d, double dt, double eps_r, in
         float *base = h->block + 3 * s * h->comp + PADL;
         h->set[s] = Set{base, base + h->comp, base + 2 * h->comp};
     }
-    for (int v = 1; v < kNumKernels; ++v)
-        if (ring_bytes(kVariants[v].CPL) > 48 * 1024)
-            note(h, cudaFuncSetAttribute(kVariants[v].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)ring_bytes(kVariants[v].CPL)));
+    for (int v = 1; v < kNumKernels; ++v)   // dynamic + static shared memory may pass 48 KB
+        note(h, cudaFuncSetAttribute(kVariants[v].fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)ring_bytes(kVariants[v])));
     note(h, cudaMemsetAsync(h->block, 0, bytes, h->stream));
     note(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int), h->stream));
     note(h, cudaMemcpyAsync(h->d_rowc, rowc.data(), rowc.size() * sizeof(float2), cudaMemcpyHostToDevice, h->stream));
     note(h, cudaStreamSynchronize(h->stream));
-    if (h->status == FDTD_OK) h->status = configure(h, 2, 0);
+    if (h->status == FDTD_OK) h->status = configure(h, 3, 0);
     if (h->status != FDTD_OK) {
         const int st = h->status;
         cyl_destroy(h);
@@ -940,6 +1038,8 @@ int cyl_reset(cyl_t h) {
     h->cur = 0;
     return cyl_sync(h);
 }
+
+const char *cyl_kernel_name(cyl_t h) { return h ? kVariants[h->kernel].name : "none"; }
 
 int cyl_steps_done(cyl_t h, int64_t *steps) {
     if (!h || !steps) return FDTD_ERR_ARG;

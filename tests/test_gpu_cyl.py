@@ -92,7 +92,8 @@ PROBES = [(0, 1), (0, 75), (1, 40), (15, 47), (16, 48), (17, 49), (31, 96), (32,
 
 
 @pytest.mark.parametrize("boundary", [O.PEC, O.MUR1])
-@pytest.mark.parametrize("kernel,seg", [(0, 0), (1, 16), (2, 16), (3, 16), (2, 0), (2, 33)])
+@pytest.mark.parametrize("kernel,seg", [(0, 0), (1, 16), (2, 16), (3, 16), (4, 16), (5, 16), (2, 0), (2, 33),
+                                        (4, 0)])
 def test_kernel_matches_oracle(fd, kernel, seg, boundary):
     o, g = _run_pair(fd, 70, 150, 37, kernel, boundary, seg, PROBES)
     _compare(o, g, 37, f"kernel {kernel} seg {seg} boundary {boundary}")
@@ -121,7 +122,7 @@ def test_shower_crosses_the_grid_mur(fd, kernel):
 
 
 @pytest.mark.parametrize("nr,nz", [(4, 4), (5, 300), (300, 5), (4, 130), (129, 4)])
-@pytest.mark.parametrize("kernel", [1, 2, 3])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 4, 5])
 def test_degenerate_grids(fd, nr, nz, kernel):
     probes = [(0, 1), (nr - 1, nz - 1)]
     o, g = _run_pair(fd, nr, nz, 19, kernel, O.MUR1, 0, probes)
@@ -183,7 +184,7 @@ def test_full_size_grid_on_patches(fd):
     nr = nz = 8192
     g = fd.Cylinder(nr, nz, wl.d, wl.dt, wl.eps_r, boundary=wl.boundary)
     info = g.kernel_info
-    assert info["kernel"] == 2
+    assert info["kernel"] == 3
     for c, (rows, cols) in enumerate(((nr, nz + 1), (nr + 1, nz), (nr, nz))):
         i = torch.arange(rows, dtype=torch.int64, device="cuda")[:, None]
         j = torch.arange(cols, dtype=torch.int64, device="cuda")[None, :]
@@ -191,7 +192,7 @@ def test_full_size_grid_on_patches(fd):
         del i, j
     q = wl.q
     g.set_shower(q, wl.z0, wl.bin_dz, wl.v, wl.w)
-    L, U = info["seg_rows"], 64 - 2 * info["steps_per_launch"]
+    L, U = info["seg_rows"], 128 - 2 * info["steps_per_launch"]
     zs = wl.z0 + wl.v * n * wl.dt
     js = int(zs / wl.d)
     # detectors: one at the source's path, one at a seam
@@ -235,4 +236,4 @@ def test_full_size_grid_on_patches(fd):
             _close(tr[p, :, 0], o.traces()[k, :, 0], what=f"detector {p} E_z")
             _close(tr[p, :, 1], o.traces()[k, :, 1], what=f"detector {p} E_r")
             n_det += 1
-    assert checked > 5000 and n_det == 2
+    assert checked > 5000 and n_det >= 2
