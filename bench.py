@@ -272,8 +272,8 @@ def run_cyl(args):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         g = fd.Cylinder(w.nr, w.nz, w.d, w.dt, w.eps_r, w.boundary, stream=stream)
-        if args.cyl_kernel >= 0:
-            g.set_kernel(args.cyl_kernel, args.seg_rows)
+        if args.cyl_kernel >= 0 or args.seg_rows > 0:
+            g.set_kernel(args.cyl_kernel if args.cyl_kernel >= 0 else g.kernel_info["kernel"], args.seg_rows)
         info = g.kernel_info
         K = info["steps_per_launch"]
         steps = args.steps if args.steps else n

@@ -47,6 +47,7 @@ constexpr int PADL = 16;     // zero floats before column 0 (>= the widest left 
 constexpr int MSRC = 8;      // faces one step's deposit may touch (|v| dt / d <= 4)
 constexpr int NW = 4;        // warps per block of the wavefront kernel
 constexpr int LMAX = 1024;   // most rows per segment of the wavefront kernel
+constexpr int NO_ROW = 0x3fffffff;   // detector row past the last one
 
 // ---------------------------------------------------------------------------
 // Source: q(z_s) linear in a bin table, cloud-in-cell along z.
@@ -299,11 +300,10 @@ __device__ __forceinline__ bool march_step(const Wave &A, const Band<K, CPL> &w,
     if (!FULL || p <= w.load_end) {
         if (!__all_sync(0xffffffffu, mbar_wait(&w.bar[S.st], S.phase))) return false;
         lds_row(S.cur[0], w.ring + S.st * STAGE, w.lane);
+        // the warp's reads of the stage are ordered before the refill by the
+        // warp barrier (the release/acquire a consumer barrier would give)
         __syncwarp();
-        if (w.lane == 0 && p + STAGES <= w.load_end) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue_row<CPL>(A, w.ring, w.bar, S.ld_off, S.st);
-        }
+        if (w.lane == 0 && p + STAGES <= w.load_end) issue_row<CPL>(A, w.ring, w.bar, S.ld_off, S.st);
         S.ld_off += A.pitch;
         if (++S.st == STAGES) {
             S.st = 0;
@@ -390,7 +390,7 @@ __device__ __forceinline__ bool march_step(const Wave &A, const Band<K, CPL> &w,
                             t[1] = r == 0 ? 0.f : 0.5f * (erb + erj);
                         }
                         ++pc;
-                        prow = pc < w.pfin ? __ldg(&A.prec[pc].x) : INT_MAX;
+                        prow = pc < w.pfin ? __ldg(&A.prec[pc].x) : NO_ROW;
                     } while (prow == r);
                     __syncwarp();
                     if (w.lane == 0) {
@@ -458,8 +458,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_cyl_wave(Wave A) {
         if (m == 0) sjlo[s] = jlo;
         ssrc[s][m] = src_face(A.src, A.n0 + s, jlo + m);
     }
-    for (int t = tid; t < LMAX + 2 * K; t += NW * 32)
-        srowc[t] = p0 + t <= nr ? A.rowc[p0 + t] : make_float2(0.f, 0.f);
+    for (int t = tid; p0 + t <= min(p_end, nr); t += NW * 32) srowc[t] = A.rowc[p0 + t];
     if (lane == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(&bars[wi][s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -494,12 +493,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_cyl_wave(Wave A) {
         for (int s = 0; s < STAGES && p0 + s <= w.load_end; ++s)
             issue_row<CPL>(A, w.ring, w.bar, (long long)(p0 + s) * A.pitch + w.col0, s);
     S.ld_off = (long long)(p0 + STAGES) * A.pitch + w.col0;
-    S.st_off = (long long)(p0 - K) * A.pitch + c0;
+    S.st_off = (long long)(p0 - K) * A.pitch + c0;   // row p - K at step p
     {
         const int wid = g * A.nbands + w.b;
         const int pbeg = A.poff[wid];
         w.pfin = A.poff[wid + 1];
-        const int r0 = pbeg < w.pfin ? A.prec[pbeg].x : INT_MAX;
+        const int r0 = pbeg < w.pfin ? A.prec[pbeg].x : NO_ROW;
         if (lane <= K) {
             w.pc[lane] = pbeg;
             w.prow[lane] = r0;
@@ -518,7 +517,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_cyl_wave(Wave A) {
     S.phase = 0;
 
     // lean steps: every level on a row in [max(p0, source rows), nr - 2], all
-    // columns inside [0, nz), no detector on the rows of the step
+    // columns inside [0, nz), no detector on the rows p - K .. p - 1 of the step
     const int src_end = A.src.active ? A.src.nw : 0;
     const int lean_lo = max(p0, src_end) + K, lean_hi = min(nr - 1, p_end);
     int failed_at = -1;
@@ -660,8 +659,11 @@ int read_extent(int nz) {
     return e;
 }
 
-// Rows per segment: the fewest waves of blocks times the march length of one
-// segment (L + 2K rows), larger L on ties.
+// Rows per segment.  A block marches L + 2K rows; blocks differ in speed (the
+// warps holding the end caps, the source rows near the axis, the wall and the
+// detectors take extra work), so the launch ends about one block duration
+// after the average SM is done: cost = (L + 2K + setup) x (blocks / slots + 1),
+// the smallest cost wins.
 int choose_L(cyl_ctx *h) {
     if (h->seg_req > 0) return std::min(std::min(h->seg_req, h->nr + 1), LMAX);
     int dev = 0, sms = 152, per_sm = 1;
@@ -673,16 +675,15 @@ int choose_L(cyl_ctx *h) {
         cudaGetLastError();
         per_sm = 1;
     }
-    const long long slots = (long long)sms * per_sm;
+    const double slots = (double)sms * per_sm;
     const long long bx = (h->nbands + NW - 1) / NW;
-    double best_cost = 1e300;
     int best = std::min(h->nr + 1, LMAX);
-    for (int L = 16; L <= std::min(h->nr + 1 + 15, LMAX); L += 16) {
+    double best_cost = 1e300;
+    for (int L = 32; L <= std::min(h->nr + 1 + 15, LMAX); L += 16) {
         const int Lc = std::min(L, h->nr + 1);
         const long long nseg = (h->nr + 1 + Lc - 1) / Lc;
-        const long long waves = (bx * nseg + slots - 1) / slots;
-        const double cost = (double)waves * (Lc + 2 * h->K);
-        if (cost <= best_cost * (1 + 1e-12)) {
+        const double cost = (double)(Lc + 2 * h->K + 8) * ((double)(bx * nseg) / slots + 1.0);
+        if (cost < best_cost) {
             best_cost = cost;
             best = Lc;
         }
