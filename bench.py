@@ -66,27 +66,34 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(files):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1001_5341_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, fn), "rb") as f:
-                h.update(fn.encode() + f.read())
+    for fn in files:
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_name, workload_name):
-    """DRAM bytes per cell-update from a committed ncu capture of this kernel,
-    or None when none exists or the kernel sources changed since."""
+def ncu_record(kernel_name, workload_name):
+    """The committed ncu DRAM capture of this kernel on this workload, or None
+    when none exists or a source file it lists changed since."""
     try:
         with open(TRAFFIC) as f:
             rec = json.load(f).get(kernel_name)
     except Exception:
         return None
-    if not rec or rec.get("source_hash") != kernel_source_hash():
+    if not rec or rec.get("workload") != workload_name:
         return None
-    return rec.get("dram_bytes_per_cell")
+    if rec.get("source_hash") != kernel_source_hash(rec.get("sources", [])):
+        return None
+    return rec
+
+
+def ncu_traffic(kernel_name, workload_name):
+    """DRAM bytes per cell-update of the 3D step kernel (see ncu_record)."""
+    rec = ncu_record(kernel_name, workload_name)
+    return rec.get("dram_bytes_per_cell") if rec else None
 
 
 class ClockSampler:
@@ -327,7 +334,8 @@ def run_cyl(args):
                    "inputs_vs_l2": f"fields {fset:.3f} GB vs 129 MB L2 (no flush: one timed call)"},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "bytes_per_launch_alg": bytes_launch, "steps_per_launch": K, "traffic": None,
+                     "bytes_per_launch_alg": bytes_launch, "steps_per_launch": K,
+                     "traffic": (ncu_record(kname, w.name) or {}).get("dram_bytes_per_launch"),
                      "single_step_equiv_GBps": round(24.0 * value, 1)},
         "e2e": {"value": round(ws * cells * steps / e2e_s / 1e9, 3), "unit": "Gcell/s",
                 "h2d_bytes_per_step": round((q.nbytes + wr.nbytes + rz.nbytes) / steps, 2),

@@ -475,10 +475,10 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
         __syncthreads();
         return false;
     }
-    if (!STAGE_IN_E && tid == 0 && rel + B.ns < B.nplanes) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    // the block barrier above orders every thread's reads of the stage
+    // before the refill (the release/acquire a consumer barrier would give)
+    if (!STAGE_IN_E && tid == 0 && rel + B.ns < B.nplanes)
         issue_plane(A, M, B, ring + s0i * B.stage, &bar[s0i], rel + B.ns);
-    }
 
     // ---- E phase ----
     if (L.roww && own) {
@@ -550,10 +550,7 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
     if (L.roww) { hxp = hxn; hyp = hyn; }
     if (STAGE_IN_E) {
         __syncthreads();  // the E psi of plane k are read: its stage is free
-        if (tid == 0 && rel + B.ns < B.nplanes) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue_plane(A, M, B, ring + s0i * B.stage, &bar[s0i], rel + B.ns);
-        }
+        if (tid == 0 && rel + B.ns < B.nplanes) issue_plane(A, M, B, ring + s0i * B.stage, &bar[s0i], rel + B.ns);
     }
     rp.s0 = s1i;
     rp.s1 = s1i + 1;
