@@ -349,6 +349,70 @@ def run_cyl(args):
     return line
 
 
+def run_adjoint(args):
+    """Gradient of a detector misfit with respect to a 256-bin charge table on
+    a 256 x 256 x 512 PEC grid (dx = 2 cm): the forward run and the adjoint
+    run, each timed on the device."""
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    import paper_1001_5341_gb300 as fd
+    from paper_1001_5341_gb300.adjoint import TraceModel
+
+    nx, ny, nz, dx = 256, 256, 512, 0.02
+    steps = args.steps or 2000
+    dt = W.courant_dt(dx, W.EPS_R_ICE)
+    rng = np.random.default_rng(5005 + rank)
+    n_bins, z0 = 256, 0.2
+    bin_dz = (nz * dx) / n_bins
+    q = fd.profile_gaussian(z0, bin_dz, n_bins, 4.0 + rng.random(), 1.2, -1e-9)
+    lw = fd.lateral_gaussian(4, 1.0)
+    cx, cy = nx // 2 * dx, ny // 2 * dx
+    r = rng.uniform(0.5, 2.2, 64)
+    ph = rng.uniform(0, 2 * np.pi, 64)
+    xyz = np.stack([cx + r * np.cos(ph), cy + r * np.sin(ph), rng.uniform(1.0, nz * dx - 1.0, 64)], axis=1)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sim = fd.Simulation(nx, ny, nz, dx, dt, W.EPS_R_ICE, boundary=fd.FDTD_PEC, stream=stream)
+        sim.set_probes(xyz, steps)
+        model = TraceModel(sim, z0, bin_dz, W.C0, lw, 4, steps)
+        qt = torch.tensor(q, requires_grad=True)
+        with torch.no_grad():
+            target = model(qt * 0.9)
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.5)   # the sampler's start-up stalls the driver for a moment
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        y = model(qt)
+        ev[1].record(stream)
+        loss = 0.5 * ((y.double() - target.double()) ** 2).sum()
+        loss.backward()
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        t_fwd = ev[0].elapsed_time(ev[1]) * 1e-3
+        t_all = ev[0].elapsed_time(ev[2]) * 1e-3
+        launches = sim.launches
+        g = qt.grad.numpy()
+        sim.close()
+    if rank != 0:
+        return None
+    cells = nx * ny * nz
+    t_adj = t_all - t_fwd
+    return {"metric": "gradient evaluations/s", "value": round(1.0 / t_all, 4), "unit": "gradients/s",
+            "solver": "adjoint", "n_gpus": ws, "steps": steps, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"pec{nx}x{ny}x{nz}", "dx_m": dx, "bins": n_bins, "probes": 64,
+                       "lateral_L": 4, "loss": "1/2 sum (traces - traces(0.9 q))^2"},
+            "forward_s": round(t_fwd, 4), "adjoint_s": round(t_adj, 4),
+            "forward_gcells": round(cells * steps / t_fwd / 1e9, 2),
+            "adjoint_gcells": round(cells * steps / t_adj / 1e9, 2),
+            "adjoint_over_forward": round(t_adj / t_fwd, 3),
+            "grad_norm": float(np.linalg.norm(g)), "gpu_launches": launches, "clocks": clk}
+
+
 # Table I: GTX285 seconds per N^2 run (step count not printed; read as N steps)
 PAPER_T_GPU = {256: 0.040, 512: 0.186, 1024: 1.167, 2048: 8.372, 4096: 67.617, 8192: 681.082}
 
@@ -486,15 +550,18 @@ def main():
     ap.add_argument("--nz", type=int, default=0,
                     help="z planes of a reduced grid with the benchmark physics (profiler captures "
                          "of a few GB); 0 = the benchmark grid")
-    ap.add_argument("--solver", choices=["yee3d", "cyl"], default="yee3d",
-                    help="cyl: the paper's 2D axisymmetric solver on an n x n grid (Table I)")
+    ap.add_argument("--solver", choices=["yee3d", "cyl", "adjoint"], default="yee3d",
+                    help="cyl: the paper's 2D axisymmetric solver on an n x n grid (Table I); "
+                         "adjoint: gradient of a detector misfit w.r.t. the charge table")
     ap.add_argument("--n", type=int, default=8192, help="cyl grid side")
     ap.add_argument("--cyl-kernel", type=int, default=-1, help="cyl kernel (-1: library default)")
     ap.add_argument("--seg-rows", type=int, default=0, help="cyl rows per segment (0: automatic)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.solver == "cyl":
+    if args.solver == "adjoint":
+        line = run_adjoint(args)
+    elif args.solver == "cyl":
         if args.impl == "reference":
             line = run_cyl_reference(args)
         else:

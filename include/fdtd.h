@@ -228,6 +228,31 @@ int fdtd_set_kernel(fdtd_t h, int which);
 /* Human-readable text of a status code (static string). */
 const char *fdtd_strerror(int status);
 
+/* ---- adjoint (PEC grids without CPML) ----------------------------------- */
+
+/*
+ * The step of Sec. III.A is linear in (E^n, H^{n-1/2}) and in the source; on
+ * the Yee grid with PEC walls its curls satisfy C_H = C_E^T, so its transpose
+ * is the same leapfrog with (kE, kH) replaced by (-kH, -kE) and no source.
+ *
+ * fdtd_adjoint_step applies n >= 0 transposed steps to the handle's fields
+ * (asynchronous; the step counter is not changed).  The handle must have
+ * boundary FDTD_PEC and no CPML (FDTD_ERR_ARG otherwise).
+ *
+ * fdtd_adjoint_gradient returns dL/dq_b, the derivative of a loss of the
+ * detector traces with respect to the shower's charge table (Sec. III.B),
+ * for the first n_steps steps from zero fields.  dl_dtrace is a device
+ * pointer laid out like the traces, float32 [n_probes][max_steps][2], holding
+ * dL/d(trace) (slots >= n_steps are not read).  grad_q (n_bins doubles) is a
+ * host (on_device = 0) or device pointer.  The adjoint state lives in the
+ * handle's field memory: the call leaves the handle reset (fields zero, step
+ * counter 0, traces kept).  Needs a shower, detectors, 1 <= n_steps <=
+ * max_steps, boundary FDTD_PEC and no CPML (FDTD_ERR_ARG otherwise).
+ * Synchronises.
+ */
+int fdtd_adjoint_step(fdtd_t h, int n);
+int fdtd_adjoint_gradient(fdtd_t h, const float *dl_dtrace, int n_steps, double *grad_q, int on_device);
+
 /* ---- host-side shower tables (Sec. III.B) ------------------------------ */
 
 /* Eq. showerModel: out[b] = q_max exp(-(z_b - z_peak)^2 / (2 l^2)), z_b = z0 + b bin_dz. */

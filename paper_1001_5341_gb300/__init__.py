@@ -49,6 +49,8 @@ _SIGS = {
     "fdtd_reset": (_i, [_vp]),
     "fdtd_energy": (_i, [_vp, _pd]),
     "fdtd_energy_noalloc": (_i, [_vp, _i, _i, _i, _d, _d, _i, _vp, _pd]),
+    "fdtd_adjoint_step": (_i, [_vp, _i]),
+    "fdtd_adjoint_gradient": (_i, [_vp, _vp, _i, _vp, _i]),
     "fdtd_save_state": (_i, [_vp, _vp, C.POINTER(_sz)]),
     "fdtd_load_state": (_i, [_vp, _vp, _sz]),
     "fdtd_timing_begin": (_i, [_vp, _i]),
@@ -233,6 +235,7 @@ class Simulation:
         q = np.ascontiguousarray(q, dtype=np.float64)
         w = np.ascontiguousarray(w, dtype=np.float64)
         check(fdtd_set_shower(self.h, _dp(q), q.size, z0, bin_dz, axis, v, _dp(w), L), "fdtd_set_shower")
+        self.n_bins = q.size
 
     def clear_shower(self):
         check(fdtd_clear_shower(self.h), "fdtd_clear_shower")
@@ -330,6 +333,27 @@ class Simulation:
     def set_kernel(self, which: int):
         """1: fused z-march (default), 0: unfused H sweep then E sweep."""
         check(fdtd_set_kernel(self.h, which), "fdtd_set_kernel")
+
+    def adjoint_step(self, n=1):
+        """n transposed steps of the fields (PEC grids without CPML)."""
+        check(fdtd_adjoint_step(self.h, n), "fdtd_adjoint_step")
+
+    def adjoint_gradient(self, dl_dtrace, n_steps, out=None):
+        """dL/dq of the charge table from dL/d(trace), a contiguous float32
+        CUDA tensor [n_probes][max_steps][2]; numpy float64, or into a float64
+        CUDA tensor.  Leaves the handle reset."""
+        import torch
+        if (dl_dtrace.dtype != torch.float32 or not dl_dtrace.is_cuda or not dl_dtrace.is_contiguous()
+                or tuple(dl_dtrace.shape) != (self.np, self.max_steps, 2)):
+            raise ValueError(f"dl_dtrace: need a contiguous float32 CUDA tensor [{self.np}, {self.max_steps}, 2]")
+        if out is not None:
+            check(fdtd_adjoint_gradient(self.h, _vp(dl_dtrace.data_ptr()), n_steps, _vp(out.data_ptr()), 1),
+                  "fdtd_adjoint_gradient")
+            return out
+        g = np.zeros(self.n_bins, dtype=np.float64)
+        check(fdtd_adjoint_gradient(self.h, _vp(dl_dtrace.data_ptr()), n_steps, _vp(g.ctypes.data), 0),
+              "fdtd_adjoint_gradient")
+        return g
 
 
 # ---- 2D axisymmetric solver ---------------------------------------------------
