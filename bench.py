@@ -413,6 +413,80 @@ def run_adjoint(args):
             "grad_norm": float(np.linalg.norm(g)), "gpu_launches": launches, "clocks": clk}
 
 
+def run_batch(args):
+    """64 independent showers on uneven grids (64^3 .. 256 x 256 x 512, dx =
+    2 cm, Mur) advanced together by the batched persistent kernel, against the
+    same simulations stepped one after another (default fused path and the
+    unfused path whose per-cell code the batch shares)."""
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    import paper_1001_5341_gb300 as fd
+
+    rng = np.random.default_rng(6006 + rank)
+    n_sims, steps = 64, args.steps or 200
+    dx = 0.02
+    dt = W.courant_dt(dx, W.EPS_R_ICE)
+    dims = [(int(rng.integers(64, 257)), int(rng.integers(64, 257)), int(rng.integers(64, 513))) for _ in range(n_sims)]
+    lw = fd.lateral_gaussian(3, 1.0)
+
+    def make(d, seed):
+        r = np.random.default_rng(seed)
+        nx, ny, nz = d
+        sim = fd.Simulation(nx, ny, nz, dx, dt, W.EPS_R_ICE, boundary=fd.FDTD_MUR1)
+        nb, z0 = 128, 0.0
+        bdz = nz * dx / (nb - 1)
+        q = fd.profile_gaussian(z0, bdz, nb, r.uniform(0.3, 0.7) * nz * dx, r.uniform(0.1, 0.3) * nz * dx, -1e-9)
+        sim.set_shower(q, z0, bdz, W.C0, lw, 3)
+        cx, cy = nx // 2 * dx, ny // 2 * dx
+        rr = r.uniform(0.2, 0.4, 8) * min(nx, ny) * dx
+        ph = r.uniform(0, 2 * np.pi, 8)
+        xyz = np.stack([cx + rr * np.cos(ph), cy + rr * np.sin(ph), r.uniform(0.2, 0.8, 8) * nz * dx], 1)
+        sim.set_probes(xyz, 4 * steps + 1000)
+        return sim
+
+    sims = [make(d, 7000 + i) for i, d in enumerate(dims)]
+    cells = sum(nx * ny * nz for nx, ny, nz in dims)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    b = fd.Batch(sims)
+    used = b.tune(trial_steps=2)
+    b.step(args.warmup)
+    b.sync()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.5)
+    t_batch = timed(lambda: (b.step(steps), b.sync()))
+    clk = clocks.stop()
+    cfg, graph = b.config, b.graph_mode
+    t_fused = timed(lambda: [s.step(steps) for s in sims])
+    for s in sims:
+        s.set_kernel(0)
+    t_unfused = timed(lambda: [s.step(steps) for s in sims])
+    b.close()
+    for s in sims:
+        s.close()
+    if rank != 0:
+        return None
+    g = lambda t: round(cells * steps / t / 1e9, 2)
+    return {"metric": "Gcell-updates/s", "value": g(t_batch), "unit": "Gcell/s", "solver": "batch",
+            "n_gpus": ws, "steps": steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"batch{n_sims}-uneven", "simulations": n_sims, "cells_total": cells,
+                       "grids": "nx, ny in [64, 256], nz in [64, 512], seeded", "boundary": "mur1",
+                       "dx_m": dx, "probes_each": 8, **cfg, "graph_replay": bool(graph == 1),
+                       "tuner_trial_steps": used},
+            "one_by_one_fused_gcells": g(t_fused), "one_by_one_unfused_gcells": g(t_unfused),
+            "batch_over_fused": round(t_fused / t_batch, 3), "batch_over_unfused": round(t_unfused / t_batch, 3),
+            "clocks": clk}
+
+
 # Table I: GTX285 seconds per N^2 run (step count not printed; read as N steps)
 PAPER_T_GPU = {256: 0.040, 512: 0.186, 1024: 1.167, 2048: 8.372, 4096: 67.617, 8192: 681.082}
 
@@ -550,7 +624,7 @@ def main():
     ap.add_argument("--nz", type=int, default=0,
                     help="z planes of a reduced grid with the benchmark physics (profiler captures "
                          "of a few GB); 0 = the benchmark grid")
-    ap.add_argument("--solver", choices=["yee3d", "cyl", "adjoint"], default="yee3d",
+    ap.add_argument("--solver", choices=["yee3d", "cyl", "adjoint", "batch"], default="yee3d",
                     help="cyl: the paper's 2D axisymmetric solver on an n x n grid (Table I); "
                          "adjoint: gradient of a detector misfit w.r.t. the charge table")
     ap.add_argument("--n", type=int, default=8192, help="cyl grid side")
@@ -561,6 +635,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.solver == "adjoint":
         line = run_adjoint(args)
+    elif args.solver == "batch":
+        line = run_batch(args)
     elif args.solver == "cyl":
         if args.impl == "reference":
             line = run_cyl_reference(args)

@@ -1,0 +1,70 @@
+/*
+ * batch.h -- many simulations advanced together (libfdtd_gb300.so).
+ *
+ * A batch borrows n simulation handles (fdtd.h) on one device, each with its
+ * own grid, boundary, shower (Sec. III.B) and detectors, and advances all of
+ * them with one persistent kernel per launch: every step of Sec. III.A runs
+ * as three phases over a shared work queue of (simulation, slab of z planes)
+ * items -- H update, E update with the shower's current, then the Mur faces
+ * and the detector readout -- separated by grid-wide barriers whose waits are
+ * bounded (FDTD_ERR_TIMEOUT if one gives up).  The kernel is a cooperative
+ * launch sized to the device's resident blocks; the launch, with the reset of
+ * its queue counters, is captured once in a CUDA graph and replayed.  Each
+ * cell is updated by the same per-cell code as the unfused path
+ * (fdtd_set_kernel 0), so a batched step gives the same numbers, bit for bit.
+ *
+ * The handles stay owned by the caller and must outlive the batch; stepping
+ * a handle on its own between batch steps is allowed (the batch re-reads the
+ * handle's step count and field set before each launch).  Status codes as in
+ * fdtd.h; errors are sticky per batch.
+ */
+#ifndef BATCH_GB300_H
+#define BATCH_GB300_H
+
+#include "fdtd.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fdtd_batch *fdtd_batch_t;
+
+/* n >= 1 distinct handles on the current device; the batch works on its own stream. */
+int fdtd_batch_create(fdtd_batch_t *out, const fdtd_t *sims, int n);
+void fdtd_batch_destroy(fdtd_batch_t b);
+
+/*
+ * Advance every simulation n >= 0 steps (asynchronous with respect to the
+ * host; ordered after earlier work on the handles' streams and before later
+ * work on them).  FDTD_ERR_CAPACITY if a simulation's trace would overflow.
+ */
+int fdtd_batch_step(fdtd_batch_t b, int n);
+
+/* Synchronise and return the sticky status. */
+int fdtd_batch_sync(fdtd_batch_t b);
+
+/*
+ * Launch configuration: threads per block (128, 256 or 512), cells per work
+ * item (a slab of whole z planes holds about this many cells, at least one
+ * plane), steps per persistent launch (1 .. 64).
+ */
+int fdtd_batch_set_config(fdtd_batch_t b, int threads, int cells_per_item, int steps_per_launch);
+int fdtd_batch_get_config(fdtd_batch_t b, int *threads, int *cells_per_item, int *steps_per_launch);
+
+/*
+ * Autotuner: runs trial_steps >= 1 steps of the batch itself with each
+ * candidate configuration (threads x cells per item), times each on the
+ * device, keeps the fastest and returns the steps it used in *steps_used.
+ * The trial steps are real steps of every simulation (the configuration
+ * does not change the arithmetic).
+ */
+int fdtd_batch_tune(fdtd_batch_t b, int trial_steps, int *steps_used);
+
+/* Whether launches are replayed from a captured graph (1) or issued directly (0). */
+int fdtd_batch_graph_mode(fdtd_batch_t b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BATCH_GB300_H */

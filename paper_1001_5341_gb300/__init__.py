@@ -82,6 +82,15 @@ _SIGS = {
     "sur_assemble": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, C.c_float, C.c_float, C.c_float, _i, _vp, _vp]),
     "sur_assemble_bwd": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, C.c_float, C.c_float, C.c_float, _i, _vp, _vp,
                               _vp]),
+    # batched persistent stepping (batch.h)
+    "fdtd_batch_create": (_i, [C.POINTER(_vp), C.POINTER(_vp), _i]),
+    "fdtd_batch_destroy": (None, [_vp]),
+    "fdtd_batch_step": (_i, [_vp, _i]),
+    "fdtd_batch_sync": (_i, [_vp]),
+    "fdtd_batch_set_config": (_i, [_vp, _i, _i, _i]),
+    "fdtd_batch_get_config": (_i, [_vp, _pi, _pi, _pi]),
+    "fdtd_batch_tune": (_i, [_vp, _i, _pi]),
+    "fdtd_batch_graph_mode": (_i, [_vp]),
     # 2D axisymmetric solver (cyl.h)
     "cyl_create": (_i, [C.POINTER(_vp), _i, _i, _d, _d, _d, _i, _vp]),
     "cyl_destroy": (None, [_vp]),
@@ -468,3 +477,56 @@ class Cylinder:
 
     def reset(self):
         check(cyl_reset(self.h), "cyl_reset")
+
+
+# ---- batched persistent stepping ------------------------------------------------
+
+class Batch:
+    """Several ``Simulation`` objects advanced together by one persistent
+    kernel per launch (batch.h).  The simulations must outlive the batch."""
+
+    def __init__(self, sims):
+        self.sims = list(sims)
+        arr = (_vp * len(self.sims))(*[s.h for s in self.sims])
+        h = _vp()
+        check(fdtd_batch_create(C.byref(h), arr, len(self.sims)), "fdtd_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            fdtd_batch_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def step(self, n=1):
+        check(fdtd_batch_step(self.h, n), "fdtd_batch_step")
+
+    def sync(self):
+        check(fdtd_batch_sync(self.h), "fdtd_batch_sync")
+
+    def set_config(self, threads=256, cells_per_item=1 << 16, steps_per_launch=8):
+        check(fdtd_batch_set_config(self.h, threads, cells_per_item, steps_per_launch), "fdtd_batch_set_config")
+
+    @property
+    def config(self):
+        t, c, s = C.c_int(), C.c_int(), C.c_int()
+        check(fdtd_batch_get_config(self.h, C.byref(t), C.byref(c), C.byref(s)), "fdtd_batch_get_config")
+        return {"threads": t.value, "cells_per_item": c.value, "steps_per_launch": s.value}
+
+    def tune(self, trial_steps=4):
+        """Autotune on the batch itself; returns the steps the trials advanced."""
+        used = C.c_int()
+        check(fdtd_batch_tune(self.h, trial_steps, C.byref(used)), "fdtd_batch_tune")
+        return used.value
+
+    @property
+    def graph_mode(self):
+        return fdtd_batch_graph_mode(self.h)
+

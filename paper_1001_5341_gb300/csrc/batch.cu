@@ -1,0 +1,471 @@
+// batch.cu -- many simulations in one persistent kernel (batch.h).
+//
+// Work queue.  For each step the kernel runs three phases; in each phase every
+// block takes items from an atomic counter until the phase's items are gone:
+//   H: item = (simulation q, slab of planes of q): H^{n+1/2} of its cells;
+//   E: same items: E^{n+1} with the shower's current;
+//   M: item = (q, face) for the six Mur faces of a Mur grid, and (q, detectors)
+//      for a grid with detectors: the boundary, then the readout of E^{n+1}.
+// Between phases a grid-wide barrier (all blocks are resident: cooperative
+// launch) with a bounded wait.  Every cell goes through cell_h / cell_e /
+// mur_cell, the code of the unfused path, so the numbers are the same.
+// Simulations keep their own ping-pong sets: in step s of a launch,
+// simulation q reads set cur_q ^ (s & 1).  At the end of a launch block 0
+// advances each descriptor's set index and step count, so that the captured
+// graph can be replayed unchanged.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "../../include/batch.h"
+#include "cell_update.cuh"
+#include "fdtd_internal.h"
+
+using namespace fdtd;
+
+namespace {
+
+constexpr int MAX_STEPS_PER_LAUNCH = 64;
+
+struct BSim {
+    Grid g;
+    float *f[2];
+    Cpml pml[2];           // views for cur = 0 and cur = 1
+    float kE, kH, mur;
+    int mur_on;
+    Source src;
+    Probes pr;
+    int cur;
+    long long n;           // steps done
+    int planes;            // z planes per H/E item
+};
+
+struct BArgs {
+    BSim *sims;
+    int nsim;
+    const int *hstart;     // [nsim + 1] prefix sums of H/E items
+    const int *mstart;     // [nsim + 1] prefix sums of M items
+    int steps;
+    unsigned *ctr;         // [3 * steps] queue counters, zero at launch
+    unsigned *bar;         // [2] barrier count and generation
+    int *flags;
+};
+
+// Grid-wide barrier: arrive, then wait (bounded) for the generation to move.
+__device__ bool grid_sync(unsigned *bar, int *flags) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        ok = 1;
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            bar[0] = 0;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g0) {
+                if (clock64() - t0 > (4LL << 30)) {
+                    atomicOr(flags, 2);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__device__ __forceinline__ int find_sim(const int *start, int nsim, int it) {
+    int lo = 0, hi = nsim - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= it) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(512) k_batch(BArgs A) {
+    __shared__ int s_item;
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int hitems = A.hstart[A.nsim], mitems = A.mstart[A.nsim];
+    for (int s = 0; s < A.steps; ++s) {
+        for (int phase = 0; phase < 3; ++phase) {
+            const int total = phase < 2 ? hitems : mitems;
+            unsigned *ctr = A.ctr + 3 * s + phase;
+            for (;;) {
+                if (tid == 0) s_item = (int)atomicAdd(ctr, 1u);
+                __syncthreads();
+                const int it = s_item;
+                __syncthreads();
+                if (it >= total) break;
+                const int q = find_sim(phase < 2 ? A.hstart : A.mstart, A.nsim, it);
+                const BSim &S = A.sims[q];
+                const Grid &g = S.g;
+                const int cur = S.cur ^ (s & 1);
+                const float *in = S.f[cur];
+                float *out = S.f[cur ^ 1];
+                if (phase < 2) {
+                    const int k0 = (it - A.hstart[q]) * S.planes, k1 = min(k0 + S.planes, g.nz);
+                    const unsigned nx = g.nx, plane_cells = nx * g.ny;   // items hold < 2^32 cells
+                    const unsigned cells = plane_cells * (k1 - k0);
+                    for (unsigned c = tid; c < cells; c += nt) {
+                        const unsigned kk = c / plane_cells, r = c - kk * plane_cells;
+                        const int j = (int)(r / nx), i = (int)(r - j * nx);
+                        const int k = k0 + (int)kk;
+                        if (phase == 0)
+                            cell_h(g, in, in + 3 * g.comp, out + 3 * g.comp, S.pml[cur], S.kH, i, j, k);
+                        else
+                            cell_e(g, in, out + 3 * g.comp, out, S.pml[cur], S.kE, S.src, S.n + s, i, j, k);
+                    }
+                } else {
+                    const int m = it - A.mstart[q];
+                    if (S.mur_on && m < 6) {
+                        const int amax = max(g.nx, g.ny) + 1, bmax = max(g.ny, g.nz) + 1;
+                        const int bb = max(bmax, g.nz + 1);
+                        for (int c = tid; c < amax * bb; c += nt) mur_cell(g, in, out, S.mur, m, c % amax, c / amax);
+                    } else {
+                        const Probes &p = S.pr;
+                        const long long slot = S.n + s;
+                        for (int t = tid; t < p.n; t += nt) {
+                            const int i = p.ijk[3 * t], j = p.ijk[3 * t + 1], k = p.ijk[3 * t + 2];
+                            const long long c = gidx(g, i, j, k);
+                            const float *Ex = out, *Ey = out + g.comp, *Ez = out + 2 * g.comp;
+                            const float ex = 0.5f * (Ex[c - 1] + Ex[c]);
+                            const float ey = 0.5f * (Ey[c - g.pitch] + Ey[c]);
+                            const float ez = 0.5f * (Ez[c - g.plane] + Ez[c]);
+                            float *o = p.trace + ((long long)t * p.max_steps + slot) * 2;
+                            o[0] = ez;
+                            o[1] = p.cxy[2 * t] * ex + p.cxy[2 * t + 1] * ey;
+                        }
+                    }
+                }
+            }
+            if (!grid_sync(A.bar, A.flags)) return;
+        }
+    }
+    if (blockIdx.x == 0)
+        for (int q = tid; q < A.nsim; q += nt) {
+            A.sims[q].cur ^= A.steps & 1;
+            A.sims[q].n += A.steps;
+        }
+}
+
+}  // namespace
+
+struct fdtd_batch {
+    std::vector<fdtd_t> sims;
+    int dev, sms;
+    cudaStream_t stream;
+    cudaEvent_t ev;
+    BSim *d_sims;
+    int *d_hstart, *d_mstart;
+    unsigned *d_ctr, *d_bar;
+    int *d_flags;
+    int threads, cells_per_item, steps_per_launch;
+    int blocks;
+    int graph_ok;          // -1 unknown, 0 direct launches, 1 graphs
+    std::map<int, cudaGraphExec_t> graphs;   // steps per launch -> executable graph
+    int status;
+};
+
+namespace {
+
+int note(fdtd_batch *b, cudaError_t e) {
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (b->status == FDTD_OK) b->status = FDTD_ERR_CUDA;
+        return FDTD_ERR_CUDA;
+    }
+    return FDTD_OK;
+}
+
+void drop_graphs(fdtd_batch *b) {
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+// Descriptors and item prefix sums from the handles' current state.
+int refresh(fdtd_batch *b) {
+    const int n = (int)b->sims.size();
+    std::vector<BSim> d(n);
+    std::vector<int> hs(n + 1, 0), ms(n + 1, 0);
+    for (int q = 0; q < n; ++q) {
+        fdtd_ctx *h = b->sims[q];
+        BSim &S = d[q];
+        S.g = h->g;
+        S.f[0] = h->fields[0];
+        S.f[1] = h->fields[1];
+        const int cur = h->cur;
+        for (int c = 0; c < 2; ++c) {
+            h->cur = c;
+            S.pml[c] = cpml_view(h);
+        }
+        h->cur = cur;
+        S.kE = (float)h->kE;
+        S.kH = (float)h->kH;
+        S.mur = (float)h->mur_m;
+        S.mur_on = h->boundary == FDTD_MUR1;
+        S.src = h->src;
+        S.pr = Probes{h->np, h->max_steps, h->d_ijk, h->d_cxy, h->d_trace};
+        S.cur = h->cur;
+        S.n = h->steps;
+        const long long plane = (long long)h->g.nx * h->g.ny;
+        S.planes = (int)std::max<long long>(1, std::min<long long>(h->g.nz, b->cells_per_item / std::max(1LL, plane)));
+        while (S.planes > 1 && plane * S.planes >= (1LL << 31)) --S.planes;
+        hs[q + 1] = hs[q] + (h->g.nz + S.planes - 1) / S.planes;
+        ms[q + 1] = ms[q] + (S.mur_on ? 6 : 0) + (h->np > 0 ? 1 : 0);
+    }
+    if (note(b, cudaMemcpyAsync(b->d_sims, d.data(), n * sizeof(BSim), cudaMemcpyHostToDevice, b->stream)) ||
+        note(b, cudaMemcpyAsync(b->d_hstart, hs.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, b->stream)) ||
+        note(b, cudaMemcpyAsync(b->d_mstart, ms.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, b->stream)))
+        return b->status;
+    // pageable sources: the copies complete before the next host change of d, hs, ms
+    return note(b, cudaStreamSynchronize(b->stream));
+}
+
+int size_grid(fdtd_batch *b) {
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch, b->threads, 0) != cudaSuccess || per < 1) {
+        cudaGetLastError();
+        return FDTD_ERR_CUDA;
+    }
+    b->blocks = per * b->sms;
+    return FDTD_OK;
+}
+
+cudaError_t issue(fdtd_batch *b, int steps) {
+    BArgs A;
+    A.sims = b->d_sims;
+    A.nsim = (int)b->sims.size();
+    A.hstart = b->d_hstart;
+    A.mstart = b->d_mstart;
+    A.steps = steps;
+    A.ctr = b->d_ctr;
+    A.bar = b->d_bar;
+    A.flags = b->d_flags;
+    cudaError_t e = cudaMemsetAsync(b->d_ctr, 0, 3 * steps * sizeof(unsigned), b->stream);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b->blocks);
+    cfg.blockDim = dim3(b->threads);
+    cfg.stream = b->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch, A);
+}
+
+// One persistent launch of `steps` steps: a replay of its captured graph, or
+// a direct launch when capture is not available.
+int launch(fdtd_batch *b, int steps) {
+    if (b->graph_ok != 0) {
+        auto it = b->graphs.find(steps);
+        if (it == b->graphs.end()) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            bool ok = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                const cudaError_t e1 = issue(b, steps);
+                const cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+                ok = e1 == cudaSuccess && e2 == cudaSuccess && graph &&
+                     cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+            }
+            if (graph) cudaGraphDestroy(graph);
+            if (!ok) {
+                cudaGetLastError();
+                if (exec) cudaGraphExecDestroy(exec);
+                b->graph_ok = 0;
+            } else {
+                b->graph_ok = 1;
+                it = b->graphs.emplace(steps, exec).first;
+            }
+        }
+        if (b->graph_ok == 1) return note(b, cudaGraphLaunch(it->second, b->stream));
+    }
+    return note(b, issue(b, steps));
+}
+
+}  // namespace
+
+extern "C" {
+
+int fdtd_batch_create(fdtd_batch_t *out, const fdtd_t *sims, int n) {
+    if (!out) return FDTD_ERR_ARG;
+    *out = nullptr;
+    if (!sims || n < 1) return FDTD_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return FDTD_ERR_CUDA;
+    }
+    for (int q = 0; q < n; ++q) {
+        if (!sims[q] || sims[q]->dev != dev) return FDTD_ERR_ARG;
+        if (sims[q]->status != FDTD_OK) return sims[q]->status;
+        for (int r = 0; r < q; ++r)
+            if (sims[r] == sims[q]) return FDTD_ERR_ARG;
+    }
+    fdtd_batch *b = new (std::nothrow) fdtd_batch();
+    if (!b) return FDTD_ERR_OOM;
+    b->sims.assign(sims, sims + n);
+    b->dev = dev;
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    b->threads = 256;
+    b->cells_per_item = 1 << 16;
+    b->steps_per_launch = 8;
+    b->graph_ok = -1;
+    b->status = FDTD_OK;
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc(&b->d_sims, n * sizeof(BSim)) != cudaSuccess ||
+        cudaMalloc(&b->d_hstart, (n + 1) * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&b->d_mstart, (n + 1) * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&b->d_ctr, 3 * MAX_STEPS_PER_LAUNCH * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&b->d_bar, 2 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&b->d_flags, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        fdtd_batch_destroy(b);
+        return FDTD_ERR_OOM;
+    }
+    if (note(b, cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), b->stream)) != FDTD_OK ||
+        note(b, cudaMemsetAsync(b->d_flags, 0, sizeof(int), b->stream)) != FDTD_OK ||
+        note(b, cudaStreamSynchronize(b->stream)) != FDTD_OK || size_grid(b) != FDTD_OK) {
+        fdtd_batch_destroy(b);
+        return FDTD_ERR_CUDA;
+    }
+    *out = b;
+    return FDTD_OK;
+}
+
+void fdtd_batch_destroy(fdtd_batch_t b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graphs(b);
+    if (b->d_sims) cudaFree(b->d_sims);
+    if (b->d_hstart) cudaFree(b->d_hstart);
+    if (b->d_mstart) cudaFree(b->d_mstart);
+    if (b->d_ctr) cudaFree(b->d_ctr);
+    if (b->d_bar) cudaFree(b->d_bar);
+    if (b->d_flags) cudaFree(b->d_flags);
+    if (b->ev) cudaEventDestroy(b->ev);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+int fdtd_batch_step(fdtd_batch_t b, int n) {
+    if (!b || n < 0) return FDTD_ERR_ARG;
+    if (b->status != FDTD_OK) return b->status;
+    for (fdtd_t h : b->sims) {
+        if (h->status != FDTD_OK) return h->status;
+        if (h->np > 0 && h->steps + n > h->max_steps) return FDTD_ERR_CAPACITY;
+    }
+    if (n == 0) return FDTD_OK;
+    // order after earlier work on the handles' streams
+    for (fdtd_t h : b->sims) {
+        if (note(b, cudaEventRecord(b->ev, h->stream)) || note(b, cudaStreamWaitEvent(b->stream, b->ev, 0)))
+            return b->status;
+    }
+    if (refresh(b) != FDTD_OK) return b->status;
+    int left = n, launches = 0;
+    while (left > 0 && b->status == FDTD_OK) {
+        const int s = std::min(left, b->steps_per_launch);
+        launch(b, s);
+        left -= s;
+        ++launches;
+    }
+    (void)launches;
+    for (fdtd_t h : b->sims) {
+        h->cur ^= n & 1;
+        h->steps += n;
+    }
+    // order later work on the handles' streams after the batch
+    if (note(b, cudaEventRecord(b->ev, b->stream)) != FDTD_OK) return b->status;
+    for (fdtd_t h : b->sims)
+        if (note(b, cudaStreamWaitEvent(h->stream, b->ev, 0)) != FDTD_OK) return b->status;
+    return b->status;
+}
+
+int fdtd_batch_sync(fdtd_batch_t b) {
+    if (!b) return FDTD_ERR_ARG;
+    if (note(b, cudaStreamSynchronize(b->stream)) != FDTD_OK) return b->status;
+    int f = 0;
+    if (note(b, cudaMemcpy(&f, b->d_flags, sizeof(int), cudaMemcpyDeviceToHost)) != FDTD_OK) return b->status;
+    if (f && b->status == FDTD_OK) b->status = FDTD_ERR_TIMEOUT;
+    return b->status;
+}
+
+int fdtd_batch_set_config(fdtd_batch_t b, int threads, int cells_per_item, int steps_per_launch) {
+    if (!b || (threads != 128 && threads != 256 && threads != 512) || cells_per_item < 1 || steps_per_launch < 1 ||
+        steps_per_launch > MAX_STEPS_PER_LAUNCH)
+        return FDTD_ERR_ARG;
+    if (b->status != FDTD_OK) return b->status;
+    if (note(b, cudaStreamSynchronize(b->stream)) != FDTD_OK) return b->status;
+    drop_graphs(b);
+    b->threads = threads;
+    b->cells_per_item = cells_per_item;
+    b->steps_per_launch = steps_per_launch;
+    return size_grid(b);
+}
+
+int fdtd_batch_get_config(fdtd_batch_t b, int *threads, int *cells_per_item, int *steps_per_launch) {
+    if (!b) return FDTD_ERR_ARG;
+    if (threads) *threads = b->threads;
+    if (cells_per_item) *cells_per_item = b->cells_per_item;
+    if (steps_per_launch) *steps_per_launch = b->steps_per_launch;
+    return FDTD_OK;
+}
+
+int fdtd_batch_tune(fdtd_batch_t b, int trial_steps, int *steps_used) {
+    if (!b || trial_steps < 1) return FDTD_ERR_ARG;
+    if (b->status != FDTD_OK) return b->status;
+    const int spl0 = b->steps_per_launch, spl = std::min(spl0, trial_steps);
+    const int thr[3] = {128, 256, 512};
+    const int cpi[4] = {1 << 14, 1 << 16, 1 << 18, 1 << 20};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return FDTD_ERR_CUDA;
+    }
+    float best_ms = 1e30f;
+    int best_t = b->threads, best_c = b->cells_per_item, used = 0, rc = FDTD_OK;
+    for (int t : thr)
+        for (int c : cpi) {
+            if ((rc = fdtd_batch_set_config(b, t, c, spl)) != FDTD_OK) break;
+            // one untimed launch builds the graph, then the timed trial
+            if ((rc = fdtd_batch_step(b, spl)) != FDTD_OK) break;
+            used += spl;
+            if ((rc = note(b, cudaEventRecord(e0, b->stream))) != FDTD_OK) break;
+            if ((rc = fdtd_batch_step(b, trial_steps)) != FDTD_OK) break;
+            used += trial_steps;
+            if ((rc = note(b, cudaEventRecord(e1, b->stream))) != FDTD_OK) break;
+            if ((rc = fdtd_batch_sync(b)) != FDTD_OK) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_t = t;
+                best_c = c;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (steps_used) *steps_used = used;
+    if (rc != FDTD_OK) return rc;
+    return fdtd_batch_set_config(b, best_t, best_c, spl0);
+}
+
+int fdtd_batch_graph_mode(fdtd_batch_t b) { return b ? b->graph_ok : -1; }
+
+}  // extern "C"
