@@ -379,21 +379,27 @@ def run_adjoint(args):
         qt = torch.tensor(q, requires_grad=True)
         with torch.no_grad():
             target = model(qt * 0.9)
+        # untimed warm-up of the whole forward + loss + backward path: the
+        # first autograd backward of a process loads torch's kernels
+        yw = model(qt)
+        (0.5 * ((yw.double() - target.double()) ** 2).sum()).backward()
+        qt.grad = None
         clocks = ClockSampler(local)
         clocks.start()
         time.sleep(0.5)   # the sampler's start-up stalls the driver for a moment
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        # both passes end in a synchronisation inside the library (traces to
+        # the tensor, gradient to the host): synchronised wall clocks
         torch.cuda.synchronize()
-        ev[0].record(stream)
+        t0 = time.perf_counter()
         y = model(qt)
-        ev[1].record(stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         loss = 0.5 * ((y.double() - target.double()) ** 2).sum()
         loss.backward()
-        ev[2].record(stream)
         torch.cuda.synchronize()
+        t2 = time.perf_counter()
         clk = clocks.stop()
-        t_fwd = ev[0].elapsed_time(ev[1]) * 1e-3
-        t_all = ev[0].elapsed_time(ev[2]) * 1e-3
+        t_fwd, t_all = t1 - t0, t2 - t0
         launches = sim.launches
         g = qt.grad.numpy()
         sim.close()
@@ -424,10 +430,16 @@ def run_batch(args):
     import paper_1001_5341_gb300 as fd
 
     rng = np.random.default_rng(6006 + rank)
-    n_sims, steps = 64, args.steps or 200
+    steps = args.steps or 200
     dx = 0.02
     dt = W.courant_dt(dx, W.EPS_R_ICE)
-    dims = [(int(rng.integers(64, 257)), int(rng.integers(64, 257)), int(rng.integers(64, 513))) for _ in range(n_sims)]
+    if args.batch_kind == "small":   # many small grids: 256 showers on 32^3 .. 96^3
+        n_sims = 256
+        dims = [tuple(int(v) for v in rng.integers(32, 97, 3)) for _ in range(n_sims)]
+    else:                            # 64 showers on 64^3 .. 256 x 256 x 512
+        n_sims = 64
+        dims = [(int(rng.integers(64, 257)), int(rng.integers(64, 257)), int(rng.integers(64, 513)))
+                for _ in range(n_sims)]
     lw = fd.lateral_gaussian(3, 1.0)
 
     def make(d, seed):
@@ -479,7 +491,8 @@ def run_batch(args):
             "n_gpus": ws, "steps": steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"batch{n_sims}-uneven", "simulations": n_sims, "cells_total": cells,
-                       "grids": "nx, ny in [64, 256], nz in [64, 512], seeded", "boundary": "mur1",
+                       "grids": ("nx, ny, nz in [32, 96]" if args.batch_kind == "small"
+                                 else "nx, ny in [64, 256], nz in [64, 512]") + ", seeded", "boundary": "mur1",
                        "dx_m": dx, "probes_each": 8, **cfg, "graph_replay": bool(graph == 1),
                        "tuner_trial_steps": used},
             "one_by_one_fused_gcells": g(t_fused), "one_by_one_unfused_gcells": g(t_unfused),
@@ -629,6 +642,8 @@ def main():
                          "adjoint: gradient of a detector misfit w.r.t. the charge table")
     ap.add_argument("--n", type=int, default=8192, help="cyl grid side")
     ap.add_argument("--cyl-kernel", type=int, default=-1, help="cyl kernel (-1: library default)")
+    ap.add_argument("--batch-kind", choices=["config4", "small"], default="config4",
+                    help="batch workload: 64 grids 64^3 .. 256x256x512, or 256 grids 32^3 .. 96^3")
     ap.add_argument("--seg-rows", type=int, default=0, help="cyl rows per segment (0: automatic)")
     args = ap.parse_args()
     if args.warmup < 3:

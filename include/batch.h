@@ -44,7 +44,7 @@ int fdtd_batch_step(fdtd_batch_t b, int n);
 int fdtd_batch_sync(fdtd_batch_t b);
 
 /*
- * Launch configuration: threads per block (128, 256 or 512), cells per work
+ * Launch configuration: threads per block (128 or 256), cells per work
  * item (a slab of whole z planes holds about this many cells, at least one
  * plane), steps per persistent launch (1 .. 64).
  */

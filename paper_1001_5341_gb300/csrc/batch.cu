@@ -95,48 +95,78 @@ __device__ __forceinline__ int find_sim(const int *start, int nsim, int it) {
     return lo;
 }
 
-__global__ void __launch_bounds__(512) k_batch(BArgs A) {
+__global__ void __launch_bounds__(256, 6) k_batch(BArgs A) {   // 40 registers: 6 blocks per SM
     __shared__ int s_item;
-    const int nt = blockDim.x, tid = threadIdx.x;
+    // the item's simulation, copied once per item: the per-cell code then
+    // reads it from shared memory, which no global store can alias
+    __shared__ Grid s_g;
+    __shared__ Cpml s_pml;
+    __shared__ Source s_src;
+    __shared__ Probes s_pr;
+    __shared__ float s_k[3];
+    __shared__ int s_q, s_mur;
+    __shared__ long long s_n;
+    __shared__ const float *s_in;
+    __shared__ float *s_out;
+    const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
     const int hitems = A.hstart[A.nsim], mitems = A.mstart[A.nsim];
     for (int s = 0; s < A.steps; ++s) {
         for (int phase = 0; phase < 3; ++phase) {
             const int total = phase < 2 ? hitems : mitems;
             unsigned *ctr = A.ctr + 3 * s + phase;
             for (;;) {
-                if (tid == 0) s_item = (int)atomicAdd(ctr, 1u);
+                if (tid == 0) {
+                    const int it = (int)atomicAdd(ctr, 1u);
+                    s_item = it;
+                    if (it < total) {
+                        const int q = find_sim(phase < 2 ? A.hstart : A.mstart, A.nsim, it);
+                        const BSim &S = A.sims[q];
+                        const int cur = S.cur ^ (s & 1);
+                        s_q = q;
+                        s_g = S.g;
+                        s_pml = S.pml[cur];
+                        s_src = S.src;
+                        s_pr = S.pr;
+                        s_k[0] = S.kE;
+                        s_k[1] = S.kH;
+                        s_k[2] = S.mur;
+                        s_mur = S.mur_on;
+                        s_n = S.n + s;
+                        s_in = S.f[cur];
+                        s_out = S.f[cur ^ 1];
+                    }
+                }
                 __syncthreads();
                 const int it = s_item;
-                __syncthreads();
-                if (it >= total) break;
-                const int q = find_sim(phase < 2 ? A.hstart : A.mstart, A.nsim, it);
-                const BSim &S = A.sims[q];
-                const Grid &g = S.g;
-                const int cur = S.cur ^ (s & 1);
-                const float *in = S.f[cur];
-                float *out = S.f[cur ^ 1];
+                if (it >= total) {
+                    __syncthreads();
+                    break;
+                }
+                const Grid g = s_g;
+                const float *in = s_in;
+                float *out = s_out;
                 if (phase < 2) {
-                    const int k0 = (it - A.hstart[q]) * S.planes, k1 = min(k0 + S.planes, g.nz);
-                    const unsigned nx = g.nx, plane_cells = nx * g.ny;   // items hold < 2^32 cells
-                    const unsigned cells = plane_cells * (k1 - k0);
-                    for (unsigned c = tid; c < cells; c += nt) {
-                        const unsigned kk = c / plane_cells, r = c - kk * plane_cells;
-                        const int j = (int)(r / nx), i = (int)(r - j * nx);
-                        const int k = k0 + (int)kk;
-                        if (phase == 0)
-                            cell_h(g, in, in + 3 * g.comp, out + 3 * g.comp, S.pml[cur], S.kH, i, j, k);
-                        else
-                            cell_e(g, in, out + 3 * g.comp, out, S.pml[cur], S.kE, S.src, S.n + s, i, j, k);
+                    const int planes = A.sims[s_q].planes;
+                    const int k0 = (it - A.hstart[s_q]) * planes, k1 = min(k0 + planes, g.nz);
+                    const int rows = g.ny * (k1 - k0);
+                    for (int row = warp; row < rows; row += nwarps) {
+                        const int kk = row / g.ny, j = row - kk * g.ny, k = k0 + kk;
+                        for (int i = lane; i < g.nx; i += 32) {
+                            if (phase == 0)
+                                cell_h(g, in, in + 3 * g.comp, out + 3 * g.comp, s_pml, s_k[1], i, j, k);
+                            else
+                                cell_e(g, in, out + 3 * g.comp, out, s_pml, s_k[0], s_src, s_n, i, j, k);
+                        }
                     }
                 } else {
-                    const int m = it - A.mstart[q];
-                    if (S.mur_on && m < 6) {
-                        const int amax = max(g.nx, g.ny) + 1, bmax = max(g.ny, g.nz) + 1;
-                        const int bb = max(bmax, g.nz + 1);
-                        for (int c = tid; c < amax * bb; c += nt) mur_cell(g, in, out, S.mur, m, c % amax, c / amax);
+                    const int m = it - A.mstart[s_q];
+                    if (s_mur && m < 6) {
+                        // face m: (a, b) over (j, k), (i, k) or (i, j)
+                        const int ax = m >> 1;
+                        const int na = (ax == 0 ? g.ny : g.nx) + 1, nb = (ax == 2 ? g.ny : g.nz) + 1;
+                        for (int c = tid; c < na * nb; c += nt) mur_cell(g, in, out, s_k[2], m, c % na, c / na);
                     } else {
-                        const Probes &p = S.pr;
-                        const long long slot = S.n + s;
+                        const Probes &p = s_pr;
                         for (int t = tid; t < p.n; t += nt) {
                             const int i = p.ijk[3 * t], j = p.ijk[3 * t + 1], k = p.ijk[3 * t + 2];
                             const long long c = gidx(g, i, j, k);
@@ -144,12 +174,13 @@ __global__ void __launch_bounds__(512) k_batch(BArgs A) {
                             const float ex = 0.5f * (Ex[c - 1] + Ex[c]);
                             const float ey = 0.5f * (Ey[c - g.pitch] + Ey[c]);
                             const float ez = 0.5f * (Ez[c - g.plane] + Ez[c]);
-                            float *o = p.trace + ((long long)t * p.max_steps + slot) * 2;
+                            float *o = p.trace + ((long long)t * p.max_steps + s_n) * 2;
                             o[0] = ez;
                             o[1] = p.cxy[2 * t] * ex + p.cxy[2 * t + 1] * ey;
                         }
                     }
                 }
+                __syncthreads();   // the item's shared copy is free again
             }
             if (!grid_sync(A.bar, A.flags)) return;
         }
@@ -407,7 +438,7 @@ int fdtd_batch_sync(fdtd_batch_t b) {
 }
 
 int fdtd_batch_set_config(fdtd_batch_t b, int threads, int cells_per_item, int steps_per_launch) {
-    if (!b || (threads != 128 && threads != 256 && threads != 512) || cells_per_item < 1 || steps_per_launch < 1 ||
+    if (!b || (threads != 128 && threads != 256) || cells_per_item < 1 || steps_per_launch < 1 ||
         steps_per_launch > MAX_STEPS_PER_LAUNCH)
         return FDTD_ERR_ARG;
     if (b->status != FDTD_OK) return b->status;
@@ -431,7 +462,7 @@ int fdtd_batch_tune(fdtd_batch_t b, int trial_steps, int *steps_used) {
     if (!b || trial_steps < 1) return FDTD_ERR_ARG;
     if (b->status != FDTD_OK) return b->status;
     const int spl0 = b->steps_per_launch, spl = std::min(spl0, trial_steps);
-    const int thr[3] = {128, 256, 512};
+    const int thr[2] = {128, 256};
     const int cpi[4] = {1 << 14, 1 << 16, 1 << 18, 1 << 20};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
