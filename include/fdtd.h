@@ -228,16 +228,20 @@ int fdtd_set_kernel(fdtd_t h, int which);
 /* Human-readable text of a status code (static string). */
 const char *fdtd_strerror(int status);
 
-/* ---- adjoint (PEC grids without CPML) ----------------------------------- */
+/* ---- adjoint (PEC and Mur grids) ---------------------------------------- */
 
 /*
  * The step of Sec. III.A is linear in (E^n, H^{n-1/2}) and in the source; on
- * the Yee grid with PEC walls its curls satisfy C_H = C_E^T, so its transpose
- * is the same leapfrog with (kE, kH) replaced by (-kH, -kE) and no source.
+ * the Yee grid its curls satisfy C_H = C_E^T on the E cells the update
+ * changes, so its transpose is the same leapfrog with (kE, kH) replaced by
+ * (-kH, -kE) and no source; on a Mur grid the transpose of the face update
+ * E'_b = E_1^n + m (E'_1 - E_b^n) is folded in (the face cells' adjoint
+ * feeds their inward neighbours before the curls, and takes the transposed
+ * curl of the new adjoint H after them).
  *
  * fdtd_adjoint_step applies n >= 0 transposed steps to the handle's fields
  * (asynchronous; the step counter is not changed).  The handle must have
- * boundary FDTD_PEC and no CPML (FDTD_ERR_ARG otherwise).
+ * boundary FDTD_PEC or FDTD_MUR1 (FDTD_ERR_ARG for CPML).
  *
  * fdtd_adjoint_gradient returns dL/dq_b, the derivative of a loss of the
  * detector traces with respect to the shower's charge table (Sec. III.B),
@@ -247,7 +251,7 @@ const char *fdtd_strerror(int status);
  * host (on_device = 0) or device pointer.  The adjoint state lives in the
  * handle's field memory: the call leaves the handle reset (fields zero, step
  * counter 0, traces kept).  Needs a shower, detectors, 1 <= n_steps <=
- * max_steps, boundary FDTD_PEC and no CPML (FDTD_ERR_ARG otherwise).
+ * max_steps, boundary FDTD_PEC or FDTD_MUR1 (FDTD_ERR_ARG otherwise).
  * Synchronises.
  */
 int fdtd_adjoint_step(fdtd_t h, int n);

@@ -1,12 +1,12 @@
 // adjoint.cu -- transposed steps and the gradient of a detector misfit with
-// respect to the shower's charge table (PEC grids without CPML).
+// respect to the shower's charge table (PEC and Mur grids).
 //
 // The step of Sec. III.A maps u^n = (E^n, H^{n-1/2}) to u^{n+1} linearly:
 //   H' = H - kH C_E E,   E' = E + kE C_H H' + S^n,
 // with C_E the forward-difference curl and C_H the backward-difference curl.
 // On the Yee grid with PEC walls C_H = C_E^T entry by entry, so the transpose
 // of the step, acting on the adjoint state mu = (mu_E, mu_H), is again a
-// leapfrog:
+// leapfrog (Mur grids: below):
 //   mu_H' = mu_H + kE C_E mu_E,   mu_E' = mu_E - kH C_H mu_H',
 // i.e. the forward field update with (kE, kH) replaced by (-kH, -kE), no
 // source.  The traces y^{n} = C u^{n} (detector slot n-1) and the source S^n
@@ -22,6 +22,7 @@
 #include <cmath>
 #include <vector>
 
+#include "cell_update.cuh"
 #include "fdtd_internal.h"
 #include "source_term.cuh"
 
@@ -107,6 +108,131 @@ __global__ void k_adj_bins(Source s, const double *__restrict__ gstep, int n_ste
     grad[b] = acc;
 }
 
+// ---- Mur grids --------------------------------------------------------------
+// The Mur step is  Etilde = E + kE C_H H' on the interior E cells (the cells
+// cell_e updates), then  E'_b = E_1^n + m (Etilde_1 - E_b^n)  on each face cell
+// b (tangential E of a face, edges excluded) with inward neighbour 1.  Its
+// transpose, from (mu_E', mu_H') in set cur to set cur^1:
+//   1. muEt = mu_E' on interior cells plus m mu_E'_b from each face cell b
+//      next to them; zero on face cells;
+//   2. mu_H = mu_H' + kE C_E muEt                  (cell_h, coefficient -kE);
+//   3. mu_E = muEt - kH C_H mu_H on interior cells (cell_e, coefficient -kH);
+//   4. face cells: mu_E_b = -kH (C_E^T mu_H)_b - m mu_E'_b, and each inward
+//      neighbour gains mu_E'_b.
+// (C_E^T mu_H)_b is the backward-difference curl at b with H outside the
+// grid taken as zero (H cells the step does not update hold zero).
+
+// whether E component c at node (i,j,k) is updated by cell_e
+__device__ __forceinline__ bool e_interior(const Grid &g, int c, int i, int j, int k) {
+    const bool xi = i >= 1 && i <= g.nx - 1, yi = j >= 1 && j <= g.ny - 1, zi = k >= 1 && k <= g.nz - 1;
+    if (c == 0) return i <= g.nx - 1 && yi && zi;
+    if (c == 1) return j <= g.ny - 1 && xi && zi;
+    return k <= g.nz - 1 && xi && yi;
+}
+
+__global__ void k_adj_mur_gather(Grid g, const float *__restrict__ Ein, float *__restrict__ Et, float m) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i > g.nx) return;
+    const long long o = gidx(g, i, j, k);
+    for (int c = 0; c < 3; ++c) {
+        const float *e = Ein + c * g.comp;
+        float v = 0.f;
+        if (e_interior(g, c, i, j, k)) {
+            v = e[o];
+            // face neighbours: the component must be tangential to the face
+            if (c != 0) {
+                if (i == 1) v += m * e[o - 1];
+                if (i == g.nx - 1) v += m * e[o + 1];
+            }
+            if (c != 1) {
+                if (j == 1) v += m * e[o - g.pitch];
+                if (j == g.ny - 1) v += m * e[o + g.pitch];
+            }
+            if (c != 2) {
+                if (k == 1) v += m * e[o - g.plane];
+                if (k == g.nz - 1) v += m * e[o + g.plane];
+            }
+        }
+        Et[c * g.comp + o] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_adj_h(Grid g, const float *__restrict__ Et, const float *__restrict__ Hin,
+                                               float *__restrict__ Hout, Cpml pml, float kH) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    cell_h(g, Et, Hin, Hout, pml, kH, i, j, k);
+}
+
+__global__ void __launch_bounds__(256) k_adj_e(Grid g, float *E, const float *__restrict__ H, Cpml pml, float kE,
+                                               Source src) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    cell_e(g, E, H, E, pml, kE, src, 0, i, j, k);   // in place: each cell reads and writes only itself
+}
+
+__device__ __forceinline__ float hval(const Grid &g, const float *Hc, int i, int j, int k) {
+    return (i < 0 || j < 0 || k < 0) ? 0.f : Hc[gidx(g, i, j, k)];
+}
+
+// Face f (0..5 = x-, x+, y-, y+, z-, z+), tangential components, (a, b) as mur_cell.
+__global__ void k_adj_mur_faces(Grid g, const float *__restrict__ Ein, float *E, const float *__restrict__ H,
+                                float kH, float m) {
+    const int f = blockIdx.z, ax = f >> 1, hi = f & 1;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y * blockDim.y + threadIdx.y;
+    const float *Hx = H, *Hy = H + g.comp, *Hz = H + 2 * g.comp;
+    for (int t = 0; t < 2; ++t) {
+        // component c on face f and its index range (as in mur_cell)
+        int c, i, j, k, di = 0, dj = 0, dk = 0;
+        bool ok;
+        if (ax == 0) {
+            c = t == 0 ? 1 : 2;
+            i = hi ? g.nx : 0; j = a; k = b; di = hi ? -1 : 1;
+            ok = c == 1 ? (a <= g.ny - 1 && b >= 1 && b <= g.nz - 1) : (a >= 1 && a <= g.ny - 1 && b <= g.nz - 1);
+        } else if (ax == 1) {
+            c = t == 0 ? 0 : 2;
+            i = a; j = hi ? g.ny : 0; k = b; dj = hi ? -1 : 1;
+            ok = c == 0 ? (a <= g.nx - 1 && b >= 1 && b <= g.nz - 1) : (a >= 1 && a <= g.nx - 1 && b <= g.nz - 1);
+        } else {
+            c = t == 0 ? 0 : 1;
+            i = a; j = b; k = hi ? g.nz : 0; dk = hi ? -1 : 1;
+            ok = c == 0 ? (a <= g.nx - 1 && b >= 1 && b <= g.ny - 1) : (a >= 1 && a <= g.nx - 1 && b <= g.ny - 1);
+        }
+        if (!ok) continue;
+        float curl;
+        if (c == 0)
+            curl = (hval(g, Hz, i, j, k) - hval(g, Hz, i, j - 1, k)) - (hval(g, Hy, i, j, k) - hval(g, Hy, i, j, k - 1));
+        else if (c == 1)
+            curl = (hval(g, Hx, i, j, k) - hval(g, Hx, i, j, k - 1)) - (hval(g, Hz, i, j, k) - hval(g, Hz, i - 1, j, k));
+        else
+            curl = (hval(g, Hy, i, j, k) - hval(g, Hy, i - 1, j, k)) - (hval(g, Hx, i, j, k) - hval(g, Hx, i, j - 1, k));
+        const long long o = gidx(g, i, j, k), o1 = gidx(g, i + di, j + dj, k + dk);
+        const float eb = Ein[c * g.comp + o];
+        E[c * g.comp + o] = -kH * curl - m * eb;
+        atomicAdd(&E[c * g.comp + o1], eb);
+    }
+}
+
+void adj_field_step_mur(fdtd_ctx *h) {
+    const Grid &g = h->g;
+    const float *in = h->fields[h->cur];
+    float *out = h->fields[h->cur ^ 1];
+    const float m = (float)h->mur_m;
+    Source none{};
+    const Cpml pml = cpml_view(h);   // P = 0 on a Mur grid
+    k_adj_mur_gather<<<dim3((g.nx + 1 + 127) / 128, g.ny + 1, g.nz + 1), 128, 0, h->stream>>>(g, in, out, m);
+    const dim3 blk(32, 8, 1), grd((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+    k_adj_h<<<grd, blk, 0, h->stream>>>(g, out, in + 3 * g.comp, out + 3 * g.comp, pml, (float)-h->kE);
+    k_adj_e<<<grd, blk, 0, h->stream>>>(g, out, out + 3 * g.comp, pml, (float)-h->kH, none);
+    int amax = (g.nx > g.ny ? g.nx : g.ny) + 1;
+    int bmax = (g.ny > g.nz ? g.ny : g.nz) + 1;
+    if (g.nz + 1 > bmax) bmax = g.nz + 1;
+    k_adj_mur_faces<<<dim3((amax + 31) / 32, (bmax + 7) / 8, 6), dim3(32, 8, 1), 0, h->stream>>>(
+        g, in, out, out + 3 * g.comp, (float)h->kH, m);
+    h->launches += 4;
+    h->cur ^= 1;
+}
+
 int note(fdtd_ctx *h, cudaError_t e) {
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -118,6 +244,10 @@ int note(fdtd_ctx *h, cudaError_t e) {
 
 // One transposed step on the current field set (result in the other set).
 void adj_field_step(fdtd_ctx *h) {
+    if (h->boundary == FDTD_MUR1) {
+        adj_field_step_mur(h);
+        return;
+    }
     const double kE = h->kE, kH = h->kH;
     const int active = h->src.active;
     h->kE = -kH;
@@ -138,7 +268,7 @@ void adj_field_step(fdtd_ctx *h) {
     h->cur ^= 1;
 }
 
-bool adjoint_ok(const fdtd_ctx *h) { return h->boundary == FDTD_PEC && h->P == 0; }
+bool adjoint_ok(const fdtd_ctx *h) { return (h->boundary == FDTD_PEC || h->boundary == FDTD_MUR1) && h->P == 0; }
 
 size_t field_bytes(const fdtd_ctx *h) { return 6 * (size_t)h->g.comp * sizeof(float); }
 
