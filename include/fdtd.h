@@ -228,7 +228,7 @@ int fdtd_set_kernel(fdtd_t h, int which);
 /* Human-readable text of a status code (static string). */
 const char *fdtd_strerror(int status);
 
-/* ---- adjoint (PEC and Mur grids) ---------------------------------------- */
+/* ---- adjoint ------------------------------------------------------------- */
 
 /*
  * The step of Sec. III.A is linear in (E^n, H^{n-1/2}) and in the source; on
@@ -237,11 +237,13 @@ const char *fdtd_strerror(int status);
  * (-kH, -kE) and no source; on a Mur grid the transpose of the face update
  * E'_b = E_1^n + m (E'_1 - E_b^n) is folded in (the face cells' adjoint
  * feeds their inward neighbours before the curls, and takes the transposed
- * curl of the new adjoint H after them).
+ * curl of the new adjoint H after them); on a CPML grid the layer memory
+ * psi' = b psi + a d of every difference d gets its adjoint, kept in the
+ * handle's psi memory like the forward's.
  *
  * fdtd_adjoint_step applies n >= 0 transposed steps to the handle's fields
- * (asynchronous; the step counter is not changed).  The handle must have
- * boundary FDTD_PEC or FDTD_MUR1 (FDTD_ERR_ARG for CPML).
+ * (asynchronous; the step counter is not changed; fields and CPML memory
+ * hold the adjoint state).
  *
  * fdtd_adjoint_gradient returns dL/dq_b, the derivative of a loss of the
  * detector traces with respect to the shower's charge table (Sec. III.B),
@@ -250,9 +252,8 @@ const char *fdtd_strerror(int status);
  * dL/d(trace) (slots >= n_steps are not read).  grad_q (n_bins doubles) is a
  * host (on_device = 0) or device pointer.  The adjoint state lives in the
  * handle's field memory: the call leaves the handle reset (fields zero, step
- * counter 0, traces kept).  Needs a shower, detectors, 1 <= n_steps <=
- * max_steps, boundary FDTD_PEC or FDTD_MUR1 (FDTD_ERR_ARG otherwise).
- * Synchronises.
+ * counter 0, CPML memory zero, traces kept).  Needs a shower, detectors,
+ * 1 <= n_steps <= max_steps (FDTD_ERR_ARG otherwise).  Synchronises.
  */
 int fdtd_adjoint_step(fdtd_t h, int n);
 int fdtd_adjoint_gradient(fdtd_t h, const float *dl_dtrace, int n_steps, double *grad_q, int on_device);

@@ -344,7 +344,7 @@ class Simulation:
         check(fdtd_set_kernel(self.h, which), "fdtd_set_kernel")
 
     def adjoint_step(self, n=1):
-        """n transposed steps of the fields (PEC and Mur grids)."""
+        """n transposed steps of the fields and CPML memory."""
         check(fdtd_adjoint_step(self.h, n), "fdtd_adjoint_step")
 
     def adjoint_gradient(self, dl_dtrace, n_steps, out=None):

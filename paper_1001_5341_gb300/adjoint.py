@@ -1,6 +1,6 @@
 """Detector traces as a differentiable function of the shower's charge table.
 
-``TraceModel(sim, ...)`` wraps a PEC or Mur ``Simulation`` with detectors: calling it
+``TraceModel(sim, ...)`` wraps a ``Simulation`` (PEC, Mur or CPML) with detectors: calling it
 with a float64 tensor q of charges per bin (Sec. III.B) runs the FDTD on the
 GPU and returns the traces [n_probes][max_steps][2] (float32, CUDA); the
 backward pass returns dL/dq from the library's adjoint

@@ -1,5 +1,5 @@
 // adjoint.cu -- transposed steps and the gradient of a detector misfit with
-// respect to the shower's charge table (PEC and Mur grids).
+// respect to the shower's charge table (PEC, Mur and CPML grids).
 //
 // The step of Sec. III.A maps u^n = (E^n, H^{n-1/2}) to u^{n+1} linearly:
 //   H' = H - kH C_E E,   E' = E + kE C_H H' + S^n,
@@ -233,6 +233,164 @@ void adj_field_step_mur(fdtd_ctx *h) {
     h->cur ^= 1;
 }
 
+// ---- CPML grids -------------------------------------------------------------
+// A term of an update reads a difference d of one component along one axis;
+// inside that axis' layer psi' = b psi + a d and the term becomes d + psi'.
+// For an E term of sign s: Ec' += kE s (d + psi'); for an H term:
+// Hc' -= kH s (d + psi').  With the adjoints mu (output) of the component and
+// of psi', the adjoint of d is
+//   E term:  G = kE s (1 + a) mu_E' + a mu_psi'
+//   H term:  F = -kH s (1 + a) mu_H + a mu_psi'
+// and the adjoint of the old psi is b (kE s mu_E' + mu_psi') (E) or
+// b (-kH s mu_H + mu_psi') (H).  d is a backward difference of H for an E
+// term (d = H(c) - H(c - off)) and a forward difference of E for an H term
+// (d = E(c + off) - E(c)); its adjoint G (or F) at cell c is added to the
+// component at c (at c + off) and subtracted at c - off (at c).
+// Stage 1 (per cell, the three H components): mu_H = mu_H' + the G of every E
+// term that reads it, then the adjoint of the H psi into the other psi set.
+// Stage 2 (per node, the three E components): mu_E = mu_E' + the F of every H
+// term that reads it, then the adjoint of the E psi in place.
+struct Term {
+    int comp;        // component the term differentiates (0..2 within E or H)
+    int axis;        // axis of the difference (0 x, 1 y, 2 z)
+    int sign;        // +1 first term of the curl, -1 second
+    int psi;         // index t of the psi array of this axis
+};
+// terms of the E update (cell_e) and of the H update (cell_h), per component
+__device__ __constant__ Term kETerms[3][2] = {{{2, 1, +1, 0}, {1, 2, -1, 0}},    // Ex: dy Hz, dz Hy
+                                              {{0, 2, +1, 1}, {2, 0, -1, 0}},    // Ey: dz Hx, dx Hz
+                                              {{1, 0, +1, 1}, {0, 1, -1, 1}}};   // Ez: dx Hy, dy Hx
+__device__ __constant__ Term kHTerms[3][2] = {{{2, 1, +1, 0}, {1, 2, -1, 0}},    // Hx: dy Ez, dz Ey
+                                              {{0, 2, +1, 1}, {2, 0, -1, 0}},    // Hy: dz Ex, dx Ez
+                                              {{1, 0, +1, 1}, {0, 1, -1, 1}}};   // Hz: dx Ey, dy Ex
+
+// psi offset of cell (i,j,k) in the layer of axis a, or -1 outside it
+__device__ __forceinline__ long long psi_at(const Grid &g, const Cpml &pml, int a, int i, int j, int k) {
+    if (a == 0) {
+        const int l = psi_x_pos(i, g.nx, pml.P);
+        return l < 0 ? -1 : psi_x(g, pml.P, l, j, k);
+    }
+    if (a == 1) {
+        const int l = slab_cell(j, g.ny, pml.P);
+        return l < 0 ? -1 : psi_y(g, pml.W, i, l, k);
+    }
+    const int l = slab_cell(k, g.nz, pml.P);
+    return l < 0 ? -1 : psi_z(g, pml.W, i, j, l);
+}
+
+__device__ __forceinline__ bool e_updated(const Grid &g, int c, int i, int j, int k) {
+    if (i < 0 || j < 0 || k < 0 || i >= g.nx || j >= g.ny || k >= g.nz) return false;
+    return c == 0 ? (j >= 1 && k >= 1) : c == 1 ? (i >= 1 && k >= 1) : (i >= 1 && j >= 1);
+}
+__device__ __forceinline__ bool h_updated(const Grid &g, int c, int i, int j, int k) {
+    if (i < 0 || j < 0 || k < 0 || i >= g.nx || j >= g.ny || k >= g.nz) return false;
+    return c == 0 ? i >= 1 : c == 1 ? j >= 1 : k >= 1;
+}
+
+// G of E term (ec, t) at cell (i,j,k): from mu_E' (E set in) and mu_psiE'
+__device__ __forceinline__ float g_term(const Grid &g, const Cpml &pml, const float *Ein, float kE, int ec, int t,
+                                        int i, int j, int k) {
+    if (!e_updated(g, ec, i, j, k)) return 0.f;
+    const Term T = kETerms[ec][t];
+    const long long o = gidx(g, i, j, k);
+    const float mu = Ein[ec * g.comp + o];
+    const long long q = psi_at(g, pml, T.axis, i, j, k);
+    if (q < 0) return kE * T.sign * mu;
+    const int pos = T.axis == 0 ? i : T.axis == 1 ? j : k;
+    const float a = pml.aE[T.axis][pos];
+    return kE * T.sign * (1.f + a) * mu + a * pml.e[T.axis][T.psi][q];
+}
+
+// F of H term (hc, t) at cell (i,j,k): from mu_H (H set out) and mu_psiH' (psi set in)
+__device__ __forceinline__ float f_term(const Grid &g, const Cpml &pml, const float *Hout, float kH, int hc, int t,
+                                        int i, int j, int k) {
+    if (!h_updated(g, hc, i, j, k)) return 0.f;
+    const Term T = kHTerms[hc][t];
+    const long long o = gidx(g, i, j, k);
+    const float mu = Hout[hc * g.comp + o];
+    const long long q = psi_at(g, pml, T.axis, i, j, k);
+    if (q < 0) return -kH * T.sign * mu;
+    const int pos = T.axis == 0 ? i : T.axis == 1 ? j : k;
+    const float a = pml.aH[T.axis][pos];
+    return -kH * T.sign * (1.f + a) * mu + a * pml.hin[T.axis][T.psi][q];
+}
+
+__global__ void __launch_bounds__(256) k_adjc_h(Grid g, Cpml pml, const float *__restrict__ Ein,
+                                                const float *__restrict__ Hin, float *__restrict__ Hout, float kE,
+                                                float kH) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const long long o = gidx(g, i, j, k);
+    for (int hc = 0; hc < 3; ++hc) {
+        if (!h_updated(g, hc, i, j, k)) continue;
+        float v = Hin[hc * g.comp + o];
+        // E terms that read H_hc: a backward difference at c = h (+G) and at c = h + off (-G)
+        for (int ec = 0; ec < 3; ++ec)
+            for (int t = 0; t < 2; ++t) {
+                const Term T = kETerms[ec][t];
+                if (T.comp != hc) continue;
+                const int di = T.axis == 0, dj = T.axis == 1, dk = T.axis == 2;
+                v += g_term(g, pml, Ein, kE, ec, t, i, j, k) - g_term(g, pml, Ein, kE, ec, t, i + di, j + dj, k + dk);
+            }
+        Hout[hc * g.comp + o] = v;
+        // adjoint of the old H psi: b (-kH s mu_H + mu_psi')
+        for (int t = 0; t < 2; ++t) {
+            const Term T = kHTerms[hc][t];
+            const long long q = psi_at(g, pml, T.axis, i, j, k);
+            if (q < 0) continue;
+            const int pos = T.axis == 0 ? i : T.axis == 1 ? j : k;
+            pml.hout[T.axis][T.psi][q] = pml.bH[T.axis][pos] * (-kH * T.sign * v + pml.hin[T.axis][T.psi][q]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_adjc_e(Grid g, Cpml pml, const float *__restrict__ Ein, float *__restrict__ Eout,
+                                                const float *__restrict__ Hout, float kE, float kH) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, k = blockIdx.z;
+    if (i > g.nx || j > g.ny) return;
+    const long long o = gidx(g, i, j, k);
+    for (int ec = 0; ec < 3; ++ec) {
+        // state cells: PEC walls keep the tangential E of the faces at zero
+        const bool state = ec == 0 ? (i <= g.nx - 1 && j >= 1 && j <= g.ny - 1 && k >= 1 && k <= g.nz - 1)
+                         : ec == 1 ? (j <= g.ny - 1 && i >= 1 && i <= g.nx - 1 && k >= 1 && k <= g.nz - 1)
+                                   : (k <= g.nz - 1 && i >= 1 && i <= g.nx - 1 && j >= 1 && j <= g.ny - 1);
+        if (!state) continue;
+        float v = Ein[ec * g.comp + o];
+        // H terms that read E_ec: a forward difference at c = e - off (+F) and at c = e (-F)
+        for (int hc = 0; hc < 3; ++hc)
+            for (int t = 0; t < 2; ++t) {
+                const Term T = kHTerms[hc][t];
+                if (T.comp != ec) continue;
+                const int di = T.axis == 0, dj = T.axis == 1, dk = T.axis == 2;
+                v += f_term(g, pml, Hout, kH, hc, t, i - di, j - dj, k - dk) - f_term(g, pml, Hout, kH, hc, t, i, j, k);
+            }
+        Eout[ec * g.comp + o] = v;
+        // adjoint of the old E psi, in place: b (kE s mu_E' + mu_psi')
+        if (!e_updated(g, ec, i, j, k)) continue;
+        const float mu = Ein[ec * g.comp + o];
+        for (int t = 0; t < 2; ++t) {
+            const Term T = kETerms[ec][t];
+            const long long q = psi_at(g, pml, T.axis, i, j, k);
+            if (q < 0) continue;
+            const int pos = T.axis == 0 ? i : T.axis == 1 ? j : k;
+            float &p = pml.e[T.axis][T.psi][q];
+            p = pml.bE[T.axis][pos] * (kE * T.sign * mu + p);
+        }
+    }
+}
+
+void adj_field_step_cpml(fdtd_ctx *h) {
+    const Grid &g = h->g;
+    const float *in = h->fields[h->cur];
+    float *out = h->fields[h->cur ^ 1];
+    const Cpml pml = cpml_view(h);   // H psi: adjoint in from set cur, out to set cur^1
+    const dim3 blk(32, 8, 1), gh((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz), ge((g.nx + 32) / 32, (g.ny + 8) / 8, g.nz + 1);
+    k_adjc_h<<<gh, blk, 0, h->stream>>>(g, pml, in, in + 3 * g.comp, out + 3 * g.comp, (float)h->kE, (float)h->kH);
+    k_adjc_e<<<ge, blk, 0, h->stream>>>(g, pml, in, out, out + 3 * g.comp, (float)h->kE, (float)h->kH);
+    h->launches += 2;
+    h->cur ^= 1;
+}
+
 int note(fdtd_ctx *h, cudaError_t e) {
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -246,6 +404,10 @@ int note(fdtd_ctx *h, cudaError_t e) {
 void adj_field_step(fdtd_ctx *h) {
     if (h->boundary == FDTD_MUR1) {
         adj_field_step_mur(h);
+        return;
+    }
+    if (h->P > 0) {
+        adj_field_step_cpml(h);
         return;
     }
     const double kE = h->kE, kH = h->kH;
@@ -268,7 +430,7 @@ void adj_field_step(fdtd_ctx *h) {
     h->cur ^= 1;
 }
 
-bool adjoint_ok(const fdtd_ctx *h) { return (h->boundary == FDTD_PEC || h->boundary == FDTD_MUR1) && h->P == 0; }
+bool adjoint_ok(const fdtd_ctx *h) { return h->boundary == FDTD_PEC || h->boundary == FDTD_MUR1 || h->boundary == FDTD_CPML; }
 
 size_t field_bytes(const fdtd_ctx *h) { return 6 * (size_t)h->g.comp * sizeof(float); }
 
@@ -299,6 +461,8 @@ int fdtd_adjoint_gradient(fdtd_t h, const float *dl_dtrace, int n_steps, double 
     int rc = FDTD_OK;
     for (int s = 0; s < 2 && rc == FDTD_OK; ++s)
         rc = note(h, cudaMemsetAsync(h->fields[s], 0, field_bytes(h), h->stream));
+    if (h->psi_block && rc == FDTD_OK)
+        rc = note(h, cudaMemsetAsync(h->psi_block, 0, h->psi_floats * sizeof(float), h->stream));
     h->cur = 0;
     const Probes p{h->np, h->max_steps, h->d_ijk, h->d_cxy, h->d_trace};
     for (int n = n_steps; n >= 1 && rc == FDTD_OK; --n) {
@@ -318,6 +482,8 @@ int fdtd_adjoint_gradient(fdtd_t h, const float *dl_dtrace, int n_steps, double 
     // the adjoint state used the field memory: leave the handle reset
     for (int s = 0; s < 2 && rc == FDTD_OK; ++s)
         rc = note(h, cudaMemsetAsync(h->fields[s], 0, field_bytes(h), h->stream));
+    if (h->psi_block && rc == FDTD_OK)
+        rc = note(h, cudaMemsetAsync(h->psi_block, 0, h->psi_floats * sizeof(float), h->stream));
     h->cur = 0;
     h->steps = 0;
     if (rc == FDTD_OK && !on_device)

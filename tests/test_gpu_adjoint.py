@@ -1,6 +1,7 @@
 """GPU adjoint (fdtd_adjoint_step, fdtd_adjoint_gradient, adjoint.TraceModel):
 the transposed step against the forward step by the dot-product identity
-<M u, mu> = <u, M^T mu> for every field path, PEC and Mur; the gradient of a quadratic
+<M u, mu> = <u, M^T mu> for every field path, PEC and Mur;
+the gradient on PEC, Mur and CPML grids the gradient of a quadratic
 trace misfit with respect to the charge table against exact central
 differences of the FP64 oracle (exact because the loss is quadratic in q),
 against central differences of the GPU forward at h = 1e-3 relative, and
@@ -34,15 +35,19 @@ def _fields(sim):
     return [sim.field(c).astype(np.float64) for c in range(6)]
 
 
-@pytest.mark.parametrize("boundary", ["pec", "mur"])
+@pytest.mark.parametrize("boundary", ["pec", "mur", "cpml"])
 @pytest.mark.parametrize("kernel", [0, 1, 3])
 @pytest.mark.parametrize("n", [1, 7])
 def test_transposed_step_dot_product(fd, kernel, n, boundary):
+    """Random fields with zero CPML memory in both u and mu: the identity
+    then holds on the fields, and over n > 1 steps it covers the memory's
+    whole evolution inside M^n and (M^T)^n."""
     nx, ny, nz = 40, 36, 50
-    bd = fd.FDTD_PEC if boundary == "pec" else fd.FDTD_MUR1
+    bd = {"pec": fd.FDTD_PEC, "mur": fd.FDTD_MUR1, "cpml": fd.FDTD_CPML}[boundary]
+    npml = 6 if boundary == "cpml" else 0
     rng = np.random.default_rng(10 + kernel + n)
-    a = fd.Simulation(nx, ny, nz, DX, DT, W.EPS_R_ICE, boundary=bd)
-    b = fd.Simulation(nx, ny, nz, DX, DT, W.EPS_R_ICE, boundary=bd)
+    a = fd.Simulation(nx, ny, nz, DX, DT, W.EPS_R_ICE, boundary=bd, npml=npml)
+    b = fd.Simulation(nx, ny, nz, DX, DT, W.EPS_R_ICE, boundary=bd, npml=npml)
     for s in (a, b):
         s.set_kernel(kernel)
     u = _rand_fields(rng, a.shape)
@@ -61,11 +66,11 @@ def test_transposed_step_dot_product(fd, kernel, n, boundary):
     scale = np.sqrt(sum(float((x * x).sum()) for x in Mu)) * np.sqrt(sum(float((y * y).sum()) for y in mu0))
     assert abs(lhs - rhs) <= 1e-5 * scale, (lhs, rhs, scale)
     # the transpose is not the step itself
-    assert np.abs(np.concatenate([x.ravel() for x in MTmu]) - np.concatenate([x.ravel() for x in _fields_after(fd, mu, kernel, n, bd)])).max() > 0
+    assert np.abs(np.concatenate([x.ravel() for x in MTmu]) - np.concatenate([x.ravel() for x in _fields_after(fd, mu, kernel, n, bd, npml)])).max() > 0
 
 
-def _fields_after(fd, f, kernel, n, bd):
-    s = fd.Simulation(40, 36, 50, DX, DT, W.EPS_R_ICE, boundary=bd)
+def _fields_after(fd, f, kernel, n, bd, npml):
+    s = fd.Simulation(40, 36, 50, DX, DT, W.EPS_R_ICE, boundary=bd, npml=npml)
     s.set_kernel(kernel)
     for c in range(6):
         s.set_field(c, f[c])
@@ -73,8 +78,8 @@ def _fields_after(fd, f, kernel, n, bd):
     return _fields(s)
 
 
-def _problem(nbins=24):
-    nx, ny, nz = 24, 24, 48
+def _problem(nbins=24, boundary=None):
+    nx, ny, nz = (40, 40, 64) if boundary == "cpml" else (24, 24, 48)
     steps = 100
     z0, bin_dz = 0.06, 0.05
     zb = z0 + bin_dz * np.arange(nbins)
@@ -85,11 +90,16 @@ def _problem(nbins=24):
     cx, cy = nx // 2 * DX, ny // 2 * DX
     xyz = np.array([[cx + 0.10, cy, 0.30], [cx, cy + 0.16, 0.55], [cx - 0.12, cy - 0.08, 0.80],
                     [cx + 0.2, cy + 0.06, 0.42]])
-    return dict(nx=nx, ny=ny, nz=nz, steps=steps, q=q, z0=z0, bin_dz=bin_dz, v=W.C0, w=w, L=L, xyz=xyz)
+    P = dict(nx=nx, ny=ny, nz=nz, steps=steps, q=q, z0=z0, bin_dz=bin_dz, v=W.C0, w=w, L=L, xyz=xyz, npml=0)
+    if boundary is not None:
+        P["boundary"] = {"pec": oracle.PEC, "mur": oracle.MUR1, "cpml": oracle.CPML}[boundary]
+        P["npml"] = 6 if boundary == "cpml" else 0
+    return P
 
 
 def _oracle_traces(P, q):
-    o = oracle.Oracle(P["nx"], P["ny"], P["nz"], DX, DT, W.EPS_R_ICE, boundary=P.get("boundary", oracle.PEC))
+    o = oracle.Oracle(P["nx"], P["ny"], P["nz"], DX, DT, W.EPS_R_ICE, boundary=P.get("boundary", oracle.PEC),
+                      npml=P["npml"])
     o.set_shower(q, P["z0"], P["bin_dz"], P["v"], P["w"], P["L"])
     o.set_probes(P["xyz"], P["steps"])
     o.step(P["steps"])
@@ -97,7 +107,8 @@ def _oracle_traces(P, q):
 
 
 def _gpu_sim(fd, P):
-    s = fd.Simulation(P["nx"], P["ny"], P["nz"], DX, DT, W.EPS_R_ICE, boundary=P.get("boundary", fd.FDTD_PEC))
+    s = fd.Simulation(P["nx"], P["ny"], P["nz"], DX, DT, W.EPS_R_ICE, boundary=P.get("boundary", fd.FDTD_PEC),
+                      npml=P["npml"])
     s.set_probes(P["xyz"], P["steps"])
     return s
 
@@ -109,11 +120,10 @@ def _gpu_traces(s, P, q):
     return s.probes().astype(np.float64)
 
 
-@pytest.mark.parametrize("boundary", ["pec", "mur"])
+@pytest.mark.parametrize("boundary", ["pec", "mur", "cpml"])
 def test_gradient_matches_exact_oracle_differences(fd, boundary):
     import torch
-    P = _problem()
-    P["boundary"] = oracle.PEC if boundary == "pec" else oracle.MUR1
+    P = _problem(boundary=boundary)
     q = P["q"]
     target = _oracle_traces(P, q * 0.8 + 2e-11 * np.cos(np.arange(q.size)))
     # L(q) = 1/2 sum (y - target)^2 is quadratic in q: central differences are exact
@@ -169,9 +179,6 @@ def test_autograd_function(fd):
 def test_adjoint_argument_checks(fd):
     import torch
     P = _problem()
-    cpml = fd.Simulation(40, 40, 40, DX, DT, W.EPS_R_ICE, boundary=fd.FDTD_CPML, npml=6)
-    with pytest.raises(fd.FdtdError):
-        cpml.adjoint_step(1)
     s = _gpu_sim(fd, P)
     dl = torch.zeros((4, P["steps"], 2), dtype=torch.float32, device="cuda")
     with pytest.raises(fd.FdtdError):       # no shower
