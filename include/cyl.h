@@ -76,7 +76,9 @@ int cyl_step(cyl_t h, int n);
  * per lane, 2 = K 8 with 2, 3 = K 4 with 4, 4 = K 4 with 4 and registers
  * bounded for 4 blocks per SM, 5 = K 8 with 2 bounded the same way.
  * seg_rows = radial rows per warp segment (at most 1024), 0 picks it from the
- * grid and the SM count.  FDTD_ERR_ARG for another index.  The default is 3.
+ * grid and the SM count.  FDTD_ERR_ARG for another index.  The default
+ * depends on the grid: 0 below 400000 cells (its steps are replayed from
+ * captured graphs of 32 steps), 1 below 1600000 cells, 3 above.
  */
 int cyl_set_kernel(cyl_t h, int which, int seg_rows);
 

@@ -106,8 +106,11 @@ struct Dev {
 // ---------------------------------------------------------------------------
 // Two-kernel path
 // ---------------------------------------------------------------------------
-__global__ void k_cyl_h(Dev D, float kH) {
+// nstep: index of the step being taken, advanced here so that a captured
+// sequence of steps can be replayed (the E and detector kernels read it).
+__global__ void k_cyl_h(Dev D, float kH, long long *nstep) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) ++*nstep;
     if (i >= D.nr || j >= D.nz) return;
     const long long o = (long long)i * D.pitch + j;
     const float der = D.f.Er[o + 1] - D.f.Er[o];
@@ -120,8 +123,9 @@ __global__ void k_cyl_h(Dev D, float kH) {
 // E_z(nr-1, j) the wall E_z(nr, j) (first-order Mur from the old and new
 // values next to them, or zero for PEC); no other thread of the launch reads
 // or writes those cells.
-__global__ void k_cyl_e(Dev D, float kE, float mur, int mur_on, Src S, long long n) {
+__global__ void k_cyl_e(Dev D, float kE, float mur, int mur_on, Src S, const long long *nstep) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+    const long long n = *nstep;
     const int nr = D.nr, nz = D.nz;
     if (i >= nr || j > nz) return;
     const long long o = (long long)i * D.pitch + j;
@@ -145,9 +149,10 @@ __global__ void k_cyl_e(Dev D, float kE, float mur, int mur_on, Src S, long long
     }
 }
 
-__global__ void k_cyl_probes(Dev D, const int *ij, int np, float *trace, int max_steps, long long slot) {
+__global__ void k_cyl_probes(Dev D, const int *ij, int np, float *trace, int max_steps, const long long *nstep) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= np) return;
+    const long long slot = *nstep;
     const int i = ij[2 * p], j = ij[2 * p + 1];
     const long long o = (long long)i * D.pitch + j;
     const float ez = 0.5f * (D.f.Ez[o - 1] + D.f.Ez[o]);
@@ -613,6 +618,14 @@ struct cyl_ctx {
     int kernel, K, CPL, U, L, nbands, nseg, seg_req;
     long long steps, launches;
     int status;
+    // two-kernel path: device step index, and graphs of G2K steps per set
+    long long *d_step;
+    long long step_host;     // staging of the step index upload
+    bool step_ok;            // d_step equals steps - 1
+    cudaStream_t gstream;
+    cudaEvent_t gev;
+    cudaGraphExec_t g2k[2];
+    bool graph_off;
 };
 
 namespace {
@@ -747,6 +760,15 @@ int configure(cyl_ctx *h, int which, int seg_rows) {
     return build_wave_probes(h);
 }
 
+// Default kernel by grid size (measured on the Table I grids): below about
+// 630^2 cells the two-kernel path replayed from graphs (the wavefront's warps
+// are too few to hide their step latency), up to about 1250^2 the wavefront
+// with 2 columns per lane (twice the warps), above it 4 columns per lane.
+int default_kernel(int nr, int nz) {
+    const long long cells = (long long)nr * nz;
+    return cells < 400000 ? 0 : cells < 1600000 ? 1 : 3;
+}
+
 Dev dev_of(const cyl_ctx *h) {
     Dev D;
     D.nr = h->nr;
@@ -757,18 +779,76 @@ Dev dev_of(const cyl_ctx *h) {
     return D;
 }
 
-void launch_two_kernel(cyl_ctx *h) {
+constexpr int G2K = 32;   // steps per captured graph of the two-kernel path
+
+// One step of the two-kernel path on stream st (host counters not touched).
+void issue_two_kernel(cyl_ctx *h, cudaStream_t st) {
     const Dev D = dev_of(h);
     const dim3 blk(256), gh((h->nz + 255) / 256, h->nr), ge((h->nz + 1 + 255) / 256, h->nr);
-    k_cyl_h<<<gh, blk, 0, h->stream>>>(D, (float)h->kH);
-    k_cyl_e<<<ge, blk, 0, h->stream>>>(D, (float)h->kE, (float)h->mur, h->boundary == FDTD_MUR1, h->src, h->steps);
-    h->launches += 2;
-    if (h->np > 0) {
-        k_cyl_probes<<<(h->np + 127) / 128, 128, 0, h->stream>>>(D, h->d_ij, h->np, h->d_trace, h->max_steps,
-                                                                 h->steps);
-        h->launches++;
+    k_cyl_h<<<gh, blk, 0, st>>>(D, (float)h->kH, h->d_step);
+    k_cyl_e<<<ge, blk, 0, st>>>(D, (float)h->kE, (float)h->mur, h->boundary == FDTD_MUR1, h->src, h->d_step);
+    if (h->np > 0)
+        k_cyl_probes<<<(h->np + 127) / 128, 128, 0, st>>>(D, h->d_ij, h->np, h->d_trace, h->max_steps, h->d_step);
+}
+
+void drop_graphs(cyl_ctx *h) {
+    for (int c = 0; c < 2; ++c)
+        if (h->g2k[c]) {
+            cudaGraphExecDestroy(h->g2k[c]);
+            h->g2k[c] = nullptr;
+        }
+}
+
+int sync_step_index(cyl_ctx *h) {
+    if (h->step_ok) return FDTD_OK;
+    h->step_host = h->steps - 1;
+    if (note(h, cudaMemcpyAsync(h->d_step, &h->step_host, sizeof(long long), cudaMemcpyHostToDevice, h->stream)) !=
+        FDTD_OK)
+        return h->status;
+    h->step_ok = true;
+    return note(h, cudaStreamSynchronize(h->stream));   // the staging value is read before it changes
+}
+
+// n steps of the two-kernel path: whole graphs of G2K steps replayed on a
+// private stream (ordered with the handle's stream by events), the rest
+// launched directly.
+void launch_two_kernel(cyl_ctx *h, int n) {
+    if (sync_step_index(h) != FDTD_OK) return;
+    int reps = h->graph_off ? 0 : n / G2K;
+    if (reps > 0 && !h->g2k[h->cur]) {
+        cudaGraph_t graph = nullptr;
+        bool ok = cudaEventRecord(h->gev, h->stream) == cudaSuccess &&
+                  cudaStreamWaitEvent(h->gstream, h->gev, 0) == cudaSuccess &&
+                  cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            for (int s = 0; s < G2K; ++s) issue_two_kernel(h, h->gstream);
+            ok = cudaStreamEndCapture(h->gstream, &graph) == cudaSuccess && graph &&
+                 cudaGraphInstantiate(&h->g2k[h->cur], graph, 0) == cudaSuccess;
+        }
+        if (graph) cudaGraphDestroy(graph);
+        if (!ok) {
+            cudaGetLastError();
+            h->g2k[h->cur] = nullptr;
+            h->graph_off = true;
+            reps = 0;
+        }
     }
-    h->steps++;
+    if (reps > 0) {
+        if (note(h, cudaEventRecord(h->gev, h->stream)) || note(h, cudaStreamWaitEvent(h->gstream, h->gev, 0)))
+            return;
+        for (int r = 0; r < reps; ++r)
+            if (note(h, cudaGraphLaunch(h->g2k[h->cur], h->gstream)) != FDTD_OK) return;
+        if (note(h, cudaEventRecord(h->gev, h->gstream)) || note(h, cudaStreamWaitEvent(h->stream, h->gev, 0)))
+            return;
+        h->launches += (long long)reps * G2K * (h->np > 0 ? 3 : 2);
+        h->steps += (long long)reps * G2K;
+        n -= reps * G2K;
+    }
+    for (; n > 0; --n) {
+        issue_two_kernel(h, h->stream);
+        h->launches += h->np > 0 ? 3 : 2;
+        h->steps++;
+    }
 }
 
 void launch_wave(cyl_ctx *h) {
@@ -799,6 +879,7 @@ void launch_wave(cyl_ctx *h) {
     h->launches++;
     h->cur ^= 1;
     h->steps += v.K;
+    h->step_ok = false;
 }
 
 size_t comp_rows(const cyl_ctx *h, int comp) { return comp == 1 ? (size_t)h->nr + 1 : (size_t)h->nr; }
@@ -846,7 +927,9 @@ int cyl_create(cyl_t *out, int nr, int nz, double d, double dt, double eps_r, in
     for (int i = 1; i <= nr; ++i)
         rowc[i] = make_float2((float)(h->kE * (i + 0.5) / i), (float)(h->kE * (i - 0.5) / i));
     if (cudaMalloc(&h->block, bytes) != cudaSuccess || cudaMalloc(&h->d_rowc, (nr + 1) * sizeof(float2)) != cudaSuccess ||
-        cudaMalloc(&h->d_flags, sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&h->d_flags, sizeof(int)) != cudaSuccess || cudaMalloc(&h->d_step, sizeof(long long)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->gev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         cyl_destroy(h);
         return FDTD_ERR_OOM;
@@ -862,7 +945,7 @@ int cyl_create(cyl_t *out, int nr, int nz, double d, double dt, double eps_r, in
     note(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int), h->stream));
     note(h, cudaMemcpyAsync(h->d_rowc, rowc.data(), rowc.size() * sizeof(float2), cudaMemcpyHostToDevice, h->stream));
     note(h, cudaStreamSynchronize(h->stream));
-    if (h->status == FDTD_OK) h->status = configure(h, 3, 0);
+    if (h->status == FDTD_OK) h->status = configure(h, default_kernel(nr, nz), 0);
     if (h->status != FDTD_OK) {
         const int st = h->status;
         cyl_destroy(h);
@@ -874,11 +957,16 @@ int cyl_create(cyl_t *out, int nr, int nz, double d, double dt, double eps_r, in
 
 void cyl_destroy(cyl_t h) {
     if (!h) return;
+    if (h->gstream) cudaStreamSynchronize(h->gstream);
+    drop_graphs(h);
     free_src(h);
     free_probes(h);
     if (h->block) cudaFree(h->block);
     if (h->d_rowc) cudaFree(h->d_rowc);
     if (h->d_flags) cudaFree(h->d_flags);
+    if (h->d_step) cudaFree(h->d_step);
+    if (h->gev) cudaEventDestroy(h->gev);
+    if (h->gstream) cudaStreamDestroy(h->gstream);
     delete h;
 }
 
@@ -904,6 +992,8 @@ int cyl_set_shower(cyl_t h, const double *q, int n_bins, double z0, double bin_d
         !std::isfinite(v) || std::fabs(v) * h->dt > 4.0 * h->d)
         return FDTD_ERR_ARG;
     if (h->status != FDTD_OK) return h->status;
+    if (note(h, cudaStreamSynchronize(h->gstream)) != FDTD_OK) return h->status;
+    drop_graphs(h);
     free_src(h);
     std::vector<float> coef(nw);
     for (int i = 0; i < nw; ++i) {
@@ -943,6 +1033,8 @@ int cyl_set_probes(cyl_t h, const double *rz, int n, int max_steps) {
         ij[2 * p] = (int)fi;
         ij[2 * p + 1] = (int)fj;
     }
+    if (note(h, cudaStreamSynchronize(h->gstream)) != FDTD_OK) return h->status;
+    drop_graphs(h);
     free_probes(h);
     if (n == 0) {
         // the wavefront kernel reads its (empty) per-warp lists
@@ -973,7 +1065,7 @@ int cyl_step(cyl_t h, int n) {
     if (h->np > 0 && h->steps + n > h->max_steps) return FDTD_ERR_CAPACITY;
     if (h->kernel > 0)
         for (; n >= h->K; n -= h->K) launch_wave(h);
-    for (; n > 0; --n) launch_two_kernel(h);
+    if (n > 0) launch_two_kernel(h, n);
     return note(h, cudaGetLastError());
 }
 
@@ -1037,6 +1129,7 @@ int cyl_reset(cyl_t h) {
         return h->status;
     h->steps = 0;
     h->cur = 0;
+    h->step_ok = false;
     return cyl_sync(h);
 }
 
