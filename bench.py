@@ -159,6 +159,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(vals, ws, device="cpu"):
+    """Element-wise maximum of a list of floats over the ranks of the process
+    group (the slowest replica sets the time); the identity with one rank."""
+    import torch
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def replica_workload(rank, **kw):
+    """The benchmark shower of one replica: rank r draws seed 2002 + r."""
+    return W.greisen384(seed=2002 + rank, **kw)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -170,8 +186,7 @@ def run_ours(args):
     import paper_1001_5341_gb300 as fd
 
     # each replica draws its own shower; rank 0 runs the named seed
-    w = W.greisen384(seed=2002 + rank, steps=args.warmup + args.steps,
-                     **({"nz": args.nz} if args.nz else {}))
+    w = replica_workload(rank, steps=args.warmup + args.steps, **({"nz": args.nz} if args.nz else {}))
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         sim = fd.Simulation.from_workload(w, max_steps=args.warmup + args.steps, stream=stream)
@@ -220,10 +235,7 @@ def run_ours(args):
         kernel_name = sim.kernel_name
         sim.close()
 
-    t = torch.tensor([ms, e2e_s * 1e3], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max, e2e_ms_max = float(t[0]), float(t[1])
+    ms_max, e2e_ms_max = max_over_ranks([ms, e2e_s * 1e3], ws, device="cuda")
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
