@@ -184,6 +184,8 @@ struct Wave {
     float *trace;
     int max_steps;
     int *flags;
+    unsigned *tiles;         // tile counter, zero at launch
+    int ntiles;              // segments x groups of NW bands
 };
 
 __device__ __forceinline__ uint32_t sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -437,6 +439,11 @@ __device__ __forceinline__ bool march_step(const Wave &A, const Band<K, CPL> &w,
     return true;
 }
 
+// Persistent: the grid is one wave of resident blocks; each block takes tiles
+// (segment g, group of NW bands) from an atomic counter until none is left,
+// so blocks that draw slow tiles (end caps, source rows, wall, detectors) do
+// not hold the launch.  A warp's ring position and parity carry over from
+// tile to tile: every row a tile issues is consumed within the tile.
 template <int K, int CPL, int MINB, int STAGES>
 __global__ void __launch_bounds__(NW * 32, MINB) k_cyl_wave(Wave A) {
     constexpr int W = 32 * CPL;          // columns per warp
@@ -450,126 +457,142 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_cyl_wave(Wave A) {
     __shared__ __align__(16) float2 srowc[LMAX + 2 * K];
     __shared__ __align__(16) float swall[NW][K * W];
     __shared__ int spc[NW][K + 1], sprow[NW][K + 1];
+    __shared__ int s_tile, s_dead;
 
     const int tid = threadIdx.x, lane = tid & 31, wi = tid >> 5;
-    const int g = blockIdx.y;
     const int nr = A.nr, nz = A.nz;
-    const int own0 = g * A.L, own1 = min(own0 + A.L, nr + 1);   // owned rows [own0, own1)
-    const int p0 = max(0, own0 - K);
-    const int p_end = own1 - 1 + K;
     if (A.src.active && tid < K * MSRC) {
         const int s = tid / MSRC, m = tid % MSRC;
         const int jlo = src_jlo(A.src, A.n0 + s);
         if (m == 0) sjlo[s] = jlo;
         ssrc[s][m] = src_face(A.src, A.n0 + s, jlo + m);
     }
-    for (int t = tid; p0 + t <= min(p_end, nr); t += NW * 32) srowc[t] = A.rowc[p0 + t];
     if (lane == 0) {
         for (int s = 0; s < STAGES; ++s) mbar_init(&bars[wi][s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    __syncthreads();
+    if (tid == 0) s_dead = 0;
+    int ring_st = 0;            // this warp's next stage and its parity, across tiles
+    uint32_t ring_phase = 0;
+    const int bxn = (A.nbands + NW - 1) / NW;
 
-    Band<K, CPL> w;
-    w.b = blockIdx.x * NW + wi;
-    if (w.b >= A.nbands) return;
-    w.lane = lane;
-    w.own0 = own0;
-    w.own1 = own1;
-    w.p0 = p0;
-    w.load_end = min(p_end, nr);
-    w.col0 = w.b * A.U - HL;
-    const int oc0 = w.b * A.U, oc1 = min(oc0 + A.U, nz + 1);   // owned columns [oc0, oc1)
-    w.ring = smem + wi * STAGES * STAGE;
-    w.bar = bars[wi];
-    w.rowc = srowc;
-    w.wall = swall[wi];
-    w.pc = spc[wi];
-    w.prow = sprow[wi];
-    const int c0 = w.col0 + lane * CPL;
-    w.owned = c0 >= oc0 && c0 < oc1;                    // a lane owns all or none of its columns
-    w.cap_lo = w.b == 0 && lane == HL / CPL;            // holds columns 0 and 1
-    w.cap_hi = nz - w.col0 >= 1 && nz - w.col0 < W;     // this warp holds columns nz - 1 and nz
-    const bool caps = w.b == 0 || w.cap_hi;
+    for (;;) {
+        __syncthreads();   // the previous tile is done with the shared tables
+        if (tid == 0) s_tile = (int)atomicAdd(A.tiles, 1u);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= A.ntiles || s_dead) break;
+        const int g = tile / bxn, bx = tile - g * bxn;
+        const int own0 = g * A.L, own1 = min(own0 + A.L, nr + 1);   // owned rows [own0, own1)
+        const int p0 = max(0, own0 - K);
+        const int p_end = own1 - 1 + K;
+        for (int t = tid; p0 + t <= min(p_end, nr); t += NW * 32) srowc[t] = A.rowc[p0 + t];
+        __syncthreads();
 
-    March<K, CPL> S;
-    if (lane == 0)
-        for (int s = 0; s < STAGES && p0 + s <= w.load_end; ++s)
-            issue_row<CPL>(A, w.ring, w.bar, (long long)(p0 + s) * A.pitch + w.col0, s);
-    S.ld_off = (long long)(p0 + STAGES) * A.pitch + w.col0;
-    S.st_off = (long long)(p0 - K) * A.pitch + c0;   // row p - K at step p
-    {
-        const int wid = g * A.nbands + w.b;
-        const int pbeg = A.poff[wid];
-        w.pfin = A.poff[wid + 1];
-        const int r0 = pbeg < w.pfin ? A.prec[pbeg].x : NO_ROW;
-        if (lane <= K) {
-            w.pc[lane] = pbeg;
-            w.prow[lane] = r0;
+        Band<K, CPL> w;
+        w.b = bx * NW + wi;
+        if (w.b >= A.nbands) continue;
+        w.lane = lane;
+        w.own0 = own0;
+        w.own1 = own1;
+        w.p0 = p0;
+        w.load_end = min(p_end, nr);
+        w.col0 = w.b * A.U - HL;
+        const int oc0 = w.b * A.U, oc1 = min(oc0 + A.U, nz + 1);   // owned columns [oc0, oc1)
+        w.ring = smem + wi * STAGES * STAGE;
+        w.bar = bars[wi];
+        w.rowc = srowc;
+        w.wall = swall[wi];
+        w.pc = spc[wi];
+        w.prow = sprow[wi];
+        const int c0 = w.col0 + lane * CPL;
+        w.owned = c0 >= oc0 && c0 < oc1;                    // a lane owns all or none of its columns
+        w.cap_lo = w.b == 0 && lane == HL / CPL;            // holds columns 0 and 1
+        w.cap_hi = nz - w.col0 >= 1 && nz - w.col0 < W;     // this warp holds columns nz - 1 and nz
+        const bool caps = w.b == 0 || w.cap_hi;
+
+        March<K, CPL> S;
+        if (lane == 0)
+            for (int s = 0; s < STAGES && p0 + s <= w.load_end; ++s)
+                issue_row<CPL>(A, w.ring, w.bar, (long long)(p0 + s) * A.pitch + w.col0, (ring_st + s) % STAGES);
+        S.ld_off = (long long)(p0 + STAGES) * A.pitch + w.col0;
+        S.st_off = (long long)(p0 - K) * A.pitch + c0;   // row p - K at step p
+        {
+            const int wid = g * A.nbands + w.b;
+            const int pbeg = A.poff[wid];
+            w.pfin = A.poff[wid + 1];
+            const int r0 = pbeg < w.pfin ? A.prec[pbeg].x : NO_ROW;
+            if (lane <= K) {
+                w.pc[lane] = pbeg;
+                w.prow[lane] = r0;
+            }
+            S.prowK = r0;
+            __syncwarp();
         }
-        S.prowK = r0;
-        __syncwarp();
-    }
 #pragma unroll
-    for (int s = 0; s <= K; ++s)
+        for (int s = 0; s <= K; ++s)
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) {
-            S.prv[s].er[q] = S.prv[s].ez[q] = S.prv[s].h[q] = 0.f;
-            S.cur[s].er[q] = S.cur[s].ez[q] = S.cur[s].h[q] = 0.f;
-        }
-    S.st = 0;
-    S.phase = 0;
+            for (int q = 0; q < CPL; ++q) {
+                S.prv[s].er[q] = S.prv[s].ez[q] = S.prv[s].h[q] = 0.f;
+                S.cur[s].er[q] = S.cur[s].ez[q] = S.cur[s].h[q] = 0.f;
+            }
+        S.st = ring_st;
+        S.phase = ring_phase;
 
-    // lean steps: every level on a row in [max(p0, source rows), nr - 2], all
-    // columns inside [0, nz), no detector on the rows p - K .. p - 1 of the step
-    const int src_end = A.src.active ? A.src.nw : 0;
-    const int lean_lo = max(p0, src_end) + K, lean_hi = min(nr - 1, p_end);
-    int failed_at = -1;
-    int p = p0;
-    while (p <= p_end) {
-        const int stop = min(lean_hi, S.prowK);
-        if (p >= lean_lo && p <= stop) {
-            bool ok = true;
-            if (caps) {
-                for (; ok && p <= stop; ++p) ok = march_step<K, CPL, STAGES, false, true>(A, w, S, p, sjlo, ssrc);
+        // lean steps: every level on a row in [max(p0, source rows), nr - 2], all
+        // columns inside [0, nz), no detector on the rows p - K .. p - 1 of the step
+        const int src_end = A.src.active ? A.src.nw : 0;
+        const int lean_lo = max(p0, src_end) + K, lean_hi = min(nr - 1, p_end);
+        int failed_at = -1;
+        int p = p0;
+        while (p <= p_end) {
+            const int stop = min(lean_hi, S.prowK);
+            if (p >= lean_lo && p <= stop) {
+                bool ok = true;
+                if (caps) {
+                    for (; ok && p <= stop; ++p) ok = march_step<K, CPL, STAGES, false, true>(A, w, S, p, sjlo, ssrc);
+                } else {
+                    for (; ok && p + 1 <= stop; p += 2) {
+                        ok = march_step<K, CPL, STAGES, false, false>(A, w, S, p, sjlo, ssrc);
+                        if (ok) ok = march_step<K, CPL, STAGES, false, false>(A, w, S, p + 1, sjlo, ssrc);
+                    }
+                    if (ok && p <= stop) {
+                        ok = march_step<K, CPL, STAGES, false, false>(A, w, S, p, sjlo, ssrc);
+                        ++p;
+                    }
+                }
+                if (!ok) {
+                    failed_at = p;
+                    break;
+                }
             } else {
-                for (; ok && p + 1 <= stop; p += 2) {
-                    ok = march_step<K, CPL, STAGES, false, false>(A, w, S, p, sjlo, ssrc);
-                    if (ok) ok = march_step<K, CPL, STAGES, false, false>(A, w, S, p + 1, sjlo, ssrc);
+                if (!march_step<K, CPL, STAGES, true, true>(A, w, S, p, sjlo, ssrc)) {
+                    failed_at = p;
+                    break;
                 }
-                if (ok && p <= stop) {
-                    ok = march_step<K, CPL, STAGES, false, false>(A, w, S, p, sjlo, ssrc);
-                    ++p;
-                }
-            }
-            if (!ok) {
-                failed_at = p;
-                break;
-            }
-        } else {
-            if (!march_step<K, CPL, STAGES, true, true>(A, w, S, p, sjlo, ssrc)) {
-                failed_at = p;
-                break;
-            }
-            ++p;
-        }
-    }
-    if (failed_at >= 0) {
-        // give up: flag it, and let the copies still in flight land before the block ends
-        if (lane == 0) {
-            atomicOr(A.flags, 1);
-            int s2 = S.st;
-            uint32_t ph = S.phase;
-            for (int m = 0; m < STAGES && failed_at + m <= w.load_end; ++m) {
-                mbar_wait(&w.bar[s2], ph);
-                if (++s2 == STAGES) {
-                    s2 = 0;
-                    ph ^= 1u;
-                }
+                ++p;
             }
         }
-        __syncwarp();
+        ring_st = S.st;
+        ring_phase = S.phase;
+        if (failed_at >= 0) {
+            // give up: flag it, let the copies still in flight land, stop the block
+            if (lane == 0) {
+                atomicOr(A.flags, 1);
+                s_dead = 1;
+                int s2 = S.st;
+                uint32_t ph = S.phase;
+                for (int m = 0; m < STAGES && failed_at + m <= w.load_end; ++m) {
+                    mbar_wait(&w.bar[s2], ph);
+                    if (++s2 == STAGES) {
+                        s2 = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+            __syncwarp();
+        }
     }
 }
 
@@ -626,6 +649,8 @@ struct cyl_ctx {
     cudaEvent_t gev;
     cudaGraphExec_t g2k[2];
     bool graph_off;
+    unsigned *d_tiles;       // wavefront tile counter
+    int slots;               // resident blocks of the wavefront kernel in use
 };
 
 namespace {
@@ -672,13 +697,8 @@ int read_extent(int nz) {
     return e;
 }
 
-// Rows per segment.  A block marches L + 2K rows; blocks differ in speed (the
-// warps holding the end caps, the source rows near the axis, the wall and the
-// detectors take extra work), so the launch ends about one block duration
-// after the average SM is done: cost = (L + 2K + setup) x (blocks / slots + 1),
-// the smallest cost wins.
-int choose_L(cyl_ctx *h) {
-    if (h->seg_req > 0) return std::min(std::min(h->seg_req, h->nr + 1), LMAX);
+// Resident blocks of the wavefront kernel in use (the persistent grid).
+int wave_slots(const cyl_ctx *h) {
     int dev = 0, sms = 152, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -688,11 +708,23 @@ int choose_L(cyl_ctx *h) {
         cudaGetLastError();
         per_sm = 1;
     }
-    const double slots = (double)sms * per_sm;
+    return sms * per_sm;
+}
+
+// Rows per segment.  A tile marches L + 2K rows (2K of them halo); the
+// resident blocks take tiles from a queue.  Tiles differ in speed (caps,
+// source rows, wall, detectors) and a block's warps wait for each other at
+// every tile, so the launch ends about one tile time after the average
+// block: cost = (L + 2K + setup) x (tiles / slots + 1), the smallest cost
+// wins (measured optimum on the Table I grids: 64, 32 and 16 rows on 8192^2,
+// 4096^2 and 2048^2).
+int choose_L(cyl_ctx *h) {
+    if (h->seg_req > 0) return std::min(std::min(h->seg_req, h->nr + 1), LMAX);
+    const double slots = (double)std::max(1, h->slots);
     const long long bx = (h->nbands + NW - 1) / NW;
     int best = std::min(h->nr + 1, LMAX);
     double best_cost = 1e300;
-    for (int L = 32; L <= std::min(h->nr + 1 + 15, LMAX); L += 16) {
+    for (int L = 16; L <= std::min(h->nr + 1 + 15, LMAX); L += 16) {
         const int Lc = std::min(L, h->nr + 1);
         const long long nseg = (h->nr + 1 + Lc - 1) / Lc;
         const double cost = (double)(Lc + 2 * h->K + 8) * ((double)(bx * nseg) / slots + 1.0);
@@ -754,6 +786,7 @@ int configure(cyl_ctx *h, int which, int seg_rows) {
         h->CPL = v.CPL;
         h->U = 32 * v.CPL - 2 * v.K;
         h->nbands = (h->nz + 1 + h->U - 1) / h->U;
+        h->slots = wave_slots(h);
         h->L = choose_L(h);
         h->nseg = (h->nr + 1 + h->L - 1) / h->L;
     }
@@ -874,7 +907,10 @@ void launch_wave(cyl_ctx *h) {
     A.trace = h->d_trace;
     A.max_steps = h->max_steps;
     A.flags = h->d_flags;
-    const dim3 grid((h->nbands + NW - 1) / NW, h->nseg);
+    A.tiles = h->d_tiles;
+    A.ntiles = h->nseg * ((h->nbands + NW - 1) / NW);
+    note(h, cudaMemsetAsync(h->d_tiles, 0, sizeof(unsigned), h->stream));
+    const int grid = std::min(A.ntiles, std::max(1, h->slots));
     v.fn<<<grid, NW * 32, ring_bytes(v), h->stream>>>(A);
     h->launches++;
     h->cur ^= 1;
@@ -928,6 +964,7 @@ int cyl_create(cyl_t *out, int nr, int nz, double d, double dt, double eps_r, in
         rowc[i] = make_float2((float)(h->kE * (i + 0.5) / i), (float)(h->kE * (i - 0.5) / i));
     if (cudaMalloc(&h->block, bytes) != cudaSuccess || cudaMalloc(&h->d_rowc, (nr + 1) * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&h->d_flags, sizeof(int)) != cudaSuccess || cudaMalloc(&h->d_step, sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&h->d_tiles, sizeof(unsigned)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->gev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
@@ -965,6 +1002,7 @@ void cyl_destroy(cyl_t h) {
     if (h->d_rowc) cudaFree(h->d_rowc);
     if (h->d_flags) cudaFree(h->d_flags);
     if (h->d_step) cudaFree(h->d_step);
+    if (h->d_tiles) cudaFree(h->d_tiles);
     if (h->gev) cudaEventDestroy(h->gev);
     if (h->gstream) cudaStreamDestroy(h->gstream);
     delete h;
