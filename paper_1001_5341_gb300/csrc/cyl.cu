@@ -715,7 +715,7 @@ int wave_slots(const cyl_ctx *h) {
 // resident blocks take tiles from a queue.  Tiles differ in speed (caps,
 // source rows, wall, detectors) and a block's warps wait for each other at
 // every tile, so the launch ends about one tile time after the average
-// block: cost = (L + 2K + setup) x (tiles / slots + 1), the smallest cost
+// block: cost = (L + 2K + setup) x (tiles / slots + 1.2), the smallest cost
 // wins (measured optimum on the Table I grids: 64, 32 and 16 rows on 8192^2,
 // 4096^2 and 2048^2).
 int choose_L(cyl_ctx *h) {
@@ -727,7 +727,7 @@ int choose_L(cyl_ctx *h) {
     for (int L = 16; L <= std::min(h->nr + 1 + 15, LMAX); L += 16) {
         const int Lc = std::min(L, h->nr + 1);
         const long long nseg = (h->nr + 1 + Lc - 1) / Lc;
-        const double cost = (double)(Lc + 2 * h->K + 8) * ((double)(bx * nseg) / slots + 1.0);
+        const double cost = (double)(Lc + 2 * h->K + 8) * ((double)(bx * nseg) / slots + 1.2);
         if (cost < best_cost) {
             best_cost = cost;
             best = Lc;
