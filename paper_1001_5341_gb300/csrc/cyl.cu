@@ -186,6 +186,7 @@ struct Wave {
     int *flags;
     unsigned *tiles;         // tile counter, zero at launch
     int ntiles;              // segments x groups of NW bands
+    int nseg;                // segments; the last one runs to the wall
 };
 
 __device__ __forceinline__ uint32_t sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -454,7 +455,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_cyl_wave(Wave A) {
     __shared__ __align__(8) uint64_t bars[NW][STAGES];
     __shared__ int sjlo[K];
     __shared__ float ssrc[K][MSRC];
-    __shared__ __align__(16) float2 srowc[LMAX + 2 * K];
+    __shared__ __align__(16) float2 srowc[LMAX + 2 * K + 1];   // a last segment may hold L + 1 rows
     __shared__ __align__(16) float swall[NW][K * W];
     __shared__ int spc[NW][K + 1], sprow[NW][K + 1];
     __shared__ int s_tile, s_dead;
@@ -484,7 +485,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_cyl_wave(Wave A) {
         const int tile = s_tile;
         if (tile >= A.ntiles || s_dead) break;
         const int g = tile / bxn, bx = tile - g * bxn;
-        const int own0 = g * A.L, own1 = min(own0 + A.L, nr + 1);   // owned rows [own0, own1)
+        // owned rows [own0, own1); the last segment runs to the wall, and it
+        // owns row nr - 1 too: the wall value of level s comes from level s at
+        // row nr - 1, valid only K rows above the segment's first loaded row
+        const int own0 = g * A.L, own1 = g == A.nseg - 1 ? nr + 1 : min(own0 + A.L, nr + 1);
         const int p0 = max(0, own0 - K);
         const int p_end = own1 - 1 + K;
         for (int t = tid; p0 + t <= min(p_end, nr); t += NW * 32) srowc[t] = A.rowc[p0 + t];
@@ -606,7 +610,7 @@ struct Variant {
 const Variant kVariants[] = {{0, 0, 0, nullptr, "k_cyl_h+k_cyl_e"},
                              {4, 2, 8, k_cyl_wave<4, 2, 1, 8>, "k_cyl_wave<4,2,1,8>"},
                              {8, 2, 8, k_cyl_wave<8, 2, 1, 8>, "k_cyl_wave<8,2,1,8>"},
-                             {4, 4, 8, k_cyl_wave<4, 4, 1, 8>, "k_cyl_wave<4,4,1,8>"},
+                             {4, 4, 8, k_cyl_wave<4, 4, 3, 8>, "k_cyl_wave<4,4,3,8>"},
                              {4, 4, 6, k_cyl_wave<4, 4, 4, 6>, "k_cyl_wave<4,4,4,6>"},
                              {8, 2, 8, k_cyl_wave<8, 2, 4, 8>, "k_cyl_wave<8,2,4,8>"}};
 constexpr int kNumKernels = 6;
@@ -748,7 +752,7 @@ int build_wave_probes(cyl_ctx *h) {
     std::vector<long long> key(h->np);
     for (int p = 0; p < h->np; ++p) {
         const int i = h->pij[2 * p], j = h->pij[2 * p + 1];
-        key[p] = ((long long)(i / h->L) * h->nbands + j / h->U);
+        key[p] = ((long long)std::min(i / h->L, h->nseg - 1) * h->nbands + j / h->U);
         off[key[p] + 1]++;
     }
     for (long long w = 0; w < nwarps; ++w) off[w + 1] += off[w];
@@ -789,6 +793,7 @@ int configure(cyl_ctx *h, int which, int seg_rows) {
         h->slots = wave_slots(h);
         h->L = choose_L(h);
         h->nseg = (h->nr + 1 + h->L - 1) / h->L;
+        if (h->nseg > 1 && (h->nr + 1) % h->L == 1) --h->nseg;   // no segment of the wall row alone
     }
     return build_wave_probes(h);
 }
@@ -909,6 +914,7 @@ void launch_wave(cyl_ctx *h) {
     A.flags = h->d_flags;
     A.tiles = h->d_tiles;
     A.ntiles = h->nseg * ((h->nbands + NW - 1) / NW);
+    A.nseg = h->nseg;
     note(h, cudaMemsetAsync(h->d_tiles, 0, sizeof(unsigned), h->stream));
     const int grid = std::min(A.ntiles, std::max(1, h->slots));
     v.fn<<<grid, NW * 32, ring_bytes(v), h->stream>>>(A);

@@ -93,7 +93,7 @@ PROBES = [(0, 1), (0, 75), (1, 40), (15, 47), (16, 48), (17, 49), (31, 96), (32,
 
 @pytest.mark.parametrize("boundary", [O.PEC, O.MUR1])
 @pytest.mark.parametrize("kernel,seg", [(0, 0), (1, 16), (2, 16), (3, 16), (4, 16), (5, 16), (2, 0), (2, 33),
-                                        (4, 0)])
+                                        (4, 0), (3, 35), (1, 14)])   # 71 rows: 35 and 14 leave one row over
 def test_kernel_matches_oracle(fd, kernel, seg, boundary):
     o, g = _run_pair(fd, 70, 150, 37, kernel, boundary, seg, PROBES)
     _compare(o, g, 37, f"kernel {kernel} seg {seg} boundary {boundary}")
