@@ -100,3 +100,60 @@ def nkg_norm(s):
     for rho(x) = C x^(s-2) (1+x)^(s-4.5), x = r/r_M:
     C = Gamma(4.5-s) / (2 pi Gamma(s) Gamma(4.5-2s))."""
     return math.gamma(4.5 - s) / (2.0 * math.pi * math.gamma(s) * math.gamma(4.5 - 2.0 * s))
+
+
+# ---- frequency domain (Sec. II and V; E_w = int E(t) exp(+i w t) dt) ----------
+
+def line_current_field_w(freqs, r_obs, z_obs, z_src, q_src, t_src, eps):
+    """Exact E_omega = (E_z, E_r) at (r_obs, z_obs) of a current along the
+    z axis (the solution of eq. GreenMethod for it), as the superposition of
+    Hertzian elements.  A charge q(z') moving along the axis passes z' at t';
+    its current is I_w dz' = q(z') dz' exp(i w t') per element (q_src holds
+    q(z') dz').  An element at distance D and polar angle th (from +z):
+        E_D  = eta (I dz) cos(th) / (2 pi D^2) (1 + i/(kD)) exp(ikD),
+        E_th = -i eta k (I dz) sin(th) / (4 pi D) (1 + i/(kD) - 1/(kD)^2) exp(ikD),
+    eta = sqrt(mu0/eps), k = w sqrt(mu0 eps).  Its charges (continuity) are
+    part of this field, so the charge the shower leaves at rest is included.
+    Returns two complex arrays [n_f]."""
+    f = np.asarray(freqs, dtype=np.float64).ravel()
+    w = 2.0 * math.pi * f
+    k = w * math.sqrt(MU0 * eps)
+    eta = math.sqrt(MU0 / eps)
+    dz = z_obs - np.asarray(z_src, dtype=np.float64)
+    D = np.sqrt(r_obs * r_obs + dz * dz)
+    c, s = dz / D, r_obs / D
+    kD = k[:, None] * D[None, :]
+    ph = np.exp(1j * (kD + w[:, None] * np.asarray(t_src)[None, :])) * np.asarray(q_src)[None, :]
+    ED = eta * c / (2 * math.pi * D * D) * (1 + 1j / kD) * ph
+    Et = -1j * eta * k[:, None] * s / (4 * math.pi * D) * (1 + 1j / kD - 1 / (kD * kD)) * ph
+    Ez = (ED * c - Et * s).sum(axis=1)
+    Er = (ED * s + Et * c).sum(axis=1)
+    return Ez, Er
+
+
+def far_field_1d(freqs, theta, R, n_idx, z_rel, q_dz, t_ref=0.0, v=C0):
+    """Eq. 1d_appro in its integral form: the theta-hat field of the
+    Fraunhofer approximation (eq. fraun_appr) for a charge q(z') moving at v
+    along the axis, the frame centred on the axis point that the charge
+    passes at t_ref, z_rel = z' measured from it, q_dz = q(z') dz':
+        E_theta = -i w mu0/(4 pi) sin(theta) exp(ikR)/R exp(i w t_ref)
+                  * sum q(z') dz' exp(i p z'),   p = w (1/v - n cos(theta)/c).
+    (The paper writes it with e N_e(z') for q(z') and the unit vector n_perp = -theta-hat.)"""
+    f = np.asarray(freqs, dtype=np.float64).ravel()
+    w = 2.0 * math.pi * f
+    k = w * n_idx / C0
+    p = w * (1.0 / v - n_idx * math.cos(theta) / C0)
+    I = (np.asarray(q_dz)[None, :] * np.exp(1j * p[:, None] * np.asarray(z_rel)[None, :])).sum(axis=1)
+    return -1j * w * MU0 / (4 * math.pi) * math.sin(theta) * np.exp(1j * (k * R + w * t_ref)) / R * I
+
+
+def far_field_1d_gauss(freqs, theta, R, n_idx, q_max, l, t_ref=0.0, v=C0):
+    """Eq. 1d_appro's closed form for the Gaussian profile q(z') = q_max
+    exp(-z'^2 / (2 l^2)) of eq. showerModel: the integral is
+    sqrt(2 pi) q_max l exp(-l^2 p^2 / 2)."""
+    f = np.asarray(freqs, dtype=np.float64).ravel()
+    w = 2.0 * math.pi * f
+    k = w * n_idx / C0
+    p = w * (1.0 / v - n_idx * math.cos(theta) / C0)
+    I = math.sqrt(2 * math.pi) * q_max * l * np.exp(-0.5 * (l * p) ** 2)
+    return -1j * w * MU0 / (4 * math.pi) * math.sin(theta) * np.exp(1j * (k * R + w * t_ref)) / R * I
