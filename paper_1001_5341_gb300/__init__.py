@@ -107,6 +107,8 @@ _SIGS = {
     "cyl_set_field": (_i, [_vp, _i, _vp, _i]),
     "cyl_reset": (_i, [_vp]),
     "cyl_launch_count": (_i, [_vp, _pi64]),
+    # spectra of detector traces (spectra.h)
+    "fdtd_trace_spectrum": (_i, [_vp, _i, _i, _i, _pd, _pi, _d, _d, _d, _pd, _i, _vp, _i, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -280,6 +282,18 @@ class Simulation:
         check(fdtd_probes(self.h, _vp(a.ctypes.data), 0), "fdtd_probes")
         return a
 
+    def spectrum(self, freqs, theta=None, coef=None, gate=None, taper=0.0):
+        """E_omega of every detector's trace (trace_spectrum; sample s at (s + 1) dt).
+        theta: per-detector polar angles for the theta-hat component; else coef
+        (default: E_z).  Returns a complex64 CUDA tensor [n_probes, n_freq]."""
+        import torch
+        tr = torch.empty((self.np, self.max_steps, 2), dtype=torch.float32, device="cuda")
+        self.probes(out=tr)
+        if theta is not None:
+            coef = theta_coef(theta)
+        return trace_spectrum(tr, self.dt, freqs, t0=self.dt, coef=coef, gate=gate, taper=taper,
+                              stream=self.stream)
+
     def field(self, comp, out=None):
         c = COMPONENTS.index(comp) if isinstance(comp, str) else comp
         if out is not None:
@@ -370,6 +384,39 @@ class Simulation:
 CYL_COMPONENTS = ("Er", "Ez", "Hphi")
 
 
+def trace_spectrum(traces, dt, freqs, t0=0.0, coef=None, gate=None, taper=0.0, stream=None):
+    """E_omega of detector traces (spectra.h), Sec. V: dt sum_m g_m x_{first+m}
+    exp(i 2 pi f t_{first+m}), t_n = t0 + n dt, x_n = sum_c coef_c X[n][c].
+
+    traces: float32 CUDA tensor [n_traces, n_t, n_comp] (or [n_traces, n_t]);
+    coef: [n_traces, n_comp] (default: the first component); gate: [n_traces, 2]
+    (first, count) (default: the whole trace); taper: Tukey fraction.
+    Returns a complex64 CUDA tensor [n_traces, n_freq] (asynchronous on the stream)."""
+    import torch
+    if not (isinstance(traces, torch.Tensor) and traces.is_cuda and traces.dtype == torch.float32):
+        raise ValueError("traces: need a float32 CUDA tensor")
+    t = (traces if traces.dim() == 3 else traces.unsqueeze(-1)).contiguous()
+    n_tr, n_t, n_c = t.shape
+    f = np.ascontiguousarray(np.asarray(freqs, dtype=np.float64).ravel())
+    co = None if coef is None else np.ascontiguousarray(np.asarray(coef, dtype=np.float64).reshape(n_tr, n_c))
+    ga = None if gate is None else np.ascontiguousarray(np.asarray(gate, dtype=np.int32).reshape(n_tr, 2))
+    if stream is None:
+        stream = torch.cuda.current_stream(t.device)
+    raw = stream if isinstance(stream, int) else stream.cuda_stream
+    out = torch.empty((n_tr, f.size, 2), dtype=torch.float32, device=t.device)
+    check(fdtd_trace_spectrum(_vp(t.data_ptr()), n_tr, n_t, n_c, None if co is None else _dp(co),
+                              None if ga is None else ga.ctypes.data_as(_pi), float(taper), float(dt), float(t0),
+                              _dp(f), f.size, _vp(out.data_ptr()), 1, _vp(raw)), "fdtd_trace_spectrum")
+    return torch.view_as_complex(out)
+
+
+def theta_coef(theta):
+    """(E_z, E_r) weights of the theta-hat component in a spherical frame whose
+    polar axis is the shower axis: E_theta = E_r cos(theta) - E_z sin(theta)."""
+    th = np.asarray(theta, dtype=np.float64).ravel()
+    return np.stack([-np.sin(th), np.cos(th)], axis=1)
+
+
 class Cylinder:
     """The paper's (E_r, E_z, H_phi) solver on an (r, z) grid of nr x nz cells
     (cyl.h).  ``stream``: a ``torch.cuda.Stream`` or raw cudaStream_t int;
@@ -451,6 +498,18 @@ class Cylinder:
         a = np.zeros((self.np, self.max_steps, 2), dtype=np.float32)
         check(cyl_probes(self.h, _vp(a.ctypes.data), 0), "cyl_probes")
         return a
+
+    def spectrum(self, freqs, theta=None, coef=None, gate=None, taper=0.0):
+        """E_omega of every detector's trace (trace_spectrum; sample s at (s + 1) dt).
+        theta: per-detector polar angles for the theta-hat component; else coef
+        (default: E_z).  Returns a complex64 CUDA tensor [n_probes, n_freq]."""
+        import torch
+        tr = torch.empty((self.np, self.max_steps, 2), dtype=torch.float32, device="cuda")
+        self.probes(out=tr)
+        if theta is not None:
+            coef = theta_coef(theta)
+        return trace_spectrum(tr, self.dt, freqs, t0=self.dt, coef=coef, gate=gate, taper=taper,
+                              stream=self.stream)
 
     def field(self, comp, out=None):
         c = CYL_COMPONENTS.index(comp) if isinstance(comp, str) else comp

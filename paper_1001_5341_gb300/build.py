@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libfdtd_gb300.so")
 
-SOURCES = ["fdtd_api.cu", "kernels_basic.cu", "kernels_fused.cu", "kernels_strip.cu", "kernels_vtile.cu", "kernels_noalloc.cu", "surrogate.cu", "cyl.cu", "adjoint.cu", "batch.cu", "tables.cpp"]
+SOURCES = ["fdtd_api.cu", "kernels_basic.cu", "kernels_fused.cu", "kernels_strip.cu", "kernels_vtile.cu", "kernels_noalloc.cu", "surrogate.cu", "cyl.cu", "adjoint.cu", "batch.cu", "spectra.cu", "tables.cpp"]
 HEADERS = ["fdtd_internal.h", "source_term.cuh", "cell_update.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-Wall",
@@ -41,7 +41,8 @@ def _stale(out: str, deps) -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
-    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "fdtd.h")]
+    inc = os.path.join(ROOT, "include")
+    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(inc, h) for h in sorted(os.listdir(inc))]
     objs, procs = [], []
     for s in SOURCES:
         src = os.path.join(CSRC, s)

@@ -135,3 +135,17 @@ def test_greisen_table_rejects_bad_energy(fd):
     out = np.zeros(4)
     assert fd.fdtd_profile_greisen(0.01, 4, 1e6, 78.6e6, 0.39, 0.2,
                                    out.ctypes.data_as(C.POINTER(C.c_double))) == -1
+
+
+def test_trace_spectrum_rejects_bad_arguments_on_host(fd):
+    f = np.array([1e8, 2e8])
+    fp = f.ctypes.data_as(C.POINTER(C.c_double))
+    out = np.zeros(8, dtype=np.float32)
+    op = C.c_void_p(out.ctypes.data)
+    # null traces, no traces, five components, taper > 1, dt <= 0, no frequencies: refused before any device call
+    assert fd.fdtd_trace_spectrum(None, 2, 10, 2, None, None, 0.0, 1e-11, 0.0, fp, 2, op, 0, None) == -1
+    assert fd.fdtd_trace_spectrum(op, 0, 10, 2, None, None, 0.0, 1e-11, 0.0, fp, 2, op, 0, None) == -1
+    assert fd.fdtd_trace_spectrum(op, 2, 10, 5, None, None, 0.0, 1e-11, 0.0, fp, 2, op, 0, None) == -1
+    assert fd.fdtd_trace_spectrum(op, 2, 10, 2, None, None, 1.5, 1e-11, 0.0, fp, 2, op, 0, None) == -1
+    assert fd.fdtd_trace_spectrum(op, 2, 10, 2, None, None, 0.0, 0.0, 0.0, fp, 2, op, 0, None) == -1
+    assert fd.fdtd_trace_spectrum(op, 2, 10, 2, None, None, 0.0, 1e-11, 0.0, fp, 0, op, 0, None) == -1
