@@ -315,6 +315,21 @@ def run_cyl(args):
         launches = g.launches - l0
         clk = clocks.stop()
         g.sync()
+        # spectra of every detector's whole trace (Sec. V) through the C ABI,
+        # timed on the same stream
+        trd = torch.empty((w.probes_rz.shape[0], args.warmup * K + steps, 2), dtype=torch.float32,
+                          device="cuda")
+        g.probes(out=trd)
+        freqs = np.linspace(10e6, 2e9, 1024)
+        th = np.full(trd.shape[0], math.acos(1 / math.sqrt(w.eps_r)))
+        fd.trace_spectrum(trd, w.dt, freqs, t0=w.dt, coef=fd.theta_coef(th), stream=stream)
+        ev0.record(stream)
+        fd.trace_spectrum(trd, w.dt, freqs, t0=w.dt, coef=fd.theta_coef(th), stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        spec_ms = ev0.elapsed_time(ev1)
+        spec_terms = trd.shape[0] * trd.shape[1] * freqs.size
+        del trd
         # end to end with host buffers
         q, wr, rz = (np.ascontiguousarray(a) for a in (w.q, w.w, w.probes_rz))
         torch.cuda.synchronize()
@@ -355,6 +370,10 @@ def run_cyl(args):
                 "what": "reset + set_shower + set_probes (host tables) + step(n) + probes() to host"},
         "gpu_launches": launches, "clocks": clk,
         "paper_table1_t_gpu_s": PAPER_T_GPU.get(n),
+        "spectrum": {"kernel": "k_trace_spectrum", "traces": int(w.probes_rz.shape[0]),
+                     "samples": int(spec_terms // (w.probes_rz.shape[0] * 1024)), "freqs": 1024,
+                     "ms": round(spec_ms, 3), "G_sample_freq_per_s": round(spec_terms / (spec_ms * 1e-3) / 1e9, 2),
+                     "what": "theta-hat E_omega of every detector's whole trace, one fdtd_trace_spectrum call"},
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cyl_cpu_baseline(w, budget_s=args.cpu_budget)
