@@ -559,8 +559,10 @@ def _oracle_sample(w, target_cells):
     sub-grid of about target_cells cells with the same aspect ratio."""
     f = (target_cells / w.cells) ** (1.0 / 3.0)
     min_n = 2 * w.npml + 8
-    nx = max(min_n, int(w.nx * f) // 2 * 2)
-    ny = max(min_n, int(w.ny * f) // 2 * 2)
+    # the lateral footprint (+-L cells about the axis) must stay clear of the CPML
+    min_xy = max(min_n, 2 * (w.npml + 1 + int(w.lateral.get("L", 0))) + 2)
+    nx = max(min_xy, int(w.nx * f) // 2 * 2)
+    ny = max(min_xy, int(w.ny * f) // 2 * 2)
     nz = max(min_n, int(w.nz * f) // 2 * 2)
     return W.greisen384(nx=nx, ny=ny, nz=nz, npml=w.npml, steps=1, n_probes=8,
                         r_lo=0.1, r_hi=min(0.3, (min(nx, ny) // 2 - w.npml - 2) * w.dx * 0.9),
