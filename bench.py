@@ -80,9 +80,11 @@ def ncu_record(kernel_name, workload_name):
     when none exists or a source file it lists changed since."""
     try:
         with open(TRAFFIC) as f:
-            rec = json.load(f).get(kernel_name)
+            data = json.load(f)
     except Exception:
         return None
+    # one record per (kernel, workload): "<kernel>@<workload>", or the kernel's own name
+    rec = data.get(f"{kernel_name}@{workload_name}") or data.get(kernel_name)
     if not rec or rec.get("workload") != workload_name:
         return None
     if rec.get("source_hash") != kernel_source_hash(rec.get("sources", [])):
@@ -170,9 +172,61 @@ def max_over_ranks(vals, ws, device="cpu"):
     return [float(x) for x in t.cpu()]
 
 
-def replica_workload(rank, **kw):
-    """The benchmark shower of one replica: rank r draws seed 2002 + r."""
-    return W.greisen384(seed=2002 + rank, **kw)
+WORKLOAD_SEEDS = {"greisen384": 2002, "gh640": 3003}
+
+
+def replica_workload(rank, workload="greisen384", **kw):
+    """The benchmark shower of one replica: rank r draws the workload's seed + r
+    (greisen384: 384 x 384 x 1536, Greisen shower; gh640: 640 x 640 x 2048,
+    dx = 3 cm, 3-6 Gaisser-Hillas subshowers over 40 m, 256 detectors)."""
+    make = {"greisen384": W.greisen384, "gh640": W.gh640}[workload]
+    return make(seed=WORKLOAD_SEEDS[workload] + rank, **kw)
+
+
+def near_field_vs_fraunhofer(fd, sim, w, stream):
+    """The detectors' theta-hat spectra (fdtd_trace_spectrum over the whole
+    trace; the CPML leaves no reflections) against the far-field formula
+    eq. 1d_appro for the same charge table, in a frame centred on the
+    charge-weighted middle of the shower:
+        E_theta = -i w mu0/(4 pi) sin(theta) exp(ikR)/R sum q(z') dz' exp(i p z'),
+        p = w (1/v - n cos(theta)/c).
+    Reports, per frequency, the median and spread of |E| / |E_formula| and
+    the median far-field parameter l^2 sin^2(theta) / (lambda R), l the
+    charge-weighted rms length of the shower."""
+    import torch
+    q, _ = fd.tables(w)
+    zq = w.z0 + w.bin_dz * np.arange(q.size)
+    aq = np.abs(q)
+    zc = float((zq * aq).sum() / aq.sum())
+    l_rms = float(np.sqrt(((zq - zc) ** 2 * aq).sum() / aq.sum()))
+    ax, ay = (w.nx // 2) * w.dx, (w.ny // 2) * w.dx
+    node = np.floor(w.probes_xyz / w.dx + 0.5) * w.dx
+    r = np.hypot(node[:, 0] - ax, node[:, 1] - ay)
+    R = np.hypot(r, node[:, 2] - zc)
+    th = np.arctan2(r, node[:, 2] - zc)
+    freqs = np.array([50e6, 100e6, 150e6, 200e6, 300e6])
+    tr = torch.empty((w.probes_xyz.shape[0], sim.max_steps, 2), dtype=torch.float32, device="cuda")
+    sim.probes(out=tr)
+    E = np.abs(fd.trace_spectrum(tr, w.dt, freqs, t0=w.dt, coef=fd.theta_coef(th), stream=stream).cpu().numpy())
+    n_idx = math.sqrt(w.eps_r)
+    mu0 = 4e-7 * math.pi
+    om = 2 * math.pi * freqs
+    ratio = np.zeros_like(E)
+    for p in range(E.shape[0]):
+        pz = om[:, None] * (1.0 / w.v - n_idx * math.cos(th[p]) / W.C0)
+        I = np.abs(((q * w.bin_dz)[None, :] * np.exp(1j * pz * (zq - zc)[None, :])).sum(axis=1))
+        Ef = om * mu0 / (4 * math.pi) * math.sin(th[p]) / R[p] * I
+        ratio[p] = E[p] / Ef
+    lam = W.C0 / (n_idx * freqs)
+    ff = np.median(l_rms ** 2 * np.sin(th)[:, None] ** 2 / (lam[None, :] * R[:, None]), axis=0)
+    return {"frame": f"charge-weighted middle z = {zc:.2f} m, rms length {l_rms:.2f} m",
+            "detectors": int(E.shape[0]), "R_m": [round(float(R.min()), 1), round(float(R.max()), 1)],
+            "freqs_MHz": (freqs / 1e6).tolist(),
+            "median_E_over_formula": np.round(np.median(ratio, axis=0), 3).tolist(),
+            "p10_E_over_formula": np.round(np.percentile(ratio, 10, axis=0), 3).tolist(),
+            "p90_E_over_formula": np.round(np.percentile(ratio, 90, axis=0), 3).tolist(),
+            "within_10pct": np.round(np.mean(np.abs(ratio - 1) <= 0.1, axis=0), 3).tolist(),
+            "median_l2sin2_over_lambdaR": np.round(ff, 2).tolist()}
 
 
 def run_ours(args):
@@ -186,7 +240,7 @@ def run_ours(args):
     import paper_1001_5341_gb300 as fd
 
     # each replica draws its own shower; rank 0 runs the named seed
-    w = replica_workload(rank, steps=args.warmup + args.steps, **({"nz": args.nz} if args.nz else {}))
+    w = replica_workload(rank, args.workload, steps=args.warmup + args.steps, **({"nz": args.nz} if args.nz else {}))
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         sim = fd.Simulation.from_workload(w, max_steps=args.warmup + args.steps, stream=stream)
@@ -216,6 +270,10 @@ def run_ours(args):
             stable = True
         except fd.FdtdError:
             stable = False
+
+        near = None
+        if w.profile["kind"] == "gh" and rank == 0 and args.warmup + args.steps >= w.steps:
+            near = near_field_vs_fraunhofer(fd, sim, w, stream)
 
         # end to end through the public API with host buffers: upload the
         # shower and detector tables, step, read the traces back to the host
@@ -252,9 +310,9 @@ def run_ours(args):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms_max / args.steps, 5), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {**w.describe(), "seed": 2002, "inputs_vs_l2": f"fields {field_gb(w):.1f} GB >> 129 MB L2 (no L2 flush needed)",
+        "config": {**w.describe(), "seed": WORKLOAD_SEEDS[args.workload], "inputs_vs_l2": f"fields {field_gb(w):.1f} GB >> 129 MB L2 (no L2 flush needed)",
                    "parallelism": f"replicas{ws}" if ws > 1 else "single-gpu",
-                   "replica_seeds": "2002 + rank"},
+                   "replica_seeds": f"{WORKLOAD_SEEDS[args.workload]} + rank"},
         "roofline": {"bound": "hbm", "kernel": kernel_name,
                      "achieved": round(achieved, 1) if achieved else None,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
@@ -271,6 +329,8 @@ def run_ours(args):
         "clocks": clk,
         "stable": stable,
     }
+    if near is not None:
+        line["near_field_vs_fraunhofer"] = near
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget)
     if ws > 1:
@@ -564,9 +624,20 @@ def _oracle_sample(w, target_cells):
     nx = max(min_xy, int(w.nx * f) // 2 * 2)
     ny = max(min_xy, int(w.ny * f) // 2 * 2)
     nz = max(min_n, int(w.nz * f) // 2 * 2)
+    r_hi = min(0.3, (min(nx, ny) // 2 - w.npml - 2) * w.dx * 0.9)
+    if w.profile["kind"] == "gh":
+        # subshowers spread over the sample's own length
+        spread = max(0.0, (nz - 2 * w.npml - 8) * w.dx - 6.0)
+        return W.gh640(nx=nx, ny=ny, nz=nz, npml=w.npml, steps=1, n_probes=8, r_lo=0.1, r_hi=r_hi,
+                       spread_m=spread)
     return W.greisen384(nx=nx, ny=ny, nz=nz, npml=w.npml, steps=1, n_probes=8,
-                        r_lo=0.1, r_hi=min(0.3, (min(nx, ny) // 2 - w.npml - 2) * w.dx * 0.9),
-                        E0=w.profile["E0_eV"])
+                        r_lo=0.1, r_hi=r_hi, E0=w.profile["E0_eV"])
+
+
+def _shower_text(w):
+    if w.profile["kind"] == "gh":
+        return f"{len(w.profile['z1'])} Gaisser-Hillas subshowers, dx {w.dx * 100:.0f} cm"
+    return f"Greisen E0={w.profile['E0_eV']:.3g} eV"
 
 
 def _omp_threads():
@@ -591,8 +662,8 @@ def cpu_baseline(w, budget_s=15.0):
     el = time.perf_counter() - t1
     return {"value": round(sw.cells * done / el / 1e9, 5), "unit": "Gcell/s", "cores": _omp_threads(),
             "kind": "oracle",
-            "sample": f"{sw.nx}x{sw.ny}x{sw.nz} cells of the same physics (CPML {sw.npml}, Greisen "
-                      f"E0={w.profile['E0_eV']:.3g} eV, NKG lateral), {done} steps, "
+            "sample": f"{sw.nx}x{sw.ny}x{sw.nz} cells of the same physics (CPML {sw.npml}, {_shower_text(w)}, "
+                      f"NKG lateral), {done} steps, "
                       f"{el:.1f} s (setup {t1 - t0:.1f} s excluded)"}
 
 
@@ -601,7 +672,7 @@ def run_reference(args):
     if rank != 0:
         return None
     import oracle
-    w = W.greisen384()
+    w = replica_workload(0, args.workload)
     # size the per-step sample so that W + K oracle steps take about two minutes
     cal = _oracle_sample(w, 2.0e5)
     o = oracle.from_workload(cal, max_steps=100)
@@ -619,12 +690,12 @@ def run_reference(args):
     el = time.perf_counter() - t0
     v = sw.cells * args.steps / el / 1e9
     sample = (f"each step: one oracle step on {sw.nx}x{sw.ny}x{sw.nz} cells of the same physics "
-              f"(CPML {sw.npml}, Greisen shower, NKG lateral)")
+              f"(CPML {sw.npml}, {_shower_text(sw)}, NKG lateral)")
     return {"impl": "reference", "metric": "Gcell-updates/s", "value": round(v, 6), "unit": "Gcell/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(el * 1e3 / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {**w.describe(), "seed": 2002},
+            "config": {**w.describe(), "seed": WORKLOAD_SEEDS[args.workload]},
             "cpu_baseline": {"value": round(v, 6), "unit": "Gcell/s", "cores": _omp_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(v, 6), "unit": "Gcell/s", "h2d_bytes_per_step": 0,
@@ -673,6 +744,8 @@ def main():
     ap.add_argument("--solver", choices=["yee3d", "cyl", "adjoint", "batch"], default="yee3d",
                     help="cyl: the paper's 2D axisymmetric solver on an n x n grid (Table I); "
                          "adjoint: gradient of a detector misfit w.r.t. the charge table")
+    ap.add_argument("--workload", choices=sorted(WORKLOAD_SEEDS), default="greisen384",
+                    help="3D workload: greisen384 (384x384x1536, the headline) or gh640 (640x640x2048, dx 3 cm)")
     ap.add_argument("--n", type=int, default=8192, help="cyl grid side")
     ap.add_argument("--cyl-kernel", type=int, default=-1, help="cyl kernel (-1: library default)")
     ap.add_argument("--batch-kind", choices=["config4", "small"], default="config4",
