@@ -75,6 +75,9 @@ namespace {
 #ifndef VT_NSMAX
 #define VT_NSMAX 8
 #endif
+#ifndef VT_L2PROMO
+#define VT_L2PROMO 2   // L2 promotion of the TMA loads: 0 none, 1 64 B, 2 128 B, 3 256 B
+#endif
 constexpr int BY = VT_BY;              // rows per tile (one warp each)
 constexpr int NSMAX = VT_NSMAX;        // most pipeline stages
 constexpr int NW = BY + 1;             // warps: BY row warps + one halo warp
@@ -726,6 +729,11 @@ struct HostState {
     size_t smem;
 };
 
+constexpr CUtensorMapL2promotion kPromotion =
+    VT_L2PROMO == 0 ? CU_TENSOR_MAP_L2_PROMOTION_NONE
+    : VT_L2PROMO == 1 ? CU_TENSOR_MAP_L2_PROMOTION_L2_64B
+    : VT_L2PROMO == 2 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B : CU_TENSOR_MAP_L2_PROMOTION_L2_256B;
+
 // 3-D float32 tensor map: extents d0 (innermost) .. d2, strides s1, s2 in
 // floats, box b0 x b1 x 1
 bool encode3(EncodeTiled encode, CUtensorMap *m, const float *base, cuuint64_t d0, cuuint64_t d1, cuuint64_t d2,
@@ -735,7 +743,7 @@ bool encode3(EncodeTiled encode, CUtensorMap *m, const float *base, cuuint64_t d
     cuuint32_t box[3] = {b0, b1, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, kPromotion,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
