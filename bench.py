@@ -567,7 +567,7 @@ def run_batch(args):
     time.sleep(0.5)
     t_batch = timed(lambda: (b.step(steps), b.sync()))
     clk = clocks.stop()
-    cfg, graph = b.config, b.graph_mode
+    cfg, graph, solo = b.config, b.graph_mode, b.solo
     t_fused = timed(lambda: [s.step(steps) for s in sims])
     for s in sims:
         s.set_kernel(0)
@@ -585,6 +585,7 @@ def run_batch(args):
                        "grids": ("nx, ny, nz in [32, 96]" if args.batch_kind == "small"
                                  else "nx, ny in [64, 256], nz in [64, 512]") + ", seeded", "boundary": "mur1",
                        "dx_m": dx, "probes_each": 8, **cfg, "graph_replay": bool(graph == 1),
+                       "solo_min_cells": solo["min_cells"], "solo_grids": solo["n_solo"],
                        "tuner_trial_steps": used},
             "one_by_one_fused_gcells": g(t_fused), "one_by_one_unfused_gcells": g(t_unfused),
             "batch_over_fused": round(t_fused / t_batch, 3), "batch_over_unfused": round(t_unfused / t_batch, 3),

@@ -12,6 +12,11 @@
  * its queue counters, is captured once in a CUDA graph and replayed.  Each
  * cell is updated by the same per-cell code as the unfused path
  * (fdtd_set_kernel 0), so a batched step gives the same numbers, bit for bit.
+ * Simulations large enough to keep the GPU busy with their own kernels can
+ * instead step alone (fdtd_batch_set_solo): after the persistent launches,
+ * their handle's selected path is issued on eight internal streams (largest
+ * grid first, each to the least loaded stream), so several run at once and
+ * each gets exactly what fdtd_step on the handle gives.
  *
  * The handles stay owned by the caller and must outlive the batch; stepping
  * a handle on its own between batch steps is allowed (the batch re-reads the
@@ -52,13 +57,27 @@ int fdtd_batch_set_config(fdtd_batch_t b, int threads, int cells_per_item, int s
 int fdtd_batch_get_config(fdtd_batch_t b, int *threads, int *cells_per_item, int *steps_per_launch);
 
 /*
- * Autotuner: runs trial_steps >= 1 steps of the batch itself with each
- * candidate configuration (threads x cells per item), times each on the
- * device, keeps the fastest and returns the steps it used in *steps_used.
- * The trial steps are real steps of every simulation (the configuration
- * does not change the arithmetic).
+ * Autotuner: first the solo threshold (none, every simulation alone, or a
+ * power of two between the smallest and the largest grid), then the launch
+ * configuration of the persistent kernel (threads x cells per item).  It runs
+ * trial_steps >= 1 steps of the batch itself with each candidate, times each
+ * on the device, keeps the fastest and returns the steps it used in
+ * *steps_used.  The trial steps are real steps of every simulation (a
+ * candidate decides which code path steps a simulation, never what that
+ * path computes).
  */
 int fdtd_batch_tune(fdtd_batch_t b, int trial_steps, int *steps_used);
+
+/*
+ * Simulations of at least min_cells cells step alone, with their handle's
+ * selected path, on the batch's internal streams; the rest share the
+ * persistent kernel.  min_cells = -1 (the default): every simulation shares it.
+ * FDTD_ERR_ARG for min_cells < -1.  fdtd_batch_get_solo returns the
+ * threshold and the number of simulations it makes step alone (either
+ * pointer may be null).
+ */
+int fdtd_batch_set_solo(fdtd_batch_t b, long long min_cells);
+int fdtd_batch_get_solo(fdtd_batch_t b, long long *min_cells, int *n_solo);
 
 /* Whether launches are replayed from a captured graph (1) or issued directly (0). */
 int fdtd_batch_graph_mode(fdtd_batch_t b);

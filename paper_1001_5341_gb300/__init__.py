@@ -91,6 +91,8 @@ _SIGS = {
     "fdtd_batch_get_config": (_i, [_vp, _pi, _pi, _pi]),
     "fdtd_batch_tune": (_i, [_vp, _i, _pi]),
     "fdtd_batch_graph_mode": (_i, [_vp]),
+    "fdtd_batch_set_solo": (_i, [_vp, C.c_longlong]),
+    "fdtd_batch_get_solo": (_i, [_vp, C.POINTER(C.c_longlong), _pi]),
     # 2D axisymmetric solver (cyl.h)
     "cyl_create": (_i, [C.POINTER(_vp), _i, _i, _d, _d, _d, _i, _vp]),
     "cyl_destroy": (None, [_vp]),
@@ -578,6 +580,17 @@ class Batch:
         t, c, s = C.c_int(), C.c_int(), C.c_int()
         check(fdtd_batch_get_config(self.h, C.byref(t), C.byref(c), C.byref(s)), "fdtd_batch_get_config")
         return {"threads": t.value, "cells_per_item": c.value, "steps_per_launch": s.value}
+
+    def set_solo(self, min_cells=-1):
+        """Simulations of at least min_cells cells step alone with their own
+        selected path (-1: all share the persistent kernel)."""
+        check(fdtd_batch_set_solo(self.h, int(min_cells)), "fdtd_batch_set_solo")
+
+    @property
+    def solo(self):
+        m, k = C.c_longlong(), C.c_int()
+        check(fdtd_batch_get_solo(self.h, C.byref(m), C.byref(k)), "fdtd_batch_get_solo")
+        return {"min_cells": m.value, "n_solo": k.value}
 
     def tune(self, trial_steps=4):
         """Autotune on the batch itself; returns the steps the trials advanced."""

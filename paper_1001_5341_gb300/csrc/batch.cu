@@ -194,6 +194,10 @@ __global__ void __launch_bounds__(256, 6) k_batch(BArgs A) {   // 40 registers: 
 
 }  // namespace
 
+// Streams over which the simulations that step alone are spread (their
+// launches rarely fill the GPU one at a time).
+constexpr int SOLO_STREAMS = 8;
+
 struct fdtd_batch {
     std::vector<fdtd_t> sims;
     int dev, sms;
@@ -204,6 +208,11 @@ struct fdtd_batch {
     unsigned *d_ctr, *d_bar;
     int *d_flags;
     int threads, cells_per_item, steps_per_launch;
+    long long solo_cells;  // simulations of at least this many cells step alone (-1: none)
+    std::vector<char> solo;
+    cudaStream_t solo_st[SOLO_STREAMS];   // the solo simulations, spread over these
+    cudaEvent_t solo_ev[SOLO_STREAMS];
+    int nshared;           // simulations inside the persistent kernel
     int blocks;
     int graph_ok;          // -1 unknown, 0 direct launches, 1 graphs
     std::map<int, cudaGraphExec_t> graphs;   // steps per launch -> executable graph
@@ -228,11 +237,22 @@ void drop_graphs(fdtd_batch *b) {
 
 // Descriptors and item prefix sums from the handles' current state.
 int refresh(fdtd_batch *b) {
-    const int n = (int)b->sims.size();
+    const int all = (int)b->sims.size();
+    std::vector<fdtd_ctx *> shared;
+    b->solo.assign(all, 0);
+    for (int q = 0; q < all; ++q) {
+        const fdtd_ctx *h = b->sims[q];
+        const long long cells = (long long)h->g.nx * h->g.ny * h->g.nz;
+        b->solo[q] = b->solo_cells >= 0 && cells >= b->solo_cells;
+        if (!b->solo[q]) shared.push_back(b->sims[q]);
+    }
+    const int n = (int)shared.size();
+    b->nshared = n;
+    if (n == 0) return FDTD_OK;
     std::vector<BSim> d(n);
     std::vector<int> hs(n + 1, 0), ms(n + 1, 0);
     for (int q = 0; q < n; ++q) {
-        fdtd_ctx *h = b->sims[q];
+        fdtd_ctx *h = shared[q];
         BSim &S = d[q];
         S.g = h->g;
         S.f[0] = h->fields[0];
@@ -278,7 +298,7 @@ int size_grid(fdtd_batch *b) {
 cudaError_t issue(fdtd_batch *b, int steps) {
     BArgs A;
     A.sims = b->d_sims;
-    A.nsim = (int)b->sims.size();
+    A.nsim = b->nshared;
     A.hstart = b->d_hstart;
     A.mstart = b->d_mstart;
     A.steps = steps;
@@ -329,6 +349,31 @@ int launch(fdtd_batch *b, int steps) {
     return note(b, issue(b, steps));
 }
 
+// One untimed step (it builds the graph), then `trial` steps timed on the
+// batch's stream; *used counts every step the trial advanced.
+int time_trial(fdtd_batch *b, int warm, int trial, float *ms, int *used) {
+    *used = 0;
+    int rc = fdtd_batch_step(b, warm);
+    if (rc != FDTD_OK) return rc;
+    *used += warm;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return FDTD_ERR_CUDA;
+    }
+    rc = note(b, cudaEventRecord(e0, b->stream));
+    if (rc == FDTD_OK) rc = fdtd_batch_step(b, trial);
+    if (rc == FDTD_OK) {
+        *used += trial;
+        rc = note(b, cudaEventRecord(e1, b->stream));
+    }
+    if (rc == FDTD_OK) rc = fdtd_batch_sync(b);
+    if (rc == FDTD_OK) cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -356,9 +401,15 @@ int fdtd_batch_create(fdtd_batch_t *out, const fdtd_t *sims, int n) {
     b->threads = 256;
     b->cells_per_item = 1 << 16;
     b->steps_per_launch = 8;
+    b->solo_cells = -1;
+    b->nshared = n;
     b->graph_ok = -1;
     b->status = FDTD_OK;
-    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+    bool streams_ok = true;
+    for (int k = 0; k < SOLO_STREAMS; ++k)
+        streams_ok = streams_ok && cudaStreamCreateWithFlags(&b->solo_st[k], cudaStreamNonBlocking) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&b->solo_ev[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!streams_ok || cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&b->d_sims, n * sizeof(BSim)) != cudaSuccess ||
         cudaMalloc(&b->d_hstart, (n + 1) * sizeof(int)) != cudaSuccess ||
@@ -392,6 +443,13 @@ void fdtd_batch_destroy(fdtd_batch_t b) {
     if (b->d_flags) cudaFree(b->d_flags);
     if (b->ev) cudaEventDestroy(b->ev);
     if (b->stream) cudaStreamDestroy(b->stream);
+    for (int k = 0; k < SOLO_STREAMS; ++k) {
+        if (b->solo_st[k]) {
+            cudaStreamSynchronize(b->solo_st[k]);
+            cudaStreamDestroy(b->solo_st[k]);
+        }
+        if (b->solo_ev[k]) cudaEventDestroy(b->solo_ev[k]);
+    }
     delete b;
 }
 
@@ -409,18 +467,49 @@ int fdtd_batch_step(fdtd_batch_t b, int n) {
             return b->status;
     }
     if (refresh(b) != FDTD_OK) return b->status;
-    int left = n, launches = 0;
-    while (left > 0 && b->status == FDTD_OK) {
-        const int s = std::min(left, b->steps_per_launch);
-        launch(b, s);
-        left -= s;
-        ++launches;
+    const int all = (int)b->sims.size();
+    if (b->nshared > 0) {
+        int left = n;
+        while (left > 0 && b->status == FDTD_OK) {
+            const int s = std::min(left, b->steps_per_launch);
+            launch(b, s);
+            left -= s;
+        }
     }
-    (void)launches;
-    for (fdtd_t h : b->sims) {
-        h->cur ^= n & 1;
-        h->steps += n;
+    // the simulations that step alone: their own selected path, after the
+    // persistent launches (which then have the GPU to themselves), spread
+    // largest first over the solo streams, each to the least loaded one
+    std::vector<int> order;
+    for (int q = 0; q < all; ++q)
+        if (b->solo[q]) order.push_back(q);
+    if (!order.empty() && b->status == FDTD_OK) {
+        auto cells = [&](int q) { return (long long)b->sims[q]->g.nx * b->sims[q]->g.ny * b->sims[q]->g.nz; };
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cells(x) > cells(y); });
+        const int ns = std::min<int>(SOLO_STREAMS, (int)order.size());
+        if (note(b, cudaEventRecord(b->ev, b->stream)) != FDTD_OK) return b->status;
+        for (int k = 0; k < ns; ++k)
+            if (note(b, cudaStreamWaitEvent(b->solo_st[k], b->ev, 0)) != FDTD_OK) return b->status;
+        long long load[SOLO_STREAMS] = {0};
+        for (int q : order) {
+            int k = 0;
+            for (int j = 1; j < ns; ++j)
+                if (load[j] < load[k]) k = j;
+            load[k] += cells(q);
+            if (fdtd::fdtd_step_on(b->sims[q], n, b->solo_st[k]) != FDTD_OK) {
+                b->status = b->sims[q]->status;
+                break;
+            }
+        }
+        for (int k = 0; k < ns; ++k)
+            if (note(b, cudaEventRecord(b->solo_ev[k], b->solo_st[k])) != FDTD_OK ||
+                note(b, cudaStreamWaitEvent(b->stream, b->solo_ev[k], 0)) != FDTD_OK)
+                return b->status;
     }
+    for (int q = 0; q < all; ++q)
+        if (!b->solo[q]) {
+            b->sims[q]->cur ^= n & 1;
+            b->sims[q]->steps += n;
+        }
     // order later work on the handles' streams after the batch
     if (note(b, cudaEventRecord(b->ev, b->stream)) != FDTD_OK) return b->status;
     for (fdtd_t h : b->sims)
@@ -458,40 +547,85 @@ int fdtd_batch_get_config(fdtd_batch_t b, int *threads, int *cells_per_item, int
     return FDTD_OK;
 }
 
+int fdtd_batch_set_solo(fdtd_batch_t b, long long min_cells) {
+    if (!b || min_cells < -1) return FDTD_ERR_ARG;
+    if (b->status != FDTD_OK) return b->status;
+    if (note(b, cudaStreamSynchronize(b->stream)) != FDTD_OK) return b->status;
+    drop_graphs(b);
+    b->solo_cells = min_cells;
+    return FDTD_OK;
+}
+
+int fdtd_batch_get_solo(fdtd_batch_t b, long long *min_cells, int *n_solo) {
+    if (!b) return FDTD_ERR_ARG;
+    if (min_cells) *min_cells = b->solo_cells;
+    if (n_solo) {
+        int k = 0;
+        for (fdtd_t h : b->sims)
+            if (b->solo_cells >= 0 && (long long)h->g.nx * h->g.ny * h->g.nz >= b->solo_cells) ++k;
+        *n_solo = k;
+    }
+    return FDTD_OK;
+}
+
 int fdtd_batch_tune(fdtd_batch_t b, int trial_steps, int *steps_used) {
     if (!b || trial_steps < 1) return FDTD_ERR_ARG;
     if (b->status != FDTD_OK) return b->status;
     const int spl0 = b->steps_per_launch, spl = std::min(spl0, trial_steps);
-    const int thr[2] = {128, 256};
-    const int cpi[4] = {1 << 14, 1 << 16, 1 << 18, 1 << 20};
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-        cudaGetLastError();
-        return FDTD_ERR_CUDA;
-    }
-    float best_ms = 1e30f;
-    int best_t = b->threads, best_c = b->cells_per_item, used = 0, rc = FDTD_OK;
-    for (int t : thr)
-        for (int c : cpi) {
-            if ((rc = fdtd_batch_set_config(b, t, c, spl)) != FDTD_OK) break;
-            // one untimed launch builds the graph, then the timed trial
-            if ((rc = fdtd_batch_step(b, spl)) != FDTD_OK) break;
-            used += spl;
-            if ((rc = note(b, cudaEventRecord(e0, b->stream))) != FDTD_OK) break;
-            if ((rc = fdtd_batch_step(b, trial_steps)) != FDTD_OK) break;
-            used += trial_steps;
-            if ((rc = note(b, cudaEventRecord(e1, b->stream))) != FDTD_OK) break;
-            if ((rc = fdtd_batch_sync(b)) != FDTD_OK) break;
+    int used = 0;
+    // first the solo threshold, with the current launch configuration: none,
+    // every simulation alone, or a power of two between the smallest and the
+    // largest grid
+    {
+        long long lo = 1LL << 62, hi = 0;
+        for (fdtd_t h : b->sims) {
+            const long long c = (long long)h->g.nx * h->g.ny * h->g.nz;
+            lo = std::min(lo, c);
+            hi = std::max(hi, c);
+        }
+        std::vector<long long> cand{-1, lo};
+        for (long long t = 2; t <= hi; t <<= 1)
+            if (t > lo) cand.push_back(t);
+        long long best = b->solo_cells;
+        float best_ms = 1e30f;
+        for (long long t : cand) {
+            int rc = fdtd_batch_set_solo(b, t);
             float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
+            int u = 0;
+            if (rc == FDTD_OK) rc = time_trial(b, spl, trial_steps, &ms, &u);
+            used += u;
+            if (rc != FDTD_OK) {
+                if (steps_used) *steps_used = used;
+                return rc;
+            }
             if (ms < best_ms) {
                 best_ms = ms;
-                best_t = t;
-                best_c = c;
+                best = t;
             }
         }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+        fdtd_batch_set_solo(b, best);
+    }
+    const int thr[2] = {128, 256};
+    const int cpi[4] = {1 << 14, 1 << 16, 1 << 18, 1 << 20};
+    // then the launch configuration of the persistent kernel, if it has work
+    float best_ms = 1e30f;
+    int best_t = b->threads, best_c = b->cells_per_item, rc = FDTD_OK;
+    refresh(b);
+    if (b->nshared > 0)
+        for (int t : thr)
+            for (int c : cpi) {
+                if ((rc = fdtd_batch_set_config(b, t, c, spl)) != FDTD_OK) break;
+                float ms = 0.f;
+                int u = 0;
+                rc = time_trial(b, spl, trial_steps, &ms, &u);
+                used += u;
+                if (rc != FDTD_OK) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_t = t;
+                    best_c = c;
+                }
+            }
     if (steps_used) *steps_used = used;
     if (rc != FDTD_OK) return rc;
     return fdtd_batch_set_config(b, best_t, best_c, spl0);

@@ -95,6 +95,41 @@ Cpml cpml_view(const fdtd_ctx *h) {
     }
     return v;
 }
+
+static void timed_launch(fdtd_ctx *h, cudaStream_t st, void (*fn)(const fdtd_ctx *, cudaStream_t)) {
+    TimingRec &t = h->timing;
+    bool rec = t.on && t.used < t.cap;
+    if (rec) cudaEventRecord(t.ev[2 * t.used], st);
+    fn(h, st);
+    if (rec) {
+        cudaEventRecord(t.ev[2 * t.used + 1], st);
+        t.used++;
+    }
+    h->launches++;
+}
+
+// n steps of the handle's selected path, issued on `st` (the handle's own
+// stream for fdtd_step; a batch's stream when the batch steps it alone).
+int fdtd_step_on(fdtd_ctx *h, int n, cudaStream_t st) {
+    for (int s = 0; s < n; ++s) {
+        if (h->kernel == 1) {
+            timed_launch(h, st, [](const fdtd_ctx *c, cudaStream_t q) { launch_vtile(const_cast<fdtd_ctx *>(c), q); });
+        } else if (h->kernel == 3) {
+            timed_launch(h, st, [](const fdtd_ctx *c, cudaStream_t q) { launch_strip(const_cast<fdtd_ctx *>(c), q); });
+        } else if (h->kernel == 2) {
+            timed_launch(h, st, [](const fdtd_ctx *c, cudaStream_t q) { launch_fused(const_cast<fdtd_ctx *>(c), q); });
+        } else {
+            timed_launch(h, st, launch_update_h);
+            timed_launch(h, st, launch_update_e);
+        }
+        if (h->boundary == FDTD_MUR1) { launch_mur(h, st); h->launches++; }
+        if (h->np > 0) { launch_probes(h, st); h->launches++; }
+        h->cur ^= 1;
+        h->steps++;
+    }
+    return note(h, cudaGetLastError());
+}
+
 }  // namespace fdtd
 
 extern "C" {
@@ -312,39 +347,11 @@ int fdtd_probe_nodes(fdtd_t h, int *ijk) {
     return FDTD_OK;
 }
 
-static void timed_launch(fdtd_ctx *h, void (*fn)(const fdtd_ctx *, cudaStream_t)) {
-    TimingRec &t = h->timing;
-    bool rec = t.on && t.used < t.cap;
-    if (rec) cudaEventRecord(t.ev[2 * t.used], h->stream);
-    fn(h, h->stream);
-    if (rec) {
-        cudaEventRecord(t.ev[2 * t.used + 1], h->stream);
-        t.used++;
-    }
-    h->launches++;
-}
-
 int fdtd_step(fdtd_t h, int n) {
     if (!h || n < 0) return FDTD_ERR_ARG;
     if (h->status != FDTD_OK) return h->status;
     if (h->np > 0 && h->steps + n > h->max_steps) return FDTD_ERR_CAPACITY;
-    for (int s = 0; s < n; ++s) {
-        if (h->kernel == 1) {
-            timed_launch(h, [](const fdtd_ctx *c, cudaStream_t st) { launch_vtile(const_cast<fdtd_ctx *>(c), st); });
-        } else if (h->kernel == 3) {
-            timed_launch(h, [](const fdtd_ctx *c, cudaStream_t st) { launch_strip(const_cast<fdtd_ctx *>(c), st); });
-        } else if (h->kernel == 2) {
-            timed_launch(h, [](const fdtd_ctx *c, cudaStream_t st) { launch_fused(const_cast<fdtd_ctx *>(c), st); });
-        } else {
-            timed_launch(h, launch_update_h);
-            timed_launch(h, launch_update_e);
-        }
-        if (h->boundary == FDTD_MUR1) { launch_mur(h, h->stream); h->launches++; }
-        if (h->np > 0) { launch_probes(h, h->stream); h->launches++; }
-        h->cur ^= 1;
-        h->steps++;
-    }
-    return note(h, cudaGetLastError());
+    return fdtd::fdtd_step_on(h, n, h->stream);
 }
 
 // Read the device error flags (after a synchronisation) into the sticky status.

@@ -209,6 +209,10 @@ void interior_box(const fdtd_ctx *h, int lo[3], int hi[3]);
 // TMA-staged vector-tile z-march over the whole grid, CPML included (kernels_vtile.cu)
 int vtile_prepare(fdtd_ctx *h);
 void launch_vtile(fdtd_ctx *h, cudaStream_t s);
+
+// n steps of the handle's selected path on stream st (fdtd_step issues them
+// on the handle's stream; a batch on its own).  Checks nothing beforehand.
+int fdtd_step_on(fdtd_ctx *h, int n, cudaStream_t st);
 const char *vtile_name();
 void vtile_release(fdtd_ctx *h);
 const char *strip_name();

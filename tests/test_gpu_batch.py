@@ -1,7 +1,8 @@
 """GPU batched persistent stepping (batch.h): uneven grids with PEC, Mur and
 CPML boundaries, showers and detectors, advanced together, must equal the
 same simulations stepped one by one on the unfused path bit for bit (the
-batch runs the same per-cell code), and the FP64 oracle within 1e-4; the
+batch runs the same per-cell code), and the FP64 oracle within 1e-4; grids
+that step alone (solo threshold) equal their handle stepped by itself; the
 autotuner's trial steps are real steps; capacity and argument checks."""
 import numpy as np
 import pytest
@@ -113,9 +114,43 @@ def test_batch_matches_oracle(fd):
     assert np.linalg.norm(tr - ref) <= 1e-4 * np.linalg.norm(ref)
 
 
+def test_solo_grids_equal_their_own_path(fd):
+    """Grids of at least the threshold step with their handle's own kernel on
+    the batch's stream; the rest share the persistent kernel."""
+    steps = 41
+    thr = 150000                          # (48, 44, 90) and (64, 64, 128) step alone
+    big = [sp[0] * sp[1] * sp[2] >= thr for sp in SPECS]
+    sims = [_make(fd, sp, steps) for sp in SPECS]
+    ref = [_make(fd, sp, steps, kernel=None if bg else 0) for sp, bg in zip(SPECS, big)]
+    for r in ref:
+        r.step(steps)
+    b = fd.Batch(sims)
+    b.set_config(256, 1 << 16, 5)
+    b.set_solo(thr)
+    assert b.solo == {"min_cells": thr, "n_solo": 2}
+    b.step(13)
+    b.step(28)
+    b.sync()
+    for s, r in zip(sims, ref):
+        (fa, ta), (fb, tb) = _state(s), _state(r)
+        for c in range(6):
+            assert np.array_equal(fa[c], fb[c]), c
+        assert np.array_equal(ta, tb)
+        assert s.steps_done == steps
+    # every grid alone, and back to none
+    b.set_solo(1)
+    assert b.solo["n_solo"] == len(SPECS)
+    b.set_solo(-1)
+    assert b.solo["n_solo"] == 0
+    with pytest.raises(fd.FdtdError):
+        b.set_solo(-2)
+
+
 def test_tuner_steps_are_real_steps(fd):
     steps = 200
-    sims = [_make(fd, sp, steps) for sp in SPECS]
+    # kernel 0 on every handle: a grid that the tuner makes step alone then
+    # runs the same per-cell code as inside the persistent kernel
+    sims = [_make(fd, sp, steps, kernel=0) for sp in SPECS]
     b = fd.Batch(sims)
     used = b.tune(trial_steps=2)
     assert used > 0 and all(s.steps_done == used for s in sims)
@@ -129,6 +164,7 @@ def test_tuner_steps_are_real_steps(fd):
             assert np.array_equal(s.field(c), r.field(c))
     cfg = b.config
     assert cfg["threads"] in (128, 256) and cfg["steps_per_launch"] == 8
+    assert b.solo["min_cells"] >= -1
 
 
 def test_mixing_batch_and_single_steps(fd):
