@@ -317,6 +317,7 @@ def run_ours(args):
                      "achieved": round(achieved, 1) if achieved else None,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": round(achieved / peak, 4) if achieved else None,
+                     "frac_of_nominal_7900": round(achieved / 7900.0, 4) if achieved else None,
                      "bytes_per_cell_alg": round(b, 3),
                      "traffic": (traffic * cells if traffic else None),
                      "kernel_ms_per_step": round(kern_ms / args.steps, 5),
@@ -661,11 +662,25 @@ def cpu_baseline(w, budget_s=15.0):
         if time.perf_counter() - t1 > budget_s:
             break
     el = time.perf_counter() - t1
-    return {"value": round(sw.cells * done / el / 1e9, 5), "unit": "Gcell/s", "cores": _omp_threads(),
+    cores = oracle.set_threads(0)
+    # the same oracle on one thread, as the paper's sequential CPU code ran
+    oracle.set_threads(1)
+    done1 = 0
+    t2 = time.perf_counter()
+    while True:
+        o.step(1)
+        done1 += 1
+        if time.perf_counter() - t2 > budget_s / 3:
+            break
+    el1 = time.perf_counter() - t2
+    oracle.set_threads(cores)
+    return {"value": round(sw.cells * done / el / 1e9, 5), "unit": "Gcell/s", "cores": cores,
             "kind": "oracle",
             "sample": f"{sw.nx}x{sw.ny}x{sw.nz} cells of the same physics (CPML {sw.npml}, {_shower_text(w)}, "
                       f"NKG lateral), {done} steps, "
-                      f"{el:.1f} s (setup {t1 - t0:.1f} s excluded)"}
+                      f"{el:.1f} s (setup {t1 - t0:.1f} s excluded)",
+            "single_thread": {"value": round(sw.cells * done1 / el1 / 1e9, 5), "unit": "Gcell/s",
+                              "sample": f"the same grid, {done1} more steps on one thread, {el1:.1f} s"}}
 
 
 def run_reference(args):

@@ -58,6 +58,8 @@ def lib():
         L.orc_set_field.argtypes = [vp, i, p]
         L.orc_get_probes.argtypes = [vp, p]
         L.orc_get_probe_nodes.argtypes = [vp, C.POINTER(C.c_int)]
+        L.orc_set_threads.argtypes = [i]
+        L.orc_set_threads.restype = i
         L.orc_source_count.argtypes = [vp]
         L.orc_get_source.argtypes = [vp, C.POINTER(C.c_int64), p]
         for f in ("orc_kE", "orc_kH", "orc_eps"):
@@ -267,3 +269,9 @@ def from_workload(w, max_steps=None):
     o.set_shower(q, w.z0, w.bin_dz, w.v, lw, w.lateral["L"])
     o.set_probes(w.probes_xyz, w.steps if max_steps is None else max_steps)
     return o
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's parallel loops from now on (n >= 1); n <= 0
+    leaves them unchanged.  Returns the count in force."""
+    return int(lib().orc_set_threads(int(n)))

@@ -34,6 +34,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_PEC 0
 #define ORC_MUR1 1
@@ -681,4 +684,16 @@ void orc_lateral_nkg(int L, double dx, double rM, double s, int nsub, double r_c
             sum += acc;
         }
     for (int t = 0; t < n * n; ++t) w[t] /= sum;
+}
+
+/* Threads of the oracle's parallel loops from now on (n >= 1), or unchanged
+   for n <= 0; returns the count in force.  1 without OpenMP. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
