@@ -15,7 +15,13 @@
  *   4. first-order Mur on the tangential E of the six faces, or PEC;
  *   5. detectors record E at fixed points (Sec. III.B, "Simulation Setup").
  * The paper is silent on the boundary, the deposit, the update order in 3D
- * and dt; the readings taken here are listed in the design doc.
+ * and dt.  Readings taken here: the leapfrog runs H^{n+1/2} then E^{n+1} from
+ * E^0 = H^{-1/2} = 0 (the paper's E-then-H order with shifted labels);
+ * dt = 0.5 dx sqrt(eps_r) / (c sqrt 3); the boundary is first-order Mur
+ * (apply_mur) or a Roden-Gedney CPML with PEC behind it (cpml_coef); the charge
+ * moves as a cloud-in-cell line whose current carries exactly the charge that
+ * crossed each face, and changes of the profile are charge created or lost at
+ * rest (build_source).
  *
  * Plain loops, no blocking, compiled with -ffp-contract=off.  The only
  * parallelism is an OpenMP loop over independent cells (bitwise
