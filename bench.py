@@ -441,18 +441,16 @@ def run_cyl(args):
     return line
 
 
-def run_adjoint(args):
-    """Gradient of a detector misfit with respect to a 256-bin charge table on
-    a 256 x 256 x 512 PEC grid (dx = 2 cm): the forward run and the adjoint
-    run, each timed on the device."""
-    import torch
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    import paper_1001_5341_gb300 as fd
-    from paper_1001_5341_gb300.adjoint import TraceModel
+ADJ_GRID = (256, 256, 512)
 
-    nx, ny, nz, dx = 256, 256, 512, 0.02
-    steps = args.steps or 2000
+
+def adjoint_problem(fd, TraceModel, rank=0, steps=2000, stream=None):
+    """The adjoint workload (seed 5005 + rank): a 256 x 256 x 512 PEC grid,
+    dx = 2 cm, a 256-bin Gaussian charge table (l = 1.2 m), Gaussian lateral
+    spread (L = 4), 64 detectors at r = 0.5-2.2 m.  Returns the simulation,
+    the differentiable trace model over `steps` steps, and the table."""
+    nx, ny, nz = ADJ_GRID
+    dx = 0.02
     dt = W.courant_dt(dx, W.EPS_R_ICE)
     rng = np.random.default_rng(5005 + rank)
     n_bins, z0 = 256, 0.2
@@ -463,11 +461,27 @@ def run_adjoint(args):
     r = rng.uniform(0.5, 2.2, 64)
     ph = rng.uniform(0, 2 * np.pi, 64)
     xyz = np.stack([cx + r * np.cos(ph), cy + r * np.sin(ph), rng.uniform(1.0, nz * dx - 1.0, 64)], axis=1)
+    kw = {} if stream is None else {"stream": stream}
+    sim = fd.Simulation(nx, ny, nz, dx, dt, W.EPS_R_ICE, boundary=fd.FDTD_PEC, **kw)
+    sim.set_probes(xyz, steps)
+    return sim, TraceModel(sim, z0, bin_dz, W.C0, lw, 4, steps), q
+
+
+def run_adjoint(args):
+    """Gradient of a detector misfit with respect to a 256-bin charge table on
+    a 256 x 256 x 512 PEC grid (dx = 2 cm): the forward run and the adjoint
+    run, each timed on the device."""
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    import paper_1001_5341_gb300 as fd
+    from paper_1001_5341_gb300.adjoint import TraceModel
+
+    nx, ny, nz = ADJ_GRID
+    steps = args.steps or 2000
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        sim = fd.Simulation(nx, ny, nz, dx, dt, W.EPS_R_ICE, boundary=fd.FDTD_PEC, stream=stream)
-        sim.set_probes(xyz, steps)
-        model = TraceModel(sim, z0, bin_dz, W.C0, lw, 4, steps)
+        sim, model, q = adjoint_problem(fd, TraceModel, rank, steps, stream=stream)
         qt = torch.tensor(q, requires_grad=True)
         with torch.no_grad():
             target = model(qt * 0.9)
@@ -502,7 +516,7 @@ def run_adjoint(args):
     return {"metric": "gradient evaluations/s", "value": round(1.0 / t_all, 4), "unit": "gradients/s",
             "solver": "adjoint", "n_gpus": ws, "steps": steps, "higher_is_better": True, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"pec{nx}x{ny}x{nz}", "dx_m": dx, "bins": n_bins, "probes": 64,
+            "config": {"workload": f"pec{nx}x{ny}x{nz}", "dx_m": 0.02, "bins": int(q.size), "probes": 64,
                        "lateral_L": 4, "loss": "1/2 sum (traces - traces(0.9 q))^2"},
             "forward_s": round(t_fwd, 4), "adjoint_s": round(t_adj, 4),
             "forward_gcells": round(cells * steps / t_fwd / 1e9, 2),
@@ -511,27 +525,23 @@ def run_adjoint(args):
             "grad_norm": float(np.linalg.norm(g)), "gpu_launches": launches, "clocks": clk}
 
 
-def run_batch(args):
-    """64 independent showers on uneven grids (64^3 .. 256 x 256 x 512, dx =
-    2 cm, Mur) advanced together by the batched persistent kernel, against the
-    same simulations stepped one after another (default fused path and the
-    unfused path whose per-cell code the batch shares)."""
-    import torch
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    import paper_1001_5341_gb300 as fd
+BATCH_DX = 0.02
 
+
+def batch_workload(fd, kind="config4", rank=0, max_steps=1800):
+    """Grid sizes and a constructor of the batch workloads (seed 6006 + rank):
+    "config4" = 64 showers on 64^3 .. 256 x 256 x 512, "small" = 256 showers
+    on 32^3 .. 96^3; dx = 2 cm, Mur, Gaussian profile and lateral spread, 8
+    detectors each.  make(dims, seed) returns a Simulation with trace room
+    for max_steps steps."""
     rng = np.random.default_rng(6006 + rank)
-    steps = args.steps or 200
-    dx = 0.02
+    dx = BATCH_DX
     dt = W.courant_dt(dx, W.EPS_R_ICE)
-    if args.batch_kind == "small":   # many small grids: 256 showers on 32^3 .. 96^3
-        n_sims = 256
-        dims = [tuple(int(v) for v in rng.integers(32, 97, 3)) for _ in range(n_sims)]
-    else:                            # 64 showers on 64^3 .. 256 x 256 x 512
-        n_sims = 64
+    if kind == "small":
+        dims = [tuple(int(v) for v in rng.integers(32, 97, 3)) for _ in range(256)]
+    else:
         dims = [(int(rng.integers(64, 257)), int(rng.integers(64, 257)), int(rng.integers(64, 513)))
-                for _ in range(n_sims)]
+                for _ in range(64)]
     lw = fd.lateral_gaussian(3, 1.0)
 
     def make(d, seed):
@@ -546,9 +556,27 @@ def run_batch(args):
         rr = r.uniform(0.2, 0.4, 8) * min(nx, ny) * dx
         ph = r.uniform(0, 2 * np.pi, 8)
         xyz = np.stack([cx + rr * np.cos(ph), cy + rr * np.sin(ph), r.uniform(0.2, 0.8, 8) * nz * dx], 1)
-        sim.set_probes(xyz, 4 * steps + 1000)
+        sim.set_probes(xyz, max_steps)
         return sim
 
+    return dims, make
+
+
+def run_batch(args):
+    """64 independent showers on uneven grids (64^3 .. 256 x 256 x 512, dx =
+    2 cm, Mur) advanced together by one batch (the persistent kernel and the
+    solo streams, as its autotuner chooses), against the same simulations
+    stepped one after another (default fused path, and the unfused path whose
+    per-cell code the persistent kernel shares)."""
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    import paper_1001_5341_gb300 as fd
+
+    steps = args.steps or 200
+    dims, make = batch_workload(fd, args.batch_kind, rank, 4 * steps + 1000)
+    n_sims = len(dims)
+    dx = BATCH_DX
     sims = [make(d, 7000 + i) for i, d in enumerate(dims)]
     cells = sum(nx * ny * nz for nx, ny, nz in dims)
 
