@@ -45,7 +45,12 @@ void fdtd_batch_destroy(fdtd_batch_t b);
  */
 int fdtd_batch_step(fdtd_batch_t b, int n);
 
-/* Synchronise and return the sticky status. */
+/*
+ * Synchronise (the solo streams included) and return the sticky status of
+ * the batch.  A bounded wait that gives up inside a simulation stepping
+ * alone is recorded on that handle, as for fdtd_step: fdtd_sync on the
+ * handle reports it.
+ */
 int fdtd_batch_sync(fdtd_batch_t b);
 
 /*
