@@ -646,18 +646,19 @@ def cyl_cpu_baseline(w, budget_s=15.0):
 
 def _oracle_sample(w, target_cells):
     """The workload's physics (dx, dt, CPML, shower, lateral spread) on a
-    sub-grid of about target_cells cells with the same aspect ratio."""
-    f = (target_cells / w.cells) ** (1.0 / 3.0)
+    sub-grid of about target_cells cells with the same aspect ratio, never
+    larger than the workload's own grid."""
+    f = min(1.0, (target_cells / w.cells) ** (1.0 / 3.0))
     min_n = 2 * w.npml + 8
     # the lateral footprint (+-L cells about the axis) must stay clear of the CPML
     min_xy = max(min_n, 2 * (w.npml + 1 + int(w.lateral.get("L", 0))) + 2)
-    nx = max(min_xy, int(w.nx * f) // 2 * 2)
-    ny = max(min_xy, int(w.ny * f) // 2 * 2)
-    nz = max(min_n, int(w.nz * f) // 2 * 2)
+    nx = min(w.nx, max(min_xy, int(w.nx * f) // 2 * 2))
+    ny = min(w.ny, max(min_xy, int(w.ny * f) // 2 * 2))
+    nz = min(w.nz, max(min_n, int(w.nz * f) // 2 * 2))
     r_hi = min(0.3, (min(nx, ny) // 2 - w.npml - 2) * w.dx * 0.9)
     if w.profile["kind"] == "gh":
         # subshowers spread over the sample's own length
-        spread = max(0.0, (nz - 2 * w.npml - 8) * w.dx - 6.0)
+        spread = min(40.0, max(0.0, (nz - 2 * w.npml - 8) * w.dx - 6.0))   # 40 m: the workload's own
         return W.gh640(nx=nx, ny=ny, nz=nz, npml=w.npml, steps=1, n_probes=8, r_lo=0.1, r_hi=r_hi,
                        spread_m=spread)
     return W.greisen384(nx=nx, ny=ny, nz=nz, npml=w.npml, steps=1, n_probes=8,

@@ -35,3 +35,12 @@ def test_traffic_record_lookup(tmp_path, monkeypatch):
     assert bench.ncu_traffic("k", "w2") == 2.0
     assert bench.ncu_traffic("k", "w3") is None
     assert bench.ncu_traffic("old", "w1") is None
+
+
+@pytest.mark.parametrize("workload", ["greisen384", "gh640"])
+def test_oracle_sample_never_exceeds_the_workload(workload):
+    """A fast host asks for more cells per step than the grid has: the sample
+    is then the workload's own grid, not a larger one."""
+    w = bench.replica_workload(0, workload)
+    sw = bench._oracle_sample(w, 1e12)
+    assert (sw.nx, sw.ny, sw.nz) == (w.nx, w.ny, w.nz)
