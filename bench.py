@@ -358,7 +358,8 @@ def run_cyl(args):
         K = info["steps_per_launch"]
         steps = args.steps if args.steps else n
         steps = max(K, steps // K * K)
-        g.set_shower(w.q, w.z0, w.bin_dz, w.v, w.w)
+        q_tab, ring_w = fd.cyl_tables(w)
+        g.set_shower(q_tab, w.z0, w.bin_dz, w.v, ring_w)
         g.set_probes(w.probes_rz, args.warmup * K + steps)
         g.step(args.warmup * K)
         g.sync()
@@ -392,7 +393,7 @@ def run_cyl(args):
         spec_terms = trd.shape[0] * trd.shape[1] * freqs.size
         del trd
         # end to end with host buffers
-        q, wr, rz = (np.ascontiguousarray(a) for a in (w.q, w.w, w.probes_rz))
+        q, wr, rz = (np.ascontiguousarray(a) for a in (q_tab, ring_w, w.probes_rz))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         g.reset()
@@ -625,13 +626,20 @@ def run_batch(args):
 PAPER_T_GPU = {256: 0.040, 512: 0.186, 1024: 1.167, 2048: 8.372, 4096: 67.617, 8192: 681.082}
 
 
+def _cyl_oracle_shower(s):
+    """set_shower arguments of the 2D oracle, its tables built by the oracle."""
+    from oracle import cyl_oracle as CO
+    q, rings = CO.tables(s)
+    return q, s.z0, s.bin_dz, s.v, rings
+
+
 def cyl_cpu_baseline(w, budget_s=15.0):
     """The 2D FP64 oracle as it stands, on a 1024 x 1024 sample of the same physics."""
     from oracle import cyl_oracle as CO
     m = min(1024, w.nr)
     s = W.cyl_table1(m, extent_m=w.d * m)
     o = CO.CylOracle(s.nr, s.nz, s.d, s.dt, s.eps_r, boundary=s.boundary)
-    o.set_shower(s.q, s.z0, s.bin_dz, s.v, s.w)
+    o.set_shower(*_cyl_oracle_shower(s))
     o.set_probes(s.probes_rz)
     o.step(1)
     done = 0
@@ -758,7 +766,7 @@ def run_cyl_reference(args):
     s = W.cyl_table1(m, extent_m=w.d * m)
     steps = args.steps or 64
     o = CO.CylOracle(s.nr, s.nz, s.d, s.dt, s.eps_r, boundary=s.boundary)
-    o.set_shower(s.q, s.z0, s.bin_dz, s.v, s.w)
+    o.set_shower(*_cyl_oracle_shower(s))
     o.set_probes(s.probes_rz)
     o.step(args.warmup)
     t0 = time.perf_counter()

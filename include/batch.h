@@ -84,6 +84,21 @@ int fdtd_batch_tune(fdtd_batch_t b, int trial_steps, int *steps_used);
 int fdtd_batch_set_solo(fdtd_batch_t b, long long min_cells);
 int fdtd_batch_get_solo(fdtd_batch_t b, long long *min_cells, int *n_solo);
 
+/*
+ * Bound of every grid-barrier wait of the persistent kernel, in SM clock
+ * cycles (0: the default, FDTD_BATCH_DEFAULT_WAIT_CYCLES, about two seconds).
+ * A wait that runs out records the failure on the device and the kernel
+ * returns; fdtd_batch_sync then reports FDTD_ERR_TIMEOUT for the batch and
+ * for every simulation that shared the persistent kernel (left part-way
+ * through a step, so its handle cannot be stepped again: the status is
+ * sticky), and later persistent launches of the batch return at once.  A
+ * small limit makes a barrier give up while the other blocks are still at
+ * work, which is how the timeout path is tested.  FDTD_ERR_ARG for
+ * cycles < 0.
+ */
+#define FDTD_BATCH_DEFAULT_WAIT_CYCLES (4LL << 30)
+int fdtd_batch_set_wait_limit(fdtd_batch_t b, long long cycles);
+
 /* Whether launches are replayed from a captured graph (1) or issued directly (0). */
 int fdtd_batch_graph_mode(fdtd_batch_t b);
 

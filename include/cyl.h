@@ -54,6 +54,17 @@ int cyl_set_shower(cyl_t h, const double *q, int n_bins, double z0, double bin_d
                    int nw);
 
 /*
+ * Ring weights of the paper's radial Gaussian spread (Sec. III.B, lateral
+ * charge density exp(-r^2 / (2 sigma_r^2)), sigma_r = 5 cm in the paper):
+ * w[i] (host, n_rings doubles) is the share of the charge in ring i, which
+ * covers r in [(i-1/2) d, (i+1/2) d] (the axis disc [0, d/2] for i = 0),
+ * renormalised to sum 1 over the n_rings rings.  The longitudinal table of
+ * the same model (Eq. showerModel) comes from fdtd_profile_gaussian (fdtd.h).
+ * FDTD_ERR_ARG for a null pointer, n_rings < 1, d <= 0 or sigma_r <= 0.
+ */
+int cyl_rings_gaussian(int n_rings, double d, double sigma_r, double *w);
+
+/*
  * Detectors at (r, z) metres (host, n*2 doubles), snapped to the nearest
  * node, 0 <= i < nr and 0 < j < nz (FDTD_ERR_ARG otherwise); trace slot s
  * holds (E_z, E_r) at step s+1 (E_z averaged over j +- 1/2, E_r over i +- 1/2,

@@ -141,7 +141,9 @@ int fdtd_fields(fdtd_t h, int comp, float *out, int on_device);
    component's updated range are ignored (kept zero). Synchronises. */
 int fdtd_set_field(fdtd_t h, int comp, const float *in, int on_device);
 
-/* Zero fields, CPML memory and traces; keep shower and detectors; steps = 0. */
+/* Zero fields, CPML memory and traces; keep shower and detectors; steps = 0.
+   Clears a sticky FDTD_ERR_UNSTABLE (the non-finite values are gone); any
+   other sticky error stays. */
 int fdtd_reset(fdtd_t h);
 
 /*
@@ -181,7 +183,10 @@ int fdtd_energy(fdtd_t h, double *energy);
  * it: calls that overlap in time (other threads, other streams) race and must
  * be serialised by the caller.  The first call on a device (with that device
  * current) looks the array up (cudaGetSymbolAddress, which may load the
- * module); make that first call before any stream capture begins.
+ * module); make that first call before any stream capture begins.  The
+ * address is kept per device and context: after a device reset (a new primary
+ * context) the next call looks it up again, so it also belongs before any
+ * capture.
  */
 #define FDTD_ENERGY_SCRATCH_BLOCKS 1024
 int fdtd_energy_noalloc(const float *d_fields, int nx, int ny, int nz, double dx, double eps_r,
@@ -218,12 +223,25 @@ const char *fdtd_kernel_name(fdtd_t h);
  * Select the field-update path (all compute the same update, Sec. III.A):
  *   1 = one pass per step: TMA-staged vector-tile z-march over the whole
  *       grid, CPML included (the default);
- *   3 = one pass per step: register-strip z-march over interior and shell;
- *   2 = one pass per step: TMA-staged z-march;
- *   0 = one H sweep then one E sweep.
+ *   0 = one H sweep then one E sweep (the reference path: the batched
+ *       persistent kernel and the adjoint use its per-cell code).
  * Returns FDTD_ERR_ARG for a path the handle cannot run.
  */
 int fdtd_set_kernel(fdtd_t h, int which);
+
+/*
+ * Watchdog of the stepping path: every `every` steps (FDTD_WATCHDOG_DEFAULT_STEPS
+ * after fdtd_create; 0 turns it off) a small kernel scans every field component
+ * on every eighth z plane and the last one for non-finite values.  An unstable
+ * run (Sec. III.A: the leapfrog is stable only below the Courant limit) or a
+ * non-finite value anywhere in the grid spreads one plane per step, so it is
+ * seen within every + 4 steps; the next fdtd_sync, fdtd_probes or other call
+ * that synchronises then returns FDTD_ERR_UNSTABLE, and the status is sticky
+ * (fdtd_reset clears it).  Cost: 1/8 of the field bytes every `every` steps
+ * (0.1 % of a step at the default).  FDTD_ERR_ARG for every < 0.
+ */
+#define FDTD_WATCHDOG_DEFAULT_STEPS 64
+int fdtd_set_watchdog(fdtd_t h, int every);
 
 /* Human-readable text of a status code (static string). */
 const char *fdtd_strerror(int status);

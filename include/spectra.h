@@ -52,6 +52,17 @@ int fdtd_trace_spectrum(const float *traces, int n_traces, int n_t, int n_comp,
                         double dt, double t0, const double *freq, int n_freq,
                         float *out, int on_device, void *stream);
 
+/*
+ * Weights of the theta-hat component for fdtd_trace_spectrum (Sec. V reads
+ * the radiation field, which lies along theta-hat of a spherical frame whose
+ * polar axis is the shower axis): E_theta = E_r cos(theta) - E_z sin(theta),
+ * so coef[2t] = -sin(theta[t]) (E_z, trace component 0) and coef[2t+1] =
+ * cos(theta[t]) (E_r, component 1).  theta: host, n radians; coef: host,
+ * n x 2 doubles.  FDTD_ERR_ARG for a null pointer, n < 1 or a theta that is
+ * not finite.
+ */
+int fdtd_theta_coef(const double *theta, int n, double *coef);
+
 #ifdef __cplusplus
 }
 #endif

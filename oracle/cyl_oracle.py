@@ -213,3 +213,27 @@ class CylOracle:
 def courant_dt(d, eps_r):
     """Half of the 2D Courant limit d sqrt(eps_r) / (c sqrt 2)."""
     return 0.5 * d * math.sqrt(eps_r) / (C0 * math.sqrt(2.0))
+
+
+def ring_weights_gaussian(n_rings, d, sigma_r):
+    """Share of a radial Gaussian charge density exp(-r^2 / (2 sigma_r^2))
+    (the paper's lateral model, Sec. III.B) in each ring i: r in
+    [(i-1/2) d, (i+1/2) d], the axis disc [0, d/2] for i = 0; renormalised to
+    sum 1 over the n_rings rings.  The charge inside radius r is
+    1 - exp(-r^2 / (2 sigma_r^2)) of the total (the integral of the density
+    over the disc)."""
+    edges = np.concatenate([[0.0], (np.arange(n_rings) + 0.5) * d])
+    inside = 1.0 - np.exp(-0.5 * (edges / sigma_r) ** 2)
+    w = np.diff(inside)
+    return w / w.sum()
+
+
+def tables(w):
+    """Charge table (Eq. showerModel, sampled by the 3D oracle's generator) and
+    ring weights of a ``workloads.CylWorkload``, built on the oracle side."""
+    import oracle
+    s = w.shower
+    if s["kind"] != "gaussian":
+        raise ValueError(s["kind"])
+    q = oracle.profile_gaussian(w.z0, w.bin_dz, s["n_bins"], s["z_peak"], s["l"], s["q_max"])
+    return q, ring_weights_gaussian(s["n_rings"], w.d, s["sigma_r"])

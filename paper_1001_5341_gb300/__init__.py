@@ -59,12 +59,14 @@ _SIGS = {
     "fdtd_timed_cells": (_i, [_vp, _pi64]),
     "fdtd_kernel_name": (C.c_char_p, [_vp]),
     "fdtd_set_kernel": (_i, [_vp, _i]),
+    "fdtd_set_watchdog": (_i, [_vp, _i]),
     "fdtd_strerror": (C.c_char_p, [_i]),
     "fdtd_profile_gaussian": (_i, [_d, _d, _i, _d, _d, _d, _pd]),
     "fdtd_profile_greisen": (_i, [_d, _i, _d, _d, _d, _d, _pd]),
     "fdtd_profile_gaisser_hillas": (_i, [_d, _d, _i, _i, _pd, _pd, _pd, _pd, _d, _pd]),
     "fdtd_lateral_gaussian": (_i, [_i, _d, _pd]),
     "fdtd_lateral_nkg": (_i, [_i, _d, _d, _d, _i, _d, _pd]),
+    "cyl_rings_gaussian": (_i, [_i, _d, _d, _pd]),
     # learned surrogate kernels (surrogate.h); pointers are device addresses
     "sur_gemm_bf16": (_i, [_vp, _i, _i, _vp, _i, _i, _vp, _i, _vp, _i, _i, _i, _vp, _i, _i, _vp]),
     "sur_conv1d_fwd": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _vp]),
@@ -93,6 +95,7 @@ _SIGS = {
     "fdtd_batch_graph_mode": (_i, [_vp]),
     "fdtd_batch_set_solo": (_i, [_vp, C.c_longlong]),
     "fdtd_batch_get_solo": (_i, [_vp, C.POINTER(C.c_longlong), _pi]),
+    "fdtd_batch_set_wait_limit": (_i, [_vp, C.c_longlong]),
     # 2D axisymmetric solver (cyl.h)
     "cyl_create": (_i, [C.POINTER(_vp), _i, _i, _d, _d, _d, _i, _vp]),
     "cyl_destroy": (None, [_vp]),
@@ -111,6 +114,7 @@ _SIGS = {
     "cyl_launch_count": (_i, [_vp, _pi64]),
     # spectra of detector traces (spectra.h)
     "fdtd_trace_spectrum": (_i, [_vp, _i, _i, _i, _pd, _pi, _d, _d, _d, _pd, _i, _vp, _i, _vp]),
+    "fdtd_theta_coef": (_i, [_pd, _i, _pd]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(lib, _name)
@@ -193,6 +197,19 @@ def tables(w):
     else:
         raise ValueError(lt["kind"])
     return q, lw
+
+
+def cyl_tables(w):
+    """Charge table and ring weights of a ``workloads.CylWorkload`` (the
+    paper's Gaussian shower model, Sec. III.B) from the library's own host
+    generators."""
+    s = w.shower
+    if s["kind"] != "gaussian":
+        raise ValueError(s["kind"])
+    q = profile_gaussian(w.z0, w.bin_dz, s["n_bins"], s["z_peak"], s["l"], s["q_max"])
+    rings = np.zeros(s["n_rings"])
+    check(cyl_rings_gaussian(s["n_rings"], w.d, s["sigma_r"], _dp(rings)), "cyl_rings_gaussian")
+    return q, rings
 
 
 # ---- simulation handle -------------------------------------------------------
@@ -413,10 +430,11 @@ def trace_spectrum(traces, dt, freqs, t0=0.0, coef=None, gate=None, taper=0.0, s
 
 
 def theta_coef(theta):
-    """(E_z, E_r) weights of the theta-hat component in a spherical frame whose
-    polar axis is the shower axis: E_theta = E_r cos(theta) - E_z sin(theta)."""
-    th = np.asarray(theta, dtype=np.float64).ravel()
-    return np.stack([-np.sin(th), np.cos(th)], axis=1)
+    """(E_z, E_r) weights of the theta-hat component (fdtd_theta_coef)."""
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).ravel())
+    out = np.zeros((th.size, 2))
+    check(fdtd_theta_coef(_dp(th), th.size, _dp(out)), "fdtd_theta_coef")
+    return out
 
 
 class Cylinder:
@@ -597,6 +615,10 @@ class Batch:
         used = C.c_int()
         check(fdtd_batch_tune(self.h, trial_steps, C.byref(used)), "fdtd_batch_tune")
         return used.value
+
+    def set_wait_limit(self, cycles=0):
+        """Bound of every grid-barrier wait in SM clock cycles (0: default)."""
+        check(fdtd_batch_set_wait_limit(self.h, int(cycles)), "fdtd_batch_set_wait_limit")
 
     @property
     def graph_mode(self):

@@ -417,8 +417,6 @@ void adj_field_step(fdtd_ctx *h) {
     h->src.active = 0;
     switch (h->kernel) {
     case 1: launch_vtile(h, h->stream); h->launches++; break;
-    case 2: launch_fused(h, h->stream); h->launches++; break;
-    case 3: launch_strip(h, h->stream); h->launches++; break;
     default:
         launch_update_h(h, h->stream);
         launch_update_e(h, h->stream);

@@ -51,12 +51,15 @@ struct BArgs {
     const int *mstart;     // [nsim + 1] prefix sums of M items
     int steps;
     unsigned *ctr;         // [3 * steps] queue counters, zero at launch
-    unsigned *bar;         // [2] barrier count and generation
+    unsigned *bar;         // [2] barrier count and generation, zero at launch
     int *flags;
+    long long spin;        // clock cycles a barrier wait may take
 };
 
-// Grid-wide barrier: arrive, then wait (bounded) for the generation to move.
-__device__ bool grid_sync(unsigned *bar, int *flags) {
+// Grid-wide barrier: arrive, then wait (bounded by spin cycles) for the
+// generation to move.  A block whose wait gives up sets flag bit 1 and stops;
+// the others then give up at this barrier or the next, so the launch ends.
+__device__ bool grid_sync(unsigned *bar, int *flags, long long spin) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -71,7 +74,7 @@ __device__ bool grid_sync(unsigned *bar, int *flags) {
         } else {
             const long long t0 = clock64();
             while (*gen == g0) {
-                if (clock64() - t0 > (4LL << 30)) {
+                if (clock64() - t0 > spin) {
                     atomicOr(flags, 2);
                     ok = 0;
                     break;
@@ -110,6 +113,13 @@ __global__ void __launch_bounds__(256, 6) k_batch(BArgs A) {   // 40 registers: 
     __shared__ float *s_out;
     const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
     const int hitems = A.hstart[A.nsim], mitems = A.mstart[A.nsim];
+    // an earlier launch (or a block of this one) gave up: the simulations are
+    // in an unknown state.  One read per block, so that its threads leave
+    // together (thread 0 alone drives the work queue).
+    __shared__ int s_stop;
+    if (tid == 0) s_stop = *(volatile int *)A.flags;
+    __syncthreads();
+    if (s_stop) return;
     for (int s = 0; s < A.steps; ++s) {
         for (int phase = 0; phase < 3; ++phase) {
             const int total = phase < 2 ? hitems : mitems;
@@ -182,7 +192,7 @@ __global__ void __launch_bounds__(256, 6) k_batch(BArgs A) {   // 40 registers: 
                 }
                 __syncthreads();   // the item's shared copy is free again
             }
-            if (!grid_sync(A.bar, A.flags)) return;
+            if (!grid_sync(A.bar, A.flags, A.spin)) return;
         }
     }
     if (blockIdx.x == 0)
@@ -213,6 +223,7 @@ struct fdtd_batch {
     cudaStream_t solo_st[SOLO_STREAMS];   // the solo simulations, spread over these
     cudaEvent_t solo_ev[SOLO_STREAMS];
     int nshared;           // simulations inside the persistent kernel
+    long long spin;        // clock cycles a grid-barrier wait may take
     int blocks;
     int graph_ok;          // -1 unknown, 0 direct launches, 1 graphs
     std::map<int, cudaGraphExec_t> graphs;   // steps per launch -> executable graph
@@ -305,7 +316,9 @@ cudaError_t issue(fdtd_batch *b, int steps) {
     A.ctr = b->d_ctr;
     A.bar = b->d_bar;
     A.flags = b->d_flags;
+    A.spin = b->spin;
     cudaError_t e = cudaMemsetAsync(b->d_ctr, 0, 3 * steps * sizeof(unsigned), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), b->stream);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(b->blocks);
@@ -403,6 +416,7 @@ int fdtd_batch_create(fdtd_batch_t *out, const fdtd_t *sims, int n) {
     b->steps_per_launch = 8;
     b->solo_cells = -1;
     b->nshared = n;
+    b->spin = FDTD_BATCH_DEFAULT_WAIT_CYCLES;
     b->graph_ok = -1;
     b->status = FDTD_OK;
     bool streams_ok = true;
@@ -522,8 +536,24 @@ int fdtd_batch_sync(fdtd_batch_t b) {
     if (note(b, cudaStreamSynchronize(b->stream)) != FDTD_OK) return b->status;
     int f = 0;
     if (note(b, cudaMemcpy(&f, b->d_flags, sizeof(int), cudaMemcpyDeviceToHost)) != FDTD_OK) return b->status;
-    if (f && b->status == FDTD_OK) b->status = FDTD_ERR_TIMEOUT;
+    if (f) {
+        // a grid barrier gave up: the simulations of the persistent kernel
+        // were left part-way through a step
+        if (b->status == FDTD_OK) b->status = FDTD_ERR_TIMEOUT;
+        for (size_t q = 0; q < b->sims.size(); ++q)
+            if (q >= b->solo.size() || !b->solo[q])
+                if (b->sims[q]->status == FDTD_OK) b->sims[q]->status = FDTD_ERR_TIMEOUT;
+    }
     return b->status;
+}
+
+int fdtd_batch_set_wait_limit(fdtd_batch_t b, long long cycles) {
+    if (!b || cycles < 0) return FDTD_ERR_ARG;
+    if (b->status != FDTD_OK) return b->status;
+    if (note(b, cudaStreamSynchronize(b->stream)) != FDTD_OK) return b->status;
+    drop_graphs(b);   // the limit is a launch argument, baked into the graphs
+    b->spin = cycles == 0 ? FDTD_BATCH_DEFAULT_WAIT_CYCLES : cycles;
+    return FDTD_OK;
 }
 
 int fdtd_batch_set_config(fdtd_batch_t b, int threads, int cells_per_item, int steps_per_launch) {

@@ -48,8 +48,6 @@ void release(fdtd_ctx *h) {
     free_dev(h->d_partial);
     free_dev(h->d_result);
     free_dev(h->d_flags);
-    fused_release(h);
-    strip_release(h);
     vtile_release(h);
     for (cudaEvent_t e : h->timing.ev) cudaEventDestroy(e);
     delete h;
@@ -62,18 +60,6 @@ size_t field_bytes(const fdtd_ctx *h) { return sizeof(float) * 6 * (size_t)h->g.
 }  // namespace
 
 namespace fdtd {
-void interior_box(const fdtd_ctx *h, int lo[3], int hi[3]) {
-    const Grid &g = h->g;
-    const int P = h->P;
-    const int l = P > 0 ? P + 1 : 0;
-    lo[0] = (l + 3) / 4 * 4;
-    hi[0] = (g.nx - P) / 4 * 4 - 1;
-    lo[1] = l;
-    hi[1] = g.ny - 1 - P;
-    lo[2] = l;
-    hi[2] = g.nz - 1 - P;
-}
-
 Cpml cpml_view(const fdtd_ctx *h) {
     Cpml v{};
     v.P = h->P;
@@ -114,10 +100,6 @@ int fdtd_step_on(fdtd_ctx *h, int n, cudaStream_t st) {
     for (int s = 0; s < n; ++s) {
         if (h->kernel == 1) {
             timed_launch(h, st, [](const fdtd_ctx *c, cudaStream_t q) { launch_vtile(const_cast<fdtd_ctx *>(c), q); });
-        } else if (h->kernel == 3) {
-            timed_launch(h, st, [](const fdtd_ctx *c, cudaStream_t q) { launch_strip(const_cast<fdtd_ctx *>(c), q); });
-        } else if (h->kernel == 2) {
-            timed_launch(h, st, [](const fdtd_ctx *c, cudaStream_t q) { launch_fused(const_cast<fdtd_ctx *>(c), q); });
         } else {
             timed_launch(h, st, launch_update_h);
             timed_launch(h, st, launch_update_e);
@@ -126,6 +108,7 @@ int fdtd_step_on(fdtd_ctx *h, int n, cudaStream_t st) {
         if (h->np > 0) { launch_probes(h, st); h->launches++; }
         h->cur ^= 1;
         h->steps++;
+        if (h->watch_every > 0 && h->steps % h->watch_every == 0) { launch_watch(h, st); h->launches++; }
     }
     return note(h, cudaGetLastError());
 }
@@ -244,12 +227,10 @@ int fdtd_create(fdtd_t *out, int nx, int ny, int nz, double dx, double dt, doubl
         return fail(FDTD_ERR_OOM);
     }
     if ((rc = note(h, cudaStreamSynchronize(h->stream))) != FDTD_OK) return fail(rc);
-    // the register-strip z-march is the default field-update path; the
-    // TMA-staged z-march and the unfused pair of sweeps stay available
-    // (fdtd_set_kernel) as cross-checks
+    // the vector-tile z-march is the default field-update path; the others
+    // stay available (fdtd_set_kernel) as cross-checks
+    h->watch_every = FDTD_WATCHDOG_DEFAULT_STEPS;
     h->kernel = 0;
-    if (fused_prepare(h) == FDTD_OK) h->kernel = 2;
-    if (strip_prepare(h) == FDTD_OK) h->kernel = 3;
     if (vtile_prepare(h) == FDTD_OK) h->kernel = 1;
     cudaGetLastError();
     *out = h;
@@ -358,7 +339,8 @@ int fdtd_step(fdtd_t h, int n) {
 static int check_flags(fdtd_ctx *h) {
     int f = 0;
     if (note(h, cudaMemcpy(&f, h->d_flags, sizeof(int), cudaMemcpyDeviceToHost)) != FDTD_OK) return h->status;
-    if (f != 0 && h->status == FDTD_OK) h->status = FDTD_ERR_TIMEOUT;
+    if (f != 0 && h->status == FDTD_OK)
+        h->status = (f & ~fdtd::FLAG_UNSTABLE) ? FDTD_ERR_TIMEOUT : FDTD_ERR_UNSTABLE;
     return h->status;
 }
 
@@ -434,6 +416,11 @@ int fdtd_reset(fdtd_t h) {
         TRY(h, cudaMemsetAsync(h->d_trace, 0, sizeof(float) * 2 * (size_t)h->np * h->max_steps, h->stream));
     h->cur = 0;
     h->steps = 0;
+    if (h->status == FDTD_ERR_UNSTABLE) {
+        // the non-finite values are gone with the fields: the handle is usable again
+        TRY(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int), h->stream));
+        h->status = FDTD_OK;
+    }
     return note(h, cudaGetLastError());
 }
 
@@ -567,15 +554,18 @@ int fdtd_launch_count(fdtd_t h, int64_t *launches) {
 
 const char *fdtd_kernel_name(fdtd_t h) {
     if (h && h->kernel == 1) return vtile_name();
-    if (h && h->kernel == 2) return fused_name();
-    if (h && h->kernel == 3) return strip_name();
     return "unfused-h-then-e";
 }
 
+int fdtd_set_watchdog(fdtd_t h, int every) {
+    if (!h || every < 0) return FDTD_ERR_ARG;
+    h->watch_every = every;
+    return FDTD_OK;
+}
+
 int fdtd_set_kernel(fdtd_t h, int which) {
-    if (!h || which < 0 || which > 3) return FDTD_ERR_ARG;
-    if ((which == 1 && !h->vtile) || (which == 2 && !h->fused) || (which == 3 && !h->strip))
-        return FDTD_ERR_ARG;
+    if (!h || which < 0 || which > 1) return FDTD_ERR_ARG;
+    if (which == 1 && !h->vtile) return FDTD_ERR_ARG;
     h->kernel = which;
     return FDTD_OK;
 }

@@ -111,14 +111,6 @@ struct Probes {
     float *trace;             // [n][max_steps][2]
 };
 
-// Cells outside the fused kernel's interior box: up to six disjoint boxes
-// [lo, hi] (inclusive, cell indices) and the prefix sums of their cell counts.
-struct Shell {
-    int n;
-    int lo[6][3], hi[6][3];
-    long long start[7];
-};
-
 struct TimingRec {
     std::vector<cudaEvent_t> ev; // start/stop pairs
     int used = 0;
@@ -144,12 +136,11 @@ struct fdtd_ctx {
     size_t psi_axis[3];       // floats of one psi array of each axis
     float *coef_block;        // aE,bE,aH,bH per axis
     const float *aE[3], *bE[3], *aH[3], *bH[3];
-    int kernel;               // field-update path: 0 unfused sweeps, 1 vector tile,
-                              // 2 TMA-staged z-march, 3 register strip
-    void *fused;              // host state of the TMA path (tensor maps, launch shape)
-    void *strip;              // host state of the register-strip path
+    int kernel;               // field-update path: 0 unfused sweeps, 1 vector tile
     void *vtile;              // host state of the vector-tile path
-    int *d_flags;             // device error flags (bit 0: a bounded wait gave up)
+    int *d_flags;             // device error flags (bits 0-1: a bounded wait gave up,
+                              // bit 2: the watchdog saw a non-finite value)
+    int watch_every;          // steps between watchdog checks (0: off)
     int num_sms;
 
     // source
@@ -185,26 +176,14 @@ void launch_update_h(const fdtd_ctx *h, cudaStream_t s);
 void launch_update_e(const fdtd_ctx *h, cudaStream_t s);
 void launch_mur(const fdtd_ctx *h, cudaStream_t s);
 void launch_probes(const fdtd_ctx *h, cudaStream_t s);
+// watchdog: every component on every WATCH_STRIDE-th z plane (and the last)
+// of the set holding the newest fields; sets flag bit 2 on a non-finite value
+constexpr int WATCH_STRIDE = 8;
+constexpr int FLAG_UNSTABLE = 4;
+void launch_watch(const fdtd_ctx *h, cudaStream_t s);
 void launch_energy(const fdtd_ctx *h, cudaStream_t s, int *launches);
-void launch_shell(const fdtd_ctx *h, const Shell &sh, cudaStream_t s, int *launches);
 void launch_set_field(const fdtd_ctx *h, int comp, const float *compact, cudaStream_t s);
 void launch_get_field(const fdtd_ctx *h, int comp, float *compact, cudaStream_t s);
-
-// fused z-march (kernels_fused.cu)
-int fused_prepare(fdtd_ctx *h);   // tensor maps + launch shape; FDTD_OK or error
-void launch_fused(fdtd_ctx *h, cudaStream_t s);
-const char *fused_name();
-void fused_release(fdtd_ctx *h);
-
-// register-strip z-march (kernels_strip.cu)
-int strip_prepare(fdtd_ctx *h);
-void launch_strip(fdtd_ctx *h, cudaStream_t s);
-
-// The CPML-free interior box, cells [lo, hi] inclusive per axis: [P+1, N-P-1]
-// (all of [0, N-1] without CPML), its x range shrunk to whole groups of four
-// columns (lo[0] and hi[0]+1 multiples of 4).  The cells around it form the
-// shell updated by the register-strip kernel's shell boxes.
-void interior_box(const fdtd_ctx *h, int lo[3], int hi[3]);
 
 // TMA-staged vector-tile z-march over the whole grid, CPML included (kernels_vtile.cu)
 int vtile_prepare(fdtd_ctx *h);
@@ -215,8 +194,6 @@ void launch_vtile(fdtd_ctx *h, cudaStream_t s);
 int fdtd_step_on(fdtd_ctx *h, int n, cudaStream_t st);
 const char *vtile_name();
 void vtile_release(fdtd_ctx *h);
-const char *strip_name();
-void strip_release(fdtd_ctx *h);
 
 // host tables (tables.cpp)
 void cpml_coefficients(int n, int P, double dx, double dt, double eps_r, float *aE, float *bE,

@@ -58,58 +58,6 @@ void launch_update_e(const fdtd_ctx *h, cudaStream_t s) {
     k_update_e<<<grd, blk, 0, s>>>(g, in, out + 3 * g.comp, out, cpml_view(h), (float)h->kE, h->src, h->steps);
 }
 
-// ---- the shell of cells outside the interior box --------------------------------
-// The shell is up to six disjoint boxes (z slabs, then y slabs, then x slabs of
-// what is left); cell number t of the shell is found by a scan of the boxes'
-// prefix sums.  H must be complete on the whole grid before E, so the shell is
-// updated by two launches after the interior kernel has written its cells.
-
-__device__ __forceinline__ bool shell_cell(const Shell &sh, long long t, int &i, int &j, int &k) {
-    int b = 0;
-    while (b < sh.n && t >= sh.start[b + 1]) ++b;
-    if (b >= sh.n) return false;
-    long long r = t - sh.start[b];
-    const int ex = sh.hi[b][0] - sh.lo[b][0] + 1, ey = sh.hi[b][1] - sh.lo[b][1] + 1;
-    i = sh.lo[b][0] + (int)(r % ex);
-    r /= ex;
-    j = sh.lo[b][1] + (int)(r % ey);
-    k = sh.lo[b][2] + (int)(r / ey);
-    return true;
-}
-
-__global__ void __launch_bounds__(256) k_shell_h(Grid g, Shell sh, const float *__restrict__ Ein,
-                                                 const float *__restrict__ Hin,
-                                                 float *__restrict__ Hout, Cpml pml, float kH) {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    int i, j, k;
-    if (t >= sh.start[sh.n] || !shell_cell(sh, t, i, j, k)) return;
-    cell_h(g, Ein, Hin, Hout, pml, kH, i, j, k);
-}
-
-__global__ void __launch_bounds__(256) k_shell_e(Grid g, Shell sh, const float *__restrict__ Ein,
-                                                 const float *__restrict__ Hnew,
-                                                 float *__restrict__ Eout, Cpml pml, float kE,
-                                                 Source src, long long n) {
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    int i, j, k;
-    if (t >= sh.start[sh.n] || !shell_cell(sh, t, i, j, k)) return;
-    cell_e(g, Ein, Hnew, Eout, pml, kE, src, n, i, j, k);
-}
-
-void launch_shell(const fdtd_ctx *h, const Shell &sh, cudaStream_t s, int *launches) {
-    *launches = 0;
-    if (sh.n == 0 || sh.start[sh.n] == 0) return;
-    const Grid &g = h->g;
-    const float *in = h->fields[h->cur];
-    float *out = h->fields[h->cur ^ 1];
-    const long long cells = sh.start[sh.n];
-    const unsigned blocks = (unsigned)((cells + 255) / 256);
-    const Cpml pml = cpml_view(h);
-    k_shell_h<<<blocks, 256, 0, s>>>(g, sh, in, in + 3 * g.comp, out + 3 * g.comp, pml, (float)h->kH);
-    k_shell_e<<<blocks, 256, 0, s>>>(g, sh, in, out + 3 * g.comp, out, pml, (float)h->kE, h->src, h->steps);
-    *launches = 2;
-}
-
 __global__ void k_mur(Grid g, const float *__restrict__ Eold, float *__restrict__ Enew, float m) {
     mur_cell(g, Eold, Enew, m, blockIdx.z, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y);
 }
@@ -142,6 +90,35 @@ __global__ void k_probes(Grid g, const float *__restrict__ E, Probes p, long lon
 void launch_probes(const fdtd_ctx *h, cudaStream_t s) {
     Probes p{h->np, h->max_steps, h->d_ijk, h->d_cxy, h->d_trace};
     k_probes<<<(h->np + 127) / 128, 128, 0, s>>>(h->g, h->fields[h->cur ^ 1], p, h->steps);
+}
+
+// Watchdog of the step path: block (x, y) scans plane k = min(y * stride,
+// nz) of the six components in chunks of 4 floats per thread; a non-finite
+// value anywhere sets flag bit 2.  An instability, or a non-finite value put
+// into any cell, spreads one plane per step (each Yee half step couples
+// neighbouring planes only), so it reaches a sampled plane within stride / 2
+// steps.
+__global__ void __launch_bounds__(256) k_watch(Grid g, const float *__restrict__ f, int stride, int *flags) {
+    const int k = min((int)blockIdx.y * stride, g.nz);
+    const long long n4 = g.plane / 4;   // plane is a multiple of 32 floats
+    bool bad = false;
+    for (int c = 0; c < 6; ++c) {
+        const float4 *p = reinterpret_cast<const float4 *>(f + c * g.comp + (long long)k * g.plane);
+        for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n4;
+             t += (long long)gridDim.x * blockDim.x) {
+            const float4 v = p[t];
+            bad |= !isfinite(v.x) || !isfinite(v.y) || !isfinite(v.z) || !isfinite(v.w);
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, FLAG_UNSTABLE);
+}
+
+void launch_watch(const fdtd_ctx *h, cudaStream_t s) {
+    const Grid &g = h->g;
+    const int planes = (g.nz + WATCH_STRIDE - 1) / WATCH_STRIDE + 1;
+    const long long n4 = g.plane / 4;
+    const int bx = (int)((n4 + 255) / 256 < 8 ? (n4 + 255) / 256 : 8);
+    k_watch<<<dim3(bx, planes), 256, 0, s>>>(g, h->fields[h->cur], WATCH_STRIDE, h->d_flags);
 }
 
 // ---- field copies -----------------------------------------------------------

@@ -4,7 +4,10 @@
 // Same two-pass reduction as the handle's energy check: pass 1 reduces
 // |E|^2, |H|^2 and a non-finite count per block into a partial slot, pass 2
 // reduces the slots into three totals.  The slots and the totals live in a
-// fixed __device__ array; its address is looked up once per device.
+// fixed __device__ array; its address is looked up once per device and
+// context (a device reset makes a new primary context, which loads the module
+// again, possibly at another address).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -23,8 +26,32 @@ constexpr int kTotals = 3 * FDTD_ENERGY_SCRATCH_BLOCKS;   // offset of the three
 // each call writes every slot it reads before reading it
 __device__ __align__(256) double g_energy_scratch[3 * FDTD_ENERGY_SCRATCH_BLOCKS + 3];
 
-// device address of g_energy_scratch per device (looked up on first use)
+// device address of g_energy_scratch per device (looked up on first use),
+// valid for the context it was looked up in
 std::atomic<double *> g_scratch_addr[kMaxDevices];
+std::atomic<void *> g_scratch_ctx[kMaxDevices];
+
+typedef CUresult (*CtxGetCurrent)(CUcontext *);
+
+// the calling thread's current context (the primary context of the current
+// device once the runtime has initialised it), or null
+void *current_context() {
+    static std::atomic<CtxGetCurrent> fn{nullptr};
+    CtxGetCurrent f = fn.load();
+    if (!f) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        f = reinterpret_cast<CtxGetCurrent>(p);
+        fn.store(f);
+    }
+    CUcontext c = nullptr;
+    return f(&c) == CUDA_SUCCESS ? static_cast<void *>(c) : nullptr;
+}
 
 __device__ __forceinline__ double warp_total(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -87,8 +114,11 @@ extern "C" int fdtd_energy_noalloc(const float *d_fields, int nx, int ny, int nz
         cudaGetLastError();
         return FDTD_ERR_CUDA;
     }
+    // before the runtime's first use of the device no context is current yet;
+    // the lookup below then makes the primary context current
+    void *ctx = current_context();
     double *scratch = g_scratch_addr[dev].load();
-    if (!scratch) {
+    if (!scratch || !ctx || g_scratch_ctx[dev].load() != ctx) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_energy_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
@@ -96,6 +126,7 @@ extern "C" int fdtd_energy_noalloc(const float *d_fields, int nx, int ny, int nz
         }
         scratch = static_cast<double *>(p);
         g_scratch_addr[dev].store(scratch);
+        g_scratch_ctx[dev].store(current_context());
     }
     if (nblocks == 0) {
         int sms = 0;

@@ -2,7 +2,8 @@
 // planes, four columns per lane, CPML folded in.
 //
 // H^{n+1/2} and E^{n+1} of a plane are computed together (Yee scheme,
-// Sec. III.A; shower current of Sec. III.B; CPML of Sec. III.C): a step reads
+// Sec. III.A; shower current of Sec. III.B; the paper names no absorbing
+// boundary, so the CPML is this library's choice, Roden-Gedney): a step reads
 // E^n and H^{n-1/2} once and writes H^{n+1/2} and E^{n+1} once, 24 B + 24 B
 // per cell, plus the CPML memory of the cells in the layers (16 B read and
 // 16 B written per cell and layer axis).

@@ -187,3 +187,14 @@ extern "C" int fdtd_trace_spectrum(const float *traces, int n_traces, int n_t, i
     if (!on_device && cudaStreamSynchronize(s) != cudaSuccess) rc = FDTD_ERR_CUDA;
     return rc;
 }
+
+extern "C" int fdtd_theta_coef(const double *theta, int n, double *coef) {
+    if (!theta || !coef || n < 1) return FDTD_ERR_ARG;
+    for (int t = 0; t < n; ++t)
+        if (!std::isfinite(theta[t])) return FDTD_ERR_ARG;
+    for (int t = 0; t < n; ++t) {
+        coef[2 * t] = -std::sin(theta[t]);
+        coef[2 * t + 1] = std::cos(theta[t]);
+    }
+    return FDTD_OK;
+}

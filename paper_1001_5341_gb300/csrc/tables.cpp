@@ -3,6 +3,7 @@
 #include <cmath>
 #include <vector>
 
+#include "../../include/cyl.h"
 #include "../../include/fdtd.h"
 
 namespace {
@@ -110,6 +111,22 @@ int fdtd_lateral_gaussian(int L, double sigma_cells, double *w) {
             tot += v;
         }
     for (int t = 0; t < n * n; ++t) w[t] /= tot;
+    return FDTD_OK;
+}
+
+int cyl_rings_gaussian(int n_rings, double d, double sigma_r, double *w) {
+    if (!w || n_rings < 1 || !(d > 0.0) || !(sigma_r > 0.0)) return FDTD_ERR_ARG;
+    // fraction of a radial Gaussian inside radius r: 1 - exp(-r^2 / (2 sigma_r^2))
+    auto inside = [&](double r) { return -std::expm1(-0.5 * (r / sigma_r) * (r / sigma_r)); };
+    double tot = 0.0, lo = 0.0;
+    for (int i = 0; i < n_rings; ++i) {
+        const double hi = (i + 0.5) * d;
+        w[i] = inside(hi) - inside(lo);
+        tot += w[i];
+        lo = hi;
+    }
+    if (!(tot > 0.0)) return FDTD_ERR_ARG;
+    for (int i = 0; i < n_rings; ++i) w[i] /= tot;
     return FDTD_OK;
 }
 

@@ -159,3 +159,37 @@ def test_patch_matches_full_grid_inside_its_dependency_cone():
             # the cone is tight: one cell closer to the cut, the patch differs
             if i0 > 0:
                 assert np.abs(p.Ez[n - 1] - full.Ez[i0 + n - 1, j0:]).max() > 1e-9 * np.abs(full.Ez).max()
+
+
+def test_ring_weights_integrate_the_radial_gaussian():
+    """The ring weights of the paper's radial Gaussian (Sec. III.B) against a
+    numerical quadrature of 2 pi r rho(r) over each ring, rho the
+    normalised 2D Gaussian density; and the library's generator agrees."""
+    integrate = pytest.importorskip("scipy.integrate")
+    d, sigma = 0.005, 0.05
+    n = 31
+    w = O.ring_weights_gaussian(n, d, sigma)
+    rho = lambda r: math.exp(-0.5 * (r / sigma) ** 2) / (2.0 * math.pi * sigma ** 2)
+    edges = [0.0] + [(i + 0.5) * d for i in range(n)]
+    ref = np.array([integrate.quad(lambda r: 2.0 * math.pi * r * rho(r), a, b, epsabs=0, epsrel=1e-13)[0]
+                    for a, b in zip(edges[:-1], edges[1:])])
+    assert abs(ref.sum() - (1.0 - math.exp(-0.5 * (edges[-1] / sigma) ** 2))) < 1e-12
+    np.testing.assert_allclose(w, ref / ref.sum(), rtol=1e-11, atol=0)
+    assert abs(w.sum() - 1.0) < 1e-14
+    # one ring: all the charge on the axis disc
+    assert np.array_equal(O.ring_weights_gaussian(1, d, sigma), [1.0])
+
+
+def test_library_and_oracle_build_the_same_2d_tables():
+    import workloads as W
+    try:
+        import paper_1001_5341_gb300 as fd
+    except ImportError:
+        pytest.skip("library not built")
+    for n in (256, 8192):
+        w = W.cyl_table1(n)
+        q_lib, w_lib = fd.cyl_tables(w)
+        q_orc, w_orc = O.tables(w)
+        np.testing.assert_allclose(q_lib, q_orc, rtol=1e-13, atol=0)
+        np.testing.assert_allclose(w_lib, w_orc, rtol=1e-12, atol=0)
+        assert abs(q_orc).max() == pytest.approx(abs(w.shower["q_max"]), rel=1e-3)

@@ -190,8 +190,9 @@ def test_full_size_grid_on_patches(fd):
         j = torch.arange(cols, dtype=torch.int64, device="cuda")[None, :]
         g.set_field(c, W.cyl_field(17, c, i, j, xp=torch).contiguous())
         del i, j
-    q = wl.q
-    g.set_shower(q, wl.z0, wl.bin_dz, wl.v, wl.w)
+    q, rings = fd.cyl_tables(wl)
+    qo, rings_o = O.tables(wl)
+    g.set_shower(q, wl.z0, wl.bin_dz, wl.v, rings)
     L, U = info["seg_rows"], 128 - 2 * info["steps_per_launch"]
     zs = wl.z0 + wl.v * n * wl.dt
     js = int(zs / wl.d)
@@ -212,7 +213,7 @@ def test_full_size_grid_on_patches(fd):
         pr, pz = i1 - i0, j1 - j0
         o = O.CylOracle(pr, pz, wl.d, wl.dt, wl.eps_r, boundary=wl.boundary, i0=i0)
         o.Er[:], o.Ez[:], o.Hp[:] = _fields(17, pr, pz, i0, j0)
-        o.set_shower(q, wl.z0 - j0 * wl.d, wl.bin_dz, wl.v, wl.w)
+        o.set_shower(qo, wl.z0 - j0 * wl.d, wl.bin_dz, wl.v, rings_o)
         lo_i = 0 if i0 == 0 else n + 2
         lo_j = 0 if j0 == 0 else n + 2
         hi_i = pr if i1 == nr else pr - n - 2

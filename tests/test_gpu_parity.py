@@ -23,9 +23,8 @@ def fd():
     return m
 
 
-# the field-update paths: 1 = vector-tile interior + register-strip CPML shell
-# (default), 3 = register strip everywhere, 2 = TMA-staged z-march, 0 = unfused
-@pytest.fixture(params=[1, 3, 2, 0], ids=["vtile", "strip", "tma", "unfused"])
+# the field-update paths: 1 = vector-tile z-march (default), 0 = unfused sweeps
+@pytest.fixture(params=[1, 0], ids=["vtile", "unfused"])
 def kernel(request):
     return request.param
 
@@ -102,7 +101,7 @@ def test_gh_small_cpml(fd, kernel):
     run_pair(fd, w, [w.steps], kernel)
 
 
-@pytest.mark.parametrize("fused", [1, 2, 3])
+@pytest.mark.parametrize("fused", [1])
 def test_fused_and_unfused_agree(fd, fused):
     """The paths compute the same update; they may differ only by FP32
     rounding (FMA contraction)."""

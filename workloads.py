@@ -28,11 +28,12 @@ The paper uses a parameterised shower instead of Monte Carlo output
                  2D Courant step, Mur-1, n steps (Table I's rates grow as
                  N_side, read as one step per cell of the side); the paper's
                  Gaussian shower model (Sec. III.B: longitudinal l = 2 m,
-                 radial sigma_r = 5 cm) given as a 256-bin charge table and
-                 ring weights, moving at c from 8 l before its maximum; 64
-                 detectors at R in [2, 0.4 n d] m, theta in [40, 70] deg
-                 around the maximum (seed 4004).  The 2D solver takes tables,
-                 so both sides receive the same tables.
+                 radial sigma_r = 5 cm) as the parameters of a 256-bin
+                 charge table and of the ring weights, moving at c from 8 l
+                 before its maximum; 64 detectors at R in [2, 0.4 n d] m,
+                 theta in [40, 70] deg around the maximum (seed 4004).  The
+                 2D solver takes tables; the library and the oracle build
+                 them from these parameters with their own code.
 * ``cyl_field(seed, comp, i, j, xp)`` counter-based initial field values
                  (uniform in [-1/2, 1/2), E in V/m, H_phi divided by the
                  impedance of ice), computable on any patch with NumPy or
@@ -296,11 +297,11 @@ class CylWorkload:
     eps_r: float
     boundary: int
     steps: int
-    q: np.ndarray          # charge per bin (C)
+    shower: dict           # Gaussian model parameters: z_peak, l, q_max (C), n_bins,
+                           # sigma_r (m), n_rings; tables are built by each side
     z0: float              # position of bin 0 (m)
     bin_dz: float
     v: float
-    w: np.ndarray          # ring weights, sum 1
     probes_rz: np.ndarray  # [n, 2] (r, z) in metres
 
     @property
@@ -310,7 +311,7 @@ class CylWorkload:
     def describe(self) -> dict:
         return {"workload": self.name, "grid_rz": [self.nr, self.nz], "d_m": self.d, "dt_s": self.dt,
                 "eps_r": self.eps_r, "boundary": {PEC: "pec", MUR1: "mur1"}[self.boundary],
-                "steps": self.steps, "rings": int(len(self.w)), "probes": int(len(self.probes_rz))}
+                "steps": self.steps, "rings": int(self.shower["n_rings"]), "probes": int(len(self.probes_rz))}
 
 
 def courant_dt_2d(d: float, eps_r: float) -> float:
@@ -328,21 +329,17 @@ def cyl_table1(n: int = 8192, seed: int = 4004, extent_m: float = 40.96, steps: 
     n_bins = 256
     z0 = z_max - 4.0 * l_m
     bin_dz = 8.0 * l_m / (n_bins - 1)
-    zb = z0 + bin_dz * np.arange(n_bins)
-    q = q_max * np.exp(-0.5 * ((zb - z_max) / l_m) ** 2)
-    # ring weights of the radial Gaussian: ring i covers [(i - 1/2) d, (i + 1/2) d]
+    # rings out to 3 sigma_r (ring i covers [(i - 1/2) d, (i + 1/2) d])
     n_rings = max(1, min(n, int(math.ceil(3.0 * sigma_r_m / d)) + 1))
-    edges = np.concatenate([[0.0], (np.arange(n_rings) + 0.5) * d])
-    cdf = 1.0 - np.exp(-0.5 * (edges / sigma_r_m) ** 2)
-    w = np.diff(cdf)
-    w = w / w.sum()
+    shower = {"kind": "gaussian", "z_peak": z_max, "l": l_m, "q_max": q_max, "n_bins": n_bins,
+              "sigma_r": sigma_r_m, "n_rings": n_rings}
     R = rng.uniform(min(2.0, 0.1 * extent_m), 0.4 * extent_m, n_probes)
     th = np.radians(rng.uniform(40.0, 70.0, n_probes))
     rz = np.stack([R * np.sin(th), z_max + R * np.cos(th)], axis=1)
     rz[:, 0] = np.clip(rz[:, 0], 0.0, (n - 1) * d)
     rz[:, 1] = np.clip(rz[:, 1], d, (n - 1) * d)
     return CylWorkload(f"cyl{n}x{n}", n, n, d, dt, EPS_R_ICE, boundary, n if steps is None else steps,
-                       q, z0, bin_dz, C0, w, rz)
+                       shower, z0, bin_dz, C0, rz)
 
 
 Z_ICE = 376.730313668 / math.sqrt(EPS_R_ICE)
