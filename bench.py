@@ -243,7 +243,8 @@ def run_ours(args):
     w = replica_workload(rank, args.workload, steps=args.warmup + args.steps, **({"nz": args.nz} if args.nz else {}))
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        sim = fd.Simulation.from_workload(w, max_steps=args.warmup + args.steps, stream=stream)
+        sim = fd.Simulation.from_workload(w, max_steps=args.warmup + args.steps, stream=stream,
+                                          kernel=args.kernel if args.kernel >= 0 else None)
         sim.step(args.warmup)
         sim.sync()
         clocks = ClockSampler(local)
@@ -801,6 +802,8 @@ def main():
                     help="3D workload: greisen384 (384x384x1536, the headline) or gh640 (640x640x2048, dx 3 cm)")
     ap.add_argument("--n", type=int, default=8192, help="cyl grid side")
     ap.add_argument("--cyl-kernel", type=int, default=-1, help="cyl kernel (-1: library default)")
+    ap.add_argument("--kernel", type=int, default=-1,
+                    help="3D field-update path (fdtd_set_kernel; -1: library default)")
     ap.add_argument("--batch-kind", choices=["config4", "small"], default="config4",
                     help="batch workload: 64 grids 64^3 .. 256x256x512, or 256 grids 32^3 .. 96^3")
     ap.add_argument("--seg-rows", type=int, default=0, help="cyl rows per segment (0: automatic)")

@@ -212,8 +212,9 @@ int fdtd_timing_begin(fdtd_t h, int max_launches);
 int fdtd_timing_end(fdtd_t h, double *total_ms, int *launches);
 int fdtd_launch_count(fdtd_t h, int64_t *launches);
 
-/* Cells updated by one launch of the timed kernel(s): the whole grid (the
-   unfused path 0 times its H sweep and its E sweep as separate launches). */
+/* Cell-updates of one launch of the timed kernel(s): the whole grid (the
+   unfused path 0 times its H sweep and its E sweep as separate launches),
+   twice the grid on path 2 (two steps per launch). */
 int fdtd_timed_cells(fdtd_t h, int64_t *cells);
 
 /* Name of the field-update path in use (static string). */
@@ -223,6 +224,11 @@ const char *fdtd_kernel_name(fdtd_t h);
  * Select the field-update path (all compute the same update, Sec. III.A):
  *   1 = one pass per step: TMA-staged vector-tile z-march over the whole
  *       grid, CPML included (the default);
+ *   2 = two steps per pass (temporal blocking of the leapfrog): each tile
+ *       recomputes the first step on a two-cell halo, so a pass reads the
+ *       fields once and writes them once for two steps; CPML and detectors
+ *       included; a last odd step of fdtd_step runs on path 1.  PEC and CPML
+ *       grids only (FDTD_ERR_ARG on a Mur grid);
  *   0 = one H sweep then one E sweep (the reference path: the batched
  *       persistent kernel and the adjoint use its per-cell code).
  * Returns FDTD_ERR_ARG for a path the handle cannot run.

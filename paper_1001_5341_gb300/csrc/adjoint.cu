@@ -462,6 +462,7 @@ int fdtd_adjoint_gradient(fdtd_t h, const float *dl_dtrace, int n_steps, double 
     if (h->psi_block && rc == FDTD_OK)
         rc = note(h, cudaMemsetAsync(h->psi_block, 0, h->psi_floats * sizeof(float), h->stream));
     h->cur = 0;
+    h->ecur = 0;
     const Probes p{h->np, h->max_steps, h->d_ijk, h->d_cxy, h->d_trace};
     for (int n = n_steps; n >= 1 && rc == FDTD_OK; --n) {
         if (n < n_steps) adj_field_step(h);   // mu^n = M^T mu^{n+1}
@@ -483,6 +484,7 @@ int fdtd_adjoint_gradient(fdtd_t h, const float *dl_dtrace, int n_steps, double 
     if (h->psi_block && rc == FDTD_OK)
         rc = note(h, cudaMemsetAsync(h->psi_block, 0, h->psi_floats * sizeof(float), h->stream));
     h->cur = 0;
+    h->ecur = 0;
     h->steps = 0;
     if (rc == FDTD_OK && !on_device)
         rc = note(h, cudaMemcpyAsync(grad_q, dgrad, sizeof(double) * h->src.nbins, cudaMemcpyDeviceToHost, h->stream));

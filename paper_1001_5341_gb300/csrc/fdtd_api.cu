@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -18,6 +19,9 @@ constexpr double kMu0 = 1.25663706212e-6;
 
 int note(fdtd_ctx *h, cudaError_t e) {
     if (e == cudaSuccess) return FDTD_OK;
+    // FDTD_DEBUG set in the environment: the CUDA error behind a status on stderr
+    static const bool debug = std::getenv("FDTD_DEBUG") != nullptr;
+    if (debug) std::fprintf(stderr, "fdtd: CUDA error %d (%s)\n", (int)e, cudaGetErrorString(e));
     int code = (e == cudaErrorMemoryAllocation) ? FDTD_ERR_OOM : FDTD_ERR_CUDA;
     if (h && h->status == FDTD_OK) h->status = code;
     return code;
@@ -39,6 +43,7 @@ void release(fdtd_ctx *h) {
     free_dev(h->fields[0]);
     free_dev(h->fields[1]);
     free_dev(h->psi_block);
+    free_dev(h->epsi2);
     free_dev(h->coef_block);
     free_dev(h->d_q);
     free_dev(h->d_w);
@@ -49,6 +54,7 @@ void release(fdtd_ctx *h) {
     free_dev(h->d_result);
     free_dev(h->d_flags);
     vtile_release(h);
+    tb2_release(h);
     for (cudaEvent_t e : h->timing.ev) cudaEventDestroy(e);
     delete h;
 }
@@ -65,7 +71,7 @@ Cpml cpml_view(const fdtd_ctx *h) {
     v.P = h->P;
     v.W = h->P > 0 ? 2 * h->P + 1 : 0;
     if (h->P <= 0) return v;
-    float *p = h->psi_block;
+    float *p = h->ecur ? h->epsi2 : h->psi_block;
     const size_t set = 2 * (h->psi_axis[0] + h->psi_axis[1] + h->psi_axis[2]);
     float *hin = h->psi_block + set * (1 + h->cur), *hout = h->psi_block + set * (1 + (h->cur ^ 1));
     size_t off = 0;
@@ -97,18 +103,31 @@ static void timed_launch(fdtd_ctx *h, cudaStream_t st, void (*fn)(const fdtd_ctx
 // n steps of the handle's selected path, issued on `st` (the handle's own
 // stream for fdtd_step; a batch's stream when the batch steps it alone).
 int fdtd_step_on(fdtd_ctx *h, int n, cudaStream_t st) {
-    for (int s = 0; s < n; ++s) {
-        if (h->kernel == 1) {
-            timed_launch(h, st, [](const fdtd_ctx *c, cudaStream_t q) { launch_vtile(const_cast<fdtd_ctx *>(c), q); });
+    for (int s = 0; s < n;) {
+        int adv = 1;
+        if (h->kernel == 2 && n - s >= 2) {
+            // two steps in one pass; the detectors of both from its records
+            timed_launch(h, st, [](const fdtd_ctx *c, cudaStream_t q) { launch_tb2(const_cast<fdtd_ctx *>(c), q); });
+            if (h->np > 0) { launch_tb2_probes(h, st); h->launches++; }
+            h->ecur ^= 1;
+            adv = 2;
         } else {
-            timed_launch(h, st, launch_update_h);
-            timed_launch(h, st, launch_update_e);
+            if (h->kernel == 1 || (h->kernel == 2 && h->vtile)) {
+                timed_launch(h, st, [](const fdtd_ctx *c, cudaStream_t q) { launch_vtile(const_cast<fdtd_ctx *>(c), q); });
+            } else {
+                timed_launch(h, st, launch_update_h);
+                timed_launch(h, st, launch_update_e);
+            }
+            if (h->boundary == FDTD_MUR1) { launch_mur(h, st); h->launches++; }
+            if (h->np > 0) { launch_probes(h, st); h->launches++; }
         }
-        if (h->boundary == FDTD_MUR1) { launch_mur(h, st); h->launches++; }
-        if (h->np > 0) { launch_probes(h, st); h->launches++; }
         h->cur ^= 1;
-        h->steps++;
-        if (h->watch_every > 0 && h->steps % h->watch_every == 0) { launch_watch(h, st); h->launches++; }
+        h->steps += adv;
+        s += adv;
+        if (h->watch_every > 0 && h->steps / h->watch_every != (h->steps - adv) / h->watch_every) {
+            launch_watch(h, st);
+            h->launches++;
+        }
     }
     return note(h, cudaGetLastError());
 }
@@ -212,6 +231,9 @@ int fdtd_create(fdtd_t *out, int nx, int ny, int nz, double dx, double dt, doubl
         h->psi_floats = 3 * 2 * (h->psi_axis[0] + h->psi_axis[1] + h->psi_axis[2]);
         if (cudaMalloc(&h->psi_block, h->psi_floats * sizeof(float)) != cudaSuccess) { cudaGetLastError(); return fail(FDTD_ERR_OOM); }
         if ((rc = note(h, cudaMemsetAsync(h->psi_block, 0, h->psi_floats * sizeof(float), h->stream))) != FDTD_OK) return fail(rc);
+        const size_t third = h->psi_floats / 3 * sizeof(float);
+        if (cudaMalloc(&h->epsi2, third) != cudaSuccess) { cudaGetLastError(); return fail(FDTD_ERR_OOM); }
+        if ((rc = note(h, cudaMemsetAsync(h->epsi2, 0, third, h->stream))) != FDTD_OK) return fail(rc);
     }
     if (cudaMalloc(&h->d_flags, sizeof(int)) != cudaSuccess) { cudaGetLastError(); return fail(FDTD_ERR_OOM); }
     if ((rc = note(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int), h->stream))) != FDTD_OK) return fail(rc);
@@ -232,6 +254,7 @@ int fdtd_create(fdtd_t *out, int nx, int ny, int nz, double dx, double dt, doubl
     h->watch_every = FDTD_WATCHDOG_DEFAULT_STEPS;
     h->kernel = 0;
     if (vtile_prepare(h) == FDTD_OK) h->kernel = 1;
+    tb2_prepare(h);   // available through fdtd_set_kernel(h, 2) where it applies
     cudaGetLastError();
     *out = h;
     return FDTD_OK;
@@ -305,6 +328,7 @@ int fdtd_set_probes(fdtd_t h, const double *xyz, int n, int max_steps) {
     free_dev(h->d_ijk); free_dev(h->d_cxy); free_dev(h->d_trace);
     h->d_ijk = nullptr; h->d_cxy = nullptr; h->d_trace = nullptr;
     h->np = 0; h->max_steps = max_steps;
+    h->probe_ver++;
     h->h_ijk.clear();
     if (n == 0) return FDTD_OK;
     size_t tb = sizeof(float) * 2 * (size_t)n * (size_t)(max_steps > 0 ? max_steps : 1);
@@ -412,6 +436,8 @@ int fdtd_reset(fdtd_t h) {
     if (!h) return FDTD_ERR_ARG;
     for (int s = 0; s < 2; ++s) TRY(h, cudaMemsetAsync(h->fields[s], 0, field_bytes(h), h->stream));
     if (h->psi_block) TRY(h, cudaMemsetAsync(h->psi_block, 0, h->psi_floats * sizeof(float), h->stream));
+    if (h->epsi2) TRY(h, cudaMemsetAsync(h->epsi2, 0, h->psi_floats / 3 * sizeof(float), h->stream));
+    h->ecur = 0;
     if (h->d_trace)
         TRY(h, cudaMemsetAsync(h->d_trace, 0, sizeof(float) * 2 * (size_t)h->np * h->max_steps, h->stream));
     h->cur = 0;
@@ -473,7 +499,7 @@ int fdtd_save_state(fdtd_t h, void *buf, size_t *bytes) {
     TRY(h, cudaMemcpy(p, h->fields[h->cur], hd.field_bytes, cudaMemcpyDeviceToHost)); p += hd.field_bytes;
     if (hd.psi_bytes) {
         const size_t third = h->psi_floats / 3 * sizeof(float);
-        TRY(h, cudaMemcpy(p, h->psi_block, third, cudaMemcpyDeviceToHost));
+        TRY(h, cudaMemcpy(p, h->ecur ? h->epsi2 : h->psi_block, third, cudaMemcpyDeviceToHost));
         TRY(h, cudaMemcpy(p + third, (char *)h->psi_block + third * (1 + h->cur), third, cudaMemcpyDeviceToHost));
         p += hd.psi_bytes;
     }
@@ -499,6 +525,7 @@ int fdtd_load_state(fdtd_t h, const void *buf, size_t bytes) {
     if (hd.psi_bytes) {
         const size_t third = h->psi_floats / 3 * sizeof(float);
         TRY(h, cudaMemcpy(h->psi_block, p, third, cudaMemcpyHostToDevice));
+        h->ecur = 0;
         TRY(h, cudaMemcpy((char *)h->psi_block + third * (1 + h->cur), p + third, third, cudaMemcpyHostToDevice));
         p += hd.psi_bytes;
     }
@@ -542,7 +569,7 @@ int fdtd_timing_end(fdtd_t h, double *total_ms, int *launches) {
 int fdtd_timed_cells(fdtd_t h, int64_t *cells) {
     if (!h || !cells) return FDTD_ERR_ARG;
     const Grid &g = h->g;
-    *cells = (int64_t)g.nx * g.ny * g.nz;
+    *cells = (int64_t)g.nx * g.ny * g.nz * (h->kernel == 2 ? 2 : 1);
     return FDTD_OK;
 }
 
@@ -554,6 +581,7 @@ int fdtd_launch_count(fdtd_t h, int64_t *launches) {
 
 const char *fdtd_kernel_name(fdtd_t h) {
     if (h && h->kernel == 1) return vtile_name();
+    if (h && h->kernel == 2) return tb2_name();
     return "unfused-h-then-e";
 }
 
@@ -564,8 +592,8 @@ int fdtd_set_watchdog(fdtd_t h, int every) {
 }
 
 int fdtd_set_kernel(fdtd_t h, int which) {
-    if (!h || which < 0 || which > 1) return FDTD_ERR_ARG;
-    if (which == 1 && !h->vtile) return FDTD_ERR_ARG;
+    if (!h || which < 0 || which > 2) return FDTD_ERR_ARG;
+    if ((which == 1 && !h->vtile) || (which == 2 && !h->tb2)) return FDTD_ERR_ARG;
     h->kernel = which;
     return FDTD_OK;
 }

@@ -19,6 +19,9 @@
 // psi are updated in place by the one thread that owns the cell; the H-update
 // psi are ping-ponged like the fields, because a tile of the fused kernel
 // recomputes its neighbours' halo H and must read their psi before the update.
+// The two-step kernel recomputes halo E as well, so it reads the E psi of one
+// set and writes the other: there are two E psi sets, and `ecur` names the one
+// holding the current values (the one-step paths update it in place).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -133,11 +136,15 @@ struct fdtd_ctx {
     // CPML
     float *psi_block;         // E psi, then two sets of H psi (one allocation)
     size_t psi_floats;        // total floats of psi_block
+    float *epsi2;             // second E psi set (psi_floats / 3 floats)
+    int ecur;                 // E psi set holding the current values (0: psi_block)
     size_t psi_axis[3];       // floats of one psi array of each axis
     float *coef_block;        // aE,bE,aH,bH per axis
     const float *aE[3], *bE[3], *aH[3], *bH[3];
-    int kernel;               // field-update path: 0 unfused sweeps, 1 vector tile
+    int kernel;               // field-update path: 0 unfused sweeps, 1 vector tile,
+                              // 2 two steps per pass (vector tile for a last odd step)
     void *vtile;              // host state of the vector-tile path
+    void *tb2;                // host state of the two-step path
     int *d_flags;             // device error flags (bits 0-1: a bounded wait gave up,
                               // bit 2: the watchdog saw a non-finite value)
     int watch_every;          // steps between watchdog checks (0: off)
@@ -154,6 +161,7 @@ struct fdtd_ctx {
     float *d_cxy;
     float *d_trace;
     std::vector<int> h_ijk;
+    int probe_ver;            // bumped by every fdtd_set_probes
 
     // energy / stability scratch
     double *d_partial;        // per-block partial sums
@@ -194,6 +202,15 @@ void launch_vtile(fdtd_ctx *h, cudaStream_t s);
 int fdtd_step_on(fdtd_ctx *h, int n, cudaStream_t st);
 const char *vtile_name();
 void vtile_release(fdtd_ctx *h);
+
+// Two leapfrog steps per pass (temporal blocking, kernels_tb2.cu): tiles of
+// 120 owned columns by 8 rows recompute a 2-cell halo of the first step
+int tb2_prepare(fdtd_ctx *h);
+void launch_tb2(fdtd_ctx *h, cudaStream_t s);          // steps n, n+1
+void launch_tb2_probes(fdtd_ctx *h, cudaStream_t s);   // detector slots n, n+1 after launch_tb2
+const char *tb2_name();
+void tb2_release(fdtd_ctx *h);
+float *tb2_probe_values(fdtd_ctx *h);   // the pass's records of E^{n+1} (6 per detector)
 
 // host tables (tables.cpp)
 void cpml_coefficients(int n, int P, double dx, double dt, double eps_r, float *aE, float *bE,

@@ -71,25 +71,57 @@ void launch_mur(const fdtd_ctx *h, cudaStream_t s) {
     k_mur<<<grd, blk, 0, s>>>(g, h->fields[h->cur], h->fields[h->cur ^ 1], (float)h->mur_m);
 }
 
-// Detector readout of E^{n+1} (set cur^1) into trace slot n.
-__global__ void k_probes(Grid g, const float *__restrict__ E, Probes p, long long slot) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= p.n) return;
-    int i = p.ijk[3 * t], j = p.ijk[3 * t + 1], k = p.ijk[3 * t + 2];
-    long long c = gidx(g, i, j, k);
-    const float *Ex = E, *Ey = E + g.comp, *Ez = E + 2 * g.comp;
-    float ex = 0.5f * (Ex[c - 1] + Ex[c]);
-    float ey = 0.5f * (Ey[c - g.pitch] + Ey[c]);
-    float ez = 0.5f * (Ez[c - g.plane] + Ez[c]);
+// Readout of detector t into trace slot `slot` from the six E values around
+// its node: Ex at i-1, i; Ey at j-1, j; Ez at k-1, k (node averages); E_r
+// about the shower axis.
+__device__ __forceinline__ void readout(const Probes &p, int t, long long slot, const float *v) {
+    float ex = 0.5f * (v[0] + v[1]);
+    float ey = 0.5f * (v[2] + v[3]);
+    float ez = 0.5f * (v[4] + v[5]);
     float er = p.cxy[2 * t] * ex + p.cxy[2 * t + 1] * ey;
     float *o = p.trace + ((long long)t * p.max_steps + slot) * 2;
     o[0] = ez;
     o[1] = er;
 }
 
+__device__ __forceinline__ void readout_fields(const Grid &g, const float *E, const Probes &p, int t,
+                                               long long slot) {
+    const int i = p.ijk[3 * t], j = p.ijk[3 * t + 1], k = p.ijk[3 * t + 2];
+    const long long c = gidx(g, i, j, k);
+    const float *Ex = E, *Ey = E + g.comp, *Ez = E + 2 * g.comp;
+    const float v[6] = {Ex[c - 1], Ex[c], Ey[c - g.pitch], Ey[c], Ez[c - g.plane], Ez[c]};
+    readout(p, t, slot, v);
+}
+
+// Detector readout of E^{n+1} (set cur^1) into trace slot n.
+__global__ void k_probes(Grid g, const float *__restrict__ E, Probes p, long long slot) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= p.n) return;
+    readout_fields(g, E, p, t, slot);
+}
+
+// After a two-step pass: slot n from the pass's records of E^{n+1} (six
+// values per detector), slot n+1 from E^{n+2} (set cur^1).
+__global__ void k_probes2(Grid g, const float *__restrict__ E, Probes p, long long slot,
+                          const float *__restrict__ rec) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= p.n) return;
+    float v[6];
+    for (int s = 0; s < 6; ++s) v[s] = rec[6 * t + s];
+    readout(p, t, slot, v);
+    readout_fields(g, E, p, t, slot + 1);
+}
+
 void launch_probes(const fdtd_ctx *h, cudaStream_t s) {
     Probes p{h->np, h->max_steps, h->d_ijk, h->d_cxy, h->d_trace};
     k_probes<<<(h->np + 127) / 128, 128, 0, s>>>(h->g, h->fields[h->cur ^ 1], p, h->steps);
+}
+
+void launch_tb2_probes(fdtd_ctx *h, cudaStream_t s) {
+    Probes p{h->np, h->max_steps, h->d_ijk, h->d_cxy, h->d_trace};
+    const float *rec = tb2_probe_values(h);
+    if (!rec) return;
+    k_probes2<<<(h->np + 127) / 128, 128, 0, s>>>(h->g, h->fields[h->cur ^ 1], p, h->steps, rec);
 }
 
 // Watchdog of the step path: block (x, y) scans plane k = min(y * stride,

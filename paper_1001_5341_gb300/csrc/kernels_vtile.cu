@@ -66,9 +66,12 @@
 
 #include "fdtd_internal.h"
 #include "source_term.cuh"
+#include "tma_pipe.cuh"
 
 namespace fdtd {
 namespace {
+
+using namespace tma;
 
 #ifndef VT_BY
 #define VT_BY 8
@@ -127,7 +130,7 @@ __host__ __device__ constexpr int head_floats(int zc) { return (2 * HSB + CZ + 4
 
 struct Maps {
     CUtensorMap f[2][6];    // fields [set][component]
-    CUtensorMap x[4][2];    // psi x: xHy, xHz (H, [set]) then xEy, xEz (E, one map)
+    CUtensorMap x[4][2];    // psi x: xHy, xHz (H, [field set]) then xEy, xEz (E, [E psi set])
     CUtensorMap y[4][2];    // psi y: yHx, yHz, yEx, yEz
     CUtensorMap z[4][2];    // psi z: zHx, zHy, zEx, zEy
 };
@@ -142,92 +145,12 @@ struct Args {
     int ring;                                   // floats available to the stage ring
     int xlo4, xhb, xbw;                         // x psi: high half start, first column of the high
                                                 // half, box width
-    int cur;
+    int cur, ecur;                              // field set read; E psi set (updated in place)
     Source src;
     SourceStep ss;
     float kE, kH;
     int *flags;
 };
-
-__device__ __forceinline__ uint32_t sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(sa(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded: gives up after about two seconds of clock cycles
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > (4LL << 30)) return false;
-    return true;
-}
-__device__ __forceinline__ void tma_load(float *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(sa(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(sa(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ float4 lds4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
-__device__ __forceinline__ void sts4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
-
-__device__ __forceinline__ float4 operator-(float4 a, float4 b) {
-    return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
-}
-// a + s * d, elementwise
-__device__ __forceinline__ float4 axpy(float4 a, float s, float4 d) {
-    return make_float4(a.x + s * d.x, a.y + s * d.y, a.z + s * d.z, a.w + s * d.w);
-}
-
-// CPML recursion psi <- b psi + a d; the derivative becomes d + psi
-__device__ __forceinline__ float cpml1(float &psi, float a, float b, float d) {
-    psi = b * psi + a * d;
-    return d + psi;
-}
-__device__ __forceinline__ float4 cpml4(float4 &psi, float a, float b, float4 d) {
-    return make_float4(cpml1(psi.x, a, b, d.x), cpml1(psi.y, a, b, d.y), cpml1(psi.z, a, b, d.z),
-                       cpml1(psi.w, a, b, d.w));
-}
-
-// elementwise coefficients
-__device__ __forceinline__ float4 cpmlv(float4 &psi, float4 a, float4 b, float4 d) {
-    return make_float4(cpml1(psi.x, a.x, b.x, d.x), cpml1(psi.y, a.y, b.y, d.y), cpml1(psi.z, a.z, b.z, d.z),
-                       cpml1(psi.w, a.w, b.w, d.w));
-}
-
-// zero the whole vector (all) or its first element (first): the components a
-// cell owns on the grid's low faces are not updated
-__device__ __forceinline__ float4 mask(float4 v, bool all, bool first) {
-    if (all) return make_float4(0.f, 0.f, 0.f, 0.f);
-    if (first) v.x = 0.f;
-    return v;
-}
-// store the first n (1..4) elements; a 16-byte store when n == 4
-__device__ __forceinline__ void st4n(float *p, float4 v, int n) {
-    if (n == 4) {
-        *reinterpret_cast<float4 *>(p) = v;
-    } else {
-        p[0] = v.x;
-        if (n > 1) p[1] = v.y;
-        if (n > 2) p[2] = v.z;
-    }
-}
 
 // stage offset of component c at box row br (row jb-1+br), box column bc
 // (column i0-4+bc)
@@ -265,13 +188,13 @@ __device__ __forceinline__ void issue_plane(const Args &A, const Maps &M, const 
     if (B.hx)
         for (int a = 0; a < 4; ++a) {
             float *d = st + B.xo + a * B.nxb * B.xb;
-            if (B.xlo >= 0) tma_load(d + B.xlo * B.xb, &M.x[a][a < 2 ? set : 0], bar, 0, B.jb - 1, z);
-            if (B.xhi >= 0) tma_load(d + B.xhi * B.xb, &M.x[a][a < 2 ? set : 0], bar, A.xlo4, B.jb - 1, z);
+            if (B.xlo >= 0) tma_load(d + B.xlo * B.xb, &M.x[a][a < 2 ? set : A.ecur], bar, 0, B.jb - 1, z);
+            if (B.xhi >= 0) tma_load(d + B.xhi * B.xb, &M.x[a][a < 2 ? set : A.ecur], bar, A.xlo4, B.jb - 1, z);
         }
     if (B.hy)
-        for (int a = 0; a < 4; ++a) tma_load(st + B.yo + a * PBOXP, &M.y[a][a < 2 ? set : 0], bar, B.i0 - 4, B.l0, z);
+        for (int a = 0; a < 4; ++a) tma_load(st + B.yo + a * PBOXP, &M.y[a][a < 2 ? set : A.ecur], bar, B.i0 - 4, B.l0, z);
     if (lz >= 0)
-        for (int a = 0; a < 4; ++a) tma_load(st + B.zo + a * PBOXP, &M.z[a][a < 2 ? set : 0], bar, B.i0 - 4, B.jb - 1, lz);
+        for (int a = 0; a < 4; ++a) tma_load(st + B.zo + a * PBOXP, &M.z[a][a < 2 ? set : A.ecur], bar, B.i0 - 4, B.jb - 1, lz);
 }
 
 // Per-lane geometry, fixed for the whole march.
@@ -719,10 +642,6 @@ __global__ void __launch_bounds__(NT, 1) k_vtile(const Args A, const __grid_cons
     }
 }
 
-typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
 struct HostState {
     Maps maps;
     int tiles_x, tiles_y, za, zb, cm, m, zc, chunks, ring;
@@ -735,17 +654,9 @@ constexpr CUtensorMapL2promotion kPromotion =
     : VT_L2PROMO == 1 ? CU_TENSOR_MAP_L2_PROMOTION_L2_64B
     : VT_L2PROMO == 2 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B : CU_TENSOR_MAP_L2_PROMOTION_L2_256B;
 
-// 3-D float32 tensor map: extents d0 (innermost) .. d2, strides s1, s2 in
-// floats, box b0 x b1 x 1
 bool encode3(EncodeTiled encode, CUtensorMap *m, const float *base, cuuint64_t d0, cuuint64_t d1, cuuint64_t d2,
              cuuint64_t s1, cuuint64_t s2, cuuint32_t b0, cuuint32_t b1) {
-    cuuint64_t dims[3] = {d0, d1, d2};
-    cuuint64_t strides[2] = {s1 * 4, s2 * 4};
-    cuuint32_t box[3] = {b0, b1, 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, kPromotion,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return tma::encode3(encode, m, base, d0, d1, d2, s1, s2, b0, b1, kPromotion);
 }
 
 }  // namespace
@@ -764,14 +675,8 @@ int vtile_prepare(fdtd_ctx *h) {
     const int WX = P > 0 ? psi_x_row(g.nx, P) : 0;
     const int xbw = P > 0 ? (xlo4 > WX - xlo4 ? xlo4 : WX - xlo4) : 4;
     if (P > 0 && (g.nx < 2 * P + 8 || xbw > 256 || g.nz < 2 * P + 2)) return FDTD_ERR_ARG;
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn) {
-        cudaGetLastError();
-        return FDTD_ERR_CUDA;
-    }
-    EncodeTiled encode = reinterpret_cast<EncodeTiled>(fn);
+    EncodeTiled encode = encoder();
+    if (!encode) return FDTD_ERR_CUDA;
     HostState *st = new (std::nothrow) HostState();
     if (!st) return FDTD_ERR_OOM;
     st->xlo4 = xlo4;
@@ -785,20 +690,20 @@ int vtile_prepare(fdtd_ctx *h) {
     if (P > 0) {
         // psi block: E psi, then H psi set 0, then H psi set 1 (each set the
         // x, y, z arrays in turn, two per axis); the H set read when cur == s
-        // is set s
+        // is set s.  The second E psi set (epsi2, same layout) is the one the
+        // two-step path leaves current every other launch.
         const size_t set = 2 * (h->psi_axis[0] + h->psi_axis[1] + h->psi_axis[2]);
         const int W = 2 * P + 1;
         for (int s = 0; s < 2; ++s) {
             size_t off = 0;
             for (int axis = 0; axis < 3; ++axis)
                 for (int t = 0; t < 2; ++t) {
-                    const float *hp = h->psi_block + set * (1 + s) + off;   // H array t of axis
-                    const float *ep = h->psi_block + off;                   // E array t of axis
+                    const float *hp = h->psi_block + set * (1 + s) + off;   // H array t of axis, field set s
+                    const float *ep = (s == 0 ? h->psi_block : h->epsi2) + off;  // E array t of axis, E set s
                     off += h->psi_axis[axis];
                     for (int half = 0; half < 2; ++half) {
                         const float *base = half == 0 ? hp : ep;
                         const int a = 2 * half + t;
-                        if (half == 1 && s == 1) continue;   // E maps: one copy
                         CUtensorMap *m = axis == 0 ? &st->maps.x[a][s] : axis == 1 ? &st->maps.y[a][s] : &st->maps.z[a][s];
                         if (axis == 0)
                             ok = ok && encode3(encode, m, base, WX, g.ny, g.nz, WX, (cuuint64_t)g.ny * WX, xbw, PR);
@@ -885,6 +790,7 @@ void launch_vtile(fdtd_ctx *h, cudaStream_t s) {
     a.xhb = st->xhb;
     a.xbw = st->xbw;
     a.cur = h->cur;
+    a.ecur = h->ecur;
     a.src = h->src;
     a.ss = source_window(h->src, h->steps);
     a.kE = (float)h->kE;
