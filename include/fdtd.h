@@ -222,13 +222,13 @@ const char *fdtd_kernel_name(fdtd_t h);
 
 /*
  * Select the field-update path (all compute the same update, Sec. III.A):
- *   1 = one pass per step: TMA-staged vector-tile z-march over the whole
- *       grid, CPML included (the default);
  *   2 = two steps per pass (temporal blocking of the leapfrog): each tile
  *       recomputes the first step on a two-cell halo, so a pass reads the
  *       fields once and writes them once for two steps; CPML and detectors
  *       included; a last odd step of fdtd_step runs on path 1.  PEC and CPML
- *       grids only (FDTD_ERR_ARG on a Mur grid);
+ *       grids only (FDTD_ERR_ARG on a Mur grid); the default there;
+ *   1 = one pass per step: TMA-staged vector-tile z-march over the whole
+ *       grid, CPML included (the default on Mur grids);
  *   0 = one H sweep then one E sweep (the reference path: the batched
  *       persistent kernel and the adjoint use its per-cell code).
  * Returns FDTD_ERR_ARG for a path the handle cannot run.

@@ -249,12 +249,13 @@ int fdtd_create(fdtd_t *out, int nx, int ny, int nz, double dx, double dt, doubl
         return fail(FDTD_ERR_OOM);
     }
     if ((rc = note(h, cudaStreamSynchronize(h->stream))) != FDTD_OK) return fail(rc);
-    // the vector-tile z-march is the default field-update path; the others
-    // stay available (fdtd_set_kernel) as cross-checks
+    // default field-update path: two steps per pass where it applies (PEC and
+    // CPML grids), else the one-step vector-tile z-march; the others stay
+    // available (fdtd_set_kernel) as cross-checks
     h->watch_every = FDTD_WATCHDOG_DEFAULT_STEPS;
     h->kernel = 0;
     if (vtile_prepare(h) == FDTD_OK) h->kernel = 1;
-    tb2_prepare(h);   // available through fdtd_set_kernel(h, 2) where it applies
+    if (tb2_prepare(h) == FDTD_OK) h->kernel = 2;
     cudaGetLastError();
     *out = h;
     return FDTD_OK;

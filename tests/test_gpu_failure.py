@@ -34,7 +34,7 @@ def _plant(sim, comp, ijk):
     sim.set_field(comp, f)
 
 
-@pytest.mark.parametrize("kernel", [None, 0])
+@pytest.mark.parametrize("kernel", [None, 1, 0])
 @pytest.mark.parametrize("boundary", ["cpml", "mur"])
 def test_watchdog_reports_planted_nan(fd, boundary, kernel):
     if boundary == "cpml":

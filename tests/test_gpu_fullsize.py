@@ -35,18 +35,21 @@ def _gh():
     return W.gh640(steps=N_STEPS, spread_m=1.0)
 
 
-@pytest.fixture(scope="module", params=[_greisen, _gh], ids=["greisen384", "gh640"])
+@pytest.fixture(scope="module", params=[(_greisen, None), (_gh, None), (_greisen, 1), (_gh, 1)],
+                ids=["greisen384", "gh640", "greisen384-onestep", "gh640-onestep"])
 def full(request):
     import torch
     torch.cuda.set_device(0)
     import paper_1001_5341_gb300 as fd
-    w = request.param()
+    make, kernel = request.param
+    w = make()
     ax = (w.nx // 2) * w.dx
     near = np.array([[ax + 0.24, ax, 0.46], [ax, ax - 0.32, 0.62], [ax + 0.2, ax + 0.2, 0.90],
                      [ax - 0.5, ax + 0.1, 0.70]])
     w.probes_xyz = np.vstack([w.probes_xyz, near])
-    sim = fd.Simulation.from_workload(w)
-    assert sim.kernel_name == "fused-vtile-128x8"     # the benchmark's launch configuration
+    sim = fd.Simulation.from_workload(w, kernel=kernel)
+    # the benchmark's launch configuration (the default path), and the one-step path
+    assert sim.kernel_name == ("tblock2-120x8" if kernel is None else "fused-vtile-128x8")
     sim.step(N_STEPS)
     sim.sync()
     yield fd, w, sim, torch

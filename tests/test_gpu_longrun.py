@@ -95,7 +95,7 @@ def _run(make, kernel):
     return w, tg, ref.probes(), e_half, e_end, name, t_ref
 
 
-@pytest.mark.parametrize("kernel", [None], ids=["default"])
+@pytest.mark.parametrize("kernel", [None, 1], ids=["default", "onestep"])
 @pytest.mark.parametrize("make", [_greisen_long, _gh_long], ids=["greisen128x128x1536", "gh112x112x2048"])
 def test_parity_at_benchmarked_step_count(make, kernel):
     w, tg, to, e_half, e_end, name, t_ref = _run(make, kernel)
