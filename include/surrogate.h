@@ -11,7 +11,9 @@
  * response depend on the offset between antenna and bin only: the learned
  * counterpart of the Green's function superposition of Sec. II).  These calls
  * are the forward and backward kernels and the optimiser step; the 1D
- * convolutions are general-purpose kernels of the same family.
+ * convolutions are general-purpose kernels of the same family.  The lattice
+ * model (sur_lattice_*, at the end) replaces the MLP by a learned response
+ * table on the grid's own lattice, where the shift invariance is exact.
  *
  * Conventions
  *   - All tensors are device buffers owned by the caller; the calls allocate
@@ -143,6 +145,49 @@ int sur_assemble(const float *G, const float *qn, const float *rz, int B, int K,
  */
 int sur_assemble_bwd(const float *dout, const float *qn, const float *rz, int B, int K, int Tg, int shift, int T,
                      float z0, float dz, float cps, int J0, float *dG, void *dGb, void *stream);
+
+/*
+ * Lattice surrogate.  With the shower moving half a cell per step (c dt =
+ * dx/2) and profile bins of 2S steps (S trace samples of two steps each, S
+ * cells), the field of bin k at an antenna is the field of bin 0 at the
+ * antenna moved S k cells back along z, S k samples earlier: the scheme and
+ * the charge-conserving deposit commute with that translation of the grid's
+ * lattice (Sec. III.A, III.B).  A trace is linear in the profile.  So, for
+ * antennas on the lattice of radial class ir (a node distance from the axis
+ * in the plane phi = 0) and axial index m (the antenna at the start of bin m),
+ *   y[b][t] = sum_k q[b][k] G[ir][m - k + moff][t - S k + J]
+ *                                   (terms with 0 <= t - S k + J < T),
+ * where G[ir][d][tau] (NR x D x T, bf16) is the learned response of one bin
+ * at lattice offset d - moff and J >= 0 lead samples (with the profile
+ * interpolated linearly between bins, bin k's charge starts to move when the
+ * shower passes bin k-1: J = S).  The weights of an antenna form a K x T
+ * matrix, W[k][t] = G[ir][m - k + moff][t - S k + J], so a batch of profiles at one
+ * antenna is a tensor-core GEMM (sur_lattice_weights, then sur_gemm_bf16).
+ *   G: bf16 [NR][D][T];  q: f32 [B][K] (K <= 1024);  ant: int [B][2] = (ir, m);
+ *   y: f32 [B][T] (overwritten);  dG: f32 [NR][D][T] (accumulated: clear it
+ *   first);  offsets outside 0..D-1 and classes outside 0..NR-1 contribute 0.
+ * sur_lattice_fwd:  y as above (f32 accumulation) from the bf16 table G, plus
+ *                   a second bf16 table Glo of the remainders if not NULL
+ *                   (G + Glo carries about 16 significant bits, see
+ *                   sur_split_bf16).
+ * sur_lattice_fwd_f32: the same from an f32 table (the training master).
+ * sur_lattice_bwd:  dG[ir][m - k + moff][tau] += q[b][k] dy[b][tau + S k - J]
+ *                   (the exact transpose of the forward map, atomic adds).
+ * sur_lattice_weights: W (bf16 [A][K][T]) of A antennas ant[A][2].
+ * B, A <= 65535.
+ */
+int sur_lattice_fwd(const void *G, const void *Glo, const float *q, const int *ant, int B, int K, int NR, int D,
+                    int T, int S, int J, int moff, float *y, void *stream);
+int sur_lattice_fwd_f32(const float *G, const float *q, const int *ant, int B, int K, int NR, int D, int T, int S,
+                        int J, int moff, float *y, void *stream);
+/* hi[i] = bf16(x[i]), lo[i] = bf16(x[i] - hi[i]), i < n: x = hi + lo to about
+   2^-17 relative, so products of split operands on the bf16 tensor cores
+   (hi hi + hi lo + lo hi, f32 accumulation) carry nearly f32 precision. */
+int sur_split_bf16(const float *x, void *hi, void *lo, long long n, void *stream);
+int sur_lattice_bwd(const float *dy, const float *q, const int *ant, int B, int K, int NR, int D, int T, int S,
+                    int J, int moff, float *dG, void *stream);
+int sur_lattice_weights(const void *G, const int *ant, int A, int K, int NR, int D, int T, int S, int J, int moff,
+                        void *W, void *stream);
 
 #ifdef __cplusplus
 }

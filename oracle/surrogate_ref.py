@@ -218,3 +218,71 @@ def adam(w, gr, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     v = b2 * v + (1 - b2) * gr * gr
     w = w - lr * (m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps)
     return w, m, v
+
+
+# ---- lattice surrogate ----------------------------------------------------------
+#
+# With the shower moving half a cell per step and bins of 2S steps (S trace
+# samples of two steps), the field of bin k at an antenna equals the field of
+# bin 0 at the antenna moved S k cells back along z, S k samples earlier (the
+# exact translation property pinned in tests/test_oracle_source.py).  The
+# trace is linear in the profile, so for an antenna of radial class ir at the
+# start of bin m:
+#     y[t] = sum_k q[k] G[ir][m - k + moff][t - S k + J]   (0 <= t - S k + J < T),
+# with G the learned response of one bin and J lead samples.  Plain loops
+# over the definition.
+
+def lattice_forward(G, q, ant, S, J, moff):
+    """y [B][T] from G [NR][D][T] (values as stored), q [B][K], ant [B][2]."""
+    NR, D, T = G.shape
+    B, K = q.shape
+    y = np.zeros((B, T))
+    for b in range(B):
+        ir, m = int(ant[b][0]), int(ant[b][1])
+        if not 0 <= ir < NR:
+            continue
+        for k in range(K):
+            d = m - k + moff
+            if not 0 <= d < D:
+                continue
+            for t in range(T):
+                tau = t - S * k + J
+                if 0 <= tau < T:
+                    y[b, t] += q[b, k] * G[ir, d, tau]
+    return y
+
+
+def lattice_grad(dy, q, ant, S, J, moff, shape):
+    """dL/dG [NR][D][T] for dL/dy = dy [B][T]: the transpose of lattice_forward."""
+    NR, D, T = shape
+    B, K = q.shape
+    g = np.zeros(shape)
+    for b in range(B):
+        ir, m = int(ant[b][0]), int(ant[b][1])
+        if not 0 <= ir < NR:
+            continue
+        for k in range(K):
+            d = m - k + moff
+            if not 0 <= d < D:
+                continue
+            for t in range(T):
+                tau = t - S * k + J
+                if 0 <= tau < T:
+                    g[ir, d, tau] += q[b, k] * dy[b, t]
+    return g
+
+
+def lattice_weights(G, ant, K, S, J, moff):
+    """W [A][K][T]: W[a][k][t] = G[ir][m - k + moff][t - S k + J] (0 elsewhere)."""
+    NR, D, T = G.shape
+    W = np.zeros((len(ant), K, T))
+    for a, (ir, m) in enumerate(ant):
+        for k in range(K):
+            d = int(m) - k + moff
+            if not (0 <= int(ir) < NR and 0 <= d < D):
+                continue
+            for t in range(T):
+                tau = t - S * k + J
+                if 0 <= tau < T:
+                    W[a, k, t] = G[int(ir), d, tau]
+    return W

@@ -84,6 +84,11 @@ _SIGS = {
     "sur_assemble": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, C.c_float, C.c_float, C.c_float, _i, _vp, _vp]),
     "sur_assemble_bwd": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, C.c_float, C.c_float, C.c_float, _i, _vp, _vp,
                               _vp]),
+    "sur_lattice_fwd": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _vp, _vp]),
+    "sur_lattice_fwd_f32": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _vp, _vp]),
+    "sur_split_bf16": (_i, [_vp, _vp, _vp, C.c_longlong, _vp]),
+    "sur_lattice_bwd": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _vp, _vp]),
+    "sur_lattice_weights": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _vp, _vp]),
     # batched persistent stepping (batch.h)
     "fdtd_batch_create": (_i, [C.POINTER(_vp), C.POINTER(_vp), _i]),
     "fdtd_batch_destroy": (None, [_vp]),

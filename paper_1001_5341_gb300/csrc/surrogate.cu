@@ -387,6 +387,87 @@ int grid_for(long long n, int threads) {
     return (int)(b < 1 ? 1 : b);
 }
 
+// ---- lattice surrogate: bin responses on the grid's own lattice ----------------
+// G[(ir * D + d) * T + tau] (bf16): response of antenna radial class ir to a
+// unit profile bin at axial lattice offset d - moff (bins), tau samples after
+// the bin's own time origin.  Antenna b has class ant[2b] and axial lattice
+// index ant[2b+1]; bin k's offset is m - k, its time origin S k - J samples
+// (J lead samples: the bin's charge starts to move one bin early).
+
+__device__ __forceinline__ float val(const bf16raw v) { return bf(v); }
+__device__ __forceinline__ float val(const float v) { return v; }
+
+// Tab: bf16raw (with an optional second bf16 table Glo of the remainders) or float
+template <typename Tab>
+__global__ void __launch_bounds__(256) k_lat_fwd(const Tab *__restrict__ G, const bf16raw *__restrict__ Glo,
+                                                 const float *__restrict__ q, const int *__restrict__ ant, int K,
+                                                 int NR, int D, int T, int S, int J, int moff,
+                                                 float *__restrict__ y) {
+    __shared__ float qs[1024];
+    const int b = blockIdx.y;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) qs[k] = q[(long long)b * K + k];
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const int ir = ant[2 * b], m = ant[2 * b + 1];
+    float acc = 0.f;
+    if (ir >= 0 && ir < NR) {
+        const long long base = (long long)ir * D * T;
+        for (int k = 0; k < K && S * k - J <= t; ++k) {
+            const int d = m - k + moff, tau = t - S * k + J;
+            if (d >= 0 && d < D && tau < T && qs[k] != 0.f) {
+                const long long i = base + (long long)d * T + tau;
+                float gv = val(G[i]);
+                if (Glo) gv += bf(Glo[i]);
+                acc += qs[k] * gv;
+            }
+        }
+    }
+    y[(long long)b * T + t] = acc;
+}
+
+__global__ void __launch_bounds__(256) k_lat_bwd(const float *__restrict__ dy, const float *__restrict__ q,
+                                                 const int *__restrict__ ant, int K, int NR, int D, int T, int S,
+                                                 int J, int moff, float *__restrict__ dG) {
+    __shared__ float qs[1024];
+    const int b = blockIdx.y;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) qs[k] = q[(long long)b * K + k];
+    __syncthreads();
+    const int tau = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tau >= T) return;
+    const int ir = ant[2 * b], m = ant[2 * b + 1];
+    if (ir < 0 || ir >= NR) return;
+    float *g = dG + (long long)ir * D * T;
+    const float *r = dy + (long long)b * T;
+    for (int k = 0; k < K && tau + S * k - J < T; ++k) {
+        const int d = m - k + moff, t = tau + S * k - J;
+        if (d >= 0 && d < D && t >= 0 && qs[k] != 0.f) atomicAdd(&g[(long long)d * T + tau], qs[k] * r[t]);
+    }
+}
+
+// hi = bf16(x), lo = bf16(x - hi): x = hi + lo to about 2^-17 relative
+__global__ void k_split_bf16(const float *__restrict__ x, bf16raw *__restrict__ hi, bf16raw *__restrict__ lo,
+                             long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const bf16raw h = tobf(x[i]);
+        hi[i] = h;
+        lo[i] = tobf(x[i] - bf(h));
+    }
+}
+
+// W[a][k][t] = G[ir_a][m_a - k + moff][t - S k + J] (0 where that time or the
+// offset is off the table): antenna a's weights, a K x T matrix, for the GEMM
+__global__ void k_lat_weights(const bf16raw *__restrict__ G, const int *__restrict__ ant, int K, int NR, int D,
+                              int T, int S, int J, int moff, bf16raw *__restrict__ W) {
+    const int a = blockIdx.z, k = blockIdx.y;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const int ir = ant[2 * a], d = ant[2 * a + 1] - k + moff, tau = t - S * k + J;
+    bf16raw v = 0;
+    if (ir >= 0 && ir < NR && d >= 0 && d < D && tau >= 0 && tau < T) v = G[((long long)ir * D + d) * T + tau];
+    W[((long long)a * K + k) * T + t] = v;
+}
+
 }  // namespace
 
 extern "C" {
@@ -528,6 +609,52 @@ int sur_assemble_bwd(const float *dout, const float *qn, const float *rz, int B,
         return FDTD_ERR_ARG;
     k_assemble_bwd<<<grid_for((long long)B * K * Tg, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         dout, qn, rz, B, K, Tg, shift, T, z0, dz, cps, J0, dG, static_cast<bf16raw *>(dGb));
+    return launched();
+}
+
+int sur_lattice_fwd(const void *G, const void *Glo, const float *q, const int *ant, int B, int K, int NR, int D,
+                    int T, int S, int J, int moff, float *y, void *stream) {
+    if (!G || !q || !ant || !y || B < 1 || B > 65535 || K < 1 || K > 1024 || NR < 1 || D < 1 || T < 1 || S < 0 ||
+        J < 0)
+        return FDTD_ERR_ARG;
+    k_lat_fwd<bf16raw><<<dim3((T + 255) / 256, B), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const bf16raw *>(G), static_cast<const bf16raw *>(Glo), q, ant, K, NR, D, T, S, J, moff, y);
+    return launched();
+}
+
+int sur_lattice_fwd_f32(const float *G, const float *q, const int *ant, int B, int K, int NR, int D, int T, int S,
+                        int J, int moff, float *y, void *stream) {
+    if (!G || !q || !ant || !y || B < 1 || B > 65535 || K < 1 || K > 1024 || NR < 1 || D < 1 || T < 1 || S < 0 ||
+        J < 0)
+        return FDTD_ERR_ARG;
+    k_lat_fwd<float><<<dim3((T + 255) / 256, B), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        G, nullptr, q, ant, K, NR, D, T, S, J, moff, y);
+    return launched();
+}
+
+int sur_split_bf16(const float *x, void *hi, void *lo, long long n, void *stream) {
+    if (!x || !hi || !lo || n < 1) return FDTD_ERR_ARG;
+    k_split_bf16<<<grid_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        x, static_cast<bf16raw *>(hi), static_cast<bf16raw *>(lo), n);
+    return launched();
+}
+
+int sur_lattice_bwd(const float *dy, const float *q, const int *ant, int B, int K, int NR, int D, int T, int S,
+                    int J, int moff, float *dG, void *stream) {
+    if (!dy || !q || !ant || !dG || B < 1 || B > 65535 || K < 1 || K > 1024 || NR < 1 || D < 1 || T < 1 || S < 0 ||
+        J < 0)
+        return FDTD_ERR_ARG;
+    k_lat_bwd<<<dim3((T + 255) / 256, B), 256, 0, static_cast<cudaStream_t>(stream)>>>(dy, q, ant, K, NR, D, T, S,
+                                                                                         J, moff, dG);
+    return launched();
+}
+
+int sur_lattice_weights(const void *G, const int *ant, int A, int K, int NR, int D, int T, int S, int J, int moff,
+                        void *W, void *stream) {
+    if (!G || !ant || !W || A < 1 || A > 65535 || K < 1 || K > 65535 || NR < 1 || D < 1 || T < 1 || S < 0 || J < 0)
+        return FDTD_ERR_ARG;
+    k_lat_weights<<<dim3((T + 255) / 256, K, A), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const bf16raw *>(G), ant, K, NR, D, T, S, J, moff, static_cast<bf16raw *>(W));
     return launched();
 }
 

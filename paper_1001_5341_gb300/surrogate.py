@@ -34,8 +34,9 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import (check, fdtd_probes, profile_gaisser_hillas, lateral_nkg, Simulation, sur_adam, sur_antenna_features,
-               sur_assemble, sur_assemble_bwd, sur_bias_grad, sur_cast_bf16, sur_gemm_bf16, sur_mse,
-               sur_normalize_rows, sur_pairs, sur_relu_bwd, sur_scale_rows)
+               sur_assemble, sur_assemble_bwd, sur_bias_grad, sur_cast_bf16, sur_gemm_bf16, sur_lattice_bwd,
+               sur_lattice_fwd, sur_lattice_fwd_f32, sur_lattice_weights, sur_mse, sur_normalize_rows, sur_pairs,
+               sur_relu_bwd, sur_scale_rows, sur_split_bf16)
 
 N_FEAT = 64
 
@@ -267,3 +268,248 @@ def rel_l2(pred, ref):
     pred = np.asarray(pred, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
     return np.linalg.norm(pred - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-300)
+
+
+# ---- lattice surrogate --------------------------------------------------------
+#
+# The lattice model drops the retarded-time interpolation of `Net`: on the grid
+# of workloads.surrogate_lattice_grid (c dt = dx/2, bins of 4 cells = 8 steps)
+# the field of bin k at an antenna is exactly the field of bin 0 at the antenna
+# moved 4k cells back, 4k samples (8k steps) earlier.  For antennas on the
+# lattice of workloads.surrogate_lattice_antennas (radial class ir, bin index
+# m) the model is therefore
+#     trace[t] = peak|q| c_out sum_k qn_k G[ir][m - k + moff][t - S k + J],
+# (J = S lead samples: with the profile interpolated linearly between bins,
+# bin k's charge starts to move one bin early), linear in the normalised
+# profile, with the table G (radial class x axial
+# lattice offset x time) learned by Adam from FDTD traces of random showers
+# through the library's kernels (f32 master: sur_lattice_fwd_f32 / _bwd /
+# sur_adam).  The weights served are bf16: the table split into a bf16 part
+# and a bf16 remainder (sur_split_bf16), so that sums with cancellation keep
+# nearly f32 precision.  Inference for a batch of profiles at one antenna is
+# one tensor-core GEMM with split operands ([q_hi, q_hi, q_lo] times
+# [W_hi; W_lo; W_hi], f32 accumulation) against the antenna's weight matrix.
+# Antennas off the lattice, or outside its range, go to FDTD.
+
+@dataclass
+class LatticeGeometry:
+    K: int = 128        # profile bins
+    NR: int = 31        # radial classes
+    m_lo: int = 3       # axial lattice index range of the antennas
+    m_hi: int = 115
+    T: int = 1024       # trace samples (every second step)
+    S: int = 4          # samples between the passages of consecutive bins
+    J: int = 4          # lead samples of a bin's response (one bin)
+
+    @classmethod
+    def of(cls, grid, ir, m, decim: int = 2):
+        cells = int(round(grid.bin_dz / grid.dx))
+        steps_per_bin = int(round(grid.bin_dz / (grid.v * grid.dt)))
+        assert steps_per_bin % decim == 0
+        return cls(K=grid.n_bins, NR=int(ir.max()) + 1, m_lo=int(m.min()), m_hi=int(m.max()),
+                   T=grid.steps // decim, S=steps_per_bin // decim, J=steps_per_bin // decim)
+
+
+class Lattice:
+    """The learned bin-response table (f32 master, bf16 copy, gradient, Adam
+    moments) on the current CUDA device."""
+
+    def __init__(self, geo: LatticeGeometry, c_out: float = 1.0):
+        import torch
+        self.geo = geo
+        self.c_out = float(c_out)
+        self.t = 0
+        shp = (geo.NR, self.D, geo.T)
+        z = lambda dt=torch.float32: torch.zeros(shp, dtype=dt, device="cuda")
+        self.G, self.dG, self.m, self.v = z(), z(), z(), z()
+        self.Ghi, self.Glo = z(torch.bfloat16), z(torch.bfloat16)   # the bf16 weights served
+        self._split = False
+        self._ws = {}
+
+    @property
+    def D(self) -> int:
+        # offsets m - k for m in [m_lo, m_hi], k in [0, K): index m - k + moff
+        return self.geo.m_hi - self.geo.m_lo + self.geo.K
+
+    @property
+    def moff(self) -> int:
+        return self.geo.K - 1 - self.geo.m_lo
+
+    @property
+    def n_params(self) -> int:
+        return self.G.numel()
+
+    def _w(self, B):
+        import torch
+        if B not in self._ws:
+            e = lambda *sh: torch.empty(sh, dtype=torch.float32, device="cuda")
+            self._ws = {B: {"qn": e(B, self.geo.K), "s": e(B), "y": e(B, self.geo.T), "tn": e(B, self.geo.T),
+                            "dy": e(B, self.geo.T), "loss": e(1)}}
+        return self._ws[B]
+
+    def split(self):
+        """The bf16 weights (part and remainder) from the f32 master."""
+        check(sur_split_bf16(_p(self.G), _p(self.Ghi), _p(self.Glo), self.G.numel(), _stream()), "sur_split_bf16")
+        self._split = True
+
+    def _fwd(self, q, ant, scale_out, master=False):
+        g = self.geo
+        B = q.shape[0]
+        w = self._w(B)
+        st = _stream()
+        check(sur_normalize_rows(_p(q), B, g.K, _p(w["qn"]), _p(w["s"]), st), "sur_normalize_rows")
+        if master:
+            check(sur_lattice_fwd_f32(_p(self.G), _p(w["qn"]), _p(ant), B, g.K, g.NR, self.D, g.T, g.S, g.J,
+                                      self.moff, _p(w["y"]), st), "sur_lattice_fwd_f32")
+        else:
+            if not self._split:
+                self.split()
+            check(sur_lattice_fwd(_p(self.Ghi), _p(self.Glo), _p(w["qn"]), _p(ant), B, g.K, g.NR, self.D, g.T, g.S,
+                                  g.J, self.moff, _p(w["y"]), st), "sur_lattice_fwd")
+        if scale_out:
+            check(sur_scale_rows(_p(w["y"]), B, g.T, _p(w["s"]), self.c_out, 0, st), "sur_scale_rows")
+        return w["y"]
+
+    def forward(self, q, ant):
+        """Traces [B, T] for profiles q [B, K] (C per bin, f32) at antennas
+        ant [B, 2] (int32: radial class, bin index), device tensors."""
+        return self._fwd(q, ant, True)
+
+    def train_batch(self, q, ant, trace, lr, b1=0.9, b2=0.999, eps=1e-8, relative=False):
+        """One Adam step on the mean squared error of the traces, each divided
+        by peak|q| c_out (relative=False) or by its own peak (relative=True:
+        every trace's relative error weighs the same); returns the loss
+        (device tensor)."""
+        g = self.geo
+        B = q.shape[0]
+        w = self._w(B)
+        st = _stream()
+        self._fwd(q, ant, False, master=True)
+        if relative:
+            if "st" not in w:
+                import torch
+                w["st"] = torch.empty(B, dtype=torch.float32, device="cuda")
+            check(sur_normalize_rows(_p(trace), B, g.T, _p(w["tn"]), _p(w["st"]), st), "sur_normalize_rows")
+            # model trace / its target's peak = y_n c_out s_q / s_t
+            check(sur_scale_rows(_p(w["y"]), B, g.T, _p(w["s"]), self.c_out, 0, st), "sur_scale_rows")
+            check(sur_scale_rows(_p(w["y"]), B, g.T, _p(w["st"]), 1.0, 1, st), "sur_scale_rows")
+        else:
+            w["tn"].copy_(trace)
+            check(sur_scale_rows(_p(w["tn"]), B, g.T, _p(w["s"]), 1.0 / self.c_out, 1, st), "sur_scale_rows")
+        check(sur_mse(_p(w["y"]), _p(w["tn"]), B * g.T, _p(w["dy"]), _p(w["loss"]), st), "sur_mse")
+        if relative:   # back to the gradient with respect to y_n
+            check(sur_scale_rows(_p(w["dy"]), B, g.T, _p(w["s"]), self.c_out, 0, st), "sur_scale_rows")
+            check(sur_scale_rows(_p(w["dy"]), B, g.T, _p(w["st"]), 1.0, 1, st), "sur_scale_rows")
+        self.dG.zero_()
+        check(sur_lattice_bwd(_p(w["dy"]), _p(w["qn"]), _p(ant), B, g.K, g.NR, self.D, g.T, g.S, g.J, self.moff,
+                              _p(self.dG), st), "sur_lattice_bwd")
+        self.t += 1
+        check(sur_adam(_p(self.G), None, _p(self.dG), _p(self.m), _p(self.v), self.G.numel(), lr, b1, b2, eps, self.t,
+                       st), "sur_adam")
+        self._split = False
+        return w["loss"]
+
+    def predict(self, q, ant, chunk: int = 8192):
+        import torch
+        out = torch.empty(q.shape[0], self.geo.T, dtype=torch.float32, device="cuda")
+        for lo in range(0, q.shape[0], chunk):
+            hi = min(q.shape[0], lo + chunk)
+            out[lo:hi].copy_(self.forward(q[lo:hi].contiguous(), ant[lo:hi].contiguous()))
+        return out
+
+    def predict_grid(self, q, ants):
+        """Every profile q [P, K] at every antenna ants [A, 2]: traces
+        [A, P, T], each antenna's batch one tensor-core GEMM (bf16 operands,
+        f32 accumulation) with its K x T weight matrix."""
+        import torch
+        g = self.geo
+        P, A, K = q.shape[0], ants.shape[0], self.geo.K
+        st = _stream()
+        if not self._split:
+            self.split()
+        qn = torch.empty(P, K, dtype=torch.float32, device="cuda")
+        s = torch.empty(P, dtype=torch.float32, device="cuda")
+        check(sur_normalize_rows(_p(q), P, K, _p(qn), _p(s), st), "sur_normalize_rows")
+        qhi = torch.empty(P, K, dtype=torch.bfloat16, device="cuda")
+        qlo = torch.empty(P, K, dtype=torch.bfloat16, device="cuda")
+        check(sur_split_bf16(_p(qn), _p(qhi), _p(qlo), P * K, st), "sur_split_bf16")
+        Q3 = torch.cat([qhi, qhi, qlo], dim=1).contiguous()               # [P, 3K]
+        W3 = torch.empty(A, 3 * K, g.T, dtype=torch.bfloat16, device="cuda")
+        Wt = torch.empty(A, K, g.T, dtype=torch.bfloat16, device="cuda")
+        for part, tab in ((0, self.Ghi), (1, self.Glo)):
+            check(sur_lattice_weights(_p(tab), _p(ants), A, K, g.NR, self.D, g.T, g.S, g.J, self.moff, _p(Wt), st),
+                  "sur_lattice_weights")
+            W3[:, part * K:(part + 1) * K].copy_(Wt)
+            if part == 0:
+                W3[:, 2 * K:].copy_(Wt)
+        out = torch.empty(A, P, g.T, dtype=torch.float32, device="cuda")
+        for a in range(A):
+            check(sur_gemm_bf16(_p(Q3), 3 * K, 1, _p(W3[a]), g.T, 0, _p(out[a]), g.T, None, P, g.T, 3 * K, None, 0,
+                                0, st), "sur_gemm_bf16")
+            check(sur_scale_rows(_p(out[a]), P, g.T, _p(s), self.c_out, 0, st), "sur_scale_rows")
+        return out
+
+
+@dataclass
+class LatticeData:
+    q: object          # [R, K] f32 device: the profile of each FDTD run
+    trace: object      # [R, A, T] f32 device: Ez at every lattice antenna, every `decim`-th step
+    ant: object        # [A, 2] int32 device: (radial class, bin index) of each antenna
+    fdtd_s: float = 0.0
+
+
+def generate_lattice(grid, runs, ir, m, xyz, decim: int = 2, log=None) -> LatticeData:
+    """One FDTD run of the library per shower of `runs` (workloads.surrogate_runs;
+    their own detectors are ignored) on the lattice grid, recording Ez at every
+    lattice antenna (one run gives them all, Sec. III.B)."""
+    import torch
+    steps, A = grid.steps, xyz.shape[0]
+    T = steps // decim
+    q_all = torch.empty(len(runs), grid.n_bins, dtype=torch.float32, device="cuda")
+    tr_all = torch.empty(len(runs), A, T, dtype=torch.float32, device="cuda")
+    lw = lateral_nkg(grid.lateral["L"], grid.dx, grid.lateral["r_moliere"], grid.lateral["age"],
+                     grid.lateral["nsub"], grid.lateral["r_cut"])
+    sim = Simulation(grid.nx, grid.ny, grid.nz, grid.dx, grid.dt, grid.eps_r, grid.boundary, grid.npml)
+    sim.set_probes(xyz, steps)
+    buf = torch.empty(A, steps, 2, dtype=torch.float32, device="cuda")
+    t_fdtd = 0.0
+    for r, run in enumerate(runs):
+        q = profile_gaisser_hillas(grid.z0, grid.bin_dz, grid.n_bins, run["z1"], run["zmax"], run["lam"],
+                                   run["nmax"], grid.profile["frac"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.reset()
+        sim.set_shower(q, grid.z0, grid.bin_dz, grid.v, lw, grid.lateral["L"])
+        sim.step(steps)
+        check(fdtd_probes(sim.h, _p(buf), 1), "fdtd_probes")
+        torch.cuda.synchronize()
+        t_fdtd += time.perf_counter() - t0
+        tr_all[r].copy_(buf[:, decim - 1::decim, 0])
+        q_all[r].copy_(torch.tensor(q, dtype=torch.float32))
+        if log and (r + 1) % max(1, len(runs) // 5) == 0:
+            log(f"fdtd run {r + 1}/{len(runs)}: {t_fdtd / (r + 1):.3f} s per run")
+    sim.close()
+    ant = torch.tensor(np.stack([ir, m], 1), dtype=torch.int32, device="cuda")
+    return LatticeData(q_all, tr_all, ant, t_fdtd)
+
+
+def train_lattice(data: LatticeData, geo: LatticeGeometry, steps: int, batch: int = 1024, lr: float = 3e-3,
+                  seed: int = 0, log=None, relative: bool = False) -> Lattice:
+    """Adam on random (shower, antenna) pairs of `data`; the learning rate
+    decays by cosine to 1 % of `lr` (relative: see Lattice.train_batch)."""
+    import torch
+    R, A, _ = data.trace.shape
+    s = data.q.abs().amax(dim=1)
+    c_out = float(torch.sqrt(torch.mean((data.trace / s[:, None, None]) ** 2)).item())
+    net = Lattice(geo, c_out=c_out)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    for it in range(steps):
+        ri = torch.randint(0, R, (batch,), device="cuda", generator=gen)
+        ai = torch.randint(0, A, (batch,), device="cuda", generator=gen)
+        lr_t = lr * (0.01 + 0.99 * 0.5 * (1.0 + math.cos(math.pi * it / steps)))
+        loss = net.train_batch(data.q[ri].contiguous(), data.ant[ai].contiguous(), data.trace[ri, ai].contiguous(),
+                               lr_t, relative=relative)
+        if log and it % max(1, steps // 10) == 0:
+            log(f"lattice step {it} loss {float(loss.item()):.3e}")
+    return net

@@ -212,3 +212,43 @@ def test_lateral_tables():
     # nodes whose cell lies well inside r_M carry about that fraction
     frac_model = wn[rr < rM].sum()
     assert abs(frac_model - inner) < 0.06
+
+
+def test_bin_responses_are_exact_lattice_translates():
+    """With the shower moving half a cell per step (c dt = dx/2, v = c) and
+    profile bins of 8 steps (4 cells), the field of a one-bin profile at bin
+    j+1 seen at a detector 4 cells further along z is the field of bin j at
+    the detector, 8 steps later: the scheme and the charge-conserving deposit
+    (Sec. III.A, III.B) commute with a translation by 4 cells and 8 steps.
+    This holds exactly until a signal from the z ends of the grid (the only
+    part that does not move along) reaches the detector; the detectors here
+    stay inside that window.  The learned surrogate rests on this property."""
+    dx = 0.02
+    nx = ny = 40
+    nz, P = 210, 8
+    dt = dx / (2.0 * W.C0)
+    z0 = (P + 4) * dx
+    bin_dz = 4 * dx
+    nb = 40
+    lw = _asym_lateral(1)
+    steps = 290
+    j0 = 22            # the bin passes z = 100 cells at step 176, 92 cells from either z layer
+    traces = []
+    for j, dk in ((j0, 0), (j0 + 1, 4)):
+        o = oracle.Oracle(nx, ny, nz, dx, dt, W.EPS_R_ICE, oracle.CPML, P)
+        q = np.zeros(nb)
+        q[j] = -1e-9
+        o.set_shower(q, z0, bin_dz, W.C0, lw, 1)
+        zc = z0 / dx + 4 * j0
+        xyz = [((nx // 2 + a) * dx, (ny // 2 + b) * dx, (zc + c + dk) * dx)
+               for a, b, c in ((5, 0, -10), (3, 4, 0), (8, 0, 8), (0, 6, 15))]
+        o.set_probes(np.array(xyz), steps + 8)
+        o.step(steps + 8)
+        traces.append(o.probes())
+    a, b = traces
+    ref = a[:, :steps]
+    sh = b[:, 8:steps + 8]
+    assert np.abs(ref).max() > 0
+    assert np.abs(sh - ref).max() <= 1e-12 * np.abs(ref).max(), np.abs(sh - ref).max() / np.abs(ref).max()
+    # and the unshifted comparison is far from equal (the test has teeth)
+    assert np.abs(b[:, :steps] - ref).max() > 1e-2 * np.abs(ref).max()

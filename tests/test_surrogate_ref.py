@@ -127,3 +127,59 @@ def test_feature_and_normalisation_definitions():
     assert np.all(f[0, 62:] == 0)
     qn, s = R.normalize_rows(np.array([[0.0, -2.0, 1.0], [0.0, 0.0, 0.0]]))
     assert np.array_equal(s, [2.0, 0.0]) and np.array_equal(qn, [[0.0, -1.0, 0.5], [0.0, 0.0, 0.0]])
+
+
+# ---- lattice surrogate reference ------------------------------------------------
+
+def _lattice_case(seed=0, NR=3, D=9, T=40, S=3, K=6, B=5):
+    rng = np.random.default_rng(seed)
+    G = R.bf16(rng.standard_normal((NR, D, T)))
+    q = rng.standard_normal((B, K))
+    moff = 4
+    ant = np.stack([rng.integers(-1, NR + 1, B), rng.integers(0, 8, B)], axis=1)
+    return G, q, ant, S, 2, moff
+
+
+def test_lattice_forward_brute_force_and_weights():
+    """The superposition against one explicit double loop over (k, t), and
+    against the product of the profile with the antenna's weight matrix."""
+    G, q, ant, S, J, moff = _lattice_case()
+    y = R.lattice_forward(G, q, ant, S, J, moff)
+    NR, D, T = G.shape
+    K = q.shape[1]
+    # the same sum written as shifted, zero-padded copies of the table rows
+    for b in range(q.shape[0]):
+        ir, m = ant[b]
+        want = np.zeros(T)
+        for k in range(K):
+            d = m - k + moff
+            if 0 <= ir < NR and 0 <= d < D:
+                row = np.concatenate([np.zeros(T + S * K), G[ir, d], np.zeros(T + S * K)])
+                lo = T + S * K + J - S * k
+                want += q[b, k] * row[lo:lo + T]
+        assert np.allclose(y[b], want, rtol=1e-12, atol=1e-12)
+    # bin 0 with a lead of J samples: its first J table entries are never used
+    assert J > 0
+    W = R.lattice_weights(G, ant, K, S, J, moff)
+    assert np.allclose(np.einsum("bk,bkt->bt", q, W), y, rtol=1e-12, atol=1e-12)
+
+
+def test_lattice_gradient_central_differences():
+    G, q, ant, S, J, moff = _lattice_case(seed=1)
+    rng = np.random.default_rng(2)
+    tgt = rng.standard_normal((q.shape[0], G.shape[2]))
+
+    def loss(Gx):
+        return 0.5 * ((R.lattice_forward(Gx, q, ant, S, J, moff) - tgt) ** 2).sum()
+
+    dy = R.lattice_forward(G, q, ant, S, J, moff) - tgt
+    g = R.lattice_grad(dy, q, ant, S, J, moff, G.shape)
+    h = 1e-6
+    for idx in [(0, 4, 0), (1, 2, 7), (2, 8, 39), (0, 0, 13), (1, 5, 20)]:
+        Gp, Gm = G.copy(), G.copy()
+        Gp[idx] += h
+        Gm[idx] -= h
+        num = (loss(Gp) - loss(Gm)) / (2 * h)
+        assert abs(num - g[idx]) <= 1e-6 * (1 + abs(num)), (idx, num, g[idx])
+    # entries no antenna reaches have no gradient
+    assert np.count_nonzero(g) < g.size

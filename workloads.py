@@ -287,6 +287,44 @@ def surrogate_runs(seed: int, n_runs: int, n_probes: int = 64, grid: Optional[Wo
     return runs
 
 
+def surrogate_lattice_grid(nx: int = 128, ny: int = 128, nz: int = 512, npml: int = 10, steps: int = 2048,
+                           n_bins: int = 128, cells_per_bin: int = 4) -> Workload:
+    """The grid of the lattice surrogate's FDTD runs: 128x128x512 cells, dx =
+    2 cm, 10-cell CPML, 2048 steps, with the time step dt = dx / (2c), so that
+    the shower (v = c) advances exactly half a cell per step (c' dt / dx =
+    0.281, under the 3D Courant limit 0.577); 128 profile bins of 4 cells
+    (8 steps) from z0 = (npml + 4) dx, covering 10.24 m; NKG lateral spread.
+    Showers come from surrogate_runs, antennas from surrogate_lattice_antennas."""
+    dx = 0.02
+    dt = dx / (2.0 * C0)
+    L = int(math.ceil(3.0 * R_MOLIERE_M / dx))
+    return Workload(
+        name=f"surrogate_lattice{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, dx=dx, dt=dt, eps_r=EPS_R_ICE,
+        boundary=CPML, npml=npml, steps=steps,
+        profile={"kind": "gh", "frac": CHARGE_EXCESS},
+        lateral={"kind": "nkg", "L": L, "r_moliere": R_MOLIERE_M, "age": 1.0, "nsub": 4,
+                 "r_cut": 3.0 * R_MOLIERE_M},
+        z0=(npml + 4) * dx, bin_dz=cells_per_bin * dx, n_bins=n_bins, v=C0, probes_xyz=np.zeros((0, 3)))
+
+
+def surrogate_lattice_antennas(grid: Workload, r_range=(0.3, 0.9), z_range=(0.5, 9.5), cells_per_bin: int = 4):
+    """The antenna lattice of the surrogate: nodes in the half plane phi = 0
+    (y on the axis, x = axis + i_r dx) with r = i_r dx in r_range, at the
+    starts of the profile bins, z = z0 + cells_per_bin m dx in z_range.
+    Returns (ir, m, xyz): radial class ir = i_r - i_r(min), bin index m, and
+    the positions in metres (node coordinates from node (0, 0, 0))."""
+    dx = grid.dx
+    i_lo, i_hi = int(math.ceil(r_range[0] / dx - 1e-9)), int(math.floor(r_range[1] / dx + 1e-9))
+    kz0 = int(round(grid.z0 / dx))
+    m_lo = int(math.ceil((z_range[0] / dx - kz0) / cells_per_bin - 1e-9))
+    m_hi = int(math.floor((z_range[1] / dx - kz0) / cells_per_bin + 1e-9))
+    ic, jc = grid.nx // 2, grid.ny // 2
+    ir, m = np.meshgrid(np.arange(i_hi - i_lo + 1), np.arange(m_lo, m_hi + 1), indexing="ij")
+    ir, m = ir.ravel(), m.ravel()
+    xyz = np.stack([(ic + i_lo + ir) * dx, np.full(ir.size, jc * dx), (kz0 + cells_per_bin * m) * dx], axis=1)
+    return ir.astype(np.int32), m.astype(np.int32), xyz
+
+
 @dataclasses.dataclass
 class CylWorkload:
     name: str
@@ -367,4 +405,5 @@ def cyl_field(seed: int, comp: int, i, j, xp=np):
 
 
 WORKLOADS = {"parity96": parity96, "greisen384": greisen384, "gh640": gh640,
-             "greisen_small": greisen_small, "gh_small": gh_small, "surrogate_grid": surrogate_grid}
+             "greisen_small": greisen_small, "gh_small": gh_small, "surrogate_grid": surrogate_grid,
+             "surrogate_lattice_grid": surrogate_lattice_grid}
