@@ -69,26 +69,101 @@ using namespace tma;
 constexpr int TY = 8;                 // owned rows
 constexpr int NWR = TY + 3;           // warps: rows j0-2 .. j0+TY
 constexpr int NT = 32 * NWR;
-constexpr int TXC = 128;              // computed columns i0-4 .. i0+123
-constexpr int TXO = 120;              // owned columns (lanes 1 .. 30)
 constexpr int BR = TY + 4;            // box rows j0-2 .. j0+TY+1
-constexpr int BOX = TXC * BR;         // floats of a field or y/z psi box
-constexpr int FIELDS = 6 * BOX;
-constexpr unsigned FIELD_BYTES = 4u * FIELDS;
-constexpr int XROW = 2 * TXC;         // exchange floats per warp row (two components)
-constexpr int XBUF = NWR * XROW;      // one exchange buffer
 constexpr int NSMAX = 8;
 constexpr int BAR_BYTES = 128;
-// CPML coefficient table (floats): aH, bH, aE, bE of the columns i0-4 ..
-// i0+123, of the rows j0-2 .. j0+TY+1, of the planes kstart .. kstart+zt-1
-constexpr int CX = 0;
-constexpr int CY = 4 * TXC;
-constexpr int CZ = CY + 4 * BR;
 static_assert(NSMAX * 8 <= BAR_BYTES, "barrier area");
-static_assert(TXO % 4 == 0 && TXC == TXO + 8, "owned columns: lanes 1 .. 30");
 
-// shared memory: barriers, three exchange buffers, coefficient table, ring
-__host__ __device__ constexpr int head_floats(int zt) { return (3 * XBUF + CZ + 4 * zt + 31) / 32 * 32; }
+// Tile geometry for lanes of VW columns (VW = 4: float4, VW = 2: float2)
+template <int VW>
+struct Geo {
+    static constexpr int TXC = 32 * VW;          // computed columns i0-4 .. i0+TXC-5
+    static constexpr int TXO = TXC - 8;          // owned columns (lanes 4/VW .. 31-4/VW)
+    static constexpr int BOX = TXC * BR;         // floats of a field or y/z psi box
+    static constexpr int FIELDS = 6 * BOX;
+    static constexpr unsigned FIELD_BYTES = 4u * FIELDS;
+    static constexpr int XROW = 2 * TXC;         // exchange floats per warp row (two components)
+    static constexpr int XBUF = NWR * XROW;      // one exchange buffer
+    // CPML coefficient table (floats): aH, bH, aE, bE of the computed columns,
+    // of the rows j0-2 .. j0+TY+1, of the planes kstart .. kstart+zt-1
+    static constexpr int CX = 0;
+    static constexpr int CY = 4 * TXC;
+    static constexpr int CZ = CY + 4 * BR;
+    static constexpr int LO = 4 / VW;            // first owned lane
+    static constexpr int HI = 31 - 4 / VW;       // last owned lane
+    // shared memory: barriers, three exchange buffers, coefficient table, ring
+    __host__ __device__ static constexpr int head_floats(int zt) { return (3 * XBUF + CZ + 4 * zt + 31) / 32 * 32; }
+};
+
+// ---- lane vectors: the same code for float4 and float2 lanes ----
+template <int VW> struct Vec;
+template <> struct Vec<4> { typedef float4 T; typedef uint4 U; };
+template <> struct Vec<2> { typedef float2 T; typedef uint2 U; };
+
+template <typename V> __device__ __forceinline__ V ldv(const float *p) { return *reinterpret_cast<const V *>(p); }
+template <typename V> __device__ __forceinline__ void stv(float *p, V v) { *reinterpret_cast<V *>(p) = v; }
+template <typename V> __device__ __forceinline__ V vzero();
+template <> __device__ __forceinline__ float4 vzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
+// the float4 forms (tma_pipe.cuh) in the same overload sets as the float2 forms
+using tma::axpy;
+using tma::cpmlv;
+using tma::operator-;
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 axpy(float2 a, float s, float2 d) { return make_float2(a.x + s * d.x, a.y + s * d.y); }
+__device__ __forceinline__ float4 cpmls(float4 &psi, float a, float b, float4 d) { return cpml4(psi, a, b, d); }
+__device__ __forceinline__ float2 cpmls(float2 &psi, float a, float b, float2 d) {
+    return make_float2(cpml1(psi.x, a, b, d.x), cpml1(psi.y, a, b, d.y));
+}
+__device__ __forceinline__ float2 cpmlv(float2 &psi, float2 a, float2 b, float2 d) {
+    return make_float2(cpml1(psi.x, a.x, b.x, d.x), cpml1(psi.y, a.y, b.y, d.y));
+}
+__device__ __forceinline__ float first(float4 v) { return v.x; }
+__device__ __forceinline__ float first(float2 v) { return v.x; }
+__device__ __forceinline__ float last(float4 v) { return v.w; }
+__device__ __forceinline__ float last(float2 v) { return v.y; }
+// the vector one column to the right (x+1) / left (x-1), edge element given
+__device__ __forceinline__ float4 right(float4 v, float r) { return make_float4(v.y, v.z, v.w, r); }
+__device__ __forceinline__ float4 left(float4 v, float l) { return make_float4(l, v.x, v.y, v.z); }
+__device__ __forceinline__ float2 right(float2 v, float r) { return make_float2(v.y, r); }
+__device__ __forceinline__ float2 left(float2 v, float l) { return make_float2(l, v.x); }
+__device__ __forceinline__ float elem(float4 v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+__device__ __forceinline__ float elem(float2 v, int e) { return e == 0 ? v.x : v.y; }
+// v with the elements outside the mask set to +0 (bitwise, so a non-finite
+// value outside the state never leaks in)
+__device__ __forceinline__ float mk(float v, unsigned b) { return __uint_as_float(__float_as_uint(v) & b); }
+template <bool MASK>
+__device__ __forceinline__ float4 keep(float4 v, uint4 b) {
+    if (!MASK) return v;
+    return make_float4(mk(v.x, b.x), mk(v.y, b.y), mk(v.z, b.z), mk(v.w, b.w));
+}
+template <bool MASK>
+__device__ __forceinline__ float2 keep(float2 v, uint2 b) {
+    if (!MASK) return v;
+    return make_float2(mk(v.x, b.x), mk(v.y, b.y));
+}
+template <typename U> __device__ __forceinline__ U uzero();
+template <> __device__ __forceinline__ uint4 uzero<uint4>() { return make_uint4(0u, 0u, 0u, 0u); }
+template <> __device__ __forceinline__ uint2 uzero<uint2>() { return make_uint2(0u, 0u); }
+__device__ __forceinline__ uint4 umask(const unsigned *m, float4) { return make_uint4(m[0], m[1], m[2], m[3]); }
+__device__ __forceinline__ uint2 umask(const unsigned *m, float2) { return make_uint2(m[0], m[1]); }
+// store the first n (1..VW) elements; one vector store when n == VW
+__device__ __forceinline__ void stn(float *p, float4 v, int n) { st4n(p, v, n); }
+__device__ __forceinline__ void stn(float *p, float2 v, int n) {
+    if (n == 2) *reinterpret_cast<float2 *>(p) = v;
+    else p[0] = v.x;
+}
+// the shower's current on the lane's Ez edges
+__device__ __forceinline__ void add_source(float4 &v, const Source &s, const SourceStep &w, int c0, int j, int k) {
+    v.x += source_at(s, w, c0, j, k);
+    v.y += source_at(s, w, c0 + 1, j, k);
+    v.z += source_at(s, w, c0 + 2, j, k);
+    v.w += source_at(s, w, c0 + 3, j, k);
+}
+__device__ __forceinline__ void add_source(float2 &v, const Source &s, const SourceStep &w, int c0, int j, int k) {
+    v.x += source_at(s, w, c0, j, k);
+    v.y += source_at(s, w, c0 + 1, j, k);
+}
 
 struct Maps {
     CUtensorMap f[2][6];    // fields [set][component]
@@ -107,6 +182,7 @@ struct Args {
     int zt;                 // planes of the z coefficient table
     int ring;               // floats of the stage ring
     int xlo4, xhb, xbw;     // x psi: high half start, first column of the high half, box width
+    int xplane;             // floats of an x psi plane (ny rows)
     int cur, ecur;
     Source src;
     SourceStep ss1, ss2;    // current of steps n and n+1
@@ -126,17 +202,19 @@ struct Blk {
     int pbeg, pend;
 };
 
+template <int VW>
 __device__ __forceinline__ void issue_plane(const Args &A, const Maps &M, const Blk &B, float *st, uint64_t *bar,
                                             int r) {
+    typedef Geo<VW> G;
     const int p = B.kstart + r;
     const int lz = (B.hz && p >= 0 && p < A.g.nz) ? slab_cell(p, A.g.nz, A.pm.P) : -1;
-    unsigned bytes = FIELD_BYTES;
+    unsigned bytes = G::FIELD_BYTES;
     if (B.hx) bytes += 16u * (unsigned)(B.nxb * A.xbw * BR);
-    if (B.hy) bytes += 16u * BOX;
-    if (lz >= 0) bytes += 16u * BOX;
+    if (B.hy) bytes += 16u * G::BOX;
+    if (lz >= 0) bytes += 16u * G::BOX;
     mbar_expect_tx(bar, bytes);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) tma_load(st + c * BOX, &M.f[A.cur][c], bar, B.i0 - 4, B.j0 - 2, p);
+    for (int c = 0; c < 6; ++c) tma_load(st + c * G::BOX, &M.f[A.cur][c], bar, B.i0 - 4, B.j0 - 2, p);
     if (B.hx)
         for (int a = 0; a < 4; ++a) {
             float *d = st + B.xo + a * B.nxb * B.xb;
@@ -145,33 +223,39 @@ __device__ __forceinline__ void issue_plane(const Args &A, const Maps &M, const 
             if (B.xhi >= 0) tma_load(d + B.xhi * B.xb, mp, bar, A.xlo4, B.j0 - 2, p);
         }
     if (B.hy)
-        for (int a = 0; a < 4; ++a) tma_load(st + B.yo + a * BOX, &M.y[a][a < 2 ? A.cur : A.ecur], bar, B.i0 - 4, B.l0, p);
+        for (int a = 0; a < 4; ++a) tma_load(st + B.yo + a * G::BOX, &M.y[a][a < 2 ? A.cur : A.ecur], bar, B.i0 - 4, B.l0, p);
     if (lz >= 0)
-        for (int a = 0; a < 4; ++a) tma_load(st + B.zo + a * BOX, &M.z[a][a < 2 ? A.cur : A.ecur], bar, B.i0 - 4, B.j0 - 2, lz);
+        for (int a = 0; a < 4; ++a) tma_load(st + B.zo + a * G::BOX, &M.z[a][a < 2 ? A.cur : A.ecur], bar, B.i0 - 4, B.j0 - 2, lz);
 }
 
+template <int VW>
 struct Lane {
+    typedef typename Vec<VW>::U U;
     int lane, w, c0, j;
     bool rowin;
     bool own;          // stores level-2 values: owned lane and row, on the grid
     int nval;          // columns of the lane on the grid
-    uint4 mcol;        // all bits of an element whose column lies in [0, nx)
-    uint4 mcol0;       // the same without column 0
+    U mcol;            // all bits of an element whose column lies in [0, nx)
+    U mcol0;           // the same without column 0
     int ly;            // y slab row of j, or -1
     bool xl;           // the lane's columns lie in an x half (row on the grid)
     int xs, xpos;      // x psi: offset in a stage's x array (box row 0), position of column c0
+    unsigned yoff, zoff, xoff;   // the lane's psi offsets in plane 0 / slab plane 0
 };
 
 // Per-plane element masks of the six components: the state a cell keeps
 // (all bits) or a zero that the one-step paths leave there (no bits): nodes
 // outside the grid, and the components a cell owns on the grid's low faces.
+template <typename U>
 struct Masks {
-    uint4 hx, hy, hz, ex, ey, ez;
+    U hx, hy, hz, ex, ey, ez;
 };
-__device__ __forceinline__ Masks masks(const Lane &L, int k, int nz) {
-    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+template <int VW>
+__device__ __forceinline__ Masks<typename Vec<VW>::U> masks(const Lane<VW> &L, int k, int nz) {
+    typedef typename Vec<VW>::U U;
+    const U z = uzero<U>();
     const bool in = L.rowin && k >= 0 && k < nz, fj = L.j != 0, fk = k != 0;
-    Masks m;
+    Masks<U> m;
     m.hx = in ? L.mcol0 : z;
     m.hy = in && fj ? L.mcol : z;
     m.hz = in && fk ? L.mcol : z;
@@ -180,28 +264,17 @@ __device__ __forceinline__ Masks masks(const Lane &L, int k, int nz) {
     m.ez = in && fj ? L.mcol0 : z;
     return m;
 }
-// v with the elements outside the mask set to +0 (bitwise, so a non-finite
-// value outside the state never leaks in)
-template <bool MASK>
-__device__ __forceinline__ float4 keep(float4 v, uint4 b) {
-    if (!MASK) return v;
-    return make_float4(__uint_as_float(__float_as_uint(v.x) & b.x), __uint_as_float(__float_as_uint(v.y) & b.y),
-                       __uint_as_float(__float_as_uint(v.z) & b.z), __uint_as_float(__float_as_uint(v.w) & b.w));
-}
-// the vector one column to the right (x+1) / left (x-1), edge element given
-__device__ __forceinline__ float4 right(float4 v, float r) { return make_float4(v.y, v.z, v.w, r); }
-__device__ __forceinline__ float4 left(float4 v, float l) { return make_float4(l, v.x, v.y, v.z); }
-__device__ __forceinline__ float elem(float4 v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
 
 constexpr unsigned FULL = 0xffffffffu;
 
 // Register state carried from one iteration to the next.
+template <typename V>
 struct State {
-    float4 ex1p, ey1p, ez1p;   // level-1 E at plane p-1
-    float4 hx1p, hy1p, hz1p;   // level-1 H at plane p-1
-    float4 hx2p, hy2p;         // level-2 H at plane p-2
+    V ex1p, ey1p, ez1p;   // level-1 E at plane p-1
+    V hx1p, hy1p, hz1p;   // level-1 H at plane p-1
+    V hx2p, hy2p;         // level-2 H at plane p-2
     // level-1 CPML memory at plane p-1 (H terms 0, 1; E terms 0, 1 per axis)
-    float4 yH0, yH1, yE0, yE1, zH0, zH1, zE0, zE1, xH0, xH1, xE0, xE1;
+    V yH0, yH1, yE0, yE1, zH0, zH1, zE0, zE1, xH0, xH1, xE0, xE1;
 };
 
 struct RingPos {
@@ -209,10 +282,13 @@ struct RingPos {
     uint32_t ph1;
 };
 
-template <bool HX, bool HY, bool HZ, bool MASK>
-__device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &L, const Blk &B, uint64_t *bar,
-                                      float *ring, float *X, const float *CT, int rel, RingPos &rp, State &S,
-                                      int &pc) {
+template <int VW, bool HX, bool HY, bool HZ, bool MASK>
+__device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane<VW> &L, const Blk &B, uint64_t *bar,
+                                      float *ring, float *X, const float *CT, int rel, RingPos &rp,
+                                      State<typename Vec<VW>::T> &S, int &pc) {
+    typedef typename Vec<VW>::T V;
+    typedef Geo<VW> G;
+    constexpr int TXC = G::TXC, BOX = G::BOX, XROW = G::XROW, XBUF = G::XBUF, CX = G::CX, CY = G::CY, CZ = G::CZ;
     const Grid &g = A.g;
     const Cpml &pm = A.pm;
     const int tid = threadIdx.x, w = L.w;
@@ -225,66 +301,63 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
     const float *s0 = ring + rp.s0 * B.stage;   // plane p
     const float *s1 = ring + rp.s1 * B.stage;   // plane p+1
     float *XA = X, *XB = X + XBUF, *XC = X + 2 * XBUF;
-    const int bc0 = 4 * L.lane;
+    const int bc0 = VW * L.lane;
     const int lzp = (HZ && p >= 0 && p < g.nz) ? slab_cell(p, g.nz, pm.P) : -1;
     const int lzq = (HZ && q >= 0 && q < g.nz) ? slab_cell(q, g.nz, pm.P) : -1;
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const V z4 = vzero<V>();
     const bool yl = HY && L.ly >= 0;
     const float *PY = s0 + B.yo + (L.ly - B.l0) * TXC + bc0;
     const float *PZ = s0 + B.zo + w * TXC + bc0;
     const float *PX = s0 + B.xo + L.xs + w * A.xbw;
     const int XA4 = B.nxb * B.xb;   // floats per x psi array in a stage
-    Masks mp, mq;
-    if (MASK) mp = masks(L, p, g.nz);
+    Masks<typename Vec<VW>::U> mp, mq;
+    if (MASK) mp = masks<VW>(L, p, g.nz);
 
     // ---- A: level-1 H at plane p (rows j0-2 .. j0+TY) ----
-    const float4 ex0 = lds4(s0 + 0 * BOX + w * TXC + bc0);
-    const float4 ey0 = lds4(s0 + 1 * BOX + w * TXC + bc0);
-    const float4 ez0 = lds4(s0 + 2 * BOX + w * TXC + bc0);
-    float4 hx1, hy1, hz1;
-    float4 yH0 = z4, yH1 = z4, zH0 = z4, zH1 = z4, xH0 = z4, xH1 = z4;
+    const V ex0 = ldv<V>(s0 + 0 * BOX + w * TXC + bc0);
+    const V ey0 = ldv<V>(s0 + 1 * BOX + w * TXC + bc0);
+    const V ez0 = ldv<V>(s0 + 2 * BOX + w * TXC + bc0);
+    V hx1, hy1, hz1;
+    V yH0 = z4, yH1 = z4, zH0 = z4, zH1 = z4, xH0 = z4, xH1 = z4;
     {
-        const float4 hx = lds4(s0 + 3 * BOX + w * TXC + bc0);
-        const float4 hy = lds4(s0 + 4 * BOX + w * TXC + bc0);
-        const float4 hz = lds4(s0 + 5 * BOX + w * TXC + bc0);
-        const float4 exU = lds4(s0 + 0 * BOX + (w + 1) * TXC + bc0);   // row j+1
-        const float4 ezU = lds4(s0 + 2 * BOX + (w + 1) * TXC + bc0);
-        const float4 exN = lds4(s1 + 0 * BOX + w * TXC + bc0);         // plane p+1
-        const float4 eyN = lds4(s1 + 1 * BOX + w * TXC + bc0);
-        const float eyR = __shfl_down_sync(FULL, ey0.x, 1);             // column +4 (lane 31: unused)
-        const float ezR = __shfl_down_sync(FULL, ez0.x, 1);
-        float4 dyEz = ezU - ez0, dzEy = eyN - ey0;                      // Hx
-        float4 dzEx = exN - ex0, dxEz = right(ez0, ezR) - ez0;          // Hy
-        float4 dxEy = right(ey0, eyR) - ey0, dyEx = exU - ex0;          // Hz
+        const V hx = ldv<V>(s0 + 3 * BOX + w * TXC + bc0);
+        const V hy = ldv<V>(s0 + 4 * BOX + w * TXC + bc0);
+        const V hz = ldv<V>(s0 + 5 * BOX + w * TXC + bc0);
+        const V exU = ldv<V>(s0 + 0 * BOX + (w + 1) * TXC + bc0);   // row j+1
+        const V ezU = ldv<V>(s0 + 2 * BOX + (w + 1) * TXC + bc0);
+        const V exN = ldv<V>(s1 + 0 * BOX + w * TXC + bc0);         // plane p+1
+        const V eyN = ldv<V>(s1 + 1 * BOX + w * TXC + bc0);
+        const float eyR = __shfl_down_sync(FULL, first(ey0), 1);             // column +4 (lane 31: unused)
+        const float ezR = __shfl_down_sync(FULL, first(ez0), 1);
+        V dyEz = ezU - ez0, dzEy = eyN - ey0;                      // Hx
+        V dzEx = exN - ex0, dxEz = right(ez0, ezR) - ez0;          // Hy
+        V dxEy = right(ey0, eyR) - ey0, dyEx = exU - ex0;          // Hz
         if (yl) {
             const float a = CT[CY + w], b = CT[CY + BR + w];
-            yH0 = lds4(PY);
-            yH1 = lds4(PY + BOX);
-            dyEz = cpml4(yH0, a, b, dyEz);
-            dyEx = cpml4(yH1, a, b, dyEx);
+            yH0 = ldv<V>(PY);
+            yH1 = ldv<V>(PY + BOX);
+            dyEz = cpmls(yH0, a, b, dyEz);
+            dyEx = cpmls(yH1, a, b, dyEx);
         }
         if (HZ && lzp >= 0) {
             const float a = CT[CZ + rel], b = CT[CZ + A.zt + rel];
-            zH0 = lds4(PZ);
-            zH1 = lds4(PZ + BOX);
-            dzEy = cpml4(zH0, a, b, dzEy);
-            dzEx = cpml4(zH1, a, b, dzEx);
+            zH0 = ldv<V>(PZ);
+            zH1 = ldv<V>(PZ + BOX);
+            dzEy = cpmls(zH0, a, b, dzEy);
+            dzEx = cpmls(zH1, a, b, dzEx);
         }
         if (HX) {
-            const float4 a = lds4(CT + CX + bc0), b = lds4(CT + CX + TXC + bc0);
-            xH0 = L.xl ? lds4(PX) : z4;
-            xH1 = L.xl ? lds4(PX + XA4) : z4;
+            const V a = ldv<V>(CT + CX + bc0), b = ldv<V>(CT + CX + TXC + bc0);
+            xH0 = L.xl ? ldv<V>(PX) : z4;
+            xH1 = L.xl ? ldv<V>(PX + XA4) : z4;
             dxEz = cpmlv(xH0, a, b, dxEz);
             dxEy = cpmlv(xH1, a, b, dxEy);
         }
         hx1 = keep<MASK>(axpy(hx, -kH, dyEz - dzEy), mp.hx);
         hy1 = keep<MASK>(axpy(hy, -kH, dzEx - dxEz), mp.hy);
         hz1 = keep<MASK>(axpy(hz, -kH, dxEy - dyEx), mp.hz);
-        yH0 = keep<MASK>(yH0, mp.hx); yH1 = keep<MASK>(yH1, mp.hz);
-        zH0 = keep<MASK>(zH0, mp.hx); zH1 = keep<MASK>(zH1, mp.hy);
-        xH0 = keep<MASK>(xH0, mp.hy); xH1 = keep<MASK>(xH1, mp.hz);
-        sts4(XA + w * XROW + bc0, hx1);
-        sts4(XA + w * XROW + TXC + bc0, hz1);
+        stv(XA + w * XROW + bc0, hx1);
+        stv(XA + w * XROW + TXC + bc0, hz1);
     }
     if (__syncthreads_or(!ok)) {
         // a wait expired: record it, let the copies in flight land, stop
@@ -298,61 +371,53 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
     }
     // the barrier orders every thread's reads of stage p before its refill
     if (!STAGE_IN_B && tid == 0 && rel + B.ns < B.nplanes)
-        issue_plane(A, M, B, ring + rp.s0 * B.stage, &bar[rp.s0], rel + B.ns);
+        issue_plane<VW>(A, M, B, ring + rp.s0 * B.stage, &bar[rp.s0], rel + B.ns);
 
     // ---- B: level-1 E at plane p (rows j0-1 .. j0+TY) ----
-    float4 ex1 = z4, ey1 = z4, ez1 = z4;
-    float4 yE0 = z4, yE1 = z4, zE0 = z4, zE1 = z4, xE0 = z4, xE1 = z4;
+    V ex1 = z4, ey1 = z4, ez1 = z4;
+    V yE0 = z4, yE1 = z4, zE0 = z4, zE1 = z4, xE0 = z4, xE1 = z4;
     if (w >= 1) {
-        const float4 hzD = lds4(XA + (w - 1) * XROW + TXC + bc0);   // row j-1
-        const float4 hxD = lds4(XA + (w - 1) * XROW + bc0);
-        const float hzL = __shfl_up_sync(FULL, hz1.w, 1);           // column -1 (lane 0: unused)
-        const float hyL = __shfl_up_sync(FULL, hy1.w, 1);
-        float4 dyHz = hz1 - hzD, dzHy = hy1 - S.hy1p;                  // Ex
-        float4 dzHx = hx1 - S.hx1p, dxHz = hz1 - left(hz1, hzL);       // Ey
-        float4 dxHy = hy1 - left(hy1, hyL), dyHx = hx1 - hxD;          // Ez
+        const V hzD = ldv<V>(XA + (w - 1) * XROW + TXC + bc0);   // row j-1
+        const V hxD = ldv<V>(XA + (w - 1) * XROW + bc0);
+        const float hzL = __shfl_up_sync(FULL, last(hz1), 1);           // column -1 (lane 0: unused)
+        const float hyL = __shfl_up_sync(FULL, last(hy1), 1);
+        V dyHz = hz1 - hzD, dzHy = hy1 - S.hy1p;                  // Ex
+        V dzHx = hx1 - S.hx1p, dxHz = hz1 - left(hz1, hzL);       // Ey
+        V dxHy = hy1 - left(hy1, hyL), dyHx = hx1 - hxD;          // Ez
         if (yl) {
             const float a = CT[CY + 2 * BR + w], b = CT[CY + 3 * BR + w];
-            yE0 = lds4(PY + 2 * BOX);
-            yE1 = lds4(PY + 3 * BOX);
-            dyHz = cpml4(yE0, a, b, dyHz);
-            dyHx = cpml4(yE1, a, b, dyHx);
+            yE0 = ldv<V>(PY + 2 * BOX);
+            yE1 = ldv<V>(PY + 3 * BOX);
+            dyHz = cpmls(yE0, a, b, dyHz);
+            dyHx = cpmls(yE1, a, b, dyHx);
         }
         if (HZ && lzp >= 0) {
             const float a = CT[CZ + 2 * A.zt + rel], b = CT[CZ + 3 * A.zt + rel];
-            zE0 = lds4(PZ + 2 * BOX);
-            zE1 = lds4(PZ + 3 * BOX);
-            dzHy = cpml4(zE0, a, b, dzHy);
-            dzHx = cpml4(zE1, a, b, dzHx);
+            zE0 = ldv<V>(PZ + 2 * BOX);
+            zE1 = ldv<V>(PZ + 3 * BOX);
+            dzHy = cpmls(zE0, a, b, dzHy);
+            dzHx = cpmls(zE1, a, b, dzHx);
         }
         if (HX) {
-            const float4 a = lds4(CT + CX + 2 * TXC + bc0), b = lds4(CT + CX + 3 * TXC + bc0);
-            xE0 = L.xl ? lds4(PX + 2 * XA4) : z4;
-            xE1 = L.xl ? lds4(PX + 3 * XA4) : z4;
+            const V a = ldv<V>(CT + CX + 2 * TXC + bc0), b = ldv<V>(CT + CX + 3 * TXC + bc0);
+            xE0 = L.xl ? ldv<V>(PX + 2 * XA4) : z4;
+            xE1 = L.xl ? ldv<V>(PX + 3 * XA4) : z4;
             dxHz = cpmlv(xE0, a, b, dxHz);
             dxHy = cpmlv(xE1, a, b, dxHy);
         }
         ex1 = axpy(ex0, kE, dyHz - dzHy);
         ey1 = axpy(ey0, kE, dzHx - dxHz);
         ez1 = axpy(ez0, kE, dxHy - dyHx);
-        if (B.src_blk) {
-            ez1.x += source_at(A.src, A.ss1, L.c0, L.j, p);
-            ez1.y += source_at(A.src, A.ss1, L.c0 + 1, L.j, p);
-            ez1.z += source_at(A.src, A.ss1, L.c0 + 2, L.j, p);
-            ez1.w += source_at(A.src, A.ss1, L.c0 + 3, L.j, p);
-        }
+        if (B.src_blk) add_source(ez1, A.src, A.ss1, L.c0, L.j, p);
         ex1 = keep<MASK>(ex1, mp.ex);
         ey1 = keep<MASK>(ey1, mp.ey);
         ez1 = keep<MASK>(ez1, mp.ez);
-        yE0 = keep<MASK>(yE0, mp.ex); yE1 = keep<MASK>(yE1, mp.ez);
-        zE0 = keep<MASK>(zE0, mp.ex); zE1 = keep<MASK>(zE1, mp.ey);
-        xE0 = keep<MASK>(xE0, mp.ey); xE1 = keep<MASK>(xE1, mp.ez);
     }
     // detector records of plane p (block-uniform walk of the block's list)
     while (pc < B.pend) {
         const int4 r = A.prec[pc];
         if (r.x != p) break;
-        if (w >= 1 && r.y == L.j && r.z >= L.c0 && r.z < L.c0 + 4) {
+        if (w >= 1 && r.y == L.j && r.z >= L.c0 && r.z < L.c0 + VW) {
             const int c = r.w & 3;
             A.pbuf[r.w >> 2] = elem(c == 0 ? ex1 : c == 1 ? ey1 : ez1, r.z - L.c0);
         }
@@ -360,118 +425,113 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
     }
 
     // ---- C: level-2 H at plane q = p-1 (rows j0-1 .. j0+TY-1) ----
-    float4 hx2 = z4, hy2 = z4, hz2 = z4;
-    if (MASK) mq = masks(L, q, g.nz);
+    V hx2 = z4, hy2 = z4, hz2 = z4;
+    if (MASK) mq = masks<VW>(L, q, g.nz);
     if (p >= B.k0 && w >= 1 && w <= TY + 1) {
-        const float4 exU = lds4(XB + (w + 1) * XROW + bc0);         // level-1 E of plane q, row j+1
-        const float4 ezU = lds4(XB + (w + 1) * XROW + TXC + bc0);
-        const float eyR = __shfl_down_sync(FULL, S.ey1p.x, 1);
-        const float ezR = __shfl_down_sync(FULL, S.ez1p.x, 1);
-        float4 dyEz = ezU - S.ez1p, dzEy = ey1 - S.ey1p;
-        float4 dzEx = ex1 - S.ex1p, dxEz = right(S.ez1p, ezR) - S.ez1p;
-        float4 dxEy = right(S.ey1p, eyR) - S.ey1p, dyEx = exU - S.ex1p;
+        const V exU = ldv<V>(XB + (w + 1) * XROW + bc0);         // level-1 E of plane q, row j+1
+        const V ezU = ldv<V>(XB + (w + 1) * XROW + TXC + bc0);
+        const float eyR = __shfl_down_sync(FULL, first(S.ey1p), 1);
+        const float ezR = __shfl_down_sync(FULL, first(S.ez1p), 1);
+        V dyEz = ezU - S.ez1p, dzEy = ey1 - S.ey1p;
+        V dzEx = ex1 - S.ex1p, dxEz = right(S.ez1p, ezR) - S.ez1p;
+        V dxEy = right(S.ey1p, eyR) - S.ey1p, dyEx = exU - S.ex1p;
         if (yl) {
             const float a = CT[CY + w], b = CT[CY + BR + w];
-            dyEz = cpml4(S.yH0, a, b, dyEz);
-            dyEx = cpml4(S.yH1, a, b, dyEx);
+            dyEz = cpmls(S.yH0, a, b, dyEz);
+            dyEx = cpmls(S.yH1, a, b, dyEx);
         }
         if (HZ && lzq >= 0) {
             const float a = CT[CZ + rel - 1], b = CT[CZ + A.zt + rel - 1];
-            dzEy = cpml4(S.zH0, a, b, dzEy);
-            dzEx = cpml4(S.zH1, a, b, dzEx);
+            dzEy = cpmls(S.zH0, a, b, dzEy);
+            dzEx = cpmls(S.zH1, a, b, dzEx);
         }
         if (HX) {
-            const float4 a = lds4(CT + CX + bc0), b = lds4(CT + CX + TXC + bc0);
+            const V a = ldv<V>(CT + CX + bc0), b = ldv<V>(CT + CX + TXC + bc0);
             dxEz = cpmlv(S.xH0, a, b, dxEz);
             dxEy = cpmlv(S.xH1, a, b, dxEy);
         }
         hx2 = keep<MASK>(axpy(S.hx1p, -kH, dyEz - dzEy), mq.hx);
         hy2 = keep<MASK>(axpy(S.hy1p, -kH, dzEx - dxEz), mq.hy);
         hz2 = keep<MASK>(axpy(S.hz1p, -kH, dxEy - dyEx), mq.hz);
-        sts4(XC + w * XROW + bc0, hx2);
-        sts4(XC + w * XROW + TXC + bc0, hz2);
+        stv(XC + w * XROW + bc0, hx2);
+        stv(XC + w * XROW + TXC + bc0, hz2);
         if (L.own && q >= B.k0 && q < B.k1) {
             const unsigned o = (unsigned)L.c0 + (unsigned)L.j * (unsigned)g.pitch + (unsigned)q * (unsigned)g.plane;
-            st4n(A.out[3] + o, hx2, L.nval);
-            st4n(A.out[4] + o, hy2, L.nval);
-            st4n(A.out[5] + o, hz2, L.nval);
+            stn(A.out[3] + o, hx2, L.nval);
+            stn(A.out[4] + o, hy2, L.nval);
+            stn(A.out[5] + o, hz2, L.nval);
             if (yl) {
-                const unsigned oy = (unsigned)psi_y(g, pm.W, L.c0, L.ly, q);
-                st4n(pm.hout[1][0] + oy, keep<MASK>(S.yH0, mq.hx), L.nval);
-                st4n(pm.hout[1][1] + oy, keep<MASK>(S.yH1, mq.hz), L.nval);
+                const unsigned oy = L.yoff + (unsigned)q * (unsigned)(pm.W * g.pitch);
+                stn(pm.hout[1][0] + oy, S.yH0, L.nval);
+                stn(pm.hout[1][1] + oy, S.yH1, L.nval);
             }
             if (HZ && lzq >= 0) {
-                const unsigned oz = (unsigned)psi_z(g, pm.W, L.c0, L.j, lzq);
-                st4n(pm.hout[2][0] + oz, keep<MASK>(S.zH0, mq.hx), L.nval);
-                st4n(pm.hout[2][1] + oz, keep<MASK>(S.zH1, mq.hy), L.nval);
+                const unsigned oz = L.zoff + (unsigned)lzq * (unsigned)(g.ny * g.pitch);
+                stn(pm.hout[2][0] + oz, S.zH0, L.nval);
+                stn(pm.hout[2][1] + oz, S.zH1, L.nval);
             }
             if (HX && L.xl) {
-                const unsigned ox = (unsigned)psi_x(g, pm.P, L.xpos, L.j, q);
-                st4n(pm.hout[0][0] + ox, keep<MASK>(S.xH0, mq.hy), L.nval);
-                st4n(pm.hout[0][1] + ox, keep<MASK>(S.xH1, mq.hz), L.nval);
+                const unsigned ox = L.xoff + (unsigned)q * (unsigned)A.xplane;
+                stn(pm.hout[0][0] + ox, S.xH0, L.nval);
+                stn(pm.hout[0][1] + ox, S.xH1, L.nval);
             }
         }
     }
     __syncthreads();
     if (STAGE_IN_B && tid == 0 && rel + B.ns < B.nplanes)
-        issue_plane(A, M, B, ring + rp.s0 * B.stage, &bar[rp.s0], rel + B.ns);
+        issue_plane<VW>(A, M, B, ring + rp.s0 * B.stage, &bar[rp.s0], rel + B.ns);
 
     // ---- D: level-1 E rows for the next C; level-2 E at plane q (owned rows) ----
     if (w >= 1) {
-        sts4(XB + w * XROW + bc0, ex1);
-        sts4(XB + w * XROW + TXC + bc0, ez1);
+        stv(XB + w * XROW + bc0, ex1);
+        stv(XB + w * XROW + TXC + bc0, ez1);
     }
     if (p >= B.k0 + 1 && w >= 2 && w <= TY + 1) {
-        const float4 hzD = lds4(XC + (w - 1) * XROW + TXC + bc0);
-        const float4 hxD = lds4(XC + (w - 1) * XROW + bc0);
-        const float hzL = __shfl_up_sync(FULL, hz2.w, 1);
-        const float hyL = __shfl_up_sync(FULL, hy2.w, 1);
-        float4 dyHz = hz2 - hzD, dzHy = hy2 - S.hy2p;
-        float4 dzHx = hx2 - S.hx2p, dxHz = hz2 - left(hz2, hzL);
-        float4 dxHy = hy2 - left(hy2, hyL), dyHx = hx2 - hxD;
+        const V hzD = ldv<V>(XC + (w - 1) * XROW + TXC + bc0);
+        const V hxD = ldv<V>(XC + (w - 1) * XROW + bc0);
+        const float hzL = __shfl_up_sync(FULL, last(hz2), 1);
+        const float hyL = __shfl_up_sync(FULL, last(hy2), 1);
+        V dyHz = hz2 - hzD, dzHy = hy2 - S.hy2p;
+        V dzHx = hx2 - S.hx2p, dxHz = hz2 - left(hz2, hzL);
+        V dxHy = hy2 - left(hy2, hyL), dyHx = hx2 - hxD;
         if (yl) {
             const float a = CT[CY + 2 * BR + w], b = CT[CY + 3 * BR + w];
-            dyHz = cpml4(S.yE0, a, b, dyHz);
-            dyHx = cpml4(S.yE1, a, b, dyHx);
+            dyHz = cpmls(S.yE0, a, b, dyHz);
+            dyHx = cpmls(S.yE1, a, b, dyHx);
         }
         if (HZ && lzq >= 0) {
             const float a = CT[CZ + 2 * A.zt + rel - 1], b = CT[CZ + 3 * A.zt + rel - 1];
-            dzHy = cpml4(S.zE0, a, b, dzHy);
-            dzHx = cpml4(S.zE1, a, b, dzHx);
+            dzHy = cpmls(S.zE0, a, b, dzHy);
+            dzHx = cpmls(S.zE1, a, b, dzHx);
         }
         if (HX) {
-            const float4 a = lds4(CT + CX + 2 * TXC + bc0), b = lds4(CT + CX + 3 * TXC + bc0);
+            const V a = ldv<V>(CT + CX + 2 * TXC + bc0), b = ldv<V>(CT + CX + 3 * TXC + bc0);
             dxHz = cpmlv(S.xE0, a, b, dxHz);
             dxHy = cpmlv(S.xE1, a, b, dxHy);
         }
-        float4 ex2 = axpy(S.ex1p, kE, dyHz - dzHy);
-        float4 ey2 = axpy(S.ey1p, kE, dzHx - dxHz);
-        float4 ez2 = axpy(S.ez1p, kE, dxHy - dyHx);
+        V ex2 = axpy(S.ex1p, kE, dyHz - dzHy);
+        V ey2 = axpy(S.ey1p, kE, dzHx - dxHz);
+        V ez2 = axpy(S.ez1p, kE, dxHy - dyHx);
         if (L.own && q < B.k1) {
-            if (B.src_blk) {
-                ez2.x += source_at(A.src, A.ss2, L.c0, L.j, q);
-                ez2.y += source_at(A.src, A.ss2, L.c0 + 1, L.j, q);
-                ez2.z += source_at(A.src, A.ss2, L.c0 + 2, L.j, q);
-                ez2.w += source_at(A.src, A.ss2, L.c0 + 3, L.j, q);
-            }
+            if (B.src_blk) add_source(ez2, A.src, A.ss2, L.c0, L.j, q);
             const unsigned o = (unsigned)L.c0 + (unsigned)L.j * (unsigned)g.pitch + (unsigned)q * (unsigned)g.plane;
-            st4n(A.out[0] + o, keep<MASK>(ex2, mq.ex), L.nval);
-            st4n(A.out[1] + o, keep<MASK>(ey2, mq.ey), L.nval);
-            st4n(A.out[2] + o, keep<MASK>(ez2, mq.ez), L.nval);
+            stn(A.out[0] + o, keep<MASK>(ex2, mq.ex), L.nval);
+            stn(A.out[1] + o, keep<MASK>(ey2, mq.ey), L.nval);
+            stn(A.out[2] + o, keep<MASK>(ez2, mq.ez), L.nval);
             if (yl) {
-                const unsigned oy = (unsigned)psi_y(g, pm.W, L.c0, L.ly, q);
-                st4n(A.eout[1][0] + oy, keep<MASK>(S.yE0, mq.ex), L.nval);
-                st4n(A.eout[1][1] + oy, keep<MASK>(S.yE1, mq.ez), L.nval);
+                const unsigned oy = L.yoff + (unsigned)q * (unsigned)(pm.W * g.pitch);
+                stn(A.eout[1][0] + oy, S.yE0, L.nval);
+                stn(A.eout[1][1] + oy, S.yE1, L.nval);
             }
             if (HZ && lzq >= 0) {
-                const unsigned oz = (unsigned)psi_z(g, pm.W, L.c0, L.j, lzq);
-                st4n(A.eout[2][0] + oz, keep<MASK>(S.zE0, mq.ex), L.nval);
-                st4n(A.eout[2][1] + oz, keep<MASK>(S.zE1, mq.ey), L.nval);
+                const unsigned oz = L.zoff + (unsigned)lzq * (unsigned)(g.ny * g.pitch);
+                stn(A.eout[2][0] + oz, S.zE0, L.nval);
+                stn(A.eout[2][1] + oz, S.zE1, L.nval);
             }
             if (HX && L.xl) {
-                const unsigned ox = (unsigned)psi_x(g, pm.P, L.xpos, L.j, q);
-                st4n(A.eout[0][0] + ox, keep<MASK>(S.xE0, mq.ey), L.nval);
-                st4n(A.eout[0][1] + ox, keep<MASK>(S.xE1, mq.ez), L.nval);
+                const unsigned ox = L.xoff + (unsigned)q * (unsigned)A.xplane;
+                stn(A.eout[0][0] + ox, S.xE0, L.nval);
+                stn(A.eout[0][1] + ox, S.xE1, L.nval);
             }
         }
     }
@@ -491,40 +551,46 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
     return true;
 }
 
-template <bool HX, bool HY, bool HZ, bool MASK>
-__device__ __forceinline__ void march(const Args &A, const Maps &M, const Lane &L, const Blk &B, uint64_t *bar,
+template <int VW, bool HX, bool HY, bool HZ, bool MASK>
+__device__ __forceinline__ void march(const Args &A, const Maps &M, const Lane<VW> &L, const Blk &B, uint64_t *bar,
                                       float *ring, float *X, const float *CT) {
-    State S;
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    typedef typename Vec<VW>::T V;
+    State<V> S;
+    const V z4 = vzero<V>();
     S.ex1p = S.ey1p = S.ez1p = S.hx1p = S.hy1p = S.hz1p = S.hx2p = S.hy2p = z4;
     S.yH0 = S.yH1 = S.yE0 = S.yE1 = S.zH0 = S.zH1 = S.zE0 = S.zE1 = S.xH0 = S.xH1 = S.xE0 = S.xE1 = z4;
     RingPos rp{0, 1, 0u};   // two stages at least
     int pc = B.pbeg;
     for (int rel = 0; rel + 1 < B.nplanes; ++rel)
-        if (!plane<HX, HY, HZ, MASK>(A, M, L, B, bar, ring, X, CT, rel, rp, S, pc)) return;
+        if (!plane<VW, HX, HY, HZ, MASK>(A, M, L, B, bar, ring, X, CT, rel, rp, S, pc)) return;
 }
 
 // the instance of a block's case: which psi boxes it carries, whether it
 // meets a face of the grid
-template <bool HX, bool HY, bool HZ>
-__device__ __forceinline__ void march_edge(bool edge, const Args &A, const Maps &M, const Lane &L, const Blk &B,
+template <int VW, bool HX, bool HY, bool HZ>
+__device__ __forceinline__ void march_edge(bool edge, const Args &A, const Maps &M, const Lane<VW> &L, const Blk &B,
                                            uint64_t *bar, float *ring, float *X, const float *CT) {
-    if (edge) march<HX, HY, HZ, true>(A, M, L, B, bar, ring, X, CT);
-    else march<HX, HY, HZ, false>(A, M, L, B, bar, ring, X, CT);
+    if (edge) march<VW, HX, HY, HZ, true>(A, M, L, B, bar, ring, X, CT);
+    else march<VW, HX, HY, HZ, false>(A, M, L, B, bar, ring, X, CT);
 }
-template <bool HX, bool HY>
-__device__ __forceinline__ void march_z(bool hz, bool edge, const Args &A, const Maps &M, const Lane &L,
+template <int VW, bool HX, bool HY>
+__device__ __forceinline__ void march_z(bool hz, bool edge, const Args &A, const Maps &M, const Lane<VW> &L,
                                         const Blk &B, uint64_t *bar, float *ring, float *X, const float *CT) {
-    if (hz) march_edge<HX, HY, true>(edge, A, M, L, B, bar, ring, X, CT);
-    else march_edge<HX, HY, false>(edge, A, M, L, B, bar, ring, X, CT);
+    if (hz) march_edge<VW, HX, HY, true>(edge, A, M, L, B, bar, ring, X, CT);
+    else march_edge<VW, HX, HY, false>(edge, A, M, L, B, bar, ring, X, CT);
 }
 
-__global__ void __launch_bounds__(NT, 1) k_tb2(const Args A, const __grid_constant__ Maps M) {
+// one block per SM with float4 lanes (168 registers), two with float2 lanes
+template <int VW>
+__global__ void __launch_bounds__(NT, VW == 4 ? 1 : 2) k_tb2(const Args A, const __grid_constant__ Maps M) {
+    typedef Geo<VW> G;
+    constexpr int TXC = G::TXC, TXO = G::TXO, BOX = G::BOX, FIELDS = G::FIELDS, XBUF = G::XBUF, CX = G::CX,
+                  CY = G::CY, CZ = G::CZ;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
     float *X = reinterpret_cast<float *>(smem_raw + BAR_BYTES);   // exchange rows
     float *CT = X + 3 * XBUF;                                      // CPML coefficients
-    float *ring = X + head_floats(A.zt);                           // stage ring
+    float *ring = X + G::head_floats(A.zt);                        // stage ring
 
     const Grid &g = A.g;
     const Cpml &pm = A.pm;
@@ -616,25 +682,29 @@ __global__ void __launch_bounds__(NT, 1) k_tb2(const Args A, const __grid_consta
     }
     __syncthreads();
     if (tid == 0)
-        for (int r = 0; r < B.ns && r < B.nplanes; ++r) issue_plane(A, M, B, ring + r * B.stage, &bar[r], r);
+        for (int r = 0; r < B.ns && r < B.nplanes; ++r) issue_plane<VW>(A, M, B, ring + r * B.stage, &bar[r], r);
 
-    Lane L;
+    Lane<VW> L;
     L.lane = tid & 31;
     L.w = tid >> 5;
-    L.c0 = B.i0 - 4 + 4 * L.lane;
+    L.c0 = B.i0 - 4 + VW * L.lane;
     L.j = B.j0 - 2 + L.w;
     L.rowin = L.j >= 0 && L.j < g.ny;
     {
+        typedef typename Vec<VW>::T V;
         unsigned m[4];
-        for (int e = 0; e < 4; ++e) m[e] = (L.c0 + e >= 0 && L.c0 + e < g.nx) ? 0xffffffffu : 0u;
-        L.mcol = make_uint4(m[0], m[1], m[2], m[3]);
-        L.mcol0 = make_uint4(L.c0 == 0 ? 0u : m[0], m[1], m[2], m[3]);
+        for (int e = 0; e < VW; ++e) m[e] = (L.c0 + e >= 0 && L.c0 + e < g.nx) ? 0xffffffffu : 0u;
+        L.mcol = umask(m, V());
+        if (L.c0 == 0) m[0] = 0u;
+        L.mcol0 = umask(m, V());
     }
-    L.nval = L.c0 >= 0 && L.c0 < g.nx ? min(4, g.nx - L.c0) : 0;
-    L.own = L.lane >= 1 && L.lane <= 30 && L.w >= 2 && L.w <= TY + 1 && L.rowin && L.nval > 0;
+    L.nval = L.c0 >= 0 && L.c0 < g.nx ? min(VW, g.nx - L.c0) : 0;
+    L.own = L.lane >= G::LO && L.lane <= G::HI && L.w >= 2 && L.w <= TY + 1 && L.rowin && L.nval > 0;
     L.ly = (P > 0 && L.rowin) ? slab_cell(L.j, g.ny, P) : -1;
     L.xl = false;
     L.xs = L.xpos = 0;
+    L.yoff = L.ly >= 0 ? (unsigned)psi_y(g, pm.W, L.c0, L.ly, 0) : 0u;
+    L.zoff = (L.rowin && L.nval > 0) ? (unsigned)psi_z(g, pm.W, L.c0, L.j, 0) : 0u;
     if (B.hx && L.rowin && L.nval > 0) {
         if (B.xlo >= 0 && L.c0 < A.xlo4) {
             L.xl = true;
@@ -646,16 +716,17 @@ __global__ void __launch_bounds__(NT, 1) k_tb2(const Args A, const __grid_consta
             L.xs = B.xhi * B.xb + (L.c0 - A.xhb);
         }
     }
+    L.xoff = L.xl ? (unsigned)psi_x(g, P, L.xpos, L.j, 0) : 0u;
 
     // blocks whose computed region stays clear of the faces need no masks
     const bool edge = B.i0 - 4 < 1 || B.i0 + TXC - 5 > g.nx - 1 || B.j0 - 2 < 1 || B.j0 + TY > g.ny - 1 ||
                       B.k0 - 2 < 1 || B.k1 > g.nz - 1;
     if (B.hx) {
-        if (B.hy) march_z<true, true>(B.hz, edge, A, M, L, B, bar, ring, X, CT);
-        else march_z<true, false>(B.hz, edge, A, M, L, B, bar, ring, X, CT);
+        if (B.hy) march_z<VW, true, true>(B.hz, edge, A, M, L, B, bar, ring, X, CT);
+        else march_z<VW, true, false>(B.hz, edge, A, M, L, B, bar, ring, X, CT);
     } else {
-        if (B.hy) march_z<false, true>(B.hz, edge, A, M, L, B, bar, ring, X, CT);
-        else march_z<false, false>(B.hz, edge, A, M, L, B, bar, ring, X, CT);
+        if (B.hy) march_z<VW, false, true>(B.hz, edge, A, M, L, B, bar, ring, X, CT);
+        else march_z<VW, false, false>(B.hz, edge, A, M, L, B, bar, ring, X, CT);
     }
 }
 
@@ -663,6 +734,7 @@ constexpr CUtensorMapL2promotion kPromotion = CU_TENSOR_MAP_L2_PROMOTION_L2_128B
 
 struct HostState {
     Maps maps;
+    int vw, txc, txo;                          // lane width and the tile's columns
     int tiles_x, tiles_y, za, zb, cm, m, zt, chunks, ring;
     int xlo4, xhb, xbw;
     size_t smem;
@@ -703,7 +775,7 @@ int build_records(fdtd_ctx *h, HostState *st) {
                                 {i, j, k, 1},     {i, j, k - 1, 2}, {i, j, k, 2}};
         for (int s = 0; s < 6; ++s) {
             const int ci = cell[s][0], cj = cell[s][1], ck = cell[s][2];
-            const int b = chunk_of(st, ck) * tiles + (cj / TY) * st->tiles_x + ci / TXO;
+            const int b = chunk_of(st, ck) * tiles + (cj / TY) * st->tiles_x + ci / st->txo;
             recs.push_back({b, make_int4(ck, cj, ci, (6 * t + s) * 4 + cell[s][3])});
         }
     }
@@ -732,9 +804,22 @@ int build_records(fdtd_ctx *h, HostState *st) {
 
 }  // namespace
 
-const char *tb2_name() { return "tblock2-120x8"; }
+const char *tb2_name(const fdtd_ctx *h) {
+    const HostState *st = static_cast<const HostState *>(h->tb2);
+    return st && st->vw == 2 ? "tblock2-56x8" : "tblock2-120x8";
+}
 
-int tb2_prepare(fdtd_ctx *h) {
+int tb2_lane_width(const fdtd_ctx *h) {
+    const HostState *st = static_cast<const HostState *>(h->tb2);
+    return st ? st->vw : 0;
+}
+
+int tb2_prepare(fdtd_ctx *h, int vw) {
+    if (vw != 2 && vw != 4) return FDTD_ERR_ARG;
+    const int TXC = 32 * vw, TXO = TXC - 8;
+    const long long BOX = (long long)TXC * BR, FIELDS = 6 * BOX;
+    const int XBUF = NWR * 2 * TXC;
+    auto head_floats = [&](int zt) { return (3 * XBUF + 4 * TXC + 4 * BR + 4 * zt + 31) / 32 * 32; };
     const Grid &g = h->g;
     const int P = h->P;
     if (h->boundary == FDTD_MUR1) return FDTD_ERR_ARG;   // the Mur faces need E^{n+1} between the steps
@@ -749,6 +834,9 @@ int tb2_prepare(fdtd_ctx *h) {
     if (!encode) return FDTD_ERR_CUDA;
     HostState *st = new (std::nothrow) HostState();
     if (!st) return FDTD_ERR_OOM;
+    st->vw = vw;
+    st->txc = TXC;
+    st->txo = TXO;
     st->xlo4 = xlo4;
     st->xhb = xhb;
     st->xbw = xbw;
@@ -815,15 +903,26 @@ int tb2_prepare(fdtd_ctx *h) {
     st->chunks = st->m + (st->za > 0 ? 1 : 0) + (st->zb < g.nz ? 1 : 0);
     const int layer = std::max(st->za, g.nz - st->zb);
     st->zt = P > 0 ? layer + 4 : 1;
-    int max_smem = 0;
+    int max_smem = 0, per_sm = 0, reserved = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, h->dev);
+    const int full = max_smem;
+    if (vw == 2) {
+        // two blocks per SM: each takes half of the SM's shared memory (a grid
+        // whose largest stages need more gets one block per SM)
+        const int half = (per_sm - 2 * reserved) / 2 / 16 * 16;
+        if (half < max_smem) max_smem = half;
+    }
     const long long xb = (xbw * BR + 31) / 32 * 32;
     const long long big = FIELDS + 8 * xb + 8LL * BOX;   // largest stage: two x halves, y and z
-    const long long ring = (long long)max_smem / 4 - BAR_BYTES / 4 - head_floats(st->zt);
+    long long ring = (long long)max_smem / 4 - BAR_BYTES / 4 - head_floats(st->zt);
+    if (ring < 2 * big) ring = (long long)full / 4 - BAR_BYTES / 4 - head_floats(st->zt);
     st->ring = (int)ring;
     st->smem = BAR_BYTES + 4 * (size_t)(head_floats(st->zt) + st->ring);
+    const void *fn = vw == 4 ? reinterpret_cast<const void *>(k_tb2<4>) : reinterpret_cast<const void *>(k_tb2<2>);
     if (ring < 2 * big ||
-        cudaFuncSetAttribute(k_tb2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->smem) != cudaSuccess) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->smem) != cudaSuccess) {
         cudaGetLastError();
         delete st;
         return FDTD_ERR_CUDA;
@@ -872,6 +971,7 @@ void launch_tb2(fdtd_ctx *h, cudaStream_t s) {
     a.xlo4 = st->xlo4;
     a.xhb = st->xhb;
     a.xbw = st->xbw;
+    a.xplane = g.ny * (h->P > 0 ? psi_x_row(g.nx, h->P) : 0);
     a.cur = h->cur;
     a.ecur = h->ecur;
     a.src = h->src;
@@ -884,7 +984,8 @@ void launch_tb2(fdtd_ctx *h, cudaStream_t s) {
     a.pidx = st->d_idx;
     a.pbuf = st->d_pbuf;
     dim3 grid(st->tiles_x * st->tiles_y, st->chunks);
-    k_tb2<<<grid, NT, st->smem, s>>>(a, st->maps);
+    if (st->vw == 2) k_tb2<2><<<grid, NT, st->smem, s>>>(a, st->maps);
+    else k_tb2<4><<<grid, NT, st->smem, s>>>(a, st->maps);
 }
 
 float *tb2_probe_values(fdtd_ctx *h) {

@@ -25,7 +25,7 @@ def fd():
 
 # the field-update paths: 1 = vector-tile z-march (default), 2 = two steps per
 # pass (PEC and CPML grids), 0 = unfused sweeps
-@pytest.fixture(params=[1, 2, 0], ids=["vtile", "tblock2", "unfused"])
+@pytest.fixture(params=[1, 2, 3, 0], ids=["vtile", "tblock2", "tblock2-f2", "unfused"])
 def kernel(request):
     return request.param
 
@@ -66,11 +66,11 @@ def compare_fields(sim, ref, tol=TOL):
     return errs
 
 
-NAMES = {0: "unfused", 1: "fused-vtile", 2: "tblock2"}
+NAMES = {0: "unfused", 1: "fused-vtile", 2: "tblock2-120", 3: "tblock2-56"}
 
 
 def run_pair(fd, w, snaps, kernel=1):
-    if kernel == 2 and w.boundary == oracle.MUR1:
+    if kernel in (2, 3) and w.boundary == oracle.MUR1:
         pytest.skip("the two-step path runs PEC and CPML grids")
     sim = fd.Simulation.from_workload(w, kernel=kernel)
     assert sim.kernel_name.startswith(NAMES[kernel])
@@ -107,7 +107,7 @@ def test_gh_small_cpml(fd, kernel):
     run_pair(fd, w, [w.steps], kernel)
 
 
-@pytest.mark.parametrize("fused", [1, 2])
+@pytest.mark.parametrize("fused", [1, 2, 3])
 def test_fused_and_unfused_agree(fd, fused):
     """The paths compute the same update; they may differ only by FP32
     rounding (FMA contraction)."""

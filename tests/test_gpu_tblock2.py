@@ -36,7 +36,7 @@ def _seam_workload(nx, ny, nz, npml, steps, seed=5):
         w.z0 = 3 * w.dx
     lo = npml + 1
     pts = []
-    for i in (119, 120, 121, 239, 240):
+    for i in (55, 56, 57, 112, 119, 120, 121, 168, 239, 240):
         for j in (lo + 3, 16, 24, ny - lo - 1):
             if lo <= i <= nx - lo and lo <= j <= ny - lo:
                 pts.append((i, j, lo + 2 + (len(pts) * 7) % (nz - 2 * lo - 4)))
@@ -72,12 +72,13 @@ def _agree(fa, fb, ta, tb, tol=TOL):
     assert per[live].max() <= 10 * tol, per[live].max()
 
 
+@pytest.mark.parametrize("kernel", [2, 3], ids=["float4", "float2"])
 @pytest.mark.parametrize("dims,npml", [((250, 60, 180), 10), ((130, 48, 96), 6), ((245, 35, 60), 0)],
                          ids=["cpml10-3tiles", "cpml6-2tiles", "pec-3tiles"])
-def test_two_step_path_equals_one_step_path(fd, dims, npml):
+def test_two_step_path_equals_one_step_path(fd, dims, npml, kernel):
     steps = 150
     w = _seam_workload(*dims, npml, steps)
-    fa, ta, name = _run(fd, w, 2, [steps])
+    fa, ta, name = _run(fd, w, kernel, [steps])
     assert name.startswith("tblock2")
     fb, tb, _ = _run(fd, w, 1, [steps])
     _agree(fa, fb, ta, tb)
@@ -107,8 +108,10 @@ def test_kernel_switch_mid_run(fd):
     sim.step(9)
     sim.set_kernel(0)
     sim.step(3)
+    sim.set_kernel(3)
+    sim.step(20)
     sim.set_kernel(2)
-    sim.step(26)
+    sim.step(6)
     fa = [sim.field(c).astype(np.float64) for c in range(6)]
     ta = sim.probes().astype(np.float64)
     sim.close()
