@@ -105,15 +105,14 @@ static void timed_launch(fdtd_ctx *h, cudaStream_t st, void (*fn)(const fdtd_ctx
 int fdtd_step_on(fdtd_ctx *h, int n, cudaStream_t st) {
     for (int s = 0; s < n;) {
         int adv = 1;
-        const bool two = h->kernel == 2 || h->kernel == 3;
-        if (two && n - s >= 2) {
+        if (h->kernel == 2 && n - s >= 2) {
             // two steps in one pass; the detectors of both from its records
             timed_launch(h, st, [](const fdtd_ctx *c, cudaStream_t q) { launch_tb2(const_cast<fdtd_ctx *>(c), q); });
             if (h->np > 0) { launch_tb2_probes(h, st); h->launches++; }
             h->ecur ^= 1;
             adv = 2;
         } else {
-            if (h->kernel == 1 || (two && h->vtile)) {
+            if (h->kernel == 1 || (h->kernel == 2 && h->vtile)) {
                 timed_launch(h, st, [](const fdtd_ctx *c, cudaStream_t q) { launch_vtile(const_cast<fdtd_ctx *>(c), q); });
             } else {
                 timed_launch(h, st, launch_update_h);
@@ -256,7 +255,7 @@ int fdtd_create(fdtd_t *out, int nx, int ny, int nz, double dx, double dt, doubl
     h->watch_every = FDTD_WATCHDOG_DEFAULT_STEPS;
     h->kernel = 0;
     if (vtile_prepare(h) == FDTD_OK) h->kernel = 1;
-    if (tb2_prepare(h, 4) == FDTD_OK) h->kernel = 2;
+    if (tb2_prepare(h) == FDTD_OK) h->kernel = 2;
     cudaGetLastError();
     *out = h;
     return FDTD_OK;
@@ -571,7 +570,7 @@ int fdtd_timing_end(fdtd_t h, double *total_ms, int *launches) {
 int fdtd_timed_cells(fdtd_t h, int64_t *cells) {
     if (!h || !cells) return FDTD_ERR_ARG;
     const Grid &g = h->g;
-    *cells = (int64_t)g.nx * g.ny * g.nz * (h->kernel == 2 || h->kernel == 3 ? 2 : 1);
+    *cells = (int64_t)g.nx * g.ny * g.nz * (h->kernel == 2 ? 2 : 1);
     return FDTD_OK;
 }
 
@@ -583,7 +582,7 @@ int fdtd_launch_count(fdtd_t h, int64_t *launches) {
 
 const char *fdtd_kernel_name(fdtd_t h) {
     if (h && h->kernel == 1) return vtile_name();
-    if (h && (h->kernel == 2 || h->kernel == 3)) return tb2_name(h);
+    if (h && h->kernel == 2) return tb2_name(h);
     return "unfused-h-then-e";
 }
 
@@ -594,20 +593,12 @@ int fdtd_set_watchdog(fdtd_t h, int every) {
 }
 
 int fdtd_set_kernel(fdtd_t h, int which) {
-    if (!h || which < 0 || which > 3) return FDTD_ERR_ARG;
+    if (!h || which < 0 || which > 2) return FDTD_ERR_ARG;
     if (which == 1 && !h->vtile) return FDTD_ERR_ARG;
-    if (which >= 2) {
-        const int vw = which == 2 ? 4 : 2;
-        if (tb2_lane_width(h) != vw) {
-            if (h->boundary == FDTD_MUR1) return FDTD_ERR_ARG;
-            TRY(h, cudaStreamSynchronize(h->stream));   // the old records may be in use
-            tb2_release(h);
-            const int rc = tb2_prepare(h, vw);
-            if (rc != FDTD_OK) {
-                if (h->kernel >= 2) h->kernel = h->vtile ? 1 : 0;
-                return rc == FDTD_ERR_CUDA ? FDTD_ERR_CUDA : FDTD_ERR_ARG;
-            }
-        }
+    if (which == 2 && !h->tb2) {
+        if (h->boundary == FDTD_MUR1) return FDTD_ERR_ARG;
+        const int rc = tb2_prepare(h);
+        if (rc != FDTD_OK) return rc == FDTD_ERR_CUDA ? FDTD_ERR_CUDA : FDTD_ERR_ARG;
     }
     h->kernel = which;
     return FDTD_OK;

@@ -204,11 +204,10 @@ const char *vtile_name();
 void vtile_release(fdtd_ctx *h);
 
 // Two leapfrog steps per pass (temporal blocking, kernels_tb2.cu): tiles of
-// 8 rows and 32 lanes of vw columns (vw = 4: 120 owned columns, one block
-// per SM; vw = 2: 56 owned columns, two blocks per SM) recompute a 2-cell
-// halo of the first step
-int tb2_prepare(fdtd_ctx *h, int vw);
-int tb2_lane_width(const fdtd_ctx *h);                 // 0 when not prepared
+// 8 rows and 32 lanes recompute a 2-cell halo of the first step; float4
+// lanes (120 owned columns) between the x layers, scalar lanes (24 owned
+// columns) over them
+int tb2_prepare(fdtd_ctx *h);
 void launch_tb2(fdtd_ctx *h, cudaStream_t s);          // steps n, n+1
 void launch_tb2_probes(fdtd_ctx *h, cudaStream_t s);   // detector slots n, n+1 after launch_tb2
 const char *tb2_name(const fdtd_ctx *h);

@@ -7,7 +7,7 @@
 // the fields are read once and written once for two steps, 24 B + 24 B per
 // cell, so 24 B per cell-update instead of 48 B.
 //
-// Tiles.  A block owns 120 columns [i0, i0+120) (i0 = 120 tx) by TY = 8 rows
+// Tiles.  A wide block owns up to 120 columns [i0, i0+120) by TY = 8 rows
 // [j0, j0+8) and marches up a chunk of z planes [k0, k1).  It computes the
 // first step (level 1: H^{n+1/2}, E^{n+1}) on a larger region and the second
 // (level 2: H^{n+3/2}, E^{n+2}) on its own cells:
@@ -19,6 +19,10 @@
 //   warps: warp w (0..10) is row j0-2+w; level-1 H on rows j0-2 .. j0+8,
 //     level-1 E on j0-1 .. j0+8, level-2 H on j0-1 .. j0+7, level-2 E on the
 //     owned rows (y neighbours through shared exchange rows).
+// On a CPML grid the x layers belong to narrow blocks (scalar lanes: 32
+// computed columns, 24 owned), and the wide blocks lie where neither their
+// owned cells nor the halo values those depend on (columns i0-2 .. end) meet
+// an x layer, so the wide blocks carry no x CPML code at all (tile_col).
 // Every value of the halo is computed from the same inputs with the same
 // arithmetic as by the tile that owns it, so it is that tile's value; values
 // of nodes outside the grid, and the components a cell owns on the grid's low
@@ -74,7 +78,8 @@ constexpr int NSMAX = 8;
 constexpr int BAR_BYTES = 128;
 static_assert(NSMAX * 8 <= BAR_BYTES, "barrier area");
 
-// Tile geometry for lanes of VW columns (VW = 4: float4, VW = 2: float2)
+// Tile geometry for lanes of VW columns (VW = 4: float4 lanes of the wide
+// tiles; VW = 1: scalar lanes of the narrow tiles over the x layers)
 template <int VW>
 struct Geo {
     static constexpr int TXC = 32 * VW;          // computed columns i0-4 .. i0+TXC-5
@@ -95,40 +100,40 @@ struct Geo {
     __host__ __device__ static constexpr int head_floats(int zt) { return (3 * XBUF + CZ + 4 * zt + 31) / 32 * 32; }
 };
 
-// ---- lane vectors: the same code for float4 and float2 lanes ----
+// ---- lane vectors: the same code for float4 and scalar lanes ----
 template <int VW> struct Vec;
 template <> struct Vec<4> { typedef float4 T; typedef uint4 U; };
-template <> struct Vec<2> { typedef float2 T; typedef uint2 U; };
+template <> struct Vec<1> { typedef float T; typedef unsigned U; };
 
 template <typename V> __device__ __forceinline__ V ldv(const float *p) { return *reinterpret_cast<const V *>(p); }
 template <typename V> __device__ __forceinline__ void stv(float *p, V v) { *reinterpret_cast<V *>(p) = v; }
 template <typename V> __device__ __forceinline__ V vzero();
 template <> __device__ __forceinline__ float4 vzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
-// the float4 forms (tma_pipe.cuh) in the same overload sets as the float2 forms
+template <> __device__ __forceinline__ float vzero<float>() { return 0.f; }
+__device__ __forceinline__ float axpy(float a, float s, float d) { return a + s * d; }
+__device__ __forceinline__ float cpmls(float &psi, float a, float b, float d) { return cpml1(psi, a, b, d); }
+__device__ __forceinline__ float cpmlv(float &psi, float a, float b, float d) { return cpml1(psi, a, b, d); }
+__device__ __forceinline__ float first(float v) { return v; }
+__device__ __forceinline__ float last(float v) { return v; }
+__device__ __forceinline__ float right(float, float r) { return r; }
+__device__ __forceinline__ float left(float, float l) { return l; }
+__device__ __forceinline__ float elem(float v, int) { return v; }
+__device__ __forceinline__ unsigned umask(const unsigned *m, float) { return m[0]; }
+__device__ __forceinline__ void stn(float *p, float v, int) { *p = v; }
+__device__ __forceinline__ void add_source(float &v, const Source &s, const SourceStep &w, int c0, int j, int k) {
+    v += source_at(s, w, c0, j, k);
+}
+// the float4 forms (tma_pipe.cuh) in the same overload sets as the scalar forms
 using tma::axpy;
 using tma::cpmlv;
 using tma::operator-;
-__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 axpy(float2 a, float s, float2 d) { return make_float2(a.x + s * d.x, a.y + s * d.y); }
 __device__ __forceinline__ float4 cpmls(float4 &psi, float a, float b, float4 d) { return cpml4(psi, a, b, d); }
-__device__ __forceinline__ float2 cpmls(float2 &psi, float a, float b, float2 d) {
-    return make_float2(cpml1(psi.x, a, b, d.x), cpml1(psi.y, a, b, d.y));
-}
-__device__ __forceinline__ float2 cpmlv(float2 &psi, float2 a, float2 b, float2 d) {
-    return make_float2(cpml1(psi.x, a.x, b.x, d.x), cpml1(psi.y, a.y, b.y, d.y));
-}
 __device__ __forceinline__ float first(float4 v) { return v.x; }
-__device__ __forceinline__ float first(float2 v) { return v.x; }
 __device__ __forceinline__ float last(float4 v) { return v.w; }
-__device__ __forceinline__ float last(float2 v) { return v.y; }
 // the vector one column to the right (x+1) / left (x-1), edge element given
 __device__ __forceinline__ float4 right(float4 v, float r) { return make_float4(v.y, v.z, v.w, r); }
 __device__ __forceinline__ float4 left(float4 v, float l) { return make_float4(l, v.x, v.y, v.z); }
-__device__ __forceinline__ float2 right(float2 v, float r) { return make_float2(v.y, r); }
-__device__ __forceinline__ float2 left(float2 v, float l) { return make_float2(l, v.x); }
 __device__ __forceinline__ float elem(float4 v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
-__device__ __forceinline__ float elem(float2 v, int e) { return e == 0 ? v.x : v.y; }
 // v with the elements outside the mask set to +0 (bitwise, so a non-finite
 // value outside the state never leaks in)
 __device__ __forceinline__ float mk(float v, unsigned b) { return __uint_as_float(__float_as_uint(v) & b); }
@@ -138,21 +143,16 @@ __device__ __forceinline__ float4 keep(float4 v, uint4 b) {
     return make_float4(mk(v.x, b.x), mk(v.y, b.y), mk(v.z, b.z), mk(v.w, b.w));
 }
 template <bool MASK>
-__device__ __forceinline__ float2 keep(float2 v, uint2 b) {
+__device__ __forceinline__ float keep(float v, unsigned b) {
     if (!MASK) return v;
-    return make_float2(mk(v.x, b.x), mk(v.y, b.y));
+    return mk(v, b);
 }
 template <typename U> __device__ __forceinline__ U uzero();
 template <> __device__ __forceinline__ uint4 uzero<uint4>() { return make_uint4(0u, 0u, 0u, 0u); }
-template <> __device__ __forceinline__ uint2 uzero<uint2>() { return make_uint2(0u, 0u); }
+template <> __device__ __forceinline__ unsigned uzero<unsigned>() { return 0u; }
 __device__ __forceinline__ uint4 umask(const unsigned *m, float4) { return make_uint4(m[0], m[1], m[2], m[3]); }
-__device__ __forceinline__ uint2 umask(const unsigned *m, float2) { return make_uint2(m[0], m[1]); }
 // store the first n (1..VW) elements; one vector store when n == VW
 __device__ __forceinline__ void stn(float *p, float4 v, int n) { st4n(p, v, n); }
-__device__ __forceinline__ void stn(float *p, float2 v, int n) {
-    if (n == 2) *reinterpret_cast<float2 *>(p) = v;
-    else p[0] = v.x;
-}
 // the shower's current on the lane's Ez edges
 __device__ __forceinline__ void add_source(float4 &v, const Source &s, const SourceStep &w, int c0, int j, int k) {
     v.x += source_at(s, w, c0, j, k);
@@ -160,27 +160,51 @@ __device__ __forceinline__ void add_source(float4 &v, const Source &s, const Sou
     v.z += source_at(s, w, c0 + 2, j, k);
     v.w += source_at(s, w, c0 + 3, j, k);
 }
-__device__ __forceinline__ void add_source(float2 &v, const Source &s, const SourceStep &w, int c0, int j, int k) {
-    v.x += source_at(s, w, c0, j, k);
-    v.y += source_at(s, w, c0 + 1, j, k);
-}
 
+// Tensor maps; fields and y/z psi per tile width (wd 0: float4 lanes, 128
+// columns; wd 1: scalar lanes, 32 columns)
 struct Maps {
-    CUtensorMap f[2][6];    // fields [set][component]
+    CUtensorMap f[2][2][6]; // fields [wd][set][component]
     CUtensorMap x[4][2];    // psi x: xHy, xHz [field set], xEy, xEz [E psi set]
-    CUtensorMap y[4][2];    // psi y: yHx, yHz, yEx, yEz
-    CUtensorMap z[4][2];    // psi z: zHx, zHy, zEx, zEy
+    CUtensorMap y[2][4][2]; // psi y [wd]: yHx, yHz, yEx, yEz
+    CUtensorMap z[2][4][2]; // psi z [wd]: zHx, zHy, zEx, zEy
 };
+
+// Tile columns: nl narrow ones (scalar lanes, up to 24 owned columns) over
+// [0, a), nw wide ones (float4 lanes, up to 120) over [a, b), then narrow ones
+// over [b, nx).  On a CPML grid the wide tiles stay clear of the x layers
+// (their owned results depend on columns i0-2 .. end+1 only), so the x layers'
+// CPML memory is updated by the narrow tiles alone, one column per lane.
+struct TileCol {
+    int i0, w, vw;
+};
+__host__ __device__ inline TileCol tile_col(int tc, int a, int b, int nl, int nw, int nx) {
+    TileCol t;
+    if (tc < nl) {
+        t.i0 = 24 * tc;
+        t.w = a - t.i0 < 24 ? a - t.i0 : 24;
+        t.vw = 1;
+    } else if (tc < nl + nw) {
+        t.i0 = a + 120 * (tc - nl);
+        t.w = b - t.i0 < 120 ? b - t.i0 : 120;
+        t.vw = 4;
+    } else {
+        t.i0 = b + 24 * (tc - nl - nw);
+        t.w = nx - t.i0 < 24 ? nx - t.i0 : 24;
+        t.vw = 1;
+    }
+    return t;
+}
 
 struct Args {
     Grid g;
     float *out[6];          // output field set
     Cpml pm;                // psi read (hin: H set cur, e: E set ecur) and coefficients
     float *eout[3][2];      // E psi written (set ecur^1); H psi: pm.hout
-    int tiles_x, tiles_y;
+    int ta, tb, nl, nw, tiles_x, tiles_y;   // tile columns (tile_col), tiles_x = their number
     int za, zb, cm, m;      // z chunks: m of cm planes over [za, zb), then [0, za), [zb, nz)
     int zt;                 // planes of the z coefficient table
-    int ring;               // floats of the stage ring
+    int smem_floats;        // floats of dynamic shared memory after the barriers
     int xlo4, xhb, xbw;     // x psi: high half start, first column of the high half, box width
     int xplane;             // floats of an x psi plane (ny rows)
     int cur, ecur;
@@ -195,6 +219,7 @@ struct Args {
 
 struct Blk {
     int i0, j0, k0, k1, kstart, nplanes;
+    int iend;               // end of the owned columns
     bool src_blk, hx, hy, hz;
     int l0;                 // first y slab row of the y box
     int xo, yo, zo, stage, ns;
@@ -213,8 +238,9 @@ __device__ __forceinline__ void issue_plane(const Args &A, const Maps &M, const 
     if (B.hy) bytes += 16u * G::BOX;
     if (lz >= 0) bytes += 16u * G::BOX;
     mbar_expect_tx(bar, bytes);
+    constexpr int WD = VW == 4 ? 0 : 1;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) tma_load(st + c * G::BOX, &M.f[A.cur][c], bar, B.i0 - 4, B.j0 - 2, p);
+    for (int c = 0; c < 6; ++c) tma_load(st + c * G::BOX, &M.f[WD][A.cur][c], bar, B.i0 - 4, B.j0 - 2, p);
     if (B.hx)
         for (int a = 0; a < 4; ++a) {
             float *d = st + B.xo + a * B.nxb * B.xb;
@@ -223,9 +249,11 @@ __device__ __forceinline__ void issue_plane(const Args &A, const Maps &M, const 
             if (B.xhi >= 0) tma_load(d + B.xhi * B.xb, mp, bar, A.xlo4, B.j0 - 2, p);
         }
     if (B.hy)
-        for (int a = 0; a < 4; ++a) tma_load(st + B.yo + a * G::BOX, &M.y[a][a < 2 ? A.cur : A.ecur], bar, B.i0 - 4, B.l0, p);
+        for (int a = 0; a < 4; ++a)
+            tma_load(st + B.yo + a * G::BOX, &M.y[WD][a][a < 2 ? A.cur : A.ecur], bar, B.i0 - 4, B.l0, p);
     if (lz >= 0)
-        for (int a = 0; a < 4; ++a) tma_load(st + B.zo + a * G::BOX, &M.z[a][a < 2 ? A.cur : A.ecur], bar, B.i0 - 4, B.j0 - 2, lz);
+        for (int a = 0; a < 4; ++a)
+            tma_load(st + B.zo + a * G::BOX, &M.z[WD][a][a < 2 ? A.cur : A.ecur], bar, B.i0 - 4, B.j0 - 2, lz);
 }
 
 template <int VW>
@@ -580,11 +608,11 @@ __device__ __forceinline__ void march_z(bool hz, bool edge, const Args &A, const
     else march_edge<VW, HX, HY, false>(edge, A, M, L, B, bar, ring, X, CT);
 }
 
-// one block per SM with float4 lanes (168 registers), two with float2 lanes
+// one block of the launch: tile column T, tile row ty
 template <int VW>
-__global__ void __launch_bounds__(NT, VW == 4 ? 1 : 2) k_tb2(const Args A, const __grid_constant__ Maps M) {
+__device__ __forceinline__ void run_block(const Args &A, const Maps &M, const TileCol T, int ty) {
     typedef Geo<VW> G;
-    constexpr int TXC = G::TXC, TXO = G::TXO, BOX = G::BOX, FIELDS = G::FIELDS, XBUF = G::XBUF, CX = G::CX,
+    constexpr int TXC = G::TXC, BOX = G::BOX, FIELDS = G::FIELDS, XBUF = G::XBUF, CX = G::CX,
                   CY = G::CY, CZ = G::CZ;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
@@ -598,8 +626,8 @@ __global__ void __launch_bounds__(NT, VW == 4 ? 1 : 2) k_tb2(const Args A, const
     const int tid = threadIdx.x;
     Blk B;
     const int tile = (int)blockIdx.x;
-    const int tx = tile % A.tiles_x, ty = tile / A.tiles_x;
-    B.i0 = tx * TXO;
+    B.i0 = T.i0;
+    B.iend = T.i0 + T.w;
     B.j0 = ty * TY;
     {
         // chunk-major launch order: the middle chunks first, the two layer
@@ -631,8 +659,8 @@ __global__ void __launch_bounds__(NT, VW == 4 ? 1 : 2) k_tb2(const Args A, const
     B.xb = (A.xbw * BR + 31) / 32 * 32;
     if (P > 0) {
         const int ilo = max(B.i0 - 4, 0), ihi = min(B.i0 + TXC - 5, g.nx - 1);
-        if (ilo <= P) B.xlo = B.nxb++;
-        if (ihi >= g.nx - P) B.xhi = B.nxb++;
+        if (VW == 1 && ilo <= P) B.xlo = B.nxb++;
+        if (VW == 1 && ihi >= g.nx - P) B.xhi = B.nxb++;
         B.hx = B.nxb > 0;
         int lmin = 1 << 30;
         for (int j = max(B.j0 - 2, 0); j < min(B.j0 + TY + 2, g.ny); ++j) {
@@ -646,7 +674,7 @@ __global__ void __launch_bounds__(NT, VW == 4 ? 1 : 2) k_tb2(const Args A, const
     B.yo = B.xo + 4 * B.nxb * B.xb;
     B.zo = B.yo + (B.hy ? 4 * BOX : 0);
     B.stage = B.zo + (B.hz ? 4 * BOX : 0);
-    B.ns = min(NSMAX, A.ring / B.stage);
+    B.ns = min(NSMAX, (A.smem_floats - G::head_floats(A.zt)) / B.stage);
 
     if (tid == 0) {
         for (int s = 0; s < B.ns; ++s) mbar_init(&bar[s], 1);
@@ -699,7 +727,9 @@ __global__ void __launch_bounds__(NT, VW == 4 ? 1 : 2) k_tb2(const Args A, const
         L.mcol0 = umask(m, V());
     }
     L.nval = L.c0 >= 0 && L.c0 < g.nx ? min(VW, g.nx - L.c0) : 0;
-    L.own = L.lane >= G::LO && L.lane <= G::HI && L.w >= 2 && L.w <= TY + 1 && L.rowin && L.nval > 0;
+    L.own = L.lane >= G::LO && L.lane <= G::HI && L.w >= 2 && L.w <= TY + 1 && L.rowin && L.nval > 0 &&
+            L.c0 < B.iend;
+    if (L.own) L.nval = min(L.nval, B.iend - L.c0);
     L.ly = (P > 0 && L.rowin) ? slab_cell(L.j, g.ny, P) : -1;
     L.xl = false;
     L.xs = L.xpos = 0;
@@ -721,21 +751,34 @@ __global__ void __launch_bounds__(NT, VW == 4 ? 1 : 2) k_tb2(const Args A, const
     // blocks whose computed region stays clear of the faces need no masks
     const bool edge = B.i0 - 4 < 1 || B.i0 + TXC - 5 > g.nx - 1 || B.j0 - 2 < 1 || B.j0 + TY > g.ny - 1 ||
                       B.k0 - 2 < 1 || B.k1 > g.nz - 1;
-    if (B.hx) {
-        if (B.hy) march_z<VW, true, true>(B.hz, edge, A, M, L, B, bar, ring, X, CT);
-        else march_z<VW, true, false>(B.hz, edge, A, M, L, B, bar, ring, X, CT);
-    } else {
+    if (VW == 1) {   // the narrow tiles of the x layers: always with masks
+        if (B.hx) {
+            if (B.hy) march_z<VW, true, true>(B.hz, true, A, M, L, B, bar, ring, X, CT);
+            else march_z<VW, true, false>(B.hz, true, A, M, L, B, bar, ring, X, CT);
+        } else {
+            if (B.hy) march_z<VW, false, true>(B.hz, true, A, M, L, B, bar, ring, X, CT);
+            else march_z<VW, false, false>(B.hz, true, A, M, L, B, bar, ring, X, CT);
+        }
+    } else {         // the wide tiles never meet an x layer
         if (B.hy) march_z<VW, false, true>(B.hz, edge, A, M, L, B, bar, ring, X, CT);
         else march_z<VW, false, false>(B.hz, edge, A, M, L, B, bar, ring, X, CT);
     }
+}
+
+__global__ void __launch_bounds__(NT, 1) k_tb2(const Args A, const __grid_constant__ Maps M) {
+    const int tile = (int)blockIdx.x;
+    const int ty = tile / A.tiles_x;
+    const TileCol T = tile_col(tile - ty * A.tiles_x, A.ta, A.tb, A.nl, A.nw, A.g.nx);
+    if (T.vw == 1) run_block<1>(A, M, T, ty);
+    else run_block<4>(A, M, T, ty);
 }
 
 constexpr CUtensorMapL2promotion kPromotion = CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
 
 struct HostState {
     Maps maps;
-    int vw, txc, txo;                          // lane width and the tile's columns
-    int tiles_x, tiles_y, za, zb, cm, m, zt, chunks, ring;
+    int ta, tb, nl, nw;                        // tile columns (tile_col)
+    int tiles_x, tiles_y, za, zb, cm, m, zt, chunks, smem_floats;
     int xlo4, xhb, xbw;
     size_t smem;
     // detector records, rebuilt when the handle's detectors change
@@ -746,6 +789,16 @@ struct HostState {
     int *d_idx;
     float *d_pbuf;
 };
+
+// tile column of column i (tile_col inverted)
+int tile_of(const HostState *st, int i, int nx) {
+    i = std::min(std::max(i, 0), nx - 1);   // a readout cell outside the grid: the edge tile
+    int tc;
+    if (i < st->ta) tc = i / 24;
+    else if (i < st->tb) tc = st->nl + (i - st->ta) / 120;
+    else tc = st->nl + st->nw + (i - st->tb) / 24;
+    return tc;
+}
 
 // chunk of plane k (the kernel's chunk decoding, inverted)
 int chunk_of(const HostState *st, int k) {
@@ -775,7 +828,7 @@ int build_records(fdtd_ctx *h, HostState *st) {
                                 {i, j, k, 1},     {i, j, k - 1, 2}, {i, j, k, 2}};
         for (int s = 0; s < 6; ++s) {
             const int ci = cell[s][0], cj = cell[s][1], ck = cell[s][2];
-            const int b = chunk_of(st, ck) * tiles + (cj / TY) * st->tiles_x + ci / st->txo;
+            const int b = chunk_of(st, ck) * tiles + (cj / TY) * st->tiles_x + tile_of(st, ci, h->g.nx);
             recs.push_back({b, make_int4(ck, cj, ci, (6 * t + s) * 4 + cell[s][3])});
         }
     }
@@ -804,22 +857,11 @@ int build_records(fdtd_ctx *h, HostState *st) {
 
 }  // namespace
 
-const char *tb2_name(const fdtd_ctx *h) {
-    const HostState *st = static_cast<const HostState *>(h->tb2);
-    return st && st->vw == 2 ? "tblock2-56x8" : "tblock2-120x8";
-}
+const char *tb2_name(const fdtd_ctx *) { return "tblock2-120x8"; }
 
-int tb2_lane_width(const fdtd_ctx *h) {
-    const HostState *st = static_cast<const HostState *>(h->tb2);
-    return st ? st->vw : 0;
-}
-
-int tb2_prepare(fdtd_ctx *h, int vw) {
-    if (vw != 2 && vw != 4) return FDTD_ERR_ARG;
-    const int TXC = 32 * vw, TXO = TXC - 8;
-    const long long BOX = (long long)TXC * BR, FIELDS = 6 * BOX;
-    const int XBUF = NWR * 2 * TXC;
-    auto head_floats = [&](int zt) { return (3 * XBUF + 4 * TXC + 4 * BR + 4 * zt + 31) / 32 * 32; };
+int tb2_prepare(fdtd_ctx *h) {
+    typedef Geo<4> G4;
+    typedef Geo<1> G1;
     const Grid &g = h->g;
     const int P = h->P;
     if (h->boundary == FDTD_MUR1) return FDTD_ERR_ARG;   // the Mur faces need E^{n+1} between the steps
@@ -834,17 +876,16 @@ int tb2_prepare(fdtd_ctx *h, int vw) {
     if (!encode) return FDTD_ERR_CUDA;
     HostState *st = new (std::nothrow) HostState();
     if (!st) return FDTD_ERR_OOM;
-    st->vw = vw;
-    st->txc = TXC;
-    st->txo = TXO;
     st->xlo4 = xlo4;
     st->xhb = xhb;
     st->xbw = xbw;
     bool ok = true;
-    for (int s = 0; s < 2; ++s)
-        for (int c = 0; c < 6; ++c)
-            ok = ok && encode3(encode, &st->maps.f[s][c], h->fields[s] + (size_t)c * g.comp, g.nx + 1, g.ny + 1,
-                               g.nz + 1, g.pitch, g.plane, TXC, BR, kPromotion);
+    const int TXCW[2] = {G4::TXC, G1::TXC};   // box width of the wide and the narrow tiles
+    for (int wd = 0; wd < 2; ++wd)
+        for (int s = 0; s < 2; ++s)
+            for (int c = 0; c < 6; ++c)
+                ok = ok && encode3(encode, &st->maps.f[wd][s][c], h->fields[s] + (size_t)c * g.comp, g.nx + 1,
+                                   g.ny + 1, g.nz + 1, g.pitch, g.plane, TXCW[wd], BR, kPromotion);
     if (P > 0) {
         // H psi sets follow the field set; E psi sets are psi_block's first
         // third and epsi2
@@ -860,13 +901,17 @@ int tb2_prepare(fdtd_ctx *h, int vw) {
                     for (int half = 0; half < 2; ++half) {
                         const float *base = half == 0 ? hp : ep;
                         const int a = 2 * half + t;
-                        CUtensorMap *m = axis == 0 ? &st->maps.x[a][s] : axis == 1 ? &st->maps.y[a][s] : &st->maps.z[a][s];
                         if (axis == 0)
-                            ok = ok && encode3(encode, m, base, WX, g.ny, g.nz, WX, (cuuint64_t)g.ny * WX, xbw, BR, kPromotion);
-                        else if (axis == 1)
-                            ok = ok && encode3(encode, m, base, g.nx, W, g.nz, g.pitch, (cuuint64_t)W * g.pitch, TXC, BR, kPromotion);
-                        else
-                            ok = ok && encode3(encode, m, base, g.nx, g.ny, W, g.pitch, (cuuint64_t)g.ny * g.pitch, TXC, BR, kPromotion);
+                            ok = ok && encode3(encode, &st->maps.x[a][s], base, WX, g.ny, g.nz, WX,
+                                               (cuuint64_t)g.ny * WX, xbw, BR, kPromotion);
+                        for (int wd = 0; wd < 2 && axis > 0; ++wd) {
+                            if (axis == 1)
+                                ok = ok && encode3(encode, &st->maps.y[wd][a][s], base, g.nx, W, g.nz, g.pitch,
+                                                   (cuuint64_t)W * g.pitch, TXCW[wd], BR, kPromotion);
+                            else
+                                ok = ok && encode3(encode, &st->maps.z[wd][a][s], base, g.nx, g.ny, W, g.pitch,
+                                                   (cuuint64_t)g.ny * g.pitch, TXCW[wd], BR, kPromotion);
+                        }
                     }
                 }
         }
@@ -875,7 +920,27 @@ int tb2_prepare(fdtd_ctx *h, int vw) {
         delete st;
         return FDTD_ERR_CUDA;
     }
-    st->tiles_x = (g.nx + TXO - 1) / TXO;
+    // tile columns: narrow tiles over the x layers [0, a), [b, nx) (a, b
+    // multiples of 4 with a - 2 > P and b + 1 < nx - P), wide tiles between;
+    // a grid too narrow for a wide part is all narrow tiles
+    if (P > 0) {
+        st->ta = (P + 3 + 3) / 4 * 4;
+        st->tb = (g.nx - P - 2) / 4 * 4;
+        if (st->tb - st->ta < 24) st->ta = st->tb = g.nx;
+    } else {
+        st->ta = st->tb = 0;
+    }
+    if (P == 0) {
+        st->nl = 0;
+        st->nw = (g.nx + G4::TXO - 1) / G4::TXO;
+        st->tiles_x = st->nw;
+        st->ta = 0;
+        st->tb = g.nx;
+    } else {
+        st->nl = (st->ta + G1::TXO - 1) / G1::TXO;
+        st->nw = (st->tb - st->ta + G4::TXO - 1) / G4::TXO;
+        st->tiles_x = st->nl + st->nw + (g.nx - st->tb + G1::TXO - 1) / G1::TXO;
+    }
     st->tiles_y = (g.ny + TY - 1) / TY;
     // z chunks: the planes of a middle chunk (k0-2 .. k1+1) stay clear of the
     // z layers, so only the two layer chunks [0, za), [zb, nz) carry z boxes;
@@ -903,26 +968,18 @@ int tb2_prepare(fdtd_ctx *h, int vw) {
     st->chunks = st->m + (st->za > 0 ? 1 : 0) + (st->zb < g.nz ? 1 : 0);
     const int layer = std::max(st->za, g.nz - st->zb);
     st->zt = P > 0 ? layer + 4 : 1;
-    int max_smem = 0, per_sm = 0, reserved = 0;
+    int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->dev);
-    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->dev);
-    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, h->dev);
-    const int full = max_smem;
-    if (vw == 2) {
-        // two blocks per SM: each takes half of the SM's shared memory (a grid
-        // whose largest stages need more gets one block per SM)
-        const int half = (per_sm - 2 * reserved) / 2 / 16 * 16;
-        if (half < max_smem) max_smem = half;
-    }
     const long long xb = (xbw * BR + 31) / 32 * 32;
-    const long long big = FIELDS + 8 * xb + 8LL * BOX;   // largest stage: two x halves, y and z
-    long long ring = (long long)max_smem / 4 - BAR_BYTES / 4 - head_floats(st->zt);
-    if (ring < 2 * big) ring = (long long)full / 4 - BAR_BYTES / 4 - head_floats(st->zt);
-    st->ring = (int)ring;
-    st->smem = BAR_BYTES + 4 * (size_t)(head_floats(st->zt) + st->ring);
-    const void *fn = vw == 4 ? reinterpret_cast<const void *>(k_tb2<4>) : reinterpret_cast<const void *>(k_tb2<2>);
-    if (ring < 2 * big ||
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->smem) != cudaSuccess) {
+    // largest stages: wide tiles with y and z boxes; narrow ones with two x
+    // halves, y and z
+    const long long big4 = G4::FIELDS + 8LL * G4::BOX;
+    const long long big1 = G1::FIELDS + 8 * xb + 8LL * G1::BOX;
+    const long long floats = (long long)max_smem / 4 - BAR_BYTES / 4;
+    st->smem_floats = (int)floats;
+    st->smem = 4 * (size_t)floats + BAR_BYTES;
+    if (floats - G4::head_floats(st->zt) < 2 * big4 || floats - G1::head_floats(st->zt) < 2 * big1 ||
+        cudaFuncSetAttribute(k_tb2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st->smem) != cudaSuccess) {
         cudaGetLastError();
         delete st;
         return FDTD_ERR_CUDA;
@@ -960,6 +1017,10 @@ void launch_tb2(fdtd_ctx *h, cudaStream_t s) {
     h->ecur ^= 1;
     for (int ax = 0; ax < 3; ++ax)
         for (int t = 0; t < 2; ++t) a.eout[ax][t] = other.e[ax][t];
+    a.ta = st->ta;
+    a.tb = st->tb;
+    a.nl = st->nl;
+    a.nw = st->nw;
     a.tiles_x = st->tiles_x;
     a.tiles_y = st->tiles_y;
     a.za = st->za;
@@ -967,7 +1028,7 @@ void launch_tb2(fdtd_ctx *h, cudaStream_t s) {
     a.cm = st->cm;
     a.m = st->m;
     a.zt = st->zt;
-    a.ring = st->ring;
+    a.smem_floats = st->smem_floats;
     a.xlo4 = st->xlo4;
     a.xhb = st->xhb;
     a.xbw = st->xbw;
@@ -984,8 +1045,7 @@ void launch_tb2(fdtd_ctx *h, cudaStream_t s) {
     a.pidx = st->d_idx;
     a.pbuf = st->d_pbuf;
     dim3 grid(st->tiles_x * st->tiles_y, st->chunks);
-    if (st->vw == 2) k_tb2<2><<<grid, NT, st->smem, s>>>(a, st->maps);
-    else k_tb2<4><<<grid, NT, st->smem, s>>>(a, st->maps);
+    k_tb2<<<grid, NT, st->smem, s>>>(a, st->maps);
 }
 
 float *tb2_probe_values(fdtd_ctx *h) {
