@@ -926,7 +926,21 @@ int tb2_prepare(fdtd_ctx *h) {
     if (P > 0) {
         st->ta = (P + 3 + 3) / 4 * 4;
         st->tb = (g.nx - P - 2) / 4 * 4;
-        if (st->tb - st->ta < 24) st->ta = st->tb = g.nx;
+        if (st->tb - st->ta < 24) {
+            st->ta = st->tb = g.nx;
+        } else {
+            // a last wide tile of r < 120 columns costs a whole wide block:
+            // move those columns to the narrow tiles where their last tiles
+            // have room for them
+            const int r = (st->tb - st->ta) % G4::TXO;
+            const int room_l = (st->ta + 23) / 24 * 24 - st->ta;
+            const int room_r = ((g.nx - st->tb + 23) / 24 * 24 - (g.nx - st->tb)) / 4 * 4;
+            if (r > 0 && st->tb - st->ta > G4::TXO && r <= room_l + room_r) {
+                const int dl = std::min(r, room_l);
+                st->ta += dl;
+                st->tb -= r - dl;
+            }
+        }
     } else {
         st->ta = st->tb = 0;
     }

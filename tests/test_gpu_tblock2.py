@@ -31,12 +31,19 @@ def _seams(nx, npml):
     """First columns of the two-step path's tiles: narrow tiles of 24 columns
     over [0, a) and [b, nx), wide ones of 120 over [a, b), where a and b are
     multiples of four clear of the x layers by two cells (all narrow when the
-    wide part would be shorter than 24 columns; all wide on a PEC grid)."""
+    wide part would be shorter than 24 columns; all wide on a PEC grid); the
+    columns of a short last wide tile move to the narrow tiles where those
+    have room."""
     if npml == 0:
         return list(range(0, nx, 120))
     a, b = (npml + 6) // 4 * 4, (nx - npml - 2) // 4 * 4
     if b - a < 24:
         return list(range(0, nx, 24))
+    r = (b - a) % 120   # a short last wide tile goes to room in the narrow tiles
+    room_l, room_r = -a % 24, (-(nx - b) % 24) // 4 * 4
+    if 0 < r <= room_l + room_r and b - a > 120:
+        dl = min(r, room_l)
+        a, b = a + dl, b - (r - dl)
     return list(range(0, a, 24)) + list(range(a, b, 120)) + list(range(b, nx, 24))
 
 
