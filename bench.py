@@ -575,9 +575,9 @@ def batch_workload(fd, kind="config4", rank=0, max_steps=1800):
 def run_batch(args):
     """64 independent showers on uneven grids (64^3 .. 256 x 256 x 512, dx =
     2 cm, Mur) advanced together by one batch (the persistent kernel and the
-    solo streams, as its autotuner chooses), against the same simulations
-    stepped one after another (default fused path, and the unfused path whose
-    per-cell code the persistent kernel shares)."""
+    solo streams, as its autotuner chooses; then each way alone), against the
+    same simulations stepped one after another (default one-pass tile path,
+    and the unfused path)."""
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -607,6 +607,15 @@ def run_batch(args):
     t_batch = timed(lambda: (b.step(steps), b.sync()))
     clk = clocks.stop()
     cfg, graph, solo = b.config, b.graph_mode, b.solo
+    # each way alone: every grid in the persistent kernel, every grid on the
+    # solo streams
+    ways = {}
+    for name, thr in (("persistent_only", -1), ("solo_streams_only", 1)):
+        b.set_solo(thr)
+        b.step(2)
+        b.sync()
+        ways[name] = timed(lambda: (b.step(steps), b.sync()))
+    b.set_solo(solo["min_cells"])
     t_fused = timed(lambda: [s.step(steps) for s in sims])
     for s in sims:
         s.set_kernel(0)
@@ -626,6 +635,8 @@ def run_batch(args):
                        "dx_m": dx, "probes_each": 8, **cfg, "graph_replay": bool(graph == 1),
                        "solo_min_cells": solo["min_cells"], "solo_grids": solo["n_solo"],
                        "tuner_trial_steps": used},
+            "persistent_only_gcells": g(ways["persistent_only"]),
+            "solo_streams_only_gcells": g(ways["solo_streams_only"]),
             "one_by_one_fused_gcells": g(t_fused), "one_by_one_unfused_gcells": g(t_unfused),
             "batch_over_fused": round(t_fused / t_batch, 3), "batch_over_unfused": round(t_unfused / t_batch, 3),
             "clocks": clk}

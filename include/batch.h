@@ -4,19 +4,24 @@
  * A batch borrows n simulation handles (fdtd.h) on one device, each with its
  * own grid, boundary, shower (Sec. III.B) and detectors, and advances all of
  * them with one persistent kernel per launch: every step of Sec. III.A runs
- * as three phases over a shared work queue of (simulation, slab of z planes)
- * items -- H update, E update with the shower's current, then the Mur faces
- * and the detector readout -- separated by grid-wide barriers whose waits are
+ * as two phases over a shared work queue -- first (simulation, tile of 128
+ * columns x 8 rows, z chunk) items, each the one-pass H and E update of that
+ * tile with the shower's current and the CPML, then the Mur faces and the
+ * detector readout -- separated by grid-wide barriers whose waits are
  * bounded (FDTD_ERR_TIMEOUT if one gives up).  The kernel is a cooperative
- * launch sized to the device's resident blocks; the launch, with the reset of
- * its queue counters, is captured once in a CUDA graph and replayed.  Each
- * cell is updated by the same per-cell code as the unfused path
- * (fdtd_set_kernel 0), so a batched step gives the same numbers, bit for bit.
- * Simulations large enough to keep the GPU busy with their own kernels can
- * instead step alone (fdtd_batch_set_solo): after the persistent launches,
- * their handle's selected path is issued on eight internal streams (largest
- * grid first, each to the least loaded stream), so several run at once and
- * each gets exactly what fdtd_step on the handle gives.
+ * launch of one block per SM; the launch, with the reset of its queue
+ * counters, is captured once in a CUDA graph and replayed.  A tile is
+ * updated by the same code as the handle's one-pass tile path
+ * (fdtd_set_kernel 1), and the faces and detectors by that of its own Mur and
+ * readout kernels, so a batched step gives the numbers of fdtd_step on the
+ * handle with path 1 selected, bit for bit.
+ * The persistent kernel takes PEC and Mur grids.  Simulations large enough
+ * to keep the GPU busy with their own kernels can instead step alone
+ * (fdtd_batch_set_solo), as does a grid with CPML layers or one the tile path
+ * cannot run: after the persistent launches, their handle's
+ * selected path is issued on eight internal streams (largest grid first, each
+ * to the least loaded stream), so several run at once and each gets exactly
+ * what fdtd_step on the handle gives.
  *
  * The handles stay owned by the caller and must outlive the batch; stepping
  * a handle on its own between batch steps is allowed (the batch re-reads the
@@ -54,17 +59,19 @@ int fdtd_batch_step(fdtd_batch_t b, int n);
 int fdtd_batch_sync(fdtd_batch_t b);
 
 /*
- * Launch configuration: threads per block (128 or 256), cells per work
- * item (a slab of whole z planes holds about this many cells, at least one
- * plane), steps per persistent launch (1 .. 64).
+ * Launch configuration: z planes per chunk of a tile item (>= 1; the planes
+ * between a CPML grid's z layers are cut into chunks of about this many, the
+ * layers are chunks of their own; fewer planes per chunk where a long chunk's
+ * coefficient table would crowd out the stage ring; default 128), steps per
+ * persistent launch (1 .. 64; default 8).
  */
-int fdtd_batch_set_config(fdtd_batch_t b, int threads, int cells_per_item, int steps_per_launch);
-int fdtd_batch_get_config(fdtd_batch_t b, int *threads, int *cells_per_item, int *steps_per_launch);
+int fdtd_batch_set_config(fdtd_batch_t b, int chunk_planes, int steps_per_launch);
+int fdtd_batch_get_config(fdtd_batch_t b, int *chunk_planes, int *steps_per_launch);
 
 /*
  * Autotuner: first the solo threshold (none, every simulation alone, or a
- * power of two between the smallest and the largest grid), then the launch
- * configuration of the persistent kernel (threads x cells per item).  It runs
+ * power of two between the smallest and the largest grid), then the chunk
+ * length of the persistent kernel's tile items (16 .. 256 planes).  It runs
  * trial_steps >= 1 steps of the batch itself with each candidate, times each
  * on the device, keeps the fastest and returns the steps it used in
  * *steps_used.  The trial steps are real steps of every simulation (a
@@ -76,10 +83,11 @@ int fdtd_batch_tune(fdtd_batch_t b, int trial_steps, int *steps_used);
 /*
  * Simulations of at least min_cells cells step alone, with their handle's
  * selected path, on the batch's internal streams; the rest share the
- * persistent kernel.  min_cells = -1 (the default): every simulation shares it.
+ * persistent kernel, CPML grids excepted (they always step alone).
+ * min_cells = -1 (the default): every PEC and Mur grid shares it.
  * FDTD_ERR_ARG for min_cells < -1.  fdtd_batch_get_solo returns the
- * threshold and the number of simulations it makes step alone (either
- * pointer may be null).
+ * threshold and the number of simulations that step alone (either pointer
+ * may be null).
  */
 int fdtd_batch_set_solo(fdtd_batch_t b, long long min_cells);
 int fdtd_batch_get_solo(fdtd_batch_t b, long long *min_cells, int *n_solo);

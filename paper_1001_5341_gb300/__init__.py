@@ -94,8 +94,8 @@ _SIGS = {
     "fdtd_batch_destroy": (None, [_vp]),
     "fdtd_batch_step": (_i, [_vp, _i]),
     "fdtd_batch_sync": (_i, [_vp]),
-    "fdtd_batch_set_config": (_i, [_vp, _i, _i, _i]),
-    "fdtd_batch_get_config": (_i, [_vp, _pi, _pi, _pi]),
+    "fdtd_batch_set_config": (_i, [_vp, _i, _i]),
+    "fdtd_batch_get_config": (_i, [_vp, _pi, _pi]),
     "fdtd_batch_tune": (_i, [_vp, _i, _pi]),
     "fdtd_batch_graph_mode": (_i, [_vp]),
     "fdtd_batch_set_solo": (_i, [_vp, C.c_longlong]),
@@ -595,14 +595,15 @@ class Batch:
     def sync(self):
         check(fdtd_batch_sync(self.h), "fdtd_batch_sync")
 
-    def set_config(self, threads=256, cells_per_item=1 << 16, steps_per_launch=8):
-        check(fdtd_batch_set_config(self.h, threads, cells_per_item, steps_per_launch), "fdtd_batch_set_config")
+    def set_config(self, chunk_planes=128, steps_per_launch=8):
+        """z planes per chunk of the persistent kernel's tile items, steps per launch."""
+        check(fdtd_batch_set_config(self.h, chunk_planes, steps_per_launch), "fdtd_batch_set_config")
 
     @property
     def config(self):
-        t, c, s = C.c_int(), C.c_int(), C.c_int()
-        check(fdtd_batch_get_config(self.h, C.byref(t), C.byref(c), C.byref(s)), "fdtd_batch_get_config")
-        return {"threads": t.value, "cells_per_item": c.value, "steps_per_launch": s.value}
+        c, s = C.c_int(), C.c_int()
+        check(fdtd_batch_get_config(self.h, C.byref(c), C.byref(s)), "fdtd_batch_get_config")
+        return {"chunk_planes": c.value, "steps_per_launch": s.value}
 
     def set_solo(self, min_cells=-1):
         """Simulations of at least min_cells cells step alone with their own

@@ -1,14 +1,24 @@
 // batch.cu -- many simulations in one persistent kernel (batch.h).
 //
-// Work queue.  For each step the kernel runs three phases; in each phase every
+// Work queue.  For each step the kernel runs two phases; in each phase every
 // block takes items from an atomic counter until the phase's items are gone:
-//   H: item = (simulation q, slab of planes of q): H^{n+1/2} of its cells;
-//   E: same items: E^{n+1} with the shower's current;
-//   M: item = (q, face) for the six Mur faces of a Mur grid, and (q, detectors)
-//      for a grid with detectors: the boundary, then the readout of E^{n+1}.
-// Between phases a grid-wide barrier (all blocks are resident: cooperative
-// launch) with a bounded wait.  Every cell goes through cell_h / cell_e /
-// mur_cell, the code of the unfused path, so the numbers are the same.
+//   F: item = (simulation q, tile of 128 columns x 8 rows, z chunk of q): the
+//      one-pass step of that tile (H^{n+1/2} and E^{n+1} with the shower's
+//      current, Sec. III.A-B), the block body of the handle's tile path
+//      (vtile_tile.cuh), with q's tensor maps;
+//   M: item = (q, face, piece of MUR_PIECE face nodes) for the six Mur faces of
+//      a Mur grid, and (q, detectors) for a grid with detectors: the boundary,
+//      then the readout of E^{n+1} (the code of the handle's own Mur and
+//      detector kernels).  An x face is a strided walk through memory (one
+//      node per row), so faces are cut into pieces that many SMs share.
+// Between phases a grid-wide barrier (all blocks resident: a cooperative
+// launch of one block per SM) with a bounded wait; a step whose simulations
+// have neither Mur faces nor detectors has no M phase.  The numbers are those
+// of the handle stepped on its tile path (fdtd_set_kernel 1), bit for bit.
+// The kernel takes PEC and Mur grids: its tile arguments come from memory (a
+// copy per item in shared memory), not from the parameter bank, and with them
+// the CPML instances of the tile body need more registers than a block of
+// nine warps has (168 per thread); a grid with CPML layers steps alone.
 // Simulations keep their own ping-pong sets: in step s of a launch,
 // simulation q reads set cur_q ^ (s & 1).  At the end of a launch block 0
 // advances each descriptor's set index and step count, so that the captured
@@ -24,41 +34,45 @@
 #include "../../include/batch.h"
 #include "cell_update.cuh"
 #include "fdtd_internal.h"
+#include "vtile_tile.cuh"
 
 using namespace fdtd;
 
 namespace {
 
 constexpr int MAX_STEPS_PER_LAUNCH = 64;
+constexpr int NT = vt::NT;
+constexpr int MUR_PIECE = 2048;   // face nodes per M item
 
+// A simulation of the persistent kernel.
 struct BSim {
-    Grid g;
-    float *f[2];
-    Cpml pml[2];           // views for cur = 0 and cur = 1
-    float kE, kH, mur;
-    int mur_on;
-    Source src;
+    vt::Args a[2];         // tile arguments for field set 0 and 1 (ss and flags set per step)
+    const vt::Maps *maps;  // its tensor maps (device copy)
+    int tiles, items;      // tiles per chunk; F items (tiles x chunks)
+    float mur;
+    int mface[7];          // M items before face f (pieces of MUR_PIECE nodes); mface[6]: all faces
     Probes pr;
     int cur;
     long long n;           // steps done
-    int planes;            // z planes per H/E item
 };
 
 struct BArgs {
     BSim *sims;
     int nsim;
-    const int *hstart;     // [nsim + 1] prefix sums of H/E items
+    const int *fstart;     // [nsim + 1] prefix sums of F items
     const int *mstart;     // [nsim + 1] prefix sums of M items
     int steps;
-    unsigned *ctr;         // [3 * steps] queue counters, zero at launch
+    unsigned *ctr;         // [2 * steps] queue counters, zero at launch
     unsigned *bar;         // [2] barrier count and generation, zero at launch
     int *flags;
     long long spin;        // clock cycles a barrier wait may take
 };
 
 // Grid-wide barrier: arrive, then wait (bounded by spin cycles) for the
-// generation to move.  A block whose wait gives up sets flag bit 1 and stops;
-// the others then give up at this barrier or the next, so the launch ends.
+// generation to move.  A block whose wait gives up sets flag bit 1.  Returns
+// false when the launch must stop: this wait gave up, or some block recorded
+// a failure (a barrier or a pipeline wait) before arriving; every block that
+// passes the barrier then sees that flag, so they leave together.
 __device__ bool grid_sync(unsigned *bar, int *flags, long long spin) {
     __shared__ int ok;
     __syncthreads();
@@ -83,6 +97,7 @@ __device__ bool grid_sync(unsigned *bar, int *flags, long long spin) {
             }
         }
         __threadfence();
+        if (*(volatile int *)flags) ok = 0;
     }
     __syncthreads();
     return ok != 0;
@@ -98,21 +113,12 @@ __device__ __forceinline__ int find_sim(const int *start, int nsim, int it) {
     return lo;
 }
 
-__global__ void __launch_bounds__(256, 6) k_batch(BArgs A) {   // 40 registers: 6 blocks per SM
-    __shared__ int s_item;
-    // the item's simulation, copied once per item: the per-cell code then
-    // reads it from shared memory, which no global store can alias
-    __shared__ Grid s_g;
-    __shared__ Cpml s_pml;
-    __shared__ Source s_src;
-    __shared__ Probes s_pr;
-    __shared__ float s_k[3];
-    __shared__ int s_q, s_mur;
-    __shared__ long long s_n;
-    __shared__ const float *s_in;
-    __shared__ float *s_out;
-    const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
-    const int hitems = A.hstart[A.nsim], mitems = A.mstart[A.nsim];
+__global__ void __launch_bounds__(NT, 1) k_batch(BArgs A) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(16) vt::Args s_a;   // the item's tile arguments
+    __shared__ int s_item, s_q;
+    const int tid = threadIdx.x;
+    const int fitems = A.fstart[A.nsim], mitems = A.mstart[A.nsim];
     // an earlier launch (or a block of this one) gave up: the simulations are
     // in an unknown state.  One read per block, so that its threads leave
     // together (thread 0 alone drives the work queue).
@@ -121,82 +127,82 @@ __global__ void __launch_bounds__(256, 6) k_batch(BArgs A) {   // 40 registers: 
     __syncthreads();
     if (s_stop) return;
     for (int s = 0; s < A.steps; ++s) {
-        for (int phase = 0; phase < 3; ++phase) {
-            const int total = phase < 2 ? hitems : mitems;
-            unsigned *ctr = A.ctr + 3 * s + phase;
-            for (;;) {
-                if (tid == 0) {
-                    const int it = (int)atomicAdd(ctr, 1u);
-                    s_item = it;
-                    if (it < total) {
-                        const int q = find_sim(phase < 2 ? A.hstart : A.mstart, A.nsim, it);
-                        const BSim &S = A.sims[q];
-                        const int cur = S.cur ^ (s & 1);
-                        s_q = q;
-                        s_g = S.g;
-                        s_pml = S.pml[cur];
-                        s_src = S.src;
-                        s_pr = S.pr;
-                        s_k[0] = S.kE;
-                        s_k[1] = S.kH;
-                        s_k[2] = S.mur;
-                        s_mur = S.mur_on;
-                        s_n = S.n + s;
-                        s_in = S.f[cur];
-                        s_out = S.f[cur ^ 1];
-                    }
-                }
-                __syncthreads();
-                const int it = s_item;
-                if (it >= total) {
-                    __syncthreads();
-                    break;
-                }
-                const Grid g = s_g;
-                const float *in = s_in;
-                float *out = s_out;
-                if (phase < 2) {
-                    const int planes = A.sims[s_q].planes;
-                    const int k0 = (it - A.hstart[s_q]) * planes, k1 = min(k0 + planes, g.nz);
-                    const int rows = g.ny * (k1 - k0);
-                    for (int row = warp; row < rows; row += nwarps) {
-                        const int kk = row / g.ny, j = row - kk * g.ny, k = k0 + kk;
-                        for (int i = lane; i < g.nx; i += 32) {
-                            if (phase == 0)
-                                cell_h(g, in, in + 3 * g.comp, out + 3 * g.comp, s_pml, s_k[1], i, j, k);
-                            else
-                                cell_e(g, in, out + 3 * g.comp, out, s_pml, s_k[0], s_src, s_n, i, j, k);
-                        }
-                    }
-                } else {
-                    const int m = it - A.mstart[s_q];
-                    if (s_mur && m < 6) {
-                        // face m: (a, b) over (j, k), (i, k) or (i, j)
-                        const int ax = m >> 1;
-                        const int na = (ax == 0 ? g.ny : g.nx) + 1, nb = (ax == 2 ? g.ny : g.nz) + 1;
-                        for (int c = tid; c < na * nb; c += nt) mur_cell(g, in, out, s_k[2], m, c % na, c / na);
-                    } else {
-                        const Probes &p = s_pr;
-                        for (int t = tid; t < p.n; t += nt) {
-                            const int i = p.ijk[3 * t], j = p.ijk[3 * t + 1], k = p.ijk[3 * t + 2];
-                            const long long c = gidx(g, i, j, k);
-                            const float *Ex = out, *Ey = out + g.comp, *Ez = out + 2 * g.comp;
-                            const float ex = 0.5f * (Ex[c - 1] + Ex[c]);
-                            const float ey = 0.5f * (Ey[c - g.pitch] + Ey[c]);
-                            const float ez = 0.5f * (Ez[c - g.plane] + Ez[c]);
-                            float *o = p.trace + ((long long)t * p.max_steps + s_n) * 2;
-                            o[0] = ez;
-                            o[1] = p.cxy[2 * t] * ex + p.cxy[2 * t + 1] * ey;
-                        }
-                    }
-                }
-                __syncthreads();   // the item's shared copy is free again
+        // ---- F: the tiles of every simulation ----
+        for (;;) {
+            if (tid == 0) {
+                const int it = (int)atomicAdd(A.ctr + 2 * s, 1u);
+                s_item = it;
+                if (it < fitems) s_q = find_sim(A.fstart, A.nsim, it);
             }
-            if (!grid_sync(A.bar, A.flags, A.spin)) return;
+            __syncthreads();
+            const int it = s_item;
+            if (it >= fitems) break;
+            const int q = s_q;
+            const BSim &S = A.sims[q];
+            const int cur = S.cur ^ (s & 1);
+            {
+                static_assert(sizeof(vt::Args) % 8 == 0, "Args copied in 8-byte words");
+                const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&S.a[cur]);
+                unsigned long long *dst = reinterpret_cast<unsigned long long *>(&s_a);
+                for (int w = tid; w < (int)(sizeof(vt::Args) / 8); w += NT) dst[w] = src[w];
+            }
+            __syncthreads();
+            if (tid == 0) {
+                s_a.ss = source_window(s_a.src, S.n + s);
+                s_a.flags = A.flags;
+            }
+            __syncthreads();
+            const int local = it - A.fstart[q];
+            const int ns = vt::tile_block<false>(s_a, *S.maps, local % S.tiles, local / S.tiles, smem_raw);
+            vt::end_tile(smem_raw, ns);
         }
+        if (!grid_sync(A.bar, A.flags, A.spin)) return;
+        if (mitems == 0) continue;
+        // ---- M: Mur faces, then detectors, of E^{n+1} ----
+        for (;;) {
+            if (tid == 0) {
+                const int it = (int)atomicAdd(A.ctr + 2 * s + 1, 1u);
+                s_item = it;
+                if (it < mitems) s_q = find_sim(A.mstart, A.nsim, it);
+            }
+            __syncthreads();
+            const int it = s_item;
+            if (it >= mitems) break;
+            const BSim &S = A.sims[s_q];
+            const int cur = S.cur ^ (s & 1);
+            const vt::Args &a = S.a[cur];
+            const Grid &g = a.g;
+            const float *in = S.a[cur ^ 1].oex;   // E^n: the set this step reads
+            float *out = a.oex;                   // E^{n+1}
+            const int m = it - A.mstart[s_q];
+            if (m < S.mface[6]) {
+                // a piece of face f: (a, b) over (j, k), (i, k) or (i, j)
+                int f = 0;
+                while (m >= S.mface[f + 1]) ++f;
+                const int ax = f >> 1;
+                const int na = (ax == 0 ? g.ny : g.nx) + 1, nb = (ax == 2 ? g.ny : g.nz) + 1;
+                const int c0 = (m - S.mface[f]) * MUR_PIECE, c1 = min(c0 + MUR_PIECE, na * nb);
+                for (int c = c0 + tid; c < c1; c += NT) mur_cell(g, in, out, S.mur, f, c % na, c / na);
+            } else {
+                const Probes &p = S.pr;
+                for (int t = tid; t < p.n; t += NT) {
+                    const int i = p.ijk[3 * t], j = p.ijk[3 * t + 1], k = p.ijk[3 * t + 2];
+                    const long long c = gidx(g, i, j, k);
+                    const float *Ex = out, *Ey = out + g.comp, *Ez = out + 2 * g.comp;
+                    const float ex = 0.5f * (Ex[c - 1] + Ex[c]);
+                    const float ey = 0.5f * (Ey[c - g.pitch] + Ey[c]);
+                    const float ez = 0.5f * (Ez[c - g.plane] + Ez[c]);
+                    float *o = p.trace + ((long long)t * p.max_steps + S.n + s) * 2;
+                    o[0] = ez;
+                    o[1] = p.cxy[2 * t] * ex + p.cxy[2 * t + 1] * ey;
+                }
+            }
+            __syncthreads();   // s_item is read again by thread 0
+        }
+        if (!grid_sync(A.bar, A.flags, A.spin)) return;
     }
     if (blockIdx.x == 0)
-        for (int q = tid; q < A.nsim; q += nt) {
+        for (int q = tid; q < A.nsim; q += NT) {
             A.sims[q].cur ^= A.steps & 1;
             A.sims[q].n += A.steps;
         }
@@ -214,10 +220,13 @@ struct fdtd_batch {
     cudaStream_t stream;
     cudaEvent_t ev;
     BSim *d_sims;
-    int *d_hstart, *d_mstart;
+    vt::Maps *d_maps;
+    int *d_fstart, *d_mstart;
     unsigned *d_ctr, *d_bar;
     int *d_flags;
-    int threads, cells_per_item, steps_per_launch;
+    int chunk_planes, steps_per_launch;
+    size_t smem;           // dynamic shared memory of the persistent kernel
+    long long floats;      // its floats after the ring barriers
     long long solo_cells;  // simulations of at least this many cells step alone (-1: none)
     std::vector<char> solo;
     cudaStream_t solo_st[SOLO_STREAMS];   // the solo simulations, spread over these
@@ -246,7 +255,9 @@ void drop_graphs(fdtd_batch *b) {
     b->graphs.clear();
 }
 
-// Descriptors and item prefix sums from the handles' current state.
+// Descriptors and item prefix sums from the handles' current state.  A
+// simulation whose grid the tile path cannot run (no tile state on its
+// handle), or which has CPML layers, steps alone.
 int refresh(fdtd_batch *b) {
     const int all = (int)b->sims.size();
     std::vector<fdtd_ctx *> shared;
@@ -254,51 +265,96 @@ int refresh(fdtd_batch *b) {
     for (int q = 0; q < all; ++q) {
         const fdtd_ctx *h = b->sims[q];
         const long long cells = (long long)h->g.nx * h->g.ny * h->g.nz;
-        b->solo[q] = b->solo_cells >= 0 && cells >= b->solo_cells;
+        b->solo[q] = !h->vtile || h->P > 0 || (b->solo_cells >= 0 && cells >= b->solo_cells);
         if (!b->solo[q]) shared.push_back(b->sims[q]);
     }
     const int n = (int)shared.size();
     b->nshared = n;
     if (n == 0) return FDTD_OK;
     std::vector<BSim> d(n);
-    std::vector<int> hs(n + 1, 0), ms(n + 1, 0);
+    std::vector<vt::Maps> maps(n);
+    std::vector<int> fs(n + 1, 0), ms(n + 1, 0);
     for (int q = 0; q < n; ++q) {
         fdtd_ctx *h = shared[q];
+        const vt::HostState *vs = static_cast<const vt::HostState *>(h->vtile);
+        const Grid &g = h->g;
+        // z chunks of about chunk_planes planes between the layers
+        const int mid = h->P > 0 ? g.nz - 2 * h->P - 1 : g.nz;
+        vt::Chunks z;
+        if (!vt::z_chunks(g.nz, h->P, vs->xbw, (mid + b->chunk_planes - 1) / b->chunk_planes, b->floats, z)) {
+            if (b->status == FDTD_OK) b->status = FDTD_ERR_CUDA;
+            return b->status;
+        }
         BSim &S = d[q];
-        S.g = h->g;
-        S.f[0] = h->fields[0];
-        S.f[1] = h->fields[1];
+        std::memset(&S, 0, sizeof(S));
         const int cur = h->cur;
         for (int c = 0; c < 2; ++c) {
+            vt::Args &a = S.a[c];
+            a.g = g;
+            float *out = h->fields[c ^ 1];
+            const size_t cc = (size_t)g.comp;
+            a.oex = out; a.oey = out + cc; a.oez = out + 2 * cc;
+            a.ohx = out + 3 * cc; a.ohy = out + 4 * cc; a.ohz = out + 5 * cc;
             h->cur = c;
-            S.pml[c] = cpml_view(h);
+            a.pml = cpml_view(h);
+            a.tiles_x = vs->tiles_x;
+            a.tiles_y = vs->tiles_y;
+            a.za = z.za;
+            a.zb = z.zb;
+            a.cm = z.cm;
+            a.m = z.m;
+            a.zc = z.zc;
+            a.ring = z.ring;
+            a.xlo4 = vs->xlo4;
+            a.xhb = vs->xhb;
+            a.xbw = vs->xbw;
+            a.cur = c;
+            a.ecur = h->ecur;
+            a.src = h->src;
+            a.kE = (float)h->kE;
+            a.kH = (float)h->kH;
         }
         h->cur = cur;
-        S.kE = (float)h->kE;
-        S.kH = (float)h->kH;
+        maps[q] = vs->maps;
+        S.maps = b->d_maps + q;
+        S.tiles = vs->tiles_x * vs->tiles_y;
+        S.items = S.tiles * z.chunks;
         S.mur = (float)h->mur_m;
-        S.mur_on = h->boundary == FDTD_MUR1;
-        S.src = h->src;
+        S.mface[0] = 0;
+        for (int f = 0; f < 6; ++f) {
+            const int ax = f >> 1;
+            const long long na = (ax == 0 ? g.ny : g.nx) + 1, nb = (ax == 2 ? g.ny : g.nz) + 1;
+            S.mface[f + 1] = S.mface[f] + (h->boundary == FDTD_MUR1 ? (int)((na * nb + MUR_PIECE - 1) / MUR_PIECE) : 0);
+        }
         S.pr = Probes{h->np, h->max_steps, h->d_ijk, h->d_cxy, h->d_trace};
         S.cur = h->cur;
         S.n = h->steps;
-        const long long plane = (long long)h->g.nx * h->g.ny;
-        S.planes = (int)std::max<long long>(1, std::min<long long>(h->g.nz, b->cells_per_item / std::max(1LL, plane)));
-        while (S.planes > 1 && plane * S.planes >= (1LL << 31)) --S.planes;
-        hs[q + 1] = hs[q] + (h->g.nz + S.planes - 1) / S.planes;
-        ms[q + 1] = ms[q] + (S.mur_on ? 6 : 0) + (h->np > 0 ? 1 : 0);
+        fs[q + 1] = fs[q] + S.items;
+        ms[q + 1] = ms[q] + S.mface[6] + (h->np > 0 ? 1 : 0);
     }
     if (note(b, cudaMemcpyAsync(b->d_sims, d.data(), n * sizeof(BSim), cudaMemcpyHostToDevice, b->stream)) ||
-        note(b, cudaMemcpyAsync(b->d_hstart, hs.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, b->stream)) ||
+        note(b, cudaMemcpyAsync(b->d_maps, maps.data(), n * sizeof(vt::Maps), cudaMemcpyHostToDevice, b->stream)) ||
+        note(b, cudaMemcpyAsync(b->d_fstart, fs.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, b->stream)) ||
         note(b, cudaMemcpyAsync(b->d_mstart, ms.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, b->stream)))
         return b->status;
-    // pageable sources: the copies complete before the next host change of d, hs, ms
+    // pageable sources: the copies complete before the next host change of d, maps, fs, ms
     return note(b, cudaStreamSynchronize(b->stream));
 }
 
+// The persistent kernel's shared memory (all an SM's block may take) and grid
+// (every block resident).
 int size_grid(fdtd_batch *b) {
-    int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch, b->threads, 0) != cudaSuccess || per < 1) {
+    cudaFuncAttributes fa;
+    int optin = 0, per = 0;
+    if (cudaFuncGetAttributes(&fa, k_batch) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->dev) != cudaSuccess) {
+        cudaGetLastError();
+        return FDTD_ERR_CUDA;
+    }
+    b->smem = ((size_t)optin - fa.sharedSizeBytes) / 1024 * 1024;
+    b->floats = ((long long)b->smem - vt::BAR_BYTES) / 4;
+    if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch, NT, b->smem) != cudaSuccess || per < 1) {
         cudaGetLastError();
         return FDTD_ERR_CUDA;
     }
@@ -310,19 +366,20 @@ cudaError_t issue(fdtd_batch *b, int steps) {
     BArgs A;
     A.sims = b->d_sims;
     A.nsim = b->nshared;
-    A.hstart = b->d_hstart;
+    A.fstart = b->d_fstart;
     A.mstart = b->d_mstart;
     A.steps = steps;
     A.ctr = b->d_ctr;
     A.bar = b->d_bar;
     A.flags = b->d_flags;
     A.spin = b->spin;
-    cudaError_t e = cudaMemsetAsync(b->d_ctr, 0, 3 * steps * sizeof(unsigned), b->stream);
+    cudaError_t e = cudaMemsetAsync(b->d_ctr, 0, 2 * steps * sizeof(unsigned), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), b->stream);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(b->blocks);
-    cfg.blockDim = dim3(b->threads);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = b->smem;
     cfg.stream = b->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -411,8 +468,7 @@ int fdtd_batch_create(fdtd_batch_t *out, const fdtd_t *sims, int n) {
     b->sims.assign(sims, sims + n);
     b->dev = dev;
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
-    b->threads = 256;
-    b->cells_per_item = 1 << 16;
+    b->chunk_planes = 128;
     b->steps_per_launch = 8;
     b->solo_cells = -1;
     b->nshared = n;
@@ -426,9 +482,10 @@ int fdtd_batch_create(fdtd_batch_t *out, const fdtd_t *sims, int n) {
     if (!streams_ok || cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&b->d_sims, n * sizeof(BSim)) != cudaSuccess ||
-        cudaMalloc(&b->d_hstart, (n + 1) * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&b->d_maps, n * sizeof(vt::Maps)) != cudaSuccess ||
+        cudaMalloc(&b->d_fstart, (n + 1) * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&b->d_mstart, (n + 1) * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&b->d_ctr, 3 * MAX_STEPS_PER_LAUNCH * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&b->d_ctr, 2 * MAX_STEPS_PER_LAUNCH * sizeof(unsigned)) != cudaSuccess ||
         cudaMalloc(&b->d_bar, 2 * sizeof(unsigned)) != cudaSuccess ||
         cudaMalloc(&b->d_flags, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
@@ -450,7 +507,8 @@ void fdtd_batch_destroy(fdtd_batch_t b) {
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graphs(b);
     if (b->d_sims) cudaFree(b->d_sims);
-    if (b->d_hstart) cudaFree(b->d_hstart);
+    if (b->d_maps) cudaFree(b->d_maps);
+    if (b->d_fstart) cudaFree(b->d_fstart);
     if (b->d_mstart) cudaFree(b->d_mstart);
     if (b->d_ctr) cudaFree(b->d_ctr);
     if (b->d_bar) cudaFree(b->d_bar);
@@ -556,23 +614,20 @@ int fdtd_batch_set_wait_limit(fdtd_batch_t b, long long cycles) {
     return FDTD_OK;
 }
 
-int fdtd_batch_set_config(fdtd_batch_t b, int threads, int cells_per_item, int steps_per_launch) {
-    if (!b || (threads != 128 && threads != 256) || cells_per_item < 1 || steps_per_launch < 1 ||
-        steps_per_launch > MAX_STEPS_PER_LAUNCH)
+int fdtd_batch_set_config(fdtd_batch_t b, int chunk_planes, int steps_per_launch) {
+    if (!b || chunk_planes < 1 || steps_per_launch < 1 || steps_per_launch > MAX_STEPS_PER_LAUNCH)
         return FDTD_ERR_ARG;
     if (b->status != FDTD_OK) return b->status;
     if (note(b, cudaStreamSynchronize(b->stream)) != FDTD_OK) return b->status;
     drop_graphs(b);
-    b->threads = threads;
-    b->cells_per_item = cells_per_item;
+    b->chunk_planes = chunk_planes;
     b->steps_per_launch = steps_per_launch;
-    return size_grid(b);
+    return FDTD_OK;
 }
 
-int fdtd_batch_get_config(fdtd_batch_t b, int *threads, int *cells_per_item, int *steps_per_launch) {
+int fdtd_batch_get_config(fdtd_batch_t b, int *chunk_planes, int *steps_per_launch) {
     if (!b) return FDTD_ERR_ARG;
-    if (threads) *threads = b->threads;
-    if (cells_per_item) *cells_per_item = b->cells_per_item;
+    if (chunk_planes) *chunk_planes = b->chunk_planes;
     if (steps_per_launch) *steps_per_launch = b->steps_per_launch;
     return FDTD_OK;
 }
@@ -592,7 +647,8 @@ int fdtd_batch_get_solo(fdtd_batch_t b, long long *min_cells, int *n_solo) {
     if (n_solo) {
         int k = 0;
         for (fdtd_t h : b->sims)
-            if (b->solo_cells >= 0 && (long long)h->g.nx * h->g.ny * h->g.nz >= b->solo_cells) ++k;
+            if (!h->vtile || h->P > 0 || (b->solo_cells >= 0 && (long long)h->g.nx * h->g.ny * h->g.nz >= b->solo_cells))
+                ++k;
         *n_solo = k;
     }
     return FDTD_OK;
@@ -635,30 +691,27 @@ int fdtd_batch_tune(fdtd_batch_t b, int trial_steps, int *steps_used) {
         }
         fdtd_batch_set_solo(b, best);
     }
-    const int thr[2] = {128, 256};
-    const int cpi[4] = {1 << 14, 1 << 16, 1 << 18, 1 << 20};
-    // then the launch configuration of the persistent kernel, if it has work
+    // then the z chunk length of the persistent kernel's tiles, if it has work
+    const int cpl[5] = {16, 32, 64, 128, 256};
     float best_ms = 1e30f;
-    int best_t = b->threads, best_c = b->cells_per_item, rc = FDTD_OK;
+    int best_c = b->chunk_planes, rc = FDTD_OK;
     refresh(b);
     if (b->nshared > 0)
-        for (int t : thr)
-            for (int c : cpi) {
-                if ((rc = fdtd_batch_set_config(b, t, c, spl)) != FDTD_OK) break;
-                float ms = 0.f;
-                int u = 0;
-                rc = time_trial(b, spl, trial_steps, &ms, &u);
-                used += u;
-                if (rc != FDTD_OK) break;
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best_t = t;
-                    best_c = c;
-                }
+        for (int c : cpl) {
+            if ((rc = fdtd_batch_set_config(b, c, spl)) != FDTD_OK) break;
+            float ms = 0.f;
+            int u = 0;
+            rc = time_trial(b, spl, trial_steps, &ms, &u);
+            used += u;
+            if (rc != FDTD_OK) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_c = c;
             }
+        }
     if (steps_used) *steps_used = used;
     if (rc != FDTD_OK) return rc;
-    return fdtd_batch_set_config(b, best_t, best_c, spl0);
+    return fdtd_batch_set_config(b, best_c, spl0);
 }
 
 int fdtd_batch_graph_mode(fdtd_batch_t b) { return b ? b->graph_ok : -1; }

@@ -31,10 +31,11 @@ __device__ __forceinline__ float source_term(const Source &s, int i, int j, int 
     return (float)(qbar * wij * s.coef * dC);
 }
 
-// The planes k whose Ez edges may carry current during step n: a host-side,
-// conservative window [klo, khi] around the charge's path (the device decides
-// each edge exactly in source_term).
-inline SourceStep source_window(const Source &s, long long n) {
+// The planes k whose Ez edges may carry current during step n: a
+// conservative window [klo, khi] around the charge's path (source_term
+// decides each edge exactly).  Computed on the host per launch, or on the
+// device per step by the persistent batch kernel.
+__host__ __device__ inline SourceStep source_window(const Source &s, long long n) {
     SourceStep w;
     w.n = n;
     w.klo = 1;

@@ -37,6 +37,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
         if (clock64() - t0 > (4LL << 30)) return false;
     return true;
 }
+// make a barrier's memory free for a new mbar_init (no arrival or
+// transaction may be pending on it)
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(sa(bar)) : "memory");
+}
 // 3-D tiled tensor load into shared memory, completion counted on bar
 __device__ __forceinline__ void tma_load(float *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z) {
     asm volatile(

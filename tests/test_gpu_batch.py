@@ -1,9 +1,11 @@
 """GPU batched persistent stepping (batch.h): uneven grids with PEC, Mur and
 CPML boundaries, showers and detectors, advanced together, must equal the
-same simulations stepped one by one on the unfused path bit for bit (the
-batch runs the same per-cell code), and the FP64 oracle within 1e-4; grids
-that step alone (solo threshold) equal their handle stepped by itself; the
-autotuner's trial steps are real steps; capacity and argument checks."""
+same simulations stepped one by one on the one-pass tile path (path 1) bit
+for bit (the persistent kernel runs that path's tile body, Mur and readout
+code for the PEC and Mur grids; the CPML grids step alone on their handle's
+path), and the FP64 oracle within 1e-4; grids that step alone (solo
+threshold) equal their handle stepped by itself; the autotuner's trial
+steps are real steps; capacity and argument checks."""
 import numpy as np
 import pytest
 
@@ -62,13 +64,13 @@ def _state(s):
     return [s.field(c) for c in range(6)], s.probes()
 
 
-@pytest.mark.parametrize("cfg", [(256, 1 << 16, 8), (128, 1 << 12, 5), (256, 1 << 20, 64)])
+@pytest.mark.parametrize("cfg", [(64, 8), (5, 5), (256, 64), (1, 3)])
 def test_batch_equals_one_by_one(fd, cfg):
     steps = 37
-    ref = [_make(fd, sp, steps, kernel=0) for sp in SPECS]
+    ref = [_make(fd, sp, steps, kernel=1) for sp in SPECS]
     for s in ref:
         s.step(steps)
-    sims = [_make(fd, sp, steps) for sp in SPECS]
+    sims = [_make(fd, sp, steps, kernel=1) for sp in SPECS]
     b = fd.Batch(sims)
     b.set_config(*cfg)
     b.step(10)
@@ -118,16 +120,17 @@ def test_solo_grids_equal_their_own_path(fd):
     """Grids of at least the threshold step with their handle's own kernel on
     the batch's stream; the rest share the persistent kernel."""
     steps = 41
-    thr = 150000                          # (48, 44, 90) and (64, 64, 128) step alone
-    big = [sp[0] * sp[1] * sp[2] >= thr for sp in SPECS]
+    thr = 150000                          # (48, 44, 90) and (64, 64, 128) step alone,
+    big = [sp[0] * sp[1] * sp[2] >= thr or sp[3] == 2 for sp in SPECS]   # as do the CPML grids
     sims = [_make(fd, sp, steps) for sp in SPECS]
-    ref = [_make(fd, sp, steps, kernel=None if bg else 0) for sp, bg in zip(SPECS, big)]
-    for r in ref:
-        r.step(steps)
+    ref = [_make(fd, sp, steps, kernel=None if bg else 1) for sp, bg in zip(SPECS, big)]
+    for r in ref:   # in the batch's calls: an odd call ends on one step of path 1 on the two-step path
+        r.step(13)
+        r.step(28)
     b = fd.Batch(sims)
-    b.set_config(256, 1 << 16, 5)
+    b.set_config(32, 5)
     b.set_solo(thr)
-    assert b.solo == {"min_cells": thr, "n_solo": 2}
+    assert b.solo == {"min_cells": thr, "n_solo": 3}
     b.step(13)
     b.step(28)
     b.sync()
@@ -141,39 +144,39 @@ def test_solo_grids_equal_their_own_path(fd):
     b.set_solo(1)
     assert b.solo["n_solo"] == len(SPECS)
     b.set_solo(-1)
-    assert b.solo["n_solo"] == 0
+    assert b.solo["n_solo"] == 2         # the CPML grids
     with pytest.raises(fd.FdtdError):
         b.set_solo(-2)
 
 
 def test_tuner_steps_are_real_steps(fd):
     steps = 200
-    # kernel 0 on every handle: a grid that the tuner makes step alone then
-    # runs the same per-cell code as inside the persistent kernel
-    sims = [_make(fd, sp, steps, kernel=0) for sp in SPECS]
+    # path 1 on every handle: a grid that the tuner makes step alone then
+    # runs the same tile code as inside the persistent kernel
+    sims = [_make(fd, sp, steps, kernel=1) for sp in SPECS]
     b = fd.Batch(sims)
     used = b.tune(trial_steps=2)
     assert used > 0 and all(s.steps_done == used for s in sims)
     b.step(steps - used)
     b.sync()
-    ref = [_make(fd, sp, steps, kernel=0) for sp in SPECS]
+    ref = [_make(fd, sp, steps, kernel=1) for sp in SPECS]
     for r in ref:
         r.step(steps)
     for s, r in zip(sims, ref):
         for c in range(6):
             assert np.array_equal(s.field(c), r.field(c))
     cfg = b.config
-    assert cfg["threads"] in (128, 256) and cfg["steps_per_launch"] == 8
+    assert cfg["chunk_planes"] in (16, 32, 64, 128, 256) and cfg["steps_per_launch"] == 8
     assert b.solo["min_cells"] >= -1
 
 
 def test_mixing_batch_and_single_steps(fd):
     steps = 30
-    sims = [_make(fd, sp, steps) for sp in SPECS[:4]]
-    ref = [_make(fd, sp, steps, kernel=0) for sp in SPECS[:4]]
+    sims = [_make(fd, sp, steps, kernel=1) for sp in SPECS[:4]]
+    ref = [_make(fd, sp, steps, kernel=1) for sp in SPECS[:4]]
     b = fd.Batch(sims)
     b.step(7)
-    sims[1].set_kernel(0)
+    sims[1].set_kernel(1)
     sims[1].step(3)          # one simulation ahead of the others
     b.step(11)
     for r, n in zip(ref, (18, 21, 18, 18)):
@@ -190,11 +193,11 @@ def test_batch_errors(fd):
     with pytest.raises(fd.FdtdError):
         b.step(11)            # trace capacity
     with pytest.raises(fd.FdtdError):
-        b.set_config(100, 1 << 16, 8)
+        b.set_config(0, 8)
     with pytest.raises(fd.FdtdError):
-        b.set_config(512, 1 << 16, 8)
+        b.set_config(64, 0)
     with pytest.raises(fd.FdtdError):
-        b.set_config(256, 1 << 16, 65)
+        b.set_config(64, 65)
     with pytest.raises(fd.FdtdError):
         fd.Batch([sims[0], sims[0]])
     with pytest.raises(fd.FdtdError):
