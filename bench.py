@@ -598,7 +598,13 @@ def run_batch(args):
         return time.perf_counter() - t0
 
     b = fd.Batch(sims)
-    used = b.tune(trial_steps=2)
+    if args.chunk_planes:
+        b.set_config(args.chunk_planes, 8)
+    if args.batch_mode == "tuned":
+        used = b.tune(trial_steps=2)
+    else:
+        used = 0
+        b.set_solo(-1 if args.batch_mode == "persistent" else 1)
     b.step(args.warmup)
     b.sync()
     clocks = ClockSampler(local)
@@ -607,25 +613,31 @@ def run_batch(args):
     t_batch = timed(lambda: (b.step(steps), b.sync()))
     clk = clocks.stop()
     cfg, graph, solo = b.config, b.graph_mode, b.solo
-    # each way alone: every grid in the persistent kernel, every grid on the
-    # solo streams
-    ways = {}
-    for name, thr in (("persistent_only", -1), ("solo_streams_only", 1)):
-        b.set_solo(thr)
-        b.step(2)
-        b.sync()
-        ways[name] = timed(lambda: (b.step(steps), b.sync()))
-    b.set_solo(solo["min_cells"])
-    t_fused = timed(lambda: [s.step(steps) for s in sims])
-    for s in sims:
-        s.set_kernel(0)
-    t_unfused = timed(lambda: [s.step(steps) for s in sims])
+    g = lambda t: round(cells * steps / t / 1e9, 2)
+    extra = {}
+    if args.batch_mode == "tuned":
+        # each way alone: every grid in the persistent kernel, every grid on
+        # the solo streams
+        ways = {}
+        for name, thr in (("persistent_only", -1), ("solo_streams_only", 1)):
+            b.set_solo(thr)
+            b.step(2)
+            b.sync()
+            ways[name] = timed(lambda: (b.step(steps), b.sync()))
+        b.set_solo(solo["min_cells"])
+        t_fused = timed(lambda: [s.step(steps) for s in sims])
+        for s in sims:
+            s.set_kernel(0)
+        t_unfused = timed(lambda: [s.step(steps) for s in sims])
+        extra = {"persistent_only_gcells": g(ways["persistent_only"]),
+                 "solo_streams_only_gcells": g(ways["solo_streams_only"]),
+                 "one_by_one_fused_gcells": g(t_fused), "one_by_one_unfused_gcells": g(t_unfused),
+                 "batch_over_fused": round(t_fused / t_batch, 3), "batch_over_unfused": round(t_unfused / t_batch, 3)}
     b.close()
     for s in sims:
         s.close()
     if rank != 0:
         return None
-    g = lambda t: round(cells * steps / t / 1e9, 2)
     return {"metric": "Gcell-updates/s", "value": g(t_batch), "unit": "Gcell/s", "solver": "batch",
             "n_gpus": ws, "steps": steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
             "data": "synthetic",
@@ -634,12 +646,8 @@ def run_batch(args):
                                  else "nx, ny in [64, 256], nz in [64, 512]") + ", seeded", "boundary": "mur1",
                        "dx_m": dx, "probes_each": 8, **cfg, "graph_replay": bool(graph == 1),
                        "solo_min_cells": solo["min_cells"], "solo_grids": solo["n_solo"],
-                       "tuner_trial_steps": used},
-            "persistent_only_gcells": g(ways["persistent_only"]),
-            "solo_streams_only_gcells": g(ways["solo_streams_only"]),
-            "one_by_one_fused_gcells": g(t_fused), "one_by_one_unfused_gcells": g(t_unfused),
-            "batch_over_fused": round(t_fused / t_batch, 3), "batch_over_unfused": round(t_unfused / t_batch, 3),
-            "clocks": clk}
+                       "tuner_trial_steps": used, "batch_mode": args.batch_mode},
+            **extra, "clocks": clk}
 
 
 # Table I: GTX285 seconds per N^2 run (step count not printed; read as N steps)
@@ -823,6 +831,10 @@ def main():
     ap.add_argument("--cyl-kernel", type=int, default=-1, help="cyl kernel (-1: library default)")
     ap.add_argument("--kernel", type=int, default=-1,
                     help="3D field-update path (fdtd_set_kernel; -1: library default)")
+    ap.add_argument("--batch-mode", choices=["tuned", "persistent", "solo"], default="tuned",
+                    help="batch: the autotuner's choice (with each way alone and one by one for comparison), "
+                         "or only the persistent kernel, or only the solo streams")
+    ap.add_argument("--chunk-planes", type=int, default=0, help="batch: z planes per tile item (0: default)")
     ap.add_argument("--batch-kind", choices=["config4", "small"], default="config4",
                     help="batch workload: 64 grids 64^3 .. 256x256x512, or 256 grids 32^3 .. 96^3")
     ap.add_argument("--seg-rows", type=int, default=0, help="cyl rows per segment (0: automatic)")

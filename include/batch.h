@@ -3,14 +3,16 @@
  *
  * A batch borrows n simulation handles (fdtd.h) on one device, each with its
  * own grid, boundary, shower (Sec. III.B) and detectors, and advances all of
- * them with one persistent kernel per launch: every step of Sec. III.A runs
- * as two phases over a shared work queue -- first (simulation, tile of 128
- * columns x 8 rows, z chunk) items, each the one-pass H and E update of that
- * tile with the shower's current and the CPML, then the Mur faces and the
- * detector readout -- separated by grid-wide barriers whose waits are
- * bounded (FDTD_ERR_TIMEOUT if one gives up).  The kernel is a cooperative
- * launch of one block per SM; the launch, with the reset of its queue
- * counters, is captured once in a CUDA graph and replayed.  A tile is
+ * them with one persistent kernel per launch: every step of Sec. III.A of a
+ * simulation is a set of work items on a shared queue -- (simulation, tile
+ * of 128 columns x 8 rows, z chunk) items, each the one-pass H and E update
+ * of that tile with the shower's current, then pieces of the Mur faces and
+ * the detector readout -- and an item waits only for the items of its own
+ * simulation it depends on (per-simulation completion counts, no grid-wide
+ * barrier inside a launch); every wait is bounded (FDTD_ERR_TIMEOUT if one
+ * gives up).  The kernel is a cooperative launch of one block per SM; the
+ * launch, with the reset of its counters, is captured once in a CUDA graph
+ * and replayed.  A tile is
  * updated by the same code as the handle's one-pass tile path
  * (fdtd_set_kernel 1), and the faces and detectors by that of its own Mur and
  * readout kernels, so a batched step gives the numbers of fdtd_step on the
@@ -62,7 +64,7 @@ int fdtd_batch_sync(fdtd_batch_t b);
  * Launch configuration: z planes per chunk of a tile item (>= 1; the planes
  * between a CPML grid's z layers are cut into chunks of about this many, the
  * layers are chunks of their own; fewer planes per chunk where a long chunk's
- * coefficient table would crowd out the stage ring; default 128), steps per
+ * coefficient table would crowd out the stage ring; default 256), steps per
  * persistent launch (1 .. 64; default 8).
  */
 int fdtd_batch_set_config(fdtd_batch_t b, int chunk_planes, int steps_per_launch);
@@ -71,7 +73,7 @@ int fdtd_batch_get_config(fdtd_batch_t b, int *chunk_planes, int *steps_per_laun
 /*
  * Autotuner: first the solo threshold (none, every simulation alone, or a
  * power of two between the smallest and the largest grid), then the chunk
- * length of the persistent kernel's tile items (16 .. 256 planes).  It runs
+ * length of the persistent kernel's tile items (64 .. 512 planes).  It runs
  * trial_steps >= 1 steps of the batch itself with each candidate, times each
  * on the device, keeps the fastest and returns the steps it used in
  * *steps_used.  The trial steps are real steps of every simulation (a
@@ -93,14 +95,15 @@ int fdtd_batch_set_solo(fdtd_batch_t b, long long min_cells);
 int fdtd_batch_get_solo(fdtd_batch_t b, long long *min_cells, int *n_solo);
 
 /*
- * Bound of every grid-barrier wait of the persistent kernel, in SM clock
- * cycles (0: the default, FDTD_BATCH_DEFAULT_WAIT_CYCLES, about two seconds).
+ * Bound of every wait of the persistent kernel (for the items an item
+ * depends on, and the grid barrier that ends a launch), in SM clock cycles
+ * (0: the default, FDTD_BATCH_DEFAULT_WAIT_CYCLES, about two seconds).
  * A wait that runs out records the failure on the device and the kernel
  * returns; fdtd_batch_sync then reports FDTD_ERR_TIMEOUT for the batch and
  * for every simulation that shared the persistent kernel (left part-way
  * through a step, so its handle cannot be stepped again: the status is
  * sticky), and later persistent launches of the batch return at once.  A
- * small limit makes a barrier give up while the other blocks are still at
+ * small limit makes a wait give up while the items it waits for are still at
  * work, which is how the timeout path is tested.  FDTD_ERR_ARG for
  * cycles < 0.
  */

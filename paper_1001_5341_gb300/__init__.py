@@ -595,7 +595,7 @@ class Batch:
     def sync(self):
         check(fdtd_batch_sync(self.h), "fdtd_batch_sync")
 
-    def set_config(self, chunk_planes=128, steps_per_launch=8):
+    def set_config(self, chunk_planes=256, steps_per_launch=8):
         """z planes per chunk of the persistent kernel's tile items, steps per launch."""
         check(fdtd_batch_set_config(self.h, chunk_planes, steps_per_launch), "fdtd_batch_set_config")
 

@@ -1,7 +1,6 @@
 // batch.cu -- many simulations in one persistent kernel (batch.h).
 //
-// Work queue.  For each step the kernel runs two phases; in each phase every
-// block takes items from an atomic counter until the phase's items are gone:
+// Work queue.  Every step of every simulation is two kinds of items:
 //   F: item = (simulation q, tile of 128 columns x 8 rows, z chunk of q): the
 //      one-pass step of that tile (H^{n+1/2} and E^{n+1} with the shower's
 //      current, Sec. III.A-B), the block body of the handle's tile path
@@ -11,10 +10,19 @@
 //      then the readout of E^{n+1} (the code of the handle's own Mur and
 //      detector kernels).  An x face is a strided walk through memory (one
 //      node per row), so faces are cut into pieces that many SMs share.
-// Between phases a grid-wide barrier (all blocks resident: a cooperative
-// launch of one block per SM) with a bounded wait; a step whose simulations
-// have neither Mur faces nor detectors has no M phase.  The numbers are those
-// of the handle stepped on its tile path (fdtd_set_kernel 1), bit for bit.
+// The blocks (one per SM, all resident: a cooperative launch) take items from
+// one atomic counter in the order (step, kind, simulation, item).  (Placing a
+// simulation's M items a wave of F items after its own, for L2 hits on its
+// faces, measured slower: the waits grew more than the reads shrank.)  An item
+// waits only for its own simulation: an F item of step s for all F and M
+// items of step s-1 of that simulation, an M item for all its F items of
+// step s; completion is counted per simulation and kind.  A simulation thus
+// runs its Mur faces and detectors, and starts its next step, while the
+// blocks still finish other simulations' tiles: no grid-wide barrier inside a
+// launch.  Every wait is for items taken earlier from the counter (by blocks
+// that are running), so the launch cannot deadlock; each wait is bounded
+// (FDTD_ERR_TIMEOUT when it gives up).  The numbers are those of the handle
+// stepped on its tile path (fdtd_set_kernel 1), bit for bit.
 // The kernel takes PEC and Mur grids: its tile arguments come from memory (a
 // copy per item in shared memory), not from the parameter bank, and with them
 // the CPML instances of the tile body need more registers than a block of
@@ -61,12 +69,33 @@ struct BArgs {
     int nsim;
     const int *fstart;     // [nsim + 1] prefix sums of F items
     const int *mstart;     // [nsim + 1] prefix sums of M items
+    const int *seg;        // [nseg + 1] item order within a step: segment g holds items
+                           // [seg[g], seg[g+1]) of kind and simulation segq[g] (2 q + 1 for M)
+    const int *segq;
+    int nseg;
     int steps;
-    unsigned *ctr;         // [2 * steps] queue counters, zero at launch
+    unsigned *ctr;         // [1 + 2 nsim] work counter, then F and M items done per simulation; zero at launch
     unsigned *bar;         // [2] barrier count and generation, zero at launch
     int *flags;
-    long long spin;        // clock cycles a barrier wait may take
+    long long spin;        // clock cycles a wait may take
 };
+
+// Wait (bounded by spin cycles; thread 0) until *c >= target.  False when the
+// wait gave up (flag bit 1 set) or another block recorded a failure.
+__device__ bool wait_count(const unsigned *c, unsigned target, int *flags, long long spin) {
+    const volatile unsigned *v = c;
+    if (*v >= target) return true;
+    const long long t0 = clock64();
+    while (*v < target) {
+        if (*(volatile int *)flags) return false;
+        if (clock64() - t0 > spin) {
+            atomicOr(flags, 2);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    return true;
+}
 
 // Grid-wide barrier: arrive, then wait (bounded by spin cycles) for the
 // generation to move.  A block whose wait gives up sets flag bit 1.  Returns
@@ -116,9 +145,9 @@ __device__ __forceinline__ int find_sim(const int *start, int nsim, int it) {
 __global__ void __launch_bounds__(NT, 1) k_batch(BArgs A) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(16) vt::Args s_a;   // the item's tile arguments
-    __shared__ int s_item, s_q;
+    __shared__ int s_go, s_step, s_q, s_item;   // s_item: F item index, or -1 - M item index
     const int tid = threadIdx.x;
-    const int fitems = A.fstart[A.nsim], mitems = A.mstart[A.nsim];
+    const int fitems = A.fstart[A.nsim], mitems = A.mstart[A.nsim];   // per step
     // an earlier launch (or a block of this one) gave up: the simulations are
     // in an unknown state.  One read per block, so that its threads leave
     // together (thread 0 alone drives the work queue).
@@ -126,20 +155,39 @@ __global__ void __launch_bounds__(NT, 1) k_batch(BArgs A) {
     if (tid == 0) s_stop = *(volatile int *)A.flags;
     __syncthreads();
     if (s_stop) return;
-    for (int s = 0; s < A.steps; ++s) {
-        // ---- F: the tiles of every simulation ----
-        for (;;) {
-            if (tid == 0) {
-                const int it = (int)atomicAdd(A.ctr + 2 * s, 1u);
-                s_item = it;
-                if (it < fitems) s_q = find_sim(A.fstart, A.nsim, it);
+    const unsigned per_step = (unsigned)(fitems + mitems);
+    const unsigned total = per_step * (unsigned)A.steps;
+    unsigned *doneF = A.ctr + 1, *doneM = A.ctr + 1 + A.nsim;
+    for (;;) {
+        if (tid == 0) {
+            const unsigned it = atomicAdd(A.ctr, 1u);
+            int ok = it < total;
+            if (ok) {
+                const int s = (int)(it / per_step), r = (int)(it % per_step);
+                const int g = find_sim(A.seg, A.nseg, r);
+                const bool f = (A.segq[g] & 1) == 0;
+                const int q = A.segq[g] >> 1;
+                const unsigned nf = (unsigned)(A.fstart[q + 1] - A.fstart[q]);
+                const unsigned nm = (unsigned)(A.mstart[q + 1] - A.mstart[q]);
+                // an F item: all of q's step s-1 done; an M item: q's F items of step s done
+                ok = f ? wait_count(doneF + q, nf * s, A.flags, A.spin) && wait_count(doneM + q, nm * s, A.flags, A.spin)
+                       : wait_count(doneF + q, nf * (s + 1), A.flags, A.spin);
+                __threadfence();
+                // the other blocks' stores of the fields, ahead of this block's tensor loads
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                s_step = s;
+                s_q = q;
+                s_item = f ? r - A.seg[g] : -1 - (r - A.seg[g]);
             }
-            __syncthreads();
-            const int it = s_item;
-            if (it >= fitems) break;
-            const int q = s_q;
-            const BSim &S = A.sims[q];
-            const int cur = S.cur ^ (s & 1);
+            s_go = ok;
+        }
+        __syncthreads();
+        if (!s_go) break;
+        const int s = s_step, q = s_q, item = s_item;
+        const BSim &S = A.sims[q];
+        const int cur = S.cur ^ (s & 1);
+        if (item >= 0) {
+            // ---- F: a tile ----
             {
                 static_assert(sizeof(vt::Args) % 8 == 0, "Args copied in 8-byte words");
                 const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&S.a[cur]);
@@ -152,29 +200,15 @@ __global__ void __launch_bounds__(NT, 1) k_batch(BArgs A) {
                 s_a.flags = A.flags;
             }
             __syncthreads();
-            const int local = it - A.fstart[q];
-            const int ns = vt::tile_block<false>(s_a, *S.maps, local % S.tiles, local / S.tiles, smem_raw);
+            const int ns = vt::tile_block<false>(s_a, *S.maps, item % S.tiles, item / S.tiles, smem_raw);
             vt::end_tile(smem_raw, ns);
-        }
-        if (!grid_sync(A.bar, A.flags, A.spin)) return;
-        if (mitems == 0) continue;
-        // ---- M: Mur faces, then detectors, of E^{n+1} ----
-        for (;;) {
-            if (tid == 0) {
-                const int it = (int)atomicAdd(A.ctr + 2 * s + 1, 1u);
-                s_item = it;
-                if (it < mitems) s_q = find_sim(A.mstart, A.nsim, it);
-            }
-            __syncthreads();
-            const int it = s_item;
-            if (it >= mitems) break;
-            const BSim &S = A.sims[s_q];
-            const int cur = S.cur ^ (s & 1);
+        } else {
+            // ---- M: a piece of a Mur face, or the detectors, of E^{n+1} ----
             const vt::Args &a = S.a[cur];
             const Grid &g = a.g;
             const float *in = S.a[cur ^ 1].oex;   // E^n: the set this step reads
             float *out = a.oex;                   // E^{n+1}
-            const int m = it - A.mstart[s_q];
+            const int m = -1 - item;
             if (m < S.mface[6]) {
                 // a piece of face f: (a, b) over (j, k), (i, k) or (i, j)
                 int f = 0;
@@ -197,10 +231,14 @@ __global__ void __launch_bounds__(NT, 1) k_batch(BArgs A) {
                     o[1] = p.cxy[2 * t] * ex + p.cxy[2 * t + 1] * ey;
                 }
             }
-            __syncthreads();   // s_item is read again by thread 0
         }
-        if (!grid_sync(A.bar, A.flags, A.spin)) return;
+        // the item's stores, then its count (release to the items that wait for it)
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) atomicAdd(item >= 0 ? doneF + q : doneM + q, 1u);
     }
+    // every item of the launch done before the descriptors advance
+    if (!grid_sync(A.bar, A.flags, A.spin)) return;
     if (blockIdx.x == 0)
         for (int q = tid; q < A.nsim; q += NT) {
             A.sims[q].cur ^= A.steps & 1;
@@ -221,7 +259,8 @@ struct fdtd_batch {
     cudaEvent_t ev;
     BSim *d_sims;
     vt::Maps *d_maps;
-    int *d_fstart, *d_mstart;
+    int *d_fstart, *d_mstart, *d_seg, *d_segq;
+    int nseg;
     unsigned *d_ctr, *d_bar;
     int *d_flags;
     int chunk_planes, steps_per_launch;
@@ -332,7 +371,20 @@ int refresh(fdtd_batch *b) {
         fs[q + 1] = fs[q] + S.items;
         ms[q + 1] = ms[q] + S.mface[6] + (h->np > 0 ? 1 : 0);
     }
-    if (note(b, cudaMemcpyAsync(b->d_sims, d.data(), n * sizeof(BSim), cudaMemcpyHostToDevice, b->stream)) ||
+    // item order of a step: the F items of each simulation in turn, then the
+    // M items of each
+    std::vector<int> seg{0}, segq;
+    for (int kind = 0; kind < 2; ++kind)
+        for (int q = 0; q < n; ++q) {
+            const int count = kind == 0 ? fs[q + 1] - fs[q] : ms[q + 1] - ms[q];
+            if (count <= 0) continue;
+            segq.push_back(2 * q + kind);
+            seg.push_back(seg.back() + count);
+        }
+    b->nseg = (int)segq.size();
+    if (note(b, cudaMemcpyAsync(b->d_seg, seg.data(), seg.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream)) ||
+        note(b, cudaMemcpyAsync(b->d_segq, segq.data(), segq.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream)) ||
+        note(b, cudaMemcpyAsync(b->d_sims, d.data(), n * sizeof(BSim), cudaMemcpyHostToDevice, b->stream)) ||
         note(b, cudaMemcpyAsync(b->d_maps, maps.data(), n * sizeof(vt::Maps), cudaMemcpyHostToDevice, b->stream)) ||
         note(b, cudaMemcpyAsync(b->d_fstart, fs.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, b->stream)) ||
         note(b, cudaMemcpyAsync(b->d_mstart, ms.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, b->stream)))
@@ -368,12 +420,15 @@ cudaError_t issue(fdtd_batch *b, int steps) {
     A.nsim = b->nshared;
     A.fstart = b->d_fstart;
     A.mstart = b->d_mstart;
+    A.seg = b->d_seg;
+    A.segq = b->d_segq;
+    A.nseg = b->nseg;
     A.steps = steps;
     A.ctr = b->d_ctr;
     A.bar = b->d_bar;
     A.flags = b->d_flags;
     A.spin = b->spin;
-    cudaError_t e = cudaMemsetAsync(b->d_ctr, 0, 2 * steps * sizeof(unsigned), b->stream);
+    cudaError_t e = cudaMemsetAsync(b->d_ctr, 0, (1 + 2 * (size_t)b->nshared) * sizeof(unsigned), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), b->stream);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -468,7 +523,7 @@ int fdtd_batch_create(fdtd_batch_t *out, const fdtd_t *sims, int n) {
     b->sims.assign(sims, sims + n);
     b->dev = dev;
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
-    b->chunk_planes = 128;
+    b->chunk_planes = 256;
     b->steps_per_launch = 8;
     b->solo_cells = -1;
     b->nshared = n;
@@ -484,8 +539,10 @@ int fdtd_batch_create(fdtd_batch_t *out, const fdtd_t *sims, int n) {
         cudaMalloc(&b->d_sims, n * sizeof(BSim)) != cudaSuccess ||
         cudaMalloc(&b->d_maps, n * sizeof(vt::Maps)) != cudaSuccess ||
         cudaMalloc(&b->d_fstart, (n + 1) * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&b->d_seg, (2 * n + 1) * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&b->d_segq, 2 * n * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&b->d_mstart, (n + 1) * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&b->d_ctr, 2 * MAX_STEPS_PER_LAUNCH * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&b->d_ctr, (1 + 2 * (size_t)n) * sizeof(unsigned)) != cudaSuccess ||
         cudaMalloc(&b->d_bar, 2 * sizeof(unsigned)) != cudaSuccess ||
         cudaMalloc(&b->d_flags, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
@@ -509,6 +566,8 @@ void fdtd_batch_destroy(fdtd_batch_t b) {
     if (b->d_sims) cudaFree(b->d_sims);
     if (b->d_maps) cudaFree(b->d_maps);
     if (b->d_fstart) cudaFree(b->d_fstart);
+    if (b->d_seg) cudaFree(b->d_seg);
+    if (b->d_segq) cudaFree(b->d_segq);
     if (b->d_mstart) cudaFree(b->d_mstart);
     if (b->d_ctr) cudaFree(b->d_ctr);
     if (b->d_bar) cudaFree(b->d_bar);
@@ -692,7 +751,7 @@ int fdtd_batch_tune(fdtd_batch_t b, int trial_steps, int *steps_used) {
         fdtd_batch_set_solo(b, best);
     }
     // then the z chunk length of the persistent kernel's tiles, if it has work
-    const int cpl[5] = {16, 32, 64, 128, 256};
+    const int cpl[4] = {64, 128, 256, 512};
     float best_ms = 1e30f;
     int best_c = b->chunk_planes, rc = FDTD_OK;
     refresh(b);

@@ -166,7 +166,7 @@ def test_tuner_steps_are_real_steps(fd):
         for c in range(6):
             assert np.array_equal(s.field(c), r.field(c))
     cfg = b.config
-    assert cfg["chunk_planes"] in (16, 32, 64, 128, 256) and cfg["steps_per_launch"] == 8
+    assert cfg["chunk_planes"] in (64, 128, 256, 512) and cfg["steps_per_launch"] == 8
     assert b.solo["min_cells"] >= -1
 
 

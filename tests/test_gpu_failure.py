@@ -4,10 +4,12 @@
   with fdtd_set_field spreads through the grid and is reported as
   FDTD_ERR_UNSTABLE by the next synchronising call; the status is sticky until
   fdtd_reset; with the watchdog off nothing is reported.
-* The bounded grid barrier of the batched persistent kernel: with a wait limit
-  of one clock cycle a barrier gives up while the other blocks still work; the
-  kernel returns, and the batch and every simulation that shared the kernel
-  report FDTD_ERR_TIMEOUT.  The context stays usable.
+* The bounded waits of the batched persistent kernel (an item waiting for the
+  items of its simulation it depends on, the grid barrier that ends a
+  launch): with a wait limit of one clock cycle a wait gives up while the
+  other blocks still work; the kernel returns, and the batch and every
+  simulation that shared the kernel report FDTD_ERR_TIMEOUT.  The context
+  stays usable.
 """
 import numpy as np
 import pytest
@@ -92,7 +94,7 @@ def test_batch_barrier_wait_runs_out(fd):
     sims = [fd.Simulation(n, n, 2 * n, dx, dt, W.EPS_R_ICE, boundary=fd.FDTD_PEC) for n in (24, 32, 40)]
     b = fd.Batch(sims)
     assert fd.fdtd_batch_set_wait_limit(b.h, -1) == -1
-    b.set_wait_limit(1)           # one clock cycle: a barrier gives up at once
+    b.set_wait_limit(1)           # one clock cycle: a wait gives up at once
     b.step(3)
     with pytest.raises(fd.FdtdError) as ex:
         b.sync()
