@@ -650,6 +650,76 @@ def run_batch(args):
             **extra, "clocks": clk}
 
 
+def run_gemm(args):
+    """The surrogate's bf16 GEMM (sur_gemm_bf16) on its two kernels: the
+    tcgen05 kernel (TMEM accumulator, TMA-staged 128-byte-swizzled slices)
+    and the mma.sync kernel.  Shapes: the lattice surrogate's serving product
+    at one antenna (P profiles x T = 1024 samples x 96: [hi, hi, lo] x 31 bins
+    padded to 96), whose output write makes it HBM-bound, and an 8192^3
+    product for the kernels' tensor throughput.  CUDA events on the launching
+    stream; the serving product rotates over outputs larger than L2."""
+    import torch
+    import ctypes as C
+    torch.cuda.set_device(0)
+    import paper_1001_5341_gb300 as fd
+    peaks = {}
+    try:
+        with open(MEASURED_PEAKS) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    tf_peak = float(peaks.get("bf16_tflops", 1900.0))
+    hbm, _ = hbm_peak()
+    steps = args.steps or 50
+    p = lambda t: C.c_void_p(t.data_ptr())
+    g = torch.Generator(device="cuda").manual_seed(9009)
+    res = {}
+
+    def time_it(fn, n):
+        for _ in range(3):
+            fn(0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(n):
+            fn(i)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    for name, (M, N, K) in (("serving", (args.gemm_profiles, 1024, 96)), ("square", (8192, 8192, 8192))):
+        A = torch.randn(M, K, generator=g, device="cuda").to(torch.bfloat16)
+        B = torch.randn(N, K, generator=g, device="cuda").to(torch.bfloat16)
+        nout = max(1, (256 << 20) // (M * N * 4)) if name == "serving" else 1
+        Ys = [torch.empty(M, N, dtype=torch.float32, device="cuda") for _ in range(nout)]
+        for path, label in ((0, "tcgen05"), (1, "mma_sync")):
+            fd.check(fd.sur_gemm_set_path(path), "path")
+            n0 = fd.sur_gemm_tc_launches()
+            fn = lambda i: fd.check(fd.sur_gemm_bf16(p(A), K, 1, p(B), K, 1, p(Ys[i % nout]), N, None, M, N, K, None,
+                                                     0, 0, None), "gemm")
+            ms = time_it(fn, steps if name == "serving" else max(3, steps // 10))
+            ran_tc = fd.sur_gemm_tc_launches() > n0
+            flops = 2.0 * M * N * K
+            byts = M * N * 4 + (M + N) * K * 2
+            res[f"{name}_{label}"] = {"shape_MNK": [M, N, K], "ms": round(ms, 5),
+                                      "tflops": round(flops / ms / 1e9, 2),
+                                      "frac_of_bf16_peak": round(flops / ms / 1e9 / tf_peak, 4),
+                                      "gbs": round(byts / ms / 1e6, 1), "frac_of_hbm": round(byts / ms / 1e6 / hbm, 4),
+                                      "tcgen05_kernel": bool(ran_tc)}
+        fd.check(fd.sur_gemm_set_path(0), "path")
+        assert fd.sur_gemm_tc_failed() == 0
+        del A, B, Ys
+        torch.cuda.empty_cache()
+    sv = res["serving_tcgen05"]
+    return {"metric": "TFLOP/s", "value": sv["tflops"], "unit": "TFLOP/s", "solver": "gemm", "n_gpus": 1,
+            "steps": steps, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"surrogate-gemm-{args.gemm_profiles}x1024x96",
+                       "inputs_vs_l2": "serving outputs rotate over > 256 MB"},
+            "roofline": {"bound": "hbm", "achieved": sv["gbs"], "peak": hbm, "unit": "GB/s",
+                         "frac": sv["frac_of_hbm"], "traffic": None},
+            "bf16_peak_tflops": tf_peak, "kernels": res}
+
+
 # Table I: GTX285 seconds per N^2 run (step count not printed; read as N steps)
 PAPER_T_GPU = {256: 0.040, 512: 0.186, 1024: 1.167, 2048: 8.372, 4096: 67.617, 8192: 681.082}
 
@@ -822,7 +892,7 @@ def main():
     ap.add_argument("--nz", type=int, default=0,
                     help="z planes of a reduced grid with the benchmark physics (profiler captures "
                          "of a few GB); 0 = the benchmark grid")
-    ap.add_argument("--solver", choices=["yee3d", "cyl", "adjoint", "batch"], default="yee3d",
+    ap.add_argument("--solver", choices=["yee3d", "cyl", "adjoint", "batch", "gemm"], default="yee3d",
                     help="cyl: the paper's 2D axisymmetric solver on an n x n grid (Table I); "
                          "adjoint: gradient of a detector misfit w.r.t. the charge table")
     ap.add_argument("--workload", choices=sorted(WORKLOAD_SEEDS), default="greisen384",
@@ -838,6 +908,7 @@ def main():
     ap.add_argument("--batch-kind", choices=["config4", "small"], default="config4",
                     help="batch workload: 64 grids 64^3 .. 256x256x512, or 256 grids 32^3 .. 96^3")
     ap.add_argument("--seg-rows", type=int, default=0, help="cyl rows per segment (0: automatic)")
+    ap.add_argument("--gemm-profiles", type=int, default=8192, help="gemm: profiles of the serving product")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -845,6 +916,8 @@ def main():
         line = run_adjoint(args)
     elif args.solver == "batch":
         line = run_batch(args)
+    elif args.solver == "gemm":
+        line = run_gemm(args)
     elif args.solver == "cyl":
         if args.impl == "reference":
             line = run_cyl_reference(args)

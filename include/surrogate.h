@@ -44,6 +44,25 @@ int sur_gemm_bf16(const void *A, int lda, int a_kmajor, const void *B, int ldb, 
                   void *Yb, int M, int N, int K, const float *bias, int relu, int accumulate, void *stream);
 
 /*
+ * The kernels behind sur_gemm_bf16.  With both operands K-major, lda and ldb
+ * multiples of 8 and A, B 16-byte aligned, the product runs on the
+ * fifth-generation tensor cores (tcgen05.mma, accumulator in tensor memory,
+ * operands staged by TMA, 128 x 128 output tiles); any other layout on the
+ * warp-level mma.sync kernel.  sur_gemm_set_path(p) selects for later calls
+ * (process-wide): 0 that automatic choice (the default), 1 mma.sync always,
+ * 2 tcgen05 with 128-byte swizzled operand slices only, 3 tcgen05 with
+ * unswizzled core-matrix slices only (K a multiple of 8); with 2 or 3 a
+ * product the tcgen05 kernel cannot take returns FDTD_ERR_ARG.
+ * sur_gemm_tc_launches: launches of the tcgen05 kernel so far.
+ * sur_gemm_tc_failed: synchronises the device and returns 1 if a bounded
+ * pipeline wait of the tcgen05 kernel gave up since the last call (that
+ * CTA's outputs were not written), else 0; FDTD_ERR_CUDA on a CUDA error.
+ */
+int sur_gemm_set_path(int path);
+long long sur_gemm_tc_launches(void);
+int sur_gemm_tc_failed(void);
+
+/*
  * 1D convolution, f32 activations, bf16 weights, f32 accumulation:
  *   y[b][o][l] = bias[o] + sum_{c,t} w[o][c][t] x[b][c][l*stride + t - pad]
  *   (x read as 0 outside 0..lin-1), then max(., 0) if relu.
@@ -188,6 +207,15 @@ int sur_lattice_bwd(const float *dy, const float *q, const int *ant, int B, int 
                     int J, int moff, float *dG, void *stream);
 int sur_lattice_weights(const void *G, const int *ant, int A, int K, int NR, int D, int T, int S, int J, int moff,
                         void *W, void *stream);
+/* The same weights K-major, as the B operand of the tcgen05 GEMM:
+   W[a][t][koff + k] (bf16, row stride ldw >= koff + K; other columns left as
+   they are).  FDTD_ERR_ARG for bad sizes. */
+int sur_lattice_weights_kmajor(const void *G, const int *ant, int A, int K, int NR, int D, int T, int S, int J,
+                               int moff, void *W, int ldw, int koff, void *stream);
+/* out[r][0..K) = out[r][K..2K) = hi(x[r]), out[r][2K..3K) = lo(x[r]) (the
+   split of sur_split_bf16), out[r][3K..ld) = 0; x f32 [rows][K], out bf16
+   [rows][ld], ld >= 3K: the A operand of [hi, hi, lo] [W_hi; W_lo; W_hi]. */
+int sur_split3_bf16(const float *x, int rows, int K, void *out, int ld, void *stream);
 
 #ifdef __cplusplus
 }

@@ -69,6 +69,9 @@ _SIGS = {
     "cyl_rings_gaussian": (_i, [_i, _d, _d, _pd]),
     # learned surrogate kernels (surrogate.h); pointers are device addresses
     "sur_gemm_bf16": (_i, [_vp, _i, _i, _vp, _i, _i, _vp, _i, _vp, _i, _i, _i, _vp, _i, _i, _vp]),
+    "sur_gemm_set_path": (_i, [_i]),
+    "sur_gemm_tc_launches": (C.c_longlong, []),
+    "sur_gemm_tc_failed": (_i, []),
     "sur_conv1d_fwd": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _vp]),
     "sur_conv1d_bwd": (_i, [_vp, _i, _vp, _vp, _vp, _i, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _vp]),
     "sur_relu_bwd": (_i, [_vp, _vp, _vp, _vp, C.c_longlong, _vp]),
@@ -89,6 +92,8 @@ _SIGS = {
     "sur_split_bf16": (_i, [_vp, _vp, _vp, C.c_longlong, _vp]),
     "sur_lattice_bwd": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _vp, _vp]),
     "sur_lattice_weights": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _vp, _vp]),
+    "sur_lattice_weights_kmajor": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _vp, _i, _i, _vp]),
+    "sur_split3_bf16": (_i, [_vp, _i, _i, _vp, _i, _vp]),
     # batched persistent stepping (batch.h)
     "fdtd_batch_create": (_i, [C.POINTER(_vp), C.POINTER(_vp), _i]),
     "fdtd_batch_destroy": (None, [_vp]),

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libfdtd_gb300.so")
 
-SOURCES = ["fdtd_api.cu", "kernels_basic.cu", "kernels_vtile.cu", "kernels_tb2.cu", "kernels_noalloc.cu", "surrogate.cu", "cyl.cu", "adjoint.cu", "batch.cu", "spectra.cu", "tables.cpp"]
+SOURCES = ["fdtd_api.cu", "kernels_basic.cu", "kernels_vtile.cu", "kernels_tb2.cu", "kernels_noalloc.cu", "surrogate.cu", "cyl.cu", "adjoint.cu", "batch.cu", "spectra.cu", "gemm_tc.cu", "tables.cpp"]
 HEADERS = ["fdtd_internal.h", "source_term.cuh", "cell_update.cuh", "tma_pipe.cuh", "vtile_tile.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-Wall",

@@ -1,0 +1,355 @@
+// gemm_tc.cu -- the surrogate's bf16 GEMM on the fifth-generation tensor
+// cores (surrogate.h, sur_gemm_bf16 with both operands K-major).
+//
+// One CTA of four warps computes a 128 x 128 tile of Y = A B^T:
+//   * thread 0 stages K slices of A (128 rows) and B (128 rows) into shared
+//     memory with TMA (cp.async.bulk.tensor), a ring of stages tracked by
+//     mbarriers, and issues tcgen05.mma (kind::f16, M = 128, N = 128, K = 16
+//     per instruction, bf16 operands read from shared memory through matrix
+//     descriptors, f32 accumulator in tensor memory); tcgen05.commit frees a
+//     stage for the next slice once the MMAs that read it have completed;
+//   * warp 0 allocates the 128 accumulator columns of tensor memory and frees
+//     them at the end;
+//   * after the last MMA, each warp reads its 32 accumulator rows (tensor
+//     memory lanes 32w .. 32w+31) with tcgen05.ld, 32 columns at a time, turns
+//     them through a 32 x 32 tile in the idle stage memory and runs the
+//     epilogue (accumulate, bias, ReLU, f32 store and bf16 copy) with each row
+//     stored by the 32 lanes together (128-byte coalesced writes).
+// Two shared-memory layouts of the operand slices:
+//   SW = 1: 64-element (128-byte) K slices written by TMA with the 128-byte
+//     swizzle; rows 128 bytes apart, 8-row groups 1024 bytes apart; the
+//     descriptor of the k-th 16-element step starts 32 k bytes in;
+//   SW = 0: 32-element K slices as 8 x 16-byte core matrices (a 3-D tensor
+//     map over (8 elements, rows, K / 8)), 8-row groups 128 bytes apart,
+//     K-adjacent core matrices 128 x 16 bytes apart.
+// Out-of-range rows and K columns read as zeros (TMA bounds), so any M, N, K
+// work; the row strides must be multiples of 8 elements (16 bytes).
+// Every mbarrier wait is bounded; on expiry the CTA records a failure
+// (sur_gemm_tc_failed), skips its stores, waits for the MMAs it issued and
+// frees its tensor memory.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fdtd.h"
+#include "../../include/surrogate.h"
+#include "tma_pipe.cuh"
+
+namespace fdtd {
+namespace gtc {
+namespace {
+
+using namespace tma;
+
+constexpr int BM = 128, BN = 128, NT = 128;
+constexpr uint32_t TMEM_COLS = BN;   // f32 accumulator: one column per N
+
+template <int SW> struct Cfg;
+template <> struct Cfg<1> {
+    static constexpr int BK = 64, NS = 3;
+};
+template <> struct Cfg<0> {
+    static constexpr int BK = 32, NS = 4;
+};
+template <int SW> __host__ __device__ constexpr int a_bytes() { return BM * Cfg<SW>::BK * 2; }
+template <int SW> __host__ __device__ constexpr int stage_bytes() { return (BM + BN) * Cfg<SW>::BK * 2; }
+// shared memory of a CTA with ns stages (fewer stages than Cfg::NS when K
+// has fewer slices, so that more CTAs share an SM; two at least, which hold
+// the epilogue's four 32 x 33 transpose tiles)
+template <int SW> __host__ __device__ constexpr int smem_bytes(int ns) { return 1024 + ns * stage_bytes<SW>() + 256; }
+static_assert(2 * stage_bytes<0>() >= 4 * 32 * 33 * 4 && 2 * stage_bytes<1>() >= 4 * 32 * 33 * 4,
+              "transpose tiles fit in two stages");
+
+// instruction descriptor, kind::f16: D f32 (bits 4-5 = 1), A and B bf16
+// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit 17,
+// M >> 4 at bit 24
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+// shared-memory matrix descriptor: start address, leading and stride byte
+// offsets (16-byte units, 14 bits each), the fixed 0b001 at bit 46, swizzle
+// mode at bit 61 (0 none, 2 128-byte)
+__device__ __forceinline__ uint64_t mdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t swz) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46) | ((uint64_t)swz << 61);
+}
+
+__device__ __forceinline__ void tma_load2(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(sa(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(sa(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load3b(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(sa(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(sa(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// the mbarrier arrives once every tcgen05 operation this thread issued has completed
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// 32 consecutive f32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ int g_fail;   // a bounded wait gave up in some CTA
+
+template <int SW>
+__global__ void __launch_bounds__(NT, 1) k_gemm_tc(const __grid_constant__ CUtensorMap ma,
+                                                   const __grid_constant__ CUtensorMap mb, float *Y, int ldy,
+                                                   unsigned short *Yb, int M, int N, int K,
+                                                   const float *__restrict__ bias, int relu, int accumulate, int NS) {
+    typedef Cfg<SW> C;
+    constexpr int BK = C::BK, KSTEPS = BK / 16;
+    extern __shared__ unsigned char smem_raw[];
+    // 1024-byte aligned stages (the 128-byte swizzle repeats every 8 rows of 128 bytes)
+    const uint32_t base = sa(smem_raw);
+    unsigned char *sm = smem_raw + ((1024u - (base & 1023u)) & 1023u);
+    uint64_t *full = reinterpret_cast<uint64_t *>(sm + NS * stage_bytes<SW>());
+    uint64_t *empty = full + NS;
+    uint64_t *done = empty + NS;
+    uint32_t *tholder = reinterpret_cast<uint32_t *>(done + 1);
+    __shared__ int s_ok;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int nk = (K + BK - 1) / BK;
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_ok = 1;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(tholder)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tholder;
+
+    if (tid == 0) {
+        auto issue = [&](int c, int s) {
+            unsigned char *a = sm + s * stage_bytes<SW>();
+            unsigned char *b = a + a_bytes<SW>();
+            mbar_expect_tx(&full[s], (uint32_t)stage_bytes<SW>());
+            if (SW) {
+                tma_load2(a, &ma, &full[s], c * BK, m0);
+                tma_load2(b, &mb, &full[s], c * BK, n0);
+            } else {
+                tma_load3b(a, &ma, &full[s], 0, m0, c * (BK / 8));
+                tma_load3b(b, &mb, &full[s], 0, n0, c * (BK / 8));
+            }
+        };
+        bool ok = true;
+        int issued = 0;   // slices whose loads were issued
+        for (int c = 0; c < NS && c < nk; ++c) issue(c, c), ++issued;
+        int c = 0;
+        for (; c < nk; ++c) {
+            const int s = c % NS;
+            if (!mbar_wait(&full[s], (uint32_t)(c / NS) & 1u)) {
+                ok = false;
+                break;
+            }
+            fence_after();
+            const uint32_t a0 = sa(sm + s * stage_bytes<SW>()), b0 = a0 + a_bytes<SW>();
+#pragma unroll
+            for (int k = 0; k < KSTEPS; ++k) {
+                uint64_t da, db;
+                if (SW) {
+                    da = mdesc(a0 + 32u * k, 16u, 1024u, 2u);
+                    db = mdesc(b0 + 32u * k, 16u, 1024u, 2u);
+                } else {
+                    da = mdesc(a0 + 2u * k * (BM * 16u), BM * 16u, 128u, 0u);
+                    db = mdesc(b0 + 2u * k * (BN * 16u), BN * 16u, 128u, 0u);
+                }
+                mma_f16(tmem, da, db, IDESC, (c | k) != 0);
+            }
+            mma_commit(&empty[s]);
+            // refill the stage of the previous slice, whose MMAs have had a slice's time to finish
+            if (c >= 1 && c - 1 + NS < nk) {
+                const int sp = (c - 1) % NS;
+                if (!mbar_wait(&empty[sp], (uint32_t)((c - 1) / NS) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                issue(c - 1 + NS, sp);
+                ++issued;
+            }
+        }
+        mma_commit(done);   // completes once every MMA issued above has
+        if (!ok) {
+            atomicOr(&g_fail, 1);
+            s_ok = 0;
+            // let the loads in flight land before the CTA ends
+            for (int r = c + 1; r < issued; ++r) mbar_wait(&full[r % NS], (uint32_t)(r / NS) & 1u);
+        }
+    }
+    const bool dok = mbar_wait(done, 0);
+    fence_after();
+    __syncthreads();
+    if (dok && s_ok) {
+        // each warp moves its 32 rows through a 32 x 32 transpose tile in the
+        // (now idle) stage memory, so that a row is stored by 32 lanes at once
+        float *tile = reinterpret_cast<float *>(sm) + warp * (32 * 33);
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int cc = 0; cc < BN; cc += 32) {
+            uint32_t r[32];
+            tmem_ld32(trow + (uint32_t)cc, r);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(r[j]);
+            __syncwarp();
+            const int n = n0 + cc + lane;
+            const float bn = (bias && n < N) ? bias[n] : 0.f;
+#pragma unroll 4
+            for (int rr = 0; rr < 32; ++rr) {
+                const int row = m0 + warp * 32 + rr;
+                if (row < M && n < N) {
+                    const long long o = (long long)row * ldy + n;
+                    float v = tile[rr * 33 + lane];
+                    if (accumulate) v += Y[o];
+                    v += bn;
+                    if (relu) v = fmaxf(v, 0.f);
+                    Y[o] = v;
+                    if (Yb) Yb[o] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+                }
+            }
+            __syncwarp();
+        }
+    } else if (!dok && tid == 0) {
+        atomicOr(&g_fail, 1);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+bool encode_kmajor(EncodeTiled enc, CUtensorMap *m, const void *p, int rows, int K, int ld, int box_rows, int sw) {
+    if (sw) {
+        cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+        cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+        cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+        cuuint32_t es[2] = {1, 1};
+        return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(p), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    // (8 elements, rows, K / 8): core matrices of 8 rows x 16 bytes
+    cuuint64_t dims[3] = {8, (cuuint64_t)rows, (cuuint64_t)(K / 8)};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 2, 16};
+    cuuint32_t box[3] = {8, (cuuint32_t)box_rows, (cuuint32_t)(Cfg<0>::BK / 8)};
+    cuuint32_t es[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(p), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int g_path = 0;                 // sur_gemm_set_path
+long long g_launches = 0;       // launches of k_gemm_tc
+
+}  // namespace
+
+int tc_path() { return g_path; }
+
+// Whether (and how) the tcgen05 kernel runs this product: 1 (128-byte
+// swizzle), 0 (core matrices), -1 (it cannot: sur_gemm_bf16 runs mma.sync).
+int tc_layout(const void *A, int lda, int a_kmajor, const void *B, int ldb, int b_kmajor, int K) {
+    if (g_path == 1) return -1;
+    const bool kmajor = a_kmajor && b_kmajor && lda % 8 == 0 && ldb % 8 == 0 &&
+                        (reinterpret_cast<uintptr_t>(A) & 15) == 0 && (reinterpret_cast<uintptr_t>(B) & 15) == 0;
+    if (!kmajor) return -1;
+    if (g_path == 3) return K % 8 == 0 ? 0 : -1;
+    return 1;
+}
+
+int gemm_tc(int layout, const void *A, int lda, const void *B, int ldb, float *Y, int ldy, void *Yb, int M, int N,
+            int K, const float *bias, int relu, int accumulate, cudaStream_t s) {
+    EncodeTiled enc = encoder();
+    if (!enc) return FDTD_ERR_CUDA;
+    CUtensorMap ma, mb;
+    if (!encode_kmajor(enc, &ma, A, M, K, lda, BM, layout) || !encode_kmajor(enc, &mb, B, N, K, ldb, BN, layout))
+        return FDTD_ERR_CUDA;
+    const dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    unsigned short *yb = static_cast<unsigned short *>(Yb);
+    cudaError_t e;
+    if (layout == 1) {
+        const int nk = (K + Cfg<1>::BK - 1) / Cfg<1>::BK, ns = nk < 2 ? 2 : nk < Cfg<1>::NS ? nk : Cfg<1>::NS;
+        e = cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>(Cfg<1>::NS));
+        if (e == cudaSuccess)
+            k_gemm_tc<1><<<grid, NT, smem_bytes<1>(ns), s>>>(ma, mb, Y, ldy, yb, M, N, K, bias, relu, accumulate, ns);
+    } else {
+        const int nk = (K + Cfg<0>::BK - 1) / Cfg<0>::BK, ns = nk < 2 ? 2 : nk < Cfg<0>::NS ? nk : Cfg<0>::NS;
+        e = cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<0>(Cfg<0>::NS));
+        if (e == cudaSuccess)
+            k_gemm_tc<0><<<grid, NT, smem_bytes<0>(ns), s>>>(ma, mb, Y, ldy, yb, M, N, K, bias, relu, accumulate, ns);
+    }
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return FDTD_ERR_CUDA;
+    ++g_launches;
+    return FDTD_OK;
+}
+
+}  // namespace gtc
+}  // namespace fdtd
+
+extern "C" {
+
+int sur_gemm_set_path(int path) {
+    if (path < 0 || path > 3) return FDTD_ERR_ARG;
+    fdtd::gtc::g_path = path;
+    return FDTD_OK;
+}
+
+long long sur_gemm_tc_launches(void) { return fdtd::gtc::g_launches; }
+
+int sur_gemm_tc_failed(void) {
+    int f = 0;
+    const int zero = 0;
+    if (cudaMemcpyFromSymbol(&f, fdtd::gtc::g_fail, sizeof(int)) != cudaSuccess ||
+        cudaMemcpyToSymbol(fdtd::gtc::g_fail, &zero, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return FDTD_ERR_CUDA;
+    }
+    return f;
+}
+
+}  // extern "C"

@@ -1,10 +1,12 @@
 // surrogate.cu -- forward/backward kernels and the optimiser step of the
 // learned near-field surrogate (declarations and contracts: surrogate.h).
 //
-// The GEMM runs on the tensor cores with the warp-level mma.sync
-// m16n8k16 bf16 instruction: 64x64 block tiles, 32-deep k slices staged in
-// shared memory (either operand layout, transposed while staging), four warps
-// of 32x32, f32 accumulators, fused bias / ReLU / bf16-copy epilogue.  The
+// The GEMM with both operands K-major (and 16-byte rows) runs on the
+// fifth-generation tensor cores (tcgen05, TMEM, TMA: gemm_tc.cu).  The other
+// operand layouts run on the warp-level mma.sync m16n8k16 bf16 instruction:
+// 64x64 block tiles, 32-deep k slices staged in shared memory (either operand
+// layout, transposed while staging), four warps of 32x32, f32 accumulators,
+// fused bias / ReLU / bf16-copy epilogue.  The
 // convolutions, the elementwise steps and the reductions are plain SIMT
 // kernels: they are a few percent of the network's arithmetic.
 #include <cuda_bf16.h>
@@ -468,7 +470,52 @@ __global__ void k_lat_weights(const bf16raw *__restrict__ G, const int *__restri
     W[((long long)a * K + k) * T + t] = v;
 }
 
+// The same weights K-major: W[a][t][koff + k] (row stride ldw), for the
+// tcgen05 GEMM; one thread per (a, t, k), k fastest
+__global__ void k_lat_weights_kmajor(const bf16raw *__restrict__ G, const int *__restrict__ ant, int A, int K, int NR,
+                                     int D, int T, int S, int J, int moff, bf16raw *__restrict__ W, int ldw,
+                                     int koff) {
+    const long long n = (long long)A * T * K;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(i % K);
+        const long long at = i / K;
+        const int t = (int)(at % T), a = (int)(at / T);
+        const int ir = ant[2 * a], d = ant[2 * a + 1] - k + moff, tau = t - S * k + J;
+        bf16raw v = 0;
+        if (ir >= 0 && ir < NR && d >= 0 && d < D && tau >= 0 && tau < T) v = G[((long long)ir * D + d) * T + tau];
+        W[at * ldw + koff + k] = v;
+    }
+}
+
+// out[r] = [hi(x[r]), hi(x[r]), lo(x[r]), 0 ...] (row stride ld >= 3K): the A
+// operand of the split-precision product [hi, hi, lo] [W_hi; W_lo; W_hi]
+__global__ void k_split3_bf16(const float *__restrict__ x, int rows, int K, bf16raw *__restrict__ out, int ld) {
+    const long long n = (long long)rows * ld;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % ld);
+        const long long r = i / ld;
+        bf16raw v = 0;
+        if (c < 3 * K) {
+            const float xv = x[r * K + c % K];
+            const bf16raw h = tobf(xv);
+            v = c < 2 * K ? h : tobf(xv - bf(h));
+        }
+        out[i] = v;
+    }
+}
+
 }  // namespace
+
+namespace fdtd {
+namespace gtc {
+// gemm_tc.cu: the tcgen05 kernel's layout for this product (-1: none), the
+// path selected by sur_gemm_set_path, and its launch
+int tc_layout(const void *A, int lda, int a_kmajor, const void *B, int ldb, int b_kmajor, int K);
+int tc_path();
+int gemm_tc(int layout, const void *A, int lda, const void *B, int ldb, float *Y, int ldy, void *Yb, int M, int N,
+            int K, const float *bias, int relu, int accumulate, cudaStream_t s);
+}  // namespace gtc
+}  // namespace fdtd
 
 extern "C" {
 
@@ -476,8 +523,12 @@ int sur_gemm_bf16(const void *A, int lda, int a_kmajor, const void *B, int ldb, 
                   void *Yb, int M, int N, int K, const float *bias, int relu, int accumulate, void *stream) {
     if (!A || !B || !Y || M < 1 || N < 1 || K < 1 || lda < 1 || ldb < 1 || ldy < N) return FDTD_ERR_ARG;
     if ((a_kmajor ? lda < K : lda < M) || (b_kmajor ? ldb < K : ldb < N)) return FDTD_ERR_ARG;
-    const dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // both operands K-major with 16-byte rows: the tcgen05 kernel; else mma.sync
+    const int layout = fdtd::gtc::tc_layout(A, lda, a_kmajor, B, ldb, b_kmajor, K);
+    if (layout >= 0) return fdtd::gtc::gemm_tc(layout, A, lda, B, ldb, Y, ldy, Yb, M, N, K, bias, relu, accumulate, s);
+    if (fdtd::gtc::tc_path() >= 2) return FDTD_ERR_ARG;   // the tcgen05 kernel alone was asked for
+    const dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM);
     const bf16raw *a = static_cast<const bf16raw *>(A), *b = static_cast<const bf16raw *>(B);
     bf16raw *yb = static_cast<bf16raw *>(Yb);
     if (a_kmajor && b_kmajor)
@@ -646,6 +697,24 @@ int sur_lattice_bwd(const float *dy, const float *q, const int *ant, int B, int 
         return FDTD_ERR_ARG;
     k_lat_bwd<<<dim3((T + 255) / 256, B), 256, 0, static_cast<cudaStream_t>(stream)>>>(dy, q, ant, K, NR, D, T, S,
                                                                                          J, moff, dG);
+    return launched();
+}
+
+int sur_lattice_weights_kmajor(const void *G, const int *ant, int A, int K, int NR, int D, int T, int S, int J,
+                               int moff, void *W, int ldw, int koff, void *stream) {
+    if (!G || !ant || !W || A < 1 || K < 1 || NR < 1 || D < 1 || T < 1 || S < 0 || J < 0 || koff < 0 ||
+        ldw < koff + K)
+        return FDTD_ERR_ARG;
+    const long long n = (long long)A * T * K;
+    k_lat_weights_kmajor<<<grid_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<const bf16raw *>(G), ant, A, K, NR, D, T, S, J, moff, static_cast<bf16raw *>(W), ldw, koff);
+    return launched();
+}
+
+int sur_split3_bf16(const float *x, int rows, int K, void *out, int ld, void *stream) {
+    if (!x || !out || rows < 1 || K < 1 || ld < 3 * K) return FDTD_ERR_ARG;
+    k_split3_bf16<<<grid_for((long long)rows * ld, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        x, rows, K, static_cast<bf16raw *>(out), ld);
     return launched();
 }
 

@@ -35,8 +35,8 @@ import numpy as np
 
 from . import (check, fdtd_probes, profile_gaisser_hillas, lateral_nkg, Simulation, sur_adam, sur_antenna_features,
                sur_assemble, sur_assemble_bwd, sur_bias_grad, sur_cast_bf16, sur_gemm_bf16, sur_lattice_bwd,
-               sur_lattice_fwd, sur_lattice_fwd_f32, sur_lattice_weights, sur_mse, sur_normalize_rows, sur_pairs,
-               sur_relu_bwd, sur_scale_rows, sur_split_bf16)
+               sur_lattice_fwd, sur_lattice_fwd_f32, sur_lattice_weights, sur_lattice_weights_kmajor, sur_mse,
+               sur_normalize_rows, sur_pairs, sur_relu_bwd, sur_scale_rows, sur_split3_bf16, sur_split_bf16)
 
 N_FEAT = 64
 
@@ -419,32 +419,29 @@ class Lattice:
 
     def predict_grid(self, q, ants):
         """Every profile q [P, K] at every antenna ants [A, 2]: traces
-        [A, P, T], each antenna's batch one tensor-core GEMM (bf16 operands,
-        f32 accumulation) with its K x T weight matrix."""
+        [A, P, T], each antenna's batch one tensor-core GEMM (tcgen05: bf16
+        operands, f32 accumulation in tensor memory) of the split profiles
+        [hi, hi, lo] [P, 3K] with the antenna's K-major weights [W_hi; W_lo;
+        W_hi]^T [T, 3K], both padded to a row of KP = 3K rounded up to 8."""
         import torch
         g = self.geo
         P, A, K = q.shape[0], ants.shape[0], self.geo.K
+        KP = (3 * K + 7) // 8 * 8
         st = _stream()
         if not self._split:
             self.split()
         qn = torch.empty(P, K, dtype=torch.float32, device="cuda")
         s = torch.empty(P, dtype=torch.float32, device="cuda")
         check(sur_normalize_rows(_p(q), P, K, _p(qn), _p(s), st), "sur_normalize_rows")
-        qhi = torch.empty(P, K, dtype=torch.bfloat16, device="cuda")
-        qlo = torch.empty(P, K, dtype=torch.bfloat16, device="cuda")
-        check(sur_split_bf16(_p(qn), _p(qhi), _p(qlo), P * K, st), "sur_split_bf16")
-        Q3 = torch.cat([qhi, qhi, qlo], dim=1).contiguous()               # [P, 3K]
-        W3 = torch.empty(A, 3 * K, g.T, dtype=torch.bfloat16, device="cuda")
-        Wt = torch.empty(A, K, g.T, dtype=torch.bfloat16, device="cuda")
-        for part, tab in ((0, self.Ghi), (1, self.Glo)):
-            check(sur_lattice_weights(_p(tab), _p(ants), A, K, g.NR, self.D, g.T, g.S, g.J, self.moff, _p(Wt), st),
-                  "sur_lattice_weights")
-            W3[:, part * K:(part + 1) * K].copy_(Wt)
-            if part == 0:
-                W3[:, 2 * K:].copy_(Wt)
+        Q3 = torch.empty(P, KP, dtype=torch.bfloat16, device="cuda")
+        check(sur_split3_bf16(_p(qn), P, K, _p(Q3), KP, st), "sur_split3_bf16")
+        W3 = torch.zeros(A, g.T, KP, dtype=torch.bfloat16, device="cuda")
+        for koff, tab in ((0, self.Ghi), (K, self.Glo), (2 * K, self.Ghi)):
+            check(sur_lattice_weights_kmajor(_p(tab), _p(ants), A, K, g.NR, self.D, g.T, g.S, g.J, self.moff, _p(W3),
+                                             KP, koff, st), "sur_lattice_weights_kmajor")
         out = torch.empty(A, P, g.T, dtype=torch.float32, device="cuda")
         for a in range(A):
-            check(sur_gemm_bf16(_p(Q3), 3 * K, 1, _p(W3[a]), g.T, 0, _p(out[a]), g.T, None, P, g.T, 3 * K, None, 0,
+            check(sur_gemm_bf16(_p(Q3), KP, 1, _p(W3[a]), KP, 1, _p(out[a]), g.T, None, P, g.T, KP, None, 0,
                                 0, st), "sur_gemm_bf16")
             check(sur_scale_rows(_p(out[a]), P, g.T, _p(s), self.c_out, 0, st), "sur_scale_rows")
         return out

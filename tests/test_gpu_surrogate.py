@@ -281,6 +281,96 @@ def test_lattice_kernels_match_reference(env):
     fd.check(fd.sur_lattice_weights(_p(Gb), _p(ad), B, K, NR, D, T, Ss, J, moff, _p(W), None), "weights")
     assert np.array_equal(_host(W), R.lattice_weights(G, ant, K, Ss, J, moff))
     assert fd.sur_lattice_fwd(None, None, _p(qd), _p(ad), B, K, NR, D, T, Ss, J, moff, _p(y), None) == -1
+    # the K-major weights of the tcgen05 GEMM: W3[a][t][koff + k], other columns untouched
+    KP = (3 * K + 7) // 8 * 8
+    W3 = torch.full((B, T, KP), 7.0, dtype=torch.bfloat16, device="cuda")
+    fd.check(fd.sur_lattice_weights_kmajor(_p(Gb), _p(ad), B, K, NR, D, T, Ss, J, moff, _p(W3), KP, K, None), "wk")
+    w3 = _host(W3)
+    assert np.array_equal(w3[:, :, K:2 * K], R.lattice_weights(G, ant, K, Ss, J, moff).transpose(0, 2, 1))
+    assert np.all(w3[:, :, :K] == 7.0) and np.all(w3[:, :, 2 * K:] == 7.0)
+    assert fd.sur_lattice_weights_kmajor(_p(Gb), _p(ad), B, K, NR, D, T, Ss, J, moff, _p(W3), 2 * K - 1, K,
+                                         None) == -1
+    # the split profile rows [hi, hi, lo, 0 ...]
+    Q3 = torch.full((B, KP), 7.0, dtype=torch.bfloat16, device="cuda")
+    fd.check(fd.sur_split3_bf16(_p(qd), B, K, _p(Q3), KP, None), "split3")
+    q32 = q.astype(np.float32)
+    hi_q, q3 = R.bf16(q32), _host(Q3)
+    assert np.array_equal(q3[:, :K], hi_q) and np.array_equal(q3[:, K:2 * K], hi_q)
+    assert np.array_equal(q3[:, 2 * K:3 * K], R.bf16(q32 - hi_q.astype(np.float32)))
+    assert np.all(q3[:, 3 * K:] == 0)
+    assert fd.sur_split3_bf16(_p(qd), B, K, _p(Q3), 3 * K - 1, None) == -1
+
+
+@pytest.mark.parametrize("M,N,K", [(70, 50, 40), (129, 200, 2112), (300, 1024, 96), (1000, 384, 256),
+                                   (4, 1024, 1024), (257, 130, 30)])
+def test_gemm_tcgen05_layouts(env, M, N, K):
+    """Both operand layouts of the tcgen05 kernel (128-byte swizzled slices,
+    unswizzled core matrices) against the FP64 product of the same bf16
+    operands, with the fused epilogue; K not a multiple of 8 reads zeros past
+    K on the swizzled path; the mma.sync kernel agrees; the launch counter
+    shows which kernel ran; no pipeline wait gave up."""
+    torch, fd, S = env
+    rng = np.random.default_rng(M * 7 + N + K)
+    lda = (K + 7) // 8 * 8
+    a = R.bf16(rng.normal(size=(M, K)))
+    b = R.bf16(rng.normal(size=(N, K)))
+    bias = rng.normal(size=N)
+    ref = np.maximum(a @ b.T + bias, 0.0)
+    A = torch.zeros(M, lda, dtype=torch.bfloat16, device="cuda")
+    Bm = torch.zeros(N, lda, dtype=torch.bfloat16, device="cuda")
+    A[:, :K] = _dev(torch, a, torch.bfloat16)
+    Bm[:, :K] = _dev(torch, b, torch.bfloat16)
+    # garbage past K in the padding: only the first K columns may count
+    A[:, K:] = 3.0
+    Bm[:, K:] = -5.0
+    bd = _dev(torch, bias)
+    ldy = N + 5
+    outs = {}
+    try:
+        for path in (2, 3, 1):
+            if path == 3 and K % 8:
+                assert fd.sur_gemm_set_path(3) == 0
+                Y = torch.zeros(M, ldy, dtype=torch.float32, device="cuda")
+                assert fd.sur_gemm_bf16(_p(A), lda, 1, _p(Bm), lda, 1, _p(Y), ldy, None, M, N, K, _p(bd), 1, 0,
+                                        None) == -1
+                continue
+            assert fd.sur_gemm_set_path(path) == 0
+            n0 = fd.sur_gemm_tc_launches()
+            Y = torch.zeros(M, ldy, dtype=torch.float32, device="cuda")
+            Yb = torch.zeros(M, ldy, dtype=torch.bfloat16, device="cuda")
+            rc = fd.sur_gemm_bf16(_p(A), lda, 1, _p(Bm), lda, 1, _p(Y), ldy, _p(Yb), M, N, K, _p(bd), 1, 0, None)
+            assert rc == 0
+            torch.cuda.synchronize()
+            assert fd.sur_gemm_tc_launches() - n0 == (0 if path == 1 else 1)
+            y = _host(Y)
+            assert np.abs(y[:, :N] - ref).max() <= 2e-5 * np.abs(ref).max(), path
+            assert np.all(y[:, N:] == 0)
+            assert np.array_equal(_host(Yb)[:, :N], R.bf16(y[:, :N]))
+            outs[path] = y[:, :N]
+            if path == 2:   # accumulate into Y, no bias, no ReLU
+                fd.check(fd.sur_gemm_bf16(_p(A), lda, 1, _p(Bm), lda, 1, _p(Y), ldy, None, M, N, K, None, 0, 1,
+                                          None), "acc")
+                torch.cuda.synchronize()
+                assert np.abs(_host(Y)[:, :N] - (y[:, :N] + a @ b.T)).max() <= 4e-5 * np.abs(ref).max()
+        assert fd.sur_gemm_tc_failed() == 0
+        assert np.abs(outs[1] - outs[2]).max() <= 2e-5 * np.abs(ref).max()
+        # an MN-major operand is not the tcgen05 kernel's: rejected when it alone was asked for
+        assert fd.sur_gemm_set_path(2) == 0
+        Y = torch.zeros(M, ldy, dtype=torch.float32, device="cuda")
+        assert fd.sur_gemm_bf16(_p(A), lda, 1, _p(Bm), N, 0, _p(Y), ldy, None, M, N, min(K, N), None, 0, 0,
+                                None) == -1
+    finally:
+        assert fd.sur_gemm_set_path(0) == 0
+    # the automatic choice: K-major operands with 16-byte rows take the tcgen05 kernel, others mma.sync
+    n0 = fd.sur_gemm_tc_launches()
+    Y = torch.zeros(M, ldy, dtype=torch.float32, device="cuda")
+    fd.check(fd.sur_gemm_bf16(_p(A), lda, 1, _p(Bm), lda, 1, _p(Y), ldy, None, M, N, K, None, 0, 0, None), "auto")
+    assert fd.sur_gemm_tc_launches() == n0 + 1
+    if K % 8:
+        At = _dev(torch, a, torch.bfloat16)
+        fd.check(fd.sur_gemm_bf16(_p(At), K, 1, _p(Bm), lda, 1, _p(Y), ldy, None, M, N, K, None, 0, 0, None), "mma")
+        assert fd.sur_gemm_tc_launches() == n0 + 1
+    assert fd.sur_gemm_set_path(4) == -1
 
 
 def test_lattice_surrogate_learns_held_out_showers(env):
