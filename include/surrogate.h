@@ -63,6 +63,20 @@ long long sur_gemm_tc_launches(void);
 int sur_gemm_tc_failed(void);
 
 /*
+ * batch products on the tcgen05 kernel in one launch:
+ *   Y[b][m*ldy + n] = alpha * (row_scale ? row_scale[m] : 1) * sum_k A_b(m,k) B_b(n,k),
+ *   A_b(m,k) = A[b*sa + m*lda + k], B_b(n,k) = B[b*sb + n*ldb + k] (bf16, both
+ *   K-major; sa or sb = 0: one operand shared by the batch), Y_b at Y + b*sy
+ *   (f32; sy >= M*ldy when batch > 1), row_scale f32 [M] or NULL.
+ * lda, ldb, sa, sb multiples of 8 and A, B 16-byte aligned; 1 <= batch <=
+ * 65535.  FDTD_ERR_ARG otherwise, and while sur_gemm_set_path has selected
+ * mma.sync (1) or the unswizzled tcgen05 layout (3).
+ */
+int sur_gemm_bf16_batched(const void *A, int lda, long long sa, const void *B, int ldb, long long sb, float *Y, int ldy,
+                          long long sy, int M, int N, int K, int batch, const float *row_scale, float alpha,
+                          void *stream);
+
+/*
  * 1D convolution, f32 activations, bf16 weights, f32 accumulation:
  *   y[b][o][l] = bias[o] + sum_{c,t} w[o][c][t] x[b][c][l*stride + t - pad]
  *   (x read as 0 outside 0..lin-1), then max(., 0) if relu.

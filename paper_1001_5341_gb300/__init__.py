@@ -72,6 +72,8 @@ _SIGS = {
     "sur_gemm_set_path": (_i, [_i]),
     "sur_gemm_tc_launches": (C.c_longlong, []),
     "sur_gemm_tc_failed": (_i, []),
+    "sur_gemm_bf16_batched": (_i, [_vp, _i, C.c_longlong, _vp, _i, C.c_longlong, _vp, _i, C.c_longlong, _i, _i, _i,
+                                   _i, _vp, C.c_float, _vp]),
     "sur_conv1d_fwd": (_i, [_vp, _i, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _i, _vp]),
     "sur_conv1d_bwd": (_i, [_vp, _i, _vp, _vp, _vp, _i, _vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _i, _vp]),
     "sur_relu_bwd": (_i, [_vp, _vp, _vp, _vp, C.c_longlong, _vp]),

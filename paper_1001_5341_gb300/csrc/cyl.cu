@@ -588,7 +588,11 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_cyl_wave(Wave A) {
                 int s2 = S.st;
                 uint32_t ph = S.phase;
                 for (int m = 0; m < STAGES && failed_at + m <= w.load_end; ++m) {
-                    mbar_wait(&w.bar[s2], ph);
+                    // a copy still in flight after these waits may land after the
+                    // block ends: flag bit 8 (the handle's status is sticky)
+                    bool landed = false;
+                    for (int t = 0; t < 4 && !landed; ++t) landed = mbar_wait(&w.bar[s2], ph);
+                    if (!landed) atomicOr(A.flags, 8);
                     if (++s2 == STAGES) {
                         s2 = 0;
                         ph ^= 1u;

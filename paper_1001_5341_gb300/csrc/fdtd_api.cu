@@ -250,12 +250,13 @@ int fdtd_create(fdtd_t *out, int nx, int ny, int nz, double dx, double dt, doubl
     }
     if ((rc = note(h, cudaStreamSynchronize(h->stream))) != FDTD_OK) return fail(rc);
     // default field-update path: two steps per pass where it applies (PEC and
-    // CPML grids), else the one-step vector-tile z-march; the others stay
-    // available (fdtd_set_kernel) as cross-checks
+    // CPML grids of at least FDTD_TWO_STEP_MIN_CELLS cells), else the one-step
+    // vector-tile z-march; the others stay available (fdtd_set_kernel) as
+    // cross-checks
     h->watch_every = FDTD_WATCHDOG_DEFAULT_STEPS;
     h->kernel = 0;
     if (vtile_prepare(h) == FDTD_OK) h->kernel = 1;
-    if (tb2_prepare(h) == FDTD_OK) h->kernel = 2;
+    if ((long long)nx * ny * nz >= FDTD_TWO_STEP_MIN_CELLS && tb2_prepare(h) == FDTD_OK) h->kernel = 2;
     cudaGetLastError();
     *out = h;
     return FDTD_OK;

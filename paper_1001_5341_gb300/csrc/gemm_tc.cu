@@ -123,11 +123,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 __device__ int g_fail;   // a bounded wait gave up in some CTA
 
+// Epilogue and batch: Y[b] = alpha diag(row_scale) A[b] B[b]^T (+ Y if
+// accumulate, + bias, ReLU if relu), Y[b] at Y + b sy; Yb a bf16 copy
+struct Epi {
+    float *Y;
+    long long sy;
+    unsigned short *Yb;
+    const float *bias, *row_scale;
+    float alpha;
+    int ldy, relu, accumulate;
+    int a3, b3;   // A, B tensor maps carry a batch dimension (else shared by the batch)
+};
+
 template <int SW>
 __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const __grid_constant__ CUtensorMap ma,
-                                                   const __grid_constant__ CUtensorMap mb, float *Y, int ldy,
-                                                   unsigned short *Yb, int M, int N, int K,
-                                                   const float *__restrict__ bias, int relu, int accumulate, int NS) {
+                                                   const __grid_constant__ CUtensorMap mb, const Epi E, int M, int N,
+                                                   int K, int NS) {
     typedef Cfg<SW> C;
     constexpr int BK = C::BK, KSTEPS = BK / 16;
     extern __shared__ unsigned char smem_raw[];
@@ -141,7 +152,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const __grid_constant__ CUten
     __shared__ int s_ok;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN, bz = blockIdx.z;
     const int nk = (K + BK - 1) / BK;
 
     if (tid == 0) {
@@ -170,8 +181,10 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const __grid_constant__ CUten
             unsigned char *b = a + a_bytes<SW>();
             mbar_expect_tx(&full[s], (uint32_t)stage_bytes<SW>());
             if (SW) {
-                tma_load2(a, &ma, &full[s], c * BK, m0);
-                tma_load2(b, &mb, &full[s], c * BK, n0);
+                if (E.a3) tma_load3b(a, &ma, &full[s], c * BK, m0, bz);
+                else tma_load2(a, &ma, &full[s], c * BK, m0);
+                if (E.b3) tma_load3b(b, &mb, &full[s], c * BK, n0, bz);
+                else tma_load2(b, &mb, &full[s], c * BK, n0);
             } else {
                 tma_load3b(a, &ma, &full[s], 0, m0, c * (BK / 8));
                 tma_load3b(b, &mb, &full[s], 0, n0, c * (BK / 8));
@@ -237,18 +250,22 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const __grid_constant__ CUten
             for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(r[j]);
             __syncwarp();
             const int n = n0 + cc + lane;
-            const float bn = (bias && n < N) ? bias[n] : 0.f;
+            const float bn = (E.bias && n < N) ? E.bias[n] : 0.f;
+            float *Yz = E.Y + (long long)bz * E.sy;
+            unsigned short *Ybz = E.Yb ? E.Yb + (long long)bz * E.sy : nullptr;
 #pragma unroll 4
             for (int rr = 0; rr < 32; ++rr) {
                 const int row = m0 + warp * 32 + rr;
                 if (row < M && n < N) {
-                    const long long o = (long long)row * ldy + n;
+                    const long long o = (long long)row * E.ldy + n;
                     float v = tile[rr * 33 + lane];
-                    if (accumulate) v += Y[o];
+                    if (E.row_scale) v *= E.alpha * E.row_scale[row];
+                    else if (E.alpha != 1.f) v *= E.alpha;
+                    if (E.accumulate) v += Yz[o];
                     v += bn;
-                    if (relu) v = fmaxf(v, 0.f);
-                    Y[o] = v;
-                    if (Yb) Yb[o] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+                    if (E.relu) v = fmaxf(v, 0.f);
+                    Yz[o] = v;
+                    if (Ybz) Ybz[o] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
                 }
             }
             __syncwarp();
@@ -264,13 +281,16 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const __grid_constant__ CUten
     }
 }
 
-bool encode_kmajor(EncodeTiled enc, CUtensorMap *m, const void *p, int rows, int K, int ld, int box_rows, int sw) {
+// batch > 1 with stride > 0 (elements): a third dimension over the batch
+bool encode_kmajor(EncodeTiled enc, CUtensorMap *m, const void *p, int rows, int K, int ld, int box_rows, int sw,
+                   int batch = 1, long long stride = 0) {
     if (sw) {
-        cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-        cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-        cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
-        cuuint32_t es[2] = {1, 1};
-        return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(p), dims, strides, box, es,
+        const int nd = batch > 1 && stride > 0 ? 3 : 2;
+        cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)batch};
+        cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)stride * 2};
+        cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
+        cuuint32_t es[3] = {1, 1, 1};
+        return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, nd, const_cast<void *>(p), dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     }
@@ -302,30 +322,53 @@ int tc_layout(const void *A, int lda, int a_kmajor, const void *B, int ldb, int 
     return 1;
 }
 
-int gemm_tc(int layout, const void *A, int lda, const void *B, int ldb, float *Y, int ldy, void *Yb, int M, int N,
-            int K, const float *bias, int relu, int accumulate, cudaStream_t s) {
+namespace {
+// launch of k_gemm_tc over batch products (layout 1 only when batch > 1)
+int launch_tc(int layout, const void *A, int lda, long long sa, const void *B, int ldb, long long sb, int batch,
+              Epi E, int M, int N, int K, cudaStream_t s) {
+    static bool attr_set[2] = {false, false};
     EncodeTiled enc = encoder();
     if (!enc) return FDTD_ERR_CUDA;
     CUtensorMap ma, mb;
-    if (!encode_kmajor(enc, &ma, A, M, K, lda, BM, layout) || !encode_kmajor(enc, &mb, B, N, K, ldb, BN, layout))
+    E.a3 = batch > 1 && sa > 0;
+    E.b3 = batch > 1 && sb > 0;
+    if (!encode_kmajor(enc, &ma, A, M, K, lda, BM, layout, batch, sa) ||
+        !encode_kmajor(enc, &mb, B, N, K, ldb, BN, layout, batch, sb))
         return FDTD_ERR_CUDA;
-    const dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
-    unsigned short *yb = static_cast<unsigned short *>(Yb);
-    cudaError_t e;
+    const dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
+    cudaError_t e = cudaSuccess;
     if (layout == 1) {
         const int nk = (K + Cfg<1>::BK - 1) / Cfg<1>::BK, ns = nk < 2 ? 2 : nk < Cfg<1>::NS ? nk : Cfg<1>::NS;
-        e = cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>(Cfg<1>::NS));
-        if (e == cudaSuccess)
-            k_gemm_tc<1><<<grid, NT, smem_bytes<1>(ns), s>>>(ma, mb, Y, ldy, yb, M, N, K, bias, relu, accumulate, ns);
+        if (!attr_set[1])
+            e = cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>(Cfg<1>::NS));
+        attr_set[1] = e == cudaSuccess;
+        if (e == cudaSuccess) k_gemm_tc<1><<<grid, NT, smem_bytes<1>(ns), s>>>(ma, mb, E, M, N, K, ns);
     } else {
         const int nk = (K + Cfg<0>::BK - 1) / Cfg<0>::BK, ns = nk < 2 ? 2 : nk < Cfg<0>::NS ? nk : Cfg<0>::NS;
-        e = cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<0>(Cfg<0>::NS));
-        if (e == cudaSuccess)
-            k_gemm_tc<0><<<grid, NT, smem_bytes<0>(ns), s>>>(ma, mb, Y, ldy, yb, M, N, K, bias, relu, accumulate, ns);
+        if (!attr_set[0])
+            e = cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<0>(Cfg<0>::NS));
+        attr_set[0] = e == cudaSuccess;
+        if (e == cudaSuccess) k_gemm_tc<0><<<grid, NT, smem_bytes<0>(ns), s>>>(ma, mb, E, M, N, K, ns);
     }
     if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return FDTD_ERR_CUDA;
     ++g_launches;
     return FDTD_OK;
+}
+}  // namespace
+
+int gemm_tc(int layout, const void *A, int lda, const void *B, int ldb, float *Y, int ldy, void *Yb, int M, int N,
+            int K, const float *bias, int relu, int accumulate, cudaStream_t s) {
+    Epi E;
+    E.Y = Y;
+    E.sy = 0;
+    E.Yb = static_cast<unsigned short *>(Yb);
+    E.bias = bias;
+    E.row_scale = nullptr;
+    E.alpha = 1.f;
+    E.ldy = ldy;
+    E.relu = relu;
+    E.accumulate = accumulate;
+    return launch_tc(layout, A, lda, 0, B, ldb, 0, 1, E, M, N, K, s);
 }
 
 }  // namespace gtc
@@ -340,6 +383,28 @@ int sur_gemm_set_path(int path) {
 }
 
 long long sur_gemm_tc_launches(void) { return fdtd::gtc::g_launches; }
+
+int sur_gemm_bf16_batched(const void *A, int lda, long long sa, const void *B, int ldb, long long sb, float *Y, int ldy,
+                          long long sy, int M, int N, int K, int batch, const float *row_scale, float alpha,
+                          void *stream) {
+    using namespace fdtd::gtc;
+    if (!A || !B || !Y || M < 1 || N < 1 || K < 1 || batch < 1 || batch > 65535 || lda < K || ldb < K || ldy < N ||
+        sa < 0 || sb < 0 || lda % 8 || ldb % 8 || sa % 8 || sb % 8 ||
+        (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15) ||
+        (batch > 1 && sy < (long long)M * ldy) || g_path == 1 || g_path == 3)
+        return FDTD_ERR_ARG;
+    Epi E;
+    E.Y = Y;
+    E.sy = sy;
+    E.Yb = nullptr;
+    E.bias = nullptr;
+    E.row_scale = row_scale;
+    E.alpha = alpha;
+    E.ldy = ldy;
+    E.relu = 0;
+    E.accumulate = 0;
+    return launch_tc(1, A, lda, sa, B, ldb, sb, batch, E, M, N, K, static_cast<cudaStream_t>(stream));
+}
 
 int sur_gemm_tc_failed(void) {
     int f = 0;

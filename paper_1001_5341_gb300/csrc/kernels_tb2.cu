@@ -52,8 +52,11 @@
 //
 // Detectors.  The level-1 E of the six cells of a detector's readout (Ex at
 // i-1, i; Ey at j-1, j; Ez at k-1, k) go to a small buffer from the tile that
-// owns them (records sorted by plane per block); the readout of step n+1 reads
-// them, that of step n+2 reads the fields.
+// owns them; the readout of step n+1 reads them, that of step n+2 reads the
+// fields.  A block's records are sorted by plane; those of plane q are served
+// in the next iteration, one per thread, from the shared rows that hold the
+// level-1 E of plane q (Ex, Ez in the exchange rows, Ey in rows of its own),
+// so thousands of detectors in one tile cost a few loads per plane.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -89,6 +92,7 @@ struct Geo {
     static constexpr unsigned FIELD_BYTES = 4u * FIELDS;
     static constexpr int XROW = 2 * TXC;         // exchange floats per warp row (two components)
     static constexpr int XBUF = NWR * XROW;      // one exchange buffer
+    static constexpr int YBUF = NWR * TXC;       // level-1 Ey rows (detector readout)
     // CPML coefficient table (floats): aH, bH, aE, bE of the computed columns,
     // of the rows j0-2 .. j0+TY+1, of the planes kstart .. kstart+zt-1
     static constexpr int CX = 0;
@@ -96,8 +100,10 @@ struct Geo {
     static constexpr int CZ = CY + 4 * BR;
     static constexpr int LO = 4 / VW;            // first owned lane
     static constexpr int HI = 31 - 4 / VW;       // last owned lane
-    // shared memory: barriers, three exchange buffers, coefficient table, ring
-    __host__ __device__ static constexpr int head_floats(int zt) { return (3 * XBUF + CZ + 4 * zt + 31) / 32 * 32; }
+    // shared memory: barriers, three exchange buffers, the Ey rows, coefficient table, ring
+    __host__ __device__ static constexpr int head_floats(int zt) {
+        return (3 * XBUF + YBUF + CZ + 4 * zt + 31) / 32 * 32;
+    }
 };
 
 // ---- lane vectors: the same code for float4 and scalar lanes ----
@@ -117,7 +123,6 @@ __device__ __forceinline__ float first(float v) { return v; }
 __device__ __forceinline__ float last(float v) { return v; }
 __device__ __forceinline__ float right(float, float r) { return r; }
 __device__ __forceinline__ float left(float, float l) { return l; }
-__device__ __forceinline__ float elem(float v, int) { return v; }
 __device__ __forceinline__ unsigned umask(const unsigned *m, float) { return m[0]; }
 __device__ __forceinline__ void stn(float *p, float v, int) { *p = v; }
 __device__ __forceinline__ void add_source(float &v, const Source &s, const SourceStep &w, int c0, int j, int k) {
@@ -133,7 +138,6 @@ __device__ __forceinline__ float last(float4 v) { return v.w; }
 // the vector one column to the right (x+1) / left (x-1), edge element given
 __device__ __forceinline__ float4 right(float4 v, float r) { return make_float4(v.y, v.z, v.w, r); }
 __device__ __forceinline__ float4 left(float4 v, float l) { return make_float4(l, v.x, v.y, v.z); }
-__device__ __forceinline__ float elem(float4 v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
 // v with the elements outside the mask set to +0 (bitwise, so a non-finite
 // value outside the state never leaks in)
 __device__ __forceinline__ float mk(float v, unsigned b) { return __uint_as_float(__float_as_uint(v) & b); }
@@ -310,7 +314,31 @@ struct RingPos {
     uint32_t ph1;
 };
 
-template <int VW, bool HX, bool HY, bool HZ, bool MASK>
+// The records of plane q from position pc of a block's list (all threads);
+// returns the new position.  Only the instances of blocks with records (REC)
+// carry it.
+__device__ __forceinline__ int serve_records(const int4 *__restrict__ prec, int pend, int pc, int q, int jb, int ib,
+                                          int txc, int xrow, const float *XB, const float *YB, float *pbuf) {
+    const int tid = threadIdx.x;
+    for (;;) {
+        const int i = pc + tid;
+        const bool live = i < pend;
+        const int4 r = live ? prec[i] : make_int4(0, 0, 0, 0);
+        const bool mine = live && r.x == q;   // (q is -1 .. -3 in the first iterations of the bottom chunk)
+        const int cnt = __syncthreads_count(mine);
+        if (mine) {
+            const int ww = r.y - jb, col = r.z - ib, c = r.w & 3;
+            // (the host assigns a record to the block that owns its cell; a
+            // record outside the block's rows is skipped, never read out of range)
+            if (ww >= 0 && ww < NWR && col >= 0 && col < txc)
+                pbuf[r.w >> 2] = c == 1 ? YB[ww * txc + col] : XB[ww * xrow + (c == 2 ? txc : 0) + col];
+        }
+        pc += cnt;
+        if (cnt < NT) return pc;
+    }
+}
+
+template <int VW, bool HX, bool HY, bool HZ, bool MASK, bool REC>
 __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane<VW> &L, const Blk &B, uint64_t *bar,
                                       float *ring, float *X, const float *CT, int rel, RingPos &rp,
                                       State<typename Vec<VW>::T> &S, int &pc) {
@@ -328,7 +356,7 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane<V
     ok = ok && mbar_wait(&bar[rp.s1], rp.ph1);
     const float *s0 = ring + rp.s0 * B.stage;   // plane p
     const float *s1 = ring + rp.s1 * B.stage;   // plane p+1
-    float *XA = X, *XB = X + XBUF, *XC = X + 2 * XBUF;
+    float *XA = X, *XB = X + XBUF, *XC = X + 2 * XBUF, *YB = X + 3 * XBUF;
     const int bc0 = VW * L.lane;
     const int lzp = (HZ && p >= 0 && p < g.nz) ? slab_cell(p, g.nz, pm.P) : -1;
     const int lzq = (HZ && q >= 0 && q < g.nz) ? slab_cell(q, g.nz, pm.P) : -1;
@@ -391,8 +419,13 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane<V
         // a wait expired: record it, let the copies in flight land, stop
         if (tid == 0) {
             atomicOr(A.flags, 1);
-            for (int r = rel; r < B.nplanes && r < rel + B.ns; ++r)
-                if (!mbar_wait(&bar[r % B.ns], (r / B.ns) & 1)) atomicOr(A.flags, 8);
+            // a copy still in flight after these waits may land after the block
+            // ends: flag bit 8 (the handle's status is sticky)
+            for (int r = rel; r < B.nplanes && r < rel + B.ns; ++r) {
+                bool landed = false;
+                for (int t = 0; t < 4 && !landed; ++t) landed = mbar_wait(&bar[r % B.ns], (r / B.ns) & 1);
+                if (!landed) atomicOr(A.flags, 8);
+            }
         }
         __syncthreads();
         return false;
@@ -400,6 +433,11 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane<V
     // the barrier orders every thread's reads of stage p before its refill
     if (!STAGE_IN_B && tid == 0 && rel + B.ns < B.nplanes)
         issue_plane<VW>(A, M, B, ring + rp.s0 * B.stage, &bar[rp.s0], rel + B.ns);
+
+    // detector records of plane q: its level-1 E are in the exchange rows (Ex,
+    // Ez) and the Ey rows since the last D; the records of a plane, contiguous
+    // in the block's sorted list, are read and served one per thread
+    if (REC) pc = serve_records(A.prec, B.pend, pc, q, B.j0 - 2, B.i0 - 4, TXC, XROW, XB, YB, A.pbuf);
 
     // ---- B: level-1 E at plane p (rows j0-1 .. j0+TY) ----
     V ex1 = z4, ey1 = z4, ez1 = z4;
@@ -440,16 +478,6 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane<V
         ex1 = keep<MASK>(ex1, mp.ex);
         ey1 = keep<MASK>(ey1, mp.ey);
         ez1 = keep<MASK>(ez1, mp.ez);
-    }
-    // detector records of plane p (block-uniform walk of the block's list)
-    while (pc < B.pend) {
-        const int4 r = A.prec[pc];
-        if (r.x != p) break;
-        if (w >= 1 && r.y == L.j && r.z >= L.c0 && r.z < L.c0 + VW) {
-            const int c = r.w & 3;
-            A.pbuf[r.w >> 2] = elem(c == 0 ? ex1 : c == 1 ? ey1 : ez1, r.z - L.c0);
-        }
-        ++pc;
     }
 
     // ---- C: level-2 H at plane q = p-1 (rows j0-1 .. j0+TY-1) ----
@@ -513,6 +541,7 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane<V
     if (w >= 1) {
         stv(XB + w * XROW + bc0, ex1);
         stv(XB + w * XROW + TXC + bc0, ez1);
+        if (REC) stv(YB + w * TXC + bc0, ey1);
     }
     if (p >= B.k0 + 1 && w >= 2 && w <= TY + 1) {
         const V hzD = ldv<V>(XC + (w - 1) * XROW + TXC + bc0);
@@ -579,7 +608,7 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane<V
     return true;
 }
 
-template <int VW, bool HX, bool HY, bool HZ, bool MASK>
+template <int VW, bool HX, bool HY, bool HZ, bool MASK, bool REC>
 __device__ __forceinline__ void march(const Args &A, const Maps &M, const Lane<VW> &L, const Blk &B, uint64_t *bar,
                                       float *ring, float *X, const float *CT) {
     typedef typename Vec<VW>::T V;
@@ -590,7 +619,7 @@ __device__ __forceinline__ void march(const Args &A, const Maps &M, const Lane<V
     RingPos rp{0, 1, 0u};   // two stages at least
     int pc = B.pbeg;
     for (int rel = 0; rel + 1 < B.nplanes; ++rel)
-        if (!plane<VW, HX, HY, HZ, MASK>(A, M, L, B, bar, ring, X, CT, rel, rp, S, pc)) return;
+        if (!plane<VW, HX, HY, HZ, MASK, REC>(A, M, L, B, bar, ring, X, CT, rel, rp, S, pc)) return;
 }
 
 // the instance of a block's case: which psi boxes it carries, whether it
@@ -598,8 +627,14 @@ __device__ __forceinline__ void march(const Args &A, const Maps &M, const Lane<V
 template <int VW, bool HX, bool HY, bool HZ>
 __device__ __forceinline__ void march_edge(bool edge, const Args &A, const Maps &M, const Lane<VW> &L, const Blk &B,
                                            uint64_t *bar, float *ring, float *X, const float *CT) {
-    if (edge) march<VW, HX, HY, HZ, true>(A, M, L, B, bar, ring, X, CT);
-    else march<VW, HX, HY, HZ, false>(A, M, L, B, bar, ring, X, CT);
+    // blocks with detector records run an instance with the record service
+    if (B.pbeg < B.pend) {
+        if (edge) march<VW, HX, HY, HZ, true, true>(A, M, L, B, bar, ring, X, CT);
+        else march<VW, HX, HY, HZ, false, true>(A, M, L, B, bar, ring, X, CT);
+    } else {
+        if (edge) march<VW, HX, HY, HZ, true, false>(A, M, L, B, bar, ring, X, CT);
+        else march<VW, HX, HY, HZ, false, false>(A, M, L, B, bar, ring, X, CT);
+    }
 }
 template <int VW, bool HX, bool HY>
 __device__ __forceinline__ void march_z(bool hz, bool edge, const Args &A, const Maps &M, const Lane<VW> &L,
@@ -617,7 +652,7 @@ __device__ __forceinline__ void run_block(const Args &A, const Maps &M, const Ti
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
     float *X = reinterpret_cast<float *>(smem_raw + BAR_BYTES);   // exchange rows
-    float *CT = X + 3 * XBUF;                                      // CPML coefficients
+    float *CT = X + 3 * XBUF + G::YBUF;                            // CPML coefficients
     float *ring = X + G::head_floats(A.zt);                        // stage ring
 
     const Grid &g = A.g;

@@ -399,7 +399,14 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
         // a wait expired: record it, let the copies in flight land, stop
         if (tid == 0) {
             atomicOr(A.flags, 1);
-            for (int r = rel; r < B.nplanes && r < rel + B.ns; ++r) mbar_wait(&bar[r % B.ns], (r / B.ns) & 1);
+            // a copy that still has not landed after these waits may write the
+            // block's shared memory after it ends: flag bit 8 (the handle's
+            // status is sticky, it is not stepped again)
+            for (int r = rel; r < B.nplanes && r < rel + B.ns; ++r) {
+                bool landed = false;
+                for (int t = 0; t < 4 && !landed; ++t) landed = mbar_wait(&bar[r % B.ns], (r / B.ns) & 1);
+                if (!landed) atomicOr(A.flags, 8);
+            }
         }
         __syncthreads();
         return false;

@@ -35,7 +35,8 @@ import numpy as np
 
 from . import (check, fdtd_probes, profile_gaisser_hillas, lateral_nkg, Simulation, sur_adam, sur_antenna_features,
                sur_assemble, sur_assemble_bwd, sur_bias_grad, sur_cast_bf16, sur_gemm_bf16, sur_lattice_bwd,
-               sur_lattice_fwd, sur_lattice_fwd_f32, sur_lattice_weights, sur_lattice_weights_kmajor, sur_mse,
+               sur_gemm_bf16_batched, sur_lattice_fwd, sur_lattice_fwd_f32, sur_lattice_weights,
+               sur_lattice_weights_kmajor, sur_mse,
                sur_normalize_rows, sur_pairs, sur_relu_bwd, sur_scale_rows, sur_split3_bf16, sur_split_bf16)
 
 N_FEAT = 64
@@ -419,10 +420,11 @@ class Lattice:
 
     def predict_grid(self, q, ants):
         """Every profile q [P, K] at every antenna ants [A, 2]: traces
-        [A, P, T], each antenna's batch one tensor-core GEMM (tcgen05: bf16
-        operands, f32 accumulation in tensor memory) of the split profiles
-        [hi, hi, lo] [P, 3K] with the antenna's K-major weights [W_hi; W_lo;
-        W_hi]^T [T, 3K], both padded to a row of KP = 3K rounded up to 8."""
+        [A, P, T]: one batched tensor-core GEMM (tcgen05: bf16 operands, f32
+        accumulation in tensor memory) of the split profiles [hi, hi, lo]
+        [P, 3K] with each antenna's K-major weights [W_hi; W_lo; W_hi]^T
+        [T, 3K], both padded to a row of KP = 3K rounded up to 8, the profile
+        scale applied in its epilogue."""
         import torch
         g = self.geo
         P, A, K = q.shape[0], ants.shape[0], self.geo.K
@@ -440,10 +442,9 @@ class Lattice:
             check(sur_lattice_weights_kmajor(_p(tab), _p(ants), A, K, g.NR, self.D, g.T, g.S, g.J, self.moff, _p(W3),
                                              KP, koff, st), "sur_lattice_weights_kmajor")
         out = torch.empty(A, P, g.T, dtype=torch.float32, device="cuda")
-        for a in range(A):
-            check(sur_gemm_bf16(_p(Q3), KP, 1, _p(W3[a]), KP, 1, _p(out[a]), g.T, None, P, g.T, KP, None, 0,
-                                0, st), "sur_gemm_bf16")
-            check(sur_scale_rows(_p(out[a]), P, g.T, _p(s), self.c_out, 0, st), "sur_scale_rows")
+        # one launch for all antennas, the profile scale fused into the epilogue
+        check(sur_gemm_bf16_batched(_p(Q3), KP, 0, _p(W3), KP, g.T * KP, _p(out), g.T, P * g.T, P, g.T, KP, A, _p(s),
+                                    self.c_out, st), "sur_gemm_bf16_batched")
         return out
 
 

@@ -113,6 +113,18 @@ def run_lattice(args, log):
     e1.record()
     torch.cuda.synchronize()
     pps_gather = reps * P * NA / (e0.elapsed_time(e1) * 1e-3)
+    # a larger serving batch: 1024 profiles x 256 antennas in one call
+    P2, NA2 = 1024, 256
+    qb2 = test.q[torch.arange(P2, device="cuda") % R].contiguous()
+    ab2 = test.ant[torch.linspace(0, A - 1, NA2, device="cuda").long()].contiguous()
+    nets[0].predict_grid(qb2, ab2)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        nets[0].predict_grid(qb2, ab2)
+    e1.record()
+    torch.cuda.synchronize()
+    pps_grid_large = reps * P2 * NA2 / (e0.elapsed_time(e1) * 1e-3)
     # the two paths give the same traces (bf16 profile rounding in the GEMM)
     yg = nets[0].predict_grid(qb, ab).permute(1, 0, 2).reshape(P * NA, -1).double().cpu().numpy()
     yf = nets[0].predict(qg, ag).double().cpu().numpy()
@@ -162,6 +174,7 @@ def run_lattice(args, log):
         "fdtd_pulses_per_s_all_antennas": round(fdtd_all, 1),
         "surrogate_pulses_per_s_batch4096_gemm": round(pps_gemm, 1),
         "surrogate_pulses_per_s_batch4096_gather": round(pps_gather, 1),
+        "surrogate_pulses_per_s_grid_1024x256_gemm": round(pps_grid_large, 1),
         "surrogate_vs_fdtd_64_antennas": round(pps_gemm / fdtd64, 1),
         "surrogate_vs_fdtd_all_antennas": round(pps_gemm / fdtd_all, 1),
         "gemm_vs_gather_rel_l2_median": gemm_vs_gather,

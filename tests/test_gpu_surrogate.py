@@ -373,6 +373,53 @@ def test_gemm_tcgen05_layouts(env, M, N, K):
     assert fd.sur_gemm_set_path(4) == -1
 
 
+@pytest.mark.parametrize("shared_a", [True, False])
+def test_gemm_tcgen05_batched(env, shared_a):
+    """Batched products in one launch (an operand shared by the batch or
+    strided), the row scale and alpha fused into the epilogue, against the
+    FP64 products of the same bf16 operands; argument checks."""
+    torch, fd, S = env
+    M, N, K, nb = 200, 300, 93, 5
+    lda = 96
+    rng = np.random.default_rng(11 + shared_a)
+    a = R.bf16(rng.normal(size=(1 if shared_a else nb, M, K)))
+    b = R.bf16(rng.normal(size=(nb, N, K)))
+    rs = rng.uniform(0.5, 2.0, size=M)
+    alpha = 0.37
+    A = torch.zeros(a.shape[0], M, lda, dtype=torch.bfloat16, device="cuda")
+    Bm = torch.zeros(nb, N, lda, dtype=torch.bfloat16, device="cuda")
+    A[:, :, :K] = _dev(torch, a, torch.bfloat16)
+    Bm[:, :, :K] = _dev(torch, b, torch.bfloat16)
+    ldy = N + 4
+    Y = torch.full((nb, M, ldy), 9.0, dtype=torch.float32, device="cuda")
+    rsd = _dev(torch, rs)
+    n0 = fd.sur_gemm_tc_launches()
+    rc = fd.sur_gemm_bf16_batched(_p(A), lda, 0 if shared_a else M * lda, _p(Bm), lda, N * lda, _p(Y), ldy, M * ldy,
+                                  M, N, K, nb, _p(rsd), C.c_float(alpha), None)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert fd.sur_gemm_tc_launches() == n0 + 1
+    y = _host(Y)
+    for z in range(nb):
+        az = a[0 if shared_a else z]
+        ref = alpha * np.float32(rs)[:, None].astype(np.float64) * (az @ b[z].T)
+        assert np.abs(y[z, :, :N] - ref).max() <= 2e-5 * np.abs(ref).max(), z
+        assert np.all(y[z, :, N:] == 9.0)
+    assert fd.sur_gemm_tc_failed() == 0
+    args = [_p(A), lda, 0, _p(Bm), lda, N * lda, _p(Y), ldy, M * ldy, M, N, K, nb, None, C.c_float(1.0), None]
+    bad = list(args); bad[1] = 93                  # lda not a multiple of 8
+    assert fd.sur_gemm_bf16_batched(*bad) == -1
+    bad = list(args); bad[8] = M * ldy - 1         # output batches overlap
+    assert fd.sur_gemm_bf16_batched(*bad) == -1
+    bad = list(args); bad[12] = 0                  # empty batch
+    assert fd.sur_gemm_bf16_batched(*bad) == -1
+    try:
+        assert fd.sur_gemm_set_path(1) == 0        # mma.sync only: no batched form
+        assert fd.sur_gemm_bf16_batched(*args) == -1
+    finally:
+        assert fd.sur_gemm_set_path(0) == 0
+
+
 def test_lattice_surrogate_learns_held_out_showers(env):
     """A small version of the lattice surrogate (64x64x256 grid, c dt = dx/2,
     bins of 8 steps, antennas at r = 0.20-0.36 m): trained by the library's
