@@ -3,6 +3,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <new>
 
 #include "fdtd_internal.h"
@@ -99,8 +100,13 @@ int vtile_prepare(fdtd_ctx *h) {
     const int mid = P > 0 ? g.nz - 2 * P - 1 : g.nz;
     const long long sms = h->num_sms > 0 ? h->num_sms : 1;
     const long long tiles = (long long)st->tiles_x * st->tiles_y;
-    long long m = 1, best = -1;
-    for (long long mm = 1; mm <= (mid / 16 > 1 ? mid / 16 : 1); ++mm) {
+    // chunks of at most CM_MAX planes: the blocks of a wave share halo rows
+    // through L2 only while they stay within a few planes of each other
+    constexpr long long CM_MAX = 160;
+    const long long m_lo = std::max(1LL, (mid + CM_MAX - 1) / CM_MAX);
+    const long long m_hi = std::max(m_lo, (long long)(mid / 16));
+    long long m = m_lo, best = -1;
+    for (long long mm = m_lo; mm <= m_hi; ++mm) {
         const long long cm = (mid + mm - 1) / mm;
         const long long cost = (tiles * mm + sms - 1) / sms * (cm + 4);
         if (best < 0 || cost < best) { best = cost; m = mm; }
