@@ -1,36 +1,35 @@
 // gemm_tc.cu -- the surrogate's bf16 GEMM on the fifth-generation tensor
-// cores (surrogate.h, sur_gemm_bf16 with both operands K-major).
+// cores (surrogate.h: sur_gemm_bf16 with both operands K-major, and
+// sur_gemm_bf16_batched).
 //
-// One CTA of four warps computes a 128 x 128 tile of Y = A B^T:
-//   * thread 0 stages K slices of A (128 rows) and B (128 rows) into shared
-//     memory with TMA (cp.async.bulk.tensor), a ring of stages tracked by
-//     mbarriers, and issues tcgen05.mma (kind::f16, M = 128, N = 128, K = 16
-//     per instruction, bf16 operands read from shared memory through matrix
-//     descriptors, f32 accumulator in tensor memory); tcgen05.commit frees a
-//     stage for the next slice once the MMAs that read it have completed;
-//   * warp 0 allocates the 128 accumulator columns of tensor memory and frees
-//     them at the end;
-//   * after the last MMA, each warp reads its 32 accumulator rows (tensor
-//     memory lanes 32w .. 32w+31) with tcgen05.ld, 32 columns at a time, turns
-//     them through a 32 x 32 tile in the idle stage memory and runs the
-//     epilogue (accumulate, bias, ReLU, f32 store and bf16 copy) with each row
-//     stored by the 32 lanes together (128-byte coalesced writes).
-// Two shared-memory layouts of the operand slices:
-//   SW = 1: 64-element (128-byte) K slices written by TMA with the 128-byte
-//     swizzle; rows 128 bytes apart, 8-row groups 1024 bytes apart; the
-//     descriptor of the k-th 16-element step starts 32 k bytes in;
-//   SW = 0: 32-element K slices as 8 x 16-byte core matrices (a 3-D tensor
-//     map over (8 elements, rows, K / 8)), 8-row groups 128 bytes apart,
-//     K-adjacent core matrices 128 x 16 bytes apart.
+// Output tiles of 128 x 128, f32 accumulators in tensor memory, operands
+// staged by TMA (cp.async.bulk.tensor) into rings of mbarrier stages, MMAs by
+// tcgen05.mma (kind::f16, M = 128, N = 128, K = 16 per instruction, bf16
+// operands read from shared memory through matrix descriptors), stages freed
+// by tcgen05.commit; the accumulator read back with tcgen05.ld (32 lanes x 32
+// columns per warp) and stored through a 32 x 33 transpose tile in shared
+// memory, so that each row is written by 32 lanes together, with the fused
+// epilogue (row scale, accumulate, bias, ReLU, f32 store and bf16 copy).
+// Two kernels:
+//   k_gemm_tcp (128-byte swizzled 64-element K slices, the default):
+//     persistent, two CTAs per SM, warp-specialised -- one thread loads, one
+//     issues MMAs into two accumulators in turn, four warps run the epilogue
+//     of the previous tile meanwhile (below);
+//   k_gemm_tc<0> (unswizzled core-matrix slices, 8 x 16 bytes from a 3-D
+//     tensor map over (8 elements, rows, K / 8)): one CTA per tile, thread 0
+//     loads and issues, the four warps run the epilogue at the end.
 // Out-of-range rows and K columns read as zeros (TMA bounds), so any M, N, K
 // work; the row strides must be multiples of 8 elements (16 bytes).
 // Every mbarrier wait is bounded; on expiry the CTA records a failure
-// (sur_gemm_tc_failed), skips its stores, waits for the MMAs it issued and
+// (sur_gemm_tc_failed), stops, lets its MMAs and loads in flight complete and
 // frees its tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <algorithm>
+#include <cstring>
 
 #include "../../include/fdtd.h"
 #include "../../include/surrogate.h"
@@ -47,7 +46,7 @@ constexpr uint32_t TMEM_COLS = BN;   // f32 accumulator: one column per N
 
 template <int SW> struct Cfg;
 template <> struct Cfg<1> {
-    static constexpr int BK = 64, NS = 3;
+    static constexpr int BK = 64;
 };
 template <> struct Cfg<0> {
     static constexpr int BK = 32, NS = 4;
@@ -133,6 +132,7 @@ struct Epi {
     float alpha;
     int ldy, relu, accumulate;
     int a3, b3;   // A, B tensor maps carry a batch dimension (else shared by the batch)
+    int ystore;   // the persistent kernel stores Y by TMA (no accumulate, no bf16 copy)
 };
 
 template <int SW>
@@ -281,6 +281,241 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const __grid_constant__ CUten
     }
 }
 
+// ---- the persistent form (128-byte swizzled slices) ----
+//
+// One CTA per half SM walks the output tiles t = blockIdx.x, + gridDim.x, ...
+// (n fastest, then m, then the batch) with its warps in three roles:
+//   warp 4 (one thread): TMA producer of the K slices, a ring of stages;
+//   warp 5 (one thread): MMA issuer, into one of two 128-column accumulators
+//     in tensor memory (tile parity), committing each stage back to the
+//     producer and each finished accumulator to the epilogue;
+//   warps 0-3: epilogue of the previous tile (tensor-memory lanes 32w ..
+//     32w+31) through a 32 x 33 transpose tile each, then they hand the
+//     accumulator back to the MMA issuer.
+// So one tile's loads and MMAs run under the previous tile's epilogue.
+constexpr int PNT = 192;
+constexpr int PNS = 2;                    // stages of 64-element slices (two CTAs per SM)
+constexpr uint32_t PTMEM_COLS = 2 * BN;   // two accumulators
+constexpr int PTILE_FLOATS = 4 * 2 * 32 * 32;   // per epilogue warp: two 32 x 32 f32 staging tiles
+static_assert(PTILE_FLOATS >= 4 * 32 * 33, "the transpose tiles fit too");
+__host__ __device__ constexpr int psmem_bytes() { return 1024 + PNS * stage_bytes<1>() + PTILE_FLOATS * 4 + 256; }
+
+__device__ __forceinline__ void tma_store3(const CUtensorMap *map, const void *src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(sa(src)), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(PNT, 1) k_gemm_tcp(const __grid_constant__ CUtensorMap ma,
+                                                     const __grid_constant__ CUtensorMap mb,
+                                                     const __grid_constant__ CUtensorMap my, const Epi E, int M,
+                                                     int N, int K, int total_tiles) {
+    constexpr int BK = Cfg<1>::BK, KSTEPS = BK / 16;
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t base = sa(smem_raw);
+    unsigned char *sm = smem_raw + ((1024u - (base & 1023u)) & 1023u);
+    float *tiles = reinterpret_cast<float *>(sm + PNS * stage_bytes<1>());
+    uint64_t *full = reinterpret_cast<uint64_t *>(tiles + PTILE_FLOATS);
+    uint64_t *empty = full + PNS;
+    uint64_t *acc_full = empty + PNS;     // [2]
+    uint64_t *acc_empty = acc_full + 2;   // [2]
+    uint64_t *drain = acc_empty + 2;
+    uint32_t *tholder = reinterpret_cast<uint32_t *>(drain + 1);
+    __shared__ int s_fail, s_issued, s_consumed;
+    volatile int *fail = &s_fail;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tn = (N + BN - 1) / BN, tpb = tn * ((M + BM - 1) / BM);
+    const int nk = (K + BK - 1) / BK;
+
+    if (tid == 0) {
+        for (int s = 0; s < PNS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);   // one arrival per epilogue warp
+        }
+        mbar_init(drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+        s_issued = s_consumed = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(tholder)),
+                     "r"(PTMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tholder;
+
+    if (warp == 4) {
+        if (lane == 0) {   // producer
+            int it = 0;
+            for (int t = blockIdx.x; t < total_tiles && !*fail; t += gridDim.x) {
+                const int b = t / tpb, r = t % tpb, m0 = (r / tn) * BM, n0 = (r % tn) * BN;
+                for (int c = 0; c < nk; ++c, ++it) {
+                    const int s = it % PNS, u = it / PNS;
+                    if (u >= 1 && !mbar_wait(&empty[s], (uint32_t)(u - 1) & 1u)) {
+                        *fail = 1;
+                        break;
+                    }
+                    unsigned char *a = sm + s * stage_bytes<1>();
+                    mbar_expect_tx(&full[s], (uint32_t)stage_bytes<1>());
+                    if (E.a3) tma_load3b(a, &ma, &full[s], c * BK, m0, b);
+                    else tma_load2(a, &ma, &full[s], c * BK, m0);
+                    if (E.b3) tma_load3b(a + a_bytes<1>(), &mb, &full[s], c * BK, n0, b);
+                    else tma_load2(a + a_bytes<1>(), &mb, &full[s], c * BK, n0);
+                }
+            }
+            s_issued = it;
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {   // MMA issuer
+            int it = 0, lt = 0;
+            for (int t = blockIdx.x; t < total_tiles && !*fail; t += gridDim.x, ++lt) {
+                const int buf = lt & 1;
+                if (lt >= 2 && !mbar_wait(&acc_empty[buf], (uint32_t)((lt >> 1) - 1) & 1u)) {
+                    *fail = 1;
+                    break;
+                }
+                fence_after();
+                const uint32_t d = tmem + (uint32_t)(buf * BN);
+                bool ok = true;
+                for (int c = 0; c < nk; ++c, ++it) {
+                    const int s = it % PNS;
+                    if (!mbar_wait(&full[s], (uint32_t)(it / PNS) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t a0 = sa(sm + s * stage_bytes<1>()), b0 = a0 + a_bytes<1>();
+#pragma unroll
+                    for (int k = 0; k < KSTEPS; ++k)
+                        mma_f16(d, mdesc(a0 + 32u * k, 16u, 1024u, 2u), mdesc(b0 + 32u * k, 16u, 1024u, 2u), IDESC,
+                                (c | k) != 0);
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(&acc_full[buf]);
+                if (!ok) {
+                    *fail = 1;
+                    break;
+                }
+            }
+            s_consumed = it;
+            // completes once every MMA issued here has
+            mma_commit(drain);
+        }
+    } else {   // epilogue warps 0-3
+        float *tile = tiles + warp * (32 * 33);
+        float *stage_y = tiles + warp * (2 * 32 * 32);   // two 4 KB staging tiles, 1024-byte aligned
+        int lt = 0, ny = 0;
+        for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++lt) {
+            const int buf = lt & 1;
+            const bool ok = mbar_wait(&acc_full[buf], (uint32_t)(lt >> 1) & 1u);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) *fail = 1;
+                break;
+            }
+            if (*fail) break;
+            fence_after();
+            const int b = t / tpb, r = t % tpb, m0 = (r / tn) * BM, n0 = (r % tn) * BN;
+            const uint32_t trow = tmem + (uint32_t)(buf * BN) + ((uint32_t)(warp * 32) << 16);
+            if (E.ystore) {
+                // row m0 + 32 w + lane in registers; scaled, biased, ReLU'd there,
+                // written to a 128-byte-swizzled staging tile and stored by TMA
+                const int row = m0 + warp * 32 + lane;
+                const float rs = E.row_scale ? (row < M ? E.alpha * E.row_scale[row] : 0.f) : E.alpha;
+#pragma unroll 1
+                for (int cc = 0; cc < BN; cc += 32, ++ny) {
+                    uint32_t rr32[32];
+                    tmem_ld32(trow + (uint32_t)cc, rr32);
+                    float *st = stage_y + (ny & 1) * (32 * 32);
+                    // the staging tile written two chunks ago has been read by its store
+                    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                    __syncwarp();
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        float4 v;
+                        float *pv = reinterpret_cast<float *>(&v);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int n = n0 + cc + 4 * q + e;
+                            float x = __uint_as_float(rr32[4 * q + e]) * rs;
+                            if (E.bias) x += n < N ? E.bias[n] : 0.f;
+                            if (E.relu) x = fmaxf(x, 0.f);
+                            pv[e] = x;
+                        }
+                        sts4(st + lane * 32 + ((q ^ (lane & 7)) * 4), v);
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (m0 + warp * 32 < M && n0 + cc < N) tma_store3(&my, st, n0 + cc, m0 + warp * 32, b);
+                        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                    }
+                }
+            } else {
+                float *Yz = E.Y + (long long)b * E.sy;
+                unsigned short *Ybz = E.Yb ? E.Yb + (long long)b * E.sy : nullptr;
+#pragma unroll 1
+                for (int cc = 0; cc < BN; cc += 32) {
+                    uint32_t rr32[32];
+                    tmem_ld32(trow + (uint32_t)cc, rr32);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(rr32[j]);
+                    __syncwarp();
+                    const int n = n0 + cc + lane;
+                    const float bn = (E.bias && n < N) ? E.bias[n] : 0.f;
+#pragma unroll 4
+                    for (int rr = 0; rr < 32; ++rr) {
+                        const int row = m0 + warp * 32 + rr;
+                        if (row < M && n < N) {
+                            const long long o = (long long)row * E.ldy + n;
+                            float v = tile[rr * 33 + lane];
+                            if (E.row_scale) v *= E.alpha * E.row_scale[row];
+                            else if (E.alpha != 1.f) v *= E.alpha;
+                            if (E.accumulate) v += Yz[o];
+                            v += bn;
+                            if (E.relu) v = fmaxf(v, 0.f);
+                            Yz[o] = v;
+                            if (Ybz) Ybz[o] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+            // the accumulator is read: hand it back to the MMA issuer
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        }
+        // the output stores complete before the CTA ends
+        if (E.ystore && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        __syncwarp();
+    }
+    __syncthreads();
+    if (warp == 5 && lane == 0) {
+        // every MMA this CTA issued has completed before its tensor memory is
+        // freed; after a failure, the loads still in flight land first
+        if (!mbar_wait(drain, 0)) *fail = 1;
+        for (int u = s_consumed; u < s_issued; ++u) mbar_wait(&full[u % PNS], (uint32_t)(u / PNS) & 1u);
+    }
+    __syncthreads();
+    if (tid == 0 && *fail) atomicOr(&g_fail, 1);
+    fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(PTMEM_COLS) : "memory");
+    }
+}
+
 // batch > 1 with stride > 0 (elements): a third dimension over the batch
 bool encode_kmajor(EncodeTiled enc, CUtensorMap *m, const void *p, int rows, int K, int ld, int box_rows, int sw,
                    int batch = 1, long long stride = 0) {
@@ -329,21 +564,47 @@ int launch_tc(int layout, const void *A, int lda, long long sa, const void *B, i
     static bool attr_set[2] = {false, false};
     EncodeTiled enc = encoder();
     if (!enc) return FDTD_ERR_CUDA;
-    CUtensorMap ma, mb;
+    CUtensorMap ma, mb, my;
     E.a3 = batch > 1 && sa > 0;
     E.b3 = batch > 1 && sb > 0;
+    // Y by TMA (persistent kernel): no accumulate, no bf16 copy, 16-byte rows and batch stride
+    E.ystore = layout == 1 && !E.accumulate && !E.Yb && E.ldy % 4 == 0 && E.sy % 4 == 0 &&
+               (reinterpret_cast<uintptr_t>(E.Y) & 15) == 0;
+    if (E.ystore) {
+        cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)M, (cuuint64_t)batch};
+        cuuint64_t strides[2] = {(cuuint64_t)E.ldy * 4, (cuuint64_t)(batch > 1 ? E.sy : (long long)M * E.ldy) * 4};
+        cuuint32_t box[3] = {32, 32, 1};
+        cuuint32_t es[3] = {1, 1, 1};
+        E.ystore = enc(&my, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, E.Y, dims, strides, box, es,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    if (!E.ystore) std::memset(&my, 0, sizeof(my));   // unused
     if (!encode_kmajor(enc, &ma, A, M, K, lda, BM, layout, batch, sa) ||
         !encode_kmajor(enc, &mb, B, N, K, ldb, BN, layout, batch, sb))
         return FDTD_ERR_CUDA;
-    const dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
     cudaError_t e = cudaSuccess;
     if (layout == 1) {
-        const int nk = (K + Cfg<1>::BK - 1) / Cfg<1>::BK, ns = nk < 2 ? 2 : nk < Cfg<1>::NS ? nk : Cfg<1>::NS;
+        // persistent: two CTAs per SM over all output tiles of the batch
+        static int sms = 0;
+        if (sms == 0) {
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                sms = 0;
+            if (sms <= 0) {
+                cudaGetLastError();
+                return FDTD_ERR_CUDA;
+            }
+        }
+        const long long tiles = (long long)((N + BN - 1) / BN) * ((M + BM - 1) / BM) * batch;
+        if (tiles > (1LL << 31) - 1) return FDTD_ERR_ARG;
+        const int grid = (int)std::min<long long>(tiles, 2LL * sms);
         if (!attr_set[1])
-            e = cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>(Cfg<1>::NS));
+            e = cudaFuncSetAttribute(k_gemm_tcp, cudaFuncAttributeMaxDynamicSharedMemorySize, psmem_bytes());
         attr_set[1] = e == cudaSuccess;
-        if (e == cudaSuccess) k_gemm_tc<1><<<grid, NT, smem_bytes<1>(ns), s>>>(ma, mb, E, M, N, K, ns);
+        if (e == cudaSuccess) k_gemm_tcp<<<grid, PNT, psmem_bytes(), s>>>(ma, mb, my, E, M, N, K, (int)tiles);
     } else {
+        const dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
         const int nk = (K + Cfg<0>::BK - 1) / Cfg<0>::BK, ns = nk < 2 ? 2 : nk < Cfg<0>::NS ? nk : Cfg<0>::NS;
         if (!attr_set[0])
             e = cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<0>(Cfg<0>::NS));

@@ -37,6 +37,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
         if (clock64() - t0 > (4LL << 30)) return false;
     return true;
 }
+// one arrival on a barrier (no transaction bytes)
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(bar)) : "memory");
+}
 // make a barrier's memory free for a new mbar_init (no arrival or
 // transaction may be pending on it)
 __device__ __forceinline__ void mbar_inval(uint64_t *bar) {
