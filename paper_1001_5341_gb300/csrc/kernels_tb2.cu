@@ -157,6 +157,13 @@ template <> __device__ __forceinline__ unsigned uzero<unsigned>() { return 0u; }
 __device__ __forceinline__ uint4 umask(const unsigned *m, float4) { return make_uint4(m[0], m[1], m[2], m[3]); }
 // store the first n (1..VW) elements; one vector store when n == VW
 __device__ __forceinline__ void stn(float *p, float4 v, int n) { st4n(p, v, n); }
+// a store of an owned lane: in the instances without masks (a block clear
+// of the grid's faces) every owned lane holds VW columns on the grid (tile
+// ends are multiples of four), so the vector store needs no count
+template <bool MASK, typename V> __device__ __forceinline__ void stw(float *p, V v, int n) {
+    if (MASK) stn(p, v, n);
+    else stv(p, v);
+}
 // the shower's current on the lane's Ez edges
 __device__ __forceinline__ void add_source(float4 &v, const Source &s, const SourceStep &w, int c0, int j, int k) {
     v.x += source_at(s, w, c0, j, k);
@@ -513,23 +520,23 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane<V
         stv(XC + w * XROW + TXC + bc0, hz2);
         if (L.own && q >= B.k0 && q < B.k1) {
             const unsigned o = (unsigned)L.c0 + (unsigned)L.j * (unsigned)g.pitch + (unsigned)q * (unsigned)g.plane;
-            stn(A.out[3] + o, hx2, L.nval);
-            stn(A.out[4] + o, hy2, L.nval);
-            stn(A.out[5] + o, hz2, L.nval);
+            stw<MASK>(A.out[3] + o, hx2, L.nval);
+            stw<MASK>(A.out[4] + o, hy2, L.nval);
+            stw<MASK>(A.out[5] + o, hz2, L.nval);
             if (yl) {
                 const unsigned oy = L.yoff + (unsigned)q * (unsigned)(pm.W * g.pitch);
-                stn(pm.hout[1][0] + oy, S.yH0, L.nval);
-                stn(pm.hout[1][1] + oy, S.yH1, L.nval);
+                stw<MASK>(pm.hout[1][0] + oy, S.yH0, L.nval);
+                stw<MASK>(pm.hout[1][1] + oy, S.yH1, L.nval);
             }
             if (HZ && lzq >= 0) {
                 const unsigned oz = L.zoff + (unsigned)lzq * (unsigned)(g.ny * g.pitch);
-                stn(pm.hout[2][0] + oz, S.zH0, L.nval);
-                stn(pm.hout[2][1] + oz, S.zH1, L.nval);
+                stw<MASK>(pm.hout[2][0] + oz, S.zH0, L.nval);
+                stw<MASK>(pm.hout[2][1] + oz, S.zH1, L.nval);
             }
             if (HX && L.xl) {
                 const unsigned ox = L.xoff + (unsigned)q * (unsigned)A.xplane;
-                stn(pm.hout[0][0] + ox, S.xH0, L.nval);
-                stn(pm.hout[0][1] + ox, S.xH1, L.nval);
+                stw<MASK>(pm.hout[0][0] + ox, S.xH0, L.nval);
+                stw<MASK>(pm.hout[0][1] + ox, S.xH1, L.nval);
             }
         }
     }
@@ -572,23 +579,23 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane<V
         if (L.own && q < B.k1) {
             if (B.src_blk) add_source(ez2, A.src, A.ss2, L.c0, L.j, q);
             const unsigned o = (unsigned)L.c0 + (unsigned)L.j * (unsigned)g.pitch + (unsigned)q * (unsigned)g.plane;
-            stn(A.out[0] + o, keep<MASK>(ex2, mq.ex), L.nval);
-            stn(A.out[1] + o, keep<MASK>(ey2, mq.ey), L.nval);
-            stn(A.out[2] + o, keep<MASK>(ez2, mq.ez), L.nval);
+            stw<MASK>(A.out[0] + o, keep<MASK>(ex2, mq.ex), L.nval);
+            stw<MASK>(A.out[1] + o, keep<MASK>(ey2, mq.ey), L.nval);
+            stw<MASK>(A.out[2] + o, keep<MASK>(ez2, mq.ez), L.nval);
             if (yl) {
                 const unsigned oy = L.yoff + (unsigned)q * (unsigned)(pm.W * g.pitch);
-                stn(A.eout[1][0] + oy, S.yE0, L.nval);
-                stn(A.eout[1][1] + oy, S.yE1, L.nval);
+                stw<MASK>(A.eout[1][0] + oy, S.yE0, L.nval);
+                stw<MASK>(A.eout[1][1] + oy, S.yE1, L.nval);
             }
             if (HZ && lzq >= 0) {
                 const unsigned oz = L.zoff + (unsigned)lzq * (unsigned)(g.ny * g.pitch);
-                stn(A.eout[2][0] + oz, S.zE0, L.nval);
-                stn(A.eout[2][1] + oz, S.zE1, L.nval);
+                stw<MASK>(A.eout[2][0] + oz, S.zE0, L.nval);
+                stw<MASK>(A.eout[2][1] + oz, S.zE1, L.nval);
             }
             if (HX && L.xl) {
                 const unsigned ox = L.xoff + (unsigned)q * (unsigned)A.xplane;
-                stn(A.eout[0][0] + ox, S.xE0, L.nval);
-                stn(A.eout[0][1] + ox, S.xE1, L.nval);
+                stw<MASK>(A.eout[0][0] + ox, S.xE0, L.nval);
+                stw<MASK>(A.eout[0][1] + ox, S.xE1, L.nval);
             }
         }
     }
