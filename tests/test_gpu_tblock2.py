@@ -167,3 +167,20 @@ def test_detectors_moved_between_calls(fd):
     assert np.linalg.norm(a - b) / np.linalg.norm(b) <= TOL
     sim.close()
     ref.close()
+
+
+def test_many_detectors_in_one_tile(fd):
+    """Detectors on every node of a row segment inside one tile: more records
+    on one plane of one block than the block has threads (5 per detector on
+    plane k, 1 on plane k-1), so the record service takes several rounds."""
+    steps = 30
+    w = _seam_workload(250, 60, 80, 10, steps)
+    j, k = 26, 36
+    pts = [(i, j, k) for i in range(20, 116)] + [(i, j + 1, k) for i in range(20, 116)]
+    w.probes_xyz = np.array(pts, dtype=np.float64) * w.dx
+    fa, ta, name = _run(fd, w, 2, [steps])
+    assert name.startswith("tblock2")
+    fb, tb, _ = _run(fd, w, 1, [steps])
+    assert len(pts) * 5 > 352
+    _agree(fa, fb, ta, tb)
+
