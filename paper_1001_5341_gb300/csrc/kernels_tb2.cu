@@ -29,18 +29,34 @@
 // faces, are zero, as the one-step paths leave them.
 //
 // z march.  Iteration p (from k0-2 to k1) waits for input plane p+1 (TMA ring
-// of stages, one mbarrier each, bounded waits), then:
+// of stages, bounded waits), then:
 //   A  level-1 H at plane p (planes p, p+1 of the stage);
-//   -- barrier --
 //   B  level-1 E at plane p (level-1 H of plane p-1 kept in registers);
 //   C  level-2 H at plane q = p-1 (level-1 E of plane p-1 kept in registers,
 //      and of plane p from B);
-//   -- barrier --
 //   D  level-2 E at plane q (level-2 H of plane q-1 kept in registers);
 //      stores of the owned H and E of plane q.
-// Exchange rows: A writes Hx, Hz of its row for B (row below); D writes the
-// level-1 Ex, Ez of plane p for the next iteration's C (row above); C writes
-// level-2 Hx, Hz for D (row below).
+// Exchange rows: A writes Hx, Hz of its row for B of the warp above (two
+// buffers, by the parity of p); C writes level-2 Hx, Hz for D of the warp
+// above; D writes the level-1 Ex, Ez of plane p for the next iteration's C
+// of the warp below.
+//
+// Synchronisation.  No block barrier inside the march: a row warp signals an
+// mbarrier of its own when its row of an exchange buffer is written and
+// waits only for the rows it reads (B for A's row below, D for C's row
+// below, and before signalling its A row, for the B row above from the last
+// iteration, which C reads).  Those waits also order every rewrite of a row
+// after its reads: warp w rewrites its A row of one parity two iterations
+// later, after it has seen the warp above finish the iteration in between;
+// its C row one iteration later, after the warp above read it (that warp's D
+// precedes its B-row signal); its B row after the warp below finished its C,
+// which D waits for.  A barrier's waits are parity waits, so its phase must
+// never run two ahead of a waiter: the warp above cannot finish iteration p
+// (B waits for this warp's A row of p) before this warp has waited for its
+// B row of p-1, and likewise for the other rows.  A twelfth warp refills the
+// ring: plane r goes into the stage of plane r - ns once every row warp has
+// signalled that stage empty.  Every wait is bounded; a warp whose wait
+// expires stops, and the warps that wait for it stop in turn.
 //
 // CPML.  The first step of a halo cell needs the CPML memory of that cell, so
 // the stages carry psi boxes (x, y, z) where the tile meets a layer.  The
@@ -74,12 +90,20 @@ namespace {
 using namespace tma;
 
 constexpr int TY = 8;                 // owned rows
-constexpr int NWR = TY + 3;           // warps: rows j0-2 .. j0+TY
-constexpr int NT = 32 * NWR;
+constexpr int NWR = TY + 3;           // row warps: rows j0-2 .. j0+TY
+constexpr int NT = 32 * (NWR + 1);    // and one warp that refills the stage ring
 constexpr int BR = TY + 4;            // box rows j0-2 .. j0+TY+1
 constexpr int NSMAX = 8;
-constexpr int BAR_BYTES = 128;
-static_assert(NSMAX * 8 <= BAR_BYTES, "barrier area");
+
+// mbarriers of a block: the stage ring (full: the stage's copies landed;
+// empty: every row warp is done with it) and the exchange rows (a row warp's
+// row of an exchange buffer is written)
+struct Bars {
+    uint64_t full[NSMAX], empty[NSMAX];
+    uint64_t xa[2][NWR], xb[NWR], xc[NWR];
+};
+constexpr int BAR_BYTES = 512;
+static_assert(sizeof(Bars) <= BAR_BYTES, "barrier area");
 
 // Tile geometry for lanes of VW columns (VW = 4: float4 lanes of the wide
 // tiles; VW = 1: scalar lanes of the narrow tiles over the x layers)
@@ -92,7 +116,6 @@ struct Geo {
     static constexpr unsigned FIELD_BYTES = 4u * FIELDS;
     static constexpr int XROW = 2 * TXC;         // exchange floats per warp row (two components)
     static constexpr int XBUF = NWR * XROW;      // one exchange buffer
-    static constexpr int YBUF = NWR * TXC;       // level-1 Ey rows (detector readout)
     // CPML coefficient table (floats): aH, bH, aE, bE of the computed columns,
     // of the rows j0-2 .. j0+TY+1, of the planes kstart .. kstart+zt-1
     static constexpr int CX = 0;
@@ -100,9 +123,10 @@ struct Geo {
     static constexpr int CZ = CY + 4 * BR;
     static constexpr int LO = 4 / VW;            // first owned lane
     static constexpr int HI = 31 - 4 / VW;       // last owned lane
-    // shared memory: barriers, three exchange buffers, the Ey rows, coefficient table, ring
+    // shared memory: barriers, four exchange buffers (A's two, B's, C's),
+    // coefficient table, ring
     __host__ __device__ static constexpr int head_floats(int zt) {
-        return (3 * XBUF + YBUF + CZ + 4 * zt + 31) / 32 * 32;
+        return (4 * XBUF + CZ + 4 * zt + 31) / 32 * 32;
     }
 };
 
@@ -321,32 +345,83 @@ struct RingPos {
     uint32_t ph1;
 };
 
-// The records of plane q from position pc of a block's list (all threads);
+// element e of lane src's vector (every lane of the warp takes part)
+__device__ __forceinline__ float shfl_elem(float v, int src, int) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ float shfl_elem(float4 v, int src, int e) {
+    const float x = __shfl_sync(0xffffffffu, v.x, src), y = __shfl_sync(0xffffffffu, v.y, src);
+    const float z = __shfl_sync(0xffffffffu, v.z, src), w = __shfl_sync(0xffffffffu, v.w, src);
+    return e == 0 ? x : e == 1 ? y : e == 2 ? z : w;
+}
+
+// The records of plane q of the warp's row from position pc of the block's
+// list (every row warp walks the list; a warp serves its own row's records
+// from the level-1 E of plane q it holds, column col in lane col / VW);
 // returns the new position.  Only the instances of blocks with records (REC)
 // carry it.
-__device__ __forceinline__ int serve_records(const int4 *__restrict__ prec, int pend, int pc, int q, int jb, int ib,
-                                          int txc, int xrow, const float *XB, const float *YB, float *pbuf) {
-    const int tid = threadIdx.x;
+template <int VW, typename V>
+__device__ __forceinline__ int serve_records(const int4 *__restrict__ prec, int pend, int pc, int q, int row, int ib,
+                                          const V &ex, const V &ey, const V &ez, float *pbuf) {
+    const int lane = threadIdx.x & 31;
     for (;;) {
-        const int i = pc + tid;
+        const int i = pc + lane;
         const bool live = i < pend;
         const int4 r = live ? prec[i] : make_int4(0, 0, 0, 0);
-        const bool mine = live && r.x == q;   // (q is -1 .. -3 in the first iterations of the bottom chunk)
-        const int cnt = __syncthreads_count(mine);
-        if (mine) {
-            const int ww = r.y - jb, col = r.z - ib, c = r.w & 3;
+        const bool now = live && r.x == q;   // (q is -1 .. -3 in the first iterations of the bottom chunk)
+        const unsigned bal = __ballot_sync(0xffffffffu, now);
+        if (bal) {
+            const int col = r.z - ib, c = r.w & 3;
             // (the host assigns a record to the block that owns its cell; a
-            // record outside the block's rows is skipped, never read out of range)
-            if (ww >= 0 && ww < NWR && col >= 0 && col < txc)
-                pbuf[r.w >> 2] = c == 1 ? YB[ww * txc + col] : XB[ww * xrow + (c == 2 ? txc : 0) + col];
+            // record outside the block's columns is skipped, never read out of range)
+            const bool mine = now && r.y == row && col >= 0 && col < 32 * VW;
+            const int src = mine ? col / VW : lane, e = mine ? col % VW : 0;
+            const float vx = shfl_elem(ex, src, e), vy = shfl_elem(ey, src, e), vz = shfl_elem(ez, src, e);
+            if (mine) pbuf[r.w >> 2] = c == 0 ? vx : c == 1 ? vy : vz;
         }
+        const int cnt = __popc(bal);
         pc += cnt;
-        if (cnt < NT) return pc;
+        if (cnt < 32) return pc;
+    }
+}
+
+// a row warp's signal: its lanes' shared stores before one arrival
+__device__ __forceinline__ void signal(uint64_t *bar) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
+}
+
+// a row warp's wait expired: record it and stop (the warps that wait for
+// this one give up in turn; the refill warp lets the copies in flight land)
+__device__ __forceinline__ bool fail(const Args &A) {
+    if ((threadIdx.x & 31) == 0) atomicOr(A.flags, 1);
+    return false;
+}
+
+// The refill warp (one thread): planes 0 .. ns-1 into the empty ring, then
+// plane r into stage r % ns once every row warp is done with plane r - ns.
+template <int VW>
+__device__ __forceinline__ void refill(const Args &A, const Maps &M, const Blk &B, Bars *bar, float *ring) {
+    for (int r = 0; r < B.ns && r < B.nplanes; ++r) issue_plane<VW>(A, M, B, ring + r * B.stage, &bar->full[r], r);
+    for (int r = B.ns; r < B.nplanes; ++r) {
+        const int s = r % B.ns;
+        if (!mbar_wait(&bar->empty[s], ((r - B.ns) / B.ns) & 1)) {
+            // a row warp stopped: let the copies in flight (planes r-ns ..
+            // r-1) land before the block ends; one that does not land within
+            // these waits may land after it: flag bit 8 (the handle's status
+            // is sticky)
+            atomicOr(A.flags, 1);
+            for (int t = r - B.ns; t < r; ++t) {
+                bool landed = false;
+                for (int n = 0; n < 4 && !landed; ++n) landed = mbar_wait(&bar->full[t % B.ns], (t / B.ns) & 1);
+                if (!landed) atomicOr(A.flags, 8);
+            }
+            return;
+        }
+        issue_plane<VW>(A, M, B, ring + s * B.stage, &bar->full[s], r);
     }
 }
 
 template <int VW, bool HX, bool HY, bool HZ, bool MASK, bool REC>
-__device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane<VW> &L, const Blk &B, uint64_t *bar,
+__device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane<VW> &L, const Blk &B, Bars *bar,
                                       float *ring, float *X, const float *CT, int rel, RingPos &rp,
                                       State<typename Vec<VW>::T> &S, int &pc) {
     typedef typename Vec<VW>::T V;
@@ -354,16 +429,18 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane<V
     constexpr int TXC = G::TXC, BOX = G::BOX, XROW = G::XROW, XBUF = G::XBUF, CX = G::CX, CY = G::CY, CZ = G::CZ;
     const Grid &g = A.g;
     const Cpml &pm = A.pm;
-    const int tid = threadIdx.x, w = L.w;
+    const int w = L.w;
     const int p = B.kstart + rel, q = p - 1;
     const float kH = A.kH, kE = A.kE;
     constexpr bool STAGE_IN_B = HX || HY || HZ;   // B reads E psi from the stage
     bool ok = true;
-    if (rel == 0) ok = mbar_wait(&bar[0], 0);
-    ok = ok && mbar_wait(&bar[rp.s1], rp.ph1);
+    if (rel == 0) ok = mbar_wait(&bar->full[0], 0);
+    ok = ok && mbar_wait(&bar->full[rp.s1], rp.ph1);
+    if (__any_sync(FULL, !ok)) return fail(A);
     const float *s0 = ring + rp.s0 * B.stage;   // plane p
     const float *s1 = ring + rp.s1 * B.stage;   // plane p+1
-    float *XA = X, *XB = X + XBUF, *XC = X + 2 * XBUF, *YB = X + 3 * XBUF;
+    // A's buffer alternates with the plane; B's and C's are single
+    float *XA = X + (rel & 1) * XBUF, *XB = X + 2 * XBUF, *XC = X + 3 * XBUF;
     const int bc0 = VW * L.lane;
     const int lzp = (HZ && p >= 0 && p < g.nz) ? slab_cell(p, g.nz, pm.P) : -1;
     const int lzq = (HZ && q >= 0 && q < g.nz) ? slab_cell(q, g.nz, pm.P) : -1;
@@ -422,34 +499,28 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane<V
         stv(XA + w * XROW + bc0, hx1);
         stv(XA + w * XROW + TXC + bc0, hz1);
     }
-    if (__syncthreads_or(!ok)) {
-        // a wait expired: record it, let the copies in flight land, stop
-        if (tid == 0) {
-            atomicOr(A.flags, 1);
-            // a copy still in flight after these waits may land after the block
-            // ends: flag bit 8 (the handle's status is sticky)
-            for (int r = rel; r < B.nplanes && r < rel + B.ns; ++r) {
-                bool landed = false;
-                for (int t = 0; t < 4 && !landed; ++t) landed = mbar_wait(&bar[r % B.ns], (r / B.ns) & 1);
-                if (!landed) atomicOr(A.flags, 8);
-            }
-        }
-        __syncthreads();
-        return false;
-    }
-    // the barrier orders every thread's reads of stage p before its refill
-    if (!STAGE_IN_B && tid == 0 && rel + B.ns < B.nplanes)
-        issue_plane<VW>(A, M, B, ring + rp.s0 * B.stage, &bar[rp.s0], rel + B.ns);
+    // B's rows of the warp above (level-1 E of plane q, written in the last
+    // iteration's D) before this warp's A rows are signalled: the warp above
+    // cannot finish this iteration before then, so that barrier is never two
+    // phases ahead of this wait; it also tells this warp that the warp above
+    // is done with the A and C rows it rewrites
+    if (w + 1 < NWR && rel >= 1 && __any_sync(FULL, !mbar_wait(&bar->xb[w + 1], (rel - 1) & 1)))
+        return fail(A);
+    signal(&bar->xa[rel & 1][w]);
+    // the warp is done with stage p (read by A, and by B where it carries psi)
+    if (!STAGE_IN_B) signal(&bar->empty[rp.s0]);
 
-    // detector records of plane q: its level-1 E are in the exchange rows (Ex,
-    // Ez) and the Ey rows since the last D; the records of a plane, contiguous
-    // in the block's sorted list, are read and served one per thread
-    if (REC) pc = serve_records(A.prec, B.pend, pc, q, B.j0 - 2, B.i0 - 4, TXC, XROW, XB, YB, A.pbuf);
+    // detector records of plane q of the warp's row: its level-1 E are the
+    // warp's registers of the last iteration; the records of a plane are
+    // contiguous in the block's sorted list
+    if (REC) pc = serve_records<VW>(A.prec, B.pend, pc, q, L.j, B.i0 - 4, S.ex1p, S.ey1p, S.ez1p, A.pbuf);
 
     // ---- B: level-1 E at plane p (rows j0-1 .. j0+TY) ----
     V ex1 = z4, ey1 = z4, ez1 = z4;
     V yE0 = z4, yE1 = z4, zE0 = z4, zE1 = z4, xE0 = z4, xE1 = z4;
     if (w >= 1) {
+        // A's rows of the warp below
+        if (__any_sync(FULL, !mbar_wait(&bar->xa[rel & 1][w - 1], (rel >> 1) & 1))) return fail(A);
         const V hzD = ldv<V>(XA + (w - 1) * XROW + TXC + bc0);   // row j-1
         const V hxD = ldv<V>(XA + (w - 1) * XROW + bc0);
         const float hzL = __shfl_up_sync(FULL, last(hz1), 1);           // column -1 (lane 0: unused)
@@ -486,6 +557,8 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane<V
         ey1 = keep<MASK>(ey1, mp.ey);
         ez1 = keep<MASK>(ez1, mp.ez);
     }
+
+    if (STAGE_IN_B) signal(&bar->empty[rp.s0]);
 
     // ---- C: level-2 H at plane q = p-1 (rows j0-1 .. j0+TY-1) ----
     V hx2 = z4, hy2 = z4, hz2 = z4;
@@ -540,16 +613,13 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane<V
             }
         }
     }
-    __syncthreads();
-    if (STAGE_IN_B && tid == 0 && rel + B.ns < B.nplanes)
-        issue_plane<VW>(A, M, B, ring + rp.s0 * B.stage, &bar[rp.s0], rel + B.ns);
+    signal(&bar->xc[w]);
 
-    // ---- D: level-1 E rows for the next C; level-2 E at plane q (owned rows) ----
-    if (w >= 1) {
-        stv(XB + w * XROW + bc0, ex1);
-        stv(XB + w * XROW + TXC + bc0, ez1);
-        if (REC) stv(YB + w * TXC + bc0, ey1);
-    }
+    // ---- D: level-2 E at plane q (owned rows); level-1 E rows for the next C ----
+    // C's rows of the warp below; every warp from the third up waits for them,
+    // which also tells it that the warp below is done with the B rows it
+    // rewrites at the end of D
+    if (w >= 2 && __any_sync(FULL, !mbar_wait(&bar->xc[w - 1], rel & 1))) return fail(A);
     if (p >= B.k0 + 1 && w >= 2 && w <= TY + 1) {
         const V hzD = ldv<V>(XC + (w - 1) * XROW + TXC + bc0);
         const V hxD = ldv<V>(XC + (w - 1) * XROW + bc0);
@@ -599,6 +669,12 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane<V
             }
         }
     }
+    // level-1 Ex, Ez of plane p for the next iteration's C of the warp below
+    if (w >= 1) {
+        stv(XB + w * XROW + bc0, ex1);
+        stv(XB + w * XROW + TXC + bc0, ez1);
+    }
+    signal(&bar->xb[w]);
     // carry to the next plane
     S.ex1p = ex1; S.ey1p = ey1; S.ez1p = ez1;
     S.hx1p = hx1; S.hy1p = hy1; S.hz1p = hz1;
@@ -616,7 +692,7 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane<V
 }
 
 template <int VW, bool HX, bool HY, bool HZ, bool MASK, bool REC>
-__device__ __forceinline__ void march(const Args &A, const Maps &M, const Lane<VW> &L, const Blk &B, uint64_t *bar,
+__device__ __forceinline__ void march(const Args &A, const Maps &M, const Lane<VW> &L, const Blk &B, Bars *bar,
                                       float *ring, float *X, const float *CT) {
     typedef typename Vec<VW>::T V;
     State<V> S;
@@ -633,7 +709,7 @@ __device__ __forceinline__ void march(const Args &A, const Maps &M, const Lane<V
 // meets a face of the grid
 template <int VW, bool HX, bool HY, bool HZ>
 __device__ __forceinline__ void march_edge(bool edge, const Args &A, const Maps &M, const Lane<VW> &L, const Blk &B,
-                                           uint64_t *bar, float *ring, float *X, const float *CT) {
+                                           Bars *bar, float *ring, float *X, const float *CT) {
     // blocks with detector records run an instance with the record service
     if (B.pbeg < B.pend) {
         if (edge) march<VW, HX, HY, HZ, true, true>(A, M, L, B, bar, ring, X, CT);
@@ -645,7 +721,7 @@ __device__ __forceinline__ void march_edge(bool edge, const Args &A, const Maps 
 }
 template <int VW, bool HX, bool HY>
 __device__ __forceinline__ void march_z(bool hz, bool edge, const Args &A, const Maps &M, const Lane<VW> &L,
-                                        const Blk &B, uint64_t *bar, float *ring, float *X, const float *CT) {
+                                        const Blk &B, Bars *bar, float *ring, float *X, const float *CT) {
     if (hz) march_edge<VW, HX, HY, true>(edge, A, M, L, B, bar, ring, X, CT);
     else march_edge<VW, HX, HY, false>(edge, A, M, L, B, bar, ring, X, CT);
 }
@@ -657,9 +733,9 @@ __device__ __forceinline__ void run_block(const Args &A, const Maps &M, const Ti
     constexpr int TXC = G::TXC, BOX = G::BOX, FIELDS = G::FIELDS, XBUF = G::XBUF, CX = G::CX,
                   CY = G::CY, CZ = G::CZ;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    Bars *bar = reinterpret_cast<Bars *>(smem_raw);
     float *X = reinterpret_cast<float *>(smem_raw + BAR_BYTES);   // exchange rows
-    float *CT = X + 3 * XBUF + G::YBUF;                            // CPML coefficients
+    float *CT = X + 4 * XBUF;                                      // CPML coefficients
     float *ring = X + G::head_floats(A.zt);                        // stage ring
 
     const Grid &g = A.g;
@@ -719,7 +795,16 @@ __device__ __forceinline__ void run_block(const Args &A, const Maps &M, const Ti
     B.ns = min(NSMAX, (A.smem_floats - G::head_floats(A.zt)) / B.stage);
 
     if (tid == 0) {
-        for (int s = 0; s < B.ns; ++s) mbar_init(&bar[s], 1);
+        for (int s = 0; s < B.ns; ++s) {
+            mbar_init(&bar->full[s], 1);
+            mbar_init(&bar->empty[s], NWR);
+        }
+        for (int w = 0; w < NWR; ++w) {
+            mbar_init(&bar->xa[0][w], 1);
+            mbar_init(&bar->xa[1][w], 1);
+            mbar_init(&bar->xb[w], 1);
+            mbar_init(&bar->xc[w], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -750,9 +835,11 @@ __device__ __forceinline__ void run_block(const Args &A, const Maps &M, const Ti
                 CT[CZ + 3 * A.zt + t] = in ? pm.bE[2][k] : 0.f;
             }
     }
-    __syncthreads();
-    if (tid == 0)
-        for (int r = 0; r < B.ns && r < B.nplanes; ++r) issue_plane<VW>(A, M, B, ring + r * B.stage, &bar[r], r);
+    __syncthreads();   // the only block barrier: barriers and coefficients are set
+    if (tid >= 32 * NWR) {
+        if (tid == 32 * NWR) refill<VW>(A, M, B, bar, ring);
+        return;
+    }
 
     Lane<VW> L;
     L.lane = tid & 31;
