@@ -363,13 +363,17 @@ def run_cyl(args):
         g = fd.Cylinder(w.nr, w.nz, w.d, w.dt, w.eps_r, w.boundary, stream=stream)
         if args.cyl_kernel >= 0 or args.seg_rows > 0:
             g.set_kernel(args.cyl_kernel if args.cyl_kernel >= 0 else g.kernel_info["kernel"], args.seg_rows)
-        info = g.kernel_info
-        K = info["steps_per_launch"]
+        K = g.kernel_info["steps_per_launch"]
         steps = args.steps if args.steps else n
         steps = max(K, steps // K * K)
         q_tab, ring_w = fd.cyl_tables(w)
         g.set_shower(q_tab, w.z0, w.bin_dz, w.v, ring_w)
-        g.set_probes(w.probes_rz, args.warmup * K + steps)
+        tune_max = 48 * 2 * K                      # cyl_tune's bound on its steps (2 launches per length)
+        g.set_probes(w.probes_rz, tune_max + args.warmup * K + steps)
+        # segment length by timing real steps (untimed, before the warm-up),
+        # unless a length was given
+        tuned = g.tune(2) if args.seg_rows == 0 and not args.no_cyl_tune else 0
+        info = g.kernel_info
         g.step(args.warmup * K)
         g.sync()
         clocks = ClockSampler(local)
@@ -388,9 +392,10 @@ def run_cyl(args):
         g.sync()
         # spectra of every detector's whole trace (Sec. V) through the C ABI,
         # timed on the same stream
-        trd = torch.empty((w.probes_rz.shape[0], args.warmup * K + steps, 2), dtype=torch.float32,
+        trd = torch.empty((w.probes_rz.shape[0], tune_max + args.warmup * K + steps, 2), dtype=torch.float32,
                           device="cuda")
         g.probes(out=trd)
+        trd = trd[:, :tuned + args.warmup * K + steps].contiguous()   # the steps done
         freqs = np.linspace(10e6, 2e9, 1024)
         th = np.full(trd.shape[0], math.acos(1 / math.sqrt(w.eps_r)))
         fd.trace_spectrum(trd, w.dt, freqs, t0=w.dt, coef=fd.theta_coef(th), stream=stream)
@@ -428,7 +433,7 @@ def run_cyl(args):
         "n_gpus": ws, "steps": steps, "warmup": args.warmup * K,
         "ms_per_step": round(ms / steps, 6), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {**w.describe(), "seed": 4004, **info,
+        "config": {**w.describe(), "seed": 4004, **info, "tuning_steps": tuned,
                    "inputs_vs_l2": f"fields {fset:.3f} GB vs 129 MB L2 (no flush: one timed call)"},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
@@ -907,7 +912,8 @@ def main():
     ap.add_argument("--chunk-planes", type=int, default=0, help="batch: z planes per tile item (0: default)")
     ap.add_argument("--batch-kind", choices=["config4", "small"], default="config4",
                     help="batch workload: 64 grids 64^3 .. 256x256x512, or 256 grids 32^3 .. 96^3")
-    ap.add_argument("--seg-rows", type=int, default=0, help="cyl rows per segment (0: automatic)")
+    ap.add_argument("--seg-rows", type=int, default=0, help="cyl rows per segment (0: tuned by cyl_tune)")
+    ap.add_argument("--no-cyl-tune", action="store_true", help="cyl: keep the library's segment model")
     ap.add_argument("--gemm-profiles", type=int, default=8192, help="gemm: profiles of the serving product")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -93,6 +93,22 @@ int cyl_step(cyl_t h, int n);
  */
 int cyl_set_kernel(cyl_t h, int which, int seg_rows);
 
+/*
+ * Autotuner of the wavefront kernel in use: it advances the simulation with
+ * each candidate segment length (12 rows and up, in steps of 4 to 64, 8 to
+ * 128 and 16 beyond, until the tiles fit one wave of the resident blocks; at
+ * most 48 candidates), `launches` (1..8) launches each, times every launch
+ * on the device and keeps the length of the fastest launch (cyl_kernel_info
+ * reports it).  The steps are real steps of the simulation, recorded by the
+ * detectors; the segment length decides how the work is cut, never what is
+ * computed, so the fields and traces are those of any other length.  Returns
+ * the steps it used in *steps_used (may be null): at most 48 x launches x K.
+ * Nothing to do (0 steps) on the two-kernel path.  FDTD_ERR_CAPACITY, before
+ * any step, if detectors are set and their trace has no room for those
+ * steps; FDTD_ERR_ARG for launches outside 1..8.
+ */
+int cyl_tune(cyl_t h, int launches, int *steps_used);
+
 /* The kernel in use, its steps per launch and rows per segment (any pointer may be null). */
 int cyl_kernel_info(cyl_t h, int *which, int *steps_per_launch, int *seg_rows);
 

@@ -115,6 +115,7 @@ _SIGS = {
     "cyl_set_probes": (_i, [_vp, _pd, _i, _i]),
     "cyl_step": (_i, [_vp, _i]),
     "cyl_set_kernel": (_i, [_vp, _i, _i]),
+    "cyl_tune": (_i, [_vp, _i, _pi]),
     "cyl_kernel_info": (_i, [_vp, _pi, _pi, _pi]),
     "cyl_kernel_name": (C.c_char_p, [_vp]),
     "cyl_steps_done": (_i, [_vp, _pi64]),
@@ -385,7 +386,8 @@ class Simulation:
         return fdtd_kernel_name(self.h).decode()
 
     def set_kernel(self, which: int):
-        """1: fused z-march (default), 0: unfused H sweep then E sweep."""
+        """2: two steps per pass (default on PEC and CPML grids from 2^24 cells),
+        1: one-pass tile z-march (default otherwise), 0: unfused H sweep then E sweep."""
         check(fdtd_set_kernel(self.h, which), "fdtd_set_kernel")
 
     def adjoint_step(self, n=1):
@@ -496,6 +498,12 @@ class Cylinder:
     def set_kernel(self, which: int, seg_rows: int = 0):
         """0: two kernels per step; 1..5: wavefront variants (cyl.h), K steps per launch."""
         check(cyl_set_kernel(self.h, which, seg_rows), "cyl_set_kernel")
+
+    def tune(self, launches: int = 2) -> int:
+        """Segment length of the wavefront kernel by timing real steps (cyl_tune); returns the steps used."""
+        used = C.c_int()
+        check(cyl_tune(self.h, launches, C.byref(used)), "cyl_tune")
+        return used.value
 
     @property
     def kernel_info(self):

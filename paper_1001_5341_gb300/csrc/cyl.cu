@@ -47,6 +47,7 @@ constexpr int PADL = 16;     // zero floats before column 0 (>= the widest left 
 constexpr int MSRC = 8;      // faces one step's deposit may touch (|v| dt / d <= 4)
 constexpr int NW = 4;        // warps per block of the wavefront kernel
 constexpr int LMAX = 1024;   // most rows per segment of the wavefront kernel
+constexpr int TUNE_MAX = 48;  // most segment lengths cyl_tune tries
 constexpr int NO_ROW = 0x3fffffff;   // detector row past the last one
 
 // ---------------------------------------------------------------------------
@@ -184,7 +185,7 @@ struct Wave {
     float *trace;
     int max_steps;
     int *flags;
-    unsigned *tiles;         // tile counter, zero at launch
+    unsigned *tiles;         // [0] next tile, [1] blocks done: zero at launch, the last block zeroes them
     int ntiles;              // segments x groups of NW bands
     int nseg;                // segments; the last one runs to the wall
 };
@@ -602,6 +603,17 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_cyl_wave(Wave A) {
             __syncwarp();
         }
     }
+    // the last block to finish zeroes the counters for the next launch (the
+    // launches of a handle are ordered on its stream), so no memset precedes
+    // a launch
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(A.tiles + 1, 1u) == gridDim.x - 1) {
+            atomicExch(A.tiles, 0u);
+            atomicExch(A.tiles + 1, 0u);
+        }
+    }
 }
 
 struct Variant {
@@ -657,7 +669,7 @@ struct cyl_ctx {
     cudaEvent_t gev;
     cudaGraphExec_t g2k[2];
     bool graph_off;
-    unsigned *d_tiles;       // wavefront tile counter
+    unsigned *d_tiles;       // wavefront tile counters (next tile, blocks done)
     int slots;               // resident blocks of the wavefront kernel in use
 };
 
@@ -919,7 +931,6 @@ void launch_wave(cyl_ctx *h) {
     A.tiles = h->d_tiles;
     A.ntiles = h->nseg * ((h->nbands + NW - 1) / NW);
     A.nseg = h->nseg;
-    note(h, cudaMemsetAsync(h->d_tiles, 0, sizeof(unsigned), h->stream));
     const int grid = std::min(A.ntiles, std::max(1, h->slots));
     v.fn<<<grid, NW * 32, ring_bytes(v), h->stream>>>(A);
     h->launches++;
@@ -974,7 +985,8 @@ int cyl_create(cyl_t *out, int nr, int nz, double d, double dt, double eps_r, in
         rowc[i] = make_float2((float)(h->kE * (i + 0.5) / i), (float)(h->kE * (i - 0.5) / i));
     if (cudaMalloc(&h->block, bytes) != cudaSuccess || cudaMalloc(&h->d_rowc, (nr + 1) * sizeof(float2)) != cudaSuccess ||
         cudaMalloc(&h->d_flags, sizeof(int)) != cudaSuccess || cudaMalloc(&h->d_step, sizeof(long long)) != cudaSuccess ||
-        cudaMalloc(&h->d_tiles, sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&h->d_tiles, 2 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(h->d_tiles, 0, 2 * sizeof(unsigned)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->gev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
@@ -1022,6 +1034,65 @@ int cyl_set_kernel(cyl_t h, int which, int seg_rows) {
     if (!h || which < 0 || which >= kNumKernels || seg_rows < 0) return FDTD_ERR_ARG;
     if (h->status != FDTD_OK) return h->status;
     const int st = configure(h, which, seg_rows);
+    if (st != FDTD_OK && h->status == FDTD_OK) h->status = st;
+    return st;
+}
+int cyl_tune(cyl_t h, int launches, int *steps_used) {
+    if (steps_used) *steps_used = 0;
+    if (!h || launches < 1 || launches > 8) return FDTD_ERR_ARG;
+    if (h->status != FDTD_OK) return h->status;
+    if (h->kernel == 0) return FDTD_OK;   // the two-kernel path has no segments
+    // candidates: 12 rows and up (steps of 4 to 64, 8 to 128, 16 beyond) until
+    // the tiles fit one wave of the resident blocks (longer segments then only
+    // lengthen every tile); at most TUNE_MAX of them
+    const long long bx = (h->nbands + NW - 1) / NW;
+    const long long slots = std::max(1, h->slots);
+    std::vector<int> cand;
+    for (int L = 12; L <= std::min(h->nr + 1, LMAX) && (int)cand.size() < TUNE_MAX;
+         L += L < 64 ? 4 : L < 128 ? 8 : 16) {
+        cand.push_back(L);
+        long long nseg = (h->nr + 1 + L - 1) / L;
+        if (nseg > 1 && (h->nr + 1) % L == 1) --nseg;
+        if (nseg * bx <= slots) break;
+    }
+    const long long need = (long long)cand.size() * launches * h->K;
+    if (h->np > 0 && h->steps + need > h->max_steps) return FDTD_ERR_CAPACITY;
+    std::vector<cudaEvent_t> ev(launches + 1, nullptr);
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            for (auto &f : ev)
+                if (f) cudaEventDestroy(f);
+            return FDTD_ERR_CUDA;
+        }
+    const int kernel = h->kernel;
+    int best = h->L;
+    float best_ms = -1.f;
+    int used = 0;
+    for (int L : cand) {
+        if (configure(h, kernel, L) != FDTD_OK) break;
+        cudaEventRecord(ev[0], h->stream);
+        for (int i = 0; i < launches; ++i) {
+            launch_wave(h);
+            cudaEventRecord(ev[i + 1], h->stream);
+        }
+        used += launches * h->K;
+        if (note(h, cudaEventSynchronize(ev[launches])) != FDTD_OK || h->status != FDTD_OK) break;
+        float ms = -1.f;   // the fastest launch of the candidate
+        for (int i = 0; i < launches; ++i) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess && (ms < 0.f || t < ms)) ms = t;
+        }
+        if (ms >= 0.f && (best_ms < 0.f || ms < best_ms)) {
+            best_ms = ms;
+            best = L;
+        }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    cudaGetLastError();
+    if (steps_used) *steps_used = used;
+    if (h->status != FDTD_OK) return h->status;
+    const int st = configure(h, kernel, best);
     if (st != FDTD_OK && h->status == FDTD_OK) h->status = st;
     return st;
 }

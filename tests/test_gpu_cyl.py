@@ -238,3 +238,51 @@ def test_full_size_grid_on_patches(fd):
             _close(tr[p, :, 1], o.traces()[k, :, 1], what=f"detector {p} E_r")
             n_det += 1
     assert checked > 5000 and n_det >= 2
+
+
+def test_tune_segment_length(fd):
+    """cyl_tune on the 2048 x 2048 grid of Table I: it tries segment lengths
+    from 12 rows until the tiles fit one wave of the resident blocks, keeps
+    one of them, and its steps are real steps: after them and 32 more, the
+    fields and traces agree with an untuned run of the same steps (2e-6: the
+    same arithmetic, up to contraction)."""
+    w = W.cyl_table1(2048, seed=4004)
+    q_tab, ring_w = fd.cyl_tables(w)
+    F = _fields(11, w.nr, w.nz)
+    runs = []
+    for tune in (True, False):
+        g = fd.Cylinder(w.nr, w.nz, w.d, w.dt, w.eps_r, w.boundary)
+        assert g.kernel_info["kernel"] == 3
+        for c in range(3):
+            g.set_field(c, F[c])
+        g.set_shower(q_tab, w.z0, w.bin_dz, w.v, ring_w)
+        g.set_probes(w.probes_rz, 512)
+        if tune:
+            used = g.tune(2)
+            info = g.kernel_info
+            assert used % 8 == 0 and used >= 16 and g.steps_done == used
+            assert info["seg_rows"] >= 12 and info["seg_rows"] % 4 == 0
+        else:
+            g.step(used)
+        g.step(32)
+        g.sync()
+        runs.append(([g.field(c) for c in range(3)], g.probes()[:, :used + 32]))
+        g.close()
+    (fa, ta), (fb, tb) = runs
+    for c in range(3):
+        _close(fa[c], fb[c], tol=2e-6, what=f"comp {c}")
+    _close(ta, tb, tol=2e-6, what="traces")
+
+
+def test_tune_capacity_and_two_kernel_path(fd):
+    d = 0.01
+    g = fd.Cylinder(1024, 1024, d, O.courant_dt(d, 3.17), 3.17)
+    g.set_kernel(3)
+    g.set_probes([[0.1, 0.2]], 7)
+    with pytest.raises(fd.FdtdError):
+        g.tune(2)                       # the trace has no room for the tuning steps (at least 2 x 4)
+    assert g.steps_done == 0
+    with pytest.raises(fd.FdtdError):
+        g.tune(0)
+    g.set_kernel(0)
+    assert g.tune(2) == 0 and g.steps_done == 0
