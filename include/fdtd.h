@@ -227,9 +227,11 @@ const char *fdtd_kernel_name(fdtd_t h);
  *       fields once and writes them once for two steps; CPML and detectors
  *       included; a last odd step of fdtd_step runs on path 1.  PEC and CPML
  *       grids only (FDTD_ERR_ARG on a Mur grid); the default there from
- *       FDTD_TWO_STEP_MIN_CELLS cells (on smaller grids its blocks are too few
- *       to hide their start-up and path 1 is faster: measured 32 against 50
- *       Gcell/s on 128 x 128 x 512, 64 against 57 on 192 x 192 x 768);
+ *       FDTD_TWO_STEP_MIN_CELLS cells, about 12.6 million (on smaller grids
+ *       its blocks are too few to hide their start-up: measured 22 against
+ *       28 Gcell/s for path 1 on 96 x 96 x 384, CPML 10, and 52.5 against
+ *       50.7 on 128 x 128 x 512, where path 1 is faster with thousands of
+ *       detectors in one tile; 69.5 against 52.2 on 160 x 160 x 640);
  *   1 = one pass per step: TMA-staged vector-tile z-march over the whole
  *       grid, CPML included (the default on Mur grids and smaller grids);
  *   0 = one H sweep then one E sweep (the reference path; the adjoint uses
@@ -250,7 +252,7 @@ int fdtd_set_kernel(fdtd_t h, int which);
  * (0.1 % of a step at the default).  FDTD_ERR_ARG for every < 0.
  */
 #define FDTD_WATCHDOG_DEFAULT_STEPS 64
-#define FDTD_TWO_STEP_MIN_CELLS (1LL << 24)
+#define FDTD_TWO_STEP_MIN_CELLS (3LL << 22)
 int fdtd_set_watchdog(fdtd_t h, int every);
 
 /* Human-readable text of a status code (static string). */

@@ -386,7 +386,7 @@ class Simulation:
         return fdtd_kernel_name(self.h).decode()
 
     def set_kernel(self, which: int):
-        """2: two steps per pass (default on PEC and CPML grids from 2^24 cells),
+        """2: two steps per pass (default on PEC and CPML grids from 3 * 2^22 cells),
         1: one-pass tile z-march (default otherwise), 0: unfused H sweep then E sweep."""
         check(fdtd_set_kernel(self.h, which), "fdtd_set_kernel")
 

@@ -47,8 +47,8 @@ def test_spectra_match_exact_solution(nx, nz, R, steps):
     ths = thc + np.radians([-25.0, -15.0, 15.0, 25.0])
     xyz = np.stack([ax + R * np.sin(ths), np.full(4, ax), zm + R * np.cos(ths)], 1)
     sim = fd.Simulation(nx, nx, nz, DX, dt, W.EPS_R_ICE, boundary=fd.FDTD_CPML, npml=NPML)
-    # the default path of a CPML grid: two steps per pass from FDTD_TWO_STEP_MIN_CELLS (2^24) cells
-    assert sim.kernel_name == ("tblock2-120x8" if nx * nx * nz >= 1 << 24 else "fused-vtile-128x8")
+    # the default path of a CPML grid: two steps per pass from FDTD_TWO_STEP_MIN_CELLS (3 * 2^22) cells
+    assert sim.kernel_name == ("tblock2-120x8" if nx * nx * nz >= 3 << 22 else "fused-vtile-128x8")
     sim.set_shower(q, z0, bdz, W.C0, np.array([1.0]), 0)
     sim.set_probes(xyz, steps)
     sim.step(steps)
