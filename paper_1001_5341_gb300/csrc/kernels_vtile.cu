@@ -14,9 +14,10 @@ namespace {
 
 using namespace vt;
 
-__global__ void __launch_bounds__(NT, 1) k_vtile(const Args A, const __grid_constant__ Maps M) {
+// the form without block barriers: NW warps and the refill warp
+__global__ void __launch_bounds__(NT + 32, 1) k_vtile(const Args A, const __grid_constant__ Maps M) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    tile_block(A, M, (int)blockIdx.x, (int)blockIdx.y, smem_raw);
+    tile_block<true, true>(A, M, (int)blockIdx.x, (int)blockIdx.y, smem_raw);
 }
 
 constexpr CUtensorMapL2promotion kPromotion =
@@ -158,7 +159,7 @@ void launch_vtile(fdtd_ctx *h, cudaStream_t s) {
     a.kH = (float)h->kH;
     a.flags = h->d_flags;
     dim3 grid(st->tiles_x * st->tiles_y, st->z.chunks);
-    k_vtile<<<grid, NT, st->smem, s>>>(a, st->maps);
+    k_vtile<<<grid, NT + 32, st->smem, s>>>(a, st->maps);
 }
 
 }  // namespace fdtd

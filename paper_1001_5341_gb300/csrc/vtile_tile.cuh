@@ -114,7 +114,7 @@ constexpr int HR = BY + 1;             // rows jb-1 .. jb+BY-1 (coefficient tabl
 // jb .. jb+BY-1
 constexpr int HS_X = 0, HS_Z = BY * TXC, HS_ZC = 2 * BY * TXC, HS_YC = HS_ZC + BY;
 constexpr int HSB = (HS_YC + BY + 31) / 32 * 32;
-constexpr int BAR_BYTES = 128;
+constexpr int BAR_BYTES = 384;
 // CPML coefficient table: aH, bH, aE, bE of the tile's columns i0-4 .. i0+127
 // (CXN each; column c at c - i0 + 4, 16-byte aligned per lane), of its rows
 // jb-1 .. jb+BY-1 (HR each), of the chunk's planes kstart .. k1-1 (zc each)
@@ -124,7 +124,17 @@ constexpr int CZ = CY + 4 * HR;
 static_assert((PW * 4) % 16 == 0 && (fb_w(0) * 4) % 16 == 0 && (fb_w(1) * 4) % 16 == 0 &&
                   (fb_w(3) * 4) % 16 == 0 && (fb_cb(3) * 4) % 16 == 0,
               "box rows and origins must be multiples of 16 bytes");
-static_assert(NSMAX * 8 <= BAR_BYTES, "barrier area");
+// mbarriers of a block (the ring's full barriers first, which is all the
+// block-barrier form uses): the stage ring (full: the stage's copies landed;
+// empty: every warp that reads it is done), and for the form without block
+// barriers the shared H plane (hrow: a row warp's H row is written; halo: the
+// halo warp's row and column, by plane parity; edone, eall: a row warp's /
+// every row warp's E phase is done, eall by plane parity)
+struct Bars {
+    uint64_t full[NSMAX], empty[NSMAX];
+    uint64_t hrow[BY - 1], halo[2], edone[BY], eall[2];
+};
+static_assert(sizeof(Bars) <= BAR_BYTES, "barrier area");
 static_assert(BY <= 32, "one halo lane per row");
 
 // shared memory: barriers, H plane, coefficient table, then the stage ring
@@ -229,7 +239,25 @@ struct RingPos {
 // lies in one).  A block runs the instance of its case, so the plain update of
 // the CPML-free interior carries no layer code at all.  Returns false when a
 // wait expired (the block then stops).
-template <bool HX, bool HYZ>
+// ---- the form without block barriers (k_vtile): warp-level waits and signals ----
+constexpr unsigned FULLM = 0xffffffffu;
+// a warp's signal: its lanes' shared stores before one arrival
+__device__ __forceinline__ void wsignal(uint64_t *bar) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
+}
+// a bounded wait, taken by the whole warp; false when it expired for any lane
+__device__ __forceinline__ bool wwait(uint64_t *bar, uint32_t parity) {
+    return !__any_sync(FULLM, !mbar_wait(bar, parity));
+}
+// a warp's wait expired: record it and stop (the warps that wait for this
+// one give up in turn; the refill warp lets the copies in flight land)
+__device__ __forceinline__ bool wfail(const Args &A) {
+    if ((threadIdx.x & 31) == 0) atomicOr(A.flags, 1);
+    return false;
+}
+
+template <bool HX, bool HYZ, bool NB>
 __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &L, const Blk &B, uint64_t *bar,
                                       float *ring, float *HS, const float *CT, int rel, RingPos &rp,
                                       float4 &hxp, float4 &hyp) {
@@ -245,6 +273,13 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
     bool ok = true;
     if (rel == 0) ok = mbar_wait(&bar[0], 0);
     ok = ok && mbar_wait(&bar[s1i], rp.ph1);
+    Bars *vb = reinterpret_cast<Bars *>(bar);
+    if (NB) {
+        if (__any_sync(FULLM, !ok)) return wfail(A);
+        // the halo warp rewrites this parity's halo row and column once every
+        // row warp is done with them (its E phase two planes back)
+        if (!L.roww && rel >= 2 && !wwait(&vb->eall[rel & 1], ((rel >> 1) - 1) & 1)) return wfail(A);
+    }
     float *H = HS + (rel & 1) * HSB;          // this plane's shared H plane
     const float *s0 = ring + s0i * B.stage;   // plane k
     const float *s1 = ring + s1i * B.stage;   // plane k+1
@@ -395,7 +430,23 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
             H[HS_ZC + b - 1] = hz - kH * (dxEy - dyEx);
         }
     }
-    if (__syncthreads_or(!ok)) {
+    if (NB) {
+        if (L.roww) {
+            // before its H row is signalled, a row warp waits until the warp
+            // above is done with its E phase of the last plane: the warp above
+            // then cannot finish this plane's E before this warp's later waits,
+            // so no barrier runs two phases ahead of a wait, and its next
+            // rewrite of this parity's row comes after that E phase read it
+            if (L.w < BY - 1) {
+                if (rel >= 1 && !wwait(&vb->edone[L.w + 1], (rel - 1) & 1)) return wfail(A);
+                wsignal(&vb->hrow[L.w]);
+            }
+            if (!STAGE_IN_E) wsignal(&vb->empty[s0i]);
+        } else {
+            wsignal(&vb->halo[rel & 1]);
+            wsignal(&vb->empty[s0i]);   // the halo warp reads the stage in the H phase only
+        }
+    } else if (__syncthreads_or(!ok)) {
         // a wait expired: record it, let the copies in flight land, stop
         if (tid == 0) {
             atomicOr(A.flags, 1);
@@ -413,10 +464,16 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
     }
     // the block barrier above orders every thread's reads of the stage
     // before the refill (the release/acquire a consumer barrier would give)
-    if (!STAGE_IN_E && tid == 0 && rel + B.ns < B.nplanes)
+    if (!NB && !STAGE_IN_E && tid == 0 && rel + B.ns < B.nplanes)
         issue_plane(A, M, B, ring + s0i * B.stage, &bar[s0i], rel + B.ns);
 
     // ---- E phase ----
+    // the H row below (the warp below's, or the halo warp's for row 0) and
+    // the halo column
+    if (NB && L.roww) {
+        if (L.w >= 1 && !wwait(&vb->hrow[L.w - 1], rel & 1)) return wfail(A);
+        if (!wwait(&vb->halo[rel & 1], (rel >> 1) & 1)) return wfail(A);
+    }
     if (L.roww && own) {
         const int br = L.w + 1;
         const float4 hzD = lds4(H + HS_Z + L.w * TXC + 4 * L.lane);   // row j-1
@@ -484,7 +541,13 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
         }
     }
     if (L.roww) { hxp = hxn; hyp = hyn; }
-    if (STAGE_IN_E) {
+    if (NB) {
+        if (L.roww) {
+            if (STAGE_IN_E) wsignal(&vb->empty[s0i]);
+            wsignal(&vb->edone[L.w]);
+            wsignal(&vb->eall[rel & 1]);
+        }
+    } else if (STAGE_IN_E) {
         __syncthreads();  // the E psi of plane k are read: its stage is free
         if (tid == 0 && rel + B.ns < B.nplanes) issue_plane(A, M, B, ring + s0i * B.stage, &bar[s0i], rel + B.ns);
     }
@@ -497,7 +560,7 @@ __device__ __forceinline__ bool plane(const Args &A, const Maps &M, const Lane &
     return true;
 }
 
-template <bool HX, bool HYZ>
+template <bool HX, bool HYZ, bool NB>
 __device__ __forceinline__ void march(const Args &A, const Maps &M, const Lane &L, const Blk &B, uint64_t *bar,
                                       float *ring, float *HS, const float *CT) {
     float4 hxp = make_float4(0.f, 0.f, 0.f, 0.f), hyp = hxp;   // own H^{n+1/2}(k-1) Hx, Hy
@@ -506,11 +569,34 @@ __device__ __forceinline__ void march(const Args &A, const Maps &M, const Lane &
     // a warm-up plane in a z layer (stages without z boxes) needs the layer
     // code once
     if (!HYZ && B.kstart < B.k0 && slab_cell(B.kstart, A.g.nz, A.pml.P) >= 0) {
-        if (!plane<HX, true>(A, M, L, B, bar, ring, HS, CT, rel, rp, hxp, hyp)) return;
+        if (!plane<HX, true, NB>(A, M, L, B, bar, ring, HS, CT, rel, rp, hxp, hyp)) return;
         ++rel;
     }
     for (; B.kstart + rel < B.k1; ++rel)
-        if (!plane<HX, HYZ>(A, M, L, B, bar, ring, HS, CT, rel, rp, hxp, hyp)) return;
+        if (!plane<HX, HYZ, NB>(A, M, L, B, bar, ring, HS, CT, rel, rp, hxp, hyp)) return;
+}
+
+// The refill warp of the form without block barriers (one thread): planes
+// 0 .. ns-1 into the empty ring, then plane r into stage r % ns once every
+// warp that reads the stage is done with plane r - ns.
+__device__ __forceinline__ void refill(const Args &A, const Maps &M, const Blk &B, Bars *vb, float *ring) {
+    for (int r = 0; r < B.ns && r < B.nplanes; ++r) issue_plane(A, M, B, ring + r * B.stage, &vb->full[r], r);
+    for (int r = B.ns; r < B.nplanes; ++r) {
+        const int s = r % B.ns;
+        if (!mbar_wait(&vb->empty[s], ((r - B.ns) / B.ns) & 1)) {
+            // a warp stopped: let the copies in flight (planes r-ns .. r-1)
+            // land before the block ends; one that does not land within these
+            // waits may land after it: flag bit 8 (the handle's status is sticky)
+            atomicOr(A.flags, 1);
+            for (int t = r - B.ns; t < r; ++t) {
+                bool landed = false;
+                for (int n = 0; n < 4 && !landed; ++n) landed = mbar_wait(&vb->full[t % B.ns], (t / B.ns) & 1);
+                if (!landed) atomicOr(A.flags, 8);
+            }
+            return;
+        }
+        issue_plane(A, M, B, ring + s * B.stage, &vb->full[s], r);
+    }
 }
 
 // One block's tile: tile column and row `tile` (row-major over tiles_x), z
@@ -523,9 +609,20 @@ __device__ __forceinline__ void march(const Args &A, const Maps &M, const Lane &
 // LAYERS false: a grid without CPML layers (only the plain instance is
 // compiled in, which keeps the register count of a caller that reads A from
 // memory within a block of NW warps).
-template <bool LAYERS = true>
+// NB true: the form without block barriers in the march, for a block of NW
+// warps plus a refill warp (NT + 32 threads): each row warp waits only for
+// the H rows it reads (the warp below's, the halo warp's) and signals its
+// own; the halo warp waits until every row warp is done with its row and
+// column of two planes back; the refill warp reloads a stage once every warp
+// that reads it has signalled it empty.  The waits are parity waits and the
+// order of waits and signals keeps every barrier within one phase of its
+// waiters (checked on a CPU model of the warps, tests/test_tb2_sync_cpu.py).
+// NB false: two block barriers per plane at most; the block's thread 0
+// refills (the batch kernel, blocks of NT threads).
+template <bool LAYERS = true, bool NB = false>
 __device__ __forceinline__ int tile_block(const Args &A, const Maps &M, int tile, int chunk,
                                           unsigned char *smem_raw) {
+    constexpr int NTB = NB ? NT + 32 : NT;   // threads of the block
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
     float *HS = reinterpret_cast<float *>(smem_raw + BAR_BYTES);  // two shared H planes
     float *CT = HS + 2 * HSB;                                     // CPML coefficient table
@@ -586,13 +683,23 @@ __device__ __forceinline__ int tile_block(const Args &A, const Maps &M, int tile
     B.ns = min(NSMAX, A.ring / B.stage);
 
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    Bars *vb = reinterpret_cast<Bars *>(smem_raw);
     if (tid == 0) {
         for (int s = 0; s < B.ns; ++s) mbar_init(&bar[s], 1);
+        if (NB) {
+            for (int s = 0; s < B.ns; ++s) mbar_init(&vb->empty[s], NW);
+            for (int w = 0; w < BY - 1; ++w) mbar_init(&vb->hrow[w], 1);
+            for (int w = 0; w < BY; ++w) mbar_init(&vb->edone[w], 1);
+            for (int b = 0; b < 2; ++b) {
+                mbar_init(&vb->halo[b], 1);
+                mbar_init(&vb->eall[b], BY);
+            }
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (P > 0) {
-        for (int t = tid; t < CXN; t += NT) {
+        for (int t = tid; t < CXN; t += NTB) {
             const int i = B.i0 - 4 + t;
             const bool in = i >= 0 && i < g.nx;
             CT[t] = in ? pm.aH[0][i] : 0.f;
@@ -600,7 +707,7 @@ __device__ __forceinline__ int tile_block(const Args &A, const Maps &M, int tile
             CT[2 * CXN + t] = in ? pm.aE[0][i] : 0.f;
             CT[3 * CXN + t] = in ? pm.bE[0][i] : 0.f;
         }
-        for (int t = tid; t < HR; t += NT) {
+        for (int t = tid; t < HR; t += NTB) {
             const int j = B.jb - 1 + t;
             const bool in = j >= 0 && j < g.ny;
             CT[CY + t] = in ? pm.aH[1][j] : 0.f;
@@ -608,7 +715,7 @@ __device__ __forceinline__ int tile_block(const Args &A, const Maps &M, int tile
             CT[CY + 2 * HR + t] = in ? pm.aE[1][j] : 0.f;
             CT[CY + 3 * HR + t] = in ? pm.bE[1][j] : 0.f;
         }
-        for (int t = tid; t < A.zc; t += NT) {
+        for (int t = tid; t < A.zc; t += NTB) {
             const int k = B.kstart + t;
             const bool in = k < B.k1;
             CT[CZ + t] = in ? pm.aH[2][k] : 0.f;
@@ -618,8 +725,14 @@ __device__ __forceinline__ int tile_block(const Args &A, const Maps &M, int tile
         }
     }
     __syncthreads();
-    if (tid == 0)
+    if (NB) {
+        if (tid >= NT) {   // the refill warp
+            if (tid == NT) refill(A, M, B, vb, ring);
+            return B.ns;
+        }
+    } else if (tid == 0) {
         for (int r = 0; r < B.ns && r < B.nplanes; ++r) issue_plane(A, M, B, ring + r * B.stage, &bar[r], r);
+    }
 
     Lane L;
     L.lane = tid & 31;
@@ -655,13 +768,13 @@ __device__ __forceinline__ int tile_block(const Args &A, const Maps &M, int tile
     }
 
     if (!LAYERS) {
-        march<false, false>(A, M, L, B, bar, ring, HS, CT);
+        march<false, false, NB>(A, M, L, B, bar, ring, HS, CT);
     } else if (B.hy || B.hz) {
-        if (B.hx) march<true, true>(A, M, L, B, bar, ring, HS, CT);
-        else march<false, true>(A, M, L, B, bar, ring, HS, CT);
+        if (B.hx) march<true, true, NB>(A, M, L, B, bar, ring, HS, CT);
+        else march<false, true, NB>(A, M, L, B, bar, ring, HS, CT);
     } else {
-        if (B.hx) march<true, false>(A, M, L, B, bar, ring, HS, CT);
-        else march<false, false>(A, M, L, B, bar, ring, HS, CT);
+        if (B.hx) march<true, false, NB>(A, M, L, B, bar, ring, HS, CT);
+        else march<false, false, NB>(A, M, L, B, bar, ring, HS, CT);
     }
     return B.ns;
 }
