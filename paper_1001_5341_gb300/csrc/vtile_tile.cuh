@@ -31,15 +31,20 @@
 //     column i0-1 (Hy, Hz).  Hx, Hz of the rows a warp below needs and the
 //     halo go to a shared H plane (two of them, used by alternate planes);
 //     own H is stored to global memory.
-//   barrier
 //   E phase: E^{n+1}(k) from the H plane (neighbour j-1), the lane to the
 //     left (neighbour i-1, a warp shuffle) and the own H^{n+1/2}(k-1) Hx, Hy
 //     kept in registers; stored.
-// Each thread waits on the mbarrier of the stages it reads itself, so the
-// barrier in the middle of the plane is the only one a block without CPML
-// boxes needs: after it no thread reads the stage of plane k, which is
-// refilled with plane k+ns at once.  Blocks with CPML boxes read E psi from
-// the stage in the E phase and refill it after a second barrier.
+// Each thread waits on the mbarrier of the stages it reads itself.  Between
+// the phases the body has two forms (tile_block's NB):
+//   without block barriers (k_vtile): a row warp's E phase waits only for
+//     the H row below and the halo warp's row and column, each signalled on
+//     an mbarrier of its writer, and a tenth warp refills a stage once every
+//     warp that reads it has signalled it empty (tile_block states the
+//     order of waits that keeps every parity wait within one phase);
+//   with block barriers (the batch kernel): one block barrier between the
+//     phases, after which no thread reads the stage of plane k and thread 0
+//     refills it with plane k+ns; blocks with CPML boxes read E psi from the
+//     stage in the E phase and refill it after a second barrier.
 // A chunk that starts above plane 0 first runs the H phase of plane k0-1
 // without stores.  Every mbarrier wait is bounded; on expiry the block records
 // the failure in a device flag and stops.
